@@ -1,0 +1,286 @@
+"""Plain FP64 CPU oracle of the explicit EM-PIC cycle (KEMPIC-3D, arxiv 2609.16575).
+
+TEST INFRASTRUCTURE ONLY.  The tests, ``__graft_entry__.smoke()`` and the
+CPU-baseline leg of ``bench.py`` may import this package; the product path
+(``paper_2609_16575_gb300``) never does, and the two share no code.
+
+The arithmetic lives in ``pic_oracle.c`` (plain C, FP64, one loop per
+operation).  This module compiles it with gcc, loads it with ctypes and adds
+numpy helpers.  It also holds two closed forms that the tests use as pins and
+inputs: the Yee vacuum eigenmode (``plane_wave``) and the discrete cold-plasma
+frequency of a two-sheets-per-cell lattice (``cold_plasma_omega``).
+
+Array conventions (see the header of ``pic_oracle.c``): a field set is a
+``(9, nz, ny, nx)`` float64 array holding Ex Ey Ez Bx By Bz Jx Jy Jz at their
+Yee locations; a species is a ``(7, np)`` float64 array holding X Y Z (cell
+units), ux uy uz and w.
+
+Parity status of every function: pinned by ``tests/test_oracle_*.py`` against
+closed forms, invariants and the paper's printed values, except where a
+docstring says "parity unpinned".
+"""
+from __future__ import annotations
+
+import ctypes
+import os
+import subprocess
+import threading
+
+import numpy as np
+
+_HERE = os.path.dirname(os.path.abspath(__file__))
+_SRC = os.path.join(_HERE, "pic_oracle.c")
+_BUILD = os.path.join(_HERE, "_build")
+_LIB_PATH = os.path.join(_BUILD, "liboracle.so")
+_lock = threading.Lock()
+_lib = None
+
+_dp = ctypes.POINTER(ctypes.c_double)
+_ip = ctypes.POINTER(ctypes.c_int)
+_lp = ctypes.POINTER(ctypes.c_long)
+
+
+def build(force: bool = False) -> str:
+    """Compile ``pic_oracle.c`` into ``_build/liboracle.so`` (FP64, no FMA contraction)."""
+    os.makedirs(_BUILD, exist_ok=True)
+    if force or not os.path.exists(_LIB_PATH) or os.path.getmtime(_LIB_PATH) < os.path.getmtime(_SRC):
+        tmp = _LIB_PATH + f".tmp{os.getpid()}"
+        cmd = ["gcc", "-O2", "-std=c99", "-fPIC", "-shared", "-ffp-contract=off", "-fno-fast-math",
+               "-o", tmp, _SRC, "-lm"]
+        subprocess.run(cmd, check=True)
+        os.replace(tmp, _LIB_PATH)
+    return _LIB_PATH
+
+
+def lib():
+    global _lib
+    with _lock:
+        if _lib is None:
+            path = build()
+            L = ctypes.CDLL(path)
+            L.or_faraday.argtypes = [_ip, _dp, ctypes.c_double, _dp, _dp, ctypes.c_double]
+            L.or_ampere.argtypes = [_ip, _dp, ctypes.c_double, _dp, _dp, _dp]
+            L.or_gather.argtypes = [_ip, _dp, _dp, _dp, _dp, _dp, _dp]
+            L.or_boris.argtypes = [ctypes.c_double, _dp, _dp, _dp]
+            L.or_boris_orbit.argtypes = [_dp, _dp, ctypes.c_double, ctypes.c_double, _dp, _dp,
+                                         ctypes.c_long, ctypes.c_int, _dp, _dp]
+            L.or_zigzag.argtypes = [_ip, _dp, ctypes.c_double, ctypes.c_double, _dp, _dp, _dp]
+            L.or_rho.argtypes = [_ip, _dp, ctypes.c_double, ctypes.c_long, _dp, _dp]
+            L.or_divergence.argtypes = [_ip, _dp, _dp, _dp]
+            L.or_divergence_b.argtypes = [_ip, _dp, _dp, _dp]
+            L.or_backpush.argtypes = [_ip, _dp, ctypes.c_double, _dp, _dp, ctypes.c_double, ctypes.c_double,
+                                      ctypes.c_long, _dp]
+            L.or_step.argtypes = [_ip, _dp, ctypes.c_double, _dp, ctypes.c_int, _dp, _lp,
+                                  ctypes.POINTER(_dp), _dp]
+            L.or_run.argtypes = [_ip, _dp, ctypes.c_double, _dp, ctypes.c_int, _dp, _lp,
+                                 ctypes.POINTER(_dp), ctypes.c_long, _dp]
+            L.or_gauss_x.argtypes = [_ip, _dp, _dp, _dp]
+            L.or_gauss_x.restype = ctypes.c_double
+            _lib = L
+    return _lib
+
+
+def _p(a: np.ndarray):
+    assert a.dtype == np.float64 and a.flags.c_contiguous
+    return a.ctypes.data_as(_dp)
+
+
+def _grid(n, d):
+    n = np.ascontiguousarray(n, dtype=np.int32)
+    d = np.ascontiguousarray(d, dtype=np.float64)
+    return n, d, n.ctypes.data_as(_ip), _p(d)
+
+
+class Species:
+    """One particle species for the oracle: charge ``q`` and mass ``m`` per physical
+    particle, and a ``(7, np)`` float64 array ``P`` (X, Y, Z in cell units; ux, uy, uz; w)."""
+
+    def __init__(self, q: float, m: float, P: np.ndarray):
+        self.q = float(q)
+        self.m = float(m)
+        self.P = np.ascontiguousarray(P, dtype=np.float64)
+        assert self.P.ndim == 2 and self.P.shape[0] == 7
+
+    @property
+    def n(self) -> int:
+        return self.P.shape[1]
+
+    def copy(self) -> "Species":
+        return Species(self.q, self.m, self.P.copy())
+
+
+def courant_dt(d, courant: float = 0.5) -> float:
+    """Time step at ``courant`` times the 3D Yee CFL limit, section 2.3, Eq. (15)."""
+    d = np.asarray(d, dtype=np.float64)
+    return courant / np.sqrt(np.sum(1.0 / d ** 2))
+
+
+def faraday(n, d, dt, E, B, frac=1.0):
+    """B <- B - frac*dt*curl E (section 2.3, Eq. (13)); E, B are (3, nz, ny, nx)."""
+    n, d, pn, pd = _grid(n, d)
+    lib().or_faraday(pn, pd, dt, _p(E), _p(B), frac)
+
+
+def ampere(n, d, dt, E, B, J):
+    """E <- E + dt (curl B - J) (section 2.3, Eq. (14))."""
+    n, d, pn, pd = _grid(n, d)
+    lib().or_ampere(pn, pd, dt, _p(E), _p(B), _p(J))
+
+
+def gather(n, d, E, B, X):
+    """Staggered CIC interpolation of E and B at one position X (cell units), section 2.5."""
+    n, d, pn, pd = _grid(n, d)
+    X = np.ascontiguousarray(X, dtype=np.float64)
+    Ep = np.zeros(3)
+    Bp = np.zeros(3)
+    lib().or_gather(pn, pd, _p(E), _p(B), _p(X), _p(Ep), _p(Bp))
+    return Ep, Bp
+
+
+def boris(eps, E, B, u):
+    """One relativistic Boris momentum update with eps = q dt / (2 m), section 2.4."""
+    u = np.array(u, dtype=np.float64)
+    lib().or_boris(eps, _p(np.ascontiguousarray(E, dtype=np.float64)),
+                   _p(np.ascontiguousarray(B, dtype=np.float64)), _p(u))
+    return u
+
+
+def boris_orbit(E, B, qm, dt, x0, u0, nsteps, backpush=False):
+    """Single particle in uniform E and B (section 3.1 problems): returns xs, us of
+    shape (nsteps+1, 3); us[k] is u^{k-1/2}."""
+    xs = np.zeros((nsteps + 1, 3))
+    us = np.zeros((nsteps + 1, 3))
+    f = lambda v: np.ascontiguousarray(v, dtype=np.float64)
+    lib().or_boris_orbit(_p(f(E)), _p(f(B)), qm, dt, _p(f(x0)), _p(f(u0)), nsteps, int(backpush), _p(xs), _p(us))
+    return xs, us
+
+
+def zigzag(n, d, dt, qw, X1, X2, J):
+    """Accumulate the zigzag current of one move X1 -> X2 (cell units, X2 unwrapped) into J."""
+    n, d, pn, pd = _grid(n, d)
+    f = lambda v: np.ascontiguousarray(v, dtype=np.float64)
+    lib().or_zigzag(pn, pd, dt, qw, _p(f(X1)), _p(f(X2)), _p(J))
+
+
+def rho(n, d, species, rho_ion=0.0):
+    """Node charge density: CIC of every species plus the uniform background rho_ion."""
+    n, d, pn, pd = _grid(n, d)
+    out = np.full((int(n[2]), int(n[1]), int(n[0])), float(rho_ion))
+    for s in species:
+        lib().or_rho(pn, pd, s.q, s.n, _p(s.P), _p(out))
+    return out
+
+
+def divergence(n, d, F):
+    """Node divergence of an edge-located vector field (3, nz, ny, nx)."""
+    n, d, pn, pd = _grid(n, d)
+    F = np.ascontiguousarray(F, dtype=np.float64)
+    out = np.zeros(F.shape[1:])
+    lib().or_divergence(pn, pd, _p(F), _p(out))
+    return out
+
+
+def divergence_b(n, d, B):
+    """Cell-centre divergence of a face-located field (3, nz, ny, nx)."""
+    n, d, pn, pd = _grid(n, d)
+    B = np.ascontiguousarray(B, dtype=np.float64)
+    out = np.zeros(B.shape[1:])
+    lib().or_divergence_b(pn, pd, _p(B), _p(out))
+    return out
+
+
+def backpush(n, d, dt, E, Bhalf, species):
+    """u^0 -> u^{-1/2} by a backward Boris half step with E^0, B^0 (in place)."""
+    n, d, pn, pd = _grid(n, d)
+    lib().or_backpush(pn, pd, dt, _p(np.ascontiguousarray(E)), _p(np.ascontiguousarray(Bhalf)),
+                      species.q, species.m, species.n, _p(species.P))
+
+
+def run(n, d, dt, F, species, nsteps=1):
+    """Advance the state ``F`` (9, nz, ny, nx) and the species in place by ``nsteps``
+    cycles of Fig. 2.  Returns the (nsteps, 3) energy history (U_E, U_B, K) of the
+    time levels n = 0 .. nsteps-1; on return F[6:9] holds the last J^{n+1/2}."""
+    n, d, pn, pd = _grid(n, d)
+    assert F.dtype == np.float64 and F.flags.c_contiguous and F.shape[0] == 9
+    ns = len(species)
+    qm = np.array([v for s in species for v in (s.q, s.m)], dtype=np.float64)
+    npc = np.array([s.n for s in species], dtype=np.int64)
+    ptrs = (_dp * ns)(*[_p(s.P) for s in species])
+    diag = np.zeros((nsteps, 3))
+    lib().or_run(pn, pd, dt, _p(F), ns, _p(qm), npc.ctypes.data_as(_lp), ptrs, nsteps, _p(diag))
+    return diag
+
+
+def gauss_x(n, d, rho_total):
+    """Ex from Gauss's law for charge varying along x only; returns (E (3,...), worst line mean)."""
+    n, d, pn, pd = _grid(n, d)
+    rho_total = np.ascontiguousarray(rho_total, dtype=np.float64)
+    E = np.zeros((3,) + rho_total.shape)
+    worst = lib().or_gauss_x(pn, pd, _p(rho_total), _p(E))
+    return E, worst
+
+
+def continuity_residual(n, d, dt, rho0, rho1, J):
+    """R = (rho^{n+1} - rho^n)/dt + div J^{n+1/2} at the nodes, Eq. (12) in discrete form."""
+    return (rho1 - rho0) / dt + divergence(n, d, J)
+
+
+def empty_fields(n):
+    return np.zeros((9, n[2], n[1], n[0]), dtype=np.float64)
+
+
+# --------------------------------------------------------------------------
+# Closed forms used as pins and as inputs.
+
+def yee_omega(kvec, d, dt):
+    """Numerical frequency of a vacuum plane wave on the Yee grid:
+    (sin(w dt/2)/dt)^2 = sum_d (sin(k_d d_d/2)/d_d)^2  (the Yee dispersion relation)."""
+    kvec = np.asarray(kvec, dtype=np.float64)
+    d = np.asarray(d, dtype=np.float64)
+    s = np.sqrt(np.sum((np.sin(kvec * d / 2) / d) ** 2))
+    return 2.0 / dt * np.arcsin(s * dt)
+
+
+def plane_wave(n, d, dt, mode, e_hat, amplitude, t_e=0.0):
+    """Exact discrete vacuum eigenmode of the Yee scheme.
+
+    ``mode`` = integer wave numbers (m_x, m_y, m_z) so that k_d = 2 pi m_d / (n_d d_d);
+    ``e_hat`` = real polarisation vector, must be orthogonal to the discrete wave
+    vector kappa_d = (2/d_d) sin(k_d d_d / 2).  Returns E (3,...) at time t_e and
+    B (3,...) at time t_e - dt/2, each component sampled at its own Yee location,
+    E = A e_hat sin(k.x - w t), B = A (kappa x e_hat)/Omega sin(k.x - w t), with
+    Omega = (2/dt) sin(w dt/2) and w from ``yee_omega``."""
+    n = [int(v) for v in n]
+    d = np.asarray(d, dtype=np.float64)
+    k = 2 * np.pi * np.asarray(mode, dtype=np.float64) / (np.asarray(n) * d)
+    w = yee_omega(k, d, dt)
+    kappa = 2.0 / d * np.sin(k * d / 2)
+    e_hat = np.asarray(e_hat, dtype=np.float64)
+    if abs(np.dot(kappa, e_hat)) > 1e-12 * np.linalg.norm(kappa) * np.linalg.norm(e_hat):
+        raise ValueError("polarisation must be orthogonal to the discrete wave vector")
+    Omega = 2.0 / dt * np.sin(w * dt / 2)
+    b_hat = np.cross(kappa, e_hat) / Omega
+    kk, jj, ii = np.meshgrid(np.arange(n[2]), np.arange(n[1]), np.arange(n[0]), indexing="ij")
+    E = np.zeros((3, n[2], n[1], n[0]))
+    B = np.zeros((3, n[2], n[1], n[0]))
+    half_e = [(0.5, 0, 0), (0, 0.5, 0), (0, 0, 0.5)]
+    half_b = [(0, 0.5, 0.5), (0.5, 0, 0.5), (0.5, 0.5, 0)]
+    for c in range(3):
+        he = half_e[c]
+        phase = k[0] * (ii + he[0]) * d[0] + k[1] * (jj + he[1]) * d[1] + k[2] * (kk + he[2]) * d[2]
+        E[c] = amplitude * e_hat[c] * np.sin(phase - w * t_e)
+        hb = half_b[c]
+        phase = k[0] * (ii + hb[0]) * d[0] + k[1] * (jj + hb[1]) * d[1] + k[2] * (kk + hb[2]) * d[2]
+        B[c] = amplitude * b_hat[c] * np.sin(phase - w * (t_e - dt / 2))
+    return E, B, w
+
+
+def cold_plasma_omega(k_cell, dt, omega_p=1.0):
+    """Linear frequency of a cold-plasma Langmuir mode (wave number k_cell per cell)
+    for sheets at cell offsets 1/4 and 3/4, with CIC charge on the nodes, Gauss's
+    law on the edges and staggered linear gather, advanced by leapfrog:
+    w_eff^2 = w_p^2 (1 - sin^2(k/2)/2), then sin(w dt/2) = w_eff dt/2.
+    (Derivation: a sheet pair in cell m sets E(m+1/2) only; the gather weights
+    1/4, 3/4 of the two sheets give the eigenvalue (3 + cos k)/4.)"""
+    w_eff = omega_p * np.sqrt(1.0 - 0.5 * np.sin(k_cell / 2) ** 2)
+    return 2.0 / dt * np.arcsin(w_eff * dt / 2)

@@ -1,0 +1,448 @@
+/*
+ * Plain FP64 CPU oracle of one explicit electromagnetic PIC cycle (KEMPIC-3D,
+ * arxiv 2609.16575).  TEST INFRASTRUCTURE ONLY: this file is built and called by
+ * the tests, by the package's smoke check and by the benchmark's CPU-baseline leg.
+ * The product path never links, loads or calls it, and it shares no code, header
+ * or constant with the CUDA library.
+ *
+ * It is deliberately slow and literal: one loop per operation, no blocking, no
+ * fusion.  Every routine cites the passage of the paper it follows.
+ *
+ * Conventions (the paper's normalised units, section 2.3 and 3.1):
+ *   c = eps0 = mu0 = 1; lengths in c/omega_p, times in 1/omega_p.
+ *   Grid of n[0] x n[1] x n[2] cells with spacings d[0..2], periodic.
+ *   Arrays hold one value per cell, index (k*ny + j)*nx + i, for each Yee
+ *   component at its own staggered location (section 2.3):
+ *     Ex(i+1/2,j,k)  Ey(i,j+1/2,k)  Ez(i,j,k+1/2)       (also Jx, Jy, Jz)
+ *     Bx(i,j+1/2,k+1/2)  By(i+1/2,j,k+1/2)  Bz(i+1/2,j+1/2,k)
+ *   Charge density rho lives on the nodes (i,j,k).
+ *   Particle positions are kept in cell units, X_d = x_d / d_d in [0, n_d);
+ *   momenta are u = gamma v.  A species has charge q and mass m per physical
+ *   particle; a super-particle of weight w carries q w and m w (Eqs. (9)-(11)).
+ *
+ * Time levels (section 2.2, Fig. 2): a state holds E^n, B^{n-1/2}, x^n, u^{n-1/2}.
+ */
+#include <math.h>
+#include <stdlib.h>
+#include <string.h>
+#include <stdint.h>
+
+typedef struct {
+    int n[3];
+    double d[3];
+    double dt;
+} or_grid;
+
+static long wrapi(long i, long n) {
+    long r = i % n;
+    return r < 0 ? r + n : r;
+}
+
+static long cell_index(const or_grid* g, long i, long j, long k) {
+    i = wrapi(i, g->n[0]);
+    j = wrapi(j, g->n[1]);
+    k = wrapi(k, g->n[2]);
+    return (k * g->n[1] + j) * (long)g->n[0] + i;
+}
+
+static long ncells(const or_grid* g) {
+    return (long)g->n[0] * g->n[1] * g->n[2];
+}
+
+/* ------------------------------------------------------------------------ */
+/* Faraday's law on the Yee grid, section 2.3, Eq. (13) for Bx and its cyclic
+ * permutations for By and Bz:  B <- B - frac*dt * curl E.
+ * frac = 1 is one full step B^{n-1/2} -> B^{n+1/2}.                          */
+void or_faraday(const int* n, const double* d, double dt, const double* E, double* B, double frac)
+{
+    or_grid g = {{n[0], n[1], n[2]}, {d[0], d[1], d[2]}, dt};
+    long N = ncells(&g);
+    const double *Ex = E, *Ey = E + N, *Ez = E + 2 * N;
+    double *Bx = B, *By = B + N, *Bz = B + 2 * N;
+    double cx = frac * dt / d[0], cy = frac * dt / d[1], cz = frac * dt / d[2];
+    for (long k = 0; k < n[2]; k++)
+        for (long j = 0; j < n[1]; j++)
+            for (long i = 0; i < n[0]; i++) {
+                long c = cell_index(&g, i, j, k);
+                /* Bx(i, j+1/2, k+1/2): -dt/dy [Ez(j+1)-Ez(j)] + dt/dz [Ey(k+1)-Ey(k)] */
+                Bx[c] += -cy * (Ez[cell_index(&g, i, j + 1, k)] - Ez[c])
+                         + cz * (Ey[cell_index(&g, i, j, k + 1)] - Ey[c]);
+                /* By(i+1/2, j, k+1/2): -dt/dz [Ex(k+1)-Ex(k)] + dt/dx [Ez(i+1)-Ez(i)] */
+                By[c] += -cz * (Ex[cell_index(&g, i, j, k + 1)] - Ex[c])
+                         + cx * (Ez[cell_index(&g, i + 1, j, k)] - Ez[c]);
+                /* Bz(i+1/2, j+1/2, k): -dt/dx [Ey(i+1)-Ey(i)] + dt/dy [Ex(j+1)-Ex(j)] */
+                Bz[c] += -cx * (Ey[cell_index(&g, i + 1, j, k)] - Ey[c])
+                         + cy * (Ex[cell_index(&g, i, j + 1, k)] - Ex[c]);
+            }
+}
+
+/* Ampere-Maxwell law on the Yee grid, section 2.3, Eq. (14) for Ex and its
+ * cyclic permutations:  E <- E + dt (curl B - J).                            */
+void or_ampere(const int* n, const double* d, double dt, double* E, const double* B, const double* J)
+{
+    or_grid g = {{n[0], n[1], n[2]}, {d[0], d[1], d[2]}, dt};
+    long N = ncells(&g);
+    double *Ex = E, *Ey = E + N, *Ez = E + 2 * N;
+    const double *Bx = B, *By = B + N, *Bz = B + 2 * N;
+    const double *Jx = J, *Jy = J + N, *Jz = J + 2 * N;
+    double cx = dt / d[0], cy = dt / d[1], cz = dt / d[2];
+    for (long k = 0; k < n[2]; k++)
+        for (long j = 0; j < n[1]; j++)
+            for (long i = 0; i < n[0]; i++) {
+                long c = cell_index(&g, i, j, k);
+                /* Ex(i+1/2, j, k): +dt/dy [Bz(j+1/2)-Bz(j-1/2)] - dt/dz [By(k+1/2)-By(k-1/2)] - dt Jx */
+                Ex[c] += cy * (Bz[c] - Bz[cell_index(&g, i, j - 1, k)])
+                         - cz * (By[c] - By[cell_index(&g, i, j, k - 1)])
+                         - dt * Jx[c];
+                /* Ey(i, j+1/2, k): +dt/dz [Bx(k+1/2)-Bx(k-1/2)] - dt/dx [Bz(i+1/2)-Bz(i-1/2)] - dt Jy */
+                Ey[c] += cz * (Bx[c] - Bx[cell_index(&g, i, j, k - 1)])
+                         - cx * (Bz[c] - Bz[cell_index(&g, i - 1, j, k)])
+                         - dt * Jy[c];
+                /* Ez(i, j, k+1/2): +dt/dx [By(i+1/2)-By(i-1/2)] - dt/dy [Bx(j+1/2)-Bx(j-1/2)] - dt Jz */
+                Ez[c] += cx * (By[c] - By[cell_index(&g, i - 1, j, k)])
+                         - cy * (Bx[c] - Bx[cell_index(&g, i, j - 1, k)])
+                         - dt * Jz[c];
+            }
+}
+
+/* ------------------------------------------------------------------------ */
+/* Staggered cloud-in-cell interpolation, section 2.5: each component is
+ * interpolated from its own Yee location with the first-order B-spline b1
+ * (Eqs. (17)-(18) with b0 clouds).  half[d] = 1 when the component sits at a
+ * half-integer position along d.                                            */
+static double interp_component(const or_grid* g, const double* F, const int half[3], const double X[3])
+{
+    long base[3];
+    double s[3];
+    for (int d = 0; d < 3; d++) {
+        double p = half[d] ? X[d] - 0.5 : X[d];   /* coordinate relative to the sample lattice */
+        double f = floor(p);
+        base[d] = (long)f;
+        s[d] = p - f;
+    }
+    double v = 0.0;
+    for (int c = 0; c < 2; c++)
+        for (int b = 0; b < 2; b++)
+            for (int a = 0; a < 2; a++) {
+                double wgt = (a ? s[0] : 1.0 - s[0]) * (b ? s[1] : 1.0 - s[1]) * (c ? s[2] : 1.0 - s[2]);
+                v += wgt * F[cell_index(g, base[0] + a, base[1] + b, base[2] + c)];
+            }
+    return v;
+}
+
+static const int HALF_E[3][3] = {{1, 0, 0}, {0, 1, 0}, {0, 0, 1}};
+static const int HALF_B[3][3] = {{0, 1, 1}, {1, 0, 1}, {1, 1, 0}};
+
+static void gather(const or_grid* g, const double* E, const double* B, const double X[3], double Ep[3], double Bp[3])
+{
+    long N = ncells(g);
+    for (int c = 0; c < 3; c++) {
+        Ep[c] = interp_component(g, E + c * N, HALF_E[c], X);
+        Bp[c] = interp_component(g, B + c * N, HALF_B[c], X);
+    }
+}
+
+void or_gather(const int* n, const double* d, const double* E, const double* B, const double* X, double* Ep, double* Bp)
+{
+    or_grid g = {{n[0], n[1], n[2]}, {d[0], d[1], d[2]}, 0.0};
+    gather(&g, E, B, X, Ep, Bp);
+}
+
+/* ------------------------------------------------------------------------ */
+/* Relativistic Boris push, section 2.4 (leapfrog Eqs. (19)-(20), Boris 1970):
+ * half electric kick, magnetic rotation, half electric kick.
+ * eps = q dt / (2 m).  u enters as u^{n-1/2} and leaves as u^{n+1/2}.       */
+void or_boris(double eps, const double* E, const double* B, double* u)
+{
+    double um[3], t[3], s[3], up[3], upl[3];
+    for (int c = 0; c < 3; c++) um[c] = u[c] + eps * E[c];
+    double gm = sqrt(1.0 + um[0] * um[0] + um[1] * um[1] + um[2] * um[2]);
+    for (int c = 0; c < 3; c++) t[c] = eps * B[c] / gm;
+    double t2 = t[0] * t[0] + t[1] * t[1] + t[2] * t[2];
+    for (int c = 0; c < 3; c++) s[c] = 2.0 * t[c] / (1.0 + t2);
+    /* u' = u- + u- x t */
+    up[0] = um[0] + (um[1] * t[2] - um[2] * t[1]);
+    up[1] = um[1] + (um[2] * t[0] - um[0] * t[2]);
+    up[2] = um[2] + (um[0] * t[1] - um[1] * t[0]);
+    /* u+ = u- + u' x s */
+    upl[0] = um[0] + (up[1] * s[2] - up[2] * s[1]);
+    upl[1] = um[1] + (up[2] * s[0] - up[0] * s[2]);
+    upl[2] = um[2] + (up[0] * s[1] - up[1] * s[0]);
+    for (int c = 0; c < 3; c++) u[c] = upl[c] + eps * E[c];
+}
+
+static double gamma_of(const double* u)
+{
+    return sqrt(1.0 + u[0] * u[0] + u[1] * u[1] + u[2] * u[2]);
+}
+
+/* Single particle in uniform fields (the verification problems of section 3.1):
+ * physical coordinates (unit cell), nsteps Boris steps, trajectory written to
+ * xs[(nsteps+1)*3] and us[(nsteps+1)*3] (us[k] holds u^{k-1/2}, us[0] the
+ * initial momentum after the optional half back-push).                      */
+void or_boris_orbit(const double* E, const double* B, double qm, double dt, const double* x0, const double* u0,
+                    long nsteps, int backpush, double* xs, double* us)
+{
+    double x[3] = {x0[0], x0[1], x0[2]}, u[3] = {u0[0], u0[1], u0[2]};
+    if (backpush) or_boris(qm * (-0.5 * dt) / 2.0, E, B, u);
+    for (int c = 0; c < 3; c++) { xs[c] = x[c]; us[c] = u[c]; }
+    for (long s = 1; s <= nsteps; s++) {
+        or_boris(qm * dt / 2.0, E, B, u);
+        double g = gamma_of(u);
+        for (int c = 0; c < 3; c++) x[c] += dt * u[c] / g;
+        for (int c = 0; c < 3; c++) { xs[3 * s + c] = x[c]; us[3 * s + c] = u[c]; }
+    }
+}
+
+/* ------------------------------------------------------------------------ */
+/* Charge-conserving current deposition, section 2.5: the zigzag scheme of
+ * Umeda et al. (2003).  Per dimension, in cell units, the move X1 -> X2 is split
+ * at the relay point
+ *     Xr = min( min(i1,i2)+1, max( max(i1,i2), (X1+X2)/2 ) )
+ * into two straight segments, each inside one cell.  A segment with
+ * displacement D (cell units) and midpoint offset W (relative to its cell)
+ * contributes to the 4 x-edges of its cell
+ *     Jx(i+1/2, j+b, k+c) += q w / (dt dy dz) * Dx * [ Wy^(b) Wz^(c) + s_bc Dy Dz / 12 ]
+ * (W^(0) = 1-W, W^(1) = W, s_bc = +1 if b == c else -1), and cyclically for Jy,
+ * Jz.  The product of midpoint weights is Umeda's form; the Dy Dz / 12 term is
+ * the exact charge flux of a straight segment through a trilinear (CIC) charge
+ * cloud (Villasenor & Buneman 1992).  It vanishes for moves in one or two
+ * dimensions (all of the paper's tests) and is what makes the deposit satisfy
+ * the discrete continuity equation (12) exactly for moves in three dimensions,
+ * the property section 2.5 requires of the scheme.
+ * X2 must be unwrapped (|floor(X2) - floor(X1)| <= 1 per dimension).         */
+static void segment_current(const or_grid* g, double qw, const long cell[3], const double D[3], const double W[3], double* J)
+{
+    long N = ncells(g);
+    double C[3] = {qw / (g->dt * g->d[1] * g->d[2]),
+                   qw / (g->dt * g->d[2] * g->d[0]),
+                   qw / (g->dt * g->d[0] * g->d[1])};
+    for (int comp = 0; comp < 3; comp++) {
+        int p = (comp + 1) % 3, r = (comp + 2) % 3;   /* the two transverse dimensions */
+        for (int b = 0; b < 2; b++)
+            for (int c = 0; c < 2; c++) {
+                double wp = b ? W[p] : 1.0 - W[p];
+                double wr = c ? W[r] : 1.0 - W[r];
+                double sgn = (b == c) ? 1.0 : -1.0;
+                double val = C[comp] * D[comp] * (wp * wr + sgn * D[p] * D[r] / 12.0);
+                long idx[3] = {cell[0], cell[1], cell[2]};
+                idx[p] += b;
+                idx[r] += c;
+                J[comp * N + cell_index(g, idx[0], idx[1], idx[2])] += val;
+            }
+    }
+}
+
+static void zigzag(const or_grid* g, double qw, const double X1[3], const double X2[3], double* J)
+{
+    long i1[3], i2[3];
+    double Xr[3], D1[3], D2[3], W1[3], W2[3];
+    for (int d = 0; d < 3; d++) {
+        i1[d] = (long)floor(X1[d]);
+        i2[d] = (long)floor(X2[d]);
+        double lo = (double)((i1[d] < i2[d] ? i1[d] : i2[d]) + 1);
+        double hi = (double)(i1[d] > i2[d] ? i1[d] : i2[d]);
+        double mid = 0.5 * (X1[d] + X2[d]);
+        Xr[d] = fmin(lo, fmax(hi, mid));
+        D1[d] = Xr[d] - X1[d];
+        D2[d] = X2[d] - Xr[d];
+        W1[d] = 0.5 * (X1[d] + Xr[d]) - (double)i1[d];
+        W2[d] = 0.5 * (Xr[d] + X2[d]) - (double)i2[d];
+    }
+    segment_current(g, qw, i1, D1, W1, J);
+    segment_current(g, qw, i2, D2, W2, J);
+}
+
+void or_zigzag(const int* n, const double* d, double dt, double qw, const double* X1, const double* X2, double* J)
+{
+    or_grid g = {{n[0], n[1], n[2]}, {d[0], d[1], d[2]}, dt};
+    zigzag(&g, qw, X1, X2, J);
+}
+
+/* Cloud-in-cell charge density on the nodes, section 2.5 (b1 weights),
+ * rho(i+a, j+b, k+c) += q w / dV * W(dx,a) W(dy,b) W(dz,c).  P holds one
+ * species as 7 rows of np values: X, Y, Z, ux, uy, uz, w.                    */
+void or_rho(const int* n, const double* d, double q, long np, const double* P, double* rho)
+{
+    or_grid g = {{n[0], n[1], n[2]}, {d[0], d[1], d[2]}, 0.0};
+    double dV = d[0] * d[1] * d[2];
+    for (long p = 0; p < np; p++) {
+        double X[3] = {P[p], P[np + p], P[2 * np + p]};
+        long base[3];
+        double s[3];
+        for (int dd = 0; dd < 3; dd++) {
+            double f = floor(X[dd]);
+            base[dd] = (long)f;
+            s[dd] = X[dd] - f;
+        }
+        double qw = q * P[6 * np + p] / dV;
+        for (int c = 0; c < 2; c++)
+            for (int b = 0; b < 2; b++)
+                for (int a = 0; a < 2; a++) {
+                    double wgt = (a ? s[0] : 1.0 - s[0]) * (b ? s[1] : 1.0 - s[1]) * (c ? s[2] : 1.0 - s[2]);
+                    rho[cell_index(&g, base[0] + a, base[1] + b, base[2] + c)] += qw * wgt;
+                }
+    }
+}
+
+/* Discrete divergence at the nodes (backward differences of the edge
+ * components), the operator of Gauss's law (2) and of continuity (12).      */
+void or_divergence(const int* n, const double* d, const double* F, double* out)
+{
+    or_grid g = {{n[0], n[1], n[2]}, {d[0], d[1], d[2]}, 0.0};
+    long N = ncells(&g);
+    for (long k = 0; k < n[2]; k++)
+        for (long j = 0; j < n[1]; j++)
+            for (long i = 0; i < n[0]; i++) {
+                long c = cell_index(&g, i, j, k);
+                out[c] = (F[c] - F[cell_index(&g, i - 1, j, k)]) / d[0]
+                       + (F[N + c] - F[N + cell_index(&g, i, j - 1, k)]) / d[1]
+                       + (F[2 * N + c] - F[2 * N + cell_index(&g, i, j, k - 1)]) / d[2];
+            }
+}
+
+/* Divergence of the magnetic field at the cell centres (i+1/2, j+1/2, k+1/2),
+ * forward differences; zero by construction of the Yee scheme (section 2.3). */
+void or_divergence_b(const int* n, const double* d, const double* B, double* out)
+{
+    or_grid g = {{n[0], n[1], n[2]}, {d[0], d[1], d[2]}, 0.0};
+    long N = ncells(&g);
+    for (long k = 0; k < n[2]; k++)
+        for (long j = 0; j < n[1]; j++)
+            for (long i = 0; i < n[0]; i++) {
+                long c = cell_index(&g, i, j, k);
+                out[c] = (B[cell_index(&g, i + 1, j, k)] - B[c]) / d[0]
+                       + (B[N + cell_index(&g, i, j + 1, k)] - B[N + c]) / d[1]
+                       + (B[2 * N + cell_index(&g, i, j, k + 1)] - B[2 * N + c]) / d[2];
+            }
+}
+
+/* ------------------------------------------------------------------------ */
+/* Initial momentum staggering: a Boris half step backwards in time on the
+ * momentum only, u^0 -> u^{-1/2} (section 2.4, momenta at half-integer times),
+ * with E^0 and B^0 = B^{-1/2} - (dt/2) curl E^0.                             */
+void or_backpush(const int* n, const double* d, double dt, const double* E, const double* Bhalf,
+                 double q, double m, long np, double* P)
+{
+    or_grid g = {{n[0], n[1], n[2]}, {d[0], d[1], d[2]}, dt};
+    long N = ncells(&g);
+    double* B0 = (double*)malloc(sizeof(double) * 3 * N);
+    memcpy(B0, Bhalf, sizeof(double) * 3 * N);
+    or_faraday(n, d, dt, E, B0, 0.5);
+    for (long p = 0; p < np; p++) {
+        double X[3] = {P[p], P[np + p], P[2 * np + p]};
+        double u[3] = {P[3 * np + p], P[4 * np + p], P[5 * np + p]};
+        double Ep[3], Bp[3];
+        gather(&g, E, B0, X, Ep, Bp);
+        or_boris(q * (-0.5 * dt) / (2.0 * m), Ep, Bp, u);
+        P[3 * np + p] = u[0];
+        P[4 * np + p] = u[1];
+        P[5 * np + p] = u[2];
+    }
+    free(B0);
+}
+
+/* ------------------------------------------------------------------------ */
+/* One PIC cycle in the order of Fig. 2 (section 2.2):
+ *   1. B^{n+1/2} = B^{n-1/2} - dt curl E^n                  (Faraday, Eq. (13))
+ *   2. B^n = (B^{n+1/2} + B^{n-1/2}) / 2                     (Eq. (21))
+ *   3. gather E^n, B^n at x^n; Boris u^{n-1/2} -> u^{n+1/2}; x^{n+1} = x^n + dt u/gamma
+ *   4. zigzag J^{n+1/2} from the move x^n -> x^{n+1}         (section 2.5)
+ *   5. E^{n+1} = E^n + dt (curl B^{n+1/2} - J^{n+1/2})       (Ampere, Eq. (14))
+ * F holds 9*N values: Ex Ey Ez Bx By Bz Jx Jy Jz.  On return J holds J^{n+1/2}.
+ * Species s has charge qm[2s], mass qm[2s+1], count np[s] and data P[s] (7 rows).
+ * diag receives the energies of time level n:
+ *   diag[0] = U_E = 1/2 dV sum E^n^2, diag[1] = U_B = 1/2 dV sum B^n^2,
+ *   diag[2] = K = sum w m ((gamma^{n-1/2} + gamma^{n+1/2})/2 - 1).
+ * Particles leaving the periodic box re-enter on the other side.            */
+void or_step(const int* n, const double* d, double dt, double* F, int ns, const double* qm, const long* np,
+             double** P, double* diag)
+{
+    or_grid g = {{n[0], n[1], n[2]}, {d[0], d[1], d[2]}, dt};
+    long N = ncells(&g);
+    double dV = d[0] * d[1] * d[2];
+    double *E = F, *B = F + 3 * N, *J = F + 6 * N;
+
+    double* Bold = (double*)malloc(sizeof(double) * 3 * N);
+    double* Bn = (double*)malloc(sizeof(double) * 3 * N);
+    memcpy(Bold, B, sizeof(double) * 3 * N);
+    or_faraday(n, d, dt, E, B, 1.0);                      /* B now holds B^{n+1/2} */
+    for (long c = 0; c < 3 * N; c++) Bn[c] = 0.5 * (B[c] + Bold[c]);
+
+    double UE = 0.0, UB = 0.0, K = 0.0;
+    for (long c = 0; c < 3 * N; c++) { UE += E[c] * E[c]; UB += Bn[c] * Bn[c]; }
+
+    for (long c = 0; c < 3 * N; c++) J[c] = 0.0;
+    for (int s = 0; s < ns; s++) {
+        double q = qm[2 * s], m = qm[2 * s + 1];
+        double* Ps = P[s];
+        long cnt = np[s];
+        for (long p = 0; p < cnt; p++) {
+            double X1[3] = {Ps[p], Ps[cnt + p], Ps[2 * cnt + p]};
+            double u[3] = {Ps[3 * cnt + p], Ps[4 * cnt + p], Ps[5 * cnt + p]};
+            double w = Ps[6 * cnt + p];
+            double Ep[3], Bp[3];
+            gather(&g, E, Bn, X1, Ep, Bp);
+            double g_old = gamma_of(u);
+            or_boris(q * dt / (2.0 * m), Ep, Bp, u);
+            double g_new = gamma_of(u);
+            K += w * m * (0.5 * (g_old + g_new) - 1.0);
+            double X2[3];
+            for (int dd = 0; dd < 3; dd++) X2[dd] = X1[dd] + dt * u[dd] / (g_new * d[dd]);
+            zigzag(&g, q * w, X1, X2, J);
+            for (int dd = 0; dd < 3; dd++) {
+                double x = X2[dd];
+                if (x >= (double)n[dd]) x -= (double)n[dd];
+                else if (x < 0.0) x += (double)n[dd];
+                if (x >= (double)n[dd]) x = 0.0;   /* x = -tiny + n rounds to n */
+                Ps[dd * cnt + p] = x;
+            }
+            Ps[3 * cnt + p] = u[0];
+            Ps[4 * cnt + p] = u[1];
+            Ps[5 * cnt + p] = u[2];
+        }
+    }
+    or_ampere(n, d, dt, E, B, J);
+    diag[0] = 0.5 * dV * UE;
+    diag[1] = 0.5 * dV * UB;
+    diag[2] = K;
+    free(Bold);
+    free(Bn);
+}
+
+/* Several cycles; diag receives 3 values per step.                          */
+void or_run(const int* n, const double* d, double dt, double* F, int ns, const double* qm, const long* np,
+            double** P, long nsteps, double* diag)
+{
+    for (long s = 0; s < nsteps; s++) or_step(n, d, dt, F, ns, qm, np, P, diag + 3 * s);
+}
+
+/* Gauss's law for an initial state whose charge varies along x only
+ * (section 2.3, Eq. (2) in discrete form): Ex(i+1/2) = Ex(i-1/2) + dx rho(i)
+ * along every x line, with zero line mean.  rho_total includes the ion
+ * background.  Ey = Ez = 0.  Returns the largest |line mean of rho_total|,
+ * which must vanish for the result to satisfy div E = rho exactly.          */
+double or_gauss_x(const int* n, const double* d, const double* rho_total, double* E)
+{
+    or_grid g = {{n[0], n[1], n[2]}, {d[0], d[1], d[2]}, 0.0};
+    long N = ncells(&g);
+    double worst = 0.0;
+    for (long c = 0; c < 3 * N; c++) E[c] = 0.0;
+    for (long k = 0; k < n[2]; k++)
+        for (long j = 0; j < n[1]; j++) {
+            double mean_rho = 0.0;
+            for (long i = 0; i < n[0]; i++) mean_rho += rho_total[cell_index(&g, i, j, k)];
+            mean_rho /= n[0];
+            if (fabs(mean_rho) > worst) worst = fabs(mean_rho);
+            /* Ex(i+1/2) - Ex(i-1/2) = dx rho(i)  <=>  Ex[i] = Ex[i-1] + dx rho(i) */
+            double acc = 0.0, mean_e = 0.0;
+            for (long i = 0; i < n[0]; i++) {
+                acc += d[0] * rho_total[cell_index(&g, i, j, k)];
+                E[cell_index(&g, i, j, k)] = acc;
+                mean_e += acc;
+            }
+            mean_e /= n[0];
+            for (long i = 0; i < n[0]; i++) E[cell_index(&g, i, j, k)] -= mean_e;
+        }
+    return worst;
+}

@@ -1,0 +1,159 @@
+"""Seeded synthetic inputs shaped like the paper's workloads.
+
+This module only draws and lays out numbers: particle positions (in cell units),
+momenta and weights, grid sizes and the time step.  It holds none of the PIC
+method's arithmetic, imports neither the CUDA binding nor the oracle, and is
+the one piece both sides share.
+
+Units are the paper's normalised units (c = eps0 = mu0 = 1, lengths in c/w_p,
+times in 1/w_p); electrons have q = -1, m = 1; a uniform density n = 1 with
+weight w = n dV / ppc gives w_p = 1.  Randomness comes from numpy's PCG64 with
+a fixed seed per workload, so every run sees identical inputs.
+"""
+from __future__ import annotations
+
+from dataclasses import dataclass, field
+
+import numpy as np
+
+
+@dataclass
+class SpeciesInput:
+    q: float
+    m: float
+    P: np.ndarray                      # (7, np) float64: X, Y, Z (cell units), ux, uy, uz, w
+    momenta_at_half_step: bool = True  # False: P holds u^0 and the solver back-pushes to u^{-1/2}
+
+    @property
+    def n(self) -> int:
+        return int(self.P.shape[1])
+
+
+@dataclass
+class Workload:
+    name: str
+    n: tuple                           # cells (nx, ny, nz)
+    d: tuple                           # cell sizes
+    dt: float
+    rho_ion: float
+    species: list = field(default_factory=list)
+    E: np.ndarray | None = None        # optional initial E (3, nz, ny, nx); None = zero
+    B: np.ndarray | None = None        # optional initial B^{-1/2}; None = zero
+    steps: int = 1
+
+    @property
+    def ncells(self) -> int:
+        return int(self.n[0] * self.n[1] * self.n[2])
+
+    @property
+    def nparticles(self) -> int:
+        return sum(s.n for s in self.species)
+
+
+def courant_dt(d, courant=0.5) -> float:
+    """Time step = courant x the 3D CFL limit 1/sqrt(sum 1/d^2)."""
+    d = np.asarray(d, dtype=np.float64)
+    return float(courant / np.sqrt(np.sum(1.0 / d ** 2)))
+
+
+def _lattice(n, per_dim):
+    """Regular lattice: per_dim^3 particles per cell at offsets (2a+1)/(2 per_dim)."""
+    off = (2 * np.arange(per_dim) + 1) / (2.0 * per_dim)
+    axes = [np.add.outer(np.arange(n[dd]), off).ravel() for dd in range(3)]
+    Z, Y, X = np.meshgrid(axes[2], axes[1], axes[0], indexing="ij")
+    return X.ravel(), Y.ravel(), Z.ravel()
+
+
+def cold_plasma(n=16, d=0.1, per_dim=2, amplitude_cells=0.01, courant=0.5, steps=200) -> Workload:
+    """Cold-plasma oscillation: periodic n^3 grid, per_dim^3 electrons per cell on a
+    regular lattice, x-displacement amplitude_cells * dx * sin(2 pi x / L), zero momenta
+    (given at t = 0), immobile neutralising ions.  The initial Ex that balances the
+    displaced charge is left to the caller (it is a Gauss's-law solve)."""
+    nn = (n, n, n)
+    dd = (d, d, d)
+    X, Y, Z = _lattice(nn, per_dim)
+    X = X + amplitude_cells * np.sin(2 * np.pi * X / n)
+    npart = X.size
+    ppc = per_dim ** 3
+    w = np.full(npart, d ** 3 / ppc)
+    P = np.stack([X, Y, Z, np.zeros(npart), np.zeros(npart), np.zeros(npart), w])
+    return Workload("cold_plasma", nn, dd, courant_dt(dd, courant), 1.0,
+                    [SpeciesInput(-1.0, 1.0, P, momenta_at_half_step=False)], steps=steps)
+
+
+def paper_cold_plasma(per_dim=2, v_amp=1e-3, courant=0.5, steps=2000) -> Workload:
+    """The paper's plasma-oscillation setup (section 3.3): L = 2 pi per side, 2 x 2 x 100
+    periodic cells, v_z = v_amp sin(z), quiet lattice start, immobile ions."""
+    nn = (2, 2, 100)
+    L = 2 * np.pi
+    dd = (L / nn[0], L / nn[1], L / nn[2])
+    X, Y, Z = _lattice(nn, per_dim)
+    npart = X.size
+    vz = v_amp * np.sin(Z * dd[2])
+    uz = vz / np.sqrt(1 - vz ** 2)
+    ppc = per_dim ** 3
+    w = np.full(npart, dd[0] * dd[1] * dd[2] / ppc)
+    P = np.stack([X, Y, Z, np.zeros(npart), np.zeros(npart), uz, w])
+    return Workload("paper_cold_plasma", nn, dd, courant_dt(dd, courant), 1.0,
+                    [SpeciesInput(-1.0, 1.0, P, momenta_at_half_step=False)], steps=steps)
+
+
+def thermal(n=(128, 128, 128), d=0.2, ppc=64, u_th=0.05, seed=1235, courant=0.5, steps=100) -> Workload:
+    """Thermal plasma: uniform random positions, Maxwellian momenta u_d ~ N(0, u_th^2)
+    per component (given at the half step), immobile neutralising ions."""
+    nn = tuple(int(v) for v in n)
+    dd = (d, d, d)
+    rng = np.random.Generator(np.random.PCG64(seed))
+    ncell = nn[0] * nn[1] * nn[2]
+    npart = ncell * ppc
+    P = np.empty((7, npart))
+    for dim in range(3):
+        P[dim] = rng.random(npart) * nn[dim]
+        # a draw of exactly n_d cannot happen (random() < 1), but rounding of the
+        # product can; fold it back onto the periodic box
+        P[dim][P[dim] >= nn[dim]] = 0.0
+    for dim in range(3):
+        P[3 + dim] = rng.standard_normal(npart) * u_th
+    P[6] = d ** 3 / ppc
+    return Workload("thermal", nn, dd, courant_dt(dd, courant), 1.0,
+                    [SpeciesInput(-1.0, 1.0, P, momenta_at_half_step=True)], steps=steps)
+
+
+def differentiable(n=32, d=0.2, ppc=16, u_th=0.02, seed=1237, courant=0.5, steps=200) -> Workload:
+    """Particles of the differentiable run (32^3, 16 per cell, u_th = 0.02); the
+    plane-wave field is added by the caller."""
+    wl = thermal((n, n, n), d, ppc, u_th, seed, courant, steps)
+    wl.name = "differentiable"
+    return wl
+
+
+def stress(n=256, d=0.2, ppc=32, u_th=0.1, seed=1238, courant=0.5, steps=1000) -> Workload:
+    """Precision-stress thermal plasma: 256^3, 32 per cell, u_th = 0.1."""
+    wl = thermal((n, n, n), d, ppc, u_th, seed, courant, steps)
+    wl.name = "stress"
+    return wl
+
+
+def quantize_fp32(P: np.ndarray) -> np.ndarray:
+    """Round a species array to what an FP32 cell + offset store can hold: the cell
+    index stays exact, the in-cell offset, momenta and weight become float32 values.
+    An offset that rounds up to 1.0 moves to offset 0 of the next cell."""
+    Q = np.empty_like(P)
+    for dim in range(3):
+        c = np.floor(P[dim])
+        off = (P[dim] - c).astype(np.float32).astype(np.float64)
+        up = off >= 1.0
+        c = c + up
+        off[up] = 0.0
+        Q[dim] = c + off
+    Q[3:7] = P[3:7].astype(np.float32).astype(np.float64)
+    return Q
+
+
+def wrap_positions(P: np.ndarray, n) -> np.ndarray:
+    """Fold positions onto the periodic box [0, n_d)."""
+    Q = P.copy()
+    for dim in range(3):
+        Q[dim] = np.mod(Q[dim], n[dim])
+        Q[dim][Q[dim] >= n[dim]] = 0.0
+    return Q
