@@ -1,0 +1,370 @@
+#!/usr/bin/env python
+"""Benchmark of the GB300 explicit EM-PIC hot path (KEMPIC-3D cycle: Faraday half
+step, fused gather + Boris + zigzag deposit, Faraday half step, Ampere).
+
+Workload: thermal plasma, 128^3 periodic cells, dx = 0.2 c/w_p, 64 electrons per
+cell (134,217,728 particles) at uniform random positions with Maxwellian momenta
+u_th = 0.05 c, immobile ions, dt = 0.5 x Courant, FP32 bulk.  One step = one full
+PIC cycle over every particle and cell.  Prints one JSON line (rank 0).
+
+  python bench.py [--gpus N] [--steps K] [--warmup W] [--impl gbpic|reference]
+
+Under torchrun every rank runs its own replica (the method has no exchange step on
+one GPU; replicas only) and the value is the sum over ranks of particle-steps
+divided by the slowest rank's time.
+"""
+from __future__ import annotations
+
+import argparse
+import hashlib
+import json
+import os
+import statistics
+import subprocess
+import sys
+import tempfile
+import time
+
+import numpy as np
+
+ROOT = os.path.dirname(os.path.abspath(__file__))
+sys.path.insert(0, ROOT)
+
+METRIC = "particle pushes/s incl. deposit (FP32 vs FP64 GPU), % HBM roofline"
+UNIT = "particle-steps/s"
+WORKLOAD = dict(n=(128, 128, 128), d=0.2, ppc=64, u_th=0.05, seed=1235)
+# algorithmic bytes (what the method must move; sorting, ghosts and the fixed-point
+# width of J are overheads counted against the achieved fraction)
+PART_BYTES = {"f32": 60, "f64": 112}       # read cell + 3 offsets + 3 momenta + w, write all but w
+TILE_GRID_BYTES = {"f32": 36, "f64": 72}   # gather reads E, B (24 B) + deposit writes J (12 B) per cell
+STEP_GRID_BYTES = {"f32": 108, "f64": 216}  # + Yee: read E, B, J, write E, B, zero J (72 B)
+
+
+def parse():
+    p = argparse.ArgumentParser()
+    p.add_argument("--gpus", type=int, default=1)
+    p.add_argument("--steps", type=int, default=50)
+    p.add_argument("--warmup", type=int, default=5)
+    p.add_argument("--impl", default="gbpic", choices=["gbpic", "reference"])
+    p.add_argument("--no-e2e", action="store_true")
+    p.add_argument("--no-fp64", action="store_true")
+    p.add_argument("--no-cpu-baseline", action="store_true")
+    p.add_argument("--small", action="store_true", help="32^3 cells instead of 128^3 (smoke)")
+    p.add_argument("--cells", type=int, default=0, help="cells per dimension (profiling cases); 0 = 128")
+    p.add_argument("--sort-every", type=int, default=0, help="tile re-sort cadence passed to the library")
+    return p.parse_args()
+
+
+def peaks():
+    try:
+        with open(os.path.join(ROOT, "MEASURED_PEAKS.json")) as f:
+            pk = json.load(f)
+        return float(pk["hbm_gbs"]), "measured"
+    except Exception:
+        return 6800.0, "fallback"
+
+
+def kernel_source_hash():
+    h = hashlib.sha256()
+    for name in ("push.cu", "pic_internal.cuh"):
+        with open(os.path.join(ROOT, "paper_2609_16575_gb300", "csrc", name), "rb") as f:
+            h.update(f.read())
+    return h.hexdigest()[:16]
+
+
+def committed_traffic(kernel, workload, n_particles):
+    """DRAM bytes per launch of `kernel` from the committed ncu summary, if it was taken
+    on the current kernel source; else None."""
+    path = os.path.join(ROOT, "profiles", f"{kernel}_{workload}.json")
+    try:
+        with open(path) as f:
+            prof = json.load(f)
+    except Exception:
+        return None
+    if prof.get("source_sha") != kernel_source_hash():
+        return None
+    per_particle = prof.get("dram_bytes_per_particle")
+    return None if per_particle is None else per_particle * n_particles
+
+
+class Clocks:
+    """Samples nvidia-smi clocks and throttle reasons while the timed region runs."""
+
+    FIELDS = ("index,clocks.sm,clocks.max.sm,power.draw,clocks_event_reasons.active,"
+              "clocks_event_reasons.hw_slowdown,clocks_event_reasons.hw_thermal_slowdown,"
+              "clocks_event_reasons.sw_thermal_slowdown,clocks_event_reasons.sw_power_cap")
+
+    def __init__(self, index):
+        self.index = index
+        self.proc = None
+        self.tmp = tempfile.NamedTemporaryFile(mode="w+", suffix=".csv", delete=False)
+
+    def __enter__(self):
+        try:
+            self.proc = subprocess.Popen(["nvidia-smi", "-i", str(self.index), f"--query-gpu={self.FIELDS}",
+                                          "--format=csv,noheader,nounits", "-lms", "100"],
+                                         stdout=self.tmp, stderr=subprocess.DEVNULL)
+            time.sleep(0.3)
+        except Exception:
+            self.proc = None
+        return self
+
+    def __exit__(self, *a):
+        if self.proc is not None:
+            time.sleep(0.2)
+            self.proc.terminate()
+            try:
+                self.proc.wait(timeout=5)
+            except Exception:
+                self.proc.kill()
+
+    def summary(self):
+        try:
+            self.tmp.flush()
+            rows = [r.split(",") for r in open(self.tmp.name).read().strip().splitlines() if r.strip()]
+        except Exception:
+            rows = []
+        os.unlink(self.tmp.name)
+        sm, smax, reasons = [], None, set()
+        names = ["hw_slowdown", "hw_thermal_slowdown", "sw_thermal_slowdown", "sw_power_cap"]
+        for r in rows:
+            r = [x.strip() for x in r]
+            try:
+                sm.append(float(r[1]))
+                smax = float(r[2])
+            except (ValueError, IndexError):
+                continue
+            for nm, v in zip(names, r[5:9]):
+                if v.lower() in ("active", "1", "yes"):
+                    reasons.add(nm)
+        if not sm:
+            return None
+        return {"sm_mhz": statistics.median(sm), "sm_max_mhz": smax, "reasons": sorted(reasons), "samples": len(sm)}
+
+
+def make_workload(small, rank, cells=0):
+    from paper_2609_16575_gb300 import workloads as W
+
+    n = (32, 32, 32) if small else (cells,) * 3 if cells else WORKLOAD["n"]
+    return W.thermal(n, WORKLOAD["d"], WORKLOAD["ppc"], WORKLOAD["u_th"], seed=WORKLOAD["seed"] + rank)
+
+
+def cpu_baseline(steps=10, n=32):
+    """The FP64 oracle, as it stands, on a bounded sample of the same workload shape:
+    a 32^3-cell box at 64 per cell (2.1M particles), `steps` cycles, one host core."""
+    import oracle
+    from paper_2609_16575_gb300 import workloads as W
+
+    wl = W.thermal((n, n, n), WORKLOAD["d"], WORKLOAD["ppc"], WORKLOAD["u_th"], seed=WORKLOAD["seed"])
+    sp = [oracle.Species(s.q, s.m, s.P) for s in wl.species]
+    F = oracle.empty_fields(wl.n)
+    oracle.run(wl.n, wl.d, wl.dt, F, sp, 1)    # warm (page-in, library load)
+    t0 = time.perf_counter()
+    oracle.run(wl.n, wl.d, wl.dt, F, sp, steps)
+    dt = time.perf_counter() - t0
+    npart = wl.nparticles
+    return {"value": npart * steps / dt, "unit": UNIT, "cores": 1, "kind": "oracle",
+            "sample": f"thermal {n}^3 cells x 64 ppc ({npart} particles), {steps} cycles, FP64, single thread",
+            "seconds": round(dt, 2)}
+
+
+def run_reference(args):
+    rank = int(os.environ.get("RANK", "0"))
+    if rank != 0:
+        return 0
+    import oracle
+
+    oracle.build()
+    from paper_2609_16575_gb300 import workloads as W
+
+    # each step: one oracle cycle over a 16^3-cell box at 64 per cell (262,144 particles)
+    wl = W.thermal((16, 16, 16), WORKLOAD["d"], WORKLOAD["ppc"], WORKLOAD["u_th"], seed=WORKLOAD["seed"])
+    sp = [oracle.Species(s.q, s.m, s.P) for s in wl.species]
+    F = oracle.empty_fields(wl.n)
+    oracle.run(wl.n, wl.d, wl.dt, F, sp, args.warmup)
+    t0 = time.perf_counter()
+    oracle.run(wl.n, wl.d, wl.dt, F, sp, args.steps)
+    dt = time.perf_counter() - t0
+    value = wl.nparticles * args.steps / dt
+    sample = f"thermal 16^3 cells x 64 ppc ({wl.nparticles} particles) per step, FP64 oracle, single thread"
+    line = {"impl": "reference", "metric": METRIC, "value": value, "unit": UNIT, "n_gpus": args.gpus,
+            "steps": args.steps, "warmup": args.warmup, "ms_per_step": dt / args.steps * 1e3,
+            "higher_is_better": True, "scaling": "weak", "vs_baseline": None, "dtype": "f64", "data": "synthetic",
+            "config": {"workload": "thermal plasma (128^3 x 64 ppc shape), bounded CPU sample", "sample": sample},
+            "cpu_baseline": {"value": value, "unit": UNIT, "cores": 1, "kind": "oracle", "sample": sample},
+            "e2e": {"value": value, "unit": UNIT, "h2d_bytes_per_step": 0, "d2h_bytes_per_step": 0}}
+    print(json.dumps(line), flush=True)
+    return 0
+
+
+def timed_steps(ctx, torch, steps, dist):
+    ctx.set_timing(True)
+    ctx.kernel_times()
+    l0 = ctx.launch_count()
+    if dist is not None:
+        dist.barrier()
+    torch.cuda.synchronize()
+    s = torch.cuda.current_stream()
+    a, b = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+    a.record(s)
+    ctx.step(steps)
+    b.record(s)
+    torch.cuda.synchronize()
+    if dist is not None:
+        dist.barrier()
+    ms = a.elapsed_time(b)
+    launches = ctx.launch_count() - l0
+    kt = ctx.kernel_times()
+    ctx.set_timing(False)
+    ctx.sync()
+    return ms, launches, kt
+
+
+def roofline(kt, dtype, n_particles, ncell, peak, peak_kind, traffic):
+    launches, ms = kt["tile_push"]
+    avg_s = ms / max(launches, 1) / 1e3
+    algo = PART_BYTES[dtype] * n_particles + TILE_GRID_BYTES[dtype] * ncell
+    achieved = algo / avg_s / 1e9
+    return {"bound": "hbm", "achieved": achieved, "peak": peak, "unit": "GB/s", "frac": achieved / peak,
+            "traffic": traffic, "kernel": "k_tile_push", "peak_kind": f"{peak_kind} hbm_gbs (copy)",
+            "algorithmic_bytes_per_launch": algo, "avg_launch_ms": avg_s * 1e3}
+
+
+def run_gbpic(args):
+    import torch
+
+    world = int(os.environ.get("WORLD_SIZE", "1"))
+    rank = int(os.environ.get("RANK", "0"))
+    local = int(os.environ.get("LOCAL_RANK", "0"))
+    dist = None
+    if world > 1:
+        import torch.distributed as dist
+
+        torch.cuda.set_device(local)
+        dist.init_process_group("nccl")
+    else:
+        torch.cuda.set_device(0)
+    import __graft_entry__
+
+    __graft_entry__.build()
+    from paper_2609_16575_gb300 import gbpic
+
+    wl = make_workload(args.small, rank, args.cells)
+    P = wl.species[0].P
+    npart = P.shape[1]
+    ncell = wl.ncells
+    peak, peak_kind = peaks()
+    dev = torch.cuda.current_device()
+
+    # --- FP32, inputs resident in HBM
+    ctx = gbpic.Context(wl.n, wl.d, wl.dt, precision=gbpic.PIC_FP32, rho_ion=wl.rho_ion, device=dev,
+                        sort_every=args.sort_every)
+    ctx.set_fields(None, None)
+    ctx.load_species_array(-1.0, 1.0, P)
+    ctx.step(args.warmup)
+    ctx.sync()
+    with Clocks(dev) as clk:
+        ms, launches, kt = timed_steps(ctx, torch, args.steps, dist)
+    clocks = clk.summary()
+    diag = ctx.diagnostics()
+    ctx.sync()
+    if diag["n_alive"] != npart:
+        raise RuntimeError(f"particles lost: {diag['n_alive']} of {npart}")
+    ctx.close()
+    del ctx
+    ms_all = ms
+    if dist is not None:
+        t = torch.tensor([ms], device="cuda", dtype=torch.float64)
+        dist.all_reduce(t, op=dist.ReduceOp.MAX)
+        ms_all = float(t.item())
+    value = npart * world * args.steps / (ms_all / 1e3)
+    wk = f"thermal{wl.n[0]}"
+    traffic = committed_traffic("tile_push", wk, npart)
+    rl = roofline(kt, "f32", npart, ncell, peak, peak_kind, traffic)
+    step_bytes = PART_BYTES["f32"] + STEP_GRID_BYTES["f32"] / WORKLOAD["ppc"]
+    kernels = {k: {"launches": v[0], "ms": round(v[1], 3)} for k, v in kt.items() if v[0]}
+
+    # --- FP64 GPU path on the same workload
+    fp64 = None
+    if not args.no_fp64:
+        k64 = max(3, args.steps // 10)
+        ctx = gbpic.Context(wl.n, wl.d, wl.dt, precision=gbpic.PIC_FP64, rho_ion=wl.rho_ion, device=dev)
+        ctx.set_fields(None, None)
+        ctx.load_species_array(-1.0, 1.0, P)
+        ctx.step(2)
+        ctx.sync()
+        ms64, _, kt64 = timed_steps(ctx, torch, k64, dist)
+        ctx.close()
+        del ctx
+        v64 = npart * k64 / (ms64 / 1e3)
+        fp64 = {"value": v64 * world, "unit": UNIT, "steps": k64, "ms_per_step": ms64 / k64,
+                "roofline": roofline(kt64, "f64", npart, ncell, peak, peak_kind, None),
+                "step_hbm_frac": v64 * (PART_BYTES["f64"] + STEP_GRID_BYTES["f64"] / WORKLOAD["ppc"]) / 1e9 / peak}
+
+    # --- end to end through the public API: host (pinned) inputs in, diagnostics out
+    e2e = None
+    if not args.no_e2e:
+        pinned = torch.empty(P.shape, dtype=torch.float64, pin_memory=True)
+        pinned.numpy()[:] = P
+        Ph = pinned.numpy()
+        torch.cuda.synchronize()
+        if dist is not None:
+            dist.barrier()
+        t0 = time.perf_counter()
+        ctx = gbpic.Context(wl.n, wl.d, wl.dt, precision=gbpic.PIC_FP32, rho_ion=wl.rho_ion, device=dev)
+        ctx.set_fields(None, None)
+        ctx.load_species_array(-1.0, 1.0, Ph)
+        ctx.step(args.steps)
+        d_e2e = ctx.diagnostics()
+        torch.cuda.synchronize()
+        t_e2e = time.perf_counter() - t0
+        ctx.close()
+        del ctx
+        if dist is not None:
+            t = torch.tensor([t_e2e], device="cuda", dtype=torch.float64)
+            dist.all_reduce(t, op=dist.ReduceOp.MAX)
+            t_e2e = float(t.item())
+        ntile = (wl.n[0] // 8) * (wl.n[1] // 8) * (wl.n[2] // 8)
+        h2d = 7 * 8 * npart + 4 * ntile * 512 + 12 * ntile
+        d2h = 4 * ntile * 512 + 8 * 8 + 4 * ntile
+        e2e = {"value": npart * world * args.steps / t_e2e, "unit": UNIT,
+               "h2d_bytes_per_step": h2d // args.steps, "d2h_bytes_per_step": d2h // args.steps,
+               "includes": "context creation, H2D of the FP64 particle arrays from pinned memory, tile sort, "
+                           f"{args.steps} steps, FP64 diagnostics and their D2H",
+               "check_n_alive": d_e2e["n_alive"] == npart}
+        del pinned
+
+    cpu = None
+    if rank == 0 and world == 1 and not args.no_cpu_baseline:
+        cpu = cpu_baseline()
+
+    if rank == 0:
+        line = {"metric": METRIC, "value": value, "unit": UNIT, "n_gpus": world, "steps": args.steps,
+                "warmup": args.warmup, "ms_per_step": ms_all / args.steps, "higher_is_better": True,
+                "scaling": "weak", "vs_baseline": None, "dtype": "f32", "data": "synthetic",
+                "config": {"workload": (f"thermal plasma {wl.n[0]}^3 periodic, dx=0.2, 64 ppc ({npart:,} electrons), "
+                                        "u_th=0.05, immobile ions, dt=0.5 Courant"),
+                           "sort_every": args.sort_every or 4,
+                           "particles_per_gpu": npart, "cells": ncell, "precision": "fp32 bulk, fp64 reductions",
+                           "parallelism": f"replicas x{world}",
+                           "l2": "inputs larger than L2 (particle SoA 4.3 GB per GPU)"},
+                "roofline": rl,
+                "step_hbm_frac": value / world * step_bytes / 1e9 / peak,
+                "cell_updates_per_s": ncell * world * args.steps / (ms_all / 1e3),
+                "kernels": kernels, "gpu_launches": launches, "clocks": clocks, "e2e": e2e,
+                "cpu_baseline": cpu, "fp64": fp64}
+        print(json.dumps(line), flush=True)
+    if dist is not None:
+        dist.destroy_process_group()
+    return 0
+
+
+def main():
+    args = parse()
+    if args.impl == "reference":
+        return run_reference(args)
+    return run_gbpic(args)
+
+
+if __name__ == "__main__":
+    sys.exit(main())

@@ -1,0 +1,175 @@
+/*
+ * gbpic.h - C ABI of the GB300 (sm_103a) explicit electromagnetic PIC hot path.
+ *
+ * The library advances the cycle of KEMPIC-3D (arxiv 2609.16575, section 2.2,
+ * Fig. 2) on one GPU:
+ *   1. B^{n-1/2} -> B^n            Faraday half step   (section 2.3, Eq. (13))
+ *   2. gather E^n, B^n at x^n      staggered CIC       (section 2.5)
+ *   3. u^{n-1/2} -> u^{n+1/2}      relativistic Boris  (section 2.4, Eqs. (19)-(20))
+ *      x^{n+1} = x^n + dt u / gamma
+ *   4. J^{n+1/2}                   zigzag deposit      (section 2.5, Umeda et al. 2003)
+ *   5. B^n -> B^{n+1/2}            Faraday half step
+ *   6. E^n -> E^{n+1}              Ampere-Maxwell      (section 2.3, Eq. (14))
+ * Steps 1 and 5 together equal the full Faraday step and give exactly the
+ * centred B^n of Eq. (21) in exact arithmetic.
+ *
+ * Units (the paper's normalised units, sections 2.3 and 3.1): c = eps0 = mu0 = 1.
+ * Grid: n[0] x n[1] x n[2] cells of size d[0..2], periodic in every dimension.
+ * Host field arrays are FP64, [component][k][j][i] with i fastest, each component
+ * at its Yee location: Ex(i+1/2,j,k) Ey(i,j+1/2,k) Ez(i,j,k+1/2),
+ * Bx(i,j+1/2,k+1/2) By(i+1/2,j,k+1/2) Bz(i+1/2,j+1/2,k); J like E.
+ * Particle positions are in cell units (X_d = x_d / d_d, 0 <= X_d < n_d).
+ *
+ * Ownership: the context owns every device buffer it allocates.  Host and device
+ * arrays passed in are borrowed for the duration of the call only.  Every entry
+ * point returns a pic_status; nothing aborts and device code never prints.
+ * Calls that enqueue work (pic_set_fields, pic_load_species, pic_step) are
+ * ordered on the context's stream; errors raised by device code surface at the
+ * next synchronising call (pic_sync, pic_get_*, pic_diagnostics).
+ * A context is not thread safe: one host thread at a time.
+ */
+#ifndef GBPIC_H
+#define GBPIC_H
+
+#include <stddef.h>
+#include <stdint.h>
+
+#ifdef __cplusplus
+extern "C" {
+#endif
+
+typedef enum pic_status {
+    PIC_OK = 0,
+    PIC_ERR_ARG = 1,            /* invalid argument (null pointer, bad size, bad species id) */
+    PIC_ERR_CFL = 2,            /* dt violates the 3D CFL bound of Eq. (15) */
+    PIC_ERR_OOM = 3,            /* device allocation failed */
+    PIC_ERR_CUDA = 4,           /* a CUDA runtime call failed; see pic_last_error */
+    PIC_ERR_TILE_OVERFLOW = 5,  /* mover or spill buffer full: particles were lost */
+    PIC_ERR_SUPERLUMINAL = 6,   /* a particle moved more than one cell in one step */
+    PIC_ERR_NAN = 7,            /* a non-finite momentum was produced */
+    PIC_ERR_STATE = 8,          /* call out of order (e.g. species before fields) */
+    PIC_ERR_TIMEOUT = 9,        /* a bounded device-side wait gave up */
+    PIC_ERR_NO_DEVICE = 10      /* no CUDA device, or not an sm_103 device */
+} pic_status;
+
+typedef enum pic_precision { PIC_FP32 = 0, PIC_FP64 = 1 } pic_precision;
+
+typedef struct pic_ctx pic_ctx;  /* opaque */
+
+/* Optional device allocator (e.g. a framework's caching allocator).  When alloc
+ * is NULL the library uses cudaMalloc/cudaFree. */
+typedef void* (*pic_alloc_fn)(size_t bytes, void* user);
+typedef void (*pic_free_fn)(void* ptr, void* user);
+
+typedef struct pic_grid_desc {
+    int32_t n[3];            /* cells per dimension, >= 1 */
+    double d[3];             /* cell sizes (> 0) */
+    double dt;               /* time step; must satisfy Eq. (15): dt <= 1/sqrt(sum 1/d^2) */
+    double rho_ion;          /* uniform immobile background charge density (diagnostics only) */
+    int32_t precision;       /* pic_precision: arithmetic of the whole step */
+    int32_t device;          /* CUDA device ordinal */
+    void* stream;            /* cudaStream_t to enqueue on; NULL: the library creates one */
+    int32_t track_ids;       /* 1: carry each particle's load-order id (pic_get_particles
+                                returns load order); 0: tile order, fewer bytes per step */
+    int32_t record_every;    /* k > 0: record (U_E, U_B, K) of every k-th step on the device */
+    int32_t history_capacity;/* records kept (ring); 0 with record_every > 0 -> 4096 */
+    int32_t sort_every;      /* re-sort each tile segment by cell every k steps (keeps the lanes of
+                                a warp in one cell); 0 -> 4, < 0 -> only at load */
+    pic_alloc_fn alloc;      /* optional */
+    pic_free_fn free;        /* optional, required when alloc is set */
+    void* alloc_user;
+} pic_grid_desc;
+
+/* A particle species (section 2.1, Eqs. (8)-(11)): q, m per physical particle;
+ * a super-particle of weight w carries q w and m w. */
+typedef struct pic_species_desc {
+    double q, m;
+    int64_t n;                     /* particles */
+    const double* X;               /* 3*n: X[0..n) Y[n..2n) Z[2n..3n), cell units, inside the box */
+    const double* u;               /* 3*n: u = gamma v (c = 1), same layout */
+    const double* w;               /* n weights (> 0) */
+    int32_t momenta_at_half_step;  /* 1: u is u^{-1/2}; 0: u is u^0 and the library applies a
+                                      backward Boris half step with E^0, B^0 (section 2.4) */
+    int32_t device_pointers;       /* 1: X, u, w are device pointers */
+    double capacity_slack;         /* tile segment headroom fraction; 0 -> 0.25 */
+} pic_species_desc;
+
+typedef struct pic_diag {
+    int64_t step;            /* steps taken */
+    double t;                /* step * dt */
+    double U_E;              /* 1/2 dV sum E^n^2 */
+    double U_B;              /* 1/2 dV sum B^n^2, B^n = B^{n-1/2} - dt/2 curl E^n (Eq. (21)) */
+    double K_half;           /* sum w m (gamma^{n-1/2} - 1) over all species */
+    double gauss_max;        /* max_nodes |div E^n - rho^n - rho_ion| (Eq. (2)) */
+    double gauss_change_max; /* max_nodes |G^n - G^ref|; G^ref = G at the first pic_diagnostics */
+    double rho_max;          /* max_nodes |rho^n| (electrons + ions) */
+    double cont_max;         /* max_nodes |(rho^n - rho^{n-1})/dt + div J^{n-1/2}| (Eq. (12)) when the
+                                previous pic_diagnostics call was exactly one step earlier, else NaN */
+    double J_max;            /* max |J^{n-1/2}| over components and cells */
+    int64_t n_alive;         /* particles held, all species */
+    int64_t n_spilled;       /* particles currently outside their tile segment (spill list) */
+} pic_diag;
+
+/* Create a context: validates n, d and the CFL bound of Eq. (15) (section 2.3),
+ * allocates the Yee fields (zero) and selects the device.  *out receives the
+ * context, or NULL on failure. */
+pic_status pic_init_grid(const pic_grid_desc* desc, pic_ctx** out);
+
+/* Set E^0 and B^{-1/2} (section 2.3 time staggering).  E and B each hold 3*N FP64
+ * values in the host layout above (N = n0 n1 n2); either may be NULL (zero).
+ * device_pointers = 1: E, B are device pointers.  Must precede pic_load_species
+ * when a species asks for the back-push. */
+pic_status pic_set_fields(pic_ctx* ctx, const double* E, const double* B, int32_t device_pointers);
+
+/* Load a species: converts positions to (cell, in-cell offset) in the working
+ * precision, sorts particles into 8^3-cell tiles, and applies the backward half
+ * push when momenta_at_half_step = 0.  *species_id receives the species index. */
+pic_status pic_load_species(pic_ctx* ctx, const pic_species_desc* desc, int32_t* species_id);
+
+/* Advance nsteps cycles (section 2.2, Fig. 2), asynchronously on the context's
+ * stream.  J of the last cycle is kept for pic_get_fields and pic_diagnostics. */
+pic_status pic_step(pic_ctx* ctx, int32_t nsteps);
+
+/* Wait for the context's stream; returns the first device-side error raised. */
+pic_status pic_sync(pic_ctx* ctx);
+
+/* Copy E^n, B^{n-1/2} and J^{n-1/2} out (3*N FP64 values each, host layout above);
+ * any pointer may be NULL.  Synchronises. */
+pic_status pic_get_fields(pic_ctx* ctx, double* E, double* B, double* J, int32_t device_pointers);
+
+/* Copy one species out as 7 rows of *n FP64 values: X, Y, Z (cell units), ux, uy,
+ * uz, w.  With track_ids the rows are in load order, else in tile order.  out may
+ * be NULL to query *n.  Synchronises. */
+pic_status pic_get_particles(pic_ctx* ctx, int32_t species, double* out, int64_t* n, int32_t device_pointers);
+
+/* FP64 device reductions of the current state (section 3.3 diagnostics).
+ * Synchronises. */
+pic_status pic_diagnostics(pic_ctx* ctx, pic_diag* out);
+
+/* Energy history recorded while stepping (record_every > 0): 3 FP64 values per
+ * record, (U_E^n, U_B^n, K^n) with K^n = sum w m ((gamma^{n-1/2} + gamma^{n+1/2})/2 - 1),
+ * oldest first.  *count receives the number of records written to out. */
+pic_status pic_get_history(pic_ctx* ctx, double* out, int32_t max_records, int32_t* count);
+
+/* Per-kernel timing with CUDA events on the context's stream.  enable = 1 starts
+ * accumulating; pic_kernel_times returns, for up to max entries, the kernel class
+ * name, number of launches and total milliseconds.  Synchronises. */
+pic_status pic_set_timing(pic_ctx* ctx, int32_t enable);
+pic_status pic_kernel_times(pic_ctx* ctx, int32_t max, const char** names, int64_t* launches, double* ms,
+                            int32_t* count);
+
+/* Total kernel launches the library has issued on this context. */
+int64_t pic_launch_count(const pic_ctx* ctx);
+
+/* Human-readable detail of the last error on ctx (never NULL). */
+const char* pic_last_error(const pic_ctx* ctx);
+const char* pic_status_string(pic_status s);
+
+/* Release every device buffer and the stream the library created. */
+void pic_destroy(pic_ctx* ctx);
+
+#ifdef __cplusplus
+}
+#endif
+
+#endif /* GBPIC_H */

@@ -12,8 +12,9 @@ frequency of a two-sheets-per-cell lattice (``cold_plasma_omega``).
 
 Array conventions (see the header of ``pic_oracle.c``): a field set is a
 ``(9, nz, ny, nx)`` float64 array holding Ex Ey Ez Bx By Bz Jx Jy Jz at their
-Yee locations; a species is a ``(7, np)`` float64 array holding X Y Z (cell
-units), ux uy uz and w.
+Yee locations; a species is given as a ``(7, np)`` float64 array holding X Y Z
+(cell units), ux uy uz and w, and kept internally as integer cells plus in-cell
+offsets.
 
 Parity status of every function: pinned by ``tests/test_oracle_*.py`` against
 closed forms, invariants and the paper's printed values, except where a
@@ -65,15 +66,15 @@ def lib():
             L.or_boris_orbit.argtypes = [_dp, _dp, ctypes.c_double, ctypes.c_double, _dp, _dp,
                                          ctypes.c_long, ctypes.c_int, _dp, _dp]
             L.or_zigzag.argtypes = [_ip, _dp, ctypes.c_double, ctypes.c_double, _dp, _dp, _dp]
-            L.or_rho.argtypes = [_ip, _dp, ctypes.c_double, ctypes.c_long, _dp, _dp]
+            L.or_rho.argtypes = [_ip, _dp, ctypes.c_double, ctypes.c_long, _dp, _dp, _dp]
             L.or_divergence.argtypes = [_ip, _dp, _dp, _dp]
             L.or_divergence_b.argtypes = [_ip, _dp, _dp, _dp]
             L.or_backpush.argtypes = [_ip, _dp, ctypes.c_double, _dp, _dp, ctypes.c_double, ctypes.c_double,
-                                      ctypes.c_long, _dp]
+                                      ctypes.c_long, _dp, _dp]
             L.or_step.argtypes = [_ip, _dp, ctypes.c_double, _dp, ctypes.c_int, _dp, _lp,
-                                  ctypes.POINTER(_dp), _dp]
+                                  ctypes.POINTER(_dp), ctypes.POINTER(_dp), _dp]
             L.or_run.argtypes = [_ip, _dp, ctypes.c_double, _dp, ctypes.c_int, _dp, _lp,
-                                 ctypes.POINTER(_dp), ctypes.c_long, _dp]
+                                 ctypes.POINTER(_dp), ctypes.POINTER(_dp), ctypes.c_long, _dp]
             L.or_gauss_x.argtypes = [_ip, _dp, _dp, _dp]
             L.or_gauss_x.restype = ctypes.c_double
             _lib = L
@@ -93,20 +94,37 @@ def _grid(n, d):
 
 class Species:
     """One particle species for the oracle: charge ``q`` and mass ``m`` per physical
-    particle, and a ``(7, np)`` float64 array ``P`` (X, Y, Z in cell units; ux, uy, uz; w)."""
+    particle.  Given as a ``(7, np)`` array (X, Y, Z in cell units; ux, uy, uz; w), it is
+    held as integer cells ``C`` (3, np) and ``Q`` (7, np: in-cell offsets, momenta,
+    weights), so that FP64 resolves 2^-53 of a cell anywhere in the box.  ``P`` returns
+    the 7-row form again (positions rounded to FP64 only there)."""
 
     def __init__(self, q: float, m: float, P: np.ndarray):
         self.q = float(q)
         self.m = float(m)
-        self.P = np.ascontiguousarray(P, dtype=np.float64)
-        assert self.P.ndim == 2 and self.P.shape[0] == 7
+        P = np.asarray(P, dtype=np.float64)
+        assert P.ndim == 2 and P.shape[0] == 7
+        self.C = np.ascontiguousarray(np.floor(P[0:3]))
+        self.Q = np.ascontiguousarray(P.copy())
+        self.Q[0:3] = P[0:3] - self.C
+        up = self.Q[0:3] >= 1.0            # a rounded offset of 1 starts the next cell
+        self.Q[0:3][up] = 0.0
+        self.C[up] += 1.0
 
     @property
     def n(self) -> int:
-        return self.P.shape[1]
+        return self.Q.shape[1]
+
+    @property
+    def P(self) -> np.ndarray:
+        out = self.Q.copy()
+        out[0:3] = self.C + self.Q[0:3]
+        return out
 
     def copy(self) -> "Species":
-        return Species(self.q, self.m, self.P.copy())
+        s = Species.__new__(Species)
+        s.q, s.m, s.C, s.Q = self.q, self.m, self.C.copy(), self.Q.copy()
+        return s
 
 
 def courant_dt(d, courant: float = 0.5) -> float:
@@ -167,7 +185,7 @@ def rho(n, d, species, rho_ion=0.0):
     n, d, pn, pd = _grid(n, d)
     out = np.full((int(n[2]), int(n[1]), int(n[0])), float(rho_ion))
     for s in species:
-        lib().or_rho(pn, pd, s.q, s.n, _p(s.P), _p(out))
+        lib().or_rho(pn, pd, s.q, s.n, _p(s.Q), _p(s.C), _p(out))
     return out
 
 
@@ -193,7 +211,7 @@ def backpush(n, d, dt, E, Bhalf, species):
     """u^0 -> u^{-1/2} by a backward Boris half step with E^0, B^0 (in place)."""
     n, d, pn, pd = _grid(n, d)
     lib().or_backpush(pn, pd, dt, _p(np.ascontiguousarray(E)), _p(np.ascontiguousarray(Bhalf)),
-                      species.q, species.m, species.n, _p(species.P))
+                      species.q, species.m, species.n, _p(species.Q), _p(species.C))
 
 
 def run(n, d, dt, F, species, nsteps=1):
@@ -205,9 +223,10 @@ def run(n, d, dt, F, species, nsteps=1):
     ns = len(species)
     qm = np.array([v for s in species for v in (s.q, s.m)], dtype=np.float64)
     npc = np.array([s.n for s in species], dtype=np.int64)
-    ptrs = (_dp * ns)(*[_p(s.P) for s in species])
+    ptrs = (_dp * ns)(*[_p(s.Q) for s in species])
+    cptrs = (_dp * ns)(*[_p(s.C) for s in species])
     diag = np.zeros((nsteps, 3))
-    lib().or_run(pn, pd, dt, _p(F), ns, _p(qm), npc.ctypes.data_as(_lp), ptrs, nsteps, _p(diag))
+    lib().or_run(pn, pd, dt, _p(F), ns, _p(qm), npc.ctypes.data_as(_lp), ptrs, cptrs, nsteps, _p(diag))
     return diag
 
 

@@ -16,9 +16,11 @@
  *     Ex(i+1/2,j,k)  Ey(i,j+1/2,k)  Ez(i,j,k+1/2)       (also Jx, Jy, Jz)
  *     Bx(i,j+1/2,k+1/2)  By(i+1/2,j,k+1/2)  Bz(i+1/2,j+1/2,k)
  *   Charge density rho lives on the nodes (i,j,k).
- *   Particle positions are kept in cell units, X_d = x_d / d_d in [0, n_d);
- *   momenta are u = gamma v.  A species has charge q and mass m per physical
- *   particle; a super-particle of weight w carries q w and m w (Eqs. (9)-(11)).
+ *   Particle positions are kept in cell units, X_d = x_d / d_d in [0, n_d), as an
+ *   integer cell index plus an in-cell offset in [0, 1) (two FP64 arrays), so that
+ *   FP64 resolves 2^-53 of a cell anywhere in the box; momenta are u = gamma v.
+ *   A species has charge q and mass m per physical particle; a super-particle of
+ *   weight w carries q w and m w (Eqs. (9)-(11)).
  *
  * Time levels (section 2.2, Fig. 2): a state holds E^n, B^{n-1/2}, x^n, u^{n-1/2}.
  */
@@ -110,14 +112,15 @@ void or_ampere(const int* n, const double* d, double dt, double* E, const double
  * interpolated from its own Yee location with the first-order B-spline b1
  * (Eqs. (17)-(18) with b0 clouds).  half[d] = 1 when the component sits at a
  * half-integer position along d.                                            */
-static double interp_component(const or_grid* g, const double* F, const int half[3], const double X[3])
+static double interp_component(const or_grid* g, const double* F, const int half[3], const long cell[3],
+                               const double off[3])
 {
     long base[3];
     double s[3];
     for (int d = 0; d < 3; d++) {
-        double p = half[d] ? X[d] - 0.5 : X[d];   /* coordinate relative to the sample lattice */
+        double p = half[d] ? off[d] - 0.5 : off[d];   /* offset relative to the sample lattice */
         double f = floor(p);
-        base[d] = (long)f;
+        base[d] = cell[d] + (long)f;
         s[d] = p - f;
     }
     double v = 0.0;
@@ -133,19 +136,33 @@ static double interp_component(const or_grid* g, const double* F, const int half
 static const int HALF_E[3][3] = {{1, 0, 0}, {0, 1, 0}, {0, 0, 1}};
 static const int HALF_B[3][3] = {{0, 1, 1}, {1, 0, 1}, {1, 1, 0}};
 
-static void gather(const or_grid* g, const double* E, const double* B, const double X[3], double Ep[3], double Bp[3])
+static void gather(const or_grid* g, const double* E, const double* B, const long cell[3], const double off[3],
+                   double Ep[3], double Bp[3])
 {
     long N = ncells(g);
     for (int c = 0; c < 3; c++) {
-        Ep[c] = interp_component(g, E + c * N, HALF_E[c], X);
-        Bp[c] = interp_component(g, B + c * N, HALF_B[c], X);
+        Ep[c] = interp_component(g, E + c * N, HALF_E[c], cell, off);
+        Bp[c] = interp_component(g, B + c * N, HALF_B[c], cell, off);
+    }
+}
+
+/* split a position in cell units into cell index and offset */
+static void split(const double X[3], long cell[3], double off[3])
+{
+    for (int d = 0; d < 3; d++) {
+        double f = floor(X[d]);
+        cell[d] = (long)f;
+        off[d] = X[d] - f;
     }
 }
 
 void or_gather(const int* n, const double* d, const double* E, const double* B, const double* X, double* Ep, double* Bp)
 {
     or_grid g = {{n[0], n[1], n[2]}, {d[0], d[1], d[2]}, 0.0};
-    gather(&g, E, B, X, Ep, Bp);
+    long cell[3];
+    double off[3];
+    split(X, cell, off);
+    gather(&g, E, B, cell, off, Ep, Bp);
 }
 
 /* ------------------------------------------------------------------------ */
@@ -210,7 +227,9 @@ void or_boris_orbit(const double* E, const double* B, double qm, double dt, cons
  * dimensions (all of the paper's tests) and is what makes the deposit satisfy
  * the discrete continuity equation (12) exactly for moves in three dimensions,
  * the property section 2.5 requires of the scheme.
- * X2 must be unwrapped (|floor(X2) - floor(X1)| <= 1 per dimension).         */
+ * X1 and X2 are given relative to an origin cell c0 (so that they stay small and
+ * FP64 keeps full resolution); X2 must be unwrapped (|floor(X2) - floor(X1)| <= 1
+ * per dimension).                                                             */
 static void segment_current(const or_grid* g, double qw, const long cell[3], const double D[3], const double W[3], double* J)
 {
     long N = ncells(g);
@@ -233,9 +252,9 @@ static void segment_current(const or_grid* g, double qw, const long cell[3], con
     }
 }
 
-static void zigzag(const or_grid* g, double qw, const double X1[3], const double X2[3], double* J)
+static void zigzag(const or_grid* g, double qw, const long c0[3], const double X1[3], const double X2[3], double* J)
 {
-    long i1[3], i2[3];
+    long i1[3], i2[3], cell1[3], cell2[3];
     double Xr[3], D1[3], D2[3], W1[3], W2[3];
     for (int d = 0; d < 3; d++) {
         i1[d] = (long)floor(X1[d]);
@@ -248,32 +267,40 @@ static void zigzag(const or_grid* g, double qw, const double X1[3], const double
         D2[d] = X2[d] - Xr[d];
         W1[d] = 0.5 * (X1[d] + Xr[d]) - (double)i1[d];
         W2[d] = 0.5 * (Xr[d] + X2[d]) - (double)i2[d];
+        cell1[d] = c0[d] + i1[d];
+        cell2[d] = c0[d] + i2[d];
     }
-    segment_current(g, qw, i1, D1, W1, J);
-    segment_current(g, qw, i2, D2, W2, J);
+    segment_current(g, qw, cell1, D1, W1, J);
+    segment_current(g, qw, cell2, D2, W2, J);
 }
 
 void or_zigzag(const int* n, const double* d, double dt, double qw, const double* X1, const double* X2, double* J)
 {
     or_grid g = {{n[0], n[1], n[2]}, {d[0], d[1], d[2]}, dt};
-    zigzag(&g, qw, X1, X2, J);
+    long c0[3];
+    double a[3], b[3];
+    for (int k = 0; k < 3; k++) {
+        c0[k] = (long)floor(X1[k]);
+        a[k] = X1[k] - (double)c0[k];
+        b[k] = X2[k] - (double)c0[k];
+    }
+    zigzag(&g, qw, c0, a, b, J);
 }
 
 /* Cloud-in-cell charge density on the nodes, section 2.5 (b1 weights),
- * rho(i+a, j+b, k+c) += q w / dV * W(dx,a) W(dy,b) W(dz,c).  P holds one
- * species as 7 rows of np values: X, Y, Z, ux, uy, uz, w.                    */
-void or_rho(const int* n, const double* d, double q, long np, const double* P, double* rho)
+ * rho(i+a, j+b, k+c) += q w / dV * W(dx,a) W(dy,b) W(dz,c).  A species is held
+ * as C (3 rows of np integer cell indices) and P (7 rows of np values: offsets in
+ * x, y, z within the cell, ux, uy, uz, w).                                     */
+void or_rho(const int* n, const double* d, double q, long np, const double* P, const double* C, double* rho)
 {
     or_grid g = {{n[0], n[1], n[2]}, {d[0], d[1], d[2]}, 0.0};
     double dV = d[0] * d[1] * d[2];
     for (long p = 0; p < np; p++) {
-        double X[3] = {P[p], P[np + p], P[2 * np + p]};
         long base[3];
         double s[3];
         for (int dd = 0; dd < 3; dd++) {
-            double f = floor(X[dd]);
-            base[dd] = (long)f;
-            s[dd] = X[dd] - f;
+            base[dd] = (long)C[dd * np + p];
+            s[dd] = P[dd * np + p];
         }
         double qw = q * P[6 * np + p] / dV;
         for (int c = 0; c < 2; c++)
@@ -322,7 +349,7 @@ void or_divergence_b(const int* n, const double* d, const double* B, double* out
  * momentum only, u^0 -> u^{-1/2} (section 2.4, momenta at half-integer times),
  * with E^0 and B^0 = B^{-1/2} - (dt/2) curl E^0.                             */
 void or_backpush(const int* n, const double* d, double dt, const double* E, const double* Bhalf,
-                 double q, double m, long np, double* P)
+                 double q, double m, long np, double* P, const double* C)
 {
     or_grid g = {{n[0], n[1], n[2]}, {d[0], d[1], d[2]}, dt};
     long N = ncells(&g);
@@ -330,10 +357,11 @@ void or_backpush(const int* n, const double* d, double dt, const double* E, cons
     memcpy(B0, Bhalf, sizeof(double) * 3 * N);
     or_faraday(n, d, dt, E, B0, 0.5);
     for (long p = 0; p < np; p++) {
-        double X[3] = {P[p], P[np + p], P[2 * np + p]};
+        long cell[3] = {(long)C[p], (long)C[np + p], (long)C[2 * np + p]};
+        double off[3] = {P[p], P[np + p], P[2 * np + p]};
         double u[3] = {P[3 * np + p], P[4 * np + p], P[5 * np + p]};
         double Ep[3], Bp[3];
-        gather(&g, E, B0, X, Ep, Bp);
+        gather(&g, E, B0, cell, off, Ep, Bp);
         or_boris(q * (-0.5 * dt) / (2.0 * m), Ep, Bp, u);
         P[3 * np + p] = u[0];
         P[4 * np + p] = u[1];
@@ -350,13 +378,14 @@ void or_backpush(const int* n, const double* d, double dt, const double* E, cons
  *   4. zigzag J^{n+1/2} from the move x^n -> x^{n+1}         (section 2.5)
  *   5. E^{n+1} = E^n + dt (curl B^{n+1/2} - J^{n+1/2})       (Ampere, Eq. (14))
  * F holds 9*N values: Ex Ey Ez Bx By Bz Jx Jy Jz.  On return J holds J^{n+1/2}.
- * Species s has charge qm[2s], mass qm[2s+1], count np[s] and data P[s] (7 rows).
+ * Species s has charge qm[2s], mass qm[2s+1], count np[s], offsets/momenta/weights
+ * P[s] (7 rows) and cell indices C[s] (3 rows).
  * diag receives the energies of time level n:
  *   diag[0] = U_E = 1/2 dV sum E^n^2, diag[1] = U_B = 1/2 dV sum B^n^2,
  *   diag[2] = K = sum w m ((gamma^{n-1/2} + gamma^{n+1/2})/2 - 1).
  * Particles leaving the periodic box re-enter on the other side.            */
 void or_step(const int* n, const double* d, double dt, double* F, int ns, const double* qm, const long* np,
-             double** P, double* diag)
+             double** P, double** C, double* diag)
 {
     or_grid g = {{n[0], n[1], n[2]}, {d[0], d[1], d[2]}, dt};
     long N = ncells(&g);
@@ -376,26 +405,30 @@ void or_step(const int* n, const double* d, double dt, double* F, int ns, const 
     for (int s = 0; s < ns; s++) {
         double q = qm[2 * s], m = qm[2 * s + 1];
         double* Ps = P[s];
+        double* Cs = C[s];
         long cnt = np[s];
         for (long p = 0; p < cnt; p++) {
-            double X1[3] = {Ps[p], Ps[cnt + p], Ps[2 * cnt + p]};
+            long cell[3] = {(long)Cs[p], (long)Cs[cnt + p], (long)Cs[2 * cnt + p]};
+            double X1[3] = {Ps[p], Ps[cnt + p], Ps[2 * cnt + p]};          /* offsets: X relative to cell */
             double u[3] = {Ps[3 * cnt + p], Ps[4 * cnt + p], Ps[5 * cnt + p]};
             double w = Ps[6 * cnt + p];
             double Ep[3], Bp[3];
-            gather(&g, E, Bn, X1, Ep, Bp);
+            gather(&g, E, Bn, cell, X1, Ep, Bp);
             double g_old = gamma_of(u);
             or_boris(q * dt / (2.0 * m), Ep, Bp, u);
             double g_new = gamma_of(u);
             K += w * m * (0.5 * (g_old + g_new) - 1.0);
             double X2[3];
             for (int dd = 0; dd < 3; dd++) X2[dd] = X1[dd] + dt * u[dd] / (g_new * d[dd]);
-            zigzag(&g, q * w, X1, X2, J);
+            zigzag(&g, q * w, cell, X1, X2, J);
             for (int dd = 0; dd < 3; dd++) {
-                double x = X2[dd];
-                if (x >= (double)n[dd]) x -= (double)n[dd];
-                else if (x < 0.0) x += (double)n[dd];
-                if (x >= (double)n[dd]) x = 0.0;   /* x = -tiny + n rounds to n */
-                Ps[dd * cnt + p] = x;
+                /* new cell and offset; an offset that rounds to 1 starts the next cell */
+                double f = floor(X2[dd]);
+                double o = X2[dd] - f;
+                long cn = cell[dd] + (long)f;
+                if (o >= 1.0) { o = 0.0; cn += 1; }
+                Cs[dd * cnt + p] = (double)wrapi(cn, n[dd]);
+                Ps[dd * cnt + p] = o;
             }
             Ps[3 * cnt + p] = u[0];
             Ps[4 * cnt + p] = u[1];
@@ -412,9 +445,9 @@ void or_step(const int* n, const double* d, double dt, double* F, int ns, const 
 
 /* Several cycles; diag receives 3 values per step.                          */
 void or_run(const int* n, const double* d, double dt, double* F, int ns, const double* qm, const long* np,
-            double** P, long nsteps, double* diag)
+            double** P, double** C, long nsteps, double* diag)
 {
-    for (long s = 0; s < nsteps; s++) or_step(n, d, dt, F, ns, qm, np, P, diag + 3 * s);
+    for (long s = 0; s < nsteps; s++) or_step(n, d, dt, F, ns, qm, np, P, C, diag + 3 * s);
 }
 
 /* Gauss's law for an initial state whose charge varies along x only

@@ -1,0 +1,459 @@
+// C ABI of the library (include/gbpic.h): context set-up, the step loop of
+// KEMPIC-3D section 2.2 (Fig. 2), read-out, diagnostics, timing and errors.
+#include <cudaTypedefs.h>
+
+#include <algorithm>
+#include <cmath>
+#include <cstdio>
+#include <cstring>
+#include <new>
+
+#include "pic_internal.cuh"
+
+namespace gbpic {
+
+void* dev_alloc(pic_ctx* c, size_t bytes) {
+    if (bytes == 0) bytes = 256;
+    void* p = nullptr;
+    if (c->desc.alloc) {
+        p = c->desc.alloc(bytes, c->desc.alloc_user);
+    } else if (cudaMalloc(&p, bytes) != cudaSuccess) {
+        cudaGetLastError();
+        p = nullptr;
+    }
+    if (p) c->allocations.push_back(p);
+    else c->err = "device allocation of " + std::to_string(bytes) + " bytes failed";
+    return p;
+}
+
+void dev_free(pic_ctx* c, void* p) {
+    if (!p) return;
+    auto it = std::find(c->allocations.begin(), c->allocations.end(), p);
+    if (it != c->allocations.end()) c->allocations.erase(it);
+    if (c->desc.alloc) c->desc.free(p, c->desc.alloc_user);
+    else cudaFree(p);
+}
+
+pic_status cuda_fail(pic_ctx* c, cudaError_t e, const char* what) {
+    c->err = std::string(what) + ": " + cudaGetErrorString(e);
+    return PIC_ERR_CUDA;
+}
+
+static cudaEvent_t take_event(pic_ctx* c) {
+    if (!c->event_pool.empty()) {
+        cudaEvent_t e = c->event_pool.back();
+        c->event_pool.pop_back();
+        return e;
+    }
+    cudaEvent_t e = nullptr;
+    cudaEventCreate(&e);
+    return e;
+}
+
+void timing_begin(pic_ctx* c, int cls, cudaEvent_t* a) {
+    (void)cls;
+    if (!c->timing) return;
+    *a = take_event(c);
+    cudaEventRecord(*a, c->stream);
+}
+
+void timing_end(pic_ctx* c, int cls, cudaEvent_t a) {
+    if (!c->timing || !a) return;
+    cudaEvent_t b = take_event(c);
+    cudaEventRecord(b, c->stream);
+    c->pending.push_back({cls, a, b});
+    // keep the number of outstanding events bounded
+    if (c->pending.size() > 4096) {
+        cudaEventSynchronize(c->pending.back().b);
+        for (auto& p : c->pending) {
+            float ms = 0;
+            cudaEventElapsedTime(&ms, p.a, p.b);
+            c->kc_ms[p.cls] += ms;
+            c->kc_n[p.cls] += 1;
+            c->event_pool.push_back(p.a);
+            c->event_pool.push_back(p.b);
+        }
+        c->pending.clear();
+    }
+}
+
+pic_status make_tensor_maps(pic_ctx* c) {
+    void* fn = nullptr;
+    cudaDriverEntryPointQueryResult q;
+    GBPIC_CHECK(c, cudaGetDriverEntryPointByVersion("cuTensorMapEncodeTiled", &fn, 12000, cudaEnableDefault, &q));
+    if (q != cudaDriverEntryPointSuccess || !fn) {
+        c->err = "cuTensorMapEncodeTiled not available from the driver";
+        return PIC_ERR_CUDA;
+    }
+    auto encode = reinterpret_cast<PFN_cuTensorMapEncodeTiled_v12000>(fn);
+    const Geom& g = c->g;
+    const bool f64 = c->prec == PIC_FP64;
+    const cuuint64_t es = f64 ? 8 : 4;
+    cuuint64_t dims[3] = {(cuuint64_t)g.n[0] + 2, (cuuint64_t)g.Gy, (cuuint64_t)g.Gz};
+    cuuint64_t strides[2] = {(cuuint64_t)g.Px * es, (cuuint64_t)g.Px * g.Gy * es};
+    cuuint32_t box[3] = {(cuuint32_t)(f64 ? Prec<double>::BX : Prec<float>::BX), (cuuint32_t)SB, (cuuint32_t)SB};
+    cuuint32_t estr[3] = {1, 1, 1};
+    for (int k = 0; k < 6; ++k) {
+        void* base = k < 3 ? c->E[k] : c->B[k - 3];
+        CUresult r = encode(&c->tmap[k], f64 ? CU_TENSOR_MAP_DATA_TYPE_FLOAT64 : CU_TENSOR_MAP_DATA_TYPE_FLOAT32, 3,
+                            base, dims, strides, box, estr, CU_TENSOR_MAP_INTERLEAVE_NONE, CU_TENSOR_MAP_SWIZZLE_NONE,
+                            CU_TENSOR_MAP_L2_PROMOTION_L2_128B, CU_TENSOR_MAP_FLOAT_OOB_FILL_NONE);
+        if (r != CUDA_SUCCESS) {
+            c->err = "cuTensorMapEncodeTiled failed with CUresult " + std::to_string((int)r);
+            return PIC_ERR_CUDA;
+        }
+    }
+    return PIC_OK;
+}
+
+static pic_status device_errors(pic_ctx* c) {
+    int worst = 0;
+    for (auto& s : c->species) {
+        Counters h;
+        GBPIC_CHECK(c, cudaMemcpy(&h, s.ctr, sizeof(Counters), cudaMemcpyDeviceToHost));
+        worst |= h.err;
+    }
+    if (worst & ERRB_TIMEOUT) { c->err = "a bounded device wait for a TMA copy gave up"; return PIC_ERR_TIMEOUT; }
+    if (worst & ERRB_OVERFLOW) { c->err = "mover or spill list overflow: particles were dropped"; return PIC_ERR_TILE_OVERFLOW; }
+    if (worst & ERRB_SUPERLUMINAL) { c->err = "a particle moved more than one cell in one step"; return PIC_ERR_SUPERLUMINAL; }
+    if (worst & ERRB_NAN) { c->err = "non-finite momentum"; return PIC_ERR_NAN; }
+    return PIC_OK;
+}
+
+}  // namespace gbpic
+
+using namespace gbpic;
+
+extern "C" {
+
+const char* pic_status_string(pic_status s) {
+    switch (s) {
+        case PIC_OK: return "ok";
+        case PIC_ERR_ARG: return "invalid argument";
+        case PIC_ERR_CFL: return "time step violates the CFL condition";
+        case PIC_ERR_OOM: return "device out of memory";
+        case PIC_ERR_CUDA: return "CUDA error";
+        case PIC_ERR_TILE_OVERFLOW: return "mover/spill overflow";
+        case PIC_ERR_SUPERLUMINAL: return "particle moved more than one cell";
+        case PIC_ERR_NAN: return "non-finite momentum";
+        case PIC_ERR_STATE: return "call out of order";
+        case PIC_ERR_TIMEOUT: return "device wait timed out";
+        case PIC_ERR_NO_DEVICE: return "no sm_103 CUDA device";
+    }
+    return "unknown";
+}
+
+const char* pic_last_error(const pic_ctx* c) { return c ? c->err.c_str() : "null context"; }
+
+int64_t pic_launch_count(const pic_ctx* c) { return c ? c->launches : 0; }
+
+pic_status pic_init_grid(const pic_grid_desc* desc, pic_ctx** out) {
+    if (!out) return PIC_ERR_ARG;
+    *out = nullptr;
+    if (!desc) return PIC_ERR_ARG;
+    for (int k = 0; k < 3; ++k)
+        if (desc->n[k] < 1 || !(desc->d[k] > 0) || !std::isfinite(desc->d[k])) return PIC_ERR_ARG;
+    if (!(desc->dt > 0) || !std::isfinite(desc->dt)) return PIC_ERR_ARG;
+    if (desc->precision != PIC_FP32 && desc->precision != PIC_FP64) return PIC_ERR_ARG;
+    if (desc->alloc && !desc->free) return PIC_ERR_ARG;
+    if ((long long)desc->n[0] * desc->n[1] * desc->n[2] > (1LL << 31) - 1) return PIC_ERR_ARG;
+    // Eq. (15): c dt <= 1 / sqrt(sum 1/d^2)
+    const double lim = 1.0 / std::sqrt(1.0 / (desc->d[0] * desc->d[0]) + 1.0 / (desc->d[1] * desc->d[1]) +
+                                       1.0 / (desc->d[2] * desc->d[2]));
+    if (desc->dt > lim * (1.0 + 1e-12)) return PIC_ERR_CFL;
+
+    int ndev = 0;
+    if (cudaGetDeviceCount(&ndev) != cudaSuccess || ndev <= desc->device || desc->device < 0) {
+        cudaGetLastError();
+        return PIC_ERR_NO_DEVICE;
+    }
+    cudaDeviceProp prop;
+    if (cudaGetDeviceProperties(&prop, desc->device) != cudaSuccess || prop.major * 10 + prop.minor != 103)
+        return PIC_ERR_NO_DEVICE;
+    if (cudaSetDevice(desc->device) != cudaSuccess) return PIC_ERR_NO_DEVICE;
+
+    pic_ctx* c = new (std::nothrow) pic_ctx();
+    if (!c) return PIC_ERR_OOM;
+    c->desc = *desc;
+    c->prec = desc->precision;
+    c->esize = c->prec == PIC_FP64 ? 8 : 4;
+    Geom& g = c->g;
+    for (int k = 0; k < 3; ++k) {
+        g.n[k] = desc->n[k];
+        g.nt[k] = (desc->n[k] + TILE - 1) / TILE;
+    }
+    g.Px = ((desc->n[0] + 2) + 7) / 8 * 8;
+    g.Gy = desc->n[1] + 2;
+    g.Gz = desc->n[2] + 2;
+    g.N = (long long)desc->n[0] * desc->n[1] * desc->n[2];
+    if (desc->stream) {
+        c->stream = static_cast<cudaStream_t>(desc->stream);
+    } else {
+        if (cudaStreamCreateWithFlags(&c->stream, cudaStreamNonBlocking) != cudaSuccess) {
+            delete c;
+            return PIC_ERR_CUDA;
+        }
+        c->own_stream = true;
+    }
+    const size_t fb = (size_t)g.padded_size() * c->esize;
+    for (int k = 0; k < 3; ++k) {
+        c->E[k] = dev_alloc(c, fb);
+        c->B[k] = dev_alloc(c, fb);
+        c->J[k] = dev_alloc(c, sizeof(long long) * (size_t)g.N);   // int64 (FP32) or double (FP64)
+        if (!c->E[k] || !c->B[k] || !c->J[k]) {
+            pic_destroy(c);
+            return PIC_ERR_OOM;
+        }
+        cudaMemsetAsync(c->E[k], 0, fb, c->stream);
+        cudaMemsetAsync(c->B[k], 0, fb, c->stream);
+        cudaMemsetAsync(c->J[k], 0, sizeof(long long) * (size_t)g.N, c->stream);
+    }
+    if (desc->record_every > 0) {
+        c->hist_cap = desc->history_capacity > 0 ? desc->history_capacity : 4096;
+        c->hist = static_cast<double*>(dev_alloc(c, sizeof(double) * 3 * (size_t)c->hist_cap));
+        if (!c->hist) {
+            pic_destroy(c);
+            return PIC_ERR_OOM;
+        }
+        cudaMemsetAsync(c->hist, 0, sizeof(double) * 3 * (size_t)c->hist_cap, c->stream);
+    }
+    pic_status st = make_tensor_maps(c);
+    if (st != PIC_OK) {
+        std::fprintf(stderr, "gbpic: %s\n", c->err.c_str());
+        pic_destroy(c);
+        return st;
+    }
+    if (cudaStreamSynchronize(c->stream) != cudaSuccess) {
+        pic_destroy(c);
+        return PIC_ERR_CUDA;
+    }
+    c->jscale = 1.0;
+    c->jinv = 1.0;
+    *out = c;
+    return PIC_OK;
+}
+
+pic_status pic_set_fields(pic_ctx* c, const double* E, const double* B, int32_t device_pointers) {
+    if (!c) return PIC_ERR_ARG;
+    cudaSetDevice(c->desc.device);
+    const size_t nb = sizeof(double) * 3 * (size_t)c->g.N;
+    const double *dE = E, *dB = B;
+    double* stage = nullptr;
+    if (!device_pointers && (E || B)) {
+        stage = static_cast<double*>(dev_alloc(c, 2 * nb));
+        if (!stage) return PIC_ERR_OOM;
+        if (E) GBPIC_CHECK(c, cudaMemcpyAsync(stage, E, nb, cudaMemcpyHostToDevice, c->stream));
+        if (B) GBPIC_CHECK(c, cudaMemcpyAsync(stage + 3 * c->g.N, B, nb, cudaMemcpyHostToDevice, c->stream));
+        dE = E ? stage : nullptr;
+        dB = B ? stage + 3 * c->g.N : nullptr;
+    }
+    pic_status st = unpack_fields(c, dE, dB);
+    GBPIC_CHECK(c, cudaStreamSynchronize(c->stream));
+    if (stage) dev_free(c, stage);
+    c->fields_set = true;
+    c->gref_valid = false;
+    c->rho_prev_step = -1;
+    return st;
+}
+
+pic_status pic_load_species(pic_ctx* c, const pic_species_desc* d, int32_t* species_id) {
+    if (!c || !d) return PIC_ERR_ARG;
+    if (d->n < 0 || (d->n > 0 && (!d->X || !d->u || !d->w)) || !(d->m > 0) || !std::isfinite(d->q)) return PIC_ERR_ARG;
+    cudaSetDevice(c->desc.device);
+    c->species.emplace_back();
+    SpeciesDev& s = c->species.back();
+    pic_status st = load_species_impl(c, d, s);
+    if (st != PIC_OK) {
+        c->species.pop_back();
+        return st;
+    }
+    if (!d->momenta_at_half_step && d->n > 0) {
+        st = launch_backpush(c, s);
+        if (st != PIC_OK) return st;
+    }
+    if (species_id) *species_id = (int32_t)c->species.size() - 1;
+    c->gref_valid = false;
+    c->rho_prev_step = -1;
+    return PIC_OK;
+}
+
+pic_status pic_step(pic_ctx* c, int32_t nsteps) {
+    if (!c || nsteps < 0) return PIC_ERR_ARG;
+    if (nsteps == 0) return PIC_OK;
+    cudaSetDevice(c->desc.device);
+    // the fixed-point unit of J (FP32 path): the coarsest unit any species needs;
+    // the FP64 path accumulates J itself
+    double js = 0;
+    for (auto& s : c->species) js = std::max(js, s.jscale);
+    if (js <= 0 || c->prec == PIC_FP64) js = 1.0;
+    c->jscale = js;
+    c->jinv = 1.0 / js;
+    if (c->j_dirty) {
+        for (int k = 0; k < 3; ++k)
+            GBPIC_CHECK(c, cudaMemsetAsync(c->J[k], 0, sizeof(long long) * (size_t)c->g.N, c->stream));
+        c->j_dirty = false;
+    }
+    for (int s = 0; s < nsteps; ++s) {
+        double* rec = nullptr;
+        if (c->hist && c->step % c->desc.record_every == 0) {
+            rec = c->hist + 3 * (c->hist_written % c->hist_cap);
+            GBPIC_CHECK(c, cudaMemsetAsync(rec, 0, sizeof(double) * 3, c->stream));
+            c->hist_written++;
+        }
+        pic_status st = launch_faraday_half(c, rec);
+        if (st != PIC_OK) return st;
+        const int sort_every = c->desc.sort_every == 0 ? 4 : c->desc.sort_every;
+        const bool sort_now = sort_every > 0 && (c->step + 1) % sort_every == 0;
+        for (auto& sp : c->species) {
+            st = launch_push_species(c, sp, (int)(c->step & 1), rec ? rec + 2 : nullptr);
+            if (st != PIC_OK) return st;
+            if (sort_now) {
+                st = launch_sort(c, sp);
+                if (st != PIC_OK) return st;
+            }
+        }
+        st = launch_faraday_half(c, nullptr);
+        if (st != PIC_OK) return st;
+        st = launch_ampere(c, s < nsteps - 1);
+        if (st != PIC_OK) return st;
+        c->step++;
+    }
+    c->j_dirty = true;
+    return PIC_OK;
+}
+
+pic_status pic_sync(pic_ctx* c) {
+    if (!c) return PIC_ERR_ARG;
+    cudaSetDevice(c->desc.device);
+    GBPIC_CHECK(c, cudaStreamSynchronize(c->stream));
+    return device_errors(c);
+}
+
+pic_status pic_get_fields(pic_ctx* c, double* E, double* B, double* J, int32_t device_pointers) {
+    if (!c) return PIC_ERR_ARG;
+    pic_status st = pic_sync(c);
+    if (st != PIC_OK && st != PIC_ERR_TILE_OVERFLOW) return st;
+    const size_t nb = sizeof(double) * 3 * (size_t)c->g.N;
+    if (device_pointers) {
+        st = pack_fields(c, E, B, J);
+        if (st != PIC_OK) return st;
+        GBPIC_CHECK(c, cudaStreamSynchronize(c->stream));
+        return PIC_OK;
+    }
+    double* stage = static_cast<double*>(dev_alloc(c, 3 * nb));
+    if (!stage) return PIC_ERR_OOM;
+    double* sE = E ? stage : nullptr;
+    double* sB = B ? stage + 3 * c->g.N : nullptr;
+    double* sJ = J ? stage + 6 * c->g.N : nullptr;
+    if (J && !c->j_dirty) GBPIC_CHECK(c, cudaMemsetAsync(sJ, 0, nb, c->stream));
+    st = pack_fields(c, sE, sB, c->j_dirty ? sJ : nullptr);
+    if (st != PIC_OK) return st;
+    if (E) GBPIC_CHECK(c, cudaMemcpyAsync(E, sE, nb, cudaMemcpyDeviceToHost, c->stream));
+    if (B) GBPIC_CHECK(c, cudaMemcpyAsync(B, sB, nb, cudaMemcpyDeviceToHost, c->stream));
+    if (J) GBPIC_CHECK(c, cudaMemcpyAsync(J, sJ, nb, cudaMemcpyDeviceToHost, c->stream));
+    GBPIC_CHECK(c, cudaStreamSynchronize(c->stream));
+    dev_free(c, stage);
+    return PIC_OK;
+}
+
+pic_status pic_get_particles(pic_ctx* c, int32_t species, double* out, int64_t* n, int32_t device_pointers) {
+    if (!c || !n || species < 0 || species >= (int32_t)c->species.size()) return PIC_ERR_ARG;
+    pic_status st = pic_sync(c);
+    if (st != PIC_OK && st != PIC_ERR_TILE_OVERFLOW) return st;
+    SpeciesDev& s = c->species[species];
+    int64_t alive = c->desc.track_ids ? s.n_loaded : count_alive(c, s, nullptr);
+    if (alive < 0) return cuda_fail(c, cudaGetLastError(), "count_alive");
+    *n = alive;
+    if (!out || alive == 0) return PIC_OK;
+    const size_t nb = sizeof(double) * 7 * (size_t)alive;
+    double* dst = out;
+    if (!device_pointers) {
+        dst = static_cast<double*>(dev_alloc(c, nb));
+        if (!dst) return PIC_ERR_OOM;
+    }
+    if (c->desc.track_ids) GBPIC_CHECK(c, cudaMemsetAsync(dst, 0xff, nb, c->stream));   // NaN for lost ids
+    st = get_particles_impl(c, s, dst, alive);
+    if (st != PIC_OK) return st;
+    if (!device_pointers) {
+        GBPIC_CHECK(c, cudaMemcpy(out, dst, nb, cudaMemcpyDeviceToHost));
+        dev_free(c, dst);
+    }
+    return PIC_OK;
+}
+
+pic_status pic_diagnostics(pic_ctx* c, pic_diag* out) {
+    if (!c || !out) return PIC_ERR_ARG;
+    pic_status st = pic_sync(c);
+    if (st != PIC_OK) return st;
+    return diagnostics_impl(c, out);
+}
+
+pic_status pic_get_history(pic_ctx* c, double* out, int32_t max_records, int32_t* count) {
+    if (!c || !count) return PIC_ERR_ARG;
+    *count = 0;
+    if (!c->hist) return PIC_OK;
+    GBPIC_CHECK(c, cudaStreamSynchronize(c->stream));
+    const int64_t have = std::min<int64_t>(c->hist_written, c->hist_cap);
+    const int64_t first = c->hist_written - have;
+    std::vector<double> h(3 * (size_t)c->hist_cap);
+    GBPIC_CHECK(c, cudaMemcpy(h.data(), c->hist, sizeof(double) * h.size(), cudaMemcpyDeviceToHost));
+    int32_t k = 0;
+    for (int64_t r = first; r < c->hist_written && k < max_records; ++r, ++k) {
+        const int64_t slot = r % c->hist_cap;
+        if (out) memcpy(out + 3 * k, h.data() + 3 * slot, sizeof(double) * 3);
+    }
+    *count = k;
+    return PIC_OK;
+}
+
+pic_status pic_set_timing(pic_ctx* c, int32_t enable) {
+    if (!c) return PIC_ERR_ARG;
+    GBPIC_CHECK(c, cudaStreamSynchronize(c->stream));
+    c->timing = enable != 0;
+    return PIC_OK;
+}
+
+pic_status pic_kernel_times(pic_ctx* c, int32_t max, const char** names, int64_t* launches, double* ms, int32_t* count) {
+    static const char* kNames[KC_COUNT] = {"faraday_half", "tile_push", "list_push", "append", "ampere", "sort",
+                                           "other"};
+    if (!c || !count) return PIC_ERR_ARG;
+    GBPIC_CHECK(c, cudaStreamSynchronize(c->stream));
+    for (auto& p : c->pending) {
+        float t = 0;
+        cudaEventElapsedTime(&t, p.a, p.b);
+        c->kc_ms[p.cls] += t;
+        c->kc_n[p.cls] += 1;
+        c->event_pool.push_back(p.a);
+        c->event_pool.push_back(p.b);
+    }
+    c->pending.clear();
+    int k = 0;
+    for (int i = 0; i < KC_COUNT && k < max; ++i, ++k) {
+        if (names) names[k] = kNames[i];
+        if (launches) launches[k] = c->kc_n[i];
+        if (ms) ms[k] = c->kc_ms[i];
+    }
+    *count = k;
+    for (int i = 0; i < KC_COUNT; ++i) {
+        c->kc_ms[i] = 0;
+        c->kc_n[i] = 0;
+    }
+    return PIC_OK;
+}
+
+void pic_destroy(pic_ctx* c) {
+    if (!c) return;
+    cudaSetDevice(c->desc.device);
+    if (c->stream) cudaStreamSynchronize(c->stream);
+    for (auto& p : c->pending) {
+        cudaEventDestroy(p.a);
+        cudaEventDestroy(p.b);
+    }
+    for (auto e : c->event_pool) cudaEventDestroy(e);
+    std::vector<void*> all = c->allocations;
+    for (void* p : all) dev_free(c, p);
+    if (c->own_stream && c->stream) cudaStreamDestroy(c->stream);
+    delete c;
+}
+
+}  // extern "C"

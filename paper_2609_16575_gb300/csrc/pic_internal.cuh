@@ -1,0 +1,553 @@
+// Internal declarations of the GB300 EM-PIC library: device helpers (inline PTX for
+// TMA, mbarrier), the particle arithmetic shared by the tile kernel and the generic
+// list kernel, field geometry, and the host-side context.
+#pragma once
+
+#include <cuda.h>
+#include <cuda_runtime.h>
+#include <stdint.h>
+
+#include <string>
+#include <vector>
+
+#include "gbpic.h"
+
+namespace gbpic {
+
+constexpr int TILE = 8;          // tile edge in cells (8^3 cells per tile)
+constexpr int TILE_CELLS = 512;
+constexpr int SB = 10;           // staged E/B extent per dim: local cells -1..8
+constexpr int SJ = 11;           // shared J extent per dim: local nodes/edges -1..9
+constexpr int SJ3 = SJ * SJ * SJ;
+constexpr int PUSH_THREADS = 256;
+constexpr int PUSH_WARPS = PUSH_THREADS / 32;
+
+// device error bits, OR-ed into Counters::err
+enum : int { ERRB_OVERFLOW = 1, ERRB_SUPERLUMINAL = 2, ERRB_NAN = 4, ERRB_TIMEOUT = 8 };
+
+// bounded waits: a try_wait loop gives up after this many polls and raises ERRB_TIMEOUT
+constexpr int MBAR_MAX_POLLS = 1 << 24;
+
+template <typename T> struct Prec;
+template <> struct Prec<float> {
+    static constexpr int BX = 12;      // TMA box inner extent: 12 floats = 48 B (multiple of 16 B)
+    static constexpr int JBITS = 40;   // fixed-point fraction bits of a bounded J contribution
+};
+template <> struct Prec<double> {
+    static constexpr int BX = 10;      // 10 doubles = 80 B
+    static constexpr int JBITS = 50;
+};
+
+// Padded Yee field geometry.  Each component array holds local indices -1..n
+// per dimension (one ghost layer on each side, periodic images), x fastest,
+// with the x pitch padded to a multiple of 8 elements (rows 16-B aligned).
+struct Geom {
+    int n[3];
+    int nt[3];        // tiles per dimension (ceil(n/8))
+    int Px, Gy, Gz;   // x pitch, padded y and z extents (n+2)
+    long long N;      // n0 n1 n2
+    __host__ __device__ long long pidx(int i, int j, int k) const {
+        return ((long long)(k + 1) * Gy + (j + 1)) * Px + (i + 1);
+    }
+    __host__ __device__ long long cidx(int i, int j, int k) const {   // compact (unpadded)
+        return ((long long)k * n[1] + j) * n[0] + i;
+    }
+    __host__ __device__ long long padded_size() const { return (long long)Px * Gy * Gz; }
+};
+
+// Accumulator of the current density J.  FP32 path: 64-bit fixed point (exact,
+// order-independent integer atomics in shared memory and HBM).  FP64 path: FP64
+// (a fixed unit cannot hold both a relativistic and a cold plasma to 1e-12).
+template <typename T> struct JTraits;
+template <> struct JTraits<float> {
+    using acc_t = long long;
+    static constexpr bool fixed = true;
+};
+template <> struct JTraits<double> {
+    using acc_t = double;
+    static constexpr bool fixed = false;
+};
+
+template <typename T> struct Fields {
+    T* E[3];
+    T* B[3];
+    typename JTraits<T>::acc_t* J[3];   // compact layout
+};
+
+// Device counters of one species (double-buffered by step parity).
+struct Counters {
+    int mover_count[2];
+    int spill_count[2];
+    int err;
+    int pad[3];
+};
+
+// One particle outside its tile segment (mover or spill record); cell is global.
+template <typename T> struct Rec {
+    int cell;
+    int id;
+    T d[3];
+    T u[3];
+    T w;
+};
+
+template <typename T> struct ParticleArrays {
+    int* cell;      // local cell within the owning tile: lx | ly << 3 | lz << 6
+    T* d[3];        // in-cell offsets in [0, 1)
+    T* u[3];        // u = gamma v
+    T* w;
+    int* id;        // optional load-order id
+    const int* seg_start;
+    int* count;
+    const int* cap;
+};
+
+// ---------------------------------------------------------------------------
+// PTX helpers (TMA and mbarrier).
+
+__device__ __forceinline__ uint32_t smem_u32(const void* p) {
+    return static_cast<uint32_t>(__cvta_generic_to_shared(p));
+}
+
+__device__ __forceinline__ void mbar_init(uint64_t* bar, uint32_t count) {
+    asm volatile("mbarrier.init.shared::cta.b64 [%0], %1;" ::"r"(smem_u32(bar)), "r"(count) : "memory");
+}
+
+__device__ __forceinline__ void fence_mbar_init() {
+    asm volatile("fence.mbarrier_init.release.cluster;" ::: "memory");
+    asm volatile("fence.proxy.async.shared::cta;" ::: "memory");
+}
+
+__device__ __forceinline__ void mbar_arrive_expect_tx(uint64_t* bar, uint32_t bytes) {
+    asm volatile("mbarrier.arrive.expect_tx.shared::cta.b64 _, [%0], %1;" ::"r"(smem_u32(bar)), "r"(bytes)
+                 : "memory");
+}
+
+__device__ __forceinline__ bool mbar_try_wait(uint64_t* bar, uint32_t phase) {
+    uint32_t ok;
+    asm volatile(
+        "{\n\t.reg .pred p;\n\t"
+        "mbarrier.try_wait.parity.shared::cta.b64 p, [%1], %2;\n\t"
+        "selp.u32 %0, 1, 0, p;\n\t}"
+        : "=r"(ok)
+        : "r"(smem_u32(bar)), "r"(phase)
+        : "memory");
+    return ok != 0;
+}
+
+// 3D tiled TMA load of one box into shared memory, completion counted on bar.
+__device__ __forceinline__ void tma_load_3d(void* dst, const CUtensorMap* map, int c0, int c1, int c2,
+                                            uint64_t* bar) {
+    asm volatile(
+        "cp.async.bulk.tensor.3d.shared::cluster.global.tile.mbarrier::complete_tx::bytes"
+        " [%0], [%1, {%2, %3, %4}], [%5];" ::"r"(smem_u32(dst)),
+        "l"(reinterpret_cast<uint64_t>(map)), "r"(c0), "r"(c1), "r"(c2), "r"(smem_u32(bar))
+        : "memory");
+}
+
+// ---------------------------------------------------------------------------
+// Particle arithmetic shared by every kernel that pushes.
+
+__device__ __forceinline__ float rsqrt_t(float x) { return rsqrtf(x); }
+__device__ __forceinline__ double rsqrt_t(double x) { return rsqrt(x); }
+__device__ __forceinline__ float floor_t(float x) { return floorf(x); }
+__device__ __forceinline__ double floor_t(double x) { return floor(x); }
+// Round-to-nearest-even of |x| < 2^41 to a 64-bit integer with FP32 adds only:
+// h = x rounded to a multiple of 2^20 (adding 1.5*2^43 leaves an ulp of 2^20), the
+// remainder l = x - h is exact, and both parts become integers by the 1.5*2^23
+// mantissa trick.  Equals llrintf(x) without the slower 64-bit conversion path.
+__device__ __forceinline__ long long fixed_rn(float x) {
+    const float big = 13194139533312.0f;   // 1.5 * 2^43
+    const float mag = 12582912.0f;         // 1.5 * 2^23
+    const float h = __fsub_rn(__fadd_rn(x, big), big);
+    const float l = __fsub_rn(x, h);
+    const int hi = __float_as_int(__fadd_rn(__fmul_rn(h, 9.5367431640625e-07f), mag)) - 0x4B400000;  // h / 2^20
+    const int lo = __float_as_int(__fadd_rn(l, mag)) - 0x4B400000;
+    return ((long long)hi << 20) + (long long)lo;
+}
+// (a warp sum of 32 bounded terms can leave the window of fixed_rn: convert those
+// rare values with the exact 64-bit instruction)
+__device__ __forceinline__ long long to_acc(float x) {
+    return fabsf(x) < 2199023255552.0f ? fixed_rn(x) : __float2ll_rn(x);   // 2^41
+}
+__device__ __forceinline__ double to_acc(double x) { return x; }
+__device__ __forceinline__ void acc_atomic(long long* p, long long v) {
+    atomicAdd(reinterpret_cast<unsigned long long*>(p), static_cast<unsigned long long>(v));
+}
+__device__ __forceinline__ void acc_atomic(double* p, double v) { atomicAdd(p, v); }
+
+// Warp reduce-scatter of 16 slots: on return lane l holds the warp sum of slot
+// l >> 1 (lanes l and l^1 hold the same slot).  16 shuffles instead of 5 x 16.
+template <typename A>
+__device__ __forceinline__ A reduce_scatter16(A v[16], int lane) {
+#pragma unroll
+    for (int j = 0; j < 8; ++j) {
+        const bool up = lane & 16;
+        const A send = up ? v[j] : v[8 + j];
+        const A keep = up ? v[8 + j] : v[j];
+        v[j] = keep + __shfl_xor_sync(0xffffffffu, send, 16);
+    }
+#pragma unroll
+    for (int j = 0; j < 4; ++j) {
+        const bool up = lane & 8;
+        const A send = up ? v[j] : v[4 + j];
+        const A keep = up ? v[4 + j] : v[j];
+        v[j] = keep + __shfl_xor_sync(0xffffffffu, send, 8);
+    }
+#pragma unroll
+    for (int j = 0; j < 2; ++j) {
+        const bool up = lane & 4;
+        const A send = up ? v[j] : v[2 + j];
+        const A keep = up ? v[2 + j] : v[j];
+        v[j] = keep + __shfl_xor_sync(0xffffffffu, send, 4);
+    }
+    {
+        const bool up = lane & 2;
+        const A send = up ? v[0] : v[1];
+        const A keep = up ? v[1] : v[0];
+        v[0] = keep + __shfl_xor_sync(0xffffffffu, send, 2);
+    }
+    return v[0] + __shfl_xor_sync(0xffffffffu, v[0], 1);
+}
+
+// Staggered CIC weights along one dimension (section 2.5).  A node-located
+// component samples cells (i, i+1) with weight s = delta; a half-located one
+// samples (i-1, i) or (i, i+1) with s = delta + 1/2 or delta - 1/2.
+template <typename T>
+__device__ __forceinline__ void half_weight(int i, T delta, int& base, T& s) {
+    if (delta >= T(0.5)) {
+        base = i;
+        s = delta - T(0.5);
+    } else {
+        base = i - 1;
+        s = delta + T(0.5);
+    }
+}
+
+// Trilinear interpolation of one component from 8 samples fetched by F(x, y, z).
+template <typename T, typename Fetch>
+__device__ __forceinline__ T trilerp(Fetch F, int bx, int by, int bz, T sx, T sy, T sz) {
+    T c00 = F(bx, by, bz) + sx * (F(bx + 1, by, bz) - F(bx, by, bz));
+    T c10 = F(bx, by + 1, bz) + sx * (F(bx + 1, by + 1, bz) - F(bx, by + 1, bz));
+    T c01 = F(bx, by, bz + 1) + sx * (F(bx + 1, by, bz + 1) - F(bx, by, bz + 1));
+    T c11 = F(bx, by + 1, bz + 1) + sx * (F(bx + 1, by + 1, bz + 1) - F(bx, by + 1, bz + 1));
+    T c0 = c00 + sy * (c10 - c00);
+    T c1 = c01 + sy * (c11 - c01);
+    return c0 + sz * (c1 - c0);
+}
+
+// Gather E and B (section 2.5) at local cell (x, y, z) + offset (dx, dy, dz);
+// F(comp, x, y, z) returns component comp (0..2 = E, 3..5 = B) at a local index.
+template <typename T, typename Fetch6>
+__device__ __forceinline__ void gather_eb(Fetch6 F, int x, int y, int z, T dx, T dy, T dz, T Ep[3], T Bp[3]) {
+    int hx, hy, hz;
+    T shx, shy, shz;
+    half_weight(x, dx, hx, shx);
+    half_weight(y, dy, hy, shy);
+    half_weight(z, dz, hz, shz);
+    // E: Ex (h,n,n), Ey (n,h,n), Ez (n,n,h);  B: Bx (n,h,h), By (h,n,h), Bz (h,h,n)
+    Ep[0] = trilerp<T>([&](int a, int b, int c) { return F(0, a, b, c); }, hx, y, z, shx, dy, dz);
+    Ep[1] = trilerp<T>([&](int a, int b, int c) { return F(1, a, b, c); }, x, hy, z, dx, shy, dz);
+    Ep[2] = trilerp<T>([&](int a, int b, int c) { return F(2, a, b, c); }, x, y, hz, dx, dy, shz);
+    Bp[0] = trilerp<T>([&](int a, int b, int c) { return F(3, a, b, c); }, x, hy, hz, dx, shy, shz);
+    Bp[1] = trilerp<T>([&](int a, int b, int c) { return F(4, a, b, c); }, hx, y, hz, shx, dy, shz);
+    Bp[2] = trilerp<T>([&](int a, int b, int c) { return F(5, a, b, c); }, hx, hy, z, shx, shy, dz);
+}
+
+// Relativistic Boris (section 2.4; Boris 1970): u^{n-1/2} -> u^{n+1/2} in place,
+// eps = q dt / (2 m).  Returns 1/gamma^{n+1/2}.
+template <typename T>
+__device__ __forceinline__ T boris(T eps, const T E[3], const T B[3], T u[3]) {
+    T um0 = u[0] + eps * E[0], um1 = u[1] + eps * E[1], um2 = u[2] + eps * E[2];
+    T ig = rsqrt_t(T(1) + um0 * um0 + um1 * um1 + um2 * um2);
+    T t0 = eps * B[0] * ig, t1 = eps * B[1] * ig, t2 = eps * B[2] * ig;
+    T f = T(2) / (T(1) + t0 * t0 + t1 * t1 + t2 * t2);
+    T s0 = f * t0, s1 = f * t1, s2 = f * t2;
+    T up0 = um0 + (um1 * t2 - um2 * t1);
+    T up1 = um1 + (um2 * t0 - um0 * t2);
+    T up2 = um2 + (um0 * t1 - um1 * t0);
+    u[0] = um0 + (up1 * s2 - up2 * s1) + eps * E[0];
+    u[1] = um1 + (up2 * s0 - up0 * s2) + eps * E[1];
+    u[2] = um2 + (up0 * s1 - up1 * s0) + eps * E[2];
+    return rsqrt_t(T(1) + u[0] * u[0] + u[1] * u[1] + u[2] * u[2]);
+}
+
+// gamma - 1 without cancellation: |u|^2 / (gamma + 1)
+template <typename T>
+__device__ __forceinline__ T gamma_minus_one(const T u[3]) {
+    T u2 = u[0] * u[0] + u[1] * u[1] + u[2] * u[2];
+    T g = T(1) / rsqrt_t(T(1) + u2);
+    return u2 / (g + T(1));
+}
+
+// Advance one coordinate: offset delta in the current cell moves by disp (cells).
+// Returns the cell step (-1, 0, +1, or beyond for a superluminal move) and the
+// new offset in [0, 1).  An offset that rounds to 1 goes to 0 of the next cell.
+template <typename T>
+__device__ __forceinline__ int advance(T delta, T disp, T& out) {
+    T x = delta + disp;
+    T f = floor_t(x);
+    T r = x - f;
+    int step = (int)f;
+    if (r >= T(1)) {
+        r = T(0);
+        step += 1;
+    }
+    out = r;
+    return step;
+}
+
+// Zigzag relay split of one coordinate (section 2.5, Umeda et al. 2003), written in
+// each segment's own cell frame so that the fluxes are exact differences of the
+// stored offsets.  Inputs: start offset x1 (cell i1), end offset x2 (cell i1 + s).
+// Outputs: segment fluxes F1, F2 (cells) and midpoint offsets W1 (frame i1), W2
+// (frame i1 + s).
+template <typename T>
+__device__ __forceinline__ void relay(T x1, T x2, int s, T& F1, T& F2, T& W1, T& W2) {
+    if (s == 0) {                 // relay point at the midpoint
+        T D = x2 - x1;
+        F1 = T(0.5) * D;
+        F2 = F1;
+        W1 = x1 + T(0.25) * D;
+        W2 = x1 + T(0.75) * D;
+    } else if (s > 0) {           // relay point on the upper face of cell i1
+        F1 = T(1) - x1;
+        F2 = x2;
+        W1 = T(0.5) * (x1 + T(1));
+        W2 = T(0.5) * x2;
+    } else {                      // relay point on the lower face of cell i1
+        F1 = -x1;
+        F2 = x2 - T(1);
+        W1 = T(0.5) * x1;
+        W2 = T(0.5) * (x2 + T(1));
+    }
+}
+
+// Current of one straight segment inside one cell: the 12 edge values
+// (units of the fixed-point accumulator).  The product of midpoint weights is
+// the zigzag form; the +-F_p F_r / 12 term is the exact flux of a straight
+// segment through a trilinear charge cloud, which keeps the deposit exactly
+// charge conserving in three dimensions.
+//   v[0..3]  Jx at (y+b, z+c), (b,c) = (0,0) (1,0) (0,1) (1,1)
+//   v[4..7]  Jy at (x+a, z+c), (a,c) = (0,0) (1,0) (0,1) (1,1)
+//   v[8..11] Jz at (x+a, y+b), (a,b) = (0,0) (1,0) (0,1) (1,1)
+template <typename T>
+__device__ __forceinline__ void segment_values(const T cw[3], const T F[3], const T W[3], T v[12]) {
+    const T wx1 = W[0], wy1 = W[1], wz1 = W[2];
+    const T wx0 = T(1) - wx1, wy0 = T(1) - wy1, wz0 = T(1) - wz1;
+    const T twelfth = T(1) / T(12);
+    T ax = cw[0] * F[0], ay = cw[1] * F[1], az = cw[2] * F[2];
+    T kx = F[1] * F[2] * twelfth, ky = F[0] * F[2] * twelfth, kz = F[0] * F[1] * twelfth;
+    v[0] = ax * (wy0 * wz0 + kx);
+    v[1] = ax * (wy1 * wz0 - kx);
+    v[2] = ax * (wy0 * wz1 - kx);
+    v[3] = ax * (wy1 * wz1 + kx);
+    v[4] = ay * (wx0 * wz0 + ky);
+    v[5] = ay * (wx1 * wz0 - ky);
+    v[6] = ay * (wx0 * wz1 - ky);
+    v[7] = ay * (wx1 * wz1 + ky);
+    v[8] = az * (wx0 * wy0 + kz);
+    v[9] = az * (wx1 * wy0 - kz);
+    v[10] = az * (wx0 * wy1 - kz);
+    v[11] = az * (wx1 * wy1 + kz);
+}
+
+// Scatter 12 segment values of the cell (x, y, z) through Add(comp, x, y, z, fixed).
+template <typename T, typename AddFn>
+__device__ __forceinline__ void scatter12(AddFn Add, int x, int y, int z, const T v[12]) {
+#pragma unroll
+    for (int q = 0; q < 4; ++q) {
+        int b = q & 1, c = q >> 1;
+        Add(0, x, y + b, z + c, to_acc(v[q]));
+        Add(1, x + b, y, z + c, to_acc(v[4 + q]));
+        Add(2, x + b, y + c, z, to_acc(v[8 + q]));
+    }
+}
+
+// Edge (component, local x, y, z) of slot s (0..11) of the cell (x, y, z), in the
+// order of segment_values.
+__device__ __forceinline__ void slot_edge(int s, int x, int y, int z, int& comp, int& ex, int& ey, int& ez) {
+    comp = s >> 2;
+    const int q = s & 3, b = q & 1, c = q >> 1;
+    ex = x + (comp == 0 ? 0 : b);
+    ey = y + (comp == 0 ? b : comp == 1 ? 0 : c);
+    ez = z + (comp == 2 ? 0 : c);
+}
+
+// Whole zigzag deposit of one move (section 2.5): start cell (x, y, z) offsets d1,
+// cell steps s[3], end offsets d2; cw = q w / (dt d_p d_r) in fixed-point units.
+template <typename T, typename AddFn>
+__device__ __forceinline__ void zigzag_deposit(AddFn Add, int x, int y, int z, const T d1[3], const int s[3],
+                                               const T d2[3], const T cw[3]) {
+    T F1[3], F2[3], W1[3], W2[3];
+#pragma unroll
+    for (int k = 0; k < 3; ++k) relay(d1[k], d2[k], s[k], F1[k], F2[k], W1[k], W2[k]);
+    T v[12];
+    segment_values(cw, F1, W1, v);
+    if ((s[0] | s[1] | s[2]) == 0) {
+        T v2[12];
+        segment_values(cw, F2, W2, v2);
+#pragma unroll
+        for (int q = 0; q < 12; ++q) v[q] += v2[q];
+        scatter12(Add, x, y, z, v);
+    } else {
+        scatter12(Add, x, y, z, v);
+        segment_values(cw, F2, W2, v);
+        scatter12(Add, x + s[0], y + s[1], z + s[2], v);
+    }
+}
+
+__device__ __forceinline__ int wrap_idx(int i, int n) {
+    i %= n;
+    return i < 0 ? i + n : i;
+}
+
+// Ghost images of interior index i along a periodic dimension of n cells.
+__device__ __forceinline__ int images(int i, int n, int out[3]) {
+    int m = 0;
+    out[m++] = i;
+    if (i == 0) out[m++] = n;
+    if (i == n - 1) out[m++] = -1;
+    return m;
+}
+
+template <typename T>
+__device__ __forceinline__ void store3(const Geom& g, T* a0, T* a1, T* a2, int i, int j, int k, T v0, T v1, T v2) {
+    const long long c = g.pidx(i, j, k);
+    a0[c] = v0;
+    a1[c] = v1;
+    a2[c] = v2;
+    const bool edge = i == 0 || i == g.n[0] - 1 || j == 0 || j == g.n[1] - 1 || k == 0 || k == g.n[2] - 1;
+    if (!edge) return;
+    int xs[3], ys[3], zs[3];
+    const int nx = images(i, g.n[0], xs), ny = images(j, g.n[1], ys), nz = images(k, g.n[2], zs);
+    for (int c3 = 0; c3 < nz; ++c3)
+        for (int b = 0; b < ny; ++b)
+            for (int a = 0; a < nx; ++a) {
+                if (a == 0 && b == 0 && c3 == 0) continue;
+                const long long q = g.pidx(xs[a], ys[b], zs[c3]);
+                a0[q] = v0;
+                a1[q] = v1;
+                a2[q] = v2;
+            }
+}
+
+// ---------------------------------------------------------------------------
+// Host side.
+
+enum KernelClass { KC_FARADAY = 0, KC_TILE_PUSH, KC_LIST_PUSH, KC_APPEND, KC_AMPERE, KC_SORT, KC_OTHER, KC_COUNT };
+
+struct SpeciesDev {
+    double q = 0, m = 0;
+    int64_t n_loaded = 0;
+    int64_t cap_total = 0;
+    void* base[2] = {nullptr, nullptr};   // SoA blocks: current and sort target (ping-pong)
+    ParticleArrays<float> pf[2] = {};     // valid when FP32
+    ParticleArrays<double> pd[2] = {};    // valid when FP64
+    int cur = 0;                          // which block holds the particles
+    int* seg_start = nullptr;
+    int* count = nullptr;
+    int* cap = nullptr;
+    void* movers = nullptr;
+    int mover_cap = 0;
+    void* spill = nullptr;
+    int spill_cap = 0;
+    Counters* ctr = nullptr;
+    double jscale = 0;               // physical J per fixed-point unit from this species
+    std::vector<int> h_seg_start, h_cap;
+};
+
+template <typename T> inline ParticleArrays<T>& arrays(SpeciesDev& s);
+template <> inline ParticleArrays<float>& arrays<float>(SpeciesDev& s) { return s.pf[s.cur]; }
+template <> inline ParticleArrays<double>& arrays<double>(SpeciesDev& s) { return s.pd[s.cur]; }
+template <typename T> inline ParticleArrays<T>& arrays_alt(SpeciesDev& s);
+template <> inline ParticleArrays<float>& arrays_alt<float>(SpeciesDev& s) { return s.pf[s.cur ^ 1]; }
+template <> inline ParticleArrays<double>& arrays_alt<double>(SpeciesDev& s) { return s.pd[s.cur ^ 1]; }
+
+struct TimingPair {
+    int cls;
+    cudaEvent_t a, b;
+};
+
+}  // namespace gbpic
+
+struct pic_ctx {
+    pic_grid_desc desc{};
+    gbpic::Geom g{};
+    int prec = 0;
+    cudaStream_t stream = nullptr;
+    bool own_stream = false;
+    size_t esize = 4;
+    void* E[3] = {};
+    void* B[3] = {};
+    void* J[3] = {};          // JTraits<T>::acc_t arrays, compact layout
+    double jscale = 0;        // physical J per fixed-point unit (shared by all species)
+    double jinv = 0;          // 1 / jscale
+    bool fields_set = false;
+    bool j_dirty = false;     // J holds the last deposit and must be cleared before stepping
+    int64_t step = 0;
+    std::vector<gbpic::SpeciesDev> species;
+    CUtensorMap tmap[6];
+    // diagnostics
+    double* rho = nullptr;
+    double* rho_prev = nullptr;
+    double* gref = nullptr;
+    bool gref_valid = false;
+    int64_t rho_prev_step = -1;
+    double* dacc = nullptr;   // device accumulators for reductions
+    double* hist = nullptr;
+    int hist_cap = 0;
+    int64_t hist_written = 0;
+    // bookkeeping
+    int64_t launches = 0;
+    bool timing = false;
+    std::vector<gbpic::TimingPair> pending;
+    std::vector<cudaEvent_t> event_pool;
+    double kc_ms[gbpic::KC_COUNT] = {};
+    int64_t kc_n[gbpic::KC_COUNT] = {};
+    std::vector<void*> allocations;
+    std::string err;
+};
+
+namespace gbpic {
+
+// launchers (defined in the .cu files)
+pic_status launch_faraday_half(pic_ctx* c, double* rec);
+pic_status launch_ampere(pic_ctx* c, bool zero_j);
+pic_status launch_push_species(pic_ctx* c, SpeciesDev& s, int parity, double* krec);
+pic_status launch_backpush(pic_ctx* c, SpeciesDev& s);
+pic_status launch_sort(pic_ctx* c, SpeciesDev& s);
+pic_status load_species_impl(pic_ctx* c, const pic_species_desc* d, SpeciesDev& s);
+pic_status get_particles_impl(pic_ctx* c, SpeciesDev& s, double* out_dev, int64_t n_out);
+pic_status pack_fields(pic_ctx* c, double* E, double* B, double* J);   // device outputs
+pic_status unpack_fields(pic_ctx* c, const double* E, const double* B); // device inputs
+pic_status diagnostics_impl(pic_ctx* c, pic_diag* out);
+pic_status make_tensor_maps(pic_ctx* c);
+
+// helpers (api.cu)
+void* dev_alloc(pic_ctx* c, size_t bytes);
+void dev_free(pic_ctx* c, void* p);
+pic_status cuda_fail(pic_ctx* c, cudaError_t e, const char* what);
+void timing_begin(pic_ctx* c, int cls, cudaEvent_t* a);
+void timing_end(pic_ctx* c, int cls, cudaEvent_t a);
+int64_t count_alive(pic_ctx* c, SpeciesDev& s, int64_t* spilled);
+
+#define GBPIC_CHECK(c, call)                                              \
+    do {                                                                  \
+        cudaError_t e_ = (call);                                          \
+        if (e_ != cudaSuccess) return ::gbpic::cuda_fail((c), e_, #call); \
+    } while (0)
+
+// Bracket one launch with optional timing events and count it.
+struct LaunchScope {
+    pic_ctx* c;
+    int cls;
+    cudaEvent_t a = nullptr;
+    LaunchScope(pic_ctx* c_, int cls_) : c(c_), cls(cls_) {
+        timing_begin(c, cls, &a);
+        c->launches++;
+    }
+    ~LaunchScope() { timing_end(c, cls, a); }
+};
+
+}  // namespace gbpic

@@ -1,0 +1,607 @@
+// Particle kernels of one PIC cycle (KEMPIC-3D, sections 2.4-2.5):
+//   k_tile_push   one CTA per 8^3-cell tile: TMA-stages E, B of the tile and its
+//                 guard cells into shared memory, gathers, Boris-pushes, moves and
+//                 zigzag-deposits every particle of the tile into a shared fixed-point
+//                 J tile, compacts the stayers in place, writes movers to a list and
+//                 flushes J to HBM with integer atomics.
+//   k_list_push   the same step for particles held in the spill list (global-memory
+//                 gather and deposit).
+//   k_append      puts movers into the segment of their new tile (or the spill list).
+#include <cuda/std/cstdint>
+
+#include "pic_internal.cuh"
+
+namespace gbpic {
+
+template <typename T> struct PushArgs {
+    Geom g;
+    ParticleArrays<T> pa;
+    Fields<T> f;
+    T eps;          // q dt / (2 m)
+    T dtd[3];       // dt / d_d
+    T cq[3];        // q / (dt d_p d_r) / jscale : fixed-point units per unit weight
+    Rec<T>* movers;
+    int mover_cap;
+    Rec<T>* spill;
+    int spill_cap;
+    Counters* ctr;
+    int parity;
+    double* krec;   // optional: accumulate sum w m ((g_old + g_new)/2 - 1) here
+    double mass;
+};
+
+template <typename T> __host__ __device__ constexpr int box_elems() { return SB * SB * Prec<T>::BX; }
+template <typename T> __host__ __device__ constexpr int box_stride() {
+    // each staged box starts on a 128-byte boundary
+    return ((box_elems<T>() * (int)sizeof(T) + 127) / 128) * 128 / (int)sizeof(T);
+}
+template <typename T> constexpr size_t tile_smem_bytes() {
+    // + 128: the kernel rounds the dynamic shared base up to a 128-byte boundary (TMA destination)
+    return (size_t)6 * box_stride<T>() * sizeof(T) + (size_t)3 * SJ3 * sizeof(long long) + 16 + 128;
+}
+
+template <typename T>
+__device__ __forceinline__ void block_add_double(double v, double* dst) {
+    for (int o = 16; o > 0; o >>= 1) v += __shfl_xor_sync(0xffffffffu, v, o);
+    __shared__ double red[PUSH_WARPS];
+    int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
+    if (lane == 0) red[warp] = v;
+    __syncthreads();
+    if (threadIdx.x == 0) {
+        double s = 0;
+        for (int w = 0; w < PUSH_WARPS; ++w) s += red[w];
+        atomicAdd(dst, s);
+    }
+}
+
+// Reserve one slot per set lane in a device list, one atomic per warp.
+__device__ __forceinline__ int warp_reserve(int* counter, bool want) {
+    unsigned m = __ballot_sync(0xffffffffu, want);
+    if (m == 0) return -1;
+    int lane = threadIdx.x & 31;
+    int leader = __ffs(m) - 1;
+    int base = 0;
+    if (lane == leader) base = atomicAdd(counter, __popc(m));
+    base = __shfl_sync(0xffffffffu, base, leader);
+    return want ? base + __popc(m & ((1u << lane) - 1)) : -1;
+}
+
+template <typename T, bool IDS, bool RECK>
+__global__ void __launch_bounds__(PUSH_THREADS)
+k_tile_push(const __grid_constant__ CUtensorMap tE0, const __grid_constant__ CUtensorMap tE1,
+            const __grid_constant__ CUtensorMap tE2, const __grid_constant__ CUtensorMap tB0,
+            const __grid_constant__ CUtensorMap tB1, const __grid_constant__ CUtensorMap tB2, PushArgs<T> A) {
+    extern __shared__ __align__(128) unsigned char smem_raw[];
+    unsigned char* smem = reinterpret_cast<unsigned char*>((reinterpret_cast<uintptr_t>(smem_raw) + 127) & ~uintptr_t(127));
+    constexpr int BX = Prec<T>::BX;
+    constexpr int BS = box_stride<T>();
+    T* sF = reinterpret_cast<T*>(smem);
+    using Acc = typename JTraits<T>::acc_t;
+    Acc* sJ = reinterpret_cast<Acc*>(smem + (size_t)6 * BS * sizeof(T));
+    uint64_t* bar = reinterpret_cast<uint64_t*>(smem + (size_t)6 * BS * sizeof(T) + (size_t)3 * SJ3 * 8);
+    __shared__ int s_wtot[2][PUSH_WARPS];
+    __shared__ int s_timeout;
+
+    const int tile = blockIdx.x;
+    const int cnt = min(A.pa.count[tile], A.pa.cap[tile]);
+    if (cnt == 0) return;
+    const int ntx = A.g.nt[0], nty = A.g.nt[1];
+    const int tx = tile % ntx, ty = (tile / ntx) % nty, tz = tile / (ntx * nty);
+    const int ox = tx * TILE, oy = ty * TILE, oz = tz * TILE;
+
+    if (threadIdx.x == 0) {
+        s_timeout = 0;
+        mbar_init(bar, 1);
+        fence_mbar_init();
+    }
+    __syncthreads();
+    if (threadIdx.x == 0) {
+        mbar_arrive_expect_tx(bar, 6u * box_elems<T>() * sizeof(T));
+        // padded coordinate of local cell -1 is the tile origin itself
+        tma_load_3d(sF + 0 * BS, &tE0, ox, oy, oz, bar);
+        tma_load_3d(sF + 1 * BS, &tE1, ox, oy, oz, bar);
+        tma_load_3d(sF + 2 * BS, &tE2, ox, oy, oz, bar);
+        tma_load_3d(sF + 3 * BS, &tB0, ox, oy, oz, bar);
+        tma_load_3d(sF + 4 * BS, &tB1, ox, oy, oz, bar);
+        tma_load_3d(sF + 5 * BS, &tB2, ox, oy, oz, bar);
+    }
+    for (int i = threadIdx.x; i < 3 * SJ3; i += PUSH_THREADS) sJ[i] = Acc(0);
+    {
+        int polls = 0;
+        while (!mbar_try_wait(bar, 0)) {
+            if (++polls > MBAR_MAX_POLLS) {
+                s_timeout = 1;
+                break;
+            }
+        }
+    }
+    __syncthreads();
+    if (s_timeout) {
+        if (threadIdx.x == 0) {
+            atomicOr(&A.ctr->err, ERRB_TIMEOUT);
+            // wait (bounded) for the copies still in flight before the CTA exits
+            int polls = 0;
+            while (!mbar_try_wait(bar, 0) && ++polls < MBAR_MAX_POLLS) {
+            }
+        }
+        __syncthreads();
+        return;
+    }
+
+    auto fetch = [&](int comp, int x, int y, int z) -> T {
+        return sF[comp * BS + ((z + 1) * SB + (y + 1)) * BX + (x + 1)];
+    };
+    auto add = [&](int comp, int x, int y, int z, Acc v) {
+        if (v != Acc(0)) acc_atomic(&sJ[comp * SJ3 + ((z + 1) * SJ + (y + 1)) * SJ + (x + 1)], v);
+    };
+
+    const int seg = A.pa.seg_start[tile];
+    const int ext[3] = {min(TILE, A.g.n[0] - ox), min(TILE, A.g.n[1] - oy), min(TILE, A.g.n[2] - oz)};
+    const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
+    int written = 0;
+    double kacc = 0.0;
+
+    for (int base = 0, it = 0; base < cnt; base += PUSH_THREADS, ++it) {
+        const int i = base + threadIdx.x;
+        const bool active = i < cnt;
+        bool stay = false, move = false;
+        int lc = 0, pid = 0;
+        bool crossed = false;
+        T d2[3], u[3], w = T(0), v[12], v2[12];
+#pragma unroll
+        for (int q = 0; q < 12; ++q) v[q] = T(0);
+        int s[3] = {0, 0, 0};
+        int x = 0, y = 0, z = 0;
+        if (active) {
+            const long long p = (long long)seg + i;
+            lc = __ldcs(A.pa.cell + p);
+            T d1[3] = {__ldcs(A.pa.d[0] + p), __ldcs(A.pa.d[1] + p), __ldcs(A.pa.d[2] + p)};
+            u[0] = __ldcs(A.pa.u[0] + p);
+            u[1] = __ldcs(A.pa.u[1] + p);
+            u[2] = __ldcs(A.pa.u[2] + p);
+            w = __ldcs(A.pa.w + p);
+            if (IDS) pid = __ldcs(A.pa.id + p);
+            x = lc & 7;
+            y = (lc >> 3) & 7;
+            z = lc >> 6;
+            T Ep[3], Bp[3];
+            gather_eb<T>(fetch, x, y, z, d1[0], d1[1], d1[2], Ep, Bp);
+            T gm1_old = T(0);
+            if (RECK) gm1_old = gamma_minus_one(u);
+            const T ig = boris(A.eps, Ep, Bp, u);
+            if (!(ig > T(0))) atomicOr(&A.ctr->err, ERRB_NAN);
+            if (RECK) kacc += (double)w * A.mass * 0.5 * ((double)gm1_old + (double)gamma_minus_one(u));
+#pragma unroll
+            for (int k = 0; k < 3; ++k) {
+                s[k] = advance(d1[k], A.dtd[k] * u[k] * ig, d2[k]);
+                if (s[k] > 1 || s[k] < -1) {
+                    atomicOr(&A.ctr->err, ERRB_SUPERLUMINAL);
+                    s[k] = s[k] > 0 ? 1 : -1;
+                }
+            }
+            const T cw[3] = {A.cq[0] * w, A.cq[1] * w, A.cq[2] * w};
+            T F1[3], F2[3], W1[3], W2[3];
+#pragma unroll
+            for (int k = 0; k < 3; ++k) relay(d1[k], d2[k], s[k], F1[k], F2[k], W1[k], W2[k]);
+            segment_values(cw, F1, W1, v);
+            segment_values(cw, F2, W2, v2);
+            crossed = (s[0] | s[1] | s[2]) != 0;
+            if (!crossed) {
+#pragma unroll
+                for (int q = 0; q < 12; ++q) v[q] += v2[q];
+            }
+        }
+        // Deposit of the start-cell segment(s), cooperatively per warp: lanes whose
+        // particles share the warp's most common start cell sum their 12 edge values
+        // with a reduce-scatter and 12 lanes add the sums; the other lanes add directly.
+        {
+            const int key = active ? lc : -1 - lane;
+            const unsigned grp = __match_any_sync(0xffffffffu, key);
+            const unsigned sz = active ? (unsigned)__popc(grp) : 0u;
+            const unsigned best = __reduce_max_sync(0xffffffffu, sz);
+            if (best >= 2) {
+                const bool lead = active && sz == best && (__ffs(grp) - 1) == lane;
+                const int ml = __ffs(__ballot_sync(0xffffffffu, lead)) - 1;
+                const unsigned mgrp = __shfl_sync(0xffffffffu, grp, ml);
+                const int mlc = __shfl_sync(0xffffffffu, lc, ml);
+                const bool in_major = (mgrp >> lane) & 1u;
+                T b[16];
+#pragma unroll
+                for (int q = 0; q < 12; ++q) b[q] = in_major ? v[q] : T(0);
+#pragma unroll
+                for (int q = 12; q < 16; ++q) b[q] = T(0);
+                const T r = reduce_scatter16(b, lane);
+                const int slot = lane >> 1;
+                if (!(lane & 1) && slot < 12) {
+                    int comp, ex, ey, ez;
+                    slot_edge(slot, mlc & 7, (mlc >> 3) & 7, mlc >> 6, comp, ex, ey, ez);
+                    const Acc a = to_acc(r);
+                    if (a != Acc(0)) add(comp, ex, ey, ez, a);
+                }
+                if (active && !in_major) scatter12(add, x, y, z, v);
+            } else if (active) {
+                scatter12(add, x, y, z, v);
+            }
+            if (crossed) scatter12(add, x + s[0], y + s[1], z + s[2], v2);
+        }
+        if (active) {
+            const int nx = x + s[0], ny = y + s[1], nz = z + s[2];
+            stay = nx >= 0 && nx < ext[0] && ny >= 0 && ny < ext[1] && nz >= 0 && nz < ext[2];
+            move = !stay;
+            if (stay) lc = nx | (ny << 3) | (nz << 6);
+        }
+        // movers: to the global list with their wrapped global cell
+        const int slot = warp_reserve(&A.ctr->mover_count[A.parity], move);
+        if (move) {
+            if (slot < A.mover_cap) {
+                Rec<T> r;
+                const int gx = wrap_idx(ox + x + s[0], A.g.n[0]);
+                const int gy = wrap_idx(oy + y + s[1], A.g.n[1]);
+                const int gz = wrap_idx(oz + z + s[2], A.g.n[2]);
+                r.cell = (gz * A.g.n[1] + gy) * A.g.n[0] + gx;
+                r.id = pid;
+                r.d[0] = d2[0];
+                r.d[1] = d2[1];
+                r.d[2] = d2[2];
+                r.u[0] = u[0];
+                r.u[1] = u[1];
+                r.u[2] = u[2];
+                r.w = w;
+                A.movers[slot] = r;
+            } else {
+                atomicOr(&A.ctr->err, ERRB_OVERFLOW);
+            }
+        }
+        // in-place, order-preserving compaction of the stayers
+        const unsigned bal = __ballot_sync(0xffffffffu, stay);
+        const int buf = it & 1;
+        if (lane == 0) s_wtot[buf][warp] = __popc(bal);
+        __syncthreads();
+        int before = 0, total = 0;
+#pragma unroll
+        for (int wv = 0; wv < PUSH_WARPS; ++wv) {
+            const int t = s_wtot[buf][wv];
+            before += wv < warp ? t : 0;
+            total += t;
+        }
+        if (stay) {
+            const long long q = (long long)seg + written + before + __popc(bal & ((1u << lane) - 1));
+            __stcs(A.pa.cell + q, lc);
+            __stcs(A.pa.d[0] + q, d2[0]);
+            __stcs(A.pa.d[1] + q, d2[1]);
+            __stcs(A.pa.d[2] + q, d2[2]);
+            __stcs(A.pa.u[0] + q, u[0]);
+            __stcs(A.pa.u[1] + q, u[1]);
+            __stcs(A.pa.u[2] + q, u[2]);
+            __stcs(A.pa.w + q, w);
+            if (IDS) __stcs(A.pa.id + q, pid);
+        }
+        written += total;
+    }
+    __syncthreads();
+    if (threadIdx.x == 0) A.pa.count[tile] = written;
+
+    // flush the shared J tile to HBM (periodic wrap of the guard layers)
+    for (int e = threadIdx.x; e < 3 * SJ3; e += PUSH_THREADS) {
+        const Acc v = sJ[e];
+        if (v == Acc(0)) continue;
+        const int comp = e / SJ3;
+        const int r = e - comp * SJ3;
+        const int lx = r % SJ - 1, ly = (r / SJ) % SJ - 1, lz = r / (SJ * SJ) - 1;
+        const int gx = wrap_idx(ox + lx, A.g.n[0]);
+        const int gy = wrap_idx(oy + ly, A.g.n[1]);
+        const int gz = wrap_idx(oz + lz, A.g.n[2]);
+        acc_atomic(A.f.J[comp] + A.g.cidx(gx, gy, gz), v);
+    }
+    if (RECK) block_add_double<T>(kacc, A.krec);
+}
+
+// Spill-list particles: same arithmetic with global-memory gather and deposit.
+template <typename T, bool RECK>
+__global__ void __launch_bounds__(256) k_list_push(PushArgs<T> A) {
+    const int n = min(A.ctr->spill_count[A.parity], A.spill_cap);
+    double kacc = 0.0;
+    for (int i = blockIdx.x * blockDim.x + threadIdx.x; i < n; i += gridDim.x * blockDim.x) {
+        Rec<T> r = A.spill[i];
+        const int gx = r.cell % A.g.n[0], gy = (r.cell / A.g.n[0]) % A.g.n[1], gz = r.cell / (A.g.n[0] * A.g.n[1]);
+        auto fetch = [&](int comp, int x, int y, int z) -> T {
+            const T* a = comp < 3 ? A.f.E[comp] : A.f.B[comp - 3];
+            return a[A.g.pidx(x, y, z)];
+        };
+        using Acc = typename JTraits<T>::acc_t;
+        auto add = [&](int comp, int x, int y, int z, Acc v) {
+            if (v != Acc(0))
+                acc_atomic(A.f.J[comp] + A.g.cidx(wrap_idx(x, A.g.n[0]), wrap_idx(y, A.g.n[1]), wrap_idx(z, A.g.n[2])), v);
+        };
+        T Ep[3], Bp[3], u[3] = {r.u[0], r.u[1], r.u[2]}, d2[3];
+        gather_eb<T>(fetch, gx, gy, gz, r.d[0], r.d[1], r.d[2], Ep, Bp);
+        T gm1_old = T(0);
+        if (RECK) gm1_old = gamma_minus_one(u);
+        const T ig = boris(A.eps, Ep, Bp, u);
+        if (!(ig > T(0))) atomicOr(&A.ctr->err, ERRB_NAN);
+        if (RECK) kacc += (double)r.w * A.mass * 0.5 * ((double)gm1_old + (double)gamma_minus_one(u));
+        int s[3];
+        for (int k = 0; k < 3; ++k) {
+            s[k] = advance(r.d[k], A.dtd[k] * u[k] * ig, d2[k]);
+            if (s[k] > 1 || s[k] < -1) {
+                atomicOr(&A.ctr->err, ERRB_SUPERLUMINAL);
+                s[k] = s[k] > 0 ? 1 : -1;
+            }
+        }
+        const T cw[3] = {A.cq[0] * r.w, A.cq[1] * r.w, A.cq[2] * r.w};
+        zigzag_deposit<T>(add, gx, gy, gz, r.d, s, d2, cw);
+        Rec<T> o;
+        o.cell = (wrap_idx(gz + s[2], A.g.n[2]) * A.g.n[1] + wrap_idx(gy + s[1], A.g.n[1])) * A.g.n[0] +
+                 wrap_idx(gx + s[0], A.g.n[0]);
+        o.id = r.id;
+        for (int k = 0; k < 3; ++k) {
+            o.d[k] = d2[k];
+            o.u[k] = u[k];
+        }
+        o.w = r.w;
+        const int slot = atomicAdd(&A.ctr->mover_count[A.parity], 1);
+        if (slot < A.mover_cap) A.movers[slot] = o;
+        else atomicOr(&A.ctr->err, ERRB_OVERFLOW);
+    }
+    if (RECK) {
+        for (int o = 16; o > 0; o >>= 1) kacc += __shfl_xor_sync(0xffffffffu, kacc, o);
+        if ((threadIdx.x & 31) == 0 && kacc != 0.0) atomicAdd(A.krec, kacc);
+    }
+}
+
+// Movers into the segment of their new tile; a full segment sends them to the
+// spill list of the next step.  Also resets the counters of the other parity.
+template <typename T, bool IDS>
+__global__ void __launch_bounds__(256) k_append(PushArgs<T> A) {
+    const int n = min(A.ctr->mover_count[A.parity], A.mover_cap);
+    const int nxt = A.parity ^ 1;
+    if (blockIdx.x == 0 && threadIdx.x == 0) {
+        A.ctr->mover_count[nxt] = 0;       // consumed by the previous step's append
+        A.ctr->spill_count[A.parity] = 0;  // consumed by this step's list push
+    }
+    for (int i = blockIdx.x * blockDim.x + threadIdx.x; i < n; i += gridDim.x * blockDim.x) {
+        const Rec<T> r = A.movers[i];
+        const int gx = r.cell % A.g.n[0], gy = (r.cell / A.g.n[0]) % A.g.n[1], gz = r.cell / (A.g.n[0] * A.g.n[1]);
+        const int tx = gx >> 3, ty = gy >> 3, tz = gz >> 3;
+        const int t = (tz * A.g.nt[1] + ty) * A.g.nt[0] + tx;
+        const int slot = atomicAdd(A.pa.count + t, 1);
+        if (slot < A.pa.cap[t]) {
+            const long long q = (long long)A.pa.seg_start[t] + slot;
+            A.pa.cell[q] = (gx & 7) | ((gy & 7) << 3) | ((gz & 7) << 6);
+            A.pa.d[0][q] = r.d[0];
+            A.pa.d[1][q] = r.d[1];
+            A.pa.d[2][q] = r.d[2];
+            A.pa.u[0][q] = r.u[0];
+            A.pa.u[1][q] = r.u[1];
+            A.pa.u[2][q] = r.u[2];
+            A.pa.w[q] = r.w;
+            if (IDS) A.pa.id[q] = r.id;
+        } else {
+            const int sp = atomicAdd(&A.ctr->spill_count[nxt], 1);
+            if (sp < A.spill_cap) A.spill[sp] = r;
+            else atomicOr(&A.ctr->err, ERRB_OVERFLOW);
+        }
+    }
+}
+
+// Backward Boris half step u^0 -> u^{-1/2} (section 2.4) for the particles of the
+// tile segments, with E^0 and B^0 read from global memory.
+template <typename T>
+__global__ void __launch_bounds__(256) k_backpush(PushArgs<T> A, const T* B0x, const T* B0y, const T* B0z) {
+    const int ntile = A.g.nt[0] * A.g.nt[1] * A.g.nt[2];
+    for (int t = blockIdx.x; t < ntile; t += gridDim.x) {
+        const int cnt = min(A.pa.count[t], A.pa.cap[t]);
+        const int tx = t % A.g.nt[0], ty = (t / A.g.nt[0]) % A.g.nt[1], tz = t / (A.g.nt[0] * A.g.nt[1]);
+        for (int i = threadIdx.x; i < cnt; i += blockDim.x) {
+            const long long p = (long long)A.pa.seg_start[t] + i;
+            const int lc = A.pa.cell[p];
+            const int gx = tx * TILE + (lc & 7), gy = ty * TILE + ((lc >> 3) & 7), gz = tz * TILE + (lc >> 6);
+            auto fetch = [&](int comp, int x, int y, int z) -> T {
+                const T* a = comp < 3 ? A.f.E[comp] : (comp == 3 ? B0x : comp == 4 ? B0y : B0z);
+                return a[A.g.pidx(x, y, z)];
+            };
+            T Ep[3], Bp[3], u[3] = {A.pa.u[0][p], A.pa.u[1][p], A.pa.u[2][p]};
+            gather_eb<T>(fetch, gx, gy, gz, A.pa.d[0][p], A.pa.d[1][p], A.pa.d[2][p], Ep, Bp);
+            boris(A.eps, Ep, Bp, u);
+            A.pa.u[0][p] = u[0];
+            A.pa.u[1][p] = u[1];
+            A.pa.u[2][p] = u[2];
+        }
+    }
+}
+
+// ---------------------------------------------------------------------------
+// Host launchers.
+
+
+template <typename T>
+static PushArgs<T> make_args(pic_ctx* c, SpeciesDev& s, int parity, double* krec, double dt_scale) {
+    PushArgs<T> A{};
+    A.g = c->g;
+    A.pa = arrays<T>(s);
+    for (int k = 0; k < 3; ++k) {
+        A.f.E[k] = static_cast<T*>(c->E[k]);
+        A.f.B[k] = static_cast<T*>(c->B[k]);
+        A.f.J[k] = static_cast<typename JTraits<T>::acc_t*>(c->J[k]);
+    }
+    const double dt = c->desc.dt * dt_scale;
+    const double* d = c->desc.d;
+    A.eps = (T)(s.q * dt / (2.0 * s.m));
+    for (int k = 0; k < 3; ++k) A.dtd[k] = (T)(dt / d[k]);
+    A.cq[0] = (T)(s.q / (dt * d[1] * d[2]) * c->jinv);
+    A.cq[1] = (T)(s.q / (dt * d[2] * d[0]) * c->jinv);
+    A.cq[2] = (T)(s.q / (dt * d[0] * d[1]) * c->jinv);
+    A.movers = static_cast<Rec<T>*>(s.movers);
+    A.mover_cap = s.mover_cap;
+    A.spill = static_cast<Rec<T>*>(s.spill);
+    A.spill_cap = s.spill_cap;
+    A.ctr = s.ctr;
+    A.parity = parity;
+    A.krec = krec;
+    A.mass = s.m;
+    return A;
+}
+
+static int sm_count(pic_ctx* c) {
+    int v = 0;
+    cudaDeviceGetAttribute(&v, cudaDevAttrMultiProcessorCount, c->desc.device);
+    return v > 0 ? v : 152;
+}
+
+template <typename T, bool IDS, bool RECK>
+static pic_status launch_tile(pic_ctx* c, PushArgs<T>& A) {
+    auto kern = k_tile_push<T, IDS, RECK>;
+    const size_t smem = tile_smem_bytes<T>();
+    static bool attr_set = false;
+    if (!attr_set) {
+        GBPIC_CHECK(c, cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem));
+        attr_set = true;
+    }
+    const int ntile = c->g.nt[0] * c->g.nt[1] * c->g.nt[2];
+    LaunchScope ls(c, KC_TILE_PUSH);
+    kern<<<ntile, PUSH_THREADS, smem, c->stream>>>(c->tmap[0], c->tmap[1], c->tmap[2], c->tmap[3], c->tmap[4],
+                                                     c->tmap[5], A);
+    GBPIC_CHECK(c, cudaGetLastError());
+    return PIC_OK;
+}
+
+template <typename T>
+static pic_status push_species_t(pic_ctx* c, SpeciesDev& s, int parity, double* krec) {
+    PushArgs<T> A = make_args<T>(c, s, parity, krec, 1.0);
+    const bool ids = c->desc.track_ids != 0, rec = krec != nullptr;
+    pic_status st;
+    if (ids) st = rec ? launch_tile<T, true, true>(c, A) : launch_tile<T, true, false>(c, A);
+    else st = rec ? launch_tile<T, false, true>(c, A) : launch_tile<T, false, false>(c, A);
+    if (st != PIC_OK) return st;
+    const int grid = 2 * sm_count(c);
+    {
+        LaunchScope ls(c, KC_LIST_PUSH);
+        if (rec) k_list_push<T, true><<<grid, 256, 0, c->stream>>>(A);
+        else k_list_push<T, false><<<grid, 256, 0, c->stream>>>(A);
+        GBPIC_CHECK(c, cudaGetLastError());
+    }
+    {
+        LaunchScope ls(c, KC_APPEND);
+        if (ids) k_append<T, true><<<grid, 256, 0, c->stream>>>(A);
+        else k_append<T, false><<<grid, 256, 0, c->stream>>>(A);
+        GBPIC_CHECK(c, cudaGetLastError());
+    }
+    return PIC_OK;
+}
+
+pic_status launch_push_species(pic_ctx* c, SpeciesDev& s, int parity, double* krec) {
+    return c->prec == PIC_FP64 ? push_species_t<double>(c, s, parity, krec)
+                               : push_species_t<float>(c, s, parity, krec);
+}
+
+template <typename T>
+static pic_status backpush_t(pic_ctx* c, SpeciesDev& s) {
+    // B^0 = B^{-1/2} - dt/2 curl E^0 into scratch arrays, then a Boris step of -dt/2
+    const size_t bytes = (size_t)c->g.padded_size() * sizeof(T);
+    T* B0[3];
+    for (int k = 0; k < 3; ++k) {
+        B0[k] = static_cast<T*>(dev_alloc(c, bytes));
+        if (!B0[k]) return PIC_ERR_OOM;
+        GBPIC_CHECK(c, cudaMemcpyAsync(B0[k], c->B[k], bytes, cudaMemcpyDeviceToDevice, c->stream));
+    }
+    void* saved[3] = {c->B[0], c->B[1], c->B[2]};
+    for (int k = 0; k < 3; ++k) c->B[k] = B0[k];
+    pic_status st = launch_faraday_half(c, nullptr);
+    for (int k = 0; k < 3; ++k) c->B[k] = saved[k];
+    if (st != PIC_OK) return st;
+    PushArgs<T> A = make_args<T>(c, s, 0, nullptr, -0.5);
+    {
+        LaunchScope ls(c, KC_OTHER);
+        k_backpush<T><<<4 * sm_count(c), 256, 0, c->stream>>>(A, B0[0], B0[1], B0[2]);
+        GBPIC_CHECK(c, cudaGetLastError());
+    }
+    GBPIC_CHECK(c, cudaStreamSynchronize(c->stream));
+    for (int k = 0; k < 3; ++k) dev_free(c, B0[k]);
+    return PIC_OK;
+}
+
+pic_status launch_backpush(pic_ctx* c, SpeciesDev& s) {
+    return c->prec == PIC_FP64 ? backpush_t<double>(c, s) : backpush_t<float>(c, s);
+}
+
+// Counting sort of every tile segment by local cell (ping-pong between the two SoA
+// blocks of a species).  Restores the cell order that the in-place compaction and
+// the appended movers erode, so that the lanes of a warp share cells: the gather
+// then reads broadcast shared-memory values and the deposit reduces per warp.
+template <typename T, bool IDS>
+__global__ void __launch_bounds__(256) k_sort_tiles(ParticleArrays<T> src, ParticleArrays<T> dst) {
+    __shared__ int hist[TILE_CELLS];
+    __shared__ int wsum[8];
+    const int t = blockIdx.x;
+    const int cnt = min(src.count[t], src.cap[t]);
+    if (cnt == 0) return;
+    const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
+    for (int i = threadIdx.x; i < TILE_CELLS; i += 256) hist[i] = 0;
+    __syncthreads();
+    const long long seg = src.seg_start[t];
+    for (int base = 0; base < cnt; base += 256) {
+        const int i = base + threadIdx.x;
+        const bool act = i < cnt;
+        const int c = act ? src.cell[seg + i] : -1 - lane;
+        const unsigned g = __match_any_sync(0xffffffffu, c);
+        if (act && (__ffs(g) - 1) == lane) atomicAdd(&hist[c], __popc(g));
+    }
+    __syncthreads();
+    // exclusive scan of the 512 counts: two per thread, warp scans, then warp offsets
+    const int a0 = hist[2 * threadIdx.x], a1 = hist[2 * threadIdx.x + 1];
+    int incl = a0 + a1;
+#pragma unroll
+    for (int o = 1; o < 32; o <<= 1) {
+        const int y = __shfl_up_sync(0xffffffffu, incl, o);
+        if (lane >= o) incl += y;
+    }
+    if (lane == 31) wsum[warp] = incl;
+    __syncthreads();
+    int woff = 0;
+    for (int w2 = 0; w2 < warp; ++w2) woff += wsum[w2];
+    const int excl = woff + incl - (a0 + a1);
+    hist[2 * threadIdx.x] = excl;
+    hist[2 * threadIdx.x + 1] = excl + a0;
+    __syncthreads();
+    for (int base = 0; base < cnt; base += 256) {
+        const int i = base + threadIdx.x;
+        const bool act = i < cnt;
+        const int c = act ? src.cell[seg + i] : -1 - lane;
+        const unsigned g = __match_any_sync(0xffffffffu, c);
+        const int leader = __ffs(g) - 1;
+        int b = 0;
+        if (act && lane == leader) b = atomicAdd(&hist[c], __popc(g));
+        b = __shfl_sync(0xffffffffu, b, leader);
+        if (act) {
+            const long long p = seg + i;
+            const long long q = seg + b + __popc(g & ((1u << lane) - 1));
+            dst.cell[q] = c;
+#pragma unroll
+            for (int k = 0; k < 3; ++k) {
+                dst.d[k][q] = __ldcs(src.d[k] + p);
+                dst.u[k][q] = __ldcs(src.u[k] + p);
+            }
+            dst.w[q] = __ldcs(src.w + p);
+            if (IDS) dst.id[q] = __ldcs(src.id + p);
+        }
+    }
+}
+
+template <typename T>
+static pic_status sort_t(pic_ctx* c, SpeciesDev& s) {
+    const int ntile = c->g.nt[0] * c->g.nt[1] * c->g.nt[2];
+    {
+        LaunchScope ls(c, KC_SORT);
+        if (c->desc.track_ids) k_sort_tiles<T, true><<<ntile, 256, 0, c->stream>>>(arrays<T>(s), arrays_alt<T>(s));
+        else k_sort_tiles<T, false><<<ntile, 256, 0, c->stream>>>(arrays<T>(s), arrays_alt<T>(s));
+        GBPIC_CHECK(c, cudaGetLastError());
+    }
+    s.cur ^= 1;
+    return PIC_OK;
+}
+
+pic_status launch_sort(pic_ctx* c, SpeciesDev& s) {
+    return c->prec == PIC_FP64 ? sort_t<double>(c, s) : sort_t<float>(c, s);
+}
+
+}  // namespace gbpic

@@ -1,0 +1,385 @@
+// Set-up and read-out kernels: species loading (positions to cell + offset in the
+// working precision, counting sort into 8^3-cell tile segments ordered by cell),
+// field upload with ghost images, and FP64 read-out of fields and particles.
+#include <algorithm>
+#include <cmath>
+#include <cstring>
+
+#include "pic_internal.cuh"
+
+namespace gbpic {
+
+
+// Position (cell units) -> global cell and in-cell offset in the working precision.
+// An offset that rounds to 1 moves to offset 0 of the next cell.  Returns false for
+// a position outside [0, n) or not finite.
+template <typename T>
+__device__ __forceinline__ bool locate(const Geom& g, const double X[3], int c[3], T dl[3]) {
+    for (int k = 0; k < 3; ++k) {
+        const double x = X[k];
+        if (!(x >= 0.0 && x < (double)g.n[k])) return false;
+        double f = floor(x);
+        int ci = (int)f;
+        T o = (T)(x - f);
+        if (o >= T(1)) {
+            o = T(0);
+            ci += 1;
+            if (ci >= g.n[k]) ci = 0;
+        }
+        c[k] = ci;
+        dl[k] = o;
+    }
+    return true;
+}
+
+__device__ __forceinline__ int key_of(const Geom& g, const int c[3]) {
+    const int t = ((c[2] >> 3) * g.nt[1] + (c[1] >> 3)) * g.nt[0] + (c[0] >> 3);
+    return t * TILE_CELLS + ((c[0] & 7) | ((c[1] & 7) << 3) | ((c[2] & 7) << 6));
+}
+
+template <typename T>
+__global__ void k_keys(Geom g, const double* X, const double* w, long long n, int* hist, int* bad,
+                       unsigned long long* wmax_bits) {
+    for (long long p = blockIdx.x * (long long)blockDim.x + threadIdx.x; p < n; p += (long long)gridDim.x * blockDim.x) {
+        const double Xp[3] = {X[p], X[n + p], X[2 * n + p]};
+        int c[3];
+        T dl[3];
+        const double wp = w[p];
+        if (!locate<T>(g, Xp, c, dl) || !(wp > 0.0) || !isfinite(wp)) {
+            atomicOr(bad, 1);
+            continue;
+        }
+        atomicAdd(hist + key_of(g, c), 1);
+        atomicMax(wmax_bits, (unsigned long long)__double_as_longlong(wp));
+    }
+}
+
+template <typename T>
+__global__ void k_scatter(Geom g, const double* X, const double* U, const double* w, long long n, int* keypos,
+                          ParticleArrays<T> pa, int track_ids) {
+    for (long long p = blockIdx.x * (long long)blockDim.x + threadIdx.x; p < n; p += (long long)gridDim.x * blockDim.x) {
+        const double Xp[3] = {X[p], X[n + p], X[2 * n + p]};
+        int c[3];
+        T dl[3];
+        if (!locate<T>(g, Xp, c, dl)) continue;
+        const int key = key_of(g, c);
+        const int q = atomicAdd(keypos + key, 1);
+        pa.cell[q] = key & (TILE_CELLS - 1);
+        for (int k = 0; k < 3; ++k) {
+            pa.d[k][q] = dl[k];
+            pa.u[k][q] = (T)U[k * n + p];
+        }
+        pa.w[q] = (T)w[p];
+        if (track_ids) pa.id[q] = (int)p;
+    }
+}
+
+static size_t align256(size_t b) { return (b + 255) & ~(size_t)255; }
+
+template <typename T>
+static pic_status load_t(pic_ctx* c, const pic_species_desc* d, SpeciesDev& s) {
+    const long long n = d->n;
+    const Geom& g = c->g;
+    const int ntile = g.nt[0] * g.nt[1] * g.nt[2];
+    const long long nkeys = (long long)ntile * TILE_CELLS;
+    // staging: device copies of the FP64 inputs
+    const double *X = d->X, *U = d->u, *W = d->w;
+    double* stage = nullptr;
+    if (!d->device_pointers && n > 0) {
+        stage = static_cast<double*>(dev_alloc(c, sizeof(double) * 7 * n));
+        if (!stage) return PIC_ERR_OOM;
+        GBPIC_CHECK(c, cudaMemcpyAsync(stage, d->X, sizeof(double) * 3 * n, cudaMemcpyHostToDevice, c->stream));
+        GBPIC_CHECK(c, cudaMemcpyAsync(stage + 3 * n, d->u, sizeof(double) * 3 * n, cudaMemcpyHostToDevice, c->stream));
+        GBPIC_CHECK(c, cudaMemcpyAsync(stage + 6 * n, d->w, sizeof(double) * n, cudaMemcpyHostToDevice, c->stream));
+        X = stage;
+        U = stage + 3 * n;
+        W = stage + 6 * n;
+    }
+    int* hist = static_cast<int*>(dev_alloc(c, sizeof(int) * (nkeys + 2) + 8));
+    if (!hist) return PIC_ERR_OOM;
+    int* bad = hist + nkeys;
+    unsigned long long* wmax_bits = reinterpret_cast<unsigned long long*>(hist + nkeys + 2);
+    GBPIC_CHECK(c, cudaMemsetAsync(hist, 0, sizeof(int) * (nkeys + 2) + 8, c->stream));
+    const int grid = 1024;
+    if (n > 0) {
+        LaunchScope ls(c, KC_OTHER);
+        k_keys<T><<<grid, 256, 0, c->stream>>>(g, X, W, n, hist, bad, wmax_bits);
+        GBPIC_CHECK(c, cudaGetLastError());
+    }
+    std::vector<int> h_hist(nkeys);
+    int h_bad = 0;
+    unsigned long long h_wbits = 0;
+    GBPIC_CHECK(c, cudaMemcpyAsync(h_hist.data(), hist, sizeof(int) * nkeys, cudaMemcpyDeviceToHost, c->stream));
+    GBPIC_CHECK(c, cudaMemcpyAsync(&h_bad, bad, sizeof(int), cudaMemcpyDeviceToHost, c->stream));
+    GBPIC_CHECK(c, cudaMemcpyAsync(&h_wbits, wmax_bits, 8, cudaMemcpyDeviceToHost, c->stream));
+    GBPIC_CHECK(c, cudaStreamSynchronize(c->stream));
+    if (h_bad) {
+        c->err = "pic_load_species: a position is outside [0, n) or a weight is not positive and finite";
+        dev_free(c, hist);
+        if (stage) dev_free(c, stage);
+        return PIC_ERR_ARG;
+    }
+    double wmax = 0;
+    memcpy(&wmax, &h_wbits, 8);
+    // tile capacities and segment starts (host), key positions within segments
+    const double slack = d->capacity_slack > 0 ? d->capacity_slack : 0.25;
+    s.h_seg_start.assign(ntile, 0);
+    s.h_cap.assign(ntile, 0);
+    std::vector<int> h_count(ntile, 0);
+    long long total = 0;
+    for (int t = 0; t < ntile; ++t) {
+        long long cnt = 0;
+        for (int l = 0; l < TILE_CELLS; ++l) cnt += h_hist[(size_t)t * TILE_CELLS + l];
+        long long cap = cnt + std::max<long long>((long long)std::ceil(slack * cnt), 32);
+        cap = (cap + 31) / 32 * 32;
+        s.h_seg_start[t] = (int)total;
+        s.h_cap[t] = (int)cap;
+        h_count[t] = (int)cnt;
+        total += cap;
+        if (total > 0x7fffff00LL) {
+            c->err = "pic_load_species: more than 2^31 particle slots";
+            return PIC_ERR_ARG;
+        }
+    }
+    std::vector<int> h_keypos(nkeys);
+    for (int t = 0; t < ntile; ++t) {
+        int acc = s.h_seg_start[t];
+        for (int l = 0; l < TILE_CELLS; ++l) {
+            h_keypos[(size_t)t * TILE_CELLS + l] = acc;
+            acc += h_hist[(size_t)t * TILE_CELLS + l];
+        }
+    }
+    GBPIC_CHECK(c, cudaMemcpyAsync(hist, h_keypos.data(), sizeof(int) * nkeys, cudaMemcpyHostToDevice, c->stream));
+    // two particle blocks (current and sort target), each: cell, d[3], u[3], w, id;
+    // then the per-tile segment arrays and the counters, shared by both blocks
+    const size_t cap = (size_t)total;
+    const size_t a_int = align256(cap * sizeof(int)), a_t = align256(cap * sizeof(T));
+    const size_t pbytes = a_int * 2 + a_t * 7;
+    const size_t bytes = pbytes + align256(sizeof(int) * ntile) * 3 + align256(sizeof(Counters));
+    unsigned char* base = static_cast<unsigned char*>(dev_alloc(c, bytes));
+    unsigned char* base2 = static_cast<unsigned char*>(dev_alloc(c, pbytes));
+    if (!base || !base2) return PIC_ERR_OOM;
+    s.base[0] = base;
+    s.base[1] = base2;
+    s.cur = 0;
+    size_t off = pbytes;
+    s.seg_start = reinterpret_cast<int*>(base + off); off += align256(sizeof(int) * ntile);
+    s.count = reinterpret_cast<int*>(base + off); off += align256(sizeof(int) * ntile);
+    s.cap = reinterpret_cast<int*>(base + off); off += align256(sizeof(int) * ntile);
+    s.ctr = reinterpret_cast<Counters*>(base + off);
+    for (int b = 0; b < 2; ++b) {
+        ParticleArrays<T>& pb = b == 0 ? arrays<T>(s) : arrays_alt<T>(s);
+        unsigned char* blk = static_cast<unsigned char*>(s.base[b]);
+        size_t o = 0;
+        pb.cell = reinterpret_cast<int*>(blk + o); o += a_int;
+        for (int k = 0; k < 3; ++k) { pb.d[k] = reinterpret_cast<T*>(blk + o); o += a_t; }
+        for (int k = 0; k < 3; ++k) { pb.u[k] = reinterpret_cast<T*>(blk + o); o += a_t; }
+        pb.w = reinterpret_cast<T*>(blk + o); o += a_t;
+        pb.id = reinterpret_cast<int*>(blk + o); o += a_int;
+        pb.seg_start = s.seg_start;
+        pb.count = s.count;
+        pb.cap = s.cap;
+    }
+    ParticleArrays<T>& pa = arrays<T>(s);
+    GBPIC_CHECK(c, cudaMemsetAsync(base, 0, bytes, c->stream));
+    GBPIC_CHECK(c, cudaMemcpyAsync(s.seg_start, s.h_seg_start.data(), sizeof(int) * ntile, cudaMemcpyHostToDevice, c->stream));
+    GBPIC_CHECK(c, cudaMemcpyAsync(s.count, h_count.data(), sizeof(int) * ntile, cudaMemcpyHostToDevice, c->stream));
+    GBPIC_CHECK(c, cudaMemcpyAsync(s.cap, s.h_cap.data(), sizeof(int) * ntile, cudaMemcpyHostToDevice, c->stream));
+    if (n > 0) {
+        LaunchScope ls(c, KC_OTHER);
+        k_scatter<T><<<grid, 256, 0, c->stream>>>(g, X, U, W, n, hist, pa, c->desc.track_ids);
+        GBPIC_CHECK(c, cudaGetLastError());
+    }
+    // mover and spill lists
+    s.mover_cap = (int)std::min<long long>(std::max<long long>(n / 4, 65536), 0x7fffff00LL);
+    s.spill_cap = (int)std::min<long long>(std::max<long long>(n / 16, 65536), 0x7fffff00LL);
+    s.movers = dev_alloc(c, sizeof(Rec<T>) * (size_t)s.mover_cap);
+    s.spill = dev_alloc(c, sizeof(Rec<T>) * (size_t)s.spill_cap);
+    if (!s.movers || !s.spill) return PIC_ERR_OOM;
+    GBPIC_CHECK(c, cudaStreamSynchronize(c->stream));
+    dev_free(c, hist);
+    if (stage) dev_free(c, stage);
+    s.q = d->q;
+    s.m = d->m;
+    s.n_loaded = n;
+    s.cap_total = (int64_t)total;
+    // fixed-point unit of J: a bound on one deposit term |q| w / (dt d_p d_r) (x 1.25
+    // for the straight-segment correction) maps to 2^JBITS units
+    const double* dd = c->desc.d;
+    const double dmin2 = std::min(dd[0] * dd[1], std::min(dd[1] * dd[2], dd[2] * dd[0]));
+    const double bound = std::fabs(d->q) * wmax / (c->desc.dt * dmin2) * 1.25;
+    s.jscale = bound > 0 ? bound / std::ldexp(1.0, Prec<T>::JBITS) : 0.0;
+    return PIC_OK;
+}
+
+pic_status load_species_impl(pic_ctx* c, const pic_species_desc* d, SpeciesDev& s) {
+    return c->prec == PIC_FP64 ? load_t<double>(c, d, s) : load_t<float>(c, d, s);
+}
+
+// ---------------------------------------------------------------------------
+// Read-out of particles as FP64 rows X, Y, Z, ux, uy, uz, w.
+
+template <typename T>
+__global__ void k_read_tiles(Geom g, ParticleArrays<T> pa, const long long* out_off, double* out, long long nout,
+                             int use_ids) {
+    const int ntile = g.nt[0] * g.nt[1] * g.nt[2];
+    for (int t = blockIdx.x; t < ntile; t += gridDim.x) {
+        const int cnt = min(pa.count[t], pa.cap[t]);
+        const int tx = t % g.nt[0], ty = (t / g.nt[0]) % g.nt[1], tz = t / (g.nt[0] * g.nt[1]);
+        for (int i = threadIdx.x; i < cnt; i += blockDim.x) {
+            const long long p = (long long)pa.seg_start[t] + i;
+            const int lc = pa.cell[p];
+            const long long o = use_ids ? (long long)pa.id[p] : out_off[t] + i;
+            if (o < 0 || o >= nout) continue;
+            out[o] = (double)(tx * TILE + (lc & 7)) + (double)pa.d[0][p];
+            out[nout + o] = (double)(ty * TILE + ((lc >> 3) & 7)) + (double)pa.d[1][p];
+            out[2 * nout + o] = (double)(tz * TILE + (lc >> 6)) + (double)pa.d[2][p];
+            out[3 * nout + o] = (double)pa.u[0][p];
+            out[4 * nout + o] = (double)pa.u[1][p];
+            out[5 * nout + o] = (double)pa.u[2][p];
+            out[6 * nout + o] = (double)pa.w[p];
+        }
+    }
+}
+
+template <typename T>
+__global__ void k_read_spill(Geom g, const Rec<T>* spill, int nsp, long long base, double* out, long long nout,
+                             int use_ids) {
+    for (int i = blockIdx.x * blockDim.x + threadIdx.x; i < nsp; i += gridDim.x * blockDim.x) {
+        const Rec<T> r = spill[i];
+        const long long o = use_ids ? (long long)r.id : base + i;
+        if (o < 0 || o >= nout) continue;
+        const int gx = r.cell % g.n[0], gy = (r.cell / g.n[0]) % g.n[1], gz = r.cell / (g.n[0] * g.n[1]);
+        out[o] = gx + (double)r.d[0];
+        out[nout + o] = gy + (double)r.d[1];
+        out[2 * nout + o] = gz + (double)r.d[2];
+        out[3 * nout + o] = (double)r.u[0];
+        out[4 * nout + o] = (double)r.u[1];
+        out[5 * nout + o] = (double)r.u[2];
+        out[6 * nout + o] = (double)r.w;
+    }
+}
+
+template <typename T>
+static pic_status read_t(pic_ctx* c, SpeciesDev& s, double* out, int64_t nout) {
+    const Geom& g = c->g;
+    const int ntile = g.nt[0] * g.nt[1] * g.nt[2];
+    std::vector<int> h_count(ntile);
+    Counters h_ctr;
+    GBPIC_CHECK(c, cudaMemcpyAsync(h_count.data(), s.count, sizeof(int) * ntile, cudaMemcpyDeviceToHost, c->stream));
+    GBPIC_CHECK(c, cudaMemcpyAsync(&h_ctr, s.ctr, sizeof(Counters), cudaMemcpyDeviceToHost, c->stream));
+    GBPIC_CHECK(c, cudaStreamSynchronize(c->stream));
+    std::vector<long long> off(ntile);
+    long long acc = 0;
+    for (int t = 0; t < ntile; ++t) {
+        off[t] = acc;
+        acc += std::min(h_count[t], s.h_cap[t]);
+    }
+    long long* d_off = static_cast<long long*>(dev_alloc(c, sizeof(long long) * ntile));
+    if (!d_off) return PIC_ERR_OOM;
+    GBPIC_CHECK(c, cudaMemcpyAsync(d_off, off.data(), sizeof(long long) * ntile, cudaMemcpyHostToDevice, c->stream));
+    const int use_ids = c->desc.track_ids ? 1 : 0;
+    {
+        LaunchScope ls(c, KC_OTHER);
+        k_read_tiles<T><<<1024, 256, 0, c->stream>>>(g, arrays<T>(s), d_off, out, nout, use_ids);
+        GBPIC_CHECK(c, cudaGetLastError());
+    }
+    const int nsp = std::min(h_ctr.spill_count[c->step & 1], s.spill_cap);
+    if (nsp > 0) {
+        LaunchScope ls(c, KC_OTHER);
+        k_read_spill<T><<<256, 256, 0, c->stream>>>(g, static_cast<const Rec<T>*>(s.spill), nsp, acc, out, nout, use_ids);
+        GBPIC_CHECK(c, cudaGetLastError());
+    }
+    GBPIC_CHECK(c, cudaStreamSynchronize(c->stream));
+    dev_free(c, d_off);
+    return PIC_OK;
+}
+
+pic_status get_particles_impl(pic_ctx* c, SpeciesDev& s, double* out_dev, int64_t n_out) {
+    return c->prec == PIC_FP64 ? read_t<double>(c, s, out_dev, n_out) : read_t<float>(c, s, out_dev, n_out);
+}
+
+int64_t count_alive(pic_ctx* c, SpeciesDev& s, int64_t* spilled) {
+    const int ntile = c->g.nt[0] * c->g.nt[1] * c->g.nt[2];
+    std::vector<int> h_count(ntile);
+    Counters h_ctr;
+    if (cudaMemcpyAsync(h_count.data(), s.count, sizeof(int) * ntile, cudaMemcpyDeviceToHost, c->stream) != cudaSuccess)
+        return -1;
+    if (cudaMemcpyAsync(&h_ctr, s.ctr, sizeof(Counters), cudaMemcpyDeviceToHost, c->stream) != cudaSuccess) return -1;
+    if (cudaStreamSynchronize(c->stream) != cudaSuccess) return -1;
+    int64_t n = 0;
+    for (int t = 0; t < ntile; ++t) n += std::min(h_count[t], s.h_cap[t]);
+    const int nsp = std::min(h_ctr.spill_count[c->step & 1], s.spill_cap);
+    if (spilled) *spilled = nsp;
+    return n + nsp;
+}
+
+// ---------------------------------------------------------------------------
+// Fields: FP64 compact host layout <-> padded working-precision device arrays.
+
+template <typename T>
+__global__ void k_unpack(Geom g, const double* src, T* a0, T* a1, T* a2) {
+    const long long N = g.N;
+    for (long long e = blockIdx.x * (long long)blockDim.x + threadIdx.x; e < N; e += (long long)gridDim.x * blockDim.x) {
+        const int i = (int)(e % g.n[0]), j = (int)((e / g.n[0]) % g.n[1]), k = (int)(e / ((long long)g.n[0] * g.n[1]));
+        const T v0 = src ? (T)src[e] : T(0), v1 = src ? (T)src[N + e] : T(0), v2 = src ? (T)src[2 * N + e] : T(0);
+        store3(g, a0, a1, a2, i, j, k, v0, v1, v2);
+    }
+}
+
+template <typename T, typename A>
+__global__ void k_pack(Geom g, const T* E0, const T* E1, const T* E2, const T* B0, const T* B1, const T* B2,
+                       const A* J0, const A* J1, const A* J2, double jscale, double* E,
+                       double* B, double* J) {
+    const long long N = g.N;
+    for (long long e = blockIdx.x * (long long)blockDim.x + threadIdx.x; e < N; e += (long long)gridDim.x * blockDim.x) {
+        const int i = (int)(e % g.n[0]), j = (int)((e / g.n[0]) % g.n[1]), k = (int)(e / ((long long)g.n[0] * g.n[1]));
+        const long long p = g.pidx(i, j, k);
+        if (E) {
+            E[e] = (double)E0[p];
+            E[N + e] = (double)E1[p];
+            E[2 * N + e] = (double)E2[p];
+        }
+        if (B) {
+            B[e] = (double)B0[p];
+            B[N + e] = (double)B1[p];
+            B[2 * N + e] = (double)B2[p];
+        }
+        if (J) {
+            J[e] = (double)J0[e] * jscale;
+            J[N + e] = (double)J1[e] * jscale;
+            J[2 * N + e] = (double)J2[e] * jscale;
+        }
+    }
+}
+
+template <typename T>
+static pic_status unpack_t(pic_ctx* c, const double* E, const double* B) {
+    LaunchScope ls(c, KC_OTHER);
+    k_unpack<T><<<1024, 256, 0, c->stream>>>(c->g, E, (T*)c->E[0], (T*)c->E[1], (T*)c->E[2]);
+    k_unpack<T><<<1024, 256, 0, c->stream>>>(c->g, B, (T*)c->B[0], (T*)c->B[1], (T*)c->B[2]);
+    c->launches++;
+    GBPIC_CHECK(c, cudaGetLastError());
+    return PIC_OK;
+}
+
+pic_status unpack_fields(pic_ctx* c, const double* E, const double* B) {
+    return c->prec == PIC_FP64 ? unpack_t<double>(c, E, B) : unpack_t<float>(c, E, B);
+}
+
+template <typename T>
+static pic_status pack_t(pic_ctx* c, double* E, double* B, double* J) {
+    LaunchScope ls(c, KC_OTHER);
+    using A = typename JTraits<T>::acc_t;
+    k_pack<T, A><<<1024, 256, 0, c->stream>>>(c->g, (T*)c->E[0], (T*)c->E[1], (T*)c->E[2], (T*)c->B[0], (T*)c->B[1],
+                                               (T*)c->B[2], (const A*)c->J[0], (const A*)c->J[1], (const A*)c->J[2],
+                                               c->jscale, E, B, J);
+    GBPIC_CHECK(c, cudaGetLastError());
+    return PIC_OK;
+}
+
+pic_status pack_fields(pic_ctx* c, double* E, double* B, double* J) {
+    return c->prec == PIC_FP64 ? pack_t<double>(c, E, B, J) : pack_t<float>(c, E, B, J);
+}
+
+}  // namespace gbpic

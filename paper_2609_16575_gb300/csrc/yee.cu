@@ -1,0 +1,160 @@
+// Yee FDTD curl updates (KEMPIC-3D section 2.3):
+//   k_faraday_half   B <- B - (dt/2) curl E          (Eq. (13) and cyclic permutations)
+//   k_ampere         E <- E + dt (curl B - J); J <- 0  (Eq. (14) and cyclic permutations)
+// One thread per cell, x fastest (coalesced rows).  Each kernel writes the value of
+// an edge cell also into its periodic ghost images (local -1 and n), so the next
+// stencil and the tile kernel's TMA staging read valid ghosts without a separate
+// halo pass.
+#include "pic_internal.cuh"
+
+namespace gbpic {
+
+template <typename T> struct YeeArgs {
+    Geom g;
+    Fields<T> f;
+    T cx, cy, cz;   // frac * dt / d
+    T dt;           // Ampere: dt
+    T jscale;       // physical J per fixed-point unit
+    int zero_j;
+    double* rec;    // optional: rec[0] += 1/2 dV sum E^2, rec[1] += 1/2 dV sum B_new^2
+    double half_dv;
+};
+
+__device__ __forceinline__ void block_add2(double a, double b, double* dst) {
+    for (int o = 16; o > 0; o >>= 1) {
+        a += __shfl_xor_sync(0xffffffffu, a, o);
+        b += __shfl_xor_sync(0xffffffffu, b, o);
+    }
+    __shared__ double ra[32], rb[32];
+    const int t = threadIdx.x + threadIdx.y * blockDim.x;
+    const int nw = (blockDim.x * blockDim.y + 31) / 32;
+    if ((t & 31) == 0) {
+        ra[t >> 5] = a;
+        rb[t >> 5] = b;
+    }
+    __syncthreads();
+    if (t == 0) {
+        double sa = 0, sb = 0;
+        for (int w = 0; w < nw; ++w) {
+            sa += ra[w];
+            sb += rb[w];
+        }
+        atomicAdd(dst, sa);
+        atomicAdd(dst + 1, sb);
+    }
+}
+
+template <typename T, bool REC>
+__global__ void __launch_bounds__(256) k_faraday_half(YeeArgs<T> A) {
+    const Geom& g = A.g;
+    const int i = blockIdx.x * blockDim.x + threadIdx.x;
+    const int j = blockIdx.y * blockDim.y + threadIdx.y;
+    const int k = blockIdx.z;
+    double se = 0, sb = 0;
+    if (i < g.n[0] && j < g.n[1]) {
+        const long long c = g.pidx(i, j, k);
+        const long long sy = g.Px, sz = (long long)g.Px * g.Gy;
+        const T* Ex = A.f.E[0];
+        const T* Ey = A.f.E[1];
+        const T* Ez = A.f.E[2];
+        const T ex = Ex[c], ey = Ey[c], ez = Ez[c];
+        // Bx(i, j+1/2, k+1/2) -= dt/dy [Ez(j+1) - Ez(j)] - dt/dz [Ey(k+1) - Ey(k)]
+        const T bx = A.f.B[0][c] - (A.cy * (Ez[c + sy] - ez) - A.cz * (Ey[c + sz] - ey));
+        // By(i+1/2, j, k+1/2) -= dt/dz [Ex(k+1) - Ex(k)] - dt/dx [Ez(i+1) - Ez(i)]
+        const T by = A.f.B[1][c] - (A.cz * (Ex[c + sz] - ex) - A.cx * (Ez[c + 1] - ez));
+        // Bz(i+1/2, j+1/2, k) -= dt/dx [Ey(i+1) - Ey(i)] - dt/dy [Ex(j+1) - Ex(j)]
+        const T bz = A.f.B[2][c] - (A.cx * (Ey[c + 1] - ey) - A.cy * (Ex[c + sy] - ex));
+        store3(g, A.f.B[0], A.f.B[1], A.f.B[2], i, j, k, bx, by, bz);
+        if (REC) {
+            se = (double)ex * ex + (double)ey * ey + (double)ez * ez;
+            sb = (double)bx * bx + (double)by * by + (double)bz * bz;
+        }
+    }
+    if (REC) block_add2(se * A.half_dv, sb * A.half_dv, A.rec);
+}
+
+// J in the working precision: fixed point times its unit (FP32), or FP64 as stored.
+__device__ __forceinline__ float j_value(long long v, float s) { return __ll2float_rn(v) * s; }
+__device__ __forceinline__ double j_value(double v, double) { return v; }
+
+template <typename T>
+__global__ void __launch_bounds__(256) k_ampere(YeeArgs<T> A) {
+    const Geom& g = A.g;
+    const int i = blockIdx.x * blockDim.x + threadIdx.x;
+    const int j = blockIdx.y * blockDim.y + threadIdx.y;
+    const int k = blockIdx.z;
+    if (i >= g.n[0] || j >= g.n[1]) return;
+    const long long c = g.pidx(i, j, k);
+    const long long cj = g.cidx(i, j, k);
+    const long long sy = g.Px, sz = (long long)g.Px * g.Gy;
+    const T* Bx = A.f.B[0];
+    const T* By = A.f.B[1];
+    const T* Bz = A.f.B[2];
+    const T bx = Bx[c], by = By[c], bz = Bz[c];
+    using Acc = typename JTraits<T>::acc_t;
+    const Acc jx = A.f.J[0][cj], jy = A.f.J[1][cj], jz = A.f.J[2][cj];
+    if (A.zero_j) {
+        A.f.J[0][cj] = Acc(0);
+        A.f.J[1][cj] = Acc(0);
+        A.f.J[2][cj] = Acc(0);
+    }
+    // Ex(i+1/2, j, k) += dt/dy [Bz(j+1/2) - Bz(j-1/2)] - dt/dz [By(k+1/2) - By(k-1/2)] - dt Jx
+    const T ex = A.f.E[0][c] + (A.cy * (bz - Bz[c - sy]) - A.cz * (by - By[c - sz])) - A.dt * j_value(jx, A.jscale);
+    // Ey(i, j+1/2, k) += dt/dz [Bx(k+1/2) - Bx(k-1/2)] - dt/dx [Bz(i+1/2) - Bz(i-1/2)] - dt Jy
+    const T ey = A.f.E[1][c] + (A.cz * (bx - Bx[c - sz]) - A.cx * (bz - Bz[c - 1])) - A.dt * j_value(jy, A.jscale);
+    // Ez(i, j, k+1/2) += dt/dx [By(i+1/2) - By(i-1/2)] - dt/dy [Bx(j+1/2) - Bx(j-1/2)] - dt Jz
+    const T ez = A.f.E[2][c] + (A.cx * (by - By[c - 1]) - A.cy * (bx - Bx[c - sy])) - A.dt * j_value(jz, A.jscale);
+    store3(g, A.f.E[0], A.f.E[1], A.f.E[2], i, j, k, ex, ey, ez);
+}
+
+template <typename T>
+static YeeArgs<T> yee_args(pic_ctx* c, double frac) {
+    YeeArgs<T> A{};
+    A.g = c->g;
+    for (int k = 0; k < 3; ++k) {
+        A.f.E[k] = static_cast<T*>(c->E[k]);
+        A.f.B[k] = static_cast<T*>(c->B[k]);
+        A.f.J[k] = static_cast<typename JTraits<T>::acc_t*>(c->J[k]);
+    }
+    const double dt = c->desc.dt;
+    A.cx = (T)(frac * dt / c->desc.d[0]);
+    A.cy = (T)(frac * dt / c->desc.d[1]);
+    A.cz = (T)(frac * dt / c->desc.d[2]);
+    A.dt = (T)dt;
+    A.jscale = (T)c->jscale;
+    A.half_dv = 0.5 * c->desc.d[0] * c->desc.d[1] * c->desc.d[2];
+    return A;
+}
+
+static dim3 yee_grid(const Geom& g) { return dim3((g.n[0] + 31) / 32, (g.n[1] + 7) / 8, g.n[2]); }
+
+template <typename T>
+static pic_status faraday_t(pic_ctx* c, double* rec) {
+    YeeArgs<T> A = yee_args<T>(c, 0.5);
+    A.rec = rec;
+    LaunchScope ls(c, KC_FARADAY);
+    if (rec) k_faraday_half<T, true><<<yee_grid(c->g), dim3(32, 8), 0, c->stream>>>(A);
+    else k_faraday_half<T, false><<<yee_grid(c->g), dim3(32, 8), 0, c->stream>>>(A);
+    GBPIC_CHECK(c, cudaGetLastError());
+    return PIC_OK;
+}
+
+template <typename T>
+static pic_status ampere_t(pic_ctx* c, bool zero_j) {
+    YeeArgs<T> A = yee_args<T>(c, 1.0);
+    A.zero_j = zero_j ? 1 : 0;
+    LaunchScope ls(c, KC_AMPERE);
+    k_ampere<T><<<yee_grid(c->g), dim3(32, 8), 0, c->stream>>>(A);
+    GBPIC_CHECK(c, cudaGetLastError());
+    return PIC_OK;
+}
+
+pic_status launch_faraday_half(pic_ctx* c, double* rec) {
+    return c->prec == PIC_FP64 ? faraday_t<double>(c, rec) : faraday_t<float>(c, rec);
+}
+
+pic_status launch_ampere(pic_ctx* c, bool zero_j) {
+    return c->prec == PIC_FP64 ? ampere_t<double>(c, zero_j) : ampere_t<float>(c, zero_j);
+}
+
+}  // namespace gbpic
