@@ -158,6 +158,29 @@ pic_status pic_set_timing(pic_ctx* ctx, int32_t enable);
 pic_status pic_kernel_times(pic_ctx* ctx, int32_t max, const char** names, int64_t* launches, double* ms,
                             int32_t* count);
 
+/* Differentiation: a hand-written discrete adjoint of the cycle of section 2.2.
+ * The loss is the field energy of the final state, L = U_E + U_B at time level N
+ * (E^N and B^N of Eq. (21)), as in pic_diagnostics.
+ *
+ * pic_adjoint_forward advances nsteps cycles from the current state s^0, keeping a
+ * device-memory snapshot of the full state every ckpt_every steps, and returns L.
+ * Needs track_ids = 1 (gradients are reported per loaded particle).
+ *
+ * pic_adjoint_backward returns, for that L,
+ *   dL_du[s]: for each species s (an array of species pointers, entries may be
+ *             NULL), 3*n_s FP64 values: dL/du^{-1/2} in load order, rows ux, uy, uz;
+ *   dL_dA:    <lambda_E^0, E_dir> + <lambda_B^{-1/2}, B_dir>, i.e. dL/dA when the
+ *             initial fields are E^0 = A E_dir and B^{-1/2} = A B_dir (E_dir, B_dir:
+ *             3*N FP64 values in the host field layout, either may be NULL).
+ * It restores each checkpoint, recomputes the segment's states and runs the adjoint
+ * kernels (Yee^T, deposit^T, position^T, Boris^T, gather^T) in reverse; adjoint
+ * arithmetic and parameter-gradient sums are FP64.  Afterwards the context holds the
+ * final state s^N again.  device_pointers = 1: E_dir, B_dir and dL_du are device
+ * pointers.  Synchronises. */
+pic_status pic_adjoint_forward(pic_ctx* ctx, int32_t nsteps, int32_t ckpt_every, double* loss);
+pic_status pic_adjoint_backward(pic_ctx* ctx, const double* E_dir, const double* B_dir, double* dL_dA,
+                                double* const* dL_du, int32_t device_pointers);
+
 /* Total kernel launches the library has issued on this context. */
 int64_t pic_launch_count(const pic_ctx* ctx);
 

@@ -1,0 +1,653 @@
+// Hand-written discrete adjoint of the PIC cycle (KEMPIC-3D section 2.2, Fig. 2) for
+// gradients of the final field energy L = U_E + U_B (time level N, B^N of Eq. (21))
+// with respect to the initial momenta u^{-1/2} and an initial-field amplitude.
+//
+// State s^n = (E^n, B^{n-1/2}, X^n, u^{n-1/2}).  One forward cycle is
+//   B_n = B^{n-1/2} - h C_E E^n        (h = dt/2; C_E the curl from E to B locations)
+//   particles: gather E^n, B_n at X^n; Boris; X^{n+1} = X^n + (dt/d) u/gamma; zigzag J
+//   B^{n+1/2} = B_n - h C_E E^n
+//   E^{n+1} = E^n + dt (C_B B^{n+1/2} - J)
+// On the Yee grid C_B = C_E^T, so the transposed field updates reuse the two curl
+// stencils.  With lambdas of s^{n+1} the adjoint step is
+//   lB  <- lB + dt C_E lE'            (lambda of B^{n+1/2} = lambda of B_n, field part)
+//   lE  <- lE' - h C_B lB             (field part of lambda of E^n)
+//   particles, lambda_J = -dt lE': deposit^T (derivatives of the zigzag fluxes and
+//     weights), position update^T, Boris^T, gather^T (scatter into lE, lB and the
+//     derivative of the interpolation weights)
+//   lE  <- lE - h C_B lB              (from B_n = B^{n-1/2} - h C_E E^n)
+// The driver keeps a full-state snapshot every K steps, recomputes each segment
+// forward, and runs the adjoint steps in reverse; all adjoint arithmetic and the
+// parameter-gradient reductions are FP64.
+#include <algorithm>
+#include <cmath>
+#include <vector>
+
+#include "pic_internal.cuh"
+
+namespace gbpic {
+
+struct SpeciesSnap {
+    void* part = nullptr;
+    void* counts = nullptr;
+    void* ctr = nullptr;
+    void* spill = nullptr;
+    int cur = 0;
+};
+
+struct Snapshot {
+    void* fields[6] = {};
+    std::vector<SpeciesSnap> sp;
+    int64_t step = 0;
+    bool alloc = false;
+};
+
+struct AdjointState {
+    int N = 0, K = 1;
+    double loss = 0;
+    std::vector<Snapshot> ckpt;
+    std::vector<Snapshot> seg;
+    Snapshot final_;
+    bool ready = false;
+};
+
+static size_t field_bytes(pic_ctx* c) { return (size_t)c->g.padded_size() * c->esize; }
+static int ntiles(pic_ctx* c) { return c->g.nt[0] * c->g.nt[1] * c->g.nt[2]; }
+static size_t rec_bytes(pic_ctx* c) { return c->prec == PIC_FP64 ? sizeof(Rec<double>) : sizeof(Rec<float>); }
+
+static pic_status snap_alloc(pic_ctx* c, Snapshot& S) {
+    if (S.alloc) return PIC_OK;
+    for (int k = 0; k < 6; ++k)
+        if (!(S.fields[k] = dev_alloc(c, field_bytes(c)))) return PIC_ERR_OOM;
+    S.sp.resize(c->species.size());
+    for (size_t i = 0; i < c->species.size(); ++i) {
+        SpeciesDev& s = c->species[i];
+        SpeciesSnap& z = S.sp[i];
+        if (!(z.part = dev_alloc(c, s.pbytes)) || !(z.counts = dev_alloc(c, sizeof(int) * ntiles(c))) ||
+            !(z.ctr = dev_alloc(c, sizeof(Counters))) || !(z.spill = dev_alloc(c, rec_bytes(c) * s.spill_cap)))
+            return PIC_ERR_OOM;
+    }
+    S.alloc = true;
+    return PIC_OK;
+}
+
+static pic_status snap_save(pic_ctx* c, Snapshot& S) {
+    pic_status st = snap_alloc(c, S);
+    if (st != PIC_OK) return st;
+    const size_t fb = field_bytes(c);
+    for (int k = 0; k < 3; ++k) {
+        GBPIC_CHECK(c, cudaMemcpyAsync(S.fields[k], c->E[k], fb, cudaMemcpyDeviceToDevice, c->stream));
+        GBPIC_CHECK(c, cudaMemcpyAsync(S.fields[3 + k], c->B[k], fb, cudaMemcpyDeviceToDevice, c->stream));
+    }
+    for (size_t i = 0; i < c->species.size(); ++i) {
+        SpeciesDev& s = c->species[i];
+        SpeciesSnap& z = S.sp[i];
+        z.cur = s.cur;
+        GBPIC_CHECK(c, cudaMemcpyAsync(z.part, s.base[s.cur], s.pbytes, cudaMemcpyDeviceToDevice, c->stream));
+        GBPIC_CHECK(c, cudaMemcpyAsync(z.counts, s.count, sizeof(int) * ntiles(c), cudaMemcpyDeviceToDevice, c->stream));
+        GBPIC_CHECK(c, cudaMemcpyAsync(z.ctr, s.ctr, sizeof(Counters), cudaMemcpyDeviceToDevice, c->stream));
+        GBPIC_CHECK(c, cudaMemcpyAsync(z.spill, s.spill, rec_bytes(c) * s.spill_cap, cudaMemcpyDeviceToDevice, c->stream));
+    }
+    S.step = c->step;
+    return PIC_OK;
+}
+
+static pic_status snap_restore(pic_ctx* c, const Snapshot& S) {
+    const size_t fb = field_bytes(c);
+    for (int k = 0; k < 3; ++k) {
+        GBPIC_CHECK(c, cudaMemcpyAsync(c->E[k], S.fields[k], fb, cudaMemcpyDeviceToDevice, c->stream));
+        GBPIC_CHECK(c, cudaMemcpyAsync(c->B[k], S.fields[3 + k], fb, cudaMemcpyDeviceToDevice, c->stream));
+        GBPIC_CHECK(c, cudaMemsetAsync(c->J[k], 0, sizeof(long long) * (size_t)c->g.N, c->stream));
+    }
+    for (size_t i = 0; i < c->species.size(); ++i) {
+        SpeciesDev& s = c->species[i];
+        const SpeciesSnap& z = S.sp[i];
+        s.cur = z.cur;
+        GBPIC_CHECK(c, cudaMemcpyAsync(s.base[s.cur], z.part, s.pbytes, cudaMemcpyDeviceToDevice, c->stream));
+        GBPIC_CHECK(c, cudaMemcpyAsync(s.count, z.counts, sizeof(int) * ntiles(c), cudaMemcpyDeviceToDevice, c->stream));
+        GBPIC_CHECK(c, cudaMemcpyAsync(s.ctr, z.ctr, sizeof(Counters), cudaMemcpyDeviceToDevice, c->stream));
+        GBPIC_CHECK(c, cudaMemcpyAsync(s.spill, z.spill, rec_bytes(c) * s.spill_cap, cudaMemcpyDeviceToDevice, c->stream));
+    }
+    c->step = S.step;
+    c->j_dirty = false;
+    return PIC_OK;
+}
+
+// ---------------------------------------------------------------------------
+// Adjoint kernels (FP64 arithmetic whatever the forward precision).
+
+template <typename T> struct AdjArgs {
+    Geom g;
+    ParticleArrays<T> pa;
+    const Rec<T>* spill;
+    int nsp;
+    const T* E[3];      // E^n
+    const T* Bn[3];     // B_n = B^{n-1/2} - dt/2 curl E^n
+    const double* lEn[3];   // lambda of E^{n+1} (padded): lambda_J = -dt lEn
+    double* accE[3];    // gather^T accumulators (compact)
+    double* accB[3];
+    double* lX;         // 3 x nload lambda of positions (cell units), load order
+    double* lU;         // 3 x nload lambda of momenta
+    long long nload;
+    double eps, dt, dtd[3], C[3];   // C = q / (dt d_p d_r)
+};
+
+// Value and gradient (w.r.t. the three fractional coordinates) of a trilinear
+// interpolation of F from base (b0, b1, b2) with fractions s.
+template <typename T>
+__device__ __forceinline__ double interp_grad(const Geom& g, const T* F, const int b[3], const double s[3], double grad[3]) {
+    double f[2][2][2];
+    for (int cc = 0; cc < 2; ++cc)
+        for (int bb = 0; bb < 2; ++bb)
+            for (int aa = 0; aa < 2; ++aa) f[cc][bb][aa] = (double)F[g.pidx(b[0] + aa, b[1] + bb, b[2] + cc)];
+    const double w0[2] = {1.0 - s[0], s[0]}, w1[2] = {1.0 - s[1], s[1]}, w2[2] = {1.0 - s[2], s[2]};
+    double v = 0, g0 = 0, g1 = 0, g2 = 0;
+    for (int cc = 0; cc < 2; ++cc)
+        for (int bb = 0; bb < 2; ++bb)
+            for (int aa = 0; aa < 2; ++aa) {
+                const double x = f[cc][bb][aa];
+                v += w0[aa] * w1[bb] * w2[cc] * x;
+                g0 += (aa ? 1.0 : -1.0) * w1[bb] * w2[cc] * x;
+                g1 += w0[aa] * (bb ? 1.0 : -1.0) * w2[cc] * x;
+                g2 += w0[aa] * w1[bb] * (cc ? 1.0 : -1.0) * x;
+            }
+    grad[0] = g0;
+    grad[1] = g1;
+    grad[2] = g2;
+    return v;
+}
+
+__device__ __forceinline__ void scatter_trilinear(const Geom& g, double* acc, const int b[3], const double s[3], double lam) {
+    if (lam == 0.0) return;
+    const double w0[2] = {1.0 - s[0], s[0]}, w1[2] = {1.0 - s[1], s[1]}, w2[2] = {1.0 - s[2], s[2]};
+    for (int cc = 0; cc < 2; ++cc)
+        for (int bb = 0; bb < 2; ++bb)
+            for (int aa = 0; aa < 2; ++aa)
+                atomicAdd(acc + g.cidx(wrap_idx(b[0] + aa, g.n[0]), wrap_idx(b[1] + bb, g.n[1]), wrap_idx(b[2] + cc, g.n[2])),
+                          lam * w0[aa] * w1[bb] * w2[cc]);
+}
+
+// Derivatives of S = sum_q L_q v_q(F, W) for one straight segment (the 12 edge
+// values of segment_values) with respect to its fluxes F and midpoint offsets W.
+__device__ __forceinline__ void segment_vjp(const double Cw[3], const double F[3], const double W[3], const double L[12],
+                                            double gF[3], double gW[3]) {
+    const double wx1 = W[0], wy1 = W[1], wz1 = W[2], wx0 = 1 - wx1, wy0 = 1 - wy1, wz0 = 1 - wz1;
+    const double Ax = L[0] * wy0 * wz0 + L[1] * wy1 * wz0 + L[2] * wy0 * wz1 + L[3] * wy1 * wz1;
+    const double Ay = L[4] * wx0 * wz0 + L[5] * wx1 * wz0 + L[6] * wx0 * wz1 + L[7] * wx1 * wz1;
+    const double Az = L[8] * wx0 * wy0 + L[9] * wx1 * wy0 + L[10] * wx0 * wy1 + L[11] * wx1 * wy1;
+    const double Gx = L[0] - L[1] - L[2] + L[3];
+    const double Gy = L[4] - L[5] - L[6] + L[7];
+    const double Gz = L[8] - L[9] - L[10] + L[11];
+    const double Fx = F[0], Fy = F[1], Fz = F[2];
+    const double Cx = Cw[0], Cy = Cw[1], Cz = Cw[2];
+    const double t = 1.0 / 12.0;
+    gF[0] = Cx * (Ax + Fy * Fz * Gx * t) + Cy * Fy * Fz * Gy * t + Cz * Fz * Fy * Gz * t;
+    gF[1] = Cy * (Ay + Fx * Fz * Gy * t) + Cx * Fx * Fz * Gx * t + Cz * Fz * Fx * Gz * t;
+    gF[2] = Cz * (Az + Fx * Fy * Gz * t) + Cx * Fx * Fy * Gx * t + Cy * Fy * Fx * Gy * t;
+    gW[0] = Cy * Fy * ((L[5] - L[4]) * wz0 + (L[7] - L[6]) * wz1) + Cz * Fz * ((L[9] - L[8]) * wy0 + (L[11] - L[10]) * wy1);
+    gW[1] = Cx * Fx * ((L[1] - L[0]) * wz0 + (L[3] - L[2]) * wz1) + Cz * Fz * ((L[10] - L[8]) * wx0 + (L[11] - L[9]) * wx1);
+    gW[2] = Cx * Fx * ((L[2] - L[0]) * wy0 + (L[3] - L[1]) * wy1) + Cy * Fy * ((L[6] - L[4]) * wx0 + (L[7] - L[5]) * wx1);
+}
+
+__device__ __forceinline__ void cross3(const double a[3], const double b[3], double o[3]) {
+    o[0] = a[1] * b[2] - a[2] * b[1];
+    o[1] = a[2] * b[0] - a[0] * b[2];
+    o[2] = a[0] * b[1] - a[1] * b[0];
+}
+
+template <typename T>
+__device__ void adjoint_particle(const AdjArgs<T>& A, int gx, int gy, int gz, const double d1[3], const double u0[3],
+                                 double w, int id) {
+    const Geom& g = A.g;
+    const int gc[3] = {gx, gy, gz};
+    // ---- forward recompute: staggered gather with weights and their gradients
+    int hb[3], nb[3];
+    double hs[3], ns[3];
+    for (int k = 0; k < 3; ++k) {
+        if (d1[k] >= 0.5) {
+            hb[k] = gc[k];
+            hs[k] = d1[k] - 0.5;
+        } else {
+            hb[k] = gc[k] - 1;
+            hs[k] = d1[k] + 0.5;
+        }
+        nb[k] = gc[k];
+        ns[k] = d1[k];
+    }
+    const int HF[6][3] = {{1, 0, 0}, {0, 1, 0}, {0, 0, 1}, {0, 1, 1}, {1, 0, 1}, {1, 1, 0}};
+    double val[6], grad[6][3];
+    int cb[6][3];
+    double cs[6][3];
+    for (int comp = 0; comp < 6; ++comp) {
+        for (int k = 0; k < 3; ++k) {
+            cb[comp][k] = HF[comp][k] ? hb[k] : nb[k];
+            cs[comp][k] = HF[comp][k] ? hs[k] : ns[k];
+        }
+        const T* F = comp < 3 ? A.E[comp] : A.Bn[comp - 3];
+        val[comp] = interp_grad(g, F, cb[comp], cs[comp], grad[comp]);
+    }
+    const double Ep[3] = {val[0], val[1], val[2]}, Bp[3] = {val[3], val[4], val[5]};
+    // Boris with its intermediates (section 2.4)
+    const double eps = A.eps;
+    double um[3], t[3], s[3], up[3], upl[3], un[3], tmp[3];
+    for (int k = 0; k < 3; ++k) um[k] = u0[k] + eps * Ep[k];
+    const double gm = sqrt(1.0 + um[0] * um[0] + um[1] * um[1] + um[2] * um[2]);
+    for (int k = 0; k < 3; ++k) t[k] = eps * Bp[k] / gm;
+    const double t2 = t[0] * t[0] + t[1] * t[1] + t[2] * t[2];
+    const double f = 2.0 / (1.0 + t2);
+    for (int k = 0; k < 3; ++k) s[k] = f * t[k];
+    cross3(um, t, tmp);
+    for (int k = 0; k < 3; ++k) up[k] = um[k] + tmp[k];
+    cross3(up, s, tmp);
+    for (int k = 0; k < 3; ++k) upl[k] = um[k] + tmp[k];
+    for (int k = 0; k < 3; ++k) un[k] = upl[k] + eps * Ep[k];
+    const double gn = sqrt(1.0 + un[0] * un[0] + un[1] * un[1] + un[2] * un[2]);
+    const double ig = 1.0 / gn;
+    // move and zigzag relay (cell-relative, as the forward kernels)
+    double d2[3], F1[3], F2[3], W1[3], W2[3];
+    int st[3];
+    for (int k = 0; k < 3; ++k) {
+        st[k] = advance(d1[k], A.dtd[k] * un[k] * ig, d2[k]);
+        st[k] = st[k] > 1 ? 1 : (st[k] < -1 ? -1 : st[k]);
+        relay(d1[k], d2[k], st[k], F1[k], F2[k], W1[k], W2[k]);
+    }
+    // ---- deposit^T: lambda_J = -dt lambda_E^{n+1} at the edges of both segment cells
+    double L1[12], L2[12];
+    for (int q = 0; q < 12; ++q) {
+        int comp, ex, ey, ez;
+        slot_edge(q, gx, gy, gz, comp, ex, ey, ez);
+        L1[q] = -A.dt * A.lEn[comp][g.pidx(wrap_idx(ex, g.n[0]), wrap_idx(ey, g.n[1]), wrap_idx(ez, g.n[2]))];
+        slot_edge(q, gx + st[0], gy + st[1], gz + st[2], comp, ex, ey, ez);
+        L2[q] = -A.dt * A.lEn[comp][g.pidx(wrap_idx(ex, g.n[0]), wrap_idx(ey, g.n[1]), wrap_idx(ez, g.n[2]))];
+    }
+    const double Cw[3] = {A.C[0] * w, A.C[1] * w, A.C[2] * w};
+    double gF1[3], gW1[3], gF2[3], gW2[3];
+    segment_vjp(Cw, F1, W1, L1, gF1, gW1);
+    segment_vjp(Cw, F2, W2, L2, gF2, gW2);
+    double lx1[3], lx2[3];
+    for (int k = 0; k < 3; ++k) {
+        if (st[k] == 0) {   // F1 = F2 = (x2 - x1)/2, W1 = (3 x1 + x2)/4, W2 = (x1 + 3 x2)/4
+            lx1[k] = -0.5 * (gF1[k] + gF2[k]) + 0.75 * gW1[k] + 0.25 * gW2[k];
+            lx2[k] = 0.5 * (gF1[k] + gF2[k]) + 0.25 * gW1[k] + 0.75 * gW2[k];
+        } else {            // F1 = +-(1 - x1) ..., W1 = (x1 [+1])/2; F2 = x2 [-1], W2 = (x2 [+1])/2
+            lx1[k] = -gF1[k] + 0.5 * gW1[k];
+            lx2[k] = gF2[k] + 0.5 * gW2[k];
+        }
+    }
+    // ---- the adjoint of the next state, and the position update X^{n+1} = X^n + dtd u / gamma
+    double lun[3], a[3];
+    for (int k = 0; k < 3; ++k) {
+        lx2[k] += A.lX[k * A.nload + id];
+        lx1[k] += lx2[k];
+        a[k] = lx2[k] * A.dtd[k];
+    }
+    const double adot = a[0] * un[0] + a[1] * un[1] + a[2] * un[2];
+    for (int k = 0; k < 3; ++k) lun[k] = A.lU[k * A.nload + id] + (a[k] - un[k] * adot * ig * ig) * ig;
+    // ---- Boris^T
+    double lum[3], lup[3], ls[3], lt[3], lE[3], lB[3];
+    for (int k = 0; k < 3; ++k) lum[k] = lun[k];           // upl = um + up x s, lambda_upl = lun
+    cross3(s, lun, lup);                                     // lambda_up = s x lambda_upl
+    cross3(lun, up, ls);                                     // lambda_s = lambda_upl x up
+    cross3(t, lup, tmp);                                     // up = um + um x t
+    for (int k = 0; k < 3; ++k) lum[k] += lup[k] + tmp[k];
+    cross3(lup, um, lt);
+    const double lst = ls[0] * t[0] + ls[1] * t[1] + ls[2] * t[2];   // s = f t, f = 2 / (1 + t.t)
+    for (int k = 0; k < 3; ++k) lt[k] += f * ls[k] - f * f * lst * t[k];
+    for (int k = 0; k < 3; ++k) lB[k] = eps / gm * lt[k];    // t = eps B / gm
+    const double lgm = -(lt[0] * t[0] + lt[1] * t[1] + lt[2] * t[2]) / gm;
+    for (int k = 0; k < 3; ++k) lum[k] += lgm * um[k] / gm;   // gm = sqrt(1 + um.um)
+    for (int k = 0; k < 3; ++k) lE[k] = eps * (lun[k] + lum[k]);   // um = u + eps E and the final kick
+    // ---- gather^T
+    for (int k = 0; k < 3; ++k) {
+        double acc = 0;
+        for (int c = 0; c < 3; ++c) acc += lE[c] * grad[c][k] + lB[c] * grad[3 + c][k];
+        lx1[k] += acc;
+    }
+    for (int c = 0; c < 3; ++c) {
+        scatter_trilinear(g, A.accE[c], cb[c], cs[c], lE[c]);
+        scatter_trilinear(g, A.accB[c], cb[3 + c], cs[3 + c], lB[c]);
+    }
+    for (int k = 0; k < 3; ++k) {
+        A.lX[k * A.nload + id] = lx1[k];
+        A.lU[k * A.nload + id] = lum[k];
+    }
+}
+
+template <typename T>
+__global__ void __launch_bounds__(256) k_adj_particles(AdjArgs<T> A) {
+    const Geom& g = A.g;
+    const int nt = g.nt[0] * g.nt[1] * g.nt[2];
+    for (int t = blockIdx.x; t < nt; t += gridDim.x) {
+        const int cnt = min(A.pa.count[t], A.pa.cap[t]);
+        const int tx = t % g.nt[0], ty = (t / g.nt[0]) % g.nt[1], tz = t / (g.nt[0] * g.nt[1]);
+        for (int i = threadIdx.x; i < cnt; i += blockDim.x) {
+            const long long p = (long long)A.pa.seg_start[t] + i;
+            const int lc = A.pa.cell[p];
+            const double d1[3] = {(double)A.pa.d[0][p], (double)A.pa.d[1][p], (double)A.pa.d[2][p]};
+            const double u0[3] = {(double)A.pa.u[0][p], (double)A.pa.u[1][p], (double)A.pa.u[2][p]};
+            adjoint_particle(A, tx * TILE + (lc & 7), ty * TILE + ((lc >> 3) & 7), tz * TILE + (lc >> 6), d1, u0,
+                             (double)A.pa.w[p], A.pa.id[p]);
+        }
+    }
+    for (int i = blockIdx.x * blockDim.x + threadIdx.x; i < A.nsp; i += gridDim.x * blockDim.x) {
+        const Rec<T> r = A.spill[i];
+        const double d1[3] = {(double)r.d[0], (double)r.d[1], (double)r.d[2]};
+        const double u0[3] = {(double)r.u[0], (double)r.u[1], (double)r.u[2]};
+        adjoint_particle(A, r.cell % g.n[0], (r.cell / g.n[0]) % g.n[1], r.cell / (g.n[0] * g.n[1]), d1, u0,
+                         (double)r.w, r.id);
+    }
+}
+
+// dst (FP64, padded) = scale * src (working precision, padded), ghosts included.
+template <typename T>
+__global__ void k_scale_copy(long long n, const T* src, double* dst, double scale) {
+    for (long long e = blockIdx.x * (long long)blockDim.x + threadIdx.x; e < n; e += (long long)gridDim.x * blockDim.x)
+        dst[e] = scale * (double)src[e];
+}
+
+// l (padded, FP64) += acc (compact), for the three components, with ghost images.
+__global__ void k_merge(Geom g, double* l0, double* l1, double* l2, const double* a0, const double* a1, const double* a2) {
+    for (long long e = blockIdx.x * (long long)blockDim.x + threadIdx.x; e < g.N; e += (long long)gridDim.x * blockDim.x) {
+        const int i = (int)(e % g.n[0]), j = (int)((e / g.n[0]) % g.n[1]), k = (int)(e / ((long long)g.n[0] * g.n[1]));
+        const long long p = g.pidx(i, j, k);
+        store3(g, l0, l1, l2, i, j, k, l0[p] + a0[e], l1[p] + a1[e], l2[p] + a2[e]);
+    }
+}
+
+// sum over cells of lE . Ed + lB . Bd (Ed, Bd compact, FP64)
+__global__ void k_dot(Geom g, const double* lE0, const double* lE1, const double* lE2, const double* lB0,
+                      const double* lB1, const double* lB2, const double* Ed, const double* Bd, double* out) {
+    double acc = 0;
+    const long long N = g.N;
+    for (long long e = blockIdx.x * (long long)blockDim.x + threadIdx.x; e < N; e += (long long)gridDim.x * blockDim.x) {
+        const int i = (int)(e % g.n[0]), j = (int)((e / g.n[0]) % g.n[1]), k = (int)(e / ((long long)g.n[0] * g.n[1]));
+        const long long p = g.pidx(i, j, k);
+        if (Ed) acc += lE0[p] * Ed[e] + lE1[p] * Ed[N + e] + lE2[p] * Ed[2 * N + e];
+        if (Bd) acc += lB0[p] * Bd[e] + lB1[p] * Bd[N + e] + lB2[p] * Bd[2 * N + e];
+    }
+    for (int o = 16; o > 0; o >>= 1) acc += __shfl_xor_sync(0xffffffffu, acc, o);
+    if ((threadIdx.x & 31) == 0 && acc != 0.0) atomicAdd(out, acc);
+}
+
+// ---------------------------------------------------------------------------
+// Driver.
+
+struct AdjBuffers {
+    double* lE[3] = {};
+    double* lB[3] = {};
+    double* lEn[3] = {};
+    double* accE[3] = {};
+    double* accB[3] = {};
+    void* Bn[3] = {};
+    std::vector<double*> lX, lU;
+};
+
+template <typename T>
+static pic_status adjoint_step_t(pic_ctx* c, AdjBuffers& b) {
+    const double dt = c->desc.dt, h = 0.5 * dt;
+    const size_t pb = sizeof(double) * (size_t)c->g.padded_size();
+    for (int k = 0; k < 3; ++k) GBPIC_CHECK(c, cudaMemcpyAsync(b.lEn[k], b.lE[k], pb, cudaMemcpyDeviceToDevice, c->stream));
+    // lB += dt C_E lE  (the Faraday stencil computes B - coef curl E)
+    pic_status st = curl_to_b<double>(c, b.lE, b.lB, -dt);
+    if (st != PIC_OK) return st;
+    // lE -= h C_B lB
+    st = curl_to_e<double>(c, b.lE, b.lB, -h);
+    if (st != PIC_OK) return st;
+    // B_n of this state
+    const size_t fb = (size_t)c->g.padded_size() * sizeof(T);
+    T* Bn[3];
+    T* E[3];
+    for (int k = 0; k < 3; ++k) {
+        Bn[k] = static_cast<T*>(b.Bn[k]);
+        E[k] = static_cast<T*>(c->E[k]);
+        GBPIC_CHECK(c, cudaMemcpyAsync(Bn[k], c->B[k], fb, cudaMemcpyDeviceToDevice, c->stream));
+    }
+    st = curl_to_b<T>(c, E, Bn, h);
+    if (st != PIC_OK) return st;
+    for (int k = 0; k < 3; ++k) {
+        GBPIC_CHECK(c, cudaMemsetAsync(b.accE[k], 0, sizeof(double) * (size_t)c->g.N, c->stream));
+        GBPIC_CHECK(c, cudaMemsetAsync(b.accB[k], 0, sizeof(double) * (size_t)c->g.N, c->stream));
+    }
+    for (size_t si = 0; si < c->species.size(); ++si) {
+        SpeciesDev& s = c->species[si];
+        Counters h_ctr;
+        GBPIC_CHECK(c, cudaMemcpyAsync(&h_ctr, s.ctr, sizeof(Counters), cudaMemcpyDeviceToHost, c->stream));
+        GBPIC_CHECK(c, cudaStreamSynchronize(c->stream));
+        AdjArgs<T> A{};
+        A.g = c->g;
+        A.pa = arrays<T>(s);
+        A.spill = static_cast<const Rec<T>*>(s.spill);
+        A.nsp = std::min(h_ctr.spill_count[c->step & 1], s.spill_cap);
+        for (int k = 0; k < 3; ++k) {
+            A.E[k] = E[k];
+            A.Bn[k] = Bn[k];
+            A.lEn[k] = b.lEn[k];
+            A.accE[k] = b.accE[k];
+            A.accB[k] = b.accB[k];
+        }
+        A.lX = b.lX[si];
+        A.lU = b.lU[si];
+        A.nload = s.n_loaded;
+        A.eps = s.q * dt / (2.0 * s.m);
+        A.dt = dt;
+        const double* d = c->desc.d;
+        for (int k = 0; k < 3; ++k) A.dtd[k] = dt / d[k];
+        A.C[0] = s.q / (dt * d[1] * d[2]);
+        A.C[1] = s.q / (dt * d[2] * d[0]);
+        A.C[2] = s.q / (dt * d[0] * d[1]);
+        LaunchScope ls(c, KC_OTHER);
+        k_adj_particles<T><<<4 * 152, 256, 0, c->stream>>>(A);
+        GBPIC_CHECK(c, cudaGetLastError());
+    }
+    {
+        LaunchScope ls(c, KC_OTHER);
+        k_merge<<<1024, 256, 0, c->stream>>>(c->g, b.lE[0], b.lE[1], b.lE[2], b.accE[0], b.accE[1], b.accE[2]);
+        k_merge<<<1024, 256, 0, c->stream>>>(c->g, b.lB[0], b.lB[1], b.lB[2], b.accB[0], b.accB[1], b.accB[2]);
+        GBPIC_CHECK(c, cudaGetLastError());
+    }
+    // lE -= h C_B lB  (B_n = B^{n-1/2} - h C_E E^n)
+    return curl_to_e<double>(c, b.lE, b.lB, -h);
+}
+
+static void snap_free(pic_ctx* c, Snapshot& S) {
+    if (!S.alloc) return;
+    for (int k = 0; k < 6; ++k) dev_free(c, S.fields[k]);
+    for (auto& z : S.sp) {
+        dev_free(c, z.part);
+        dev_free(c, z.counts);
+        dev_free(c, z.ctr);
+        dev_free(c, z.spill);
+    }
+    S.alloc = false;
+}
+
+static void adjoint_release(pic_ctx* c) {
+    AdjointState* S = static_cast<AdjointState*>(c->adj);
+    if (!S) return;
+    if (c->stream) cudaStreamSynchronize(c->stream);
+    for (auto& z : S->ckpt) snap_free(c, z);
+    for (auto& z : S->seg) snap_free(c, z);
+    snap_free(c, S->final_);
+    delete S;
+    c->adj = nullptr;
+}
+
+template <typename T>
+static pic_status backward_t(pic_ctx* c, AdjointState& S, const double* Ed, const double* Bd, double* dL_dA,
+                             double* const* dL_du, int devptr) {
+    AdjBuffers b;
+    const size_t pb = sizeof(double) * (size_t)c->g.padded_size();
+    const size_t cb = sizeof(double) * (size_t)c->g.N;
+    const size_t fb = (size_t)c->g.padded_size() * sizeof(T);
+    std::vector<void*> temp;
+    auto alloc = [&](size_t n) {
+        void* p = dev_alloc(c, n);
+        if (p) temp.push_back(p);
+        return p;
+    };
+    for (int k = 0; k < 3; ++k) {
+        b.lE[k] = static_cast<double*>(alloc(pb));
+        b.lB[k] = static_cast<double*>(alloc(pb));
+        b.lEn[k] = static_cast<double*>(alloc(pb));
+        b.accE[k] = static_cast<double*>(alloc(cb));
+        b.accB[k] = static_cast<double*>(alloc(cb));
+        b.Bn[k] = alloc(fb);
+        if (!b.lE[k] || !b.lB[k] || !b.lEn[k] || !b.accE[k] || !b.accB[k] || !b.Bn[k]) return PIC_ERR_OOM;
+    }
+    for (auto& s : c->species) {
+        double* x = static_cast<double*>(alloc(sizeof(double) * 3 * std::max<int64_t>(s.n_loaded, 1)));
+        double* u = static_cast<double*>(alloc(sizeof(double) * 3 * std::max<int64_t>(s.n_loaded, 1)));
+        if (!x || !u) return PIC_ERR_OOM;
+        GBPIC_CHECK(c, cudaMemsetAsync(x, 0, sizeof(double) * 3 * s.n_loaded, c->stream));
+        GBPIC_CHECK(c, cudaMemsetAsync(u, 0, sizeof(double) * 3 * s.n_loaded, c->stream));
+        b.lX.push_back(x);
+        b.lU.push_back(u);
+    }
+    // the final state and the adjoint of L = 1/2 dV sum (E^N^2 + B_N^2)
+    pic_status st = snap_restore(c, S.final_);
+    if (st != PIC_OK) return st;
+    const double dV = c->desc.d[0] * c->desc.d[1] * c->desc.d[2], h = 0.5 * c->desc.dt;
+    T* E[3];
+    T* Bn[3];
+    for (int k = 0; k < 3; ++k) {
+        E[k] = static_cast<T*>(c->E[k]);
+        Bn[k] = static_cast<T*>(b.Bn[k]);
+        GBPIC_CHECK(c, cudaMemcpyAsync(Bn[k], c->B[k], fb, cudaMemcpyDeviceToDevice, c->stream));
+    }
+    st = curl_to_b<T>(c, E, Bn, h);
+    if (st != PIC_OK) return st;
+    {
+        LaunchScope ls(c, KC_OTHER);
+        for (int k = 0; k < 3; ++k) {
+            k_scale_copy<T><<<1024, 256, 0, c->stream>>>(c->g.padded_size(), Bn[k], b.lB[k], dV);
+            k_scale_copy<T><<<1024, 256, 0, c->stream>>>(c->g.padded_size(), E[k], b.lE[k], dV);
+        }
+        GBPIC_CHECK(c, cudaGetLastError());
+    }
+    st = curl_to_e<double>(c, b.lE, b.lB, -h);
+    if (st != PIC_OK) return st;
+    // segments in reverse: restore, recompute the states, adjoint steps backwards
+    const int nseg = (int)S.ckpt.size();
+    for (int sg = nseg - 1; sg >= 0; --sg) {
+        const int a = sg * S.K, e = std::min(S.N, a + S.K);
+        st = snap_restore(c, S.ckpt[sg]);
+        if (st != PIC_OK) return st;
+        for (int n = a; n < e; ++n) {
+            st = snap_save(c, S.seg[n - a]);
+            if (st != PIC_OK) return st;
+            if (n < e - 1) {
+                st = step_once(c, nullptr, false);
+                if (st != PIC_OK) return st;
+            }
+        }
+        for (int n = e - 1; n >= a; --n) {
+            st = snap_restore(c, S.seg[n - a]);
+            if (st != PIC_OK) return st;
+            st = adjoint_step_t<T>(c, b);
+            if (st != PIC_OK) return st;
+        }
+    }
+    // parameter gradients (FP64)
+    if (dL_dA) {
+        double* stage = static_cast<double*>(alloc(sizeof(double) * (6 * (size_t)c->g.N + 1)));
+        if (!stage) return PIC_ERR_OOM;
+        const double* dEd = Ed;
+        const double* dBd = Bd;
+        if (!devptr) {
+            if (Ed) GBPIC_CHECK(c, cudaMemcpyAsync(stage, Ed, 3 * cb, cudaMemcpyHostToDevice, c->stream));
+            if (Bd) GBPIC_CHECK(c, cudaMemcpyAsync(stage + 3 * c->g.N, Bd, 3 * cb, cudaMemcpyHostToDevice, c->stream));
+            dEd = Ed ? stage : nullptr;
+            dBd = Bd ? stage + 3 * c->g.N : nullptr;
+        }
+        double* out = stage + 6 * c->g.N;
+        GBPIC_CHECK(c, cudaMemsetAsync(out, 0, sizeof(double), c->stream));
+        {
+            LaunchScope ls(c, KC_OTHER);
+            k_dot<<<1024, 256, 0, c->stream>>>(c->g, b.lE[0], b.lE[1], b.lE[2], b.lB[0], b.lB[1], b.lB[2], dEd, dBd, out);
+            GBPIC_CHECK(c, cudaGetLastError());
+        }
+        GBPIC_CHECK(c, cudaMemcpyAsync(dL_dA, out, sizeof(double), cudaMemcpyDeviceToHost, c->stream));
+    }
+    if (dL_du) {
+        for (size_t si = 0; si < c->species.size(); ++si) {
+            if (!dL_du[si]) continue;
+            GBPIC_CHECK(c, cudaMemcpyAsync(dL_du[si], b.lU[si], sizeof(double) * 3 * c->species[si].n_loaded,
+                                           devptr ? cudaMemcpyDeviceToDevice : cudaMemcpyDeviceToHost, c->stream));
+        }
+    }
+    GBPIC_CHECK(c, cudaStreamSynchronize(c->stream));
+    for (void* p : temp) dev_free(c, p);
+    // leave the context at the final state
+    st = snap_restore(c, S.final_);
+    if (st != PIC_OK) return st;
+    GBPIC_CHECK(c, cudaStreamSynchronize(c->stream));
+    return PIC_OK;
+}
+
+}  // namespace gbpic
+
+using namespace gbpic;
+
+extern "C" {
+
+pic_status pic_adjoint_forward(pic_ctx* c, int32_t nsteps, int32_t ckpt_every, double* loss) {
+    if (!c || nsteps < 1 || ckpt_every < 1 || !loss) return PIC_ERR_ARG;
+    if (!c->desc.track_ids || c->species.empty()) {
+        c->err = "pic_adjoint_forward needs track_ids and at least one species";
+        return PIC_ERR_STATE;
+    }
+    cudaSetDevice(c->desc.device);
+    adjoint_release(c);
+    AdjointState* S = new AdjointState();
+    c->adj = S;
+    S->N = nsteps;
+    S->K = ckpt_every;
+    S->ckpt.resize((nsteps + ckpt_every - 1) / ckpt_every);
+    S->seg.resize(std::min(nsteps, ckpt_every));
+    update_jscale(c);
+    if (c->j_dirty) {
+        for (int k = 0; k < 3; ++k)
+            GBPIC_CHECK(c, cudaMemsetAsync(c->J[k], 0, sizeof(long long) * (size_t)c->g.N, c->stream));
+        c->j_dirty = false;
+    }
+    for (int n = 0; n < nsteps; ++n) {
+        pic_status st;
+        if (n % ckpt_every == 0) {
+            st = snap_save(c, S->ckpt[n / ckpt_every]);
+            if (st != PIC_OK) return st;
+        }
+        st = step_once(c, nullptr, false);
+        if (st != PIC_OK) return st;
+    }
+    pic_status st = snap_save(c, S->final_);
+    if (st != PIC_OK) return st;
+    double UE = 0, UB = 0;
+    st = energy_sums(c, &UE, &UB);
+    if (st != PIC_OK) return st;
+    st = pic_sync(c);
+    if (st != PIC_OK) return st;
+    S->loss = UE + UB;
+    S->ready = true;
+    *loss = S->loss;
+    return PIC_OK;
+}
+
+pic_status pic_adjoint_backward(pic_ctx* c, const double* E_dir, const double* B_dir, double* dL_dA,
+                                double* const* dL_du, int32_t device_pointers) {
+    if (!c) return PIC_ERR_ARG;
+    AdjointState* S = static_cast<AdjointState*>(c->adj);
+    if (!S || !S->ready) {
+        c->err = "pic_adjoint_backward needs a preceding pic_adjoint_forward";
+        return PIC_ERR_STATE;
+    }
+    cudaSetDevice(c->desc.device);
+    pic_status st = c->prec == PIC_FP64 ? backward_t<double>(c, *S, E_dir, B_dir, dL_dA, dL_du, device_pointers)
+                                        : backward_t<float>(c, *S, E_dir, B_dir, dL_dA, dL_du, device_pointers);
+    if (st != PIC_OK) return st;
+    return pic_sync(c);
+}
+
+}  // extern "C"
+
+namespace gbpic {
+void adjoint_free(pic_ctx* c) { adjoint_release(c); }
+}  // namespace gbpic

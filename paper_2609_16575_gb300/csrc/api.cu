@@ -120,6 +120,40 @@ static pic_status device_errors(pic_ctx* c) {
     return PIC_OK;
 }
 
+// The fixed-point unit of J (FP32 path): the coarsest unit any species needs; the
+// FP64 path accumulates J itself.
+void update_jscale(pic_ctx* c) {
+    double js = 0;
+    for (auto& s : c->species) js = std::max(js, s.jscale);
+    if (js <= 0 || c->prec == PIC_FP64) js = 1.0;
+    c->jscale = js;
+    c->jinv = 1.0 / js;
+}
+
+// One cycle of section 2.2, Fig. 2: Faraday half step, per species the tile push, the
+// spill-list push, the mover append (and the periodic tile sort), Faraday half step,
+// Ampere.  J is cleared by Ampere unless keep_j.  Expects J = 0 on entry.
+pic_status step_once(pic_ctx* c, double* rec, bool keep_j) {
+    pic_status st = launch_faraday_half(c, rec);
+    if (st != PIC_OK) return st;
+    const int sort_every = c->desc.sort_every == 0 ? 4 : c->desc.sort_every;
+    const bool sort_now = sort_every > 0 && (c->step + 1) % sort_every == 0;
+    for (auto& sp : c->species) {
+        st = launch_push_species(c, sp, (int)(c->step & 1), rec ? rec + 2 : nullptr);
+        if (st != PIC_OK) return st;
+        if (sort_now) {
+            st = launch_sort(c, sp);
+            if (st != PIC_OK) return st;
+        }
+    }
+    st = launch_faraday_half(c, nullptr);
+    if (st != PIC_OK) return st;
+    st = launch_ampere(c, !keep_j);
+    if (st != PIC_OK) return st;
+    c->step++;
+    return PIC_OK;
+}
+
 }  // namespace gbpic
 
 using namespace gbpic;
@@ -281,13 +315,7 @@ pic_status pic_step(pic_ctx* c, int32_t nsteps) {
     if (!c || nsteps < 0) return PIC_ERR_ARG;
     if (nsteps == 0) return PIC_OK;
     cudaSetDevice(c->desc.device);
-    // the fixed-point unit of J (FP32 path): the coarsest unit any species needs;
-    // the FP64 path accumulates J itself
-    double js = 0;
-    for (auto& s : c->species) js = std::max(js, s.jscale);
-    if (js <= 0 || c->prec == PIC_FP64) js = 1.0;
-    c->jscale = js;
-    c->jinv = 1.0 / js;
+    update_jscale(c);
     if (c->j_dirty) {
         for (int k = 0; k < 3; ++k)
             GBPIC_CHECK(c, cudaMemsetAsync(c->J[k], 0, sizeof(long long) * (size_t)c->g.N, c->stream));
@@ -300,23 +328,8 @@ pic_status pic_step(pic_ctx* c, int32_t nsteps) {
             GBPIC_CHECK(c, cudaMemsetAsync(rec, 0, sizeof(double) * 3, c->stream));
             c->hist_written++;
         }
-        pic_status st = launch_faraday_half(c, rec);
+        pic_status st = step_once(c, rec, s == nsteps - 1);
         if (st != PIC_OK) return st;
-        const int sort_every = c->desc.sort_every == 0 ? 4 : c->desc.sort_every;
-        const bool sort_now = sort_every > 0 && (c->step + 1) % sort_every == 0;
-        for (auto& sp : c->species) {
-            st = launch_push_species(c, sp, (int)(c->step & 1), rec ? rec + 2 : nullptr);
-            if (st != PIC_OK) return st;
-            if (sort_now) {
-                st = launch_sort(c, sp);
-                if (st != PIC_OK) return st;
-            }
-        }
-        st = launch_faraday_half(c, nullptr);
-        if (st != PIC_OK) return st;
-        st = launch_ampere(c, s < nsteps - 1);
-        if (st != PIC_OK) return st;
-        c->step++;
     }
     c->j_dirty = true;
     return PIC_OK;
@@ -445,6 +458,7 @@ void pic_destroy(pic_ctx* c) {
     if (!c) return;
     cudaSetDevice(c->desc.device);
     if (c->stream) cudaStreamSynchronize(c->stream);
+    adjoint_free(c);
     for (auto& p : c->pending) {
         cudaEventDestroy(p.a);
         cudaEventDestroy(p.b);

@@ -186,6 +186,40 @@ static pic_status diag_t(pic_ctx* c, pic_diag* out) {
     return PIC_OK;
 }
 
+// U_E = 1/2 dV sum E^n^2 and U_B = 1/2 dV sum B^n^2 of the current state (FP64).
+template <typename T>
+static pic_status energy_t(pic_ctx* c, double* UE, double* UB) {
+    if (!c->dacc) {
+        c->dacc = static_cast<double*>(dev_alloc(c, sizeof(double) * (DACC_N + 3)));
+        if (!c->dacc) return PIC_ERR_OOM;
+    }
+    GBPIC_CHECK(c, cudaMemsetAsync(c->dacc, 0, sizeof(double) * DACC_N, c->stream));
+    Fields<T> f;
+    for (int k = 0; k < 3; ++k) {
+        f.E[k] = static_cast<T*>(c->E[k]);
+        f.B[k] = static_cast<T*>(c->B[k]);
+        f.J[k] = nullptr;
+    }
+    const double dt = c->desc.dt;
+    const double* d = c->desc.d;
+    {
+        LaunchScope ls(c, KC_OTHER);
+        k_energy<T><<<1024, 256, 0, c->stream>>>(c->g, f, 0.5 * dt / d[0], 0.5 * dt / d[1], 0.5 * dt / d[2],
+                                                  0.5 * d[0] * d[1] * d[2], c->dacc);
+        GBPIC_CHECK(c, cudaGetLastError());
+    }
+    double h[2];
+    GBPIC_CHECK(c, cudaMemcpyAsync(h, c->dacc, sizeof(h), cudaMemcpyDeviceToHost, c->stream));
+    GBPIC_CHECK(c, cudaStreamSynchronize(c->stream));
+    *UE = h[S_UE];
+    *UB = h[S_UB];
+    return PIC_OK;
+}
+
+pic_status energy_sums(pic_ctx* c, double* UE, double* UB) {
+    return c->prec == PIC_FP64 ? energy_t<double>(c, UE, UB) : energy_t<float>(c, UE, UB);
+}
+
 pic_status diagnostics_impl(pic_ctx* c, pic_diag* out) {
     return c->prec == PIC_FP64 ? diag_t<double>(c, out) : diag_t<float>(c, out);
 }

@@ -19,8 +19,9 @@ constexpr int TILE_CELLS = 512;
 constexpr int SB = 10;           // staged E/B extent per dim: local cells -1..8
 constexpr int SJ = 11;           // shared J extent per dim: local nodes/edges -1..9
 constexpr int SJ3 = SJ * SJ * SJ;
-constexpr int PUSH_THREADS = 256;
+constexpr int PUSH_THREADS = 512;
 constexpr int PUSH_WARPS = PUSH_THREADS / 32;
+constexpr int GROUP_ROUNDS = 3;   // warp reduce-scatter rounds per chunk before the sparse path
 
 // device error bits, OR-ed into Counters::err
 enum : int { ERRB_OVERFLOW = 1, ERRB_SUPERLUMINAL = 2, ERRB_NAN = 4, ERRB_TIMEOUT = 8 };
@@ -30,10 +31,14 @@ constexpr int MBAR_MAX_POLLS = 1 << 24;
 
 template <typename T> struct Prec;
 template <> struct Prec<float> {
+    static constexpr int THREADS = 512;   // tile kernel CTA (2 CTAs per SM at 64 registers)
+    static constexpr int MINB = 2;
     static constexpr int BX = 12;      // TMA box inner extent: 12 floats = 48 B (multiple of 16 B)
     static constexpr int JBITS = 40;   // fixed-point fraction bits of a bounded J contribution
 };
 template <> struct Prec<double> {
+    static constexpr int THREADS = 256;   // FP64 needs ~130 registers per thread
+    static constexpr int MINB = 1;
     static constexpr int BX = 10;      // 10 doubles = 80 B
     static constexpr int JBITS = 50;
 };
@@ -176,6 +181,32 @@ __device__ __forceinline__ void acc_atomic(long long* p, long long v) {
 }
 __device__ __forceinline__ void acc_atomic(double* p, double v) { atomicAdd(p, v); }
 
+// Shared-memory J tile accumulators.  FP32 path: each 64-bit fixed-point element is a
+// pair of 32-bit words (lo, hi) updated with native 32-bit shared atomics and an
+// explicit carry (exact modulo 2^64, so the final pair is the exact sum).  FP64 path:
+// FP64 shared atomics.  Element e of the lo words sits at byte 4e, of the hi words at
+// byte 4(NE + e), of the FP64 tile at byte 8e.
+__device__ __forceinline__ void jtile_add(uint32_t base, int e, long long v, int NE) {
+    const unsigned l = static_cast<unsigned>(v);
+    unsigned hh = static_cast<unsigned>(static_cast<unsigned long long>(v) >> 32);
+    unsigned old;
+    asm volatile("atom.shared.add.u32 %0, [%1], %2;" : "=r"(old) : "r"(base + 4u * e), "r"(l) : "memory");
+    hh += (old + l < old) ? 1u : 0u;
+    if (hh) asm volatile("red.shared.add.u32 [%0], %1;" ::"r"(base + 4u * (NE + e)), "r"(hh) : "memory");
+}
+__device__ __forceinline__ void jtile_add(uint32_t base, int e, double v, int) {
+    double old;
+    asm volatile("atom.shared.add.f64 %0, [%1], %2;" : "=d"(old) : "r"(base + 8u * e), "d"(v) : "memory");
+    (void)old;
+}
+__device__ __forceinline__ long long jtile_get(const unsigned char* s, int e, int NE, long long) {
+    const unsigned* w = reinterpret_cast<const unsigned*>(s);
+    return static_cast<long long>((static_cast<unsigned long long>(w[NE + e]) << 32) | w[e]);
+}
+__device__ __forceinline__ double jtile_get(const unsigned char* s, int e, int, double) {
+    return reinterpret_cast<const double*>(s)[e];
+}
+
 // Warp reduce-scatter of 16 slots: on return lane l holds the warp sum of slot
 // l >> 1 (lanes l and l^1 hold the same slot).  16 shuffles instead of 5 x 16.
 template <typename A>
@@ -209,6 +240,11 @@ __device__ __forceinline__ A reduce_scatter16(A v[16], int lane) {
     }
     return v[0] + __shfl_xor_sync(0xffffffffu, v[0], 1);
 }
+
+// 2 / x: the FP32 path uses the fast approximate division (error ~2 ulp, far inside
+// the FP32 tolerance); the FP64 path divides exactly.
+__device__ __forceinline__ float two_over(float x) { return __fdividef(2.0f, x); }
+__device__ __forceinline__ double two_over(double x) { return 2.0 / x; }
 
 // Staggered CIC weights along one dimension (section 2.5).  A node-located
 // component samples cells (i, i+1) with weight s = delta; a half-located one
@@ -261,7 +297,7 @@ __device__ __forceinline__ T boris(T eps, const T E[3], const T B[3], T u[3]) {
     T um0 = u[0] + eps * E[0], um1 = u[1] + eps * E[1], um2 = u[2] + eps * E[2];
     T ig = rsqrt_t(T(1) + um0 * um0 + um1 * um1 + um2 * um2);
     T t0 = eps * B[0] * ig, t1 = eps * B[1] * ig, t2 = eps * B[2] * ig;
-    T f = T(2) / (T(1) + t0 * t0 + t1 * t1 + t2 * t2);
+    T f = two_over(T(1) + t0 * t0 + t1 * t1 + t2 * t2);
     T s0 = f * t0, s1 = f * t1, s2 = f * t2;
     T up0 = um0 + (um1 * t2 - um2 * t1);
     T up1 = um1 + (um2 * t0 - um0 * t2);
@@ -364,6 +400,14 @@ __device__ __forceinline__ void scatter12(AddFn Add, int x, int y, int z, const 
     }
 }
 
+// Local cell coordinates in -1..8 packed as (x+1) | (y+1) << 4 | (z+1) << 8.
+__device__ __forceinline__ int pack_cell(int x, int y, int z) { return (x + 1) | ((y + 1) << 4) | ((z + 1) << 8); }
+__device__ __forceinline__ void unpack_cell(int k, int& x, int& y, int& z) {
+    x = (k & 15) - 1;
+    y = ((k >> 4) & 15) - 1;
+    z = ((k >> 8) & 15) - 1;
+}
+
 // Edge (component, local x, y, z) of slot s (0..11) of the cell (x, y, z), in the
 // order of segment_values.
 __device__ __forceinline__ void slot_edge(int s, int x, int y, int z, int& comp, int& ex, int& ey, int& ez) {
@@ -445,6 +489,7 @@ struct SpeciesDev {
     ParticleArrays<float> pf[2] = {};     // valid when FP32
     ParticleArrays<double> pd[2] = {};    // valid when FP64
     int cur = 0;                          // which block holds the particles
+    size_t pbytes = 0;                    // bytes of one SoA block
     int* seg_start = nullptr;
     int* count = nullptr;
     int* cap = nullptr;
@@ -507,6 +552,7 @@ struct pic_ctx {
     int64_t kc_n[gbpic::KC_COUNT] = {};
     std::vector<void*> allocations;
     std::string err;
+    void* adj = nullptr;      // checkpointed adjoint state (adjoint.cu)
 };
 
 namespace gbpic {
@@ -517,6 +563,12 @@ pic_status launch_ampere(pic_ctx* c, bool zero_j);
 pic_status launch_push_species(pic_ctx* c, SpeciesDev& s, int parity, double* krec);
 pic_status launch_backpush(pic_ctx* c, SpeciesDev& s);
 pic_status launch_sort(pic_ctx* c, SpeciesDev& s);
+template <typename T> pic_status curl_to_b(pic_ctx* c, T* const E[3], T* const B[3], double coef);
+template <typename T> pic_status curl_to_e(pic_ctx* c, T* const E[3], T* const B[3], double coef);
+pic_status step_once(pic_ctx* c, double* rec, bool keep_j);
+void update_jscale(pic_ctx* c);
+void adjoint_free(pic_ctx* c);
+pic_status energy_sums(pic_ctx* c, double* UE, double* UB);
 pic_status load_species_impl(pic_ctx* c, const pic_species_desc* d, SpeciesDev& s);
 pic_status get_particles_impl(pic_ctx* c, SpeciesDev& s, double* out_dev, int64_t n_out);
 pic_status pack_fields(pic_ctx* c, double* E, double* B, double* J);   // device outputs

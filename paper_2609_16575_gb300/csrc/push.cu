@@ -35,12 +35,13 @@ template <typename T> __host__ __device__ constexpr int box_stride() {
     // each staged box starts on a 128-byte boundary
     return ((box_elems<T>() * (int)sizeof(T) + 127) / 128) * 128 / (int)sizeof(T);
 }
+constexpr int JT_ELEMS = 3 * SJ3;   // elements of the shared J tile
 template <typename T> constexpr size_t tile_smem_bytes() {
-    // + 128: the kernel rounds the dynamic shared base up to a 128-byte boundary (TMA destination)
-    return (size_t)6 * box_stride<T>() * sizeof(T) + (size_t)3 * SJ3 * sizeof(long long) + 16 + 128;
+    // staged E, B boxes + J tile (8 bytes per element either way) + mbarrier; + 128: the
+    // kernel rounds the dynamic shared base up to a 128-byte boundary (TMA destination)
+    return (size_t)6 * box_stride<T>() * sizeof(T) + (size_t)JT_ELEMS * 8 + 16 + 128;
 }
 
-template <typename T>
 __device__ __forceinline__ void block_add_double(double v, double* dst) {
     for (int o = 16; o > 0; o >>= 1) v += __shfl_xor_sync(0xffffffffu, v, o);
     __shared__ double red[PUSH_WARPS];
@@ -49,7 +50,7 @@ __device__ __forceinline__ void block_add_double(double v, double* dst) {
     __syncthreads();
     if (threadIdx.x == 0) {
         double s = 0;
-        for (int w = 0; w < PUSH_WARPS; ++w) s += red[w];
+        for (int w = 0; w < (int)(blockDim.x >> 5); ++w) s += red[w];
         atomicAdd(dst, s);
     }
 }
@@ -66,19 +67,53 @@ __device__ __forceinline__ int warp_reserve(int* counter, bool want) {
     return want ? base + __popc(m & ((1u << lane) - 1)) : -1;
 }
 
+// Deposit of the 12 edge values R of the cells with packed keys K for the lanes in
+// mask M, two records per pass: lanes 0..11 take the 12 values of the first record,
+// lanes 12..23 those of the second.  Used for the few records the group reduction
+// leaves (cell crossers' second segment, singleton cells), so that no lane executes
+// 12 atomics on its own while the rest of its warp idles.
+template <typename T, typename AddFn>
+__device__ __forceinline__ void sparse_deposit(unsigned M, const T R[12], int K, int lane, AddFn add) {
+    const int rec = lane < 12 ? 0 : (lane < 24 ? 1 : 2);
+    const int q = lane - 12 * rec;
+    while (M) {
+        const int r0 = __ffs(M) - 1;
+        M &= M - 1;
+        const int r1 = M ? __ffs(M) - 1 : -1;
+        if (r1 >= 0) M &= M - 1;
+        const int src = rec == 0 ? r0 : (rec == 1 ? r1 : -1);
+        const int sl = src < 0 ? 0 : src;
+        T val = T(0);
+#pragma unroll
+        for (int k = 0; k < 12; ++k) {
+            const T t = __shfl_sync(0xffffffffu, R[k], sl);
+            val = (k == q) ? t : val;
+        }
+        const int key = __shfl_sync(0xffffffffu, K, sl);
+        if (src >= 0) {
+            int cx, cy, cz, comp, ex, ey, ez;
+            unpack_cell(key, cx, cy, cz);
+            slot_edge(q, cx, cy, cz, comp, ex, ey, ez);
+            add(comp, ex, ey, ez, to_acc(val));
+        }
+    }
+}
+
 template <typename T, bool IDS, bool RECK>
-__global__ void __launch_bounds__(PUSH_THREADS)
+__global__ void __launch_bounds__(Prec<T>::THREADS, Prec<T>::MINB)
 k_tile_push(const __grid_constant__ CUtensorMap tE0, const __grid_constant__ CUtensorMap tE1,
             const __grid_constant__ CUtensorMap tE2, const __grid_constant__ CUtensorMap tB0,
             const __grid_constant__ CUtensorMap tB1, const __grid_constant__ CUtensorMap tB2, PushArgs<T> A) {
     extern __shared__ __align__(128) unsigned char smem_raw[];
     unsigned char* smem = reinterpret_cast<unsigned char*>((reinterpret_cast<uintptr_t>(smem_raw) + 127) & ~uintptr_t(127));
+    using Acc = typename JTraits<T>::acc_t;
+    constexpr int NT = Prec<T>::THREADS, NW = NT / 32;
     constexpr int BX = Prec<T>::BX;
     constexpr int BS = box_stride<T>();
     T* sF = reinterpret_cast<T*>(smem);
-    using Acc = typename JTraits<T>::acc_t;
-    Acc* sJ = reinterpret_cast<Acc*>(smem + (size_t)6 * BS * sizeof(T));
-    uint64_t* bar = reinterpret_cast<uint64_t*>(smem + (size_t)6 * BS * sizeof(T) + (size_t)3 * SJ3 * 8);
+    unsigned char* sJ = smem + (size_t)6 * BS * sizeof(T);
+    const uint32_t sJa = smem_u32(sJ);
+    uint64_t* bar = reinterpret_cast<uint64_t*>(sJ + (size_t)JT_ELEMS * 8);
     __shared__ int s_wtot[2][PUSH_WARPS];
     __shared__ int s_timeout;
 
@@ -105,7 +140,28 @@ k_tile_push(const __grid_constant__ CUtensorMap tE0, const __grid_constant__ CUt
         tma_load_3d(sF + 4 * BS, &tB1, ox, oy, oz, bar);
         tma_load_3d(sF + 5 * BS, &tB2, ox, oy, oz, bar);
     }
-    for (int i = threadIdx.x; i < 3 * SJ3; i += PUSH_THREADS) sJ[i] = Acc(0);
+    {
+        unsigned long long* z = reinterpret_cast<unsigned long long*>(sJ);
+        for (int i = threadIdx.x; i < JT_ELEMS; i += NT) z[i] = 0ull;
+    }
+    // first chunk of particles, loaded while the TMA copies fly
+    const int seg = A.pa.seg_start[tile];
+    int n_lc = 0, n_id = 0;
+    T n_d[3] = {T(0), T(0), T(0)}, n_u[3] = {T(0), T(0), T(0)}, n_w = T(0);
+    auto load = [&](int i) {
+        if (i < cnt) {
+            const long long p = (long long)seg + i;
+            n_lc = __ldcs(A.pa.cell + p);
+#pragma unroll
+            for (int k = 0; k < 3; ++k) {
+                n_d[k] = __ldcs(A.pa.d[k] + p);
+                n_u[k] = __ldcs(A.pa.u[k] + p);
+            }
+            n_w = __ldcs(A.pa.w + p);
+            if (IDS) n_id = __ldcs(A.pa.id + p);
+        }
+    };
+    load(threadIdx.x);
     {
         int polls = 0;
         while (!mbar_try_wait(bar, 0)) {
@@ -132,35 +188,30 @@ k_tile_push(const __grid_constant__ CUtensorMap tE0, const __grid_constant__ CUt
         return sF[comp * BS + ((z + 1) * SB + (y + 1)) * BX + (x + 1)];
     };
     auto add = [&](int comp, int x, int y, int z, Acc v) {
-        if (v != Acc(0)) acc_atomic(&sJ[comp * SJ3 + ((z + 1) * SJ + (y + 1)) * SJ + (x + 1)], v);
+        if (v != Acc(0)) jtile_add(sJa, comp * SJ3 + ((z + 1) * SJ + (y + 1)) * SJ + (x + 1), v, JT_ELEMS);
     };
 
-    const int seg = A.pa.seg_start[tile];
     const int ext[3] = {min(TILE, A.g.n[0] - ox), min(TILE, A.g.n[1] - oy), min(TILE, A.g.n[2] - oz)};
     const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
     int written = 0;
     double kacc = 0.0;
 
-    for (int base = 0, it = 0; base < cnt; base += PUSH_THREADS, ++it) {
+    for (int base = 0, it = 0; base < cnt; base += NT, ++it) {
         const int i = base + threadIdx.x;
         const bool active = i < cnt;
-        bool stay = false, move = false;
-        int lc = 0, pid = 0;
-        bool crossed = false;
-        T d2[3], u[3], w = T(0), v[12], v2[12];
-#pragma unroll
-        for (int q = 0; q < 12; ++q) v[q] = T(0);
+        int lc = n_lc, pid = n_id;
+        T d1[3] = {n_d[0], n_d[1], n_d[2]}, u[3] = {n_u[0], n_u[1], n_u[2]}, w = n_w;
+        load(i + NT);   // next chunk: positions the compaction below cannot reach
+        bool stay = false, move = false, crossed = false;
+        T d2[3] = {T(0), T(0), T(0)}, v[12], v2[12];
         int s[3] = {0, 0, 0};
         int x = 0, y = 0, z = 0;
+#pragma unroll
+        for (int q = 0; q < 12; ++q) {
+            v[q] = T(0);
+            v2[q] = T(0);
+        }
         if (active) {
-            const long long p = (long long)seg + i;
-            lc = __ldcs(A.pa.cell + p);
-            T d1[3] = {__ldcs(A.pa.d[0] + p), __ldcs(A.pa.d[1] + p), __ldcs(A.pa.d[2] + p)};
-            u[0] = __ldcs(A.pa.u[0] + p);
-            u[1] = __ldcs(A.pa.u[1] + p);
-            u[2] = __ldcs(A.pa.u[2] + p);
-            w = __ldcs(A.pa.w + p);
-            if (IDS) pid = __ldcs(A.pa.id + p);
             x = lc & 7;
             y = (lc >> 3) & 7;
             z = lc >> 6;
@@ -180,34 +231,47 @@ k_tile_push(const __grid_constant__ CUtensorMap tE0, const __grid_constant__ CUt
                 }
             }
             const T cw[3] = {A.cq[0] * w, A.cq[1] * w, A.cq[2] * w};
-            T F1[3], F2[3], W1[3], W2[3];
-#pragma unroll
-            for (int k = 0; k < 3; ++k) relay(d1[k], d2[k], s[k], F1[k], F2[k], W1[k], W2[k]);
-            segment_values(cw, F1, W1, v);
-            segment_values(cw, F2, W2, v2);
             crossed = (s[0] | s[1] | s[2]) != 0;
             if (!crossed) {
+                // both zigzag segments lie in the start cell: their two midpoint products
+                // and D_p D_r / 48 terms add up to one straight segment x1 -> x2 with
+                // midpoint weights and the D_p D_r / 12 term
+                T D[3], Wm[3];
 #pragma unroll
-                for (int q = 0; q < 12; ++q) v[q] += v2[q];
+                for (int k = 0; k < 3; ++k) {
+                    D[k] = d2[k] - d1[k];
+                    Wm[k] = d1[k] + T(0.5) * D[k];
+                }
+                segment_values(cw, D, Wm, v);
+            } else {
+                T F1[3], F2[3], W1[3], W2[3];
+#pragma unroll
+                for (int k = 0; k < 3; ++k) relay(d1[k], d2[k], s[k], F1[k], F2[k], W1[k], W2[k]);
+                segment_values(cw, F1, W1, v);
+                segment_values(cw, F2, W2, v2);
             }
         }
-        // Deposit of the start-cell segment(s), cooperatively per warp: lanes whose
-        // particles share the warp's most common start cell sum their 12 edge values
-        // with a reduce-scatter and 12 lanes add the sums; the other lanes add directly.
+        // Deposit.  The start-cell values v are reduced per group of lanes sharing a
+        // cell (largest groups first, one warp reduce-scatter and 12 atomics each);
+        // what remains, and the crossers' second segment v2, take the sparse path.
         {
             const int key = active ? lc : -1 - lane;
             const unsigned grp = __match_any_sync(0xffffffffu, key);
-            const unsigned sz = active ? (unsigned)__popc(grp) : 0u;
-            const unsigned best = __reduce_max_sync(0xffffffffu, sz);
-            if (best >= 2) {
-                const bool lead = active && sz == best && (__ffs(grp) - 1) == lane;
+            unsigned pend = __ballot_sync(0xffffffffu, active);
+#pragma unroll 1
+            for (int round = 0; round < GROUP_ROUNDS && pend; ++round) {
+                const unsigned mine = (pend >> lane) & 1u ? grp & pend : 0u;
+                const unsigned sz = __popc(mine);
+                const unsigned best = __reduce_max_sync(0xffffffffu, sz);
+                if (best < 3) break;   // a reduction round costs about three sparse records
+                const bool lead = sz == best && (__ffs(mine) - 1) == lane;
                 const int ml = __ffs(__ballot_sync(0xffffffffu, lead)) - 1;
-                const unsigned mgrp = __shfl_sync(0xffffffffu, grp, ml);
+                const unsigned mg = __shfl_sync(0xffffffffu, mine, ml);
                 const int mlc = __shfl_sync(0xffffffffu, lc, ml);
-                const bool in_major = (mgrp >> lane) & 1u;
+                const bool in = (mg >> lane) & 1u;
                 T b[16];
 #pragma unroll
-                for (int q = 0; q < 12; ++q) b[q] = in_major ? v[q] : T(0);
+                for (int q = 0; q < 12; ++q) b[q] = in ? v[q] : T(0);
 #pragma unroll
                 for (int q = 12; q < 16; ++q) b[q] = T(0);
                 const T r = reduce_scatter16(b, lane);
@@ -215,14 +279,13 @@ k_tile_push(const __grid_constant__ CUtensorMap tE0, const __grid_constant__ CUt
                 if (!(lane & 1) && slot < 12) {
                     int comp, ex, ey, ez;
                     slot_edge(slot, mlc & 7, (mlc >> 3) & 7, mlc >> 6, comp, ex, ey, ez);
-                    const Acc a = to_acc(r);
-                    if (a != Acc(0)) add(comp, ex, ey, ez, a);
+                    add(comp, ex, ey, ez, to_acc(r));
                 }
-                if (active && !in_major) scatter12(add, x, y, z, v);
-            } else if (active) {
-                scatter12(add, x, y, z, v);
+                pend &= ~mg;
             }
-            if (crossed) scatter12(add, x + s[0], y + s[1], z + s[2], v2);
+            sparse_deposit<T>(pend, v, pack_cell(x, y, z), lane, add);
+            sparse_deposit<T>(__ballot_sync(0xffffffffu, crossed), v2, pack_cell(x + s[0], y + s[1], z + s[2]), lane,
+                              add);
         }
         if (active) {
             const int nx = x + s[0], ny = y + s[1], nz = z + s[2];
@@ -257,13 +320,15 @@ k_tile_push(const __grid_constant__ CUtensorMap tE0, const __grid_constant__ CUt
         const int buf = it & 1;
         if (lane == 0) s_wtot[buf][warp] = __popc(bal);
         __syncthreads();
-        int before = 0, total = 0;
+        // prefix of the per-warp stayer counts: one load per lane and a shuffle scan
+        int incl = lane < NW ? s_wtot[buf][lane] : 0;
 #pragma unroll
-        for (int wv = 0; wv < PUSH_WARPS; ++wv) {
-            const int t = s_wtot[buf][wv];
-            before += wv < warp ? t : 0;
-            total += t;
+        for (int o = 1; o < NW; o <<= 1) {
+            const int y = __shfl_up_sync(0xffffffffu, incl, o);
+            if (lane >= o) incl += y;
         }
+        const int total = __shfl_sync(0xffffffffu, incl, NW - 1);
+        const int before = warp ? __shfl_sync(0xffffffffu, incl, warp - 1) : 0;
         if (stay) {
             const long long q = (long long)seg + written + before + __popc(bal & ((1u << lane) - 1));
             __stcs(A.pa.cell + q, lc);
@@ -282,8 +347,8 @@ k_tile_push(const __grid_constant__ CUtensorMap tE0, const __grid_constant__ CUt
     if (threadIdx.x == 0) A.pa.count[tile] = written;
 
     // flush the shared J tile to HBM (periodic wrap of the guard layers)
-    for (int e = threadIdx.x; e < 3 * SJ3; e += PUSH_THREADS) {
-        const Acc v = sJ[e];
+    for (int e = threadIdx.x; e < JT_ELEMS; e += NT) {
+        const Acc v = jtile_get(sJ, e, JT_ELEMS, Acc(0));
         if (v == Acc(0)) continue;
         const int comp = e / SJ3;
         const int r = e - comp * SJ3;
@@ -293,7 +358,7 @@ k_tile_push(const __grid_constant__ CUtensorMap tE0, const __grid_constant__ CUt
         const int gz = wrap_idx(oz + lz, A.g.n[2]);
         acc_atomic(A.f.J[comp] + A.g.cidx(gx, gy, gz), v);
     }
-    if (RECK) block_add_double<T>(kacc, A.krec);
+    if (RECK) block_add_double(kacc, A.krec);
 }
 
 // Spill-list particles: same arithmetic with global-memory gather and deposit.
@@ -459,7 +524,7 @@ static pic_status launch_tile(pic_ctx* c, PushArgs<T>& A) {
     }
     const int ntile = c->g.nt[0] * c->g.nt[1] * c->g.nt[2];
     LaunchScope ls(c, KC_TILE_PUSH);
-    kern<<<ntile, PUSH_THREADS, smem, c->stream>>>(c->tmap[0], c->tmap[1], c->tmap[2], c->tmap[3], c->tmap[4],
+    kern<<<ntile, Prec<T>::THREADS, smem, c->stream>>>(c->tmap[0], c->tmap[1], c->tmap[2], c->tmap[3], c->tmap[4],
                                                      c->tmap[5], A);
     GBPIC_CHECK(c, cudaGetLastError());
     return PIC_OK;

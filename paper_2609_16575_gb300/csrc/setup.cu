@@ -161,6 +161,7 @@ static pic_status load_t(pic_ctx* c, const pic_species_desc* d, SpeciesDev& s) {
     if (!base || !base2) return PIC_ERR_OOM;
     s.base[0] = base;
     s.base[1] = base2;
+    s.pbytes = pbytes;
     s.cur = 0;
     size_t off = pbytes;
     s.seg_start = reinterpret_cast<int*>(base + off); off += align256(sizeof(int) * ntile);

@@ -16,6 +16,7 @@ template <typename T> struct YeeArgs {
     T dt;           // Ampere: dt
     T jscale;       // physical J per fixed-point unit
     int zero_j;
+    int has_j;      // 0: curl update only (adjoint fields)
     double* rec;    // optional: rec[0] += 1/2 dV sum E^2, rec[1] += 1/2 dV sum B_new^2
     double half_dv;
 };
@@ -92,8 +93,9 @@ __global__ void __launch_bounds__(256) k_ampere(YeeArgs<T> A) {
     const T* Bz = A.f.B[2];
     const T bx = Bx[c], by = By[c], bz = Bz[c];
     using Acc = typename JTraits<T>::acc_t;
-    const Acc jx = A.f.J[0][cj], jy = A.f.J[1][cj], jz = A.f.J[2][cj];
-    if (A.zero_j) {
+    const Acc jx = A.has_j ? A.f.J[0][cj] : Acc(0), jy = A.has_j ? A.f.J[1][cj] : Acc(0),
+              jz = A.has_j ? A.f.J[2][cj] : Acc(0);
+    if (A.has_j && A.zero_j) {
         A.f.J[0][cj] = Acc(0);
         A.f.J[1][cj] = Acc(0);
         A.f.J[2][cj] = Acc(0);
@@ -143,6 +145,7 @@ template <typename T>
 static pic_status ampere_t(pic_ctx* c, bool zero_j) {
     YeeArgs<T> A = yee_args<T>(c, 1.0);
     A.zero_j = zero_j ? 1 : 0;
+    A.has_j = 1;
     LaunchScope ls(c, KC_AMPERE);
     k_ampere<T><<<yee_grid(c->g), dim3(32, 8), 0, c->stream>>>(A);
     GBPIC_CHECK(c, cudaGetLastError());
@@ -156,5 +159,46 @@ pic_status launch_faraday_half(pic_ctx* c, double* rec) {
 pic_status launch_ampere(pic_ctx* c, bool zero_j) {
     return c->prec == PIC_FP64 ? ampere_t<double>(c, zero_j) : ampere_t<float>(c, zero_j);
 }
+
+// Curl updates on arbitrary arrays (the adjoint fields): B <- B - coef curl E on the
+// Faraday stencil, and E <- E + coef curl B on the Ampere stencil, with ghost images.
+template <typename T>
+pic_status curl_to_b(pic_ctx* c, T* const E[3], T* const B[3], double coef) {
+    YeeArgs<T> A{};
+    A.g = c->g;
+    for (int k = 0; k < 3; ++k) {
+        A.f.E[k] = E[k];
+        A.f.B[k] = B[k];
+    }
+    A.cx = (T)(coef / c->desc.d[0]);
+    A.cy = (T)(coef / c->desc.d[1]);
+    A.cz = (T)(coef / c->desc.d[2]);
+    LaunchScope ls(c, KC_OTHER);
+    k_faraday_half<T, false><<<yee_grid(c->g), dim3(32, 8), 0, c->stream>>>(A);
+    GBPIC_CHECK(c, cudaGetLastError());
+    return PIC_OK;
+}
+
+template <typename T>
+pic_status curl_to_e(pic_ctx* c, T* const E[3], T* const B[3], double coef) {
+    YeeArgs<T> A{};
+    A.g = c->g;
+    for (int k = 0; k < 3; ++k) {
+        A.f.E[k] = E[k];
+        A.f.B[k] = B[k];
+    }
+    A.cx = (T)(coef / c->desc.d[0]);
+    A.cy = (T)(coef / c->desc.d[1]);
+    A.cz = (T)(coef / c->desc.d[2]);
+    A.has_j = 0;
+    LaunchScope ls(c, KC_OTHER);
+    k_ampere<T><<<yee_grid(c->g), dim3(32, 8), 0, c->stream>>>(A);
+    GBPIC_CHECK(c, cudaGetLastError());
+    return PIC_OK;
+}
+
+template pic_status curl_to_b<float>(pic_ctx*, float* const*, float* const*, double);
+template pic_status curl_to_b<double>(pic_ctx*, double* const*, double* const*, double);
+template pic_status curl_to_e<double>(pic_ctx*, double* const*, double* const*, double);
 
 }  // namespace gbpic

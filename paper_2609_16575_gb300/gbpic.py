@@ -89,6 +89,9 @@ def lib():
             L.pic_kernel_times.argtypes = [P, ctypes.c_int32, ctypes.POINTER(ctypes.c_char_p),
                                            ctypes.POINTER(ctypes.c_int64), ctypes.POINTER(ctypes.c_double),
                                            ctypes.POINTER(ctypes.c_int32)]
+            L.pic_adjoint_forward.argtypes = [P, ctypes.c_int32, ctypes.c_int32, ctypes.POINTER(ctypes.c_double)]
+            L.pic_adjoint_backward.argtypes = [P, P, P, ctypes.POINTER(ctypes.c_double), ctypes.POINTER(ctypes.c_void_p),
+                                               ctypes.c_int32]
             L.pic_launch_count.argtypes = [P]
             L.pic_launch_count.restype = ctypes.c_int64
             L.pic_last_error.argtypes = [P]
@@ -99,7 +102,7 @@ def lib():
             L.pic_destroy.restype = None
             for name in ("pic_init_grid", "pic_set_fields", "pic_load_species", "pic_step", "pic_sync",
                          "pic_get_fields", "pic_get_particles", "pic_diagnostics", "pic_get_history",
-                         "pic_set_timing", "pic_kernel_times"):
+                         "pic_set_timing", "pic_kernel_times", "pic_adjoint_forward", "pic_adjoint_backward"):
                 getattr(L, name).restype = ctypes.c_int
             _lib = L
     return _lib
@@ -107,7 +110,8 @@ def lib():
 
 EXPORTED = ("pic_init_grid", "pic_set_fields", "pic_load_species", "pic_step", "pic_sync", "pic_get_fields",
             "pic_get_particles", "pic_diagnostics", "pic_get_history", "pic_set_timing", "pic_kernel_times",
-            "pic_launch_count", "pic_last_error", "pic_status_string", "pic_destroy")
+            "pic_adjoint_forward", "pic_adjoint_backward", "pic_launch_count", "pic_last_error", "pic_status_string",
+            "pic_destroy")
 
 
 def _ptr(a):
@@ -295,3 +299,21 @@ class Context:
 
     def launch_count(self):
         return lib().pic_launch_count(self.ptr)
+
+    def adjoint_forward(self, nsteps, ckpt_every):
+        """Advance nsteps keeping checkpoints; returns L = U_E + U_B of the final state."""
+        L = ctypes.c_double()
+        _check(self.ptr, lib().pic_adjoint_forward(self.ptr, int(nsteps), int(ckpt_every), ctypes.byref(L)),
+               "pic_adjoint_forward")
+        return L.value
+
+    def adjoint_backward(self, E_dir=None, B_dir=None):
+        """Gradients of the last adjoint_forward loss: (dL/dA, [dL/du^{-1/2} (3, n) per species])."""
+        outs = [np.zeros((3, n)) for n in self.species_n]
+        ptrs = (ctypes.c_void_p * max(len(outs), 1))(*[o.ctypes.data for o in outs])
+        dA = ctypes.c_double()
+        pe, _ = _ptr(E_dir)
+        pb, _ = _ptr(B_dir)
+        _check(self.ptr, lib().pic_adjoint_backward(self.ptr, pe, pb, ctypes.byref(dA), ptrs, 0),
+               "pic_adjoint_backward")
+        return dA.value, outs
