@@ -181,6 +181,26 @@ pic_status pic_adjoint_forward(pic_ctx* ctx, int32_t nsteps, int32_t ckpt_every,
 pic_status pic_adjoint_backward(pic_ctx* ctx, const double* E_dir, const double* B_dir, double* dL_dA,
                                 double* const* dL_du, int32_t device_pointers);
 
+/* Allocation-free Gauss check.  The paper has no counterpart: this entry point exists
+ * for callers that cannot allocate device memory, e.g. an application whose memory
+ * pool already owns the device memory it may use, or a monitoring hook that must not
+ * trigger the device-wide synchronisation cudaMalloc/cudaFree can cause while other
+ * streams are busy.  It computes the same two values as the gauss_max and rho_max
+ * fields of pic_diagnostics (FP64 cloud-in-cell charge of every species on the nodes;
+ * max |div E - rho - rho_ion| and max |rho + rho_ion|) but keeps the node charge in a
+ * static device array of the library instead of memory it allocates:
+ *   - at most 1,048,576 cells (2^20, e.g. 128 x 128 x 64); a larger grid returns
+ *     PIC_ERR_ARG with the reason in pic_last_error;
+ *   - the array (8 MB) is held by every GPU that loads the library until the process
+ *     exits; the first call on a device looks up the array's device address
+ *     (cudaGetSymbolAddress, with that device current): make that first call before
+ *     any stream capture;
+ *   - all calls share the array and it keeps the last call's contents; each call
+ *     clears what it uses, but calls whose work overlaps on the GPU race on it.
+ * It calls no cudaMalloc or cudaFree and allocates nothing through the context's
+ * allocator.  Synchronises. */
+pic_status pic_gauss_check_static(pic_ctx* ctx, double* gauss_max, double* rho_max);
+
 /* Total kernel launches the library has issued on this context. */
 int64_t pic_launch_count(const pic_ctx* ctx);
 

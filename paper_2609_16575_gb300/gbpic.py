@@ -92,6 +92,7 @@ def lib():
             L.pic_adjoint_forward.argtypes = [P, ctypes.c_int32, ctypes.c_int32, ctypes.POINTER(ctypes.c_double)]
             L.pic_adjoint_backward.argtypes = [P, P, P, ctypes.POINTER(ctypes.c_double), ctypes.POINTER(ctypes.c_void_p),
                                                ctypes.c_int32]
+            L.pic_gauss_check_static.argtypes = [P, ctypes.POINTER(ctypes.c_double), ctypes.POINTER(ctypes.c_double)]
             L.pic_launch_count.argtypes = [P]
             L.pic_launch_count.restype = ctypes.c_int64
             L.pic_last_error.argtypes = [P]
@@ -102,7 +103,8 @@ def lib():
             L.pic_destroy.restype = None
             for name in ("pic_init_grid", "pic_set_fields", "pic_load_species", "pic_step", "pic_sync",
                          "pic_get_fields", "pic_get_particles", "pic_diagnostics", "pic_get_history",
-                         "pic_set_timing", "pic_kernel_times", "pic_adjoint_forward", "pic_adjoint_backward"):
+                         "pic_set_timing", "pic_kernel_times", "pic_adjoint_forward", "pic_adjoint_backward",
+                         "pic_gauss_check_static"):
                 getattr(L, name).restype = ctypes.c_int
             _lib = L
     return _lib
@@ -110,8 +112,8 @@ def lib():
 
 EXPORTED = ("pic_init_grid", "pic_set_fields", "pic_load_species", "pic_step", "pic_sync", "pic_get_fields",
             "pic_get_particles", "pic_diagnostics", "pic_get_history", "pic_set_timing", "pic_kernel_times",
-            "pic_adjoint_forward", "pic_adjoint_backward", "pic_launch_count", "pic_last_error", "pic_status_string",
-            "pic_destroy")
+            "pic_adjoint_forward", "pic_adjoint_backward", "pic_gauss_check_static", "pic_launch_count",
+            "pic_last_error", "pic_status_string", "pic_destroy")
 
 
 def _ptr(a):
@@ -299,6 +301,13 @@ class Context:
 
     def launch_count(self):
         return lib().pic_launch_count(self.ptr)
+
+    def gauss_check_static(self):
+        """(gauss_max, rho_max) from the allocation-free entry point."""
+        g, r = ctypes.c_double(), ctypes.c_double()
+        _check(self.ptr, lib().pic_gauss_check_static(self.ptr, ctypes.byref(g), ctypes.byref(r)),
+               "pic_gauss_check_static")
+        return g.value, r.value
 
     def adjoint_forward(self, nsteps, ckpt_every):
         """Advance nsteps keeping checkpoints; returns L = U_E + U_B of the final state."""
