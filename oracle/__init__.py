@@ -74,7 +74,7 @@ def lib():
             L.or_step.argtypes = [_ip, _dp, ctypes.c_double, _dp, ctypes.c_int, _dp, _lp,
                                   ctypes.POINTER(_dp), ctypes.POINTER(_dp), _dp]
             L.or_run.argtypes = [_ip, _dp, ctypes.c_double, _dp, ctypes.c_int, _dp, _lp,
-                                 ctypes.POINTER(_dp), ctypes.POINTER(_dp), ctypes.c_long, _dp]
+                                 ctypes.POINTER(_dp), ctypes.POINTER(_dp), ctypes.c_long, _dp, ctypes.c_long, _dp]
             L.or_gauss_x.argtypes = [_ip, _dp, _dp, _dp]
             L.or_gauss_x.restype = ctypes.c_double
             _lib = L
@@ -87,9 +87,17 @@ def _p(a: np.ndarray):
 
 
 def _grid(n, d):
+    """n = (nx, ny, nz) for a periodic box, or (nx, ny, nz, 1) for an open x dimension."""
+    n = list(n) + [0] * (4 - len(n))
     n = np.ascontiguousarray(n, dtype=np.int32)
     d = np.ascontiguousarray(d, dtype=np.float64)
     return n, d, n.ctypes.data_as(_ip), _p(d)
+
+
+def field_shape(n):
+    """(nz, ny, values per x line): nx, or nx + 1 nodes with an open x dimension."""
+    open_x = len(n) > 3 and n[3]
+    return (int(n[2]), int(n[1]), int(n[0]) + (1 if open_x else 0))
 
 
 class Species:
@@ -182,8 +190,9 @@ def zigzag(n, d, dt, qw, X1, X2, J):
 
 def rho(n, d, species, rho_ion=0.0):
     """Node charge density: CIC of every species plus the uniform background rho_ion."""
+    shape = field_shape(n)
     n, d, pn, pd = _grid(n, d)
-    out = np.full((int(n[2]), int(n[1]), int(n[0])), float(rho_ion))
+    out = np.full(shape, float(rho_ion))
     for s in species:
         lib().or_rho(pn, pd, s.q, s.n, _p(s.Q), _p(s.C), _p(out))
     return out
@@ -214,10 +223,12 @@ def backpush(n, d, dt, E, Bhalf, species):
                       species.q, species.m, species.n, _p(species.Q), _p(species.C))
 
 
-def run(n, d, dt, F, species, nsteps=1):
-    """Advance the state ``F`` (9, nz, ny, nx) and the species in place by ``nsteps``
+def run(n, d, dt, F, species, nsteps=1, step0=0, laser=None):
+    """Advance the state ``F`` (9, nz, ny, nx[+1]) and the species in place by ``nsteps``
     cycles of Fig. 2.  Returns the (nsteps, 3) energy history (U_E, U_B, K) of the
-    time levels n = 0 .. nsteps-1; on return F[6:9] holds the last J^{n+1/2}."""
+    time levels n = 0 .. nsteps-1; on return F[6:9] holds the last J^{n+1/2}.
+    ``step0`` is the index of the first cycle (it sets the laser time); ``laser`` =
+    (a0, omega, w0, tau_fwhm, t_peak, i_s, yc, zc) adds the soft laser sheet."""
     n, d, pn, pd = _grid(n, d)
     assert F.dtype == np.float64 and F.flags.c_contiguous and F.shape[0] == 9
     ns = len(species)
@@ -226,7 +237,9 @@ def run(n, d, dt, F, species, nsteps=1):
     ptrs = (_dp * ns)(*[_p(s.Q) for s in species])
     cptrs = (_dp * ns)(*[_p(s.C) for s in species])
     diag = np.zeros((nsteps, 3))
-    lib().or_run(pn, pd, dt, _p(F), ns, _p(qm), npc.ctypes.data_as(_lp), ptrs, cptrs, nsteps, _p(diag))
+    las = None if laser is None else np.ascontiguousarray(laser, dtype=np.float64)
+    lib().or_run(pn, pd, dt, _p(F), ns, _p(qm), npc.ctypes.data_as(_lp), ptrs, cptrs, nsteps, _p(diag), int(step0),
+                 None if las is None else _p(las))
     return diag
 
 
@@ -245,7 +258,7 @@ def continuity_residual(n, d, dt, rho0, rho1, J):
 
 
 def empty_fields(n):
-    return np.zeros((9, n[2], n[1], n[0]), dtype=np.float64)
+    return np.zeros((9,) + field_shape(n), dtype=np.float64)
 
 
 # --------------------------------------------------------------------------

@@ -33,22 +33,46 @@ typedef struct {
     int n[3];
     double d[3];
     double dt;
+    int open_x;    /* 1: x is bounded (absorbing faces), not periodic */
+    long nxs;      /* values stored per x line: n[0], or n[0] + 1 nodes when open_x */
 } or_grid;
+
+/* The exported functions take n as 4 ints: n[0..2] cells, n[3] = open_x.  With an
+ * open x dimension the arrays store nx + 1 values per x line (nodes 0..nx), so the
+ * node-located components (Ey, Ez, Bx, Jy, Jz, rho) include the boundary plane x = nx;
+ * the half-located ones (Ex, By, Bz, Jx) leave index nx unused.                   */
+static or_grid mkgrid(const int* n, const double* d, double dt)
+{
+    or_grid g = {{n[0], n[1], n[2]}, {d[0], d[1], d[2]}, dt, n[3], n[0] + (n[3] ? 1 : 0)};
+    return g;
+}
 
 static long wrapi(long i, long n) {
     long r = i % n;
     return r < 0 ? r + n : r;
 }
 
+/* Index of (i, j, k); y and z are periodic, x periodic or open.  Outside an open x
+ * range (i < 0 or i > nx) there is no value: -1.                                  */
 static long cell_index(const or_grid* g, long i, long j, long k) {
-    i = wrapi(i, g->n[0]);
+    if (g->open_x) {
+        if (i < 0 || i > g->n[0]) return -1;
+    } else {
+        i = wrapi(i, g->n[0]);
+    }
     j = wrapi(j, g->n[1]);
     k = wrapi(k, g->n[2]);
-    return (k * g->n[1] + j) * (long)g->n[0] + i;
+    return (k * g->n[1] + j) * g->nxs + i;
 }
 
 static long ncells(const or_grid* g) {
-    return (long)g->n[0] * g->n[1] * g->n[2];
+    return g->nxs * g->n[1] * g->n[2];
+}
+
+/* value at (i, j, k), zero outside an open x range */
+static double at(const or_grid* g, const double* F, long i, long j, long k) {
+    long c = cell_index(g, i, j, k);
+    return c < 0 ? 0.0 : F[c];
 }
 
 /* ------------------------------------------------------------------------ */
@@ -57,24 +81,25 @@ static long ncells(const or_grid* g) {
  * frac = 1 is one full step B^{n-1/2} -> B^{n+1/2}.                          */
 void or_faraday(const int* n, const double* d, double dt, const double* E, double* B, double frac)
 {
-    or_grid g = {{n[0], n[1], n[2]}, {d[0], d[1], d[2]}, dt};
+    or_grid g = mkgrid(n, d, dt);
     long N = ncells(&g);
     const double *Ex = E, *Ey = E + N, *Ez = E + 2 * N;
     double *Bx = B, *By = B + N, *Bz = B + 2 * N;
     double cx = frac * dt / d[0], cy = frac * dt / d[1], cz = frac * dt / d[2];
     for (long k = 0; k < n[2]; k++)
         for (long j = 0; j < n[1]; j++)
-            for (long i = 0; i < n[0]; i++) {
+            for (long i = 0; i < g.nxs; i++) {
                 long c = cell_index(&g, i, j, k);
                 /* Bx(i, j+1/2, k+1/2): -dt/dy [Ez(j+1)-Ez(j)] + dt/dz [Ey(k+1)-Ey(k)] */
-                Bx[c] += -cy * (Ez[cell_index(&g, i, j + 1, k)] - Ez[c])
-                         + cz * (Ey[cell_index(&g, i, j, k + 1)] - Ey[c]);
+                Bx[c] += -cy * (at(&g, Ez, i, j + 1, k) - Ez[c])
+                         + cz * (at(&g, Ey, i, j, k + 1) - Ey[c]);
+                if (i == n[0]) continue;   /* By, Bz sit at x = i + 1/2: none beyond the last cell */
                 /* By(i+1/2, j, k+1/2): -dt/dz [Ex(k+1)-Ex(k)] + dt/dx [Ez(i+1)-Ez(i)] */
-                By[c] += -cz * (Ex[cell_index(&g, i, j, k + 1)] - Ex[c])
-                         + cx * (Ez[cell_index(&g, i + 1, j, k)] - Ez[c]);
+                By[c] += -cz * (at(&g, Ex, i, j, k + 1) - Ex[c])
+                         + cx * (at(&g, Ez, i + 1, j, k) - Ez[c]);
                 /* Bz(i+1/2, j+1/2, k): -dt/dx [Ey(i+1)-Ey(i)] + dt/dy [Ex(j+1)-Ex(j)] */
-                Bz[c] += -cx * (Ey[cell_index(&g, i + 1, j, k)] - Ey[c])
-                         + cy * (Ex[cell_index(&g, i, j + 1, k)] - Ex[c]);
+                Bz[c] += -cx * (at(&g, Ey, i + 1, j, k) - Ey[c])
+                         + cy * (at(&g, Ex, i, j + 1, k) - Ex[c]);
             }
 }
 
@@ -82,7 +107,7 @@ void or_faraday(const int* n, const double* d, double dt, const double* E, doubl
  * cyclic permutations:  E <- E + dt (curl B - J).                            */
 void or_ampere(const int* n, const double* d, double dt, double* E, const double* B, const double* J)
 {
-    or_grid g = {{n[0], n[1], n[2]}, {d[0], d[1], d[2]}, dt};
+    or_grid g = mkgrid(n, d, dt);
     long N = ncells(&g);
     double *Ex = E, *Ey = E + N, *Ez = E + 2 * N;
     const double *Bx = B, *By = B + N, *Bz = B + 2 * N;
@@ -93,18 +118,44 @@ void or_ampere(const int* n, const double* d, double dt, double* E, const double
             for (long i = 0; i < n[0]; i++) {
                 long c = cell_index(&g, i, j, k);
                 /* Ex(i+1/2, j, k): +dt/dy [Bz(j+1/2)-Bz(j-1/2)] - dt/dz [By(k+1/2)-By(k-1/2)] - dt Jx */
-                Ex[c] += cy * (Bz[c] - Bz[cell_index(&g, i, j - 1, k)])
-                         - cz * (By[c] - By[cell_index(&g, i, j, k - 1)])
+                Ex[c] += cy * (Bz[c] - at(&g, Bz, i, j - 1, k))
+                         - cz * (By[c] - at(&g, By, i, j, k - 1))
                          - dt * Jx[c];
+                /* with open x the boundary nodes x = 0 (and x = nx, outside this loop) of
+                 * Ey and Ez belong to the absorbing boundary, not to this update */
+                if (g.open_x && i == 0) continue;
                 /* Ey(i, j+1/2, k): +dt/dz [Bx(k+1/2)-Bx(k-1/2)] - dt/dx [Bz(i+1/2)-Bz(i-1/2)] - dt Jy */
-                Ey[c] += cz * (Bx[c] - Bx[cell_index(&g, i, j, k - 1)])
-                         - cx * (Bz[c] - Bz[cell_index(&g, i - 1, j, k)])
+                Ey[c] += cz * (Bx[c] - at(&g, Bx, i, j, k - 1))
+                         - cx * (Bz[c] - at(&g, Bz, i - 1, j, k))
                          - dt * Jy[c];
                 /* Ez(i, j, k+1/2): +dt/dx [By(i+1/2)-By(i-1/2)] - dt/dy [Bx(j+1/2)-Bx(j-1/2)] - dt Jz */
-                Ez[c] += cx * (By[c] - By[cell_index(&g, i - 1, j, k)])
-                         - cy * (Bx[c] - Bx[cell_index(&g, i, j - 1, k)])
+                Ez[c] += cx * (By[c] - at(&g, By, i - 1, j, k))
+                         - cy * (Bx[c] - at(&g, Bx, i, j - 1, k))
                          - dt * Jz[c];
             }
+}
+
+/* First-order Mur absorbing condition on the tangential E (Ey, Ez) of the two x faces
+ * of an open x dimension, for a wave leaving along -x at x = 0 and +x at x = nx:
+ *   E^{n+1}(0)  = E^n(1)    + k (E^{n+1}(1)    - E^n(0)),   k = (dt - dx) / (dt + dx),
+ * and the mirror image at nx.  old holds Ey, Ez of planes 0, 1, nx-1, nx before the
+ * Ampere update (layout [comp][plane][k][j]).                                     */
+static void mur_x(const or_grid* g, const double* old, double* E)
+{
+    long N = ncells(g);
+    long P = (long)g->n[1] * g->n[2];
+    double kk = (g->dt - g->d[0]) / (g->dt + g->d[0]);
+    int nx = g->n[0];
+    for (int comp = 1; comp <= 2; comp++) {
+        double* F = E + comp * N;
+        const double* o = old + (comp - 1) * 4 * P;
+        for (long k = 0; k < g->n[2]; k++)
+            for (long j = 0; j < g->n[1]; j++) {
+                long p = k * g->n[1] + j;
+                F[cell_index(g, 0, j, k)] = o[1 * P + p] + kk * (F[cell_index(g, 1, j, k)] - o[0 * P + p]);
+                F[cell_index(g, nx, j, k)] = o[2 * P + p] + kk * (F[cell_index(g, nx - 1, j, k)] - o[3 * P + p]);
+            }
+    }
 }
 
 /* ------------------------------------------------------------------------ */
@@ -128,7 +179,7 @@ static double interp_component(const or_grid* g, const double* F, const int half
         for (int b = 0; b < 2; b++)
             for (int a = 0; a < 2; a++) {
                 double wgt = (a ? s[0] : 1.0 - s[0]) * (b ? s[1] : 1.0 - s[1]) * (c ? s[2] : 1.0 - s[2]);
-                v += wgt * F[cell_index(g, base[0] + a, base[1] + b, base[2] + c)];
+                v += wgt * at(g, F, base[0] + a, base[1] + b, base[2] + c);
             }
     return v;
 }
@@ -158,7 +209,7 @@ static void split(const double X[3], long cell[3], double off[3])
 
 void or_gather(const int* n, const double* d, const double* E, const double* B, const double* X, double* Ep, double* Bp)
 {
-    or_grid g = {{n[0], n[1], n[2]}, {d[0], d[1], d[2]}, 0.0};
+    or_grid g = mkgrid(n, d, 0.0);
     long cell[3];
     double off[3];
     split(X, cell, off);
@@ -247,7 +298,8 @@ static void segment_current(const or_grid* g, double qw, const long cell[3], con
                 long idx[3] = {cell[0], cell[1], cell[2]};
                 idx[p] += b;
                 idx[r] += c;
-                J[comp * N + cell_index(g, idx[0], idx[1], idx[2])] += val;
+                long e = cell_index(g, idx[0], idx[1], idx[2]);
+                if (e >= 0) J[comp * N + e] += val;   /* deposits outside an open x range leave the box */
             }
     }
 }
@@ -276,7 +328,7 @@ static void zigzag(const or_grid* g, double qw, const long c0[3], const double X
 
 void or_zigzag(const int* n, const double* d, double dt, double qw, const double* X1, const double* X2, double* J)
 {
-    or_grid g = {{n[0], n[1], n[2]}, {d[0], d[1], d[2]}, dt};
+    or_grid g = mkgrid(n, d, dt);
     long c0[3];
     double a[3], b[3];
     for (int k = 0; k < 3; k++) {
@@ -293,7 +345,7 @@ void or_zigzag(const int* n, const double* d, double dt, double qw, const double
  * x, y, z within the cell, ux, uy, uz, w).                                     */
 void or_rho(const int* n, const double* d, double q, long np, const double* P, const double* C, double* rho)
 {
-    or_grid g = {{n[0], n[1], n[2]}, {d[0], d[1], d[2]}, 0.0};
+    or_grid g = mkgrid(n, d, 0.0);
     double dV = d[0] * d[1] * d[2];
     for (long p = 0; p < np; p++) {
         long base[3];
@@ -307,7 +359,8 @@ void or_rho(const int* n, const double* d, double q, long np, const double* P, c
             for (int b = 0; b < 2; b++)
                 for (int a = 0; a < 2; a++) {
                     double wgt = (a ? s[0] : 1.0 - s[0]) * (b ? s[1] : 1.0 - s[1]) * (c ? s[2] : 1.0 - s[2]);
-                    rho[cell_index(&g, base[0] + a, base[1] + b, base[2] + c)] += qw * wgt;
+                    long e = cell_index(&g, base[0] + a, base[1] + b, base[2] + c);
+                    if (e >= 0) rho[e] += qw * wgt;
                 }
     }
 }
@@ -316,15 +369,15 @@ void or_rho(const int* n, const double* d, double q, long np, const double* P, c
  * components), the operator of Gauss's law (2) and of continuity (12).      */
 void or_divergence(const int* n, const double* d, const double* F, double* out)
 {
-    or_grid g = {{n[0], n[1], n[2]}, {d[0], d[1], d[2]}, 0.0};
+    or_grid g = mkgrid(n, d, 0.0);
     long N = ncells(&g);
     for (long k = 0; k < n[2]; k++)
         for (long j = 0; j < n[1]; j++)
             for (long i = 0; i < n[0]; i++) {
                 long c = cell_index(&g, i, j, k);
-                out[c] = (F[c] - F[cell_index(&g, i - 1, j, k)]) / d[0]
-                       + (F[N + c] - F[N + cell_index(&g, i, j - 1, k)]) / d[1]
-                       + (F[2 * N + c] - F[2 * N + cell_index(&g, i, j, k - 1)]) / d[2];
+                out[c] = (F[c] - at(&g, F, i - 1, j, k)) / d[0]
+                       + (F[N + c] - at(&g, F + N, i, j - 1, k)) / d[1]
+                       + (F[2 * N + c] - at(&g, F + 2 * N, i, j, k - 1)) / d[2];
             }
 }
 
@@ -332,15 +385,15 @@ void or_divergence(const int* n, const double* d, const double* F, double* out)
  * forward differences; zero by construction of the Yee scheme (section 2.3). */
 void or_divergence_b(const int* n, const double* d, const double* B, double* out)
 {
-    or_grid g = {{n[0], n[1], n[2]}, {d[0], d[1], d[2]}, 0.0};
+    or_grid g = mkgrid(n, d, 0.0);
     long N = ncells(&g);
     for (long k = 0; k < n[2]; k++)
         for (long j = 0; j < n[1]; j++)
             for (long i = 0; i < n[0]; i++) {
                 long c = cell_index(&g, i, j, k);
-                out[c] = (B[cell_index(&g, i + 1, j, k)] - B[c]) / d[0]
-                       + (B[N + cell_index(&g, i, j + 1, k)] - B[N + c]) / d[1]
-                       + (B[2 * N + cell_index(&g, i, j, k + 1)] - B[2 * N + c]) / d[2];
+                out[c] = (at(&g, B, i + 1, j, k) - B[c]) / d[0]
+                       + (at(&g, B + N, i, j + 1, k) - B[N + c]) / d[1]
+                       + (at(&g, B + 2 * N, i, j, k + 1) - B[2 * N + c]) / d[2];
             }
 }
 
@@ -351,7 +404,7 @@ void or_divergence_b(const int* n, const double* d, const double* B, double* out
 void or_backpush(const int* n, const double* d, double dt, const double* E, const double* Bhalf,
                  double q, double m, long np, double* P, const double* C)
 {
-    or_grid g = {{n[0], n[1], n[2]}, {d[0], d[1], d[2]}, dt};
+    or_grid g = mkgrid(n, d, dt);
     long N = ncells(&g);
     double* B0 = (double*)malloc(sizeof(double) * 3 * N);
     memcpy(B0, Bhalf, sizeof(double) * 3 * N);
@@ -383,11 +436,37 @@ void or_backpush(const int* n, const double* d, double dt, const double* E, cons
  * diag receives the energies of time level n:
  *   diag[0] = U_E = 1/2 dV sum E^n^2, diag[1] = U_B = 1/2 dV sum B^n^2,
  *   diag[2] = K = sum w m ((gamma^{n-1/2} + gamma^{n+1/2})/2 - 1).
- * Particles leaving the periodic box re-enter on the other side.            */
-void or_step(const int* n, const double* d, double dt, double* F, int ns, const double* qm, const long* np,
-             double** P, double** C, double* diag)
+ * Particles leaving the periodic box re-enter on the other side.  With an open x
+ * dimension (n[3] = 1) particles that leave in x are removed (their weight is set
+ * to 0 and they are skipped from then on), Ey and Ez of the two x faces follow the
+ * first-order Mur condition, and an optional laser sheet adds to J (laser != NULL).
+ * step is the index n of the cycle (time of J^{n+1/2} = (n + 1/2) dt).         */
+/* Soft laser source (the external electromagnetic source module of section 2.6,
+ * parameters of the laser-wakefield setup of section 4): a sheet of current J_y on the
+ * node plane x = i_s, J_y = -2 a(t) exp(-r^2 / w0^2) / dx with
+ * a(t) = a0 exp(-2 ln2 (t - t_p)^2 / tau^2) sin(omega (t - t_p)), tau the intensity FWHM,
+ * r the distance from (yc, zc) (cell units) of the J_y point (y_{j+1/2}, z_k).  In
+ * vacuum it radiates a wave of field amplitude a(t) to each side.
+ * laser = {a0, omega, w0, tau, t_p, i_s, yc, zc}; t is the time of J^{n+1/2}.      */
+static void laser_source(const or_grid* g, const double* laser, double t, double* J)
 {
-    or_grid g = {{n[0], n[1], n[2]}, {d[0], d[1], d[2]}, dt};
+    long N = ncells(g);
+    double a0 = laser[0], om = laser[1], w0 = laser[2], tau = laser[3], tp = laser[4];
+    long is = (long)laser[5];
+    double yc = laser[6] * g->d[1], zc = laser[7] * g->d[2];
+    double s = t - tp;
+    double a = a0 * exp(-2.0 * log(2.0) * s * s / (tau * tau)) * sin(om * s);
+    for (long k = 0; k < g->n[2]; k++)
+        for (long j = 0; j < g->n[1]; j++) {
+            double y = (j + 0.5) * g->d[1] - yc, z = k * g->d[2] - zc;
+            J[N + cell_index(g, is, j, k)] += -2.0 * a * exp(-(y * y + z * z) / (w0 * w0)) / g->d[0];
+        }
+}
+
+void or_step(const int* n, const double* d, double dt, double* F, int ns, const double* qm, const long* np,
+             double** P, double** C, double* diag, long step, const double* laser)
+{
+    or_grid g = mkgrid(n, d, dt);
     long N = ncells(&g);
     double dV = d[0] * d[1] * d[2];
     double *E = F, *B = F + 3 * N, *J = F + 6 * N;
@@ -408,6 +487,7 @@ void or_step(const int* n, const double* d, double dt, double* F, int ns, const 
         double* Cs = C[s];
         long cnt = np[s];
         for (long p = 0; p < cnt; p++) {
+            if (Ps[6 * cnt + p] == 0.0) continue;   /* removed through an open face */
             long cell[3] = {(long)Cs[p], (long)Cs[cnt + p], (long)Cs[2 * cnt + p]};
             double X1[3] = {Ps[p], Ps[cnt + p], Ps[2 * cnt + p]};          /* offsets: X relative to cell */
             double u[3] = {Ps[3 * cnt + p], Ps[4 * cnt + p], Ps[5 * cnt + p]};
@@ -421,21 +501,41 @@ void or_step(const int* n, const double* d, double dt, double* F, int ns, const 
             double X2[3];
             for (int dd = 0; dd < 3; dd++) X2[dd] = X1[dd] + dt * u[dd] / (g_new * d[dd]);
             zigzag(&g, q * w, cell, X1, X2, J);
+            int gone = 0;
             for (int dd = 0; dd < 3; dd++) {
                 /* new cell and offset; an offset that rounds to 1 starts the next cell */
                 double f = floor(X2[dd]);
                 double o = X2[dd] - f;
                 long cn = cell[dd] + (long)f;
                 if (o >= 1.0) { o = 0.0; cn += 1; }
+                if (dd == 0 && g.open_x && (cn < 0 || cn >= n[0])) gone = 1;
                 Cs[dd * cnt + p] = (double)wrapi(cn, n[dd]);
                 Ps[dd * cnt + p] = o;
             }
+            if (gone) Ps[6 * cnt + p] = 0.0;
             Ps[3 * cnt + p] = u[0];
             Ps[4 * cnt + p] = u[1];
             Ps[5 * cnt + p] = u[2];
         }
     }
+    if (laser) laser_source(&g, laser, (step + 0.5) * dt, J);
+    double* old = NULL;
+    if (g.open_x) {
+        /* Ey, Ez of planes 0, 1, nx-1, nx before the update, for the Mur condition */
+        long Pn = (long)n[1] * n[2];
+        long planes[4] = {0, 1, n[0] - 1, n[0]};
+        old = (double*)malloc(sizeof(double) * 8 * Pn);
+        for (int comp = 1; comp <= 2; comp++)
+            for (int q = 0; q < 4; q++)
+                for (long k = 0; k < n[2]; k++)
+                    for (long j = 0; j < n[1]; j++)
+                        old[((comp - 1) * 4 + q) * Pn + k * n[1] + j] = E[comp * N + cell_index(&g, planes[q], j, k)];
+    }
     or_ampere(n, d, dt, E, B, J);
+    if (old) {
+        mur_x(&g, old, E);
+        free(old);
+    }
     diag[0] = 0.5 * dV * UE;
     diag[1] = 0.5 * dV * UB;
     diag[2] = K;
@@ -445,9 +545,9 @@ void or_step(const int* n, const double* d, double dt, double* F, int ns, const 
 
 /* Several cycles; diag receives 3 values per step.                          */
 void or_run(const int* n, const double* d, double dt, double* F, int ns, const double* qm, const long* np,
-            double** P, double** C, long nsteps, double* diag)
+            double** P, double** C, long nsteps, double* diag, long step0, const double* laser)
 {
-    for (long s = 0; s < nsteps; s++) or_step(n, d, dt, F, ns, qm, np, P, C, diag + 3 * s);
+    for (long s = 0; s < nsteps; s++) or_step(n, d, dt, F, ns, qm, np, P, C, diag + 3 * s, step0 + s, laser);
 }
 
 /* Gauss's law for an initial state whose charge varies along x only
@@ -457,7 +557,7 @@ void or_run(const int* n, const double* d, double dt, double* F, int ns, const d
  * which must vanish for the result to satisfy div E = rho exactly.          */
 double or_gauss_x(const int* n, const double* d, const double* rho_total, double* E)
 {
-    or_grid g = {{n[0], n[1], n[2]}, {d[0], d[1], d[2]}, 0.0};
+    or_grid g = mkgrid(n, d, 0.0);
     long N = ncells(&g);
     double worst = 0.0;
     for (long c = 0; c < 3 * N; c++) E[c] = 0.0;

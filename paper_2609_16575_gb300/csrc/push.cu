@@ -604,12 +604,16 @@ __global__ void __launch_bounds__(256) k_sort_tiles(ParticleArrays<T> src, Parti
     for (int i = threadIdx.x; i < TILE_CELLS; i += 256) hist[i] = 0;
     __syncthreads();
     const long long seg = src.seg_start[t];
+    // runs of equal cells within a warp (nearly sorted input: few runs) count once
     for (int base = 0; base < cnt; base += 256) {
         const int i = base + threadIdx.x;
         const bool act = i < cnt;
         const int c = act ? src.cell[seg + i] : -1 - lane;
-        const unsigned g = __match_any_sync(0xffffffffu, c);
-        if (act && (__ffs(g) - 1) == lane) atomicAdd(&hist[c], __popc(g));
+        const int cp = __shfl_up_sync(0xffffffffu, c, 1);
+        const unsigned heads = __ballot_sync(0xffffffffu, lane == 0 || c != cp);
+        const unsigned after = heads & ~((2u << lane) - 1u);      // heads above this lane
+        const int end = after ? __ffs(after) - 1 : 32;            // one past the end of my run
+        if (act && ((heads >> lane) & 1u)) atomicAdd(&hist[c], end - lane);
     }
     __syncthreads();
     // exclusive scan of the 512 counts: two per thread, warp scans, then warp offsets
@@ -632,14 +636,17 @@ __global__ void __launch_bounds__(256) k_sort_tiles(ParticleArrays<T> src, Parti
         const int i = base + threadIdx.x;
         const bool act = i < cnt;
         const int c = act ? src.cell[seg + i] : -1 - lane;
-        const unsigned g = __match_any_sync(0xffffffffu, c);
-        const int leader = __ffs(g) - 1;
+        const int cp = __shfl_up_sync(0xffffffffu, c, 1);
+        const unsigned heads = __ballot_sync(0xffffffffu, lane == 0 || c != cp);
+        const int head = 31 - __clz(heads & ((2u << lane) - 1u));  // first lane of my run
+        const unsigned after = heads & ~((2u << lane) - 1u);
+        const int end = after ? __ffs(after) - 1 : 32;
         int b = 0;
-        if (act && lane == leader) b = atomicAdd(&hist[c], __popc(g));
-        b = __shfl_sync(0xffffffffu, b, leader);
+        if (act && lane == head) b = atomicAdd(&hist[c], end - lane);
+        b = __shfl_sync(0xffffffffu, b, head);
         if (act) {
             const long long p = seg + i;
-            const long long q = seg + b + __popc(g & ((1u << lane) - 1));
+            const long long q = seg + b + (lane - head);
             dst.cell[q] = c;
 #pragma unroll
             for (int k = 0; k < 3; ++k) {
