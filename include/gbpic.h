@@ -14,10 +14,14 @@
  * centred B^n of Eq. (21) in exact arithmetic.
  *
  * Units (the paper's normalised units, sections 2.3 and 3.1): c = eps0 = mu0 = 1.
- * Grid: n[0] x n[1] x n[2] cells of size d[0..2], periodic in every dimension.
+ * Grid: n[0] x n[1] x n[2] cells of size d[0..2], periodic in y and z, and in x
+ * unless bc_x = 1 (open x: absorbing faces, see pic_grid_desc).
  * Host field arrays are FP64, [component][k][j][i] with i fastest, each component
  * at its Yee location: Ex(i+1/2,j,k) Ey(i,j+1/2,k) Ez(i,j,k+1/2),
- * Bx(i,j+1/2,k+1/2) By(i+1/2,j,k+1/2) Bz(i+1/2,j+1/2,k); J like E.
+ * Bx(i,j+1/2,k+1/2) By(i+1/2,j,k+1/2) Bz(i+1/2,j+1/2,k); J like E.  Each x line
+ * holds n[0] values, or n[0] + 1 with an open x (nodes 0..n[0]: the node-located
+ * Ey, Ez, Bx include the face x = n[0]; Ex, By, Bz and all of J read 0 there, since
+ * the face Ey, Ez follow the Mur condition and no update reads J on that plane).
  * Particle positions are in cell units (X_d = x_d / d_d, 0 <= X_d < n_d).
  *
  * Ownership: the context owns every device buffer it allocates.  Host and device
@@ -78,7 +82,24 @@ typedef struct pic_grid_desc {
     pic_alloc_fn alloc;      /* optional */
     pic_free_fn free;        /* optional, required when alloc is set */
     void* alloc_user;
+    int32_t bc_x;            /* 0: periodic x; 1: open x (boundary modules of section 2.6 as used
+                                for the laser wakefield of section 4): first-order Mur on Ey, Ez of
+                                the faces x = 0 and x = n[0], particles leaving in x removed */
+    int32_t reserved1;
 } pic_grid_desc;
+
+/* Soft laser source on an open x (external-source module, section 2.6; section 4):
+ * a sheet J_y on the node plane x = plane, J_y = -2 a(t) exp(-r^2 / w0^2) / d[0] with
+ * a(t) = a0 exp(-2 ln2 (t - t_peak)^2 / tau^2) sin(omega (t - t_peak)), tau the
+ * intensity FWHM and r the distance of the J_y point (y_{j+1/2}, z_k) from (yc, zc)
+ * (cell units).  In vacuum the sheet radiates a field of amplitude a(t) to each
+ * side; the backward half leaves through the x = 0 face. */
+typedef struct pic_laser_desc {
+    double a0, omega, w0, tau, t_peak;
+    int32_t plane;
+    int32_t reserved;
+    double yc, zc;
+} pic_laser_desc;
 
 /* A particle species (section 2.1, Eqs. (8)-(11)): q, m per physical particle;
  * a super-particle of weight w carries q w and m w. */
@@ -108,6 +129,7 @@ typedef struct pic_diag {
     double J_max;            /* max |J^{n-1/2}| over components and cells */
     int64_t n_alive;         /* particles held, all species */
     int64_t n_spilled;       /* particles currently outside their tile segment (spill list) */
+    int64_t n_escaped;       /* particles removed through the open x faces so far */
 } pic_diag;
 
 /* Create a context: validates n, d and the CFL bound of Eq. (15) (section 2.3),
@@ -116,7 +138,8 @@ typedef struct pic_diag {
 pic_status pic_init_grid(const pic_grid_desc* desc, pic_ctx** out);
 
 /* Set E^0 and B^{-1/2} (section 2.3 time staggering).  E and B each hold 3*N FP64
- * values in the host layout above (N = n0 n1 n2); either may be NULL (zero).
+ * values in the host layout above (N = n0 n1 n2, or (n0 + 1) n1 n2 with an open x);
+ * either may be NULL (zero).
  * device_pointers = 1: E, B are device pointers.  Must precede pic_load_species
  * when a species asks for the back-push. */
 pic_status pic_set_fields(pic_ctx* ctx, const double* E, const double* B, int32_t device_pointers);
@@ -125,6 +148,10 @@ pic_status pic_set_fields(pic_ctx* ctx, const double* E, const double* B, int32_
  * precision, sorts particles into 8^3-cell tiles, and applies the backward half
  * push when momenta_at_half_step = 0.  *species_id receives the species index. */
 pic_status pic_load_species(pic_ctx* ctx, const pic_species_desc* desc, int32_t* species_id);
+
+/* Set (or, with NULL, remove) the laser sheet of an open x.  PIC_ERR_STATE without
+ * bc_x = 1; PIC_ERR_ARG for a plane outside 1..n[0]-1. */
+pic_status pic_set_laser(pic_ctx* ctx, const pic_laser_desc* laser);
 
 /* Advance nsteps cycles (section 2.2, Fig. 2), asynchronously on the context's
  * stream.  J of the last cycle is kept for pic_get_fields and pic_diagnostics. */
@@ -138,8 +165,9 @@ pic_status pic_sync(pic_ctx* ctx);
 pic_status pic_get_fields(pic_ctx* ctx, double* E, double* B, double* J, int32_t device_pointers);
 
 /* Copy one species out as 7 rows of *n FP64 values: X, Y, Z (cell units), ux, uy,
- * uz, w.  With track_ids the rows are in load order, else in tile order.  out may
- * be NULL to query *n.  Synchronises. */
+ * uz, w.  With track_ids the rows are in load order (*n = the number loaded; a
+ * particle removed through an open x face reads as NaN in every row), else in tile
+ * order (*n = the number alive).  out may be NULL to query *n.  Synchronises. */
 pic_status pic_get_particles(pic_ctx* ctx, int32_t species, double* out, int64_t* n, int32_t device_pointers);
 
 /* FP64 device reductions of the current state (section 3.3 diagnostics).

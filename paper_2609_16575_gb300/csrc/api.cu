@@ -120,11 +120,12 @@ static pic_status device_errors(pic_ctx* c) {
     return PIC_OK;
 }
 
-// The fixed-point unit of J (FP32 path): the coarsest unit any species needs; the
-// FP64 path accumulates J itself.
+// The fixed-point unit of J (FP32 path): the coarsest unit any species, or the laser
+// sheet (|J_y| <= 2 a0 / dx at one edge), needs; the FP64 path accumulates J itself.
 void update_jscale(pic_ctx* c) {
     double js = 0;
     for (auto& s : c->species) js = std::max(js, s.jscale);
+    if (c->laser_on) js = std::max(js, 2.0 * std::fabs(c->laser.a0) / c->desc.d[0] / std::ldexp(1.0, Prec<float>::JBITS));
     if (js <= 0 || c->prec == PIC_FP64) js = 1.0;
     c->jscale = js;
     c->jinv = 1.0 / js;
@@ -134,6 +135,7 @@ void update_jscale(pic_ctx* c) {
 // spill-list push, the mover append (and the periodic tile sort), Faraday half step,
 // Ampere.  J is cleared by Ampere unless keep_j.  Expects J = 0 on entry.
 pic_status step_once(pic_ctx* c, double* rec, bool keep_j) {
+    c->jscale_J = c->jscale;
     pic_status st = launch_faraday_half(c, rec);
     if (st != PIC_OK) return st;
     const int sort_every = c->desc.sort_every == 0 ? 4 : c->desc.sort_every;
@@ -148,8 +150,16 @@ pic_status step_once(pic_ctx* c, double* rec, bool keep_j) {
     }
     st = launch_faraday_half(c, nullptr);
     if (st != PIC_OK) return st;
+    if (c->g.open_x) {
+        st = launch_open_x_before_ampere(c);   // laser sheet into J, face planes saved for Mur
+        if (st != PIC_OK) return st;
+    }
     st = launch_ampere(c, !keep_j);
     if (st != PIC_OK) return st;
+    if (c->g.open_x) {
+        st = launch_open_x_after_ampere(c);    // Mur condition on the two x faces
+        if (st != PIC_OK) return st;
+    }
     c->step++;
     return PIC_OK;
 }
@@ -191,6 +201,8 @@ pic_status pic_init_grid(const pic_grid_desc* desc, pic_ctx** out) {
     if (desc->precision != PIC_FP32 && desc->precision != PIC_FP64) return PIC_ERR_ARG;
     if (desc->alloc && !desc->free) return PIC_ERR_ARG;
     if ((long long)desc->n[0] * desc->n[1] * desc->n[2] > (1LL << 31) - 1) return PIC_ERR_ARG;
+    if (desc->bc_x != 0 && desc->bc_x != 1) return PIC_ERR_ARG;
+    if (desc->bc_x == 1 && desc->n[0] < 3) return PIC_ERR_ARG;
     // Eq. (15): c dt <= 1 / sqrt(sum 1/d^2)
     const double lim = 1.0 / std::sqrt(1.0 / (desc->d[0] * desc->d[0]) + 1.0 / (desc->d[1] * desc->d[1]) +
                                        1.0 / (desc->d[2] * desc->d[2]));
@@ -220,6 +232,7 @@ pic_status pic_init_grid(const pic_grid_desc* desc, pic_ctx** out) {
     g.Gy = desc->n[1] + 2;
     g.Gz = desc->n[2] + 2;
     g.N = (long long)desc->n[0] * desc->n[1] * desc->n[2];
+    g.open_x = desc->bc_x == 1 ? 1 : 0;
     if (desc->stream) {
         c->stream = static_cast<cudaStream_t>(desc->stream);
     } else {
@@ -241,6 +254,13 @@ pic_status pic_init_grid(const pic_grid_desc* desc, pic_ctx** out) {
         cudaMemsetAsync(c->E[k], 0, fb, c->stream);
         cudaMemsetAsync(c->B[k], 0, fb, c->stream);
         cudaMemsetAsync(c->J[k], 0, sizeof(long long) * (size_t)g.N, c->stream);
+    }
+    if (g.open_x) {
+        c->mur_old = dev_alloc(c, (size_t)8 * desc->n[1] * desc->n[2] * c->esize);
+        if (!c->mur_old) {
+            pic_destroy(c);
+            return PIC_ERR_OOM;
+        }
     }
     if (desc->record_every > 0) {
         c->hist_cap = desc->history_capacity > 0 ? desc->history_capacity : 4096;
@@ -270,16 +290,16 @@ pic_status pic_init_grid(const pic_grid_desc* desc, pic_ctx** out) {
 pic_status pic_set_fields(pic_ctx* c, const double* E, const double* B, int32_t device_pointers) {
     if (!c) return PIC_ERR_ARG;
     cudaSetDevice(c->desc.device);
-    const size_t nb = sizeof(double) * 3 * (size_t)c->g.N;
+    const size_t nb = sizeof(double) * 3 * (size_t)c->g.host_N();
     const double *dE = E, *dB = B;
     double* stage = nullptr;
     if (!device_pointers && (E || B)) {
         stage = static_cast<double*>(dev_alloc(c, 2 * nb));
         if (!stage) return PIC_ERR_OOM;
         if (E) GBPIC_CHECK(c, cudaMemcpyAsync(stage, E, nb, cudaMemcpyHostToDevice, c->stream));
-        if (B) GBPIC_CHECK(c, cudaMemcpyAsync(stage + 3 * c->g.N, B, nb, cudaMemcpyHostToDevice, c->stream));
+        if (B) GBPIC_CHECK(c, cudaMemcpyAsync(stage + 3 * c->g.host_N(), B, nb, cudaMemcpyHostToDevice, c->stream));
         dE = E ? stage : nullptr;
-        dB = B ? stage + 3 * c->g.N : nullptr;
+        dB = B ? stage + 3 * c->g.host_N() : nullptr;
     }
     pic_status st = unpack_fields(c, dE, dB);
     GBPIC_CHECK(c, cudaStreamSynchronize(c->stream));
@@ -335,6 +355,26 @@ pic_status pic_step(pic_ctx* c, int32_t nsteps) {
     return PIC_OK;
 }
 
+pic_status pic_set_laser(pic_ctx* c, const pic_laser_desc* laser) {
+    if (!c) return PIC_ERR_ARG;
+    if (!c->g.open_x) {
+        c->err = "pic_set_laser needs an open x (bc_x = 1)";
+        return PIC_ERR_STATE;
+    }
+    if (!laser) {
+        c->laser_on = false;
+        update_jscale(c);
+        return PIC_OK;
+    }
+    if (laser->plane < 1 || laser->plane > c->g.n[0] - 1 || !(laser->tau > 0) || !(laser->w0 > 0) ||
+        !std::isfinite(laser->a0) || !std::isfinite(laser->omega) || !std::isfinite(laser->t_peak))
+        return PIC_ERR_ARG;
+    c->laser = *laser;
+    c->laser_on = true;
+    update_jscale(c);
+    return PIC_OK;
+}
+
 pic_status pic_sync(pic_ctx* c) {
     if (!c) return PIC_ERR_ARG;
     cudaSetDevice(c->desc.device);
@@ -346,7 +386,7 @@ pic_status pic_get_fields(pic_ctx* c, double* E, double* B, double* J, int32_t d
     if (!c) return PIC_ERR_ARG;
     pic_status st = pic_sync(c);
     if (st != PIC_OK && st != PIC_ERR_TILE_OVERFLOW) return st;
-    const size_t nb = sizeof(double) * 3 * (size_t)c->g.N;
+    const size_t nb = sizeof(double) * 3 * (size_t)c->g.host_N();
     if (device_pointers) {
         st = pack_fields(c, E, B, J);
         if (st != PIC_OK) return st;
@@ -356,8 +396,8 @@ pic_status pic_get_fields(pic_ctx* c, double* E, double* B, double* J, int32_t d
     double* stage = static_cast<double*>(dev_alloc(c, 3 * nb));
     if (!stage) return PIC_ERR_OOM;
     double* sE = E ? stage : nullptr;
-    double* sB = B ? stage + 3 * c->g.N : nullptr;
-    double* sJ = J ? stage + 6 * c->g.N : nullptr;
+    double* sB = B ? stage + 3 * c->g.host_N() : nullptr;
+    double* sJ = J ? stage + 6 * c->g.host_N() : nullptr;
     if (J && !c->j_dirty) GBPIC_CHECK(c, cudaMemsetAsync(sJ, 0, nb, c->stream));
     st = pack_fields(c, sE, sB, c->j_dirty ? sJ : nullptr);
     if (st != PIC_OK) return st;

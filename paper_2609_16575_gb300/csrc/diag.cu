@@ -38,6 +38,13 @@ __global__ void k_energy(Geom g, Fields<T> f, double hx, double hy, double hz, d
         const double bz = f.B[2][c] - (hx * ((double)f.E[1][c + 1] - ey) - hy * ((double)f.E[0][c + sy] - ex));
         se += ex * ex + ey * ey + ez * ez;
         sb += bx * bx + by * by + bz * bz;
+        if (g.open_x && i == g.n[0] - 1) {   // the face x = n: Ey, Ez and Bx live there
+            const long long q = g.pidx(i + 1, j, k);
+            const double eyf = f.E[1][q], ezf = f.E[2][q];
+            const double bxf = f.B[0][q] - (hy * ((double)f.E[2][q + sy] - ezf) - hz * ((double)f.E[1][q + sz] - eyf));
+            se += eyf * eyf + ezf * ezf;
+            sb += bxf * bxf;
+        }
     }
     acc_sum(acc, S_UE, se * half_dv);
     acc_sum(acc, S_UB, sb * half_dv);
@@ -56,7 +63,9 @@ __global__ void k_particles(Geom g, ParticleArrays<T> pa, const Rec<T>* spill, i
         for (int c = 0; c < 2; ++c)
             for (int b = 0; b < 2; ++b)
                 for (int a = 0; a < 2; ++a) {
-                    const long long e = g.cidx(wrap_idx(gx + a, g.n[0]), wrap_idx(gy + b, g.n[1]), wrap_idx(gz + c, g.n[2]));
+                    const int xx = x_after(g, gx + a);   // the face node of an open x has no slot
+                    if (xx < 0) continue;
+                    const long long e = g.cidx(xx, wrap_idx(gy + b, g.n[1]), wrap_idx(gz + c, g.n[2]));
                     atomicAdd(rho + e, qdv * w * wx[a] * wy[b] * wz[c]);
                 }
     };
@@ -96,13 +105,15 @@ __global__ void k_nodes(Geom g, Fields<T> f, const double* d, double rho_ion, do
         mr = fmax(mr, fabs(rt));
         if (gref_valid) mgc = fmax(mgc, fabs(G - gref[e]));
         else gref[e] = G;
-        const long long ex = g.cidx(wrap_idx(i - 1, g.n[0]), j, k);
+        // an open x has no edge left of node 0: its Jx there is zero
+        const long long ex = (g.open_x && i == 0) ? -1 : g.cidx(wrap_idx(i - 1, g.n[0]), j, k);
         const long long ey = g.cidx(i, wrap_idx(j - 1, g.n[1]), k);
         const long long ez = g.cidx(i, j, wrap_idx(k - 1, g.n[2]));
         const double jx = (double)f.J[0][e] * jscale, jy = (double)f.J[1][e] * jscale, jz = (double)f.J[2][e] * jscale;
         mj = fmax(mj, fmax(fabs(jx), fmax(fabs(jy), fabs(jz))));
         if (cont_valid) {
-            const double divJ = (jx - (double)f.J[0][ex] * jscale) / d[0] + (jy - (double)f.J[1][ey] * jscale) / d[1] +
+            const double jxm = ex < 0 ? 0.0 : (double)f.J[0][ex] * jscale;
+            const double divJ = (jx - jxm) / d[0] + (jy - (double)f.J[1][ey] * jscale) / d[1] +
                                 (jz - (double)f.J[2][ez] * jscale) / d[2];
             mc = fmax(mc, fabs((rho[e] - rho_prev[e]) / dt + divJ));
         }
@@ -162,7 +173,7 @@ static pic_status diag_t(pic_ctx* c, pic_diag* out) {
     const int cont_valid = (c->rho_prev_step >= 0 && c->step == c->rho_prev_step + 1 && c->j_dirty) ? 1 : 0;
     {
         LaunchScope ls(c, KC_OTHER);
-        k_nodes<T><<<1024, 256, 0, c->stream>>>(g, f, dd, c->desc.rho_ion, dt, c->jscale, c->rho, c->rho_prev, c->gref,
+        k_nodes<T><<<1024, 256, 0, c->stream>>>(g, f, dd, c->desc.rho_ion, dt, c->jscale_J, c->rho, c->rho_prev, c->gref,
                                                  c->gref_valid ? 1 : 0, cont_valid, c->dacc);
         GBPIC_CHECK(c, cudaGetLastError());
     }
@@ -181,6 +192,12 @@ static pic_status diag_t(pic_ctx* c, pic_diag* out) {
     out->J_max = c->j_dirty ? h[M_J] : 0.0;
     out->n_alive = alive;
     out->n_spilled = spilled;
+    out->n_escaped = 0;
+    for (auto& s : c->species) {
+        Counters h;
+        GBPIC_CHECK(c, cudaMemcpy(&h, s.ctr, sizeof(Counters), cudaMemcpyDeviceToHost));
+        out->n_escaped += h.escaped;
+    }
     c->gref_valid = true;
     c->rho_prev_step = c->step;
     return PIC_OK;

@@ -48,6 +48,7 @@ template <> struct Prec<double> {
 // with the x pitch padded to a multiple of 8 elements (rows 16-B aligned).
 struct Geom {
     int n[3];
+    int open_x;       // 1: x is open (absorbing faces); the ghost x = n holds the face nodes
     int nt[3];        // tiles per dimension (ceil(n/8))
     int Px, Gy, Gz;   // x pitch, padded y and z extents (n+2)
     long long N;      // n0 n1 n2
@@ -58,6 +59,8 @@ struct Geom {
         return ((long long)k * n[1] + j) * n[0] + i;
     }
     __host__ __device__ long long padded_size() const { return (long long)Px * Gy * Gz; }
+    // values of one component in the host layout (an open x line holds n0 + 1 nodes)
+    __host__ __device__ long long host_N() const { return (long long)(n[0] + open_x) * n[1] * n[2]; }
 };
 
 // Accumulator of the current density J.  FP32 path: 64-bit fixed point (exact,
@@ -84,7 +87,8 @@ struct Counters {
     int mover_count[2];
     int spill_count[2];
     int err;
-    int pad[3];
+    int escaped;      // particles removed through open x faces
+    int pad[2];
 };
 
 // One particle outside its tile segment (mover or spill record); cell is global.
@@ -455,16 +459,23 @@ __device__ __forceinline__ int images(int i, int n, int out[3]) {
     return m;
 }
 
+// Store v0..v2 at (i, j, k) and at its periodic ghost images.  An open x has no x
+// images (its ghost x = -1 stays zero and x = n holds the face nodes), and i may then
+// be n itself.
 template <typename T>
 __device__ __forceinline__ void store3(const Geom& g, T* a0, T* a1, T* a2, int i, int j, int k, T v0, T v1, T v2) {
     const long long c = g.pidx(i, j, k);
     a0[c] = v0;
     a1[c] = v1;
     a2[c] = v2;
-    const bool edge = i == 0 || i == g.n[0] - 1 || j == 0 || j == g.n[1] - 1 || k == 0 || k == g.n[2] - 1;
+    const bool edge = (!g.open_x && (i == 0 || i == g.n[0] - 1)) || j == 0 || j == g.n[1] - 1 || k == 0 ||
+                      k == g.n[2] - 1;
     if (!edge) return;
     int xs[3], ys[3], zs[3];
-    const int nx = images(i, g.n[0], xs), ny = images(j, g.n[1], ys), nz = images(k, g.n[2], zs);
+    int nx = 1;
+    xs[0] = i;
+    if (!g.open_x) nx = images(i, g.n[0], xs);
+    const int ny = images(j, g.n[1], ys), nz = images(k, g.n[2], zs);
     for (int c3 = 0; c3 < nz; ++c3)
         for (int b = 0; b < ny; ++b)
             for (int a = 0; a < nx; ++a) {
@@ -474,6 +485,21 @@ __device__ __forceinline__ void store3(const Geom& g, T* a0, T* a1, T* a2, int i
                 a1[q] = v1;
                 a2[q] = v2;
             }
+}
+
+// One component at (i, j, k) with its y and z images (face planes of an open x).
+template <typename T>
+__device__ __forceinline__ void store1_yz(const Geom& g, T* a, int i, int j, int k, T v) {
+    int ys[3], zs[3];
+    const int ny = images(j, g.n[1], ys), nz = images(k, g.n[2], zs);
+    for (int c3 = 0; c3 < nz; ++c3)
+        for (int b = 0; b < ny; ++b) a[g.pidx(i, ys[b], zs[c3])] = v;
+}
+
+// x index of a global cell after a move: wrapped (periodic) or -1 when it left an open x.
+__device__ __forceinline__ int x_after(const Geom& g, int gx) {
+    if (g.open_x) return (gx < 0 || gx >= g.n[0]) ? -1 : gx;
+    return wrap_idx(gx, g.n[0]);
 }
 
 // ---------------------------------------------------------------------------
@@ -528,6 +554,7 @@ struct pic_ctx {
     void* J[3] = {};          // JTraits<T>::acc_t arrays, compact layout
     double jscale = 0;        // physical J per fixed-point unit (shared by all species)
     double jinv = 0;          // 1 / jscale
+    double jscale_J = 1.0;    // the unit of the J the last cycle kept (jscale then)
     bool fields_set = false;
     bool j_dirty = false;     // J holds the last deposit and must be cleared before stepping
     int64_t step = 0;
@@ -553,6 +580,10 @@ struct pic_ctx {
     std::vector<void*> allocations;
     std::string err;
     void* adj = nullptr;      // checkpointed adjoint state (adjoint.cu)
+    // open x: the laser sheet and the Mur buffer (Ey, Ez of planes 0, 1, n-1, n)
+    bool laser_on = false;
+    pic_laser_desc laser{};
+    void* mur_old = nullptr;
 };
 
 namespace gbpic {
@@ -569,6 +600,8 @@ pic_status step_once(pic_ctx* c, double* rec, bool keep_j);
 void update_jscale(pic_ctx* c);
 void adjoint_free(pic_ctx* c);
 pic_status energy_sums(pic_ctx* c, double* UE, double* UB);
+pic_status launch_open_x_before_ampere(pic_ctx* c);
+pic_status launch_open_x_after_ampere(pic_ctx* c);
 pic_status load_species_impl(pic_ctx* c, const pic_species_desc* d, SpeciesDev& s);
 pic_status get_particles_impl(pic_ctx* c, SpeciesDev& s, double* out_dev, int64_t n_out);
 pic_status pack_fields(pic_ctx* c, double* E, double* B, double* J);   // device outputs

@@ -293,12 +293,22 @@ k_tile_push(const __grid_constant__ CUtensorMap tE0, const __grid_constant__ CUt
             move = !stay;
             if (stay) lc = nx | (ny << 3) | (nz << 6);
         }
-        // movers: to the global list with their wrapped global cell
+        // movers: to the global list with their wrapped global cell; a particle that
+        // left an open x face is removed instead
+        int gxm = 0;
+        if (move) {
+            gxm = x_after(A.g, ox + x + s[0]);
+            if (gxm < 0) move = false;
+        }
+        if (__ballot_sync(0xffffffffu, active && !stay && !move)) {
+            const unsigned gone = __ballot_sync(0xffffffffu, active && !stay && !move);
+            if (lane == __ffs(gone) - 1) atomicAdd(&A.ctr->escaped, __popc(gone));
+        }
         const int slot = warp_reserve(&A.ctr->mover_count[A.parity], move);
         if (move) {
             if (slot < A.mover_cap) {
                 Rec<T> r;
-                const int gx = wrap_idx(ox + x + s[0], A.g.n[0]);
+                const int gx = gxm;
                 const int gy = wrap_idx(oy + y + s[1], A.g.n[1]);
                 const int gz = wrap_idx(oz + z + s[2], A.g.n[2]);
                 r.cell = (gz * A.g.n[1] + gy) * A.g.n[0] + gx;
@@ -353,7 +363,8 @@ k_tile_push(const __grid_constant__ CUtensorMap tE0, const __grid_constant__ CUt
         const int comp = e / SJ3;
         const int r = e - comp * SJ3;
         const int lx = r % SJ - 1, ly = (r / SJ) % SJ - 1, lz = r / (SJ * SJ) - 1;
-        const int gx = wrap_idx(ox + lx, A.g.n[0]);
+        const int gx = x_after(A.g, ox + lx);
+        if (gx < 0) continue;   // current leaving an open x face
         const int gy = wrap_idx(oy + ly, A.g.n[1]);
         const int gz = wrap_idx(oz + lz, A.g.n[2]);
         acc_atomic(A.f.J[comp] + A.g.cidx(gx, gy, gz), v);
@@ -375,8 +386,9 @@ __global__ void __launch_bounds__(256) k_list_push(PushArgs<T> A) {
         };
         using Acc = typename JTraits<T>::acc_t;
         auto add = [&](int comp, int x, int y, int z, Acc v) {
-            if (v != Acc(0))
-                acc_atomic(A.f.J[comp] + A.g.cidx(wrap_idx(x, A.g.n[0]), wrap_idx(y, A.g.n[1]), wrap_idx(z, A.g.n[2])), v);
+            const int xx = x_after(A.g, x);
+            if (v != Acc(0) && xx >= 0)
+                acc_atomic(A.f.J[comp] + A.g.cidx(xx, wrap_idx(y, A.g.n[1]), wrap_idx(z, A.g.n[2])), v);
         };
         T Ep[3], Bp[3], u[3] = {r.u[0], r.u[1], r.u[2]}, d2[3];
         gather_eb<T>(fetch, gx, gy, gz, r.d[0], r.d[1], r.d[2], Ep, Bp);
@@ -395,9 +407,13 @@ __global__ void __launch_bounds__(256) k_list_push(PushArgs<T> A) {
         }
         const T cw[3] = {A.cq[0] * r.w, A.cq[1] * r.w, A.cq[2] * r.w};
         zigzag_deposit<T>(add, gx, gy, gz, r.d, s, d2, cw);
+        const int nxg = x_after(A.g, gx + s[0]);
+        if (nxg < 0) {   // left an open x face: removed
+            atomicAdd(&A.ctr->escaped, 1);
+            continue;
+        }
         Rec<T> o;
-        o.cell = (wrap_idx(gz + s[2], A.g.n[2]) * A.g.n[1] + wrap_idx(gy + s[1], A.g.n[1])) * A.g.n[0] +
-                 wrap_idx(gx + s[0], A.g.n[0]);
+        o.cell = (wrap_idx(gz + s[2], A.g.n[2]) * A.g.n[1] + wrap_idx(gy + s[1], A.g.n[1])) * A.g.n[0] + nxg;
         o.id = r.id;
         for (int k = 0; k < 3; ++k) {
             o.d[k] = d2[k];

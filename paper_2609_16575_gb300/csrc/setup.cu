@@ -320,9 +320,10 @@ int64_t count_alive(pic_ctx* c, SpeciesDev& s, int64_t* spilled) {
 
 template <typename T>
 __global__ void k_unpack(Geom g, const double* src, T* a0, T* a1, T* a2) {
-    const long long N = g.N;
+    const long long N = g.host_N();
+    const int nxs = g.n[0] + g.open_x;
     for (long long e = blockIdx.x * (long long)blockDim.x + threadIdx.x; e < N; e += (long long)gridDim.x * blockDim.x) {
-        const int i = (int)(e % g.n[0]), j = (int)((e / g.n[0]) % g.n[1]), k = (int)(e / ((long long)g.n[0] * g.n[1]));
+        const int i = (int)(e % nxs), j = (int)((e / nxs) % g.n[1]), k = (int)(e / ((long long)nxs * g.n[1]));
         const T v0 = src ? (T)src[e] : T(0), v1 = src ? (T)src[N + e] : T(0), v2 = src ? (T)src[2 * N + e] : T(0);
         store3(g, a0, a1, a2, i, j, k, v0, v1, v2);
     }
@@ -332,10 +333,12 @@ template <typename T, typename A>
 __global__ void k_pack(Geom g, const T* E0, const T* E1, const T* E2, const T* B0, const T* B1, const T* B2,
                        const A* J0, const A* J1, const A* J2, double jscale, double* E,
                        double* B, double* J) {
-    const long long N = g.N;
+    const long long N = g.host_N();
+    const int nxs = g.n[0] + g.open_x;
     for (long long e = blockIdx.x * (long long)blockDim.x + threadIdx.x; e < N; e += (long long)gridDim.x * blockDim.x) {
-        const int i = (int)(e % g.n[0]), j = (int)((e / g.n[0]) % g.n[1]), k = (int)(e / ((long long)g.n[0] * g.n[1]));
+        const int i = (int)(e % nxs), j = (int)((e / nxs) % g.n[1]), k = (int)(e / ((long long)nxs * g.n[1]));
         const long long p = g.pidx(i, j, k);
+        const long long cj = i < g.n[0] ? g.cidx(i, j, k) : -1;   // J has no slot on an open face
         if (E) {
             E[e] = (double)E0[p];
             E[N + e] = (double)E1[p];
@@ -347,9 +350,9 @@ __global__ void k_pack(Geom g, const T* E0, const T* E1, const T* E2, const T* B
             B[2 * N + e] = (double)B2[p];
         }
         if (J) {
-            J[e] = (double)J0[e] * jscale;
-            J[N + e] = (double)J1[e] * jscale;
-            J[2 * N + e] = (double)J2[e] * jscale;
+            J[e] = cj < 0 ? 0.0 : (double)J0[cj] * jscale;
+            J[N + e] = cj < 0 ? 0.0 : (double)J1[cj] * jscale;
+            J[2 * N + e] = cj < 0 ? 0.0 : (double)J2[cj] * jscale;
         }
     }
 }
@@ -374,7 +377,7 @@ static pic_status pack_t(pic_ctx* c, double* E, double* B, double* J) {
     using A = typename JTraits<T>::acc_t;
     k_pack<T, A><<<1024, 256, 0, c->stream>>>(c->g, (T*)c->E[0], (T*)c->E[1], (T*)c->E[2], (T*)c->B[0], (T*)c->B[1],
                                                (T*)c->B[2], (const A*)c->J[0], (const A*)c->J[1], (const A*)c->J[2],
-                                               c->jscale, E, B, J);
+                                               c->jscale_J, E, B, J);
     GBPIC_CHECK(c, cudaGetLastError());
     return PIC_OK;
 }

@@ -34,9 +34,12 @@ __global__ void k_static_charge(Geom g, ParticleArrays<T> pa, const Rec<T>* spil
         const double wx[2] = {1.0 - dx, dx}, wy[2] = {1.0 - dy, dy}, wz[2] = {1.0 - dz, dz};
         for (int c = 0; c < 2; ++c)
             for (int b = 0; b < 2; ++b)
-                for (int a = 0; a < 2; ++a)
-                    atomicAdd(rho + g.cidx(wrap_idx(gx + a, g.n[0]), wrap_idx(gy + b, g.n[1]), wrap_idx(gz + c, g.n[2])),
+                for (int a = 0; a < 2; ++a) {
+                    const int xx = x_after(g, gx + a);   // the face node of an open x has no slot
+                    if (xx < 0) continue;
+                    atomicAdd(rho + g.cidx(xx, wrap_idx(gy + b, g.n[1]), wrap_idx(gz + c, g.n[2])),
                               qdv * w * wx[a] * wy[b] * wz[c]);
+                }
     };
     for (int t = blockIdx.x; t < ntile; t += gridDim.x) {
         const int cnt = min(pa.count[t], pa.cap[t]);

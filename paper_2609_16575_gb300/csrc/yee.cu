@@ -5,6 +5,8 @@
 // an edge cell also into its periodic ghost images (local -1 and n), so the next
 // stencil and the tile kernel's TMA staging read valid ghosts without a separate
 // halo pass.
+#include <cmath>
+
 #include "pic_internal.cuh"
 
 namespace gbpic {
@@ -70,6 +72,17 @@ __global__ void __launch_bounds__(256) k_faraday_half(YeeArgs<T> A) {
             se = (double)ex * ex + (double)ey * ey + (double)ez * ez;
             sb = (double)bx * bx + (double)by * by + (double)bz * bz;
         }
+        if (g.open_x && i == g.n[0] - 1) {
+            // the face x = n of an open x carries Bx (and Ey, Ez set by the Mur condition)
+            const long long f = g.pidx(i + 1, j, k);
+            const T eyf = Ey[f], ezf = Ez[f];
+            const T bxf = A.f.B[0][f] - (A.cy * (Ez[f + sy] - ezf) - A.cz * (Ey[f + sz] - eyf));
+            store1_yz(g, A.f.B[0], i + 1, j, k, bxf);
+            if (REC) {
+                se += (double)eyf * eyf + (double)ezf * ezf;
+                sb += (double)bxf * bxf;
+            }
+        }
     }
     if (REC) block_add2(se * A.half_dv, sb * A.half_dv, A.rec);
 }
@@ -103,9 +116,13 @@ __global__ void __launch_bounds__(256) k_ampere(YeeArgs<T> A) {
     // Ex(i+1/2, j, k) += dt/dy [Bz(j+1/2) - Bz(j-1/2)] - dt/dz [By(k+1/2) - By(k-1/2)] - dt Jx
     const T ex = A.f.E[0][c] + (A.cy * (bz - Bz[c - sy]) - A.cz * (by - By[c - sz])) - A.dt * j_value(jx, A.jscale);
     // Ey(i, j+1/2, k) += dt/dz [Bx(k+1/2) - Bx(k-1/2)] - dt/dx [Bz(i+1/2) - Bz(i-1/2)] - dt Jy
-    const T ey = A.f.E[1][c] + (A.cz * (bx - Bx[c - sz]) - A.cx * (bz - Bz[c - 1])) - A.dt * j_value(jy, A.jscale);
+    T ey = A.f.E[1][c] + (A.cz * (bx - Bx[c - sz]) - A.cx * (bz - Bz[c - 1])) - A.dt * j_value(jy, A.jscale);
     // Ez(i, j, k+1/2) += dt/dx [By(i+1/2) - By(i-1/2)] - dt/dy [Bx(j+1/2) - Bx(j-1/2)] - dt Jz
-    const T ez = A.f.E[2][c] + (A.cx * (by - By[c - 1]) - A.cy * (bx - Bx[c - sy])) - A.dt * j_value(jz, A.jscale);
+    T ez = A.f.E[2][c] + (A.cx * (by - By[c - 1]) - A.cy * (bx - Bx[c - sy])) - A.dt * j_value(jz, A.jscale);
+    if (g.open_x && i == 0) {   // the face x = 0 of an open x follows the Mur condition instead
+        ey = A.f.E[1][c];
+        ez = A.f.E[2][c];
+    }
     store3(g, A.f.E[0], A.f.E[1], A.f.E[2], i, j, k, ex, ey, ez);
 }
 
@@ -200,5 +217,91 @@ pic_status curl_to_e(pic_ctx* c, T* const E[3], T* const B[3], double coef) {
 template pic_status curl_to_b<float>(pic_ctx*, float* const*, float* const*, double);
 template pic_status curl_to_b<double>(pic_ctx*, double* const*, double* const*, double);
 template pic_status curl_to_e<double>(pic_ctx*, double* const*, double* const*, double);
+
+// ---------------------------------------------------------------------------
+// Open x (boundary and external-source modules of section 2.6; section 4 set-up).
+
+// Ey, Ez of the planes x = 0, 1, n-1, n before the Ampere update: old[comp][plane][k][j].
+template <typename T>
+__global__ void k_mur_save(Geom g, const T* Ey, const T* Ez, T* old) {
+    const int j = blockIdx.x * blockDim.x + threadIdx.x, k = blockIdx.y;
+    if (j >= g.n[1]) return;
+    const long long P = (long long)g.n[1] * g.n[2], p = (long long)k * g.n[1] + j;
+    const int planes[4] = {0, 1, g.n[0] - 1, g.n[0]};
+    for (int q = 0; q < 4; ++q) {
+        old[q * P + p] = Ey[g.pidx(planes[q], j, k)];
+        old[(4 + q) * P + p] = Ez[g.pidx(planes[q], j, k)];
+    }
+}
+
+// First-order Mur on the two faces: E^{n+1}(0) = E^n(1) + kk (E^{n+1}(1) - E^n(0)),
+// E^{n+1}(n) = E^n(n-1) + kk (E^{n+1}(n-1) - E^n(n)), kk = (dt - dx) / (dt + dx).
+template <typename T>
+__global__ void k_mur_apply(Geom g, T* Ey, T* Ez, const T* old, T kk) {
+    const int j = blockIdx.x * blockDim.x + threadIdx.x, k = blockIdx.y;
+    if (j >= g.n[1]) return;
+    const long long P = (long long)g.n[1] * g.n[2], p = (long long)k * g.n[1] + j;
+    const int n = g.n[0];
+    T* F[2] = {Ey, Ez};
+    for (int c = 0; c < 2; ++c) {
+        const T* o = old + (long long)c * 4 * P;
+        const T e0 = o[1 * P + p] + kk * (F[c][g.pidx(1, j, k)] - o[0 * P + p]);
+        const T en = o[2 * P + p] + kk * (F[c][g.pidx(n - 1, j, k)] - o[3 * P + p]);
+        store1_yz(g, F[c], 0, j, k, e0);
+        store1_yz(g, F[c], n, j, k, en);
+    }
+}
+
+// Laser sheet: J_y(plane, j, k) += -2 a exp(-r^2 / w0^2) / dx (a = a(t) from the host).
+__device__ __forceinline__ void j_add(long long* J, long long e, double v, double jinv) { J[e] += __double2ll_rn(v * jinv); }
+__device__ __forceinline__ void j_add(double* J, long long e, double v, double) { J[e] += v; }
+
+template <typename A>
+__global__ void k_laser(Geom g, A* Jy, int plane, double amp, double w0, double yc, double zc, double dx, double dy,
+                        double dz, double jinv) {
+    const int j = blockIdx.x * blockDim.x + threadIdx.x, k = blockIdx.y;
+    if (j >= g.n[1]) return;
+    const double y = (j + 0.5) * dy - yc, z = k * dz - zc;
+    j_add(Jy, g.cidx(plane, j, k), -2.0 * amp * exp(-(y * y + z * z) / (w0 * w0)) / dx, jinv);
+}
+
+template <typename T>
+static pic_status open_before_t(pic_ctx* c) {
+    const Geom& g = c->g;
+    dim3 grid((g.n[1] + 127) / 128, g.n[2]);
+    if (c->laser_on) {
+        const pic_laser_desc& L = c->laser;
+        const double t = (c->step + 0.5) * c->desc.dt, s = t - L.t_peak;
+        const double amp = L.a0 * std::exp(-2.0 * std::log(2.0) * s * s / (L.tau * L.tau)) * std::sin(L.omega * s);
+        const double* d = c->desc.d;
+        LaunchScope ls(c, KC_OTHER);
+        using Acc = typename JTraits<T>::acc_t;
+        k_laser<Acc><<<grid, 128, 0, c->stream>>>(g, static_cast<Acc*>(c->J[1]), L.plane, amp, L.w0, L.yc * d[1],
+                                                   L.zc * d[2], d[0], d[1], d[2], c->jinv);
+        GBPIC_CHECK(c, cudaGetLastError());
+    }
+    LaunchScope ls(c, KC_OTHER);
+    k_mur_save<T><<<grid, 128, 0, c->stream>>>(g, (const T*)c->E[1], (const T*)c->E[2], (T*)c->mur_old);
+    GBPIC_CHECK(c, cudaGetLastError());
+    return PIC_OK;
+}
+
+template <typename T>
+static pic_status open_after_t(pic_ctx* c) {
+    const Geom& g = c->g;
+    dim3 grid((g.n[1] + 127) / 128, g.n[2]);
+    const double kk = (c->desc.dt - c->desc.d[0]) / (c->desc.dt + c->desc.d[0]);
+    LaunchScope ls(c, KC_OTHER);
+    k_mur_apply<T><<<grid, 128, 0, c->stream>>>(g, (T*)c->E[1], (T*)c->E[2], (const T*)c->mur_old, (T)kk);
+    GBPIC_CHECK(c, cudaGetLastError());
+    return PIC_OK;
+}
+
+pic_status launch_open_x_before_ampere(pic_ctx* c) {
+    return c->prec == PIC_FP64 ? open_before_t<double>(c) : open_before_t<float>(c);
+}
+pic_status launch_open_x_after_ampere(pic_ctx* c) {
+    return c->prec == PIC_FP64 ? open_after_t<double>(c) : open_after_t<float>(c);
+}
 
 }  // namespace gbpic

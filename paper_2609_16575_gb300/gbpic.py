@@ -37,7 +37,14 @@ class pic_grid_desc(ctypes.Structure):
                 ("rho_ion", ctypes.c_double), ("precision", ctypes.c_int32), ("device", ctypes.c_int32),
                 ("stream", ctypes.c_void_p), ("track_ids", ctypes.c_int32), ("record_every", ctypes.c_int32),
                 ("history_capacity", ctypes.c_int32), ("sort_every", ctypes.c_int32),
-                ("alloc", ALLOC_FN), ("free", FREE_FN), ("alloc_user", ctypes.c_void_p)]
+                ("alloc", ALLOC_FN), ("free", FREE_FN), ("alloc_user", ctypes.c_void_p),
+                ("bc_x", ctypes.c_int32), ("reserved1", ctypes.c_int32)]
+
+
+class pic_laser_desc(ctypes.Structure):
+    _fields_ = [("a0", ctypes.c_double), ("omega", ctypes.c_double), ("w0", ctypes.c_double), ("tau", ctypes.c_double),
+                ("t_peak", ctypes.c_double), ("plane", ctypes.c_int32), ("reserved", ctypes.c_int32),
+                ("yc", ctypes.c_double), ("zc", ctypes.c_double)]
 
 
 class pic_species_desc(ctypes.Structure):
@@ -51,7 +58,8 @@ class pic_diag(ctypes.Structure):
     _fields_ = [("step", ctypes.c_int64), ("t", ctypes.c_double), ("U_E", ctypes.c_double),
                 ("U_B", ctypes.c_double), ("K_half", ctypes.c_double), ("gauss_max", ctypes.c_double),
                 ("gauss_change_max", ctypes.c_double), ("rho_max", ctypes.c_double), ("cont_max", ctypes.c_double),
-                ("J_max", ctypes.c_double), ("n_alive", ctypes.c_int64), ("n_spilled", ctypes.c_int64)]
+                ("J_max", ctypes.c_double), ("n_alive", ctypes.c_int64), ("n_spilled", ctypes.c_int64),
+                ("n_escaped", ctypes.c_int64)]
 
     def as_dict(self):
         return {k: getattr(self, k) for k, _ in self._fields_}
@@ -92,6 +100,7 @@ def lib():
             L.pic_adjoint_forward.argtypes = [P, ctypes.c_int32, ctypes.c_int32, ctypes.POINTER(ctypes.c_double)]
             L.pic_adjoint_backward.argtypes = [P, P, P, ctypes.POINTER(ctypes.c_double), ctypes.POINTER(ctypes.c_void_p),
                                                ctypes.c_int32]
+            L.pic_set_laser.argtypes = [P, ctypes.POINTER(pic_laser_desc)]
             L.pic_gauss_check_static.argtypes = [P, ctypes.POINTER(ctypes.c_double), ctypes.POINTER(ctypes.c_double)]
             L.pic_launch_count.argtypes = [P]
             L.pic_launch_count.restype = ctypes.c_int64
@@ -104,7 +113,7 @@ def lib():
             for name in ("pic_init_grid", "pic_set_fields", "pic_load_species", "pic_step", "pic_sync",
                          "pic_get_fields", "pic_get_particles", "pic_diagnostics", "pic_get_history",
                          "pic_set_timing", "pic_kernel_times", "pic_adjoint_forward", "pic_adjoint_backward",
-                         "pic_gauss_check_static"):
+                         "pic_gauss_check_static", "pic_set_laser"):
                 getattr(L, name).restype = ctypes.c_int
             _lib = L
     return _lib
@@ -112,7 +121,7 @@ def lib():
 
 EXPORTED = ("pic_init_grid", "pic_set_fields", "pic_load_species", "pic_step", "pic_sync", "pic_get_fields",
             "pic_get_particles", "pic_diagnostics", "pic_get_history", "pic_set_timing", "pic_kernel_times",
-            "pic_adjoint_forward", "pic_adjoint_backward", "pic_gauss_check_static", "pic_launch_count",
+            "pic_adjoint_forward", "pic_adjoint_backward", "pic_gauss_check_static", "pic_set_laser", "pic_launch_count",
             "pic_last_error", "pic_status_string", "pic_destroy")
 
 
@@ -158,7 +167,7 @@ class _TorchAllocator:
 
 
 def pic_init_grid(n, d, dt, precision=PIC_FP32, rho_ion=0.0, device=0, stream=None, track_ids=False,
-                  record_every=0, history_capacity=0, allocator=None, sort_every=0):
+                  record_every=0, history_capacity=0, allocator=None, sort_every=0, bc_x=0):
     """Create a context; returns (ctx pointer, keep-alive tuple)."""
     desc = pic_grid_desc()
     desc.n = (ctypes.c_int32 * 3)(*[int(v) for v in n])
@@ -172,6 +181,7 @@ def pic_init_grid(n, d, dt, precision=PIC_FP32, rho_ion=0.0, device=0, stream=No
     desc.record_every = int(record_every)
     desc.history_capacity = int(history_capacity)
     desc.sort_every = int(sort_every)
+    desc.bc_x = int(bc_x)
     if allocator is not None:
         desc.alloc = allocator.alloc
         desc.free = allocator.free
@@ -185,7 +195,7 @@ class Context:
     and enqueues on torch's current stream of ``device``."""
 
     def __init__(self, n, d, dt, precision=PIC_FP32, rho_ion=0.0, device=0, track_ids=False, record_every=0,
-                 history_capacity=0, use_torch=True, sort_every=0):
+                 history_capacity=0, use_torch=True, sort_every=0, bc_x=0):
         stream = None
         allocator = None
         if use_torch:
@@ -197,10 +207,11 @@ class Context:
             # library enqueues on that same stream instead of creating its own
             stream = s.cuda_stream or 1
             allocator = _TorchAllocator(device, s.cuda_stream)
-        self.n = tuple(int(v) for v in n)
+        self.n = tuple(int(v) for v in n[:3])
+        self.bc_x = int(bc_x)
         self.ncell = self.n[0] * self.n[1] * self.n[2]
-        self.ptr, self._keep = pic_init_grid(n, d, dt, precision, rho_ion, device, stream, track_ids, record_every,
-                                             history_capacity, allocator, sort_every)
+        self.ptr, self._keep = pic_init_grid(self.n, d, dt, precision, rho_ion, device, stream, track_ids,
+                                             record_every, history_capacity, allocator, sort_every, bc_x)
         self.species_n = []
 
     def close(self):
@@ -215,6 +226,11 @@ class Context:
             pass
 
     def set_fields(self, E=None, B=None):
+        """E^0, B^{-1/2}: (3, nz, ny, nx [+ 1 with an open x]) float64 each, or None."""
+        want = 3 * self.n[2] * self.n[1] * (self.n[0] + self.bc_x)
+        for a in (E, B):
+            if a is not None and int(np.prod(a.shape)) != want:
+                raise ValueError(f"field array of {int(np.prod(a.shape))} values, expected {want}")
         pe, de = _ptr(E)
         pb, db = _ptr(B)
         if E is not None and B is not None and de != db:
@@ -257,7 +273,7 @@ class Context:
 
     def get_fields(self):
         """Returns E, B, J as (3, nz, ny, nx) float64 numpy arrays (E^n, B^{n-1/2}, J^{n-1/2})."""
-        shape = (3, self.n[2], self.n[1], self.n[0])
+        shape = (3, self.n[2], self.n[1], self.n[0] + self.bc_x)
         E = np.empty(shape)
         B = np.empty(shape)
         J = np.empty(shape)
@@ -301,6 +317,11 @@ class Context:
 
     def launch_count(self):
         return lib().pic_launch_count(self.ptr)
+
+    def set_laser(self, a0, omega, w0, tau, t_peak, plane, yc, zc):
+        """Laser sheet of an open x (see pic_laser_desc)."""
+        L = pic_laser_desc(a0, omega, w0, tau, t_peak, int(plane), 0, yc, zc)
+        _check(self.ptr, lib().pic_set_laser(self.ptr, ctypes.byref(L)), "pic_set_laser")
 
     def gauss_check_static(self):
         """(gauss_max, rho_max) from the allocation-free entry point."""

@@ -40,6 +40,8 @@ class Workload:
     E: np.ndarray | None = None        # optional initial E (3, nz, ny, nx); None = zero
     B: np.ndarray | None = None        # optional initial B^{-1/2}; None = zero
     steps: int = 1
+    bc_x: int = 0                      # 1: open x (absorbing faces, particles leaving in x removed)
+    laser: object = None               # LaserInput for an open x
 
     @property
     def ncells(self) -> int:
@@ -131,6 +133,51 @@ def stress(n=256, d=0.2, ppc=32, u_th=0.1, seed=1238, courant=0.5, steps=1000) -
     """Precision-stress thermal plasma: 256^3, 32 per cell, u_th = 0.1."""
     wl = thermal((n, n, n), d, ppc, u_th, seed, courant, steps)
     wl.name = "stress"
+    return wl
+
+
+@dataclass
+class LaserInput:
+    a0: float
+    omega: float
+    w0: float
+    tau: float        # intensity FWHM
+    t_peak: float
+    plane: int
+    yc: float         # cell units
+    zc: float
+
+    def as_tuple(self):
+        return (self.a0, self.omega, self.w0, self.tau, self.t_peak, self.plane, self.yc, self.zc)
+
+
+def lwfa(n=(512, 128, 128), ppc_per_dim=2, density=0.01, x0=20, ramp=50, a0=2.0, w0_lambda=8.0, fwhm_periods=10.0,
+         courant=0.5, steps=2000, plane=2) -> Workload:
+    """Laser wakefield in an underdense plasma (units of the laser: omega0 = 1, c = 1,
+    lambda = 2 pi, density in units of the critical density): dx = lambda/20,
+    dy = dz = lambda/8; open x (absorbing faces), periodic y and z; electrons on a
+    regular per_dim^3 lattice where the density is non-zero: zero for x < x0 cells, a
+    linear ramp over `ramp` cells, then `density`; zero momenta; immobile ions.  The
+    linearly polarised (y) Gaussian pulse (a0, waist w0_lambda wavelengths, intensity
+    FWHM fwhm_periods periods) enters through a current sheet on the node plane
+    `plane`, peaking two FWHM after t = 0.  Returns the workload (bc_x = 1) with
+    `.laser` set."""
+    lam = 2 * np.pi
+    dd = (lam / 20, lam / 8, lam / 8)
+    nn = tuple(int(v) for v in n)
+    X, Y, Z = _lattice(nn, ppc_per_dim)
+    prof = np.clip((X - x0) / ramp, 0.0, 1.0) * density
+    keep = prof > 0
+    X, Y, Z, prof = X[keep], Y[keep], Z[keep], prof[keep]
+    ppc = ppc_per_dim ** 3
+    w = prof * dd[0] * dd[1] * dd[2] / ppc
+    npart = X.size
+    P = np.stack([X, Y, Z, np.zeros(npart), np.zeros(npart), np.zeros(npart), w])
+    wl = Workload("lwfa", nn, dd, courant_dt(dd, courant), 0.0,
+                  [SpeciesInput(-1.0, 1.0, P, momenta_at_half_step=True)], steps=steps)
+    tau = fwhm_periods * lam
+    wl.laser = LaserInput(a0, 1.0, w0_lambda * lam, tau, 2.0 * tau, plane, nn[1] / 2.0, nn[2] / 2.0)
+    wl.bc_x = 1
     return wl
 
 

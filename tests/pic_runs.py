@@ -30,7 +30,9 @@ def run_gpu(wl: W.Workload, precision: int, steps: int, track_ids=True, record_e
 
     sp, E, B = prepare(wl, precision)
     ctx = gbpic.Context(wl.n, wl.d, wl.dt, precision=precision, rho_ion=wl.rho_ion, track_ids=track_ids,
-                        record_every=record_every)
+                        record_every=record_every, bc_x=wl.bc_x)
+    if wl.laser is not None:
+        ctx.set_laser(*wl.laser.as_tuple())
     ctx.set_fields(E, B)
     for s in sp:
         ctx.load_species_array(s.q, s.m, s.P, s.momenta_at_half_step, capacity_slack=slack)
@@ -44,9 +46,16 @@ def run_gpu(wl: W.Workload, precision: int, steps: int, track_ids=True, record_e
     return ctx
 
 
+def oracle_n(wl: W.Workload):
+    """Grid description for the oracle: (nx, ny, nz[, open x])."""
+    return tuple(wl.n) + ((1,) if wl.bc_x else ())
+
+
 def run_oracle(wl: W.Workload, precision: int, steps: int, per_step=None):
     sp, E, B = prepare(wl, precision)
-    F = oracle.empty_fields(wl.n)
+    n = oracle_n(wl)
+    laser = None if wl.laser is None else wl.laser.as_tuple()
+    F = oracle.empty_fields(n)
     if E is not None:
         F[0:3] = E
     if B is not None:
@@ -54,15 +63,15 @@ def run_oracle(wl: W.Workload, precision: int, steps: int, per_step=None):
     osp = [oracle.Species(s.q, s.m, s.P.copy()) for s in sp]
     for s, si in zip(osp, sp):
         if not si.momenta_at_half_step:
-            oracle.backpush(wl.n, wl.d, wl.dt, F[0:3], F[3:6], s)
+            oracle.backpush(n, wl.d, wl.dt, F[0:3], F[3:6], s)
     hist = []
     if per_step is None:
         if steps:
-            hist = oracle.run(wl.n, wl.d, wl.dt, F, osp, steps)
+            hist = oracle.run(n, wl.d, wl.dt, F, osp, steps, laser=laser)
     else:
         for k in range(steps):
             per_step(F, osp, k)
-            hist.append(oracle.run(wl.n, wl.d, wl.dt, F, osp, 1)[0])
+            hist.append(oracle.run(n, wl.d, wl.dt, F, osp, 1, step0=k, laser=laser)[0])
         hist = np.array(hist)
     return F, osp, hist
 
