@@ -62,7 +62,7 @@ static pic_status snap_alloc(pic_ctx* c, Snapshot& S) {
     for (size_t i = 0; i < c->species.size(); ++i) {
         SpeciesDev& s = c->species[i];
         SpeciesSnap& z = S.sp[i];
-        if (!(z.part = dev_alloc(c, s.pbytes)) || !(z.counts = dev_alloc(c, sizeof(int) * ntiles(c))) ||
+        if (!(z.part = dev_alloc(c, s.pbytes)) || !(z.counts = dev_alloc(c, 2 * sizeof(int) * ntiles(c))) ||
             !(z.ctr = dev_alloc(c, sizeof(Counters))) || !(z.spill = dev_alloc(c, rec_bytes(c) * s.spill_cap)))
             return PIC_ERR_OOM;
     }
@@ -84,6 +84,8 @@ static pic_status snap_save(pic_ctx* c, Snapshot& S) {
         z.cur = s.cur;
         GBPIC_CHECK(c, cudaMemcpyAsync(z.part, s.base[s.cur], s.pbytes, cudaMemcpyDeviceToDevice, c->stream));
         GBPIC_CHECK(c, cudaMemcpyAsync(z.counts, s.count, sizeof(int) * ntiles(c), cudaMemcpyDeviceToDevice, c->stream));
+        GBPIC_CHECK(c, cudaMemcpyAsync(static_cast<int*>(z.counts) + ntiles(c), s.holes, sizeof(int) * ntiles(c),
+                                       cudaMemcpyDeviceToDevice, c->stream));
         GBPIC_CHECK(c, cudaMemcpyAsync(z.ctr, s.ctr, sizeof(Counters), cudaMemcpyDeviceToDevice, c->stream));
         GBPIC_CHECK(c, cudaMemcpyAsync(z.spill, s.spill, rec_bytes(c) * s.spill_cap, cudaMemcpyDeviceToDevice, c->stream));
     }
@@ -104,6 +106,8 @@ static pic_status snap_restore(pic_ctx* c, const Snapshot& S) {
         s.cur = z.cur;
         GBPIC_CHECK(c, cudaMemcpyAsync(s.base[s.cur], z.part, s.pbytes, cudaMemcpyDeviceToDevice, c->stream));
         GBPIC_CHECK(c, cudaMemcpyAsync(s.count, z.counts, sizeof(int) * ntiles(c), cudaMemcpyDeviceToDevice, c->stream));
+        GBPIC_CHECK(c, cudaMemcpyAsync(s.holes, static_cast<const int*>(z.counts) + ntiles(c), sizeof(int) * ntiles(c),
+                                       cudaMemcpyDeviceToDevice, c->stream));
         GBPIC_CHECK(c, cudaMemcpyAsync(s.ctr, z.ctr, sizeof(Counters), cudaMemcpyDeviceToDevice, c->stream));
         GBPIC_CHECK(c, cudaMemcpyAsync(s.spill, z.spill, rec_bytes(c) * s.spill_cap, cudaMemcpyDeviceToDevice, c->stream));
     }
@@ -322,6 +326,7 @@ __global__ void __launch_bounds__(256) k_adj_particles(AdjArgs<T> A) {
         for (int i = threadIdx.x; i < cnt; i += blockDim.x) {
             const long long p = (long long)A.pa.seg_start[t] + i;
             const int lc = A.pa.cell[p];
+            if (lc < 0) continue;
             const double d1[3] = {(double)A.pa.d[0][p], (double)A.pa.d[1][p], (double)A.pa.d[2][p]};
             const double u0[3] = {(double)A.pa.u[0][p], (double)A.pa.u[1][p], (double)A.pa.u[2][p]};
             adjoint_particle(A, tx * TILE + (lc & 7), ty * TILE + ((lc >> 3) & 7), tz * TILE + (lc >> 6), d1, u0,

@@ -19,9 +19,8 @@ constexpr int TILE_CELLS = 512;
 constexpr int SB = 10;           // staged E/B extent per dim: local cells -1..8
 constexpr int SJ = 11;           // shared J extent per dim: local nodes/edges -1..9
 constexpr int SJ3 = SJ * SJ * SJ;
-constexpr int PUSH_THREADS = 512;
-constexpr int PUSH_WARPS = PUSH_THREADS / 32;
-constexpr int GROUP_ROUNDS = 3;   // warp reduce-scatter rounds per chunk before the sparse path
+constexpr int PUSH_WARPS_MAX = 16;   // the tile kernel's CTA has at most 512 threads
+constexpr int HOLE = -1;             // cell value of a slot a particle has left (until the next re-sort)
 
 // device error bits, OR-ed into Counters::err
 enum : int { ERRB_OVERFLOW = 1, ERRB_SUPERLUMINAL = 2, ERRB_NAN = 4, ERRB_TIMEOUT = 8 };
@@ -31,14 +30,16 @@ constexpr int MBAR_MAX_POLLS = 1 << 24;
 
 template <typename T> struct Prec;
 template <> struct Prec<float> {
-    static constexpr int THREADS = 512;   // tile kernel CTA (2 CTAs per SM at 64 registers)
+    static constexpr int THREADS = 256;   // tile kernel CTA
     static constexpr int MINB = 2;
+    static constexpr int R = 4;        // consecutive particle slots per lane (one 16-byte load per array)
     static constexpr int BX = 12;      // TMA box inner extent: 12 floats = 48 B (multiple of 16 B)
     static constexpr int JBITS = 40;   // fixed-point fraction bits of a bounded J contribution
 };
 template <> struct Prec<double> {
-    static constexpr int THREADS = 256;   // FP64 needs ~130 registers per thread
+    static constexpr int THREADS = 256;
     static constexpr int MINB = 1;
+    static constexpr int R = 2;
     static constexpr int BX = 10;      // 10 doubles = 80 B
     static constexpr int JBITS = 50;
 };
@@ -107,8 +108,9 @@ template <typename T> struct ParticleArrays {
     T* w;
     int* id;        // optional load-order id
     const int* seg_start;
-    int* count;
+    int* count;     // slots in use: the particles and the holes (cell == HOLE) among them
     const int* cap;
+    int* holes;     // holes among the first count slots (cleared by the re-sort)
 };
 
 // ---------------------------------------------------------------------------
@@ -185,64 +187,13 @@ __device__ __forceinline__ void acc_atomic(long long* p, long long v) {
 }
 __device__ __forceinline__ void acc_atomic(double* p, double v) { atomicAdd(p, v); }
 
-// Shared-memory J tile accumulators.  FP32 path: each 64-bit fixed-point element is a
-// pair of 32-bit words (lo, hi) updated with native 32-bit shared atomics and an
-// explicit carry (exact modulo 2^64, so the final pair is the exact sum).  FP64 path:
-// FP64 shared atomics.  Element e of the lo words sits at byte 4e, of the hi words at
-// byte 4(NE + e), of the FP64 tile at byte 8e.
-__device__ __forceinline__ void jtile_add(uint32_t base, int e, long long v, int NE) {
-    const unsigned l = static_cast<unsigned>(v);
-    unsigned hh = static_cast<unsigned>(static_cast<unsigned long long>(v) >> 32);
-    unsigned old;
-    asm volatile("atom.shared.add.u32 %0, [%1], %2;" : "=r"(old) : "r"(base + 4u * e), "r"(l) : "memory");
-    hh += (old + l < old) ? 1u : 0u;
-    if (hh) asm volatile("red.shared.add.u32 [%0], %1;" ::"r"(base + 4u * (NE + e)), "r"(hh) : "memory");
+// Shared-memory J tile of the tile kernel: FP32 elements on the FP32 path, FP64 on the
+// FP64 path, added to with native shared-memory float reductions (byte address).
+__device__ __forceinline__ void tile_red(uint32_t addr, float v) {
+    asm volatile("red.shared.add.f32 [%0], %1;" ::"r"(addr), "f"(v) : "memory");
 }
-__device__ __forceinline__ void jtile_add(uint32_t base, int e, double v, int) {
-    double old;
-    asm volatile("atom.shared.add.f64 %0, [%1], %2;" : "=d"(old) : "r"(base + 8u * e), "d"(v) : "memory");
-    (void)old;
-}
-__device__ __forceinline__ long long jtile_get(const unsigned char* s, int e, int NE, long long) {
-    const unsigned* w = reinterpret_cast<const unsigned*>(s);
-    return static_cast<long long>((static_cast<unsigned long long>(w[NE + e]) << 32) | w[e]);
-}
-__device__ __forceinline__ double jtile_get(const unsigned char* s, int e, int, double) {
-    return reinterpret_cast<const double*>(s)[e];
-}
-
-// Warp reduce-scatter of 16 slots: on return lane l holds the warp sum of slot
-// l >> 1 (lanes l and l^1 hold the same slot).  16 shuffles instead of 5 x 16.
-template <typename A>
-__device__ __forceinline__ A reduce_scatter16(A v[16], int lane) {
-#pragma unroll
-    for (int j = 0; j < 8; ++j) {
-        const bool up = lane & 16;
-        const A send = up ? v[j] : v[8 + j];
-        const A keep = up ? v[8 + j] : v[j];
-        v[j] = keep + __shfl_xor_sync(0xffffffffu, send, 16);
-    }
-#pragma unroll
-    for (int j = 0; j < 4; ++j) {
-        const bool up = lane & 8;
-        const A send = up ? v[j] : v[4 + j];
-        const A keep = up ? v[4 + j] : v[j];
-        v[j] = keep + __shfl_xor_sync(0xffffffffu, send, 8);
-    }
-#pragma unroll
-    for (int j = 0; j < 2; ++j) {
-        const bool up = lane & 4;
-        const A send = up ? v[j] : v[2 + j];
-        const A keep = up ? v[2 + j] : v[j];
-        v[j] = keep + __shfl_xor_sync(0xffffffffu, send, 4);
-    }
-    {
-        const bool up = lane & 2;
-        const A send = up ? v[0] : v[1];
-        const A keep = up ? v[1] : v[0];
-        v[0] = keep + __shfl_xor_sync(0xffffffffu, send, 2);
-    }
-    return v[0] + __shfl_xor_sync(0xffffffffu, v[0], 1);
+__device__ __forceinline__ void tile_red(uint32_t addr, double v) {
+    asm volatile("red.shared.add.f64 [%0], %1;" ::"r"(addr), "d"(v) : "memory");
 }
 
 // 2 / x: the FP32 path uses the fast approximate division (error ~2 ulp, far inside
@@ -404,14 +355,6 @@ __device__ __forceinline__ void scatter12(AddFn Add, int x, int y, int z, const 
     }
 }
 
-// Local cell coordinates in -1..8 packed as (x+1) | (y+1) << 4 | (z+1) << 8.
-__device__ __forceinline__ int pack_cell(int x, int y, int z) { return (x + 1) | ((y + 1) << 4) | ((z + 1) << 8); }
-__device__ __forceinline__ void unpack_cell(int k, int& x, int& y, int& z) {
-    x = (k & 15) - 1;
-    y = ((k >> 4) & 15) - 1;
-    z = ((k >> 8) & 15) - 1;
-}
-
 // Edge (component, local x, y, z) of slot s (0..11) of the cell (x, y, z), in the
 // order of segment_values.
 __device__ __forceinline__ void slot_edge(int s, int x, int y, int z, int& comp, int& ex, int& ey, int& ez) {
@@ -519,6 +462,7 @@ struct SpeciesDev {
     int* seg_start = nullptr;
     int* count = nullptr;
     int* cap = nullptr;
+    int* holes = nullptr;
     void* movers = nullptr;
     int mover_cap = 0;
     void* spill = nullptr;

@@ -2,8 +2,8 @@
 //   k_tile_push   one CTA per 8^3-cell tile: TMA-stages E, B of the tile and its
 //                 guard cells into shared memory, gathers, Boris-pushes, moves and
 //                 zigzag-deposits every particle of the tile into a shared fixed-point
-//                 J tile, compacts the stayers in place, writes movers to a list and
-//                 flushes J to HBM with integer atomics.
+//                 J tile, updates the stayers in their slots, writes movers to a list
+//                 (leaving holes) and flushes J to HBM with integer atomics.
 //   k_list_push   the same step for particles held in the spill list (global-memory
 //                 gather and deposit).
 //   k_append      puts movers into the segment of their new tile (or the spill list).
@@ -35,16 +35,19 @@ template <typename T> __host__ __device__ constexpr int box_stride() {
     // each staged box starts on a 128-byte boundary
     return ((box_elems<T>() * (int)sizeof(T) + 127) / 128) * 128 / (int)sizeof(T);
 }
-constexpr int JT_ELEMS = 3 * SJ3;   // elements of the shared J tile
+constexpr int JT_ELEMS = 3 * SJ3;   // elements of the shared J tile (working precision)
+constexpr int QCAP_ = 64;   // record queue per warp (QCAP below)
 template <typename T> constexpr size_t tile_smem_bytes() {
-    // staged E, B boxes + J tile (8 bytes per element either way) + mbarrier; + 128: the
-    // kernel rounds the dynamic shared base up to a 128-byte boundary (TMA destination)
-    return (size_t)6 * box_stride<T>() * sizeof(T) + (size_t)JT_ELEMS * 8 + 16 + 128;
+    // staged E, B boxes + J tile (working precision) + record queues +
+    // mbarrier; + 128: the kernel rounds the dynamic shared base up to a 128-byte
+    // boundary (TMA destination)
+    return (size_t)6 * box_stride<T>() * sizeof(T) + ((size_t)JT_ELEMS * sizeof(T) + 15) / 16 * 16 +
+           (size_t)(Prec<T>::THREADS / 32) * QCAP_ * 13 * sizeof(T) + 16 + 128;
 }
 
 __device__ __forceinline__ void block_add_double(double v, double* dst) {
     for (int o = 16; o > 0; o >>= 1) v += __shfl_xor_sync(0xffffffffu, v, o);
-    __shared__ double red[PUSH_WARPS];
+    __shared__ double red[PUSH_WARPS_MAX];
     int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
     if (lane == 0) red[warp] = v;
     __syncthreads();
@@ -67,38 +70,124 @@ __device__ __forceinline__ int warp_reserve(int* counter, bool want) {
     return want ? base + __popc(m & ((1u << lane) - 1)) : -1;
 }
 
-// Deposit of the 12 edge values R of the cells with packed keys K for the lanes in
-// mask M, two records per pass: lanes 0..11 take the 12 values of the first record,
-// lanes 12..23 those of the second.  Used for the few records the group reduction
-// leaves (cell crossers' second segment, singleton cells), so that no lane executes
-// 12 atomics on its own while the rest of its warp idles.
-template <typename T, typename AddFn>
-__device__ __forceinline__ void sparse_deposit(unsigned M, const T R[12], int K, int lane, AddFn add) {
-    const int rec = lane < 12 ? 0 : (lane < 24 ? 1 : 2);
-    const int q = lane - 12 * rec;
-    while (M) {
-        const int r0 = __ffs(M) - 1;
-        M &= M - 1;
-        const int r1 = M ? __ffs(M) - 1 : -1;
-        if (r1 >= 0) M &= M - 1;
-        const int src = rec == 0 ? r0 : (rec == 1 ? r1 : -1);
-        const int sl = src < 0 ? 0 : src;
-        T val = T(0);
-#pragma unroll
-        for (int k = 0; k < 12; ++k) {
-            const T t = __shfl_sync(0xffffffffu, R[k], sl);
-            val = (k == q) ? t : val;
-        }
-        const int key = __shfl_sync(0xffffffffu, K, sl);
-        if (src >= 0) {
-            int cx, cy, cz, comp, ex, ey, ez;
-            unpack_cell(key, cx, cy, cz);
-            slot_edge(q, cx, cy, cz, comp, ex, ey, ez);
-            add(comp, ex, ey, ez, to_acc(val));
-        }
-    }
+// Index of the shared J tile element of (component, local x, y, z), -1..9 each.
+__device__ __forceinline__ int tile_index(int comp, int x, int y, int z) {
+    return comp * SJ3 + ((z + 1) * SJ + (y + 1)) * SJ + (x + 1);
+}
+// Offset of slot q (0..11, the order of segment_values) from the index of its cell's
+// (component 0) origin edge.
+__device__ __forceinline__ int slot_offset(int q) {
+    int comp, ex, ey, ez;
+    slot_edge(q, 0, 0, 0, comp, ex, ey, ez);
+    return tile_index(comp, ex, ey, ez) - tile_index(0, 0, 0, 0);
 }
 
+// Warp-private record queue in shared memory for the few deposits that do not fit the
+// per-lane sums (a particle starting outside its lane's cell, a cell crosser's second
+// segment).  Queuing them and adding them later with 24 lanes (one record value per
+// lane, two records per pass) keeps the warp converged instead of letting one lane
+// run 12 atomics while the others idle.  Records are 13 words: 12 values, then the
+// tile index of the cell's origin edge; a stride coprime to the 32 banks keeps the
+// push and the drain free of bank conflicts.
+constexpr int QCAP = QCAP_;   // records per warp: a particle step adds at most 64 (the queue is
+                              // drained after every step that added some), a flush stages 32
+template <typename T> struct WarpQueue {
+    T* rec;      // [QCAP][13]
+    __device__ __forceinline__ int& key(int j) const { return *reinterpret_cast<int*>(rec + j * 13 + 12); }
+};
+
+// Append the 12 values v of the cell with origin index k for every lane with `want`
+// (warp-collective).
+template <typename T>
+__device__ __forceinline__ void q_push(WarpQueue<T> Q, int& qn, bool want, int k, const T v[12], int lane) {
+    const unsigned m = __ballot_sync(0xffffffffu, want);
+    if (!m) return;
+    if (want) {
+        const int slot = qn + __popc(m & ((1u << lane) - 1u));
+        Q.key(slot) = k;
+#pragma unroll
+        for (int q = 0; q < 12; ++q) Q.rec[slot * 13 + q] = v[q];
+    }
+    qn += __popc(m);
+}
+
+// Add every queued record to the shared J tile: lane 12h + q (h = 0, 1) adds value q of
+// records 2j + h; sJa is the tile's byte address, qoff this lane's slot offset.
+template <typename T>
+__device__ __forceinline__ void q_drain(WarpQueue<T> Q, int& qn, int lane, uint32_t sJa, int qoff) {
+    __syncwarp();
+    if (lane < 24) {
+        const int h = lane >= 12 ? 1 : 0, q = lane - 12 * h;
+        for (int j = h; j < qn; j += 2) tile_red(sJa + (uint32_t)sizeof(T) * (Q.key(j) + qoff), Q.rec[j * 13 + q]);
+    }
+    __syncwarp();
+    qn = 0;
+}
+
+// Warp flush of per-lane current sums acc (12 edge values of the cell with origin
+// index key, or none for key < 0) into the shared J tile.  The 32 sums are staged in
+// the (empty) record queue; then lane 12h + q walks records 16h .. 16h + 15 of value q
+// and adds one sum per run of equal keys.  The segments being sorted by cell, the keys
+// of a warp form a few runs, so a flush costs a few atomics per value instead of 32
+// (shared atomics from many lanes on one address serialise).
+template <typename T>
+__device__ __forceinline__ void flush_warp(const T acc[12], int key, int lane, WarpQueue<T> Q, uint32_t sJa, int qoff) {
+#pragma unroll
+    for (int q = 0; q < 12; ++q) Q.rec[lane * 13 + q] = acc[q];
+    Q.key(lane) = key;
+    __syncwarp();
+    if (lane < 24) {
+        const int h = lane >= 12 ? 1 : 0, q = lane - 12 * h;
+        int ck = -1;
+        T sum = T(0);
+#pragma unroll 4
+        for (int j = 16 * h; j < 16 * h + 16; ++j) {
+            const int k = Q.key(j);
+            const T v = Q.rec[j * 13 + q];
+            if (k != ck) {
+                if (ck >= 0 && sum != T(0)) tile_red(sJa + (uint32_t)sizeof(T) * (ck + qoff), sum);
+                ck = k;
+                sum = v;
+            } else {
+                sum += v;
+            }
+        }
+        if (ck >= 0 && sum != T(0)) tile_red(sJa + (uint32_t)sizeof(T) * (ck + qoff), sum);
+    }
+    __syncwarp();
+}
+
+// Cells of a lane's R slots (one 16- or 8-byte load) and the start cell its current
+// sums are kept for: the cell most of the R particles start in (a particle that moved
+// since the last re-sort, or a cell boundary inside the group, then costs one queued
+// record instead of R - 1).
+template <int R> struct RowCells;
+template <> struct RowCells<4> {
+    static __device__ __forceinline__ void ld(const int* p, int c[4]) {
+        const int4 a = __ldg(reinterpret_cast<const int4*>(p));
+        c[0] = a.x; c[1] = a.y; c[2] = a.z; c[3] = a.w;
+    }
+    static __device__ __forceinline__ int key(const int c[4]) {
+        int k = c[2] == c[3] ? c[2] : c[1];
+        if (k < 0) k = c[0] >= 0 ? c[0] : (c[1] >= 0 ? c[1] : (c[2] >= 0 ? c[2] : c[3]));
+        return k;
+    }
+};
+template <> struct RowCells<2> {
+    static __device__ __forceinline__ void ld(const int* p, int c[2]) {
+        const int2 a = __ldg(reinterpret_cast<const int2*>(p));
+        c[0] = a.x; c[1] = a.y;
+    }
+    static __device__ __forceinline__ int key(const int c[2]) { return c[0] >= 0 ? c[0] : c[1]; }
+};
+
+// One CTA per tile.  Lane l of warp w handles the R consecutive slots of slot group
+// 32 row + l for rows w, w + warps, ...: particles stay in their slots (a particle that
+// leaves the tile leaves a hole, which the periodic re-sort removes), so warps need no
+// block-wide step.  Because the segments are kept sorted by cell, a lane's R particles
+// nearly always start in one cell: their straight-segment currents are summed in
+// registers and each row ends with one warp flush of those sums; everything else goes
+// through the warp's record queue.
 template <typename T, bool IDS, bool RECK>
 __global__ void __launch_bounds__(Prec<T>::THREADS, Prec<T>::MINB)
 k_tile_push(const __grid_constant__ CUtensorMap tE0, const __grid_constant__ CUtensorMap tE1,
@@ -107,14 +196,15 @@ k_tile_push(const __grid_constant__ CUtensorMap tE0, const __grid_constant__ CUt
     extern __shared__ __align__(128) unsigned char smem_raw[];
     unsigned char* smem = reinterpret_cast<unsigned char*>((reinterpret_cast<uintptr_t>(smem_raw) + 127) & ~uintptr_t(127));
     using Acc = typename JTraits<T>::acc_t;
-    constexpr int NT = Prec<T>::THREADS, NW = NT / 32;
+    constexpr int NT = Prec<T>::THREADS, NW = NT / 32, R = Prec<T>::R;
     constexpr int BX = Prec<T>::BX;
     constexpr int BS = box_stride<T>();
+    static_assert(NW <= PUSH_WARPS_MAX, "tile kernel CTA too large");
     T* sF = reinterpret_cast<T*>(smem);
     unsigned char* sJ = smem + (size_t)6 * BS * sizeof(T);
     const uint32_t sJa = smem_u32(sJ);
-    uint64_t* bar = reinterpret_cast<uint64_t*>(sJ + (size_t)JT_ELEMS * 8);
-    __shared__ int s_wtot[2][PUSH_WARPS];
+    unsigned char* sQ = sJ + ((size_t)JT_ELEMS * sizeof(T) + 15) / 16 * 16;
+    uint64_t* bar = reinterpret_cast<uint64_t*>(sQ + (size_t)NW * QCAP * 13 * sizeof(T));
     __shared__ int s_timeout;
 
     const int tile = blockIdx.x;
@@ -141,27 +231,9 @@ k_tile_push(const __grid_constant__ CUtensorMap tE0, const __grid_constant__ CUt
         tma_load_3d(sF + 5 * BS, &tB2, ox, oy, oz, bar);
     }
     {
-        unsigned long long* z = reinterpret_cast<unsigned long long*>(sJ);
-        for (int i = threadIdx.x; i < JT_ELEMS; i += NT) z[i] = 0ull;
+        T* z = reinterpret_cast<T*>(sJ);
+        for (int i = threadIdx.x; i < JT_ELEMS; i += NT) z[i] = T(0);
     }
-    // first chunk of particles, loaded while the TMA copies fly
-    const int seg = A.pa.seg_start[tile];
-    int n_lc = 0, n_id = 0;
-    T n_d[3] = {T(0), T(0), T(0)}, n_u[3] = {T(0), T(0), T(0)}, n_w = T(0);
-    auto load = [&](int i) {
-        if (i < cnt) {
-            const long long p = (long long)seg + i;
-            n_lc = __ldcs(A.pa.cell + p);
-#pragma unroll
-            for (int k = 0; k < 3; ++k) {
-                n_d[k] = __ldcs(A.pa.d[k] + p);
-                n_u[k] = __ldcs(A.pa.u[k] + p);
-            }
-            n_w = __ldcs(A.pa.w + p);
-            if (IDS) n_id = __ldcs(A.pa.id + p);
-        }
-    };
-    load(threadIdx.x);
     {
         int polls = 0;
         while (!mbar_try_wait(bar, 0)) {
@@ -187,179 +259,167 @@ k_tile_push(const __grid_constant__ CUtensorMap tE0, const __grid_constant__ CUt
     auto fetch = [&](int comp, int x, int y, int z) -> T {
         return sF[comp * BS + ((z + 1) * SB + (y + 1)) * BX + (x + 1)];
     };
-    auto add = [&](int comp, int x, int y, int z, Acc v) {
-        if (v != Acc(0)) jtile_add(sJa, comp * SJ3 + ((z + 1) * SJ + (y + 1)) * SJ + (x + 1), v, JT_ELEMS);
-    };
 
     const int ext[3] = {min(TILE, A.g.n[0] - ox), min(TILE, A.g.n[1] - oy), min(TILE, A.g.n[2] - oz)};
     const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
-    int written = 0;
+    WarpQueue<T> Q;
+    Q.rec = reinterpret_cast<T*>(sQ) + (size_t)warp * 13 * QCAP;
+    const int qoff = slot_offset(lane < 12 ? lane : (lane < 24 ? lane - 12 : 0));
+    int qn = 0;                   // queued records (warp-uniform)
+    const long long seg = A.pa.seg_start[tile];
+    const int ngroups = (cnt + R - 1) / R;
     double kacc = 0.0;
-
-    for (int base = 0, it = 0; base < cnt; base += NT, ++it) {
-        const int i = base + threadIdx.x;
-        const bool active = i < cnt;
-        int lc = n_lc, pid = n_id;
-        T d1[3] = {n_d[0], n_d[1], n_d[2]}, u[3] = {n_u[0], n_u[1], n_u[2]}, w = n_w;
-        load(i + NT);   // next chunk: positions the compaction below cannot reach
-        bool stay = false, move = false, crossed = false;
-        T d2[3] = {T(0), T(0), T(0)}, v[12], v2[12];
-        int s[3] = {0, 0, 0};
-        int x = 0, y = 0, z = 0;
-#pragma unroll
-        for (int q = 0; q < 12; ++q) {
-            v[q] = T(0);
-            v2[q] = T(0);
-        }
-        if (active) {
-            x = lc & 7;
-            y = (lc >> 3) & 7;
-            z = lc >> 6;
-            T Ep[3], Bp[3];
-            gather_eb<T>(fetch, x, y, z, d1[0], d1[1], d1[2], Ep, Bp);
-            T gm1_old = T(0);
-            if (RECK) gm1_old = gamma_minus_one(u);
-            const T ig = boris(A.eps, Ep, Bp, u);
-            if (!(ig > T(0))) atomicOr(&A.ctr->err, ERRB_NAN);
-            if (RECK) kacc += (double)w * A.mass * 0.5 * ((double)gm1_old + (double)gamma_minus_one(u));
+    int left = 0;                 // particles this lane moved out of the tile or removed
+    // the next particle's state, loaded one particle step ahead (L1-cached loads: the
+    // R slots of a lane share a 32-byte sector)
+    int n_lc = HOLE;
+    T n_d[3], n_u[3], n_w;
+    auto prefetch = [&](int i) {
+        n_lc = i < cnt ? __ldg(A.pa.cell + seg + i) : HOLE;
+        if (n_lc >= 0) {
 #pragma unroll
             for (int k = 0; k < 3; ++k) {
-                s[k] = advance(d1[k], A.dtd[k] * u[k] * ig, d2[k]);
-                if (s[k] > 1 || s[k] < -1) {
-                    atomicOr(&A.ctr->err, ERRB_SUPERLUMINAL);
-                    s[k] = s[k] > 0 ? 1 : -1;
-                }
+                n_d[k] = __ldg(A.pa.d[k] + seg + i);
+                n_u[k] = __ldg(A.pa.u[k] + seg + i);
             }
-            const T cw[3] = {A.cq[0] * w, A.cq[1] * w, A.cq[2] * w};
-            crossed = (s[0] | s[1] | s[2]) != 0;
-            if (!crossed) {
-                // both zigzag segments lie in the start cell: their two midpoint products
-                // and D_p D_r / 48 terms add up to one straight segment x1 -> x2 with
-                // midpoint weights and the D_p D_r / 12 term
-                T D[3], Wm[3];
+            n_w = __ldg(A.pa.w + seg + i);
+        }
+    };
+    prefetch((warp * 32 + lane) * R);
+    int n_cells[R];               // the cells of the next row's R slots (for its key)
+    auto prefetch_cells = [&](int i0) {
+        if (i0 < cnt) RowCells<R>::ld(A.pa.cell + seg + i0, n_cells);
+#pragma unroll
+        for (int r = 0; r < R; ++r)
+            if (i0 + r >= cnt) n_cells[r] = HOLE;
+    };
+    prefetch_cells((warp * 32 + lane) * R);
+
+    for (int row = warp; row * 32 < ngroups; row += NW) {
+        T acc[12];                // summed straight-segment currents of start cell `key`
+        int key = RowCells<R>::key(n_cells);
+#pragma unroll
+        for (int q = 0; q < 12; ++q) acc[q] = T(0);
+        const int s0 = (row * 32 + lane) * R;   // first slot of this lane
+        prefetch_cells(((row + NW) * 32 + lane) * R);
+#pragma unroll 1
+        for (int r = 0; r < R; ++r) {
+            const int i = s0 + r;
+            const long long p = seg + i;
+            const int lc = n_lc;
+            const bool active = lc >= 0;
+            T u[3] = {n_u[0], n_u[1], n_u[2]}, d2[3] = {T(0), T(0), T(0)}, w = n_w;
+            const T d1[3] = {n_d[0], n_d[1], n_d[2]};
+            prefetch(r + 1 < R ? i + 1 : ((row + NW) * 32 + lane) * R);
+            T v[12], v2[12];
+            int s[3] = {0, 0, 0};
+            int x = 0, y = 0, z = 0;
+            bool stay = false, move = false, crossed = false;
+            if (active) {
+                x = lc & 7;
+                y = (lc >> 3) & 7;
+                z = lc >> 6;
+                T Ep[3], Bp[3];
+                gather_eb<T>(fetch, x, y, z, d1[0], d1[1], d1[2], Ep, Bp);
+                T gm1_old = T(0);
+                if (RECK) gm1_old = gamma_minus_one(u);
+                const T ig = boris(A.eps, Ep, Bp, u);
+                if (!(ig > T(0))) atomicOr(&A.ctr->err, ERRB_NAN);
+                if (RECK) kacc += (double)w * A.mass * 0.5 * ((double)gm1_old + (double)gamma_minus_one(u));
 #pragma unroll
                 for (int k = 0; k < 3; ++k) {
-                    D[k] = d2[k] - d1[k];
-                    Wm[k] = d1[k] + T(0.5) * D[k];
+                    s[k] = advance(d1[k], A.dtd[k] * u[k] * ig, d2[k]);
+                    if (s[k] > 1 || s[k] < -1) {
+                        atomicOr(&A.ctr->err, ERRB_SUPERLUMINAL);
+                        s[k] = s[k] > 0 ? 1 : -1;
+                    }
                 }
-                segment_values(cw, D, Wm, v);
-            } else {
-                T F1[3], F2[3], W1[3], W2[3];
+                const T cw[3] = {A.cq[0] * w, A.cq[1] * w, A.cq[2] * w};
+                crossed = (s[0] | s[1] | s[2]) != 0;
+                if (!crossed) {
+                    // both zigzag segments lie in the start cell: their two midpoint
+                    // products and D_p D_r / 48 terms add up to one straight segment
+                    // x1 -> x2 with midpoint weights and the D_p D_r / 12 term
+                    T D[3], Wm[3];
 #pragma unroll
-                for (int k = 0; k < 3; ++k) relay(d1[k], d2[k], s[k], F1[k], F2[k], W1[k], W2[k]);
-                segment_values(cw, F1, W1, v);
-                segment_values(cw, F2, W2, v2);
-            }
-        }
-        // Deposit.  The start-cell values v are reduced per group of lanes sharing a
-        // cell (largest groups first, one warp reduce-scatter and 12 atomics each);
-        // what remains, and the crossers' second segment v2, take the sparse path.
-        {
-            const int key = active ? lc : -1 - lane;
-            const unsigned grp = __match_any_sync(0xffffffffu, key);
-            unsigned pend = __ballot_sync(0xffffffffu, active);
-#pragma unroll 1
-            for (int round = 0; round < GROUP_ROUNDS && pend; ++round) {
-                const unsigned mine = (pend >> lane) & 1u ? grp & pend : 0u;
-                const unsigned sz = __popc(mine);
-                const unsigned best = __reduce_max_sync(0xffffffffu, sz);
-                if (best < 3) break;   // a reduction round costs about three sparse records
-                const bool lead = sz == best && (__ffs(mine) - 1) == lane;
-                const int ml = __ffs(__ballot_sync(0xffffffffu, lead)) - 1;
-                const unsigned mg = __shfl_sync(0xffffffffu, mine, ml);
-                const int mlc = __shfl_sync(0xffffffffu, lc, ml);
-                const bool in = (mg >> lane) & 1u;
-                T b[16];
+                    for (int k = 0; k < 3; ++k) {
+                        D[k] = d2[k] - d1[k];
+                        Wm[k] = d1[k] + T(0.5) * D[k];
+                    }
+                    segment_values(cw, D, Wm, v);
+                } else {
+                    T F1[3], F2[3], W1[3], W2[3];
 #pragma unroll
-                for (int q = 0; q < 12; ++q) b[q] = in ? v[q] : T(0);
-#pragma unroll
-                for (int q = 12; q < 16; ++q) b[q] = T(0);
-                const T r = reduce_scatter16(b, lane);
-                const int slot = lane >> 1;
-                if (!(lane & 1) && slot < 12) {
-                    int comp, ex, ey, ez;
-                    slot_edge(slot, mlc & 7, (mlc >> 3) & 7, mlc >> 6, comp, ex, ey, ez);
-                    add(comp, ex, ey, ez, to_acc(r));
+                    for (int k = 0; k < 3; ++k) relay(d1[k], d2[k], s[k], F1[k], F2[k], W1[k], W2[k]);
+                    segment_values(cw, F1, W1, v);
+                    segment_values(cw, F2, W2, v2);
                 }
-                pend &= ~mg;
-            }
-            sparse_deposit<T>(pend, v, pack_cell(x, y, z), lane, add);
-            sparse_deposit<T>(__ballot_sync(0xffffffffu, crossed), v2, pack_cell(x + s[0], y + s[1], z + s[2]), lane,
-                              add);
-        }
-        if (active) {
-            const int nx = x + s[0], ny = y + s[1], nz = z + s[2];
-            stay = nx >= 0 && nx < ext[0] && ny >= 0 && ny < ext[1] && nz >= 0 && nz < ext[2];
-            move = !stay;
-            if (stay) lc = nx | (ny << 3) | (nz << 6);
-        }
-        // movers: to the global list with their wrapped global cell; a particle that
-        // left an open x face is removed instead
-        int gxm = 0;
-        if (move) {
-            gxm = x_after(A.g, ox + x + s[0]);
-            if (gxm < 0) move = false;
-        }
-        if (__ballot_sync(0xffffffffu, active && !stay && !move)) {
-            const unsigned gone = __ballot_sync(0xffffffffu, active && !stay && !move);
-            if (lane == __ffs(gone) - 1) atomicAdd(&A.ctr->escaped, __popc(gone));
-        }
-        const int slot = warp_reserve(&A.ctr->mover_count[A.parity], move);
-        if (move) {
-            if (slot < A.mover_cap) {
-                Rec<T> r;
-                const int gx = gxm;
-                const int gy = wrap_idx(oy + y + s[1], A.g.n[1]);
-                const int gz = wrap_idx(oz + z + s[2], A.g.n[2]);
-                r.cell = (gz * A.g.n[1] + gy) * A.g.n[0] + gx;
-                r.id = pid;
-                r.d[0] = d2[0];
-                r.d[1] = d2[1];
-                r.d[2] = d2[2];
-                r.u[0] = u[0];
-                r.u[1] = u[1];
-                r.u[2] = u[2];
-                r.w = w;
-                A.movers[slot] = r;
-            } else {
-                atomicOr(&A.ctr->err, ERRB_OVERFLOW);
-            }
-        }
-        // in-place, order-preserving compaction of the stayers
-        const unsigned bal = __ballot_sync(0xffffffffu, stay);
-        const int buf = it & 1;
-        if (lane == 0) s_wtot[buf][warp] = __popc(bal);
-        __syncthreads();
-        // prefix of the per-warp stayer counts: one load per lane and a shuffle scan
-        int incl = lane < NW ? s_wtot[buf][lane] : 0;
+                const int nx = x + s[0], ny = y + s[1], nz = z + s[2];
+                stay = nx >= 0 && nx < ext[0] && ny >= 0 && ny < ext[1] && nz >= 0 && nz < ext[2];
+                move = !stay;
+                // in place: the stayer's new state, or a hole
+                __stcs(A.pa.cell + p, stay ? (nx | (ny << 3) | (nz << 6)) : HOLE);
+                if (stay) {
 #pragma unroll
-        for (int o = 1; o < NW; o <<= 1) {
-            const int y = __shfl_up_sync(0xffffffffu, incl, o);
-            if (lane >= o) incl += y;
+                    for (int k = 0; k < 3; ++k) {
+                        __stcs(A.pa.d[k] + p, d2[k]);
+                        __stcs(A.pa.u[k] + p, u[k]);
+                    }
+                } else {
+                    ++left;
+                }
+            }
+            const bool summed = active && lc == key;
+            if (summed) {
+#pragma unroll
+                for (int q = 0; q < 12; ++q) acc[q] += v[q];
+            }
+            q_push(Q, qn, active && !summed, tile_index(0, x, y, z), v, lane);
+            q_push(Q, qn, crossed, tile_index(0, x + s[0], y + s[1], z + s[2]), v2, lane);
+            if (qn) q_drain(Q, qn, lane, sJa, qoff);
+            // movers: to the global list with their wrapped global cell; a particle that
+            // left an open x face is removed instead
+            int gxm = 0;
+            if (move) {
+                gxm = x_after(A.g, ox + x + s[0]);
+                if (gxm < 0) move = false;
+            }
+            {
+                const unsigned gone = __ballot_sync(0xffffffffu, active && !stay && !move);
+                if (gone && lane == __ffs(gone) - 1) atomicAdd(&A.ctr->escaped, __popc(gone));
+            }
+            const int slot = warp_reserve(&A.ctr->mover_count[A.parity], move);
+            if (move) {
+                if (slot < A.mover_cap) {
+                    Rec<T> rc;
+                    const int gy = wrap_idx(oy + y + s[1], A.g.n[1]);
+                    const int gz = wrap_idx(oz + z + s[2], A.g.n[2]);
+                    rc.cell = (gz * A.g.n[1] + gy) * A.g.n[0] + gxm;
+                    rc.id = IDS ? A.pa.id[p] : 0;
+                    rc.d[0] = d2[0];
+                    rc.d[1] = d2[1];
+                    rc.d[2] = d2[2];
+                    rc.u[0] = u[0];
+                    rc.u[1] = u[1];
+                    rc.u[2] = u[2];
+                    rc.w = w;
+                    A.movers[slot] = rc;
+                } else {
+                    atomicOr(&A.ctr->err, ERRB_OVERFLOW);
+                }
+            }
         }
-        const int total = __shfl_sync(0xffffffffu, incl, NW - 1);
-        const int before = warp ? __shfl_sync(0xffffffffu, incl, warp - 1) : 0;
-        if (stay) {
-            const long long q = (long long)seg + written + before + __popc(bal & ((1u << lane) - 1));
-            __stcs(A.pa.cell + q, lc);
-            __stcs(A.pa.d[0] + q, d2[0]);
-            __stcs(A.pa.d[1] + q, d2[1]);
-            __stcs(A.pa.d[2] + q, d2[2]);
-            __stcs(A.pa.u[0] + q, u[0]);
-            __stcs(A.pa.u[1] + q, u[1]);
-            __stcs(A.pa.u[2] + q, u[2]);
-            __stcs(A.pa.w + q, w);
-            if (IDS) __stcs(A.pa.id + q, pid);
-        }
-        written += total;
+        flush_warp<T>(acc, key >= 0 ? tile_index(0, key & 7, (key >> 3) & 7, key >> 6) : -1, lane, Q, sJa, qoff);
     }
+    for (int o = 16; o > 0; o >>= 1) left += __shfl_xor_sync(0xffffffffu, left, o);
+    if (lane == 0 && left) atomicAdd(A.pa.holes + tile, left);
     __syncthreads();
-    if (threadIdx.x == 0) A.pa.count[tile] = written;
 
     // flush the shared J tile to HBM (periodic wrap of the guard layers)
     for (int e = threadIdx.x; e < JT_ELEMS; e += NT) {
-        const Acc v = jtile_get(sJ, e, JT_ELEMS, Acc(0));
-        if (v == Acc(0)) continue;
+        const T tv = reinterpret_cast<const T*>(sJ)[e];
+        if (tv == T(0)) continue;
+        const Acc v = to_acc(tv);
         const int comp = e / SJ3;
         const int r = e - comp * SJ3;
         const int lx = r % SJ - 1, ly = (r / SJ) % SJ - 1, lz = r / (SJ * SJ) - 1;
@@ -476,6 +536,7 @@ __global__ void __launch_bounds__(256) k_backpush(PushArgs<T> A, const T* B0x, c
         for (int i = threadIdx.x; i < cnt; i += blockDim.x) {
             const long long p = (long long)A.pa.seg_start[t] + i;
             const int lc = A.pa.cell[p];
+            if (lc < 0) continue;
             const int gx = tx * TILE + (lc & 7), gy = ty * TILE + ((lc >> 3) & 7), gz = tz * TILE + (lc >> 6);
             auto fetch = [&](int comp, int x, int y, int z) -> T {
                 const T* a = comp < 3 ? A.f.E[comp] : (comp == 3 ? B0x : comp == 4 ? B0y : B0z);
@@ -606,9 +667,10 @@ pic_status launch_backpush(pic_ctx* c, SpeciesDev& s) {
 }
 
 // Counting sort of every tile segment by local cell (ping-pong between the two SoA
-// blocks of a species).  Restores the cell order that the in-place compaction and
-// the appended movers erode, so that the lanes of a warp share cells: the gather
-// then reads broadcast shared-memory values and the deposit reduces per warp.
+// blocks of a species), dropping the holes.  Restores the cell order that moves and
+// the appended movers erode, so that the lanes of a warp share cells (the gather then
+// reads broadcast shared-memory values) and a lane's consecutive particles share their
+// start cell (the deposit then sums them in registers).
 template <typename T, bool IDS>
 __global__ void __launch_bounds__(256) k_sort_tiles(ParticleArrays<T> src, ParticleArrays<T> dst) {
     __shared__ int hist[TILE_CELLS];
@@ -623,8 +685,9 @@ __global__ void __launch_bounds__(256) k_sort_tiles(ParticleArrays<T> src, Parti
     // runs of equal cells within a warp (nearly sorted input: few runs) count once
     for (int base = 0; base < cnt; base += 256) {
         const int i = base + threadIdx.x;
-        const bool act = i < cnt;
-        const int c = act ? src.cell[seg + i] : -1 - lane;
+        int c = i < cnt ? src.cell[seg + i] : HOLE;
+        const bool act = c >= 0;
+        if (!act) c = -1 - lane;
         const int cp = __shfl_up_sync(0xffffffffu, c, 1);
         const unsigned heads = __ballot_sync(0xffffffffu, lane == 0 || c != cp);
         const unsigned after = heads & ~((2u << lane) - 1u);      // heads above this lane
@@ -647,11 +710,16 @@ __global__ void __launch_bounds__(256) k_sort_tiles(ParticleArrays<T> src, Parti
     const int excl = woff + incl - (a0 + a1);
     hist[2 * threadIdx.x] = excl;
     hist[2 * threadIdx.x + 1] = excl + a0;
+    if (threadIdx.x == 255) {   // every thread has read count: the segment now holds no holes
+        src.count[t] = woff + incl;
+        src.holes[t] = 0;
+    }
     __syncthreads();
     for (int base = 0; base < cnt; base += 256) {
         const int i = base + threadIdx.x;
-        const bool act = i < cnt;
-        const int c = act ? src.cell[seg + i] : -1 - lane;
+        int c = i < cnt ? src.cell[seg + i] : HOLE;
+        const bool act = c >= 0;
+        if (!act) c = -1 - lane;
         const int cp = __shfl_up_sync(0xffffffffu, c, 1);
         const unsigned heads = __ballot_sync(0xffffffffu, lane == 0 || c != cp);
         const int head = 31 - __clz(heads & ((2u << lane) - 1u));  // first lane of my run

@@ -155,7 +155,7 @@ static pic_status load_t(pic_ctx* c, const pic_species_desc* d, SpeciesDev& s) {
     const size_t cap = (size_t)total;
     const size_t a_int = align256(cap * sizeof(int)), a_t = align256(cap * sizeof(T));
     const size_t pbytes = a_int * 2 + a_t * 7;
-    const size_t bytes = pbytes + align256(sizeof(int) * ntile) * 3 + align256(sizeof(Counters));
+    const size_t bytes = pbytes + align256(sizeof(int) * ntile) * 4 + align256(sizeof(Counters));
     unsigned char* base = static_cast<unsigned char*>(dev_alloc(c, bytes));
     unsigned char* base2 = static_cast<unsigned char*>(dev_alloc(c, pbytes));
     if (!base || !base2) return PIC_ERR_OOM;
@@ -167,6 +167,7 @@ static pic_status load_t(pic_ctx* c, const pic_species_desc* d, SpeciesDev& s) {
     s.seg_start = reinterpret_cast<int*>(base + off); off += align256(sizeof(int) * ntile);
     s.count = reinterpret_cast<int*>(base + off); off += align256(sizeof(int) * ntile);
     s.cap = reinterpret_cast<int*>(base + off); off += align256(sizeof(int) * ntile);
+    s.holes = reinterpret_cast<int*>(base + off); off += align256(sizeof(int) * ntile);
     s.ctr = reinterpret_cast<Counters*>(base + off);
     for (int b = 0; b < 2; ++b) {
         ParticleArrays<T>& pb = b == 0 ? arrays<T>(s) : arrays_alt<T>(s);
@@ -180,6 +181,7 @@ static pic_status load_t(pic_ctx* c, const pic_species_desc* d, SpeciesDev& s) {
         pb.seg_start = s.seg_start;
         pb.count = s.count;
         pb.cap = s.cap;
+        pb.holes = s.holes;
     }
     ParticleArrays<T>& pa = arrays<T>(s);
     GBPIC_CHECK(c, cudaMemsetAsync(base, 0, bytes, c->stream));
@@ -220,17 +222,35 @@ pic_status load_species_impl(pic_ctx* c, const pic_species_desc* d, SpeciesDev& 
 // ---------------------------------------------------------------------------
 // Read-out of particles as FP64 rows X, Y, Z, ux, uy, uz, w.
 
+// One CTA of 256 threads per tile; without ids the particles keep their slot order
+// (holes skipped by a block-wide prefix count).
 template <typename T>
-__global__ void k_read_tiles(Geom g, ParticleArrays<T> pa, const long long* out_off, double* out, long long nout,
-                             int use_ids) {
+__global__ void __launch_bounds__(256) k_read_tiles(Geom g, ParticleArrays<T> pa, const long long* out_off, double* out,
+                                                    long long nout, int use_ids) {
+    __shared__ int wtot[8];
     const int ntile = g.nt[0] * g.nt[1] * g.nt[2];
+    const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
     for (int t = blockIdx.x; t < ntile; t += gridDim.x) {
         const int cnt = min(pa.count[t], pa.cap[t]);
         const int tx = t % g.nt[0], ty = (t / g.nt[0]) % g.nt[1], tz = t / (g.nt[0] * g.nt[1]);
-        for (int i = threadIdx.x; i < cnt; i += blockDim.x) {
+        long long written = 0;
+        for (int base = 0; base < cnt; base += 256) {
+            const int i = base + threadIdx.x;
             const long long p = (long long)pa.seg_start[t] + i;
-            const int lc = pa.cell[p];
-            const long long o = use_ids ? (long long)pa.id[p] : out_off[t] + i;
+            const int lc = i < cnt ? pa.cell[p] : HOLE;
+            const unsigned bal = __ballot_sync(0xffffffffu, lc >= 0);
+            __syncthreads();   // the previous chunk's totals are consumed
+            if (lane == 0) wtot[warp] = __popc(bal);
+            __syncthreads();
+            int before = 0, total = 0;
+            for (int w = 0; w < 8; ++w) {
+                before += w < warp ? wtot[w] : 0;
+                total += wtot[w];
+            }
+            const long long rank = written + before + __popc(bal & ((1u << lane) - 1u));
+            written += total;
+            if (lc < 0) continue;
+            const long long o = use_ids ? (long long)pa.id[p] : out_off[t] + rank;
             if (o < 0 || o >= nout) continue;
             out[o] = (double)(tx * TILE + (lc & 7)) + (double)pa.d[0][p];
             out[nout + o] = (double)(ty * TILE + ((lc >> 3) & 7)) + (double)pa.d[1][p];
@@ -265,16 +285,17 @@ template <typename T>
 static pic_status read_t(pic_ctx* c, SpeciesDev& s, double* out, int64_t nout) {
     const Geom& g = c->g;
     const int ntile = g.nt[0] * g.nt[1] * g.nt[2];
-    std::vector<int> h_count(ntile);
+    std::vector<int> h_count(ntile), h_holes(ntile);
     Counters h_ctr;
     GBPIC_CHECK(c, cudaMemcpyAsync(h_count.data(), s.count, sizeof(int) * ntile, cudaMemcpyDeviceToHost, c->stream));
+    GBPIC_CHECK(c, cudaMemcpyAsync(h_holes.data(), s.holes, sizeof(int) * ntile, cudaMemcpyDeviceToHost, c->stream));
     GBPIC_CHECK(c, cudaMemcpyAsync(&h_ctr, s.ctr, sizeof(Counters), cudaMemcpyDeviceToHost, c->stream));
     GBPIC_CHECK(c, cudaStreamSynchronize(c->stream));
     std::vector<long long> off(ntile);
     long long acc = 0;
     for (int t = 0; t < ntile; ++t) {
         off[t] = acc;
-        acc += std::min(h_count[t], s.h_cap[t]);
+        acc += std::min(h_count[t], s.h_cap[t]) - h_holes[t];
     }
     long long* d_off = static_cast<long long*>(dev_alloc(c, sizeof(long long) * ntile));
     if (!d_off) return PIC_ERR_OOM;
@@ -302,14 +323,16 @@ pic_status get_particles_impl(pic_ctx* c, SpeciesDev& s, double* out_dev, int64_
 
 int64_t count_alive(pic_ctx* c, SpeciesDev& s, int64_t* spilled) {
     const int ntile = c->g.nt[0] * c->g.nt[1] * c->g.nt[2];
-    std::vector<int> h_count(ntile);
+    std::vector<int> h_count(ntile), h_holes(ntile);
     Counters h_ctr;
     if (cudaMemcpyAsync(h_count.data(), s.count, sizeof(int) * ntile, cudaMemcpyDeviceToHost, c->stream) != cudaSuccess)
+        return -1;
+    if (cudaMemcpyAsync(h_holes.data(), s.holes, sizeof(int) * ntile, cudaMemcpyDeviceToHost, c->stream) != cudaSuccess)
         return -1;
     if (cudaMemcpyAsync(&h_ctr, s.ctr, sizeof(Counters), cudaMemcpyDeviceToHost, c->stream) != cudaSuccess) return -1;
     if (cudaStreamSynchronize(c->stream) != cudaSuccess) return -1;
     int64_t n = 0;
-    for (int t = 0; t < ntile; ++t) n += std::min(h_count[t], s.h_cap[t]);
+    for (int t = 0; t < ntile; ++t) n += std::min(h_count[t], s.h_cap[t]) - h_holes[t];
     const int nsp = std::min(h_ctr.spill_count[c->step & 1], s.spill_cap);
     if (spilled) *spilled = nsp;
     return n + nsp;

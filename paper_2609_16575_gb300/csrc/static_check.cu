@@ -47,6 +47,7 @@ __global__ void k_static_charge(Geom g, ParticleArrays<T> pa, const Rec<T>* spil
         for (int i = threadIdx.x; i < cnt; i += blockDim.x) {
             const long long p = (long long)pa.seg_start[t] + i;
             const int lc = pa.cell[p];
+            if (lc < 0) continue;
             one(tx * TILE + (lc & 7), ty * TILE + ((lc >> 3) & 7), tz * TILE + (lc >> 6), pa.d[0][p], pa.d[1][p],
                 pa.d[2][p], pa.w[p]);
         }
