@@ -245,6 +245,63 @@ __device__ __forceinline__ void gather_eb(Fetch6 F, int x, int y, int z, T dx, T
     Bp[2] = trilerp<T>([&](int a, int b, int c) { return F(5, a, b, c); }, hx, hy, z, shx, shy, dz);
 }
 
+// Two lanes of arithmetic at once: the FP32 path uses Blackwell's paired FP32
+// instructions (one fused multiply-add or add per pair, each element rounded as its
+// scalar counterpart), the FP64 path plain scalar pairs.
+template <typename T> struct Pair;
+template <> struct Pair<float> {
+    using t = float2;
+    static __device__ __forceinline__ float2 splat(float v) { return make_float2(v, v); }
+    static __device__ __forceinline__ float2 make(float a, float b) { return make_float2(a, b); }
+    static __device__ __forceinline__ float2 fma(float2 a, float2 b, float2 c) { return __ffma2_rn(a, b, c); }
+    static __device__ __forceinline__ float2 mul(float2 a, float2 b) { return __fmul2_rn(a, b); }
+    static __device__ __forceinline__ float2 add(float2 a, float2 b) { return __fadd2_rn(a, b); }
+    // b - a, rounded once
+    static __device__ __forceinline__ float2 sub(float2 b, float2 a) { return __ffma2_rn(a, make_float2(-1.0f, -1.0f), b); }
+};
+template <> struct Pair<double> {
+    using t = double2;
+    static __device__ __forceinline__ double2 splat(double v) { return make_double2(v, v); }
+    static __device__ __forceinline__ double2 make(double a, double b) { return make_double2(a, b); }
+    static __device__ __forceinline__ double2 fma(double2 a, double2 b, double2 c) {
+        return make_double2(::fma(a.x, b.x, c.x), ::fma(a.y, b.y, c.y));
+    }
+    static __device__ __forceinline__ double2 mul(double2 a, double2 b) { return make_double2(a.x * b.x, a.y * b.y); }
+    static __device__ __forceinline__ double2 add(double2 a, double2 b) { return make_double2(a.x + b.x, a.y + b.y); }
+    static __device__ __forceinline__ double2 sub(double2 b, double2 a) { return make_double2(b.x - a.x, b.y - a.y); }
+};
+
+// Gather E and B (section 2.5) from z-paired staged fields: PF(comp, x, y, z) returns
+// the pair (F(x, y, z), F(x, y, z + 1)) of component comp.  Each component is the same
+// trilinear interpolation as trilerp (x, then y, then z), with the x and y stages done
+// on both z planes at once.
+template <typename T, typename PF>
+__device__ __forceinline__ void gather_eb_pairs(PF P, int x, int y, int z, T dx, T dy, T dz, T Ep[3], T Bp[3]) {
+    using PT = Pair<T>;
+    using P2 = typename PT::t;
+    int hx, hy, hz;
+    T shx, shy, shz;
+    half_weight(x, dx, hx, shx);
+    half_weight(y, dy, hy, shy);
+    half_weight(z, dz, hz, shz);
+    auto tri = [&](int c, int bx, int by, int bz, T sx, T sy, T sz) -> T {
+        const P2 a00 = P(c, bx, by, bz), a10 = P(c, bx + 1, by, bz);
+        const P2 a01 = P(c, bx, by + 1, bz), a11 = P(c, bx + 1, by + 1, bz);
+        const P2 sx2 = PT::splat(sx);
+        const P2 q0 = PT::fma(sx2, PT::sub(a10, a00), a00);
+        const P2 q1 = PT::fma(sx2, PT::sub(a11, a01), a01);
+        const P2 r = PT::fma(PT::splat(sy), PT::sub(q1, q0), q0);
+        return r.x + sz * (r.y - r.x);
+    };
+    // E: Ex (h,n,n), Ey (n,h,n), Ez (n,n,h);  B: Bx (n,h,h), By (h,n,h), Bz (h,h,n)
+    Ep[0] = tri(0, hx, y, z, shx, dy, dz);
+    Ep[1] = tri(1, x, hy, z, dx, shy, dz);
+    Ep[2] = tri(2, x, y, hz, dx, dy, shz);
+    Bp[0] = tri(3, x, hy, hz, dx, shy, shz);
+    Bp[1] = tri(4, hx, y, hz, shx, dy, shz);
+    Bp[2] = tri(5, hx, hy, z, shx, shy, dz);
+}
+
 // Relativistic Boris (section 2.4; Boris 1970): u^{n-1/2} -> u^{n+1/2} in place,
 // eps = q dt / (2 m).  Returns 1/gamma^{n+1/2}.
 template <typename T>
@@ -341,6 +398,25 @@ __device__ __forceinline__ void segment_values(const T cw[3], const T F[3], cons
     v[9] = az * (wx1 * wy0 - kz);
     v[10] = az * (wx0 * wy1 - kz);
     v[11] = az * (wx1 * wy1 + kz);
+}
+
+// segment_values as six pairs (v[0], v[1]), (v[2], v[3]), ... of the same values.
+template <typename T>
+__device__ __forceinline__ void segment_values_pairs(const T cw[3], const T F[3], const T W[3],
+                                                     typename Pair<T>::t v[6]) {
+    using PT = Pair<T>;
+    using P2 = typename PT::t;
+    const T twelfth = T(1) / T(12);
+    const T kx = F[1] * F[2] * twelfth, ky = F[0] * F[2] * twelfth, kz = F[0] * F[1] * twelfth;
+    const P2 wx = PT::make(T(1) - W[0], W[0]), wy = PT::make(T(1) - W[1], W[1]);
+    const T wz0 = T(1) - W[2], wz1 = W[2], wy0 = T(1) - W[1], wy1 = W[1];
+    const P2 ax = PT::splat(cw[0] * F[0]), ay = PT::splat(cw[1] * F[1]), az = PT::splat(cw[2] * F[2]);
+    v[0] = PT::mul(ax, PT::fma(wy, PT::splat(wz0), PT::make(kx, -kx)));
+    v[1] = PT::mul(ax, PT::fma(wy, PT::splat(wz1), PT::make(-kx, kx)));
+    v[2] = PT::mul(ay, PT::fma(wx, PT::splat(wz0), PT::make(ky, -ky)));
+    v[3] = PT::mul(ay, PT::fma(wx, PT::splat(wz1), PT::make(-ky, ky)));
+    v[4] = PT::mul(az, PT::fma(wx, PT::splat(wy0), PT::make(kz, -kz)));
+    v[5] = PT::mul(az, PT::fma(wx, PT::splat(wy1), PT::make(-kz, kz)));
 }
 
 // Scatter 12 segment values of the cell (x, y, z) through Add(comp, x, y, z, fixed).

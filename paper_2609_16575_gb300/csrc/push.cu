@@ -37,12 +37,23 @@ template <typename T> __host__ __device__ constexpr int box_stride() {
 }
 constexpr int JT_ELEMS = 3 * SJ3;   // elements of the shared J tile (working precision)
 constexpr int QCAP_ = 64;   // record queue per warp (QCAP below)
+constexpr int PSX = 10, PSY = 10, PSZ = 9;   // z-paired staged fields: x, y -1..8, pair base z -1..7
+constexpr int PS = PSX * PSY * PSZ;          // pairs per component
+// Shared memory of the tile kernel, in order: region A = the TMA destination of the
+// six raw E, B boxes, reused for the warps' record queues once the boxes have been
+// converted; the z-paired fields; the J tile; the mbarrier.  Offsets are multiples of
+// 128 bytes.
+__host__ __device__ constexpr size_t align128(size_t b) { return (b + 127) / 128 * 128; }
+template <typename T> __host__ __device__ constexpr size_t region_a_bytes() {
+    return align128((size_t)6 * box_stride<T>() * sizeof(T) > (size_t)(Prec<T>::THREADS / 32) * QCAP_ * 13 * sizeof(T)
+                        ? (size_t)6 * box_stride<T>() * sizeof(T)
+                        : (size_t)(Prec<T>::THREADS / 32) * QCAP_ * 13 * sizeof(T));
+}
+template <typename T> __host__ __device__ constexpr size_t pairs_bytes() { return align128((size_t)6 * PS * 2 * sizeof(T)); }
+template <typename T> __host__ __device__ constexpr size_t jtile_bytes() { return align128((size_t)JT_ELEMS * sizeof(T)); }
 template <typename T> constexpr size_t tile_smem_bytes() {
-    // staged E, B boxes + J tile (working precision) + record queues +
-    // mbarrier; + 128: the kernel rounds the dynamic shared base up to a 128-byte
-    // boundary (TMA destination)
-    return (size_t)6 * box_stride<T>() * sizeof(T) + ((size_t)JT_ELEMS * sizeof(T) + 15) / 16 * 16 +
-           (size_t)(Prec<T>::THREADS / 32) * QCAP_ * 13 * sizeof(T) + 16 + 128;
+    // + 128: the kernel rounds the dynamic shared base up to a 128-byte boundary
+    return region_a_bytes<T>() + pairs_bytes<T>() + jtile_bytes<T>() + 16 + 128;
 }
 
 __device__ __forceinline__ void block_add_double(double v, double* dst) {
@@ -99,14 +110,18 @@ template <typename T> struct WarpQueue {
 // Append the 12 values v of the cell with origin index k for every lane with `want`
 // (warp-collective).
 template <typename T>
-__device__ __forceinline__ void q_push(WarpQueue<T> Q, int& qn, bool want, int k, const T v[12], int lane) {
+__device__ __forceinline__ void q_push(WarpQueue<T> Q, int& qn, bool want, int k, const typename Pair<T>::t v[6],
+                                       int lane) {
     const unsigned m = __ballot_sync(0xffffffffu, want);
     if (!m) return;
     if (want) {
         const int slot = qn + __popc(m & ((1u << lane) - 1u));
         Q.key(slot) = k;
 #pragma unroll
-        for (int q = 0; q < 12; ++q) Q.rec[slot * 13 + q] = v[q];
+        for (int q = 0; q < 6; ++q) {
+            Q.rec[slot * 13 + 2 * q] = v[q].x;
+            Q.rec[slot * 13 + 2 * q + 1] = v[q].y;
+        }
     }
     qn += __popc(m);
 }
@@ -131,9 +146,13 @@ __device__ __forceinline__ void q_drain(WarpQueue<T> Q, int& qn, int lane, uint3
 // of a warp form a few runs, so a flush costs a few atomics per value instead of 32
 // (shared atomics from many lanes on one address serialise).
 template <typename T>
-__device__ __forceinline__ void flush_warp(const T acc[12], int key, int lane, WarpQueue<T> Q, uint32_t sJa, int qoff) {
+__device__ __forceinline__ void flush_warp(const typename Pair<T>::t acc[6], int key, int lane, WarpQueue<T> Q,
+                                           uint32_t sJa, int qoff) {
 #pragma unroll
-    for (int q = 0; q < 12; ++q) Q.rec[lane * 13 + q] = acc[q];
+    for (int q = 0; q < 6; ++q) {
+        Q.rec[lane * 13 + 2 * q] = acc[q].x;
+        Q.rec[lane * 13 + 2 * q + 1] = acc[q].y;
+    }
     Q.key(lane) = key;
     __syncwarp();
     if (lane < 24) {
@@ -200,11 +219,13 @@ k_tile_push(const __grid_constant__ CUtensorMap tE0, const __grid_constant__ CUt
     constexpr int BX = Prec<T>::BX;
     constexpr int BS = box_stride<T>();
     static_assert(NW <= PUSH_WARPS_MAX, "tile kernel CTA too large");
-    T* sF = reinterpret_cast<T*>(smem);
-    unsigned char* sJ = smem + (size_t)6 * BS * sizeof(T);
+    using P2 = typename Pair<T>::t;
+    T* sF = reinterpret_cast<T*>(smem);                     // raw boxes, then the queues
+    unsigned char* sQ = smem;
+    P2* sP = reinterpret_cast<P2*>(smem + region_a_bytes<T>());
+    unsigned char* sJ = smem + region_a_bytes<T>() + pairs_bytes<T>();
     const uint32_t sJa = smem_u32(sJ);
-    unsigned char* sQ = sJ + ((size_t)JT_ELEMS * sizeof(T) + 15) / 16 * 16;
-    uint64_t* bar = reinterpret_cast<uint64_t*>(sQ + (size_t)NW * QCAP * 13 * sizeof(T));
+    uint64_t* bar = reinterpret_cast<uint64_t*>(sJ + jtile_bytes<T>());
     __shared__ int s_timeout;
 
     const int tile = blockIdx.x;
@@ -255,9 +276,17 @@ k_tile_push(const __grid_constant__ CUtensorMap tE0, const __grid_constant__ CUt
         __syncthreads();
         return;
     }
+    // z pairs (F(x, y, z), F(x, y, z + 1)) of every component, local x, y -1..8, z -1..7
+    for (int e = threadIdx.x; e < 6 * PS; e += NT) {
+        const int c = e / PS, r = e - c * PS;
+        const int xi = r % PSX, yi = (r / PSX) % PSY, zi = r / (PSX * PSY);
+        const T* F = sF + c * BS + (zi * SB + yi) * BX + xi;
+        sP[e] = Pair<T>::make(F[0], F[SB * BX]);
+    }
+    __syncthreads();   // region A now holds the record queues
 
-    auto fetch = [&](int comp, int x, int y, int z) -> T {
-        return sF[comp * BS + ((z + 1) * SB + (y + 1)) * BX + (x + 1)];
+    auto pfetch = [&](int comp, int x, int y, int z) -> P2 {
+        return sP[comp * PS + ((z + 1) * PSY + (y + 1)) * PSX + (x + 1)];
     };
 
     const int ext[3] = {min(TILE, A.g.n[0] - ox), min(TILE, A.g.n[1] - oy), min(TILE, A.g.n[2] - oz)};
@@ -296,10 +325,10 @@ k_tile_push(const __grid_constant__ CUtensorMap tE0, const __grid_constant__ CUt
     prefetch_cells((warp * 32 + lane) * R);
 
     for (int row = warp; row * 32 < ngroups; row += NW) {
-        T acc[12];                // summed straight-segment currents of start cell `key`
+        P2 acc[6];                // summed straight-segment currents of start cell `key`
         int key = RowCells<R>::key(n_cells);
 #pragma unroll
-        for (int q = 0; q < 12; ++q) acc[q] = T(0);
+        for (int q = 0; q < 6; ++q) acc[q] = Pair<T>::splat(T(0));
         const int s0 = (row * 32 + lane) * R;   // first slot of this lane
         prefetch_cells(((row + NW) * 32 + lane) * R);
 #pragma unroll 1
@@ -311,7 +340,7 @@ k_tile_push(const __grid_constant__ CUtensorMap tE0, const __grid_constant__ CUt
             T u[3] = {n_u[0], n_u[1], n_u[2]}, d2[3] = {T(0), T(0), T(0)}, w = n_w;
             const T d1[3] = {n_d[0], n_d[1], n_d[2]};
             prefetch(r + 1 < R ? i + 1 : ((row + NW) * 32 + lane) * R);
-            T v[12], v2[12];
+            P2 v[6], v2[6];
             int s[3] = {0, 0, 0};
             int x = 0, y = 0, z = 0;
             bool stay = false, move = false, crossed = false;
@@ -320,7 +349,7 @@ k_tile_push(const __grid_constant__ CUtensorMap tE0, const __grid_constant__ CUt
                 y = (lc >> 3) & 7;
                 z = lc >> 6;
                 T Ep[3], Bp[3];
-                gather_eb<T>(fetch, x, y, z, d1[0], d1[1], d1[2], Ep, Bp);
+                gather_eb_pairs<T>(pfetch, x, y, z, d1[0], d1[1], d1[2], Ep, Bp);
                 T gm1_old = T(0);
                 if (RECK) gm1_old = gamma_minus_one(u);
                 const T ig = boris(A.eps, Ep, Bp, u);
@@ -346,13 +375,13 @@ k_tile_push(const __grid_constant__ CUtensorMap tE0, const __grid_constant__ CUt
                         D[k] = d2[k] - d1[k];
                         Wm[k] = d1[k] + T(0.5) * D[k];
                     }
-                    segment_values(cw, D, Wm, v);
+                    segment_values_pairs(cw, D, Wm, v);
                 } else {
                     T F1[3], F2[3], W1[3], W2[3];
 #pragma unroll
                     for (int k = 0; k < 3; ++k) relay(d1[k], d2[k], s[k], F1[k], F2[k], W1[k], W2[k]);
-                    segment_values(cw, F1, W1, v);
-                    segment_values(cw, F2, W2, v2);
+                    segment_values_pairs(cw, F1, W1, v);
+                    segment_values_pairs(cw, F2, W2, v2);
                 }
                 const int nx = x + s[0], ny = y + s[1], nz = z + s[2];
                 stay = nx >= 0 && nx < ext[0] && ny >= 0 && ny < ext[1] && nz >= 0 && nz < ext[2];
@@ -372,7 +401,7 @@ k_tile_push(const __grid_constant__ CUtensorMap tE0, const __grid_constant__ CUt
             const bool summed = active && lc == key;
             if (summed) {
 #pragma unroll
-                for (int q = 0; q < 12; ++q) acc[q] += v[q];
+                for (int q = 0; q < 6; ++q) acc[q] = Pair<T>::add(acc[q], v[q]);
             }
             q_push(Q, qn, active && !summed, tile_index(0, x, y, z), v, lane);
             q_push(Q, qn, crossed, tile_index(0, x + s[0], y + s[1], z + s[2]), v2, lane);
@@ -666,13 +695,33 @@ pic_status launch_backpush(pic_ctx* c, SpeciesDev& s) {
     return c->prec == PIC_FP64 ? backpush_t<double>(c, s) : backpush_t<float>(c, s);
 }
 
+// R consecutive slots of one working-precision array: one 16-byte load.
+template <typename T, int R> struct Slots;
+template <> struct Slots<float, 4> {
+    static __device__ __forceinline__ void ld(const float* p, float v[4]) {
+        const float4 a = __ldcs(reinterpret_cast<const float4*>(p));
+        v[0] = a.x; v[1] = a.y; v[2] = a.z; v[3] = a.w;
+    }
+};
+template <> struct Slots<double, 2> {
+    static __device__ __forceinline__ void ld(const double* p, double v[2]) {
+        const double2 a = __ldcs(reinterpret_cast<const double2*>(p));
+        v[0] = a.x; v[1] = a.y;
+    }
+};
+
 // Counting sort of every tile segment by local cell (ping-pong between the two SoA
 // blocks of a species), dropping the holes.  Restores the cell order that moves and
 // the appended movers erode, so that the lanes of a warp share cells (the gather then
 // reads broadcast shared-memory values) and a lane's consecutive particles share their
-// start cell (the deposit then sums them in registers).
+// start cell (the deposit then sums them in registers).  One CTA of 256 threads per
+// tile; each lane reads R consecutive slots with 16-byte loads.  Lanes holding the same
+// cell in one step are counted (and given destination slots) with one shared atomic
+// per warp and cell, since many lanes adding to one shared address serialise.  Within
+// a cell the order is not kept.
 template <typename T, bool IDS>
 __global__ void __launch_bounds__(256) k_sort_tiles(ParticleArrays<T> src, ParticleArrays<T> dst) {
+    constexpr int R = Prec<T>::R;
     __shared__ int hist[TILE_CELLS];
     __shared__ int wsum[8];
     const int t = blockIdx.x;
@@ -682,17 +731,22 @@ __global__ void __launch_bounds__(256) k_sort_tiles(ParticleArrays<T> src, Parti
     for (int i = threadIdx.x; i < TILE_CELLS; i += 256) hist[i] = 0;
     __syncthreads();
     const long long seg = src.seg_start[t];
-    // runs of equal cells within a warp (nearly sorted input: few runs) count once
-    for (int base = 0; base < cnt; base += 256) {
-        const int i = base + threadIdx.x;
-        int c = i < cnt ? src.cell[seg + i] : HOLE;
-        const bool act = c >= 0;
-        if (!act) c = -1 - lane;
-        const int cp = __shfl_up_sync(0xffffffffu, c, 1);
-        const unsigned heads = __ballot_sync(0xffffffffu, lane == 0 || c != cp);
-        const unsigned after = heads & ~((2u << lane) - 1u);      // heads above this lane
-        const int end = after ? __ffs(after) - 1 : 32;            // one past the end of my run
-        if (act && ((heads >> lane) & 1u)) atomicAdd(&hist[c], end - lane);
+    const int ng = (cnt + R - 1) / R;
+    auto cells = [&](int g, int c[R]) {
+        if (g < ng) RowCells<R>::ld(src.cell + seg + (long long)g * R, c);
+#pragma unroll
+        for (int r = 0; r < R; ++r)
+            if (g >= ng || g * R + r >= cnt) c[r] = HOLE;
+    };
+    for (int base = 0; base < ng; base += 256) {
+        int c[R];
+        cells(base + threadIdx.x, c);
+#pragma unroll
+        for (int r = 0; r < R; ++r) {
+            const bool ok = c[r] >= 0;
+            const unsigned grp = __match_any_sync(0xffffffffu, ok ? c[r] : -1 - lane);
+            if (ok && lane == __ffs(grp) - 1) atomicAdd(&hist[c[r]], __popc(grp));
+        }
     }
     __syncthreads();
     // exclusive scan of the 512 counts: two per thread, warp scans, then warp offsets
@@ -715,30 +769,40 @@ __global__ void __launch_bounds__(256) k_sort_tiles(ParticleArrays<T> src, Parti
         src.holes[t] = 0;
     }
     __syncthreads();
-    for (int base = 0; base < cnt; base += 256) {
-        const int i = base + threadIdx.x;
-        int c = i < cnt ? src.cell[seg + i] : HOLE;
-        const bool act = c >= 0;
-        if (!act) c = -1 - lane;
-        const int cp = __shfl_up_sync(0xffffffffu, c, 1);
-        const unsigned heads = __ballot_sync(0xffffffffu, lane == 0 || c != cp);
-        const int head = 31 - __clz(heads & ((2u << lane) - 1u));  // first lane of my run
-        const unsigned after = heads & ~((2u << lane) - 1u);
-        const int end = after ? __ffs(after) - 1 : 32;
-        int b = 0;
-        if (act && lane == head) b = atomicAdd(&hist[c], end - lane);
-        b = __shfl_sync(0xffffffffu, b, head);
-        if (act) {
-            const long long p = seg + i;
-            const long long q = seg + b + (lane - head);
-            dst.cell[q] = c;
+    for (int base = 0; base < ng; base += 256) {
+        const int g = base + threadIdx.x;
+        const long long p0 = seg + (long long)g * R;
+        int c[R], id[R];
+        T d[3][R], u[3][R], w[R];
+        cells(g, c);
+        if (g < ng) {
 #pragma unroll
             for (int k = 0; k < 3; ++k) {
-                dst.d[k][q] = __ldcs(src.d[k] + p);
-                dst.u[k][q] = __ldcs(src.u[k] + p);
+                Slots<T, R>::ld(src.d[k] + p0, d[k]);
+                Slots<T, R>::ld(src.u[k] + p0, u[k]);
             }
-            dst.w[q] = __ldcs(src.w + p);
-            if (IDS) dst.id[q] = __ldcs(src.id + p);
+            Slots<T, R>::ld(src.w + p0, w);
+            if (IDS) RowCells<R>::ld(src.id + p0, id);
+        }
+#pragma unroll
+        for (int r = 0; r < R; ++r) {
+            const bool ok = c[r] >= 0;
+            const unsigned grp = __match_any_sync(0xffffffffu, ok ? c[r] : -1 - lane);
+            const int leader = __ffs(grp) - 1;
+            int b = 0;
+            if (ok && lane == leader) b = atomicAdd(&hist[c[r]], __popc(grp));
+            b = __shfl_sync(0xffffffffu, b, leader);
+            if (ok) {
+                const long long q = seg + b + __popc(grp & ((1u << lane) - 1u));
+                dst.cell[q] = c[r];
+#pragma unroll
+                for (int k = 0; k < 3; ++k) {
+                    dst.d[k][q] = d[k][r];
+                    dst.u[k][q] = u[k][r];
+                }
+                dst.w[q] = w[r];
+                if (IDS) dst.id[q] = id[r];
+            }
         }
     }
 }
