@@ -49,6 +49,7 @@ def parse():
     p.add_argument("--no-e2e", action="store_true")
     p.add_argument("--no-fp64", action="store_true")
     p.add_argument("--no-cpu-baseline", action="store_true")
+    p.add_argument("--no-extra", action="store_true", help="skip the other workloads and the adjoint cost")
     p.add_argument("--small", action="store_true", help="32^3 cells instead of 128^3 (smoke)")
     p.add_argument("--cells", type=int, default=0, help="cells per dimension (profiling cases); 0 = 128")
     p.add_argument("--sort-every", type=int, default=0, help="tile re-sort cadence passed to the library")
@@ -168,6 +169,138 @@ def cpu_baseline(steps=10, n=32):
             "seconds": round(dt, 2)}
 
 
+def time_steps(ctx, torch, steps):
+    """CUDA-event time (ms) of `steps` cycles on the context's stream."""
+    torch.cuda.synchronize()
+    st = torch.cuda.current_stream()
+    a, b = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+    ctx.set_timing(True)
+    ctx.kernel_times()
+    a.record(st)
+    ctx.step(steps)
+    b.record(st)
+    torch.cuda.synchronize()
+    kt = ctx.kernel_times()
+    ctx.set_timing(False)
+    return a.elapsed_time(b), kt
+
+
+def other_workloads(torch, peak):
+    """Throughput on the other workload shapes: the cold-plasma oscillation (16^3, 8 per
+    cell, FP64 and FP32) and the laser wakefield (512 x 128 x 128, open x, 8 per cell,
+    FP32)."""
+    from paper_2609_16575_gb300 import gbpic
+    from paper_2609_16575_gb300 import workloads as W
+
+    out = {}
+    wl = W.cold_plasma(n=16)
+    for prec, name in ((gbpic.PIC_FP64, "f64"), (gbpic.PIC_FP32, "f32")):
+        ctx = gbpic.Context(wl.n, wl.d, wl.dt, precision=prec, rho_ion=wl.rho_ion)
+        s = wl.species[0]
+        ctx.load_species_array(s.q, s.m, s.P, True)
+        time_steps(ctx, torch, 5)
+        ms, _ = time_steps(ctx, torch, 200)
+        out[f"cold_plasma_16_{name}"] = {"value": s.n * 200 / (ms / 1e3), "unit": UNIT, "steps": 200,
+                                          "ms_per_step": ms / 200, "particles": s.n,
+                                          "note": "launch-bound: 32,768 particles fill 8 tiles"}
+        ctx.close()
+    wl = W.lwfa()
+    ctx = gbpic.Context(wl.n, wl.d, wl.dt, precision=gbpic.PIC_FP32, rho_ion=wl.rho_ion, bc_x=1)
+    ctx.set_laser(*wl.laser.as_tuple())
+    s = wl.species[0]
+    ctx.load_species_array(s.q, s.m, s.P, s.momenta_at_half_step)
+    time_steps(ctx, torch, 3)
+    steps = 20
+    ms, kt = time_steps(ctx, torch, steps)
+    npart = s.n
+    ncell = wl.n[0] * wl.n[1] * wl.n[2]
+    tl, tms = kt["tile_push"]
+    algo = PART_BYTES["f32"] * npart + TILE_GRID_BYTES["f32"] * ncell
+    achieved = algo / (tms / tl / 1e3) / 1e9
+    out["lwfa_512x128x128_f32"] = {"value": npart * steps / (ms / 1e3), "unit": UNIT, "steps": steps,
+                                   "ms_per_step": ms / steps, "particles": npart,
+                                   "tile_push": {"avg_launch_ms": tms / tl, "achieved_gbs": achieved,
+                                                 "frac": achieved / peak},
+                                   "yee": yee_line(kt, ncell, peak),
+                                   "note": "steps 4-23 of the run: the pulse has not reached the plasma yet"}
+    ctx.close()
+    return out
+
+
+def adjoint_cost(torch):
+    """Backward/forward cost of the checkpointed adjoint on the differentiable-run
+    workload (32^3, 16 per cell, u_th = 0.02, plane wave of amplitude 0.05, 200 steps,
+    checkpoints every 20, FP64)."""
+    import numpy as np
+    from paper_2609_16575_gb300 import gbpic
+    from paper_2609_16575_gb300 import workloads as W
+
+    wl = W.differentiable()
+    n, d = wl.n, wl.d
+    # a vacuum plane wave along x polarised in y: E_y = cos(k x), B_z = cos(k x') one half
+    # step earlier at the B location (an input shape only)
+    k = 2 * np.pi / (n[0] * d[0])
+    x_e = np.arange(n[0]) * d[0]
+    x_b = (np.arange(n[0]) + 0.5) * d[0]
+    E = np.zeros((3, n[2], n[1], n[0]))
+    B = np.zeros_like(E)
+    E[1] = np.cos(k * x_e)[None, None, :]
+    B[2] = np.cos(k * (x_b + 0.5 * wl.dt))[None, None, :]
+    A = 0.05
+    s = wl.species[0]
+    ctx = gbpic.Context(n, d, wl.dt, precision=gbpic.PIC_FP64, rho_ion=wl.rho_ion, track_ids=True)
+    ctx.set_fields(A * E, A * B)
+    ctx.load_species_array(s.q, s.m, s.P, True)
+    torch.cuda.synchronize()
+    t0 = time.perf_counter()
+    ctx.step(200)
+    ctx.sync()
+    t_plain = time.perf_counter() - t0
+    ctx.close()
+    ctx = gbpic.Context(n, d, wl.dt, precision=gbpic.PIC_FP64, rho_ion=wl.rho_ion, track_ids=True)
+    ctx.set_fields(A * E, A * B)
+    ctx.load_species_array(s.q, s.m, s.P, True)
+    torch.cuda.synchronize()
+    t0 = time.perf_counter()
+    ctx.adjoint_forward(200, 20)
+    t_fwd = time.perf_counter() - t0
+    t0 = time.perf_counter()
+    ctx.adjoint_backward(E, B)
+    t_bwd = time.perf_counter() - t0
+    ctx.close()
+    return {"workload": "32^3, 16 ppc, u_th=0.02, plane wave A=0.05, 200 steps, checkpoint every 20, FP64",
+            "forward_plain_s": t_plain, "forward_with_checkpoints_s": t_fwd, "backward_s": t_bwd,
+            "backward_over_forward": t_bwd / t_plain}
+
+
+def arm_config(n, npart, ncell, world, sort_every):
+    """The workload description both arms print."""
+    return {"workload": (f"thermal plasma {n}^3 periodic, dx=0.2, 64 ppc ({npart:,} electrons), "
+                         "u_th=0.05, immobile ions, dt=0.5 Courant"),
+            "sort_every": sort_every or 4,
+            "particles_per_gpu": npart, "cells": ncell, "precision": "fp32 bulk, fp64 reductions",
+            "parallelism": f"replicas x{world}",
+            "l2": "inputs larger than L2 (particle SoA 4.3 GB per GPU)"}
+
+
+# Yee kernels per cell and step (FP32): two Faraday half steps (read E, B; write B: 36 B
+# each) and Ampere (read E, B and the 64-bit J; write E; clear J: 84 B)
+YEE_BYTES_PER_CELL = 2 * 36 + 84
+
+
+def yee_line(kt, ncell, peak):
+    """Yee cell updates per second from the CUDA-event times of the field kernels."""
+    fl, fms = kt.get("faraday_half", (0, 0.0))
+    al, ams = kt.get("ampere", (0, 0.0))
+    if not al or not fl:
+        return None
+    per_step_s = (fms / fl * 2 + ams / al) / 1e3
+    gbs = YEE_BYTES_PER_CELL * ncell / per_step_s / 1e9
+    return {"cell_updates_per_s": ncell / per_step_s, "ms_per_step": per_step_s * 1e3,
+            "bytes_per_cell": YEE_BYTES_PER_CELL, "achieved_gbs": gbs, "frac_of_hbm": gbs / peak,
+            "note": "fields (about 105 MB at 128^3) largely stay in the 129 MB L2 between kernels"}
+
+
 def run_reference(args):
     rank = int(os.environ.get("RANK", "0"))
     if rank != 0:
@@ -190,7 +323,8 @@ def run_reference(args):
     line = {"impl": "reference", "metric": METRIC, "value": value, "unit": UNIT, "n_gpus": args.gpus,
             "steps": args.steps, "warmup": args.warmup, "ms_per_step": dt / args.steps * 1e3,
             "higher_is_better": True, "scaling": "weak", "vs_baseline": None, "dtype": "f64", "data": "synthetic",
-            "config": {"workload": "thermal plasma (128^3 x 64 ppc shape), bounded CPU sample", "sample": sample},
+            "config": arm_config(WORKLOAD["n"][0], WORKLOAD["ppc"] * WORKLOAD["n"][0] ** 3, WORKLOAD["n"][0] ** 3,
+                                 args.gpus, args.sort_every),
             "cpu_baseline": {"value": value, "unit": UNIT, "cores": 1, "kind": "oracle", "sample": sample},
             "e2e": {"value": value, "unit": UNIT, "h2d_bytes_per_step": 0, "d2h_bytes_per_step": 0}}
     print(json.dumps(line), flush=True)
@@ -337,22 +471,22 @@ def run_gbpic(args):
     cpu = None
     if rank == 0 and world == 1 and not args.no_cpu_baseline:
         cpu = cpu_baseline()
+    extra, adj = None, None
+    if rank == 0 and world == 1 and not args.no_extra:
+        extra = other_workloads(torch, peak)
+        adj = adjoint_cost(torch)
 
     if rank == 0:
         line = {"metric": METRIC, "value": value, "unit": UNIT, "n_gpus": world, "steps": args.steps,
                 "warmup": args.warmup, "ms_per_step": ms_all / args.steps, "higher_is_better": True,
                 "scaling": "weak", "vs_baseline": None, "dtype": "f32", "data": "synthetic",
-                "config": {"workload": (f"thermal plasma {wl.n[0]}^3 periodic, dx=0.2, 64 ppc ({npart:,} electrons), "
-                                        "u_th=0.05, immobile ions, dt=0.5 Courant"),
-                           "sort_every": args.sort_every or 4,
-                           "particles_per_gpu": npart, "cells": ncell, "precision": "fp32 bulk, fp64 reductions",
-                           "parallelism": f"replicas x{world}",
-                           "l2": "inputs larger than L2 (particle SoA 4.3 GB per GPU)"},
+                "config": arm_config(wl.n[0], npart, ncell, world, args.sort_every),
                 "roofline": rl,
                 "step_hbm_frac": value / world * step_bytes / 1e9 / peak,
-                "cell_updates_per_s": ncell * world * args.steps / (ms_all / 1e3),
+                "cell_steps_per_s": ncell * world * args.steps / (ms_all / 1e3),
+                "yee": yee_line(kt, ncell * world, peak),
                 "kernels": kernels, "gpu_launches": launches, "clocks": clocks, "e2e": e2e,
-                "cpu_baseline": cpu, "fp64": fp64}
+                "cpu_baseline": cpu, "fp64": fp64, "other_workloads": extra, "adjoint": adj}
         print(json.dumps(line), flush=True)
     if dist is not None:
         dist.destroy_process_group()
