@@ -331,6 +331,21 @@ def run_reference(args):
     return 0
 
 
+def replica_rate(ms, npart, steps, dist):
+    """Whole-job rate of N independent replicas: the slowest rank's time (max over ranks)
+    and all ranks' particle-steps over it.  Returns (max ms, particle-steps/s)."""
+    import torch
+
+    world = 1
+    if dist is not None:
+        world = dist.get_world_size()
+        dev = "cuda" if dist.get_backend() == "nccl" else "cpu"
+        t = torch.tensor([ms], device=dev, dtype=torch.float64)
+        dist.all_reduce(t, op=dist.ReduceOp.MAX)
+        ms = float(t.item())
+    return ms, npart * world * steps / (ms / 1e3)
+
+
 def timed_steps(ctx, torch, steps, dist):
     ctx.set_timing(True)
     ctx.kernel_times()
@@ -406,12 +421,7 @@ def run_gbpic(args):
         raise RuntimeError(f"particles lost: {diag['n_alive']} of {npart}")
     ctx.close()
     del ctx
-    ms_all = ms
-    if dist is not None:
-        t = torch.tensor([ms], device="cuda", dtype=torch.float64)
-        dist.all_reduce(t, op=dist.ReduceOp.MAX)
-        ms_all = float(t.item())
-    value = npart * world * args.steps / (ms_all / 1e3)
+    ms_all, value = replica_rate(ms, npart, args.steps, dist)
     wk = f"thermal{wl.n[0]}"
     traffic = committed_traffic("tile_push", wk, npart)
     rl = roofline(kt, "f32", npart, ncell, peak, peak_kind, traffic)
