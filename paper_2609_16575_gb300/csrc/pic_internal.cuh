@@ -539,6 +539,7 @@ struct SpeciesDev {
     int* count = nullptr;
     int* cap = nullptr;
     int* holes = nullptr;
+    int* perm = nullptr;                  // re-sort scratch: source slot of every destination slot
     void* movers = nullptr;
     int mover_cap = 0;
     void* spill = nullptr;

@@ -186,6 +186,9 @@ template <> struct RowCells<4> {
         const int4 a = __ldg(reinterpret_cast<const int4*>(p));
         c[0] = a.x; c[1] = a.y; c[2] = a.z; c[3] = a.w;
     }
+    static __device__ __forceinline__ void st(int* p, const int c[4]) {
+        __stcs(reinterpret_cast<int4*>(p), make_int4(c[0], c[1], c[2], c[3]));
+    }
     static __device__ __forceinline__ int key(const int c[4]) {
         int k = c[2] == c[3] ? c[2] : c[1];
         if (k < 0) k = c[0] >= 0 ? c[0] : (c[1] >= 0 ? c[1] : (c[2] >= 0 ? c[2] : c[3]));
@@ -196,6 +199,9 @@ template <> struct RowCells<2> {
     static __device__ __forceinline__ void ld(const int* p, int c[2]) {
         const int2 a = __ldg(reinterpret_cast<const int2*>(p));
         c[0] = a.x; c[1] = a.y;
+    }
+    static __device__ __forceinline__ void st(int* p, const int c[2]) {
+        __stcs(reinterpret_cast<int2*>(p), make_int2(c[0], c[1]));
     }
     static __device__ __forceinline__ int key(const int c[2]) { return c[0] >= 0 ? c[0] : c[1]; }
 };
@@ -702,11 +708,17 @@ template <> struct Slots<float, 4> {
         const float4 a = __ldcs(reinterpret_cast<const float4*>(p));
         v[0] = a.x; v[1] = a.y; v[2] = a.z; v[3] = a.w;
     }
+    static __device__ __forceinline__ void st(float* p, const float v[4]) {
+        __stcs(reinterpret_cast<float4*>(p), make_float4(v[0], v[1], v[2], v[3]));
+    }
 };
 template <> struct Slots<double, 2> {
     static __device__ __forceinline__ void ld(const double* p, double v[2]) {
         const double2 a = __ldcs(reinterpret_cast<const double2*>(p));
         v[0] = a.x; v[1] = a.y;
+    }
+    static __device__ __forceinline__ void st(double* p, const double v[2]) {
+        __stcs(reinterpret_cast<double2*>(p), make_double2(v[0], v[1]));
     }
 };
 
@@ -715,12 +727,18 @@ template <> struct Slots<double, 2> {
 // the appended movers erode, so that the lanes of a warp share cells (the gather then
 // reads broadcast shared-memory values) and a lane's consecutive particles share their
 // start cell (the deposit then sums them in registers).  One CTA of 256 threads per
-// tile; each lane reads R consecutive slots with 16-byte loads.  Lanes holding the same
-// cell in one step are counted (and given destination slots) with one shared atomic
-// per warp and cell, since many lanes adding to one shared address serialise.  Within
-// a cell the order is not kept.
+// tile, each lane owning R consecutive slots:
+//   1. histogram of the cells (a lane whose R particles share a cell, the usual case,
+//      counts them with one shared atomic per warp and cell: many lanes adding to one
+//      shared address serialise);
+//   2. exclusive scan;
+//   3. destination slot of every particle (same grouping; within a cell the particles
+//      keep their order except around lanes that straddle a cell boundary), written as
+//      the permutation perm[destination] = source;
+//   4. copy in destination order: each lane reads its R destinations' sources (nearly
+//      consecutive slots) and writes R slots of every array with one 16-byte store.
 template <typename T, bool IDS>
-__global__ void __launch_bounds__(256) k_sort_tiles(ParticleArrays<T> src, ParticleArrays<T> dst) {
+__global__ void __launch_bounds__(256) k_sort_tiles(ParticleArrays<T> src, ParticleArrays<T> dst, int* perm) {
     constexpr int R = Prec<T>::R;
     __shared__ int hist[TILE_CELLS];
     __shared__ int wsum[8];
@@ -738,15 +756,32 @@ __global__ void __launch_bounds__(256) k_sort_tiles(ParticleArrays<T> src, Parti
         for (int r = 0; r < R; ++r)
             if (g >= ng || g * R + r >= cnt) c[r] = HOLE;
     };
+    // Slots for the particles of one lane group: lanes whose R particles share a cell
+    // take R consecutive slots per lane from one atomic of their warp group; the others
+    // take one slot per particle.  f(r, slot) receives the tile-relative slot.
+    auto claim = [&](const int c[R], auto f) {
+        bool uni = c[0] >= 0;
+#pragma unroll
+        for (int r = 1; r < R; ++r) uni = uni && c[r] == c[0];
+        const unsigned grp = __match_any_sync(0xffffffffu, uni ? c[0] : -1 - lane);
+        const int leader = __ffs(grp) - 1;
+        int b = 0;
+        if (uni && lane == leader) b = atomicAdd(&hist[c[0]], R * __popc(grp));
+        b = __shfl_sync(0xffffffffu, b, leader);
+        if (uni) {
+            const int b0 = b + R * __popc(grp & ((1u << lane) - 1u));
+#pragma unroll
+            for (int r = 0; r < R; ++r) f(r, b0 + r);
+        } else {
+#pragma unroll
+            for (int r = 0; r < R; ++r)
+                if (c[r] >= 0) f(r, atomicAdd(&hist[c[r]], 1));
+        }
+    };
     for (int base = 0; base < ng; base += 256) {
         int c[R];
         cells(base + threadIdx.x, c);
-#pragma unroll
-        for (int r = 0; r < R; ++r) {
-            const bool ok = c[r] >= 0;
-            const unsigned grp = __match_any_sync(0xffffffffu, ok ? c[r] : -1 - lane);
-            if (ok && lane == __ffs(grp) - 1) atomicAdd(&hist[c[r]], __popc(grp));
-        }
+        claim(c, [](int, int) {});
     }
     __syncthreads();
     // exclusive scan of the 512 counts: two per thread, warp scans, then warp offsets
@@ -764,46 +799,49 @@ __global__ void __launch_bounds__(256) k_sort_tiles(ParticleArrays<T> src, Parti
     const int excl = woff + incl - (a0 + a1);
     hist[2 * threadIdx.x] = excl;
     hist[2 * threadIdx.x + 1] = excl + a0;
+    __shared__ int s_alive;
     if (threadIdx.x == 255) {   // every thread has read count: the segment now holds no holes
         src.count[t] = woff + incl;
         src.holes[t] = 0;
+        s_alive = woff + incl;
     }
     __syncthreads();
     for (int base = 0; base < ng; base += 256) {
         const int g = base + threadIdx.x;
-        const long long p0 = seg + (long long)g * R;
-        int c[R], id[R];
-        T d[3][R], u[3][R], w[R];
+        int c[R];
         cells(g, c);
-        if (g < ng) {
+        claim(c, [&](int r, int slot) { perm[seg + slot] = g * R + r; });
+    }
+    __syncthreads();   // the block's permutation writes are visible to the block
+    const int alive = s_alive;
+    const int nout = (alive + R - 1) / R;
+    for (int g = threadIdx.x; g < nout; g += 256) {
+        const long long q0 = seg + (long long)g * R;
+        int from[R];
 #pragma unroll
-            for (int k = 0; k < 3; ++k) {
-                Slots<T, R>::ld(src.d[k] + p0, d[k]);
-                Slots<T, R>::ld(src.u[k] + p0, u[k]);
-            }
-            Slots<T, R>::ld(src.w + p0, w);
-            if (IDS) RowCells<R>::ld(src.id + p0, id);
-        }
+        for (int r = 0; r < R; ++r) from[r] = g * R + r < alive ? __ldcs(perm + q0 + r) : -1;
+        int cv[R], id[R];
+        T d[3][R], u[3][R], w[R];
 #pragma unroll
         for (int r = 0; r < R; ++r) {
-            const bool ok = c[r] >= 0;
-            const unsigned grp = __match_any_sync(0xffffffffu, ok ? c[r] : -1 - lane);
-            const int leader = __ffs(grp) - 1;
-            int b = 0;
-            if (ok && lane == leader) b = atomicAdd(&hist[c[r]], __popc(grp));
-            b = __shfl_sync(0xffffffffu, b, leader);
-            if (ok) {
-                const long long q = seg + b + __popc(grp & ((1u << lane) - 1u));
-                dst.cell[q] = c[r];
+            const long long p = seg + (from[r] < 0 ? 0 : from[r]);
+            cv[r] = src.cell[p];
 #pragma unroll
-                for (int k = 0; k < 3; ++k) {
-                    dst.d[k][q] = d[k][r];
-                    dst.u[k][q] = u[k][r];
-                }
-                dst.w[q] = w[r];
-                if (IDS) dst.id[q] = id[r];
+            for (int k = 0; k < 3; ++k) {
+                d[k][r] = src.d[k][p];
+                u[k][r] = src.u[k][p];
             }
+            w[r] = src.w[p];
+            if (IDS) id[r] = src.id[p];
         }
+        RowCells<R>::st(dst.cell + q0, cv);
+#pragma unroll
+        for (int k = 0; k < 3; ++k) {
+            Slots<T, R>::st(dst.d[k] + q0, d[k]);
+            Slots<T, R>::st(dst.u[k] + q0, u[k]);
+        }
+        Slots<T, R>::st(dst.w + q0, w);
+        if (IDS) RowCells<R>::st(dst.id + q0, id);
     }
 }
 
@@ -812,8 +850,9 @@ static pic_status sort_t(pic_ctx* c, SpeciesDev& s) {
     const int ntile = c->g.nt[0] * c->g.nt[1] * c->g.nt[2];
     {
         LaunchScope ls(c, KC_SORT);
-        if (c->desc.track_ids) k_sort_tiles<T, true><<<ntile, 256, 0, c->stream>>>(arrays<T>(s), arrays_alt<T>(s));
-        else k_sort_tiles<T, false><<<ntile, 256, 0, c->stream>>>(arrays<T>(s), arrays_alt<T>(s));
+        if (c->desc.track_ids)
+            k_sort_tiles<T, true><<<ntile, 256, 0, c->stream>>>(arrays<T>(s), arrays_alt<T>(s), s.perm);
+        else k_sort_tiles<T, false><<<ntile, 256, 0, c->stream>>>(arrays<T>(s), arrays_alt<T>(s), s.perm);
         GBPIC_CHECK(c, cudaGetLastError());
     }
     s.cur ^= 1;

@@ -158,7 +158,8 @@ static pic_status load_t(pic_ctx* c, const pic_species_desc* d, SpeciesDev& s) {
     const size_t bytes = pbytes + align256(sizeof(int) * ntile) * 4 + align256(sizeof(Counters));
     unsigned char* base = static_cast<unsigned char*>(dev_alloc(c, bytes));
     unsigned char* base2 = static_cast<unsigned char*>(dev_alloc(c, pbytes));
-    if (!base || !base2) return PIC_ERR_OOM;
+    s.perm = static_cast<int*>(dev_alloc(c, sizeof(int) * cap));
+    if (!base || !base2 || !s.perm) return PIC_ERR_OOM;
     s.base[0] = base;
     s.base[1] = base2;
     s.pbytes = pbytes;
