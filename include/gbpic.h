@@ -77,9 +77,8 @@ typedef struct pic_grid_desc {
                                 returns load order); 0: tile order, fewer bytes per step */
     int32_t record_every;    /* k > 0: record (U_E, U_B, K) of every k-th step on the device */
     int32_t history_capacity;/* records kept (ring); 0 with record_every > 0 -> 4096 */
-    int32_t sort_every;      /* re-sort each tile segment by cell every k steps (keeps the lanes of
-                                a warp in one cell and removes the slots of departed particles);
-                                0 -> 4, < 0 -> 16 */
+    int32_t sort_every;      /* unused (kept for layout): every step writes each tile's particles
+                                grouped by cell into the other particle block */
     pic_alloc_fn alloc;      /* optional */
     pic_free_fn free;        /* optional, required when alloc is set */
     void* alloc_user;

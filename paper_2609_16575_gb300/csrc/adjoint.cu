@@ -62,7 +62,8 @@ static pic_status snap_alloc(pic_ctx* c, Snapshot& S) {
     for (size_t i = 0; i < c->species.size(); ++i) {
         SpeciesDev& s = c->species[i];
         SpeciesSnap& z = S.sp[i];
-        if (!(z.part = dev_alloc(c, s.pbytes)) || !(z.counts = dev_alloc(c, 2 * sizeof(int) * ntiles(c))) ||
+        if (!(z.part = dev_alloc(c, s.pbytes)) ||
+            !(z.counts = dev_alloc(c, (2 + TILE_CELLS) * sizeof(int) * ntiles(c))) ||
             !(z.ctr = dev_alloc(c, sizeof(Counters))) || !(z.spill = dev_alloc(c, rec_bytes(c) * s.spill_cap)))
             return PIC_ERR_OOM;
     }
@@ -86,6 +87,8 @@ static pic_status snap_save(pic_ctx* c, Snapshot& S) {
         GBPIC_CHECK(c, cudaMemcpyAsync(z.counts, s.count, sizeof(int) * ntiles(c), cudaMemcpyDeviceToDevice, c->stream));
         GBPIC_CHECK(c, cudaMemcpyAsync(static_cast<int*>(z.counts) + ntiles(c), s.holes, sizeof(int) * ntiles(c),
                                        cudaMemcpyDeviceToDevice, c->stream));
+        GBPIC_CHECK(c, cudaMemcpyAsync(static_cast<int*>(z.counts) + 2 * ntiles(c), s.hist[s.cur],
+                                       sizeof(int) * TILE_CELLS * ntiles(c), cudaMemcpyDeviceToDevice, c->stream));
         GBPIC_CHECK(c, cudaMemcpyAsync(z.ctr, s.ctr, sizeof(Counters), cudaMemcpyDeviceToDevice, c->stream));
         GBPIC_CHECK(c, cudaMemcpyAsync(z.spill, s.spill, rec_bytes(c) * s.spill_cap, cudaMemcpyDeviceToDevice, c->stream));
     }
@@ -108,6 +111,8 @@ static pic_status snap_restore(pic_ctx* c, const Snapshot& S) {
         GBPIC_CHECK(c, cudaMemcpyAsync(s.count, z.counts, sizeof(int) * ntiles(c), cudaMemcpyDeviceToDevice, c->stream));
         GBPIC_CHECK(c, cudaMemcpyAsync(s.holes, static_cast<const int*>(z.counts) + ntiles(c), sizeof(int) * ntiles(c),
                                        cudaMemcpyDeviceToDevice, c->stream));
+        GBPIC_CHECK(c, cudaMemcpyAsync(s.hist[s.cur], static_cast<const int*>(z.counts) + 2 * ntiles(c),
+                                       sizeof(int) * TILE_CELLS * ntiles(c), cudaMemcpyDeviceToDevice, c->stream));
         GBPIC_CHECK(c, cudaMemcpyAsync(s.ctr, z.ctr, sizeof(Counters), cudaMemcpyDeviceToDevice, c->stream));
         GBPIC_CHECK(c, cudaMemcpyAsync(s.spill, z.spill, rec_bytes(c) * s.spill_cap, cudaMemcpyDeviceToDevice, c->stream));
     }

@@ -138,16 +138,9 @@ pic_status step_once(pic_ctx* c, double* rec, bool keep_j) {
     c->jscale_J = c->jscale;
     pic_status st = launch_faraday_half(c, rec);
     if (st != PIC_OK) return st;
-    // the re-sort also removes the holes departed particles leave, so it always runs
-    const int sort_every = c->desc.sort_every == 0 ? 4 : (c->desc.sort_every < 0 ? 16 : c->desc.sort_every);
-    const bool sort_now = (c->step + 1) % sort_every == 0;
     for (auto& sp : c->species) {
         st = launch_push_species(c, sp, (int)(c->step & 1), rec ? rec + 2 : nullptr);
         if (st != PIC_OK) return st;
-        if (sort_now) {
-            st = launch_sort(c, sp);
-            if (st != PIC_OK) return st;
-        }
     }
     st = launch_faraday_half(c, nullptr);
     if (st != PIC_OK) return st;

@@ -539,7 +539,7 @@ struct SpeciesDev {
     int* count = nullptr;
     int* cap = nullptr;
     int* holes = nullptr;
-    int* perm = nullptr;                  // re-sort scratch: source slot of every destination slot
+    int* hist[2] = {nullptr, nullptr};    // per tile and block: particles per cell (TILE_CELLS ints)
     void* movers = nullptr;
     int mover_cap = 0;
     void* spill = nullptr;
@@ -614,7 +614,6 @@ pic_status launch_faraday_half(pic_ctx* c, double* rec);
 pic_status launch_ampere(pic_ctx* c, bool zero_j);
 pic_status launch_push_species(pic_ctx* c, SpeciesDev& s, int parity, double* krec);
 pic_status launch_backpush(pic_ctx* c, SpeciesDev& s);
-pic_status launch_sort(pic_ctx* c, SpeciesDev& s);
 template <typename T> pic_status curl_to_b(pic_ctx* c, T* const E[3], T* const B[3], double coef);
 template <typename T> pic_status curl_to_e(pic_ctx* c, T* const E[3], T* const B[3], double coef);
 pic_status step_once(pic_ctx* c, double* rec, bool keep_j);

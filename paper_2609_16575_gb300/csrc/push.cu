@@ -15,7 +15,10 @@ namespace gbpic {
 
 template <typename T> struct PushArgs {
     Geom g;
-    ParticleArrays<T> pa;
+    ParticleArrays<T> pa;   // the block the step reads
+    ParticleArrays<T> pb;   // the block the step writes (tile kernel, append)
+    const int* hin;         // per tile: cell histogram of pa (TILE_CELLS ints)
+    int* hout;              // per tile: cell histogram of pb, built by the step
     Fields<T> f;
     T eps;          // q dt / (2 m)
     T dtd[3];       // dt / d_d
@@ -206,13 +209,17 @@ template <> struct RowCells<2> {
     static __device__ __forceinline__ int key(const int c[2]) { return c[0] >= 0 ? c[0] : c[1]; }
 };
 
-// One CTA per tile.  Lane l of warp w handles the R consecutive slots of slot group
-// 32 row + l for rows w, w + warps, ...: particles stay in their slots (a particle that
-// leaves the tile leaves a hole, which the periodic re-sort removes), so warps need no
-// block-wide step.  Because the segments are kept sorted by cell, a lane's R particles
-// nearly always start in one cell: their straight-segment currents are summed in
-// registers and each row ends with one warp flush of those sums; everything else goes
-// through the warp's record queue.
+// One CTA per tile.  The tile's particles are read from one SoA block and written to
+// the other, grouped by the cell each particle starts the step in: the block read is
+// grouped by the cells of the step before, so only the particles that crossed a cell
+// face last step (and the movers appended at the segment's end) are out of place.  The
+// output ranges come from the cell histogram of the input (kept from the previous
+// step); a particle that leaves the tile leaves a hole in its range, and the histogram
+// of the output's cells is built for the next step.  Lane l of warp w handles the R
+// consecutive input slots of slot group 32 row + l for rows w, w + warps, ...; a lane's
+// R particles nearly always start in one cell: their straight-segment currents are
+// summed in registers and each row ends with one warp flush of those sums; everything
+// else goes through the warp's record queue.
 template <typename T, bool IDS, bool RECK>
 __global__ void __launch_bounds__(Prec<T>::THREADS, Prec<T>::MINB)
 k_tile_push(const __grid_constant__ CUtensorMap tE0, const __grid_constant__ CUtensorMap tE1,
@@ -225,6 +232,7 @@ k_tile_push(const __grid_constant__ CUtensorMap tE0, const __grid_constant__ CUt
     constexpr int BX = Prec<T>::BX;
     constexpr int BS = box_stride<T>();
     static_assert(NW <= PUSH_WARPS_MAX, "tile kernel CTA too large");
+    static_assert(NT == 256, "the histogram scan assumes 256 threads");
     using P2 = typename Pair<T>::t;
     T* sF = reinterpret_cast<T*>(smem);                     // raw boxes, then the queues
     unsigned char* sQ = smem;
@@ -232,17 +240,28 @@ k_tile_push(const __grid_constant__ CUtensorMap tE0, const __grid_constant__ CUt
     unsigned char* sJ = smem + region_a_bytes<T>() + pairs_bytes<T>();
     const uint32_t sJa = smem_u32(sJ);
     uint64_t* bar = reinterpret_cast<uint64_t*>(sJ + jtile_bytes<T>());
-    __shared__ int s_timeout;
+    __shared__ int s_off[TILE_CELLS];   // next free output slot of each input cell's range
+    __shared__ int s_hn[TILE_CELLS];    // cell histogram of the output
+    __shared__ int s_wsum[NW];
+    __shared__ int s_timeout, s_total, s_left;
 
     const int tile = blockIdx.x;
     const int cnt = min(A.pa.count[tile], A.pa.cap[tile]);
-    if (cnt == 0) return;
+    const int* hin = A.hin + (size_t)tile * TILE_CELLS;
+    int* hout = A.hout + (size_t)tile * TILE_CELLS;
+    const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
+    if (cnt == 0) {
+        for (int i = threadIdx.x; i < TILE_CELLS; i += NT) hout[i] = 0;
+        if (threadIdx.x == 0) A.pa.holes[tile] = 0;
+        return;
+    }
     const int ntx = A.g.nt[0], nty = A.g.nt[1];
     const int tx = tile % ntx, ty = (tile / ntx) % nty, tz = tile / (ntx * nty);
     const int ox = tx * TILE, oy = ty * TILE, oz = tz * TILE;
 
     if (threadIdx.x == 0) {
         s_timeout = 0;
+        s_left = 0;
         mbar_init(bar, 1);
         fence_mbar_init();
     }
@@ -260,6 +279,26 @@ k_tile_push(const __grid_constant__ CUtensorMap tE0, const __grid_constant__ CUt
     {
         T* z = reinterpret_cast<T*>(sJ);
         for (int i = threadIdx.x; i < JT_ELEMS; i += NT) z[i] = T(0);
+    }
+    // output ranges: exclusive scan of the input histogram (two cells per thread)
+    {
+        const int a0 = hin[2 * threadIdx.x], a1 = hin[2 * threadIdx.x + 1];
+        int incl = a0 + a1;
+#pragma unroll
+        for (int o = 1; o < 32; o <<= 1) {
+            const int y = __shfl_up_sync(0xffffffffu, incl, o);
+            if (lane >= o) incl += y;
+        }
+        if (lane == 31) s_wsum[warp] = incl;
+        __syncthreads();
+        int woff = 0;
+        for (int w2 = 0; w2 < warp; ++w2) woff += s_wsum[w2];
+        const int excl = woff + incl - (a0 + a1);
+        s_off[2 * threadIdx.x] = excl;
+        s_off[2 * threadIdx.x + 1] = excl + a0;
+        s_hn[2 * threadIdx.x] = 0;
+        s_hn[2 * threadIdx.x + 1] = 0;
+        if (threadIdx.x == NT - 1) s_total = woff + incl;
     }
     {
         int polls = 0;
@@ -296,7 +335,6 @@ k_tile_push(const __grid_constant__ CUtensorMap tE0, const __grid_constant__ CUt
     };
 
     const int ext[3] = {min(TILE, A.g.n[0] - ox), min(TILE, A.g.n[1] - oy), min(TILE, A.g.n[2] - oz)};
-    const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
     WarpQueue<T> Q;
     Q.rec = reinterpret_cast<T*>(sQ) + (size_t)warp * 13 * QCAP;
     const int qoff = slot_offset(lane < 12 ? lane : (lane < 24 ? lane - 12 : 0));
@@ -321,7 +359,7 @@ k_tile_push(const __grid_constant__ CUtensorMap tE0, const __grid_constant__ CUt
         }
     };
     prefetch((warp * 32 + lane) * R);
-    int n_cells[R];               // the cells of the next row's R slots (for its key)
+    int n_cells[R];               // the cells of the next row's R slots
     auto prefetch_cells = [&](int i0) {
         if (i0 < cnt) RowCells<R>::ld(A.pa.cell + seg + i0, n_cells);
 #pragma unroll
@@ -333,6 +371,21 @@ k_tile_push(const __grid_constant__ CUtensorMap tE0, const __grid_constant__ CUt
     for (int row = warp; row * 32 < ngroups; row += NW) {
         P2 acc[6];                // summed straight-segment currents of start cell `key`
         int key = RowCells<R>::key(n_cells);
+        // output slots: a lane whose R particles start in one cell takes R consecutive
+        // slots of that cell's range with one shared atomic per warp and cell; the other
+        // lanes claim one slot per particle below
+        bool uni = n_cells[0] >= 0;
+#pragma unroll
+        for (int r = 1; r < R; ++r) uni = uni && n_cells[r] == n_cells[0];
+        int obase;
+        {
+            const unsigned grp = __match_any_sync(0xffffffffu, uni ? n_cells[0] : -1 - lane);
+            const int leader = __ffs(grp) - 1;
+            int b = 0;
+            if (uni && lane == leader) b = atomicAdd(&s_off[n_cells[0]], R * __popc(grp));
+            b = __shfl_sync(0xffffffffu, b, leader);
+            obase = uni ? b + R * __popc(grp & ((1u << lane) - 1u)) : -1;
+        }
 #pragma unroll
         for (int q = 0; q < 6; ++q) acc[q] = Pair<T>::splat(T(0));
         const int s0 = (row * 32 + lane) * R;   // first slot of this lane
@@ -348,7 +401,7 @@ k_tile_push(const __grid_constant__ CUtensorMap tE0, const __grid_constant__ CUt
             prefetch(r + 1 < R ? i + 1 : ((row + NW) * 32 + lane) * R);
             P2 v[6], v2[6];
             int s[3] = {0, 0, 0};
-            int x = 0, y = 0, z = 0;
+            int x = 0, y = 0, z = 0, nlc = -1;
             bool stay = false, move = false, crossed = false;
             if (active) {
                 x = lc & 7;
@@ -392,17 +445,26 @@ k_tile_push(const __grid_constant__ CUtensorMap tE0, const __grid_constant__ CUt
                 const int nx = x + s[0], ny = y + s[1], nz = z + s[2];
                 stay = nx >= 0 && nx < ext[0] && ny >= 0 && ny < ext[1] && nz >= 0 && nz < ext[2];
                 move = !stay;
-                // in place: the stayer's new state, or a hole
-                __stcs(A.pa.cell + p, stay ? (nx | (ny << 3) | (nz << 6)) : HOLE);
+                if (stay) nlc = nx | (ny << 3) | (nz << 6);
+                // the particle's slot in its start cell's output range: the state after
+                // the step, or a hole
+                const long long o = seg + (obase >= 0 ? obase + r : atomicAdd(&s_off[lc], 1));
+                __stcs(A.pb.cell + o, stay ? nlc : HOLE);
                 if (stay) {
 #pragma unroll
                     for (int k = 0; k < 3; ++k) {
-                        __stcs(A.pa.d[k] + p, d2[k]);
-                        __stcs(A.pa.u[k] + p, u[k]);
+                        __stcs(A.pb.d[k] + o, d2[k]);
+                        __stcs(A.pb.u[k] + o, u[k]);
                     }
+                    __stcs(A.pb.w + o, w);
+                    if (IDS) __stcs(A.pb.id + o, __ldg(A.pa.id + p));
                 } else {
                     ++left;
                 }
+            }
+            {   // cell histogram of the output, one shared atomic per warp and cell
+                const unsigned grp = __match_any_sync(0xffffffffu, nlc >= 0 ? nlc : -1 - lane);
+                if (nlc >= 0 && lane == __ffs(grp) - 1) atomicAdd(&s_hn[nlc], __popc(grp));
             }
             const bool summed = active && lc == key;
             if (summed) {
@@ -447,8 +509,15 @@ k_tile_push(const __grid_constant__ CUtensorMap tE0, const __grid_constant__ CUt
         flush_warp<T>(acc, key >= 0 ? tile_index(0, key & 7, (key >> 3) & 7, key >> 6) : -1, lane, Q, sJa, qoff);
     }
     for (int o = 16; o > 0; o >>= 1) left += __shfl_xor_sync(0xffffffffu, left, o);
-    if (lane == 0 && left) atomicAdd(A.pa.holes + tile, left);
+    if (lane == 0 && left) atomicAdd(&s_left, left);
     __syncthreads();
+    // the output segment: the input cells' ranges (with the holes of the departed) and,
+    // appended later, this step's arrivals
+    for (int i = threadIdx.x; i < TILE_CELLS; i += NT) hout[i] = s_hn[i];
+    if (threadIdx.x == 0) {
+        A.pa.count[tile] = s_total;
+        A.pa.holes[tile] = s_left;
+    }
 
     // flush the shared J tile to HBM (periodic wrap of the guard layers)
     for (int e = threadIdx.x; e < JT_ELEMS; e += NT) {
@@ -525,8 +594,9 @@ __global__ void __launch_bounds__(256) k_list_push(PushArgs<T> A) {
     }
 }
 
-// Movers into the segment of their new tile; a full segment sends them to the
-// spill list of the next step.  Also resets the counters of the other parity.
+// Movers into the end of the segment of their new tile in the block the step writes
+// (and into that tile's cell histogram); a full segment sends them to the spill list of
+// the next step.  Also resets the counters of the other parity.
 template <typename T, bool IDS>
 __global__ void __launch_bounds__(256) k_append(PushArgs<T> A) {
     const int n = min(A.ctr->mover_count[A.parity], A.mover_cap);
@@ -540,18 +610,20 @@ __global__ void __launch_bounds__(256) k_append(PushArgs<T> A) {
         const int gx = r.cell % A.g.n[0], gy = (r.cell / A.g.n[0]) % A.g.n[1], gz = r.cell / (A.g.n[0] * A.g.n[1]);
         const int tx = gx >> 3, ty = gy >> 3, tz = gz >> 3;
         const int t = (tz * A.g.nt[1] + ty) * A.g.nt[0] + tx;
-        const int slot = atomicAdd(A.pa.count + t, 1);
-        if (slot < A.pa.cap[t]) {
-            const long long q = (long long)A.pa.seg_start[t] + slot;
-            A.pa.cell[q] = (gx & 7) | ((gy & 7) << 3) | ((gz & 7) << 6);
-            A.pa.d[0][q] = r.d[0];
-            A.pa.d[1][q] = r.d[1];
-            A.pa.d[2][q] = r.d[2];
-            A.pa.u[0][q] = r.u[0];
-            A.pa.u[1][q] = r.u[1];
-            A.pa.u[2][q] = r.u[2];
-            A.pa.w[q] = r.w;
-            if (IDS) A.pa.id[q] = r.id;
+        const int slot = atomicAdd(A.pb.count + t, 1);
+        if (slot < A.pb.cap[t]) {
+            const long long q = (long long)A.pb.seg_start[t] + slot;
+            const int lc = (gx & 7) | ((gy & 7) << 3) | ((gz & 7) << 6);
+            A.pb.cell[q] = lc;
+            A.pb.d[0][q] = r.d[0];
+            A.pb.d[1][q] = r.d[1];
+            A.pb.d[2][q] = r.d[2];
+            A.pb.u[0][q] = r.u[0];
+            A.pb.u[1][q] = r.u[1];
+            A.pb.u[2][q] = r.u[2];
+            A.pb.w[q] = r.w;
+            if (IDS) A.pb.id[q] = r.id;
+            atomicAdd(A.hout + (size_t)t * TILE_CELLS + lc, 1);
         } else {
             const int sp = atomicAdd(&A.ctr->spill_count[nxt], 1);
             if (sp < A.spill_cap) A.spill[sp] = r;
@@ -596,6 +668,9 @@ static PushArgs<T> make_args(pic_ctx* c, SpeciesDev& s, int parity, double* krec
     PushArgs<T> A{};
     A.g = c->g;
     A.pa = arrays<T>(s);
+    A.pb = arrays_alt<T>(s);
+    A.hin = s.hist[s.cur];
+    A.hout = s.hist[s.cur ^ 1];
     for (int k = 0; k < 3; ++k) {
         A.f.E[k] = static_cast<T*>(c->E[k]);
         A.f.B[k] = static_cast<T*>(c->B[k]);
@@ -663,6 +738,7 @@ static pic_status push_species_t(pic_ctx* c, SpeciesDev& s, int parity, double* 
         else k_append<T, false><<<grid, 256, 0, c->stream>>>(A);
         GBPIC_CHECK(c, cudaGetLastError());
     }
+    s.cur ^= 1;   // the block just written holds the particles now
     return PIC_OK;
 }
 
@@ -699,168 +775,6 @@ static pic_status backpush_t(pic_ctx* c, SpeciesDev& s) {
 
 pic_status launch_backpush(pic_ctx* c, SpeciesDev& s) {
     return c->prec == PIC_FP64 ? backpush_t<double>(c, s) : backpush_t<float>(c, s);
-}
-
-// R consecutive slots of one working-precision array: one 16-byte load.
-template <typename T, int R> struct Slots;
-template <> struct Slots<float, 4> {
-    static __device__ __forceinline__ void ld(const float* p, float v[4]) {
-        const float4 a = __ldcs(reinterpret_cast<const float4*>(p));
-        v[0] = a.x; v[1] = a.y; v[2] = a.z; v[3] = a.w;
-    }
-    static __device__ __forceinline__ void st(float* p, const float v[4]) {
-        __stcs(reinterpret_cast<float4*>(p), make_float4(v[0], v[1], v[2], v[3]));
-    }
-};
-template <> struct Slots<double, 2> {
-    static __device__ __forceinline__ void ld(const double* p, double v[2]) {
-        const double2 a = __ldcs(reinterpret_cast<const double2*>(p));
-        v[0] = a.x; v[1] = a.y;
-    }
-    static __device__ __forceinline__ void st(double* p, const double v[2]) {
-        __stcs(reinterpret_cast<double2*>(p), make_double2(v[0], v[1]));
-    }
-};
-
-// Counting sort of every tile segment by local cell (ping-pong between the two SoA
-// blocks of a species), dropping the holes.  Restores the cell order that moves and
-// the appended movers erode, so that the lanes of a warp share cells (the gather then
-// reads broadcast shared-memory values) and a lane's consecutive particles share their
-// start cell (the deposit then sums them in registers).  One CTA of 256 threads per
-// tile, each lane owning R consecutive slots:
-//   1. histogram of the cells (a lane whose R particles share a cell, the usual case,
-//      counts them with one shared atomic per warp and cell: many lanes adding to one
-//      shared address serialise);
-//   2. exclusive scan;
-//   3. destination slot of every particle (same grouping; within a cell the particles
-//      keep their order except around lanes that straddle a cell boundary), written as
-//      the permutation perm[destination] = source;
-//   4. copy in destination order: each lane reads its R destinations' sources (nearly
-//      consecutive slots) and writes R slots of every array with one 16-byte store.
-template <typename T, bool IDS>
-__global__ void __launch_bounds__(256) k_sort_tiles(ParticleArrays<T> src, ParticleArrays<T> dst, int* perm) {
-    constexpr int R = Prec<T>::R;
-    __shared__ int hist[TILE_CELLS];
-    __shared__ int wsum[8];
-    const int t = blockIdx.x;
-    const int cnt = min(src.count[t], src.cap[t]);
-    if (cnt == 0) return;
-    const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
-    for (int i = threadIdx.x; i < TILE_CELLS; i += 256) hist[i] = 0;
-    __syncthreads();
-    const long long seg = src.seg_start[t];
-    const int ng = (cnt + R - 1) / R;
-    auto cells = [&](int g, int c[R]) {
-        if (g < ng) RowCells<R>::ld(src.cell + seg + (long long)g * R, c);
-#pragma unroll
-        for (int r = 0; r < R; ++r)
-            if (g >= ng || g * R + r >= cnt) c[r] = HOLE;
-    };
-    // Slots for the particles of one lane group: lanes whose R particles share a cell
-    // take R consecutive slots per lane from one atomic of their warp group; the others
-    // take one slot per particle.  f(r, slot) receives the tile-relative slot.
-    auto claim = [&](const int c[R], auto f) {
-        bool uni = c[0] >= 0;
-#pragma unroll
-        for (int r = 1; r < R; ++r) uni = uni && c[r] == c[0];
-        const unsigned grp = __match_any_sync(0xffffffffu, uni ? c[0] : -1 - lane);
-        const int leader = __ffs(grp) - 1;
-        int b = 0;
-        if (uni && lane == leader) b = atomicAdd(&hist[c[0]], R * __popc(grp));
-        b = __shfl_sync(0xffffffffu, b, leader);
-        if (uni) {
-            const int b0 = b + R * __popc(grp & ((1u << lane) - 1u));
-#pragma unroll
-            for (int r = 0; r < R; ++r) f(r, b0 + r);
-        } else {
-#pragma unroll
-            for (int r = 0; r < R; ++r)
-                if (c[r] >= 0) f(r, atomicAdd(&hist[c[r]], 1));
-        }
-    };
-    for (int base = 0; base < ng; base += 256) {
-        int c[R];
-        cells(base + threadIdx.x, c);
-        claim(c, [](int, int) {});
-    }
-    __syncthreads();
-    // exclusive scan of the 512 counts: two per thread, warp scans, then warp offsets
-    const int a0 = hist[2 * threadIdx.x], a1 = hist[2 * threadIdx.x + 1];
-    int incl = a0 + a1;
-#pragma unroll
-    for (int o = 1; o < 32; o <<= 1) {
-        const int y = __shfl_up_sync(0xffffffffu, incl, o);
-        if (lane >= o) incl += y;
-    }
-    if (lane == 31) wsum[warp] = incl;
-    __syncthreads();
-    int woff = 0;
-    for (int w2 = 0; w2 < warp; ++w2) woff += wsum[w2];
-    const int excl = woff + incl - (a0 + a1);
-    hist[2 * threadIdx.x] = excl;
-    hist[2 * threadIdx.x + 1] = excl + a0;
-    __shared__ int s_alive;
-    if (threadIdx.x == 255) {   // every thread has read count: the segment now holds no holes
-        src.count[t] = woff + incl;
-        src.holes[t] = 0;
-        s_alive = woff + incl;
-    }
-    __syncthreads();
-    for (int base = 0; base < ng; base += 256) {
-        const int g = base + threadIdx.x;
-        int c[R];
-        cells(g, c);
-        claim(c, [&](int r, int slot) { perm[seg + slot] = g * R + r; });
-    }
-    __syncthreads();   // the block's permutation writes are visible to the block
-    const int alive = s_alive;
-    const int nout = (alive + R - 1) / R;
-    for (int g = threadIdx.x; g < nout; g += 256) {
-        const long long q0 = seg + (long long)g * R;
-        int from[R];
-#pragma unroll
-        for (int r = 0; r < R; ++r) from[r] = g * R + r < alive ? __ldcs(perm + q0 + r) : -1;
-        int cv[R], id[R];
-        T d[3][R], u[3][R], w[R];
-#pragma unroll
-        for (int r = 0; r < R; ++r) {
-            const long long p = seg + (from[r] < 0 ? 0 : from[r]);
-            cv[r] = src.cell[p];
-#pragma unroll
-            for (int k = 0; k < 3; ++k) {
-                d[k][r] = src.d[k][p];
-                u[k][r] = src.u[k][p];
-            }
-            w[r] = src.w[p];
-            if (IDS) id[r] = src.id[p];
-        }
-        RowCells<R>::st(dst.cell + q0, cv);
-#pragma unroll
-        for (int k = 0; k < 3; ++k) {
-            Slots<T, R>::st(dst.d[k] + q0, d[k]);
-            Slots<T, R>::st(dst.u[k] + q0, u[k]);
-        }
-        Slots<T, R>::st(dst.w + q0, w);
-        if (IDS) RowCells<R>::st(dst.id + q0, id);
-    }
-}
-
-template <typename T>
-static pic_status sort_t(pic_ctx* c, SpeciesDev& s) {
-    const int ntile = c->g.nt[0] * c->g.nt[1] * c->g.nt[2];
-    {
-        LaunchScope ls(c, KC_SORT);
-        if (c->desc.track_ids)
-            k_sort_tiles<T, true><<<ntile, 256, 0, c->stream>>>(arrays<T>(s), arrays_alt<T>(s), s.perm);
-        else k_sort_tiles<T, false><<<ntile, 256, 0, c->stream>>>(arrays<T>(s), arrays_alt<T>(s), s.perm);
-        GBPIC_CHECK(c, cudaGetLastError());
-    }
-    s.cur ^= 1;
-    return PIC_OK;
-}
-
-pic_status launch_sort(pic_ctx* c, SpeciesDev& s) {
-    return c->prec == PIC_FP64 ? sort_t<double>(c, s) : sort_t<float>(c, s);
 }
 
 }  // namespace gbpic

@@ -158,8 +158,9 @@ static pic_status load_t(pic_ctx* c, const pic_species_desc* d, SpeciesDev& s) {
     const size_t bytes = pbytes + align256(sizeof(int) * ntile) * 4 + align256(sizeof(Counters));
     unsigned char* base = static_cast<unsigned char*>(dev_alloc(c, bytes));
     unsigned char* base2 = static_cast<unsigned char*>(dev_alloc(c, pbytes));
-    s.perm = static_cast<int*>(dev_alloc(c, sizeof(int) * cap));
-    if (!base || !base2 || !s.perm) return PIC_ERR_OOM;
+    s.hist[0] = static_cast<int*>(dev_alloc(c, sizeof(int) * (size_t)nkeys));
+    s.hist[1] = static_cast<int*>(dev_alloc(c, sizeof(int) * (size_t)nkeys));
+    if (!base || !base2 || !s.hist[0] || !s.hist[1]) return PIC_ERR_OOM;
     s.base[0] = base;
     s.base[1] = base2;
     s.pbytes = pbytes;
@@ -189,6 +190,8 @@ static pic_status load_t(pic_ctx* c, const pic_species_desc* d, SpeciesDev& s) {
     GBPIC_CHECK(c, cudaMemcpyAsync(s.seg_start, s.h_seg_start.data(), sizeof(int) * ntile, cudaMemcpyHostToDevice, c->stream));
     GBPIC_CHECK(c, cudaMemcpyAsync(s.count, h_count.data(), sizeof(int) * ntile, cudaMemcpyHostToDevice, c->stream));
     GBPIC_CHECK(c, cudaMemcpyAsync(s.cap, s.h_cap.data(), sizeof(int) * ntile, cudaMemcpyHostToDevice, c->stream));
+    // the cell histogram of the loaded block (the tile kernel's output ranges)
+    GBPIC_CHECK(c, cudaMemcpyAsync(s.hist[0], h_hist.data(), sizeof(int) * nkeys, cudaMemcpyHostToDevice, c->stream));
     if (n > 0) {
         LaunchScope ls(c, KC_OTHER);
         k_scatter<T><<<grid, 256, 0, c->stream>>>(g, X, U, W, n, hist, pa, c->desc.track_ids);
