@@ -187,13 +187,29 @@ __device__ __forceinline__ void acc_atomic(long long* p, long long v) {
 }
 __device__ __forceinline__ void acc_atomic(double* p, double v) { atomicAdd(p, v); }
 
-// Shared-memory J tile of the tile kernel: FP32 elements on the FP32 path, FP64 on the
-// FP64 path, added to with native shared-memory float reductions (byte address).
-__device__ __forceinline__ void tile_red(uint32_t addr, float v) {
-    asm volatile("red.shared.add.f32 [%0], %1;" ::"r"(addr), "f"(v) : "memory");
+// Shared-memory J tile of the tile kernel (element e of NE).  FP32 path: each element
+// is a 64-bit fixed-point sum kept as two 32-bit words, lo (bits 0..19 of every term,
+// unsigned) at word e and hi (the rest, signed, in units of 2^20) at word NE + e, both
+// added with native 32-bit shared reductions (no carry: lo stays below 2^32 for up to
+// 4096 terms); the element is hi * 2^20 + lo, an exact integer sum in any order.  The
+// value v (fixed-point units as a float) is split exactly: hi = floor(v / 2^20), and
+// lo = rint(v - hi * 2^20), an integer in [0, 2^20].  FP64 path: FP64 elements.
+__device__ __forceinline__ void tile_add(uint32_t base, int e, int NE, float v) {
+    const float hf = floorf(v * 9.5367431640625e-07f);           // v / 2^20
+    const int hi = __float2int_rz(hf);
+    const unsigned lo = (unsigned)__float2int_rn(__fmaf_rn(hf, -1048576.0f, v));
+    asm volatile("red.shared.add.u32 [%0], %1;" ::"r"(base + 4u * e), "r"(lo) : "memory");
+    asm volatile("red.shared.add.u32 [%0], %1;" ::"r"(base + 4u * (NE + e)), "r"((unsigned)hi) : "memory");
 }
-__device__ __forceinline__ void tile_red(uint32_t addr, double v) {
-    asm volatile("red.shared.add.f64 [%0], %1;" ::"r"(addr), "d"(v) : "memory");
+__device__ __forceinline__ void tile_add(uint32_t base, int e, int, double v) {
+    asm volatile("red.shared.add.f64 [%0], %1;" ::"r"(base + 8u * e), "d"(v) : "memory");
+}
+__device__ __forceinline__ long long tile_get(const unsigned char* s, int e, int NE, float) {
+    const unsigned* w = reinterpret_cast<const unsigned*>(s);
+    return ((long long)(int)w[NE + e] << 20) + (long long)w[e];
+}
+__device__ __forceinline__ double tile_get(const unsigned char* s, int e, int, double) {
+    return reinterpret_cast<const double*>(s)[e];
 }
 
 // 2 / x: the FP32 path uses the fast approximate division (error ~2 ulp, far inside

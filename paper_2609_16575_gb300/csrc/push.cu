@@ -38,7 +38,7 @@ template <typename T> __host__ __device__ constexpr int box_stride() {
     // each staged box starts on a 128-byte boundary
     return ((box_elems<T>() * (int)sizeof(T) + 127) / 128) * 128 / (int)sizeof(T);
 }
-constexpr int JT_ELEMS = 3 * SJ3;   // elements of the shared J tile (working precision)
+constexpr int JT_ELEMS = 3 * SJ3;   // elements of the shared J tile (8 bytes each: see tile_add)
 constexpr int QCAP_ = 64;   // record queue per warp (QCAP below)
 constexpr int PSX = 10, PSY = 10, PSZ = 9;   // z-paired staged fields: x, y -1..8, pair base z -1..7
 constexpr int PS = PSX * PSY * PSZ;          // pairs per component
@@ -53,7 +53,7 @@ template <typename T> __host__ __device__ constexpr size_t region_a_bytes() {
                         : (size_t)(Prec<T>::THREADS / 32) * QCAP_ * 13 * sizeof(T));
 }
 template <typename T> __host__ __device__ constexpr size_t pairs_bytes() { return align128((size_t)6 * PS * 2 * sizeof(T)); }
-template <typename T> __host__ __device__ constexpr size_t jtile_bytes() { return align128((size_t)JT_ELEMS * sizeof(T)); }
+template <typename T> __host__ __device__ constexpr size_t jtile_bytes() { return align128((size_t)JT_ELEMS * 8); }
 template <typename T> constexpr size_t tile_smem_bytes() {
     // + 128: the kernel rounds the dynamic shared base up to a 128-byte boundary
     return region_a_bytes<T>() + pairs_bytes<T>() + jtile_bytes<T>() + 16 + 128;
@@ -136,7 +136,7 @@ __device__ __forceinline__ void q_drain(WarpQueue<T> Q, int& qn, int lane, uint3
     __syncwarp();
     if (lane < 24) {
         const int h = lane >= 12 ? 1 : 0, q = lane - 12 * h;
-        for (int j = h; j < qn; j += 2) tile_red(sJa + (uint32_t)sizeof(T) * (Q.key(j) + qoff), Q.rec[j * 13 + q]);
+        for (int j = h; j < qn; j += 2) tile_add(sJa, Q.key(j) + qoff, JT_ELEMS, Q.rec[j * 13 + q]);
     }
     __syncwarp();
     qn = 0;
@@ -167,14 +167,14 @@ __device__ __forceinline__ void flush_warp(const typename Pair<T>::t acc[6], int
             const int k = Q.key(j);
             const T v = Q.rec[j * 13 + q];
             if (k != ck) {
-                if (ck >= 0 && sum != T(0)) tile_red(sJa + (uint32_t)sizeof(T) * (ck + qoff), sum);
+                if (ck >= 0 && sum != T(0)) tile_add(sJa, ck + qoff, JT_ELEMS, sum);
                 ck = k;
                 sum = v;
             } else {
                 sum += v;
             }
         }
-        if (ck >= 0 && sum != T(0)) tile_red(sJa + (uint32_t)sizeof(T) * (ck + qoff), sum);
+        if (ck >= 0 && sum != T(0)) tile_add(sJa, ck + qoff, JT_ELEMS, sum);
     }
     __syncwarp();
 }
@@ -232,7 +232,7 @@ k_tile_push(const __grid_constant__ CUtensorMap tE0, const __grid_constant__ CUt
     constexpr int BX = Prec<T>::BX;
     constexpr int BS = box_stride<T>();
     static_assert(NW <= PUSH_WARPS_MAX, "tile kernel CTA too large");
-    static_assert(NT == 256, "the histogram scan assumes 256 threads");
+    static_assert(NT >= 256 && NT % 32 == 0, "the histogram scan uses the first 256 threads");
     using P2 = typename Pair<T>::t;
     T* sF = reinterpret_cast<T*>(smem);                     // raw boxes, then the queues
     unsigned char* sQ = smem;
@@ -242,7 +242,7 @@ k_tile_push(const __grid_constant__ CUtensorMap tE0, const __grid_constant__ CUt
     uint64_t* bar = reinterpret_cast<uint64_t*>(sJ + jtile_bytes<T>());
     __shared__ int s_off[TILE_CELLS];   // next free output slot of each input cell's range
     __shared__ int s_hn[TILE_CELLS];    // cell histogram of the output
-    __shared__ int s_wsum[NW];
+    __shared__ int s_wsum[8];
     __shared__ int s_timeout, s_total, s_left;
 
     const int tile = blockIdx.x;
@@ -277,28 +277,32 @@ k_tile_push(const __grid_constant__ CUtensorMap tE0, const __grid_constant__ CUt
         tma_load_3d(sF + 5 * BS, &tB2, ox, oy, oz, bar);
     }
     {
-        T* z = reinterpret_cast<T*>(sJ);
-        for (int i = threadIdx.x; i < JT_ELEMS; i += NT) z[i] = T(0);
+        unsigned long long* z = reinterpret_cast<unsigned long long*>(sJ);
+        for (int i = threadIdx.x; i < JT_ELEMS; i += NT) z[i] = 0ull;
     }
-    // output ranges: exclusive scan of the input histogram (two cells per thread)
+    // output ranges: exclusive scan of the input histogram (two cells per thread of the
+    // first 256 threads)
     {
-        const int a0 = hin[2 * threadIdx.x], a1 = hin[2 * threadIdx.x + 1];
+        const bool sc = threadIdx.x < 256;
+        const int a0 = sc ? hin[2 * threadIdx.x] : 0, a1 = sc ? hin[2 * threadIdx.x + 1] : 0;
         int incl = a0 + a1;
 #pragma unroll
         for (int o = 1; o < 32; o <<= 1) {
             const int y = __shfl_up_sync(0xffffffffu, incl, o);
             if (lane >= o) incl += y;
         }
-        if (lane == 31) s_wsum[warp] = incl;
+        if (lane == 31 && sc) s_wsum[warp] = incl;
         __syncthreads();
-        int woff = 0;
-        for (int w2 = 0; w2 < warp; ++w2) woff += s_wsum[w2];
-        const int excl = woff + incl - (a0 + a1);
-        s_off[2 * threadIdx.x] = excl;
-        s_off[2 * threadIdx.x + 1] = excl + a0;
-        s_hn[2 * threadIdx.x] = 0;
-        s_hn[2 * threadIdx.x + 1] = 0;
-        if (threadIdx.x == NT - 1) s_total = woff + incl;
+        if (sc) {
+            int woff = 0;
+            for (int w2 = 0; w2 < warp; ++w2) woff += s_wsum[w2];
+            const int excl = woff + incl - (a0 + a1);
+            s_off[2 * threadIdx.x] = excl;
+            s_off[2 * threadIdx.x + 1] = excl + a0;
+            s_hn[2 * threadIdx.x] = 0;
+            s_hn[2 * threadIdx.x + 1] = 0;
+            if (threadIdx.x == 255) s_total = woff + incl;
+        }
     }
     {
         int polls = 0;
@@ -521,9 +525,8 @@ k_tile_push(const __grid_constant__ CUtensorMap tE0, const __grid_constant__ CUt
 
     // flush the shared J tile to HBM (periodic wrap of the guard layers)
     for (int e = threadIdx.x; e < JT_ELEMS; e += NT) {
-        const T tv = reinterpret_cast<const T*>(sJ)[e];
-        if (tv == T(0)) continue;
-        const Acc v = to_acc(tv);
+        const Acc v = tile_get(sJ, e, JT_ELEMS, T(0));
+        if (v == Acc(0)) continue;
         const int comp = e / SJ3;
         const int r = e - comp * SJ3;
         const int lx = r % SJ - 1, ly = (r / SJ) % SJ - 1, lz = r / (SJ * SJ) - 1;
