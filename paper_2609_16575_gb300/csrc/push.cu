@@ -48,9 +48,9 @@ constexpr int PS = PSX * PSY * PSZ;          // pairs per component
 // 128 bytes.
 __host__ __device__ constexpr size_t align128(size_t b) { return (b + 127) / 128 * 128; }
 template <typename T> __host__ __device__ constexpr size_t region_a_bytes() {
-    return align128((size_t)6 * box_stride<T>() * sizeof(T) > (size_t)(Prec<T>::THREADS / 32) * QCAP_ * 13 * sizeof(T)
+    return align128((size_t)6 * box_stride<T>() * sizeof(T) > (size_t)(Prec<T>::THREADS / 32) * QCAP_ * 14 * sizeof(T)
                         ? (size_t)6 * box_stride<T>() * sizeof(T)
-                        : (size_t)(Prec<T>::THREADS / 32) * QCAP_ * 13 * sizeof(T));
+                        : (size_t)(Prec<T>::THREADS / 32) * QCAP_ * 14 * sizeof(T));
 }
 template <typename T> __host__ __device__ constexpr size_t pairs_bytes() { return align128((size_t)6 * PS * 2 * sizeof(T)); }
 template <typename T> __host__ __device__ constexpr size_t jtile_bytes() { return align128((size_t)JT_ELEMS * 8); }
@@ -105,38 +105,40 @@ __device__ __forceinline__ int slot_offset(int q) {
 // push and the drain free of bank conflicts.
 constexpr int QCAP = QCAP_;   // records per warp: a particle step adds at most 64 (the queue is
                               // drained after every step that added some), a flush stages 32
+constexpr int QS = 14;        // words per record: 12 values, the key, one pad (pairs stay aligned)
 template <typename T> struct WarpQueue {
-    T* rec;      // [QCAP][13]
-    __device__ __forceinline__ int& key(int j) const { return *reinterpret_cast<int*>(rec + j * 13 + 12); }
+    T* rec;      // [QCAP][QS]
+    __device__ __forceinline__ int& key(int j) const { return *reinterpret_cast<int*>(rec + j * QS + 12); }
+    __device__ __forceinline__ void put(int j, int k, const typename Pair<T>::t v[6]) const {
+        typename Pair<T>::t* r = reinterpret_cast<typename Pair<T>::t*>(rec + j * QS);
+#pragma unroll
+        for (int q = 0; q < 6; ++q) r[q] = v[q];
+        key(j) = k;
+    }
 };
 
-// Append the 12 values v of the cell with origin index k for every lane with `want`
-// (warp-collective).
+// Append, for every lane, the record (ka, va) if want_a and (kb, vb) if want_b: 12
+// values of the cell with origin index k (warp-collective).
 template <typename T>
-__device__ __forceinline__ void q_push(WarpQueue<T> Q, int& qn, bool want, int k, const typename Pair<T>::t v[6],
-                                       int lane) {
-    const unsigned m = __ballot_sync(0xffffffffu, want);
-    if (!m) return;
-    if (want) {
-        const int slot = qn + __popc(m & ((1u << lane) - 1u));
-        Q.key(slot) = k;
-#pragma unroll
-        for (int q = 0; q < 6; ++q) {
-            Q.rec[slot * 13 + 2 * q] = v[q].x;
-            Q.rec[slot * 13 + 2 * q + 1] = v[q].y;
-        }
-    }
-    qn += __popc(m);
+__device__ __forceinline__ void q_push(WarpQueue<T> Q, int& qn, bool want_a, int ka, const typename Pair<T>::t va[6],
+                                       bool want_b, int kb, const typename Pair<T>::t vb[6], int lane) {
+    const unsigned ma = __ballot_sync(0xffffffffu, want_a), mb = __ballot_sync(0xffffffffu, want_b);
+    if (!(ma | mb)) return;
+    const unsigned lt = (1u << lane) - 1u;
+    if (want_a) Q.put(qn + __popc(ma & lt), ka, va);
+    if (want_b) Q.put(qn + __popc(ma) + __popc(mb & lt), kb, vb);
+    qn += __popc(ma) + __popc(mb);
 }
 
 // Add every queued record to the shared J tile: lane 12h + q (h = 0, 1) adds value q of
-// records 2j + h; sJa is the tile's byte address, qoff this lane's slot offset.
+// records 2j + h; sJa is the tile's byte address, qoff this lane's slot offset.  The two
+// records of a pass lie QS words apart: their 24 words fall in distinct banks.
 template <typename T>
 __device__ __forceinline__ void q_drain(WarpQueue<T> Q, int& qn, int lane, uint32_t sJa, int qoff) {
     __syncwarp();
     if (lane < 24) {
         const int h = lane >= 12 ? 1 : 0, q = lane - 12 * h;
-        for (int j = h; j < qn; j += 2) tile_add(sJa, Q.key(j) + qoff, JT_ELEMS, Q.rec[j * 13 + q]);
+        for (int j = h; j < qn; j += 2) tile_add(sJa, Q.key(j) + qoff, JT_ELEMS, Q.rec[j * QS + q]);
     }
     __syncwarp();
     qn = 0;
@@ -144,35 +146,38 @@ __device__ __forceinline__ void q_drain(WarpQueue<T> Q, int& qn, int lane, uint3
 
 // Warp flush of per-lane current sums acc (12 edge values of the cell with origin
 // index key, or none for key < 0) into the shared J tile.  The 32 sums are staged in
-// the (empty) record queue; then lane 12h + q walks records 16h .. 16h + 15 of value q
-// and adds one sum per run of equal keys.  The segments being sorted by cell, the keys
-// of a warp form a few runs, so a flush costs a few atomics per value instead of 32
-// (shared atomics from many lanes on one address serialise).
+// the (empty) record queue (the second half 16 words further, so that the two halves'
+// reads fall in distinct banks); then lane 12h + q walks records 16h .. 16h + 15 of
+// value q and adds one sum per run of equal keys.  The segments being sorted by cell,
+// the keys of a warp form a few runs, so a flush costs a few atomics per value instead
+// of 32 (shared atomics from many lanes on one address serialise).  A run ends for all
+// lanes of a half at once; the additions of both halves are issued together.
 template <typename T>
 __device__ __forceinline__ void flush_warp(const typename Pair<T>::t acc[6], int key, int lane, WarpQueue<T> Q,
                                            uint32_t sJa, int qoff) {
-#pragma unroll
-    for (int q = 0; q < 6; ++q) {
-        Q.rec[lane * 13 + 2 * q] = acc[q].x;
-        Q.rec[lane * 13 + 2 * q + 1] = acc[q].y;
-    }
-    Q.key(lane) = key;
+    WarpQueue<T> S;
+    S.rec = Q.rec + (lane >= 16 ? 16 : 0);
+    S.put(lane, key, acc);
     __syncwarp();
     if (lane < 24) {
         const int h = lane >= 12 ? 1 : 0, q = lane - 12 * h;
+        WarpQueue<T> W;
+        W.rec = Q.rec + 16 * h;
         int ck = -1;
         T sum = T(0);
 #pragma unroll 4
         for (int j = 16 * h; j < 16 * h + 16; ++j) {
-            const int k = Q.key(j);
-            const T v = Q.rec[j * 13 + q];
-            if (k != ck) {
-                if (ck >= 0 && sum != T(0)) tile_add(sJa, ck + qoff, JT_ELEMS, sum);
-                ck = k;
-                sum = v;
-            } else {
-                sum += v;
+            const int k = W.key(j);
+            const T v = W.rec[j * QS + q];
+            const bool brk = k != ck;
+            if (__any_sync(0x00ffffffu, brk)) {
+                if (brk && ck >= 0 && sum != T(0)) tile_add(sJa, ck + qoff, JT_ELEMS, sum);
+                if (brk) {
+                    ck = k;
+                    sum = T(0);
+                }
             }
+            sum += v;
         }
         if (ck >= 0 && sum != T(0)) tile_add(sJa, ck + qoff, JT_ELEMS, sum);
     }
@@ -340,7 +345,7 @@ k_tile_push(const __grid_constant__ CUtensorMap tE0, const __grid_constant__ CUt
 
     const int ext[3] = {min(TILE, A.g.n[0] - ox), min(TILE, A.g.n[1] - oy), min(TILE, A.g.n[2] - oz)};
     WarpQueue<T> Q;
-    Q.rec = reinterpret_cast<T*>(sQ) + (size_t)warp * 13 * QCAP;
+    Q.rec = reinterpret_cast<T*>(sQ) + (size_t)warp * QS * QCAP;
     const int qoff = slot_offset(lane < 12 ? lane : (lane < 24 ? lane - 12 : 0));
     int qn = 0;                   // queued records (warp-uniform)
     const long long seg = A.pa.seg_start[tile];
@@ -475,8 +480,8 @@ k_tile_push(const __grid_constant__ CUtensorMap tE0, const __grid_constant__ CUt
 #pragma unroll
                 for (int q = 0; q < 6; ++q) acc[q] = Pair<T>::add(acc[q], v[q]);
             }
-            q_push(Q, qn, active && !summed, tile_index(0, x, y, z), v, lane);
-            q_push(Q, qn, crossed, tile_index(0, x + s[0], y + s[1], z + s[2]), v2, lane);
+            q_push(Q, qn, active && !summed, tile_index(0, x, y, z), v, crossed,
+                   tile_index(0, x + s[0], y + s[1], z + s[2]), v2, lane);
             if (qn) q_drain(Q, qn, lane, sJa, qoff);
             // movers: to the global list with their wrapped global cell; a particle that
             // left an open x face is removed instead
