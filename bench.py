@@ -230,7 +230,7 @@ def other_workloads(torch, peak):
 def adjoint_cost(torch):
     """Backward/forward cost of the checkpointed adjoint on the differentiable-run
     workload (32^3, 16 per cell, u_th = 0.02, plane wave of amplitude 0.05, 200 steps,
-    checkpoints every 20, FP64)."""
+    checkpoints every 20), on the FP64 and the FP32 path."""
     import numpy as np
     from paper_2609_16575_gb300 import gbpic
     from paper_2609_16575_gb300 import workloads as W
@@ -248,29 +248,31 @@ def adjoint_cost(torch):
     B[2] = np.cos(k * (x_b + 0.5 * wl.dt))[None, None, :]
     A = 0.05
     s = wl.species[0]
-    ctx = gbpic.Context(n, d, wl.dt, precision=gbpic.PIC_FP64, rho_ion=wl.rho_ion, track_ids=True)
-    ctx.set_fields(A * E, A * B)
-    ctx.load_species_array(s.q, s.m, s.P, True)
-    torch.cuda.synchronize()
-    t0 = time.perf_counter()
-    ctx.step(200)
-    ctx.sync()
-    t_plain = time.perf_counter() - t0
-    ctx.close()
-    ctx = gbpic.Context(n, d, wl.dt, precision=gbpic.PIC_FP64, rho_ion=wl.rho_ion, track_ids=True)
-    ctx.set_fields(A * E, A * B)
-    ctx.load_species_array(s.q, s.m, s.P, True)
-    torch.cuda.synchronize()
-    t0 = time.perf_counter()
-    ctx.adjoint_forward(200, 20)
-    t_fwd = time.perf_counter() - t0
-    t0 = time.perf_counter()
-    ctx.adjoint_backward(E, B)
-    t_bwd = time.perf_counter() - t0
-    ctx.close()
-    return {"workload": "32^3, 16 ppc, u_th=0.02, plane wave A=0.05, 200 steps, checkpoint every 20, FP64",
-            "forward_plain_s": t_plain, "forward_with_checkpoints_s": t_fwd, "backward_s": t_bwd,
-            "backward_over_forward": t_bwd / t_plain}
+    out = {"workload": "32^3, 16 ppc, u_th=0.02, plane wave A=0.05, 200 steps, checkpoint every 20"}
+    for prec, name in ((gbpic.PIC_FP64, "f64"), (gbpic.PIC_FP32, "f32")):
+        def fresh():
+            c = gbpic.Context(n, d, wl.dt, precision=prec, rho_ion=wl.rho_ion, track_ids=True)
+            c.set_fields(A * E, A * B)
+            c.load_species_array(s.q, s.m, s.P, True)
+            torch.cuda.synchronize()
+            return c
+        ctx = fresh()
+        t0 = time.perf_counter()
+        ctx.step(200)
+        ctx.sync()
+        t_plain = time.perf_counter() - t0
+        ctx.close()
+        ctx = fresh()
+        t0 = time.perf_counter()
+        ctx.adjoint_forward(200, 20)
+        t_fwd = time.perf_counter() - t0
+        t0 = time.perf_counter()
+        ctx.adjoint_backward(E, B)
+        t_bwd = time.perf_counter() - t0
+        ctx.close()
+        out[name] = {"forward_plain_s": t_plain, "forward_with_checkpoints_s": t_fwd, "backward_s": t_bwd,
+                     "backward_over_forward": t_bwd / t_plain}
+    return out
 
 
 def arm_config(n, npart, ncell, world, sort_every):

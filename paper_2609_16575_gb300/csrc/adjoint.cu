@@ -122,7 +122,8 @@ static pic_status snap_restore(pic_ctx* c, const Snapshot& S) {
 }
 
 // ---------------------------------------------------------------------------
-// Adjoint kernels (FP64 arithmetic whatever the forward precision).
+// Adjoint kernels: per-particle arithmetic in the working precision, FP64 adjoint state
+// and accumulation.
 
 template <typename T> struct AdjArgs {
     Geom g;
@@ -141,23 +142,23 @@ template <typename T> struct AdjArgs {
 };
 
 // Value and gradient (w.r.t. the three fractional coordinates) of a trilinear
-// interpolation of F from base (b0, b1, b2) with fractions s.
-template <typename T>
-__device__ __forceinline__ double interp_grad(const Geom& g, const T* F, const int b[3], const double s[3], double grad[3]) {
-    double f[2][2][2];
+// interpolation of F from base (b0, b1, b2) with fractions s, in arithmetic C.
+template <typename T, typename C>
+__device__ __forceinline__ C interp_grad(const Geom& g, const T* F, const int b[3], const C s[3], C grad[3]) {
+    C f[2][2][2];
     for (int cc = 0; cc < 2; ++cc)
         for (int bb = 0; bb < 2; ++bb)
-            for (int aa = 0; aa < 2; ++aa) f[cc][bb][aa] = (double)F[g.pidx(b[0] + aa, b[1] + bb, b[2] + cc)];
-    const double w0[2] = {1.0 - s[0], s[0]}, w1[2] = {1.0 - s[1], s[1]}, w2[2] = {1.0 - s[2], s[2]};
-    double v = 0, g0 = 0, g1 = 0, g2 = 0;
+            for (int aa = 0; aa < 2; ++aa) f[cc][bb][aa] = (C)F[g.pidx(b[0] + aa, b[1] + bb, b[2] + cc)];
+    const C w0[2] = {C(1) - s[0], s[0]}, w1[2] = {C(1) - s[1], s[1]}, w2[2] = {C(1) - s[2], s[2]};
+    C v = 0, g0 = 0, g1 = 0, g2 = 0;
     for (int cc = 0; cc < 2; ++cc)
         for (int bb = 0; bb < 2; ++bb)
             for (int aa = 0; aa < 2; ++aa) {
-                const double x = f[cc][bb][aa];
+                const C x = f[cc][bb][aa];
                 v += w0[aa] * w1[bb] * w2[cc] * x;
-                g0 += (aa ? 1.0 : -1.0) * w1[bb] * w2[cc] * x;
-                g1 += w0[aa] * (bb ? 1.0 : -1.0) * w2[cc] * x;
-                g2 += w0[aa] * w1[bb] * (cc ? 1.0 : -1.0) * x;
+                g0 += (aa ? C(1) : C(-1)) * w1[bb] * w2[cc] * x;
+                g1 += w0[aa] * (bb ? C(1) : C(-1)) * w2[cc] * x;
+                g2 += w0[aa] * w1[bb] * (cc ? C(1) : C(-1)) * x;
             }
     grad[0] = g0;
     grad[1] = g1;
@@ -165,30 +166,31 @@ __device__ __forceinline__ double interp_grad(const Geom& g, const T* F, const i
     return v;
 }
 
-__device__ __forceinline__ void scatter_trilinear(const Geom& g, double* acc, const int b[3], const double s[3], double lam) {
-    if (lam == 0.0) return;
-    const double w0[2] = {1.0 - s[0], s[0]}, w1[2] = {1.0 - s[1], s[1]}, w2[2] = {1.0 - s[2], s[2]};
+// FP64 accumulation of lam times the trilinear weights of component comp through
+// Add(comp, x, y, z, value) at the eight nodes from base b.
+template <typename C, typename AddFn>
+__device__ __forceinline__ void scatter_trilinear(AddFn Add, int comp, const int b[3], const C s[3], C lam) {
+    if (lam == C(0)) return;
+    const C w0[2] = {C(1) - s[0], s[0]}, w1[2] = {C(1) - s[1], s[1]}, w2[2] = {C(1) - s[2], s[2]};
     for (int cc = 0; cc < 2; ++cc)
         for (int bb = 0; bb < 2; ++bb)
-            for (int aa = 0; aa < 2; ++aa)
-                atomicAdd(acc + g.cidx(wrap_idx(b[0] + aa, g.n[0]), wrap_idx(b[1] + bb, g.n[1]), wrap_idx(b[2] + cc, g.n[2])),
-                          lam * w0[aa] * w1[bb] * w2[cc]);
+            for (int aa = 0; aa < 2; ++aa) Add(comp, b[0] + aa, b[1] + bb, b[2] + cc, (double)(lam * w0[aa] * w1[bb] * w2[cc]));
 }
 
 // Derivatives of S = sum_q L_q v_q(F, W) for one straight segment (the 12 edge
 // values of segment_values) with respect to its fluxes F and midpoint offsets W.
-__device__ __forceinline__ void segment_vjp(const double Cw[3], const double F[3], const double W[3], const double L[12],
-                                            double gF[3], double gW[3]) {
-    const double wx1 = W[0], wy1 = W[1], wz1 = W[2], wx0 = 1 - wx1, wy0 = 1 - wy1, wz0 = 1 - wz1;
-    const double Ax = L[0] * wy0 * wz0 + L[1] * wy1 * wz0 + L[2] * wy0 * wz1 + L[3] * wy1 * wz1;
-    const double Ay = L[4] * wx0 * wz0 + L[5] * wx1 * wz0 + L[6] * wx0 * wz1 + L[7] * wx1 * wz1;
-    const double Az = L[8] * wx0 * wy0 + L[9] * wx1 * wy0 + L[10] * wx0 * wy1 + L[11] * wx1 * wy1;
-    const double Gx = L[0] - L[1] - L[2] + L[3];
-    const double Gy = L[4] - L[5] - L[6] + L[7];
-    const double Gz = L[8] - L[9] - L[10] + L[11];
-    const double Fx = F[0], Fy = F[1], Fz = F[2];
-    const double Cx = Cw[0], Cy = Cw[1], Cz = Cw[2];
-    const double t = 1.0 / 12.0;
+template <typename C>
+__device__ __forceinline__ void segment_vjp(const C Cw[3], const C F[3], const C W[3], const C L[12], C gF[3], C gW[3]) {
+    const C wx1 = W[0], wy1 = W[1], wz1 = W[2], wx0 = 1 - wx1, wy0 = 1 - wy1, wz0 = 1 - wz1;
+    const C Ax = L[0] * wy0 * wz0 + L[1] * wy1 * wz0 + L[2] * wy0 * wz1 + L[3] * wy1 * wz1;
+    const C Ay = L[4] * wx0 * wz0 + L[5] * wx1 * wz0 + L[6] * wx0 * wz1 + L[7] * wx1 * wz1;
+    const C Az = L[8] * wx0 * wy0 + L[9] * wx1 * wy0 + L[10] * wx0 * wy1 + L[11] * wx1 * wy1;
+    const C Gx = L[0] - L[1] - L[2] + L[3];
+    const C Gy = L[4] - L[5] - L[6] + L[7];
+    const C Gz = L[8] - L[9] - L[10] + L[11];
+    const C Fx = F[0], Fy = F[1], Fz = F[2];
+    const C Cx = Cw[0], Cy = Cw[1], Cz = Cw[2];
+    const C t = C(1) / C(12);
     gF[0] = Cx * (Ax + Fy * Fz * Gx * t) + Cy * Fy * Fz * Gy * t + Cz * Fz * Fy * Gz * t;
     gF[1] = Cy * (Ay + Fx * Fz * Gy * t) + Cx * Fx * Fz * Gx * t + Cz * Fz * Fx * Gz * t;
     gF[2] = Cz * (Az + Fx * Fy * Gz * t) + Cx * Fx * Fy * Gx * t + Cy * Fy * Fx * Gy * t;
@@ -197,153 +199,192 @@ __device__ __forceinline__ void segment_vjp(const double Cw[3], const double F[3
     gW[2] = Cx * Fx * ((L[2] - L[0]) * wy0 + (L[3] - L[1]) * wy1) + Cy * Fy * ((L[6] - L[4]) * wx0 + (L[7] - L[5]) * wx1);
 }
 
-__device__ __forceinline__ void cross3(const double a[3], const double b[3], double o[3]) {
+template <typename C>
+__device__ __forceinline__ void cross3(const C a[3], const C b[3], C o[3]) {
     o[0] = a[1] * b[2] - a[2] * b[1];
     o[1] = a[2] * b[0] - a[0] * b[2];
     o[2] = a[0] * b[1] - a[1] * b[0];
 }
 
-template <typename T>
-__device__ void adjoint_particle(const AdjArgs<T>& A, int gx, int gy, int gz, const double d1[3], const double u0[3],
-                                 double w, int id) {
+// The particle part of one adjoint step.  The per-particle Jacobian products run in
+// the working precision C (FP32 on the FP32 path); the adjoint states carried across
+// steps (lambda of positions and momenta) and the field accumulators are FP64.
+template <typename T, typename C, typename AddFn>
+__device__ void adjoint_particle(const AdjArgs<T>& A, AddFn Add, int gx, int gy, int gz, const C d1[3], const C u0[3], C w,
+                                 int id) {
     const Geom& g = A.g;
     const int gc[3] = {gx, gy, gz};
     // ---- forward recompute: staggered gather with weights and their gradients
     int hb[3], nb[3];
-    double hs[3], ns[3];
+    C hs[3], ns[3];
     for (int k = 0; k < 3; ++k) {
-        if (d1[k] >= 0.5) {
+        if (d1[k] >= C(0.5)) {
             hb[k] = gc[k];
-            hs[k] = d1[k] - 0.5;
+            hs[k] = d1[k] - C(0.5);
         } else {
             hb[k] = gc[k] - 1;
-            hs[k] = d1[k] + 0.5;
+            hs[k] = d1[k] + C(0.5);
         }
         nb[k] = gc[k];
         ns[k] = d1[k];
     }
     const int HF[6][3] = {{1, 0, 0}, {0, 1, 0}, {0, 0, 1}, {0, 1, 1}, {1, 0, 1}, {1, 1, 0}};
-    double val[6], grad[6][3];
+    C val[6], grad[6][3];
     int cb[6][3];
-    double cs[6][3];
+    C cs[6][3];
     for (int comp = 0; comp < 6; ++comp) {
         for (int k = 0; k < 3; ++k) {
             cb[comp][k] = HF[comp][k] ? hb[k] : nb[k];
             cs[comp][k] = HF[comp][k] ? hs[k] : ns[k];
         }
         const T* F = comp < 3 ? A.E[comp] : A.Bn[comp - 3];
-        val[comp] = interp_grad(g, F, cb[comp], cs[comp], grad[comp]);
+        val[comp] = interp_grad<T, C>(g, F, cb[comp], cs[comp], grad[comp]);
     }
-    const double Ep[3] = {val[0], val[1], val[2]}, Bp[3] = {val[3], val[4], val[5]};
+    const C Ep[3] = {val[0], val[1], val[2]}, Bp[3] = {val[3], val[4], val[5]};
     // Boris with its intermediates (section 2.4)
-    const double eps = A.eps;
-    double um[3], t[3], s[3], up[3], upl[3], un[3], tmp[3];
+    const C eps = (C)A.eps;
+    C um[3], t[3], s[3], up[3], upl[3], un[3], tmp[3];
     for (int k = 0; k < 3; ++k) um[k] = u0[k] + eps * Ep[k];
-    const double gm = sqrt(1.0 + um[0] * um[0] + um[1] * um[1] + um[2] * um[2]);
+    const C gm = sqrt(C(1) + um[0] * um[0] + um[1] * um[1] + um[2] * um[2]);
     for (int k = 0; k < 3; ++k) t[k] = eps * Bp[k] / gm;
-    const double t2 = t[0] * t[0] + t[1] * t[1] + t[2] * t[2];
-    const double f = 2.0 / (1.0 + t2);
+    const C t2 = t[0] * t[0] + t[1] * t[1] + t[2] * t[2];
+    const C f = C(2) / (C(1) + t2);
     for (int k = 0; k < 3; ++k) s[k] = f * t[k];
     cross3(um, t, tmp);
     for (int k = 0; k < 3; ++k) up[k] = um[k] + tmp[k];
     cross3(up, s, tmp);
     for (int k = 0; k < 3; ++k) upl[k] = um[k] + tmp[k];
     for (int k = 0; k < 3; ++k) un[k] = upl[k] + eps * Ep[k];
-    const double gn = sqrt(1.0 + un[0] * un[0] + un[1] * un[1] + un[2] * un[2]);
-    const double ig = 1.0 / gn;
+    const C gn = sqrt(C(1) + un[0] * un[0] + un[1] * un[1] + un[2] * un[2]);
+    const C ig = C(1) / gn;
     // move and zigzag relay (cell-relative, as the forward kernels)
-    double d2[3], F1[3], F2[3], W1[3], W2[3];
+    C d2[3], F1[3], F2[3], W1[3], W2[3];
     int st[3];
     for (int k = 0; k < 3; ++k) {
-        st[k] = advance(d1[k], A.dtd[k] * un[k] * ig, d2[k]);
+        st[k] = advance(d1[k], (C)A.dtd[k] * un[k] * ig, d2[k]);
         st[k] = st[k] > 1 ? 1 : (st[k] < -1 ? -1 : st[k]);
         relay(d1[k], d2[k], st[k], F1[k], F2[k], W1[k], W2[k]);
     }
     // ---- deposit^T: lambda_J = -dt lambda_E^{n+1} at the edges of both segment cells
-    double L1[12], L2[12];
+    C L1[12], L2[12];
     for (int q = 0; q < 12; ++q) {
         int comp, ex, ey, ez;
         slot_edge(q, gx, gy, gz, comp, ex, ey, ez);
-        L1[q] = -A.dt * A.lEn[comp][g.pidx(wrap_idx(ex, g.n[0]), wrap_idx(ey, g.n[1]), wrap_idx(ez, g.n[2]))];
+        L1[q] = (C)(-A.dt * A.lEn[comp][g.pidx(wrap_idx(ex, g.n[0]), wrap_idx(ey, g.n[1]), wrap_idx(ez, g.n[2]))]);
         slot_edge(q, gx + st[0], gy + st[1], gz + st[2], comp, ex, ey, ez);
-        L2[q] = -A.dt * A.lEn[comp][g.pidx(wrap_idx(ex, g.n[0]), wrap_idx(ey, g.n[1]), wrap_idx(ez, g.n[2]))];
+        L2[q] = (C)(-A.dt * A.lEn[comp][g.pidx(wrap_idx(ex, g.n[0]), wrap_idx(ey, g.n[1]), wrap_idx(ez, g.n[2]))]);
     }
-    const double Cw[3] = {A.C[0] * w, A.C[1] * w, A.C[2] * w};
-    double gF1[3], gW1[3], gF2[3], gW2[3];
+    const C Cw[3] = {(C)A.C[0] * w, (C)A.C[1] * w, (C)A.C[2] * w};
+    C gF1[3], gW1[3], gF2[3], gW2[3];
     segment_vjp(Cw, F1, W1, L1, gF1, gW1);
     segment_vjp(Cw, F2, W2, L2, gF2, gW2);
-    double lx1[3], lx2[3];
+    C lx1c[3], lx2c[3];
     for (int k = 0; k < 3; ++k) {
         if (st[k] == 0) {   // F1 = F2 = (x2 - x1)/2, W1 = (3 x1 + x2)/4, W2 = (x1 + 3 x2)/4
-            lx1[k] = -0.5 * (gF1[k] + gF2[k]) + 0.75 * gW1[k] + 0.25 * gW2[k];
-            lx2[k] = 0.5 * (gF1[k] + gF2[k]) + 0.25 * gW1[k] + 0.75 * gW2[k];
+            lx1c[k] = C(-0.5) * (gF1[k] + gF2[k]) + C(0.75) * gW1[k] + C(0.25) * gW2[k];
+            lx2c[k] = C(0.5) * (gF1[k] + gF2[k]) + C(0.25) * gW1[k] + C(0.75) * gW2[k];
         } else {            // F1 = +-(1 - x1) ..., W1 = (x1 [+1])/2; F2 = x2 [-1], W2 = (x2 [+1])/2
-            lx1[k] = -gF1[k] + 0.5 * gW1[k];
-            lx2[k] = gF2[k] + 0.5 * gW2[k];
+            lx1c[k] = -gF1[k] + C(0.5) * gW1[k];
+            lx2c[k] = gF2[k] + C(0.5) * gW2[k];
         }
     }
-    // ---- the adjoint of the next state, and the position update X^{n+1} = X^n + dtd u / gamma
-    double lun[3], a[3];
+    // ---- the adjoint of the next state (FP64), and the position update
+    // X^{n+1} = X^n + dtd u / gamma
+    double lx1[3];
+    C lun[3], a[3];
     for (int k = 0; k < 3; ++k) {
-        lx2[k] += A.lX[k * A.nload + id];
-        lx1[k] += lx2[k];
-        a[k] = lx2[k] * A.dtd[k];
+        const double lx2 = (double)lx2c[k] + A.lX[k * A.nload + id];
+        lx1[k] = (double)lx1c[k] + lx2;
+        a[k] = (C)(lx2 * A.dtd[k]);
     }
-    const double adot = a[0] * un[0] + a[1] * un[1] + a[2] * un[2];
-    for (int k = 0; k < 3; ++k) lun[k] = A.lU[k * A.nload + id] + (a[k] - un[k] * adot * ig * ig) * ig;
+    const C adot = a[0] * un[0] + a[1] * un[1] + a[2] * un[2];
+    for (int k = 0; k < 3; ++k) lun[k] = (C)A.lU[k * A.nload + id] + (a[k] - un[k] * adot * ig * ig) * ig;
     // ---- Boris^T
-    double lum[3], lup[3], ls[3], lt[3], lE[3], lB[3];
+    C lum[3], lup[3], ls[3], lt[3], lE[3], lB[3];
     for (int k = 0; k < 3; ++k) lum[k] = lun[k];           // upl = um + up x s, lambda_upl = lun
     cross3(s, lun, lup);                                     // lambda_up = s x lambda_upl
     cross3(lun, up, ls);                                     // lambda_s = lambda_upl x up
     cross3(t, lup, tmp);                                     // up = um + um x t
     for (int k = 0; k < 3; ++k) lum[k] += lup[k] + tmp[k];
     cross3(lup, um, lt);
-    const double lst = ls[0] * t[0] + ls[1] * t[1] + ls[2] * t[2];   // s = f t, f = 2 / (1 + t.t)
+    const C lst = ls[0] * t[0] + ls[1] * t[1] + ls[2] * t[2];   // s = f t, f = 2 / (1 + t.t)
     for (int k = 0; k < 3; ++k) lt[k] += f * ls[k] - f * f * lst * t[k];
     for (int k = 0; k < 3; ++k) lB[k] = eps / gm * lt[k];    // t = eps B / gm
-    const double lgm = -(lt[0] * t[0] + lt[1] * t[1] + lt[2] * t[2]) / gm;
+    const C lgm = -(lt[0] * t[0] + lt[1] * t[1] + lt[2] * t[2]) / gm;
     for (int k = 0; k < 3; ++k) lum[k] += lgm * um[k] / gm;   // gm = sqrt(1 + um.um)
     for (int k = 0; k < 3; ++k) lE[k] = eps * (lun[k] + lum[k]);   // um = u + eps E and the final kick
     // ---- gather^T
     for (int k = 0; k < 3; ++k) {
-        double acc = 0;
+        C acc = 0;
         for (int c = 0; c < 3; ++c) acc += lE[c] * grad[c][k] + lB[c] * grad[3 + c][k];
-        lx1[k] += acc;
+        lx1[k] += (double)acc;
     }
     for (int c = 0; c < 3; ++c) {
-        scatter_trilinear(g, A.accE[c], cb[c], cs[c], lE[c]);
-        scatter_trilinear(g, A.accB[c], cb[3 + c], cs[3 + c], lB[c]);
+        scatter_trilinear(Add, c, cb[c], cs[c], lE[c]);
+        scatter_trilinear(Add, 3 + c, cb[3 + c], cs[3 + c], lB[c]);
     }
     for (int k = 0; k < 3; ++k) {
         A.lX[k * A.nload + id] = lx1[k];
-        A.lU[k * A.nload + id] = lum[k];
+        A.lU[k * A.nload + id] = (double)lum[k];
     }
 }
 
+// Each CTA takes a chunk of ADJ_CHUNK slots of one tile (blocks beyond the tiles'
+// chunks take the spill list).  The gather^T contributions of the chunk are summed in a
+// shared FP64 box of the tile's nodes -1..8 per dimension and added to the global
+// accumulators once per node.  Lane l of warp w handles slots 32 l + w + 8 m: the lanes
+// of a warp sit 32 slots apart in the cell-sorted segment, so they rarely add to the
+// same node at once (shared FP64 additions to one address serialise).
+constexpr int AB = 10;           // nodes per dimension of the shared adjoint box
+constexpr int ADJ_CHUNK = 1024;  // slots per CTA (8 warps x 32 lanes x 4)
 template <typename T>
-__global__ void __launch_bounds__(256) k_adj_particles(AdjArgs<T> A) {
+__global__ void __launch_bounds__(256) k_adj_particles(AdjArgs<T> A, int chunks_per_tile) {
+    __shared__ double sacc[6 * AB * AB * AB];
     const Geom& g = A.g;
     const int nt = g.nt[0] * g.nt[1] * g.nt[2];
-    for (int t = blockIdx.x; t < nt; t += gridDim.x) {
-        const int cnt = min(A.pa.count[t], A.pa.cap[t]);
-        const int tx = t % g.nt[0], ty = (t / g.nt[0]) % g.nt[1], tz = t / (g.nt[0] * g.nt[1]);
-        for (int i = threadIdx.x; i < cnt; i += blockDim.x) {
-            const long long p = (long long)A.pa.seg_start[t] + i;
-            const int lc = A.pa.cell[p];
-            if (lc < 0) continue;
-            const double d1[3] = {(double)A.pa.d[0][p], (double)A.pa.d[1][p], (double)A.pa.d[2][p]};
-            const double u0[3] = {(double)A.pa.u[0][p], (double)A.pa.u[1][p], (double)A.pa.u[2][p]};
-            adjoint_particle(A, tx * TILE + (lc & 7), ty * TILE + ((lc >> 3) & 7), tz * TILE + (lc >> 6), d1, u0,
-                             (double)A.pa.w[p], A.pa.id[p]);
+    auto gadd = [&](int comp, int x, int y, int z, double v) {
+        double* acc = comp < 3 ? A.accE[comp] : A.accB[comp - 3];
+        atomicAdd(acc + g.cidx(wrap_idx(x, g.n[0]), wrap_idx(y, g.n[1]), wrap_idx(z, g.n[2])), v);
+    };
+    const long long nblk_tiles = (long long)nt * chunks_per_tile;
+    if (blockIdx.x >= nblk_tiles) {   // the spill list
+        for (long long i = (blockIdx.x - nblk_tiles) * blockDim.x + threadIdx.x; i < A.nsp;
+             i += (gridDim.x - nblk_tiles) * blockDim.x) {
+            const Rec<T> r = A.spill[i];
+            adjoint_particle<T, T>(A, gadd, r.cell % g.n[0], (r.cell / g.n[0]) % g.n[1], r.cell / (g.n[0] * g.n[1]),
+                                   r.d, r.u, r.w, r.id);
         }
+        return;
     }
-    for (int i = blockIdx.x * blockDim.x + threadIdx.x; i < A.nsp; i += gridDim.x * blockDim.x) {
-        const Rec<T> r = A.spill[i];
-        const double d1[3] = {(double)r.d[0], (double)r.d[1], (double)r.d[2]};
-        const double u0[3] = {(double)r.u[0], (double)r.u[1], (double)r.u[2]};
-        adjoint_particle(A, r.cell % g.n[0], (r.cell / g.n[0]) % g.n[1], r.cell / (g.n[0] * g.n[1]), d1, u0,
-                         (double)r.w, r.id);
+    const int t = blockIdx.x / chunks_per_tile, chunk = blockIdx.x % chunks_per_tile;
+    const int cnt = min(A.pa.count[t], A.pa.cap[t]);
+    const int i0 = chunk * ADJ_CHUNK;
+    if (i0 >= cnt) return;
+    const int tx = t % g.nt[0], ty = (t / g.nt[0]) % g.nt[1], tz = t / (g.nt[0] * g.nt[1]);
+    const int ox = tx * TILE, oy = ty * TILE, oz = tz * TILE;
+    for (int i = threadIdx.x; i < 6 * AB * AB * AB; i += blockDim.x) sacc[i] = 0.0;
+    __syncthreads();
+    auto sadd = [&](int comp, int x, int y, int z, double v) {
+        atomicAdd(sacc + ((comp * AB + (z - oz + 1)) * AB + (y - oy + 1)) * AB + (x - ox + 1), v);
+    };
+    const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
+    for (int m = 0; m < ADJ_CHUNK / 256; ++m) {
+        const int i = i0 + 32 * lane + warp + 8 * m;
+        if (i >= cnt) continue;
+        const long long p = (long long)A.pa.seg_start[t] + i;
+        const int lc = A.pa.cell[p];
+        if (lc < 0) continue;
+        const T d1[3] = {A.pa.d[0][p], A.pa.d[1][p], A.pa.d[2][p]};
+        const T u0[3] = {A.pa.u[0][p], A.pa.u[1][p], A.pa.u[2][p]};
+        adjoint_particle<T, T>(A, sadd, ox + (lc & 7), oy + ((lc >> 3) & 7), oz + (lc >> 6), d1, u0, A.pa.w[p],
+                               A.pa.id[p]);
+    }
+    __syncthreads();
+    for (int e = threadIdx.x; e < 6 * AB * AB * AB; e += blockDim.x) {
+        const double v = sacc[e];
+        if (v == 0.0) continue;
+        const int lx = e % AB, ly = (e / AB) % AB, lz = (e / (AB * AB)) % AB, comp = e / (AB * AB * AB);
+        gadd(comp, ox + lx - 1, oy + ly - 1, oz + lz - 1, v);
     }
 }
 
@@ -444,8 +485,12 @@ static pic_status adjoint_step_t(pic_ctx* c, AdjBuffers& b) {
         A.C[0] = s.q / (dt * d[1] * d[2]);
         A.C[1] = s.q / (dt * d[2] * d[0]);
         A.C[2] = s.q / (dt * d[0] * d[1]);
+        int maxcap = 0;
+        for (int cap : s.h_cap) maxcap = std::max(maxcap, cap);
+        const int chunks = std::max(1, (maxcap + ADJ_CHUNK - 1) / ADJ_CHUNK);
+        const long long blocks = (long long)ntiles(c) * chunks + std::max(1, (A.nsp + 255) / 256);
         LaunchScope ls(c, KC_OTHER);
-        k_adj_particles<T><<<4 * 152, 256, 0, c->stream>>>(A);
+        k_adj_particles<T><<<(unsigned)blocks, 256, 0, c->stream>>>(A, chunks);
         GBPIC_CHECK(c, cudaGetLastError());
     }
     {
