@@ -50,6 +50,8 @@ def parse():
     p.add_argument("--no-fp64", action="store_true")
     p.add_argument("--no-cpu-baseline", action="store_true")
     p.add_argument("--no-extra", action="store_true", help="skip the other workloads and the adjoint cost")
+    p.add_argument("--stress", type=int, default=0,
+                   help="also run the 256^3 x 32 ppc precision-stress workload for this many steps (FP32 and FP64)")
     p.add_argument("--small", action="store_true", help="32^3 cells instead of 128^3 (smoke)")
     p.add_argument("--cells", type=int, default=0, help="cells per dimension (profiling cases); 0 = 128")
     p.add_argument("--sort-every", type=int, default=0, help="tile re-sort cadence passed to the library")
@@ -275,11 +277,55 @@ def adjoint_cost(torch):
     return out
 
 
+def stress_run(torch, steps):
+    """The precision-stress workload: 256^3 periodic cells, 32 electrons per cell
+    (536,870,912), u_th = 0.1, dx = 0.2, immobile ions.  Inputs are drawn on the device
+    (torch's Philox generator, seed 1238: uniform positions, Gaussian momenta) and loaded
+    through device pointers.  FP32 and FP64 paths from the same inputs: throughput,
+    relative change of the total energy U_E + U_B + K over `steps` cycles, and the
+    largest change of the Gauss residual."""
+    from paper_2609_16575_gb300 import gbpic
+    from paper_2609_16575_gb300 import workloads as W
+
+    n, ppc, d, u_th = 256, 32, 0.2, 0.1
+    npart = n ** 3 * ppc
+    gen = torch.Generator(device="cuda")
+    gen.manual_seed(1238)
+    X = torch.rand((3, npart), generator=gen, device="cuda", dtype=torch.float64) * n
+    X.clamp_(max=n * (1 - 2 ** -40))
+    U = torch.randn((3, npart), generator=gen, device="cuda", dtype=torch.float64) * u_th
+    w = torch.full((npart,), d ** 3 / ppc, device="cuda", dtype=torch.float64)
+    dt = W.courant_dt((d, d, d), 0.5)
+    out = {"workload": f"256^3 periodic, 32 ppc ({npart:,} electrons), u_th=0.1, dx=0.2, dt=0.5 Courant, "
+                       f"{steps} steps, inputs drawn on the device (Philox, seed 1238)"}
+    for prec, name in ((gbpic.PIC_FP32, "f32"), (gbpic.PIC_FP64, "f64")):
+        ctx = gbpic.Context((n, n, n), (d, d, d), dt, precision=prec, rho_ion=1.0)
+        ctx.load_species(-1.0, 1.0, X, U, w, True)
+        d0 = ctx.diagnostics()
+        torch.cuda.synchronize()
+        st = torch.cuda.current_stream()
+        a, b = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+        a.record(st)
+        ctx.step(steps)
+        b.record(st)
+        torch.cuda.synchronize()
+        ms = a.elapsed_time(b)
+        d1 = ctx.diagnostics()
+        e0 = d0["U_E"] + d0["U_B"] + d0["K_half"]
+        e1 = d1["U_E"] + d1["U_B"] + d1["K_half"]
+        out[name] = {"value": npart * steps / (ms / 1e3), "unit": UNIT, "ms_per_step": ms / steps,
+                     "energy_rel_change": (e1 - e0) / e0, "gauss_change_max": d1["gauss_change_max"],
+                     "rho_max": d1["rho_max"], "n_alive": d1["n_alive"]}
+        ctx.close()
+        del ctx
+    del X, U, w
+    return out
+
+
 def arm_config(n, npart, ncell, world, sort_every):
     """The workload description both arms print."""
     return {"workload": (f"thermal plasma {n}^3 periodic, dx=0.2, 64 ppc ({npart:,} electrons), "
                          "u_th=0.05, immobile ions, dt=0.5 Courant"),
-            "sort_every": sort_every or 4,
             "particles_per_gpu": npart, "cells": ncell, "precision": "fp32 bulk, fp64 reductions",
             "parallelism": f"replicas x{world}",
             "l2": "inputs larger than L2 (particle SoA 4.3 GB per GPU)"}
@@ -483,10 +529,12 @@ def run_gbpic(args):
     cpu = None
     if rank == 0 and world == 1 and not args.no_cpu_baseline:
         cpu = cpu_baseline()
-    extra, adj = None, None
+    extra, adj, stress = None, None, None
     if rank == 0 and world == 1 and not args.no_extra:
         extra = other_workloads(torch, peak)
         adj = adjoint_cost(torch)
+    if rank == 0 and world == 1 and args.stress > 0:
+        stress = stress_run(torch, args.stress)
 
     if rank == 0:
         line = {"metric": METRIC, "value": value, "unit": UNIT, "n_gpus": world, "steps": args.steps,
@@ -499,6 +547,8 @@ def run_gbpic(args):
                 "yee": yee_line(kt, ncell * world, peak),
                 "kernels": kernels, "gpu_launches": launches, "clocks": clocks, "e2e": e2e,
                 "cpu_baseline": cpu, "fp64": fp64, "other_workloads": extra, "adjoint": adj}
+        if stress is not None:
+            line["precision_stress"] = stress
         print(json.dumps(line), flush=True)
     if dist is not None:
         dist.destroy_process_group()
