@@ -39,21 +39,23 @@ template <typename T> __host__ __device__ constexpr int box_stride() {
     return ((box_elems<T>() * (int)sizeof(T) + 127) / 128) * 128 / (int)sizeof(T);
 }
 constexpr int JT_ELEMS = 3 * SJ3;   // elements of the shared J tile (8 bytes each: see tile_add)
-constexpr int QCAP_ = 64;   // record queue per warp (QCAP below)
+constexpr int QCAP_ = 32;   // record queue per warp (QCAP below)
 constexpr int PSX = 10, PSY = 10, PSZ = 9;   // z-paired staged fields: x, y -1..8, pair base z -1..7
 constexpr int PS = PSX * PSY * PSZ;          // pairs per component
-// Shared memory of the tile kernel, in order: region A = the TMA destination of the
-// six raw E, B boxes, reused for the warps' record queues once the boxes have been
-// converted; the z-paired fields; the J tile; the mbarrier.  Offsets are multiples of
-// 128 bytes.
+// Shared memory of the tile kernel, in order: the warps' record queues; the z-paired
+// fields; the J tile, which first receives the six raw E, B boxes from TMA (it is
+// cleared once they have been converted to pairs); the mbarrier.  Offsets are
+// multiples of 128 bytes.
 __host__ __device__ constexpr size_t align128(size_t b) { return (b + 127) / 128 * 128; }
+constexpr int QWORDS_ = (QCAP_ * 14 > 32 * 14 + 16 ? QCAP_ * 14 : 32 * 14 + 16);   // QWORDS below
 template <typename T> __host__ __device__ constexpr size_t region_a_bytes() {
-    return align128((size_t)6 * box_stride<T>() * sizeof(T) > (size_t)(Prec<T>::THREADS / 32) * QCAP_ * 14 * sizeof(T)
-                        ? (size_t)6 * box_stride<T>() * sizeof(T)
-                        : (size_t)(Prec<T>::THREADS / 32) * QCAP_ * 14 * sizeof(T));
+    return align128((size_t)(Prec<T>::THREADS / 32) * QWORDS_ * sizeof(T));
 }
 template <typename T> __host__ __device__ constexpr size_t pairs_bytes() { return align128((size_t)6 * PS * 2 * sizeof(T)); }
-template <typename T> __host__ __device__ constexpr size_t jtile_bytes() { return align128((size_t)JT_ELEMS * 8); }
+template <typename T> __host__ __device__ constexpr size_t jtile_bytes() {
+    return align128((size_t)JT_ELEMS * 8 > (size_t)6 * box_stride<T>() * sizeof(T) ? (size_t)JT_ELEMS * 8
+                                                                                  : (size_t)6 * box_stride<T>() * sizeof(T));
+}
 template <typename T> constexpr size_t tile_smem_bytes() {
     // + 128: the kernel rounds the dynamic shared base up to a 128-byte boundary
     return region_a_bytes<T>() + pairs_bytes<T>() + jtile_bytes<T>() + 16 + 128;
@@ -103,9 +105,14 @@ __device__ __forceinline__ int slot_offset(int q) {
 // run 12 atomics while the others idle.  Records are 13 words: 12 values, then the
 // tile index of the cell's origin edge; a stride coprime to the 32 banks keeps the
 // push and the drain free of bank conflicts.
-constexpr int QCAP = QCAP_;   // records per warp: a particle step adds at most 64 (the queue is
-                              // drained after every step that added some), a flush stages 32
+constexpr int QCAP = QCAP_;   // records per warp: one record kind of a particle step adds at most
+                              // 32 (the queue is drained in between and after every step that
+                              // added some); a flush stages 32
 constexpr int QS = 14;        // words per record: 12 values, the key, one pad (pairs stay aligned)
+// words of one warp's queue: QCAP records, or the 32 staged sums of a flush with the
+// second half shifted by 16 words, whichever is larger
+constexpr int QWORDS = (QCAP * QS > 32 * QS + 16 ? QCAP * QS : 32 * QS + 16);
+static_assert(QWORDS == QWORDS_ && QS == 14, "queue layout of the shared-memory plan");
 template <typename T> struct WarpQueue {
     T* rec;      // [QCAP][QS]
     __device__ __forceinline__ int& key(int j) const { return *reinterpret_cast<int*>(rec + j * QS + 12); }
@@ -118,16 +125,23 @@ template <typename T> struct WarpQueue {
 };
 
 // Append, for every lane, the record (ka, va) if want_a and (kb, vb) if want_b: 12
-// values of the cell with origin index k (warp-collective).
+// values of the cell with origin index k (warp-collective).  Called with an empty
+// queue; when both kinds together exceed its capacity, the first kind is drained
+// before the second is queued.
+template <typename T>
+__device__ __forceinline__ void q_drain(WarpQueue<T> Q, int& qn, int lane, uint32_t sJa, int qoff);
 template <typename T>
 __device__ __forceinline__ void q_push(WarpQueue<T> Q, int& qn, bool want_a, int ka, const typename Pair<T>::t va[6],
-                                       bool want_b, int kb, const typename Pair<T>::t vb[6], int lane) {
+                                       bool want_b, int kb, const typename Pair<T>::t vb[6], int lane, uint32_t sJa,
+                                       int qoff) {
     const unsigned ma = __ballot_sync(0xffffffffu, want_a), mb = __ballot_sync(0xffffffffu, want_b);
     if (!(ma | mb)) return;
     const unsigned lt = (1u << lane) - 1u;
     if (want_a) Q.put(qn + __popc(ma & lt), ka, va);
-    if (want_b) Q.put(qn + __popc(ma) + __popc(mb & lt), kb, vb);
-    qn += __popc(ma) + __popc(mb);
+    qn += __popc(ma);
+    if (qn + __popc(mb) > QCAP) q_drain(Q, qn, lane, sJa, qoff);
+    if (want_b) Q.put(qn + __popc(mb & lt), kb, vb);
+    qn += __popc(mb);
 }
 
 // Add every queued record to the shared J tile: lane 12h + q (h = 0, 1) adds value q of
@@ -239,10 +253,10 @@ k_tile_push(const __grid_constant__ CUtensorMap tE0, const __grid_constant__ CUt
     static_assert(NW <= PUSH_WARPS_MAX, "tile kernel CTA too large");
     static_assert(NT >= 256 && NT % 32 == 0, "the histogram scan uses the first 256 threads");
     using P2 = typename Pair<T>::t;
-    T* sF = reinterpret_cast<T*>(smem);                     // raw boxes, then the queues
     unsigned char* sQ = smem;
     P2* sP = reinterpret_cast<P2*>(smem + region_a_bytes<T>());
     unsigned char* sJ = smem + region_a_bytes<T>() + pairs_bytes<T>();
+    T* sF = reinterpret_cast<T*>(sJ);                       // raw boxes, then the J tile
     const uint32_t sJa = smem_u32(sJ);
     uint64_t* bar = reinterpret_cast<uint64_t*>(sJ + jtile_bytes<T>());
     __shared__ int s_off[TILE_CELLS];   // next free output slot of each input cell's range
@@ -280,10 +294,6 @@ k_tile_push(const __grid_constant__ CUtensorMap tE0, const __grid_constant__ CUt
         tma_load_3d(sF + 3 * BS, &tB0, ox, oy, oz, bar);
         tma_load_3d(sF + 4 * BS, &tB1, ox, oy, oz, bar);
         tma_load_3d(sF + 5 * BS, &tB2, ox, oy, oz, bar);
-    }
-    {
-        unsigned long long* z = reinterpret_cast<unsigned long long*>(sJ);
-        for (int i = threadIdx.x; i < JT_ELEMS; i += NT) z[i] = 0ull;
     }
     // output ranges: exclusive scan of the input histogram (two cells per thread of the
     // first 256 threads)
@@ -337,7 +347,12 @@ k_tile_push(const __grid_constant__ CUtensorMap tE0, const __grid_constant__ CUt
         const T* F = sF + c * BS + (zi * SB + yi) * BX + xi;
         sP[e] = Pair<T>::make(F[0], F[SB * BX]);
     }
-    __syncthreads();   // region A now holds the record queues
+    __syncthreads();   // the raw boxes are consumed: clear the J tile in their place
+    {
+        unsigned long long* z = reinterpret_cast<unsigned long long*>(sJ);
+        for (int i = threadIdx.x; i < JT_ELEMS; i += NT) z[i] = 0ull;
+    }
+    __syncthreads();
 
     auto pfetch = [&](int comp, int x, int y, int z) -> P2 {
         return sP[comp * PS + ((z + 1) * PSY + (y + 1)) * PSX + (x + 1)];
@@ -345,7 +360,7 @@ k_tile_push(const __grid_constant__ CUtensorMap tE0, const __grid_constant__ CUt
 
     const int ext[3] = {min(TILE, A.g.n[0] - ox), min(TILE, A.g.n[1] - oy), min(TILE, A.g.n[2] - oz)};
     WarpQueue<T> Q;
-    Q.rec = reinterpret_cast<T*>(sQ) + (size_t)warp * QS * QCAP;
+    Q.rec = reinterpret_cast<T*>(sQ) + (size_t)warp * QWORDS;
     const int qoff = slot_offset(lane < 12 ? lane : (lane < 24 ? lane - 12 : 0));
     int qn = 0;                   // queued records (warp-uniform)
     const long long seg = A.pa.seg_start[tile];
@@ -380,20 +395,23 @@ k_tile_push(const __grid_constant__ CUtensorMap tE0, const __grid_constant__ CUt
     for (int row = warp; row * 32 < ngroups; row += NW) {
         P2 acc[6];                // summed straight-segment currents of start cell `key`
         int key = RowCells<R>::key(n_cells);
-        // output slots: a lane whose R particles start in one cell takes R consecutive
-        // slots of that cell's range with one shared atomic per warp and cell; the other
-        // lanes claim one slot per particle below
+        // output slots: the lanes whose R particles start in one cell claim R slots each
+        // of that cell's range with one shared atomic per warp and cell; the other lanes
+        // claim one slot per particle below
         bool uni = n_cells[0] >= 0;
 #pragma unroll
         for (int r = 1; r < R; ++r) uni = uni && n_cells[r] == n_cells[0];
-        int obase;
+        int obase, ostride;
         {
             const unsigned grp = __match_any_sync(0xffffffffu, uni ? n_cells[0] : -1 - lane);
             const int leader = __ffs(grp) - 1;
             int b = 0;
             if (uni && lane == leader) b = atomicAdd(&s_off[n_cells[0]], R * __popc(grp));
             b = __shfl_sync(0xffffffffu, b, leader);
-            obase = uni ? b + R * __popc(grp & ((1u << lane) - 1u)) : -1;
+            // particle r of the group's k-th lane takes slot b + r G + k (G lanes): at each
+            // particle step the group writes G consecutive slots
+            obase = uni ? b + __popc(grp & ((1u << lane) - 1u)) : -1;
+            ostride = __popc(grp);
         }
 #pragma unroll
         for (int q = 0; q < 6; ++q) acc[q] = Pair<T>::splat(T(0));
@@ -457,7 +475,7 @@ k_tile_push(const __grid_constant__ CUtensorMap tE0, const __grid_constant__ CUt
                 if (stay) nlc = nx | (ny << 3) | (nz << 6);
                 // the particle's slot in its start cell's output range: the state after
                 // the step, or a hole
-                const long long o = seg + (obase >= 0 ? obase + r : atomicAdd(&s_off[lc], 1));
+                const long long o = seg + (obase >= 0 ? obase + r * ostride : atomicAdd(&s_off[lc], 1));
                 __stcs(A.pb.cell + o, stay ? nlc : HOLE);
                 if (stay) {
 #pragma unroll
@@ -481,7 +499,7 @@ k_tile_push(const __grid_constant__ CUtensorMap tE0, const __grid_constant__ CUt
                 for (int q = 0; q < 6; ++q) acc[q] = Pair<T>::add(acc[q], v[q]);
             }
             q_push(Q, qn, active && !summed, tile_index(0, x, y, z), v, crossed,
-                   tile_index(0, x + s[0], y + s[1], z + s[2]), v2, lane);
+                   tile_index(0, x + s[0], y + s[1], z + s[2]), v2, lane, sJa, qoff);
             if (qn) q_drain(Q, qn, lane, sJa, qoff);
             // movers: to the global list with their wrapped global cell; a particle that
             // left an open x face is removed instead
