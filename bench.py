@@ -50,6 +50,8 @@ def parse():
     p.add_argument("--no-fp64", action="store_true")
     p.add_argument("--no-cpu-baseline", action="store_true")
     p.add_argument("--no-extra", action="store_true", help="skip the other workloads and the adjoint cost")
+    p.add_argument("--adjoint-only", type=int, default=0,
+                   help="only time the FP64 checkpointed adjoint of the differentiable run over this many steps")
     p.add_argument("--stress", type=int, default=0,
                    help="also run the 256^3 x 32 ppc precision-stress workload for this many steps (FP32 and FP64)")
     p.add_argument("--small", action="store_true", help="32^3 cells instead of 128^3 (smoke)")
@@ -229,7 +231,7 @@ def other_workloads(torch, peak):
     return out
 
 
-def adjoint_cost(torch):
+def adjoint_cost(torch, steps=200, precisions=("f64", "f32")):
     """Backward/forward cost of the checkpointed adjoint on the differentiable-run
     workload (32^3, 16 per cell, u_th = 0.02, plane wave of amplitude 0.05, 200 steps,
     checkpoints every 20), on the FP64 and the FP32 path."""
@@ -250,8 +252,10 @@ def adjoint_cost(torch):
     B[2] = np.cos(k * (x_b + 0.5 * wl.dt))[None, None, :]
     A = 0.05
     s = wl.species[0]
-    out = {"workload": "32^3, 16 ppc, u_th=0.02, plane wave A=0.05, 200 steps, checkpoint every 20"}
+    out = {"workload": f"32^3, 16 ppc, u_th=0.02, plane wave A=0.05, {steps} steps, checkpoint every 20"}
     for prec, name in ((gbpic.PIC_FP64, "f64"), (gbpic.PIC_FP32, "f32")):
+        if name not in precisions:
+            continue
         def fresh():
             c = gbpic.Context(n, d, wl.dt, precision=prec, rho_ion=wl.rho_ion, track_ids=True)
             c.set_fields(A * E, A * B)
@@ -260,13 +264,13 @@ def adjoint_cost(torch):
             return c
         ctx = fresh()
         t0 = time.perf_counter()
-        ctx.step(200)
+        ctx.step(steps)
         ctx.sync()
         t_plain = time.perf_counter() - t0
         ctx.close()
         ctx = fresh()
         t0 = time.perf_counter()
-        ctx.adjoint_forward(200, 20)
+        ctx.adjoint_forward(steps, 20)
         t_fwd = time.perf_counter() - t0
         t0 = time.perf_counter()
         ctx.adjoint_backward(E, B)
@@ -557,6 +561,15 @@ def run_gbpic(args):
 
 def main():
     args = parse()
+    if args.adjoint_only > 0:
+        import torch
+
+        torch.cuda.set_device(0)
+        import __graft_entry__
+
+        __graft_entry__.build()
+        print(json.dumps(adjoint_cost(torch, args.adjoint_only, ("f64",))), flush=True)
+        return 0
     if args.impl == "reference":
         return run_reference(args)
     return run_gbpic(args)
