@@ -421,6 +421,24 @@ def timed_steps(ctx, torch, steps, dist):
     return ms, launches, kt
 
 
+# FP64 tile kernel: FP64 operations per particle-step (2 DFMA + DADD + DMUL thread
+# instructions, counted by ncu on the thermal workload: 1.584e9 DFMA, 1.338e9 DADD,
+# 0.803e9 DMUL for 16,777,216 particles), and the FP64 peak of a GB300 from its unit
+# counts and clock: 2 FP64 FMA per clock per SM x 152 SMs x 2.07 GHz x 2 operations.
+FP64_OPS_PER_PARTICLE = 316.5
+FP64_PEAK_TFLOPS = 2 * 152 * 2.07e9 * 2 / 1e12
+
+
+def fp64_alu_roofline(kt, n_particles):
+    launches, ms = kt["tile_push"]
+    avg_s = ms / max(launches, 1) / 1e3
+    achieved = FP64_OPS_PER_PARTICLE * n_particles / avg_s / 1e12
+    return {"bound": "alu", "achieved": achieved, "peak": FP64_PEAK_TFLOPS, "unit": "TFLOP/s",
+            "frac": achieved / FP64_PEAK_TFLOPS, "kernel": "k_tile_push<double>",
+            "peak_kind": "derived: 2 DFMA/clock/SM x 152 SMs x 2.07 GHz (a DFMA probe reached 1.02 TFLOP/s)",
+            "ops_per_particle": FP64_OPS_PER_PARTICLE}
+
+
 def roofline(kt, dtype, n_particles, ncell, peak, peak_kind, traffic):
     launches, ms = kt["tile_push"]
     avg_s = ms / max(launches, 1) / 1e3
@@ -495,6 +513,7 @@ def run_gbpic(args):
         v64 = npart * k64 / (ms64 / 1e3)
         fp64 = {"value": v64 * world, "unit": UNIT, "steps": k64, "ms_per_step": ms64 / k64,
                 "roofline": roofline(kt64, "f64", npart, ncell, peak, peak_kind, None),
+                "alu_roofline": fp64_alu_roofline(kt64, npart),
                 "step_hbm_frac": v64 * (PART_BYTES["f64"] + STEP_GRID_BYTES["f64"] / WORKLOAD["ppc"]) / 1e9 / peak}
 
     # --- end to end through the public API: host (pinned) inputs in, diagnostics out

@@ -20,7 +20,7 @@ constexpr int SB = 10;           // staged E/B extent per dim: local cells -1..8
 constexpr int SJ = 11;           // shared J extent per dim: local nodes/edges -1..9
 constexpr int SJ3 = SJ * SJ * SJ;
 constexpr int PUSH_WARPS_MAX = 16;   // the tile kernel's CTA has at most 512 threads
-constexpr int HOLE = -1;             // cell value of a slot a particle has left (until the next re-sort)
+constexpr int HOLE = -1;             // cell value of a slot whose particle left the tile last step
 
 // device error bits, OR-ed into Counters::err
 enum : int { ERRB_OVERFLOW = 1, ERRB_SUPERLUMINAL = 2, ERRB_NAN = 4, ERRB_TIMEOUT = 8 };
@@ -110,7 +110,7 @@ template <typename T> struct ParticleArrays {
     const int* seg_start;
     int* count;     // slots in use: the particles and the holes (cell == HOLE) among them
     const int* cap;
-    int* holes;     // holes among the first count slots (cleared by the re-sort)
+    int* holes;     // holes among the first count slots (the particles that left last step)
 };
 
 // ---------------------------------------------------------------------------

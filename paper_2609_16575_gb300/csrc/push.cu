@@ -199,8 +199,8 @@ __device__ __forceinline__ void flush_warp(const typename Pair<T>::t acc[6], int
 }
 
 // Cells of a lane's R slots (one 16- or 8-byte load) and the start cell its current
-// sums are kept for: the cell most of the R particles start in (a particle that moved
-// since the last re-sort, or a cell boundary inside the group, then costs one queued
+// sums are kept for: the cell most of the R particles start in (a particle that crossed
+// a cell face last step, or a cell boundary inside the group, then costs one queued
 // record instead of R - 1).
 template <int R> struct RowCells;
 template <> struct RowCells<4> {
