@@ -115,8 +115,9 @@ static pic_status device_errors(pic_ctx* c) {
     }
     if (worst & ERRB_TIMEOUT) { c->err = "a bounded device wait for a TMA copy gave up"; return PIC_ERR_TIMEOUT; }
     if (worst & ERRB_OVERFLOW) { c->err = "mover or spill list overflow: particles were dropped"; return PIC_ERR_TILE_OVERFLOW; }
-    if (worst & ERRB_SUPERLUMINAL) { c->err = "a particle moved more than one cell in one step"; return PIC_ERR_SUPERLUMINAL; }
+    // a non-finite momentum also makes its move look superluminal: report the cause
     if (worst & ERRB_NAN) { c->err = "non-finite momentum"; return PIC_ERR_NAN; }
+    if (worst & ERRB_SUPERLUMINAL) { c->err = "a particle moved more than one cell in one step"; return PIC_ERR_SUPERLUMINAL; }
     return PIC_OK;
 }
 

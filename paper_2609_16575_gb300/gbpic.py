@@ -22,6 +22,8 @@ _HERE = os.path.dirname(os.path.abspath(__file__))
 LIB_PATH = os.path.join(_HERE, "_build", "libgbpic.so")
 
 PIC_OK = 0
+PIC_ERR_ARG, PIC_ERR_CFL, PIC_ERR_OOM, PIC_ERR_CUDA, PIC_ERR_TILE_OVERFLOW = 1, 2, 3, 4, 5
+PIC_ERR_SUPERLUMINAL, PIC_ERR_NAN, PIC_ERR_STATE, PIC_ERR_TIMEOUT, PIC_ERR_NO_DEVICE = 6, 7, 8, 9, 10
 PIC_FP32 = 0
 PIC_FP64 = 1
 STATUS_NAMES = {0: "PIC_OK", 1: "PIC_ERR_ARG", 2: "PIC_ERR_CFL", 3: "PIC_ERR_OOM", 4: "PIC_ERR_CUDA",
