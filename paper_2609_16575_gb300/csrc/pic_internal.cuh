@@ -287,37 +287,6 @@ template <> struct Pair<double> {
     static __device__ __forceinline__ double2 sub(double2 b, double2 a) { return make_double2(b.x - a.x, b.y - a.y); }
 };
 
-// Gather E and B (section 2.5) from z-paired staged fields: PF(comp, x, y, z) returns
-// the pair (F(x, y, z), F(x, y, z + 1)) of component comp.  Each component is the same
-// trilinear interpolation as trilerp (x, then y, then z), with the x and y stages done
-// on both z planes at once.
-template <typename T, typename PF>
-__device__ __forceinline__ void gather_eb_pairs(PF P, int x, int y, int z, T dx, T dy, T dz, T Ep[3], T Bp[3]) {
-    using PT = Pair<T>;
-    using P2 = typename PT::t;
-    int hx, hy, hz;
-    T shx, shy, shz;
-    half_weight(x, dx, hx, shx);
-    half_weight(y, dy, hy, shy);
-    half_weight(z, dz, hz, shz);
-    auto tri = [&](int c, int bx, int by, int bz, T sx, T sy, T sz) -> T {
-        const P2 a00 = P(c, bx, by, bz), a10 = P(c, bx + 1, by, bz);
-        const P2 a01 = P(c, bx, by + 1, bz), a11 = P(c, bx + 1, by + 1, bz);
-        const P2 sx2 = PT::splat(sx);
-        const P2 q0 = PT::fma(sx2, PT::sub(a10, a00), a00);
-        const P2 q1 = PT::fma(sx2, PT::sub(a11, a01), a01);
-        const P2 r = PT::fma(PT::splat(sy), PT::sub(q1, q0), q0);
-        return r.x + sz * (r.y - r.x);
-    };
-    // E: Ex (h,n,n), Ey (n,h,n), Ez (n,n,h);  B: Bx (n,h,h), By (h,n,h), Bz (h,h,n)
-    Ep[0] = tri(0, hx, y, z, shx, dy, dz);
-    Ep[1] = tri(1, x, hy, z, dx, shy, dz);
-    Ep[2] = tri(2, x, y, hz, dx, dy, shz);
-    Bp[0] = tri(3, x, hy, hz, dx, shy, shz);
-    Bp[1] = tri(4, hx, y, hz, shx, dy, shz);
-    Bp[2] = tri(5, hx, hy, z, shx, shy, dz);
-}
-
 // Relativistic Boris (section 2.4; Boris 1970): u^{n-1/2} -> u^{n+1/2} in place,
 // eps = q dt / (2 m).  Returns 1/gamma^{n+1/2}.
 template <typename T>

@@ -198,6 +198,41 @@ __device__ __forceinline__ void flush_warp(const typename Pair<T>::t acc[6], int
     __syncwarp();
 }
 
+// Gather E and B (section 2.5) from the tile's z-paired staged fields sP: pair
+// (F(x, y, z), F(x, y, z + 1)) of component c at local (x, y, z) is
+// sP[c PS + ((z + 1) PSY + (y + 1)) PSX + x + 1].  The cell's pair index is
+// computed once and each component's stencil origin is a fixed offset from it (a
+// half-located dimension shifts by -1 when the offset is below one half).  Each
+// component is the trilinear interpolation of trilerp (x, then y, then z), with the
+// x and y stages done on both z planes at once.
+template <typename T>
+__device__ __forceinline__ void gather_tile(const typename Pair<T>::t* sP, int x, int y, int z, T dx, T dy, T dz,
+                                            T Ep[3], T Bp[3]) {
+    using PT = Pair<T>;
+    using P2 = typename PT::t;
+    const bool ux = dx >= T(0.5), uy = dy >= T(0.5), uz = dz >= T(0.5);
+    const T shx = ux ? dx - T(0.5) : dx + T(0.5);
+    const T shy = uy ? dy - T(0.5) : dy + T(0.5);
+    const T shz = uz ? dz - T(0.5) : dz + T(0.5);
+    const int ox = ux ? 0 : -1, oy = uy ? 0 : -PSX, oz = uz ? 0 : -PSX * PSY;
+    const P2* p = sP + ((z + 1) * PSY + (y + 1)) * PSX + (x + 1);
+    auto tri = [&](const P2* q, T sx, T sy, T sz) -> T {
+        const P2 a00 = q[0], a10 = q[1], a01 = q[PSX], a11 = q[PSX + 1];
+        const P2 sx2 = PT::splat(sx);
+        const P2 q0 = PT::fma(sx2, PT::sub(a10, a00), a00);
+        const P2 q1 = PT::fma(sx2, PT::sub(a11, a01), a01);
+        const P2 r = PT::fma(PT::splat(sy), PT::sub(q1, q0), q0);
+        return r.x + sz * (r.y - r.x);
+    };
+    // E: Ex (h,n,n), Ey (n,h,n), Ez (n,n,h);  B: Bx (n,h,h), By (h,n,h), Bz (h,h,n)
+    Ep[0] = tri(p + 0 * PS + ox, shx, dy, dz);
+    Ep[1] = tri(p + 1 * PS + oy, dx, shy, dz);
+    Ep[2] = tri(p + 2 * PS + oz, dx, dy, shz);
+    Bp[0] = tri(p + 3 * PS + oy + oz, dx, shy, shz);
+    Bp[1] = tri(p + 4 * PS + ox + oz, shx, dy, shz);
+    Bp[2] = tri(p + 5 * PS + ox + oy, shx, shy, dz);
+}
+
 // Cells of a lane's R slots (one 16- or 8-byte load) and the start cell its current
 // sums are kept for: the cell most of the R particles start in (a particle that crossed
 // a cell face last step, or a cell boundary inside the group, then costs one queued
@@ -354,10 +389,6 @@ k_tile_push(const __grid_constant__ CUtensorMap tE0, const __grid_constant__ CUt
     }
     __syncthreads();
 
-    auto pfetch = [&](int comp, int x, int y, int z) -> P2 {
-        return sP[comp * PS + ((z + 1) * PSY + (y + 1)) * PSX + (x + 1)];
-    };
-
     const int ext[3] = {min(TILE, A.g.n[0] - ox), min(TILE, A.g.n[1] - oy), min(TILE, A.g.n[2] - oz)};
     WarpQueue<T> Q;
     Q.rec = reinterpret_cast<T*>(sQ) + (size_t)warp * QWORDS;
@@ -372,15 +403,16 @@ k_tile_push(const __grid_constant__ CUtensorMap tE0, const __grid_constant__ CUt
     int n_lc = HOLE;
     T n_d[3], n_u[3], n_w;
     auto prefetch = [&](int i) {
-        n_lc = i < cnt ? __ldg(A.pa.cell + seg + i) : HOLE;
-        if (n_lc >= 0) {
+        const bool in = i < cnt;
+        const long long q = seg + (in ? i : 0);   // slots past count read slot 0, unused
+        const int c = __ldg(A.pa.cell + q);
+        n_lc = in ? c : HOLE;
 #pragma unroll
-            for (int k = 0; k < 3; ++k) {
-                n_d[k] = __ldg(A.pa.d[k] + seg + i);
-                n_u[k] = __ldg(A.pa.u[k] + seg + i);
-            }
-            n_w = __ldg(A.pa.w + seg + i);
+        for (int k = 0; k < 3; ++k) {
+            n_d[k] = __ldg(A.pa.d[k] + q);
+            n_u[k] = __ldg(A.pa.u[k] + q);
         }
+        n_w = __ldg(A.pa.w + q);
     };
     prefetch((warp * 32 + lane) * R);
     int n_cells[R];               // the cells of the next row's R slots
@@ -435,20 +467,20 @@ k_tile_push(const __grid_constant__ CUtensorMap tE0, const __grid_constant__ CUt
                 y = (lc >> 3) & 7;
                 z = lc >> 6;
                 T Ep[3], Bp[3];
-                gather_eb_pairs<T>(pfetch, x, y, z, d1[0], d1[1], d1[2], Ep, Bp);
+                gather_tile<T>(sP, x, y, z, d1[0], d1[1], d1[2], Ep, Bp);
                 T gm1_old = T(0);
                 if (RECK) gm1_old = gamma_minus_one(u);
                 const T ig = boris(A.eps, Ep, Bp, u);
-                if (!(ig > T(0))) atomicOr(&A.ctr->err, ERRB_NAN);
                 if (RECK) kacc += (double)w * A.mass * 0.5 * ((double)gm1_old + (double)gamma_minus_one(u));
+                bool far = false;
 #pragma unroll
                 for (int k = 0; k < 3; ++k) {
                     s[k] = advance(d1[k], A.dtd[k] * u[k] * ig, d2[k]);
-                    if (s[k] > 1 || s[k] < -1) {
-                        atomicOr(&A.ctr->err, ERRB_SUPERLUMINAL);
-                        s[k] = s[k] > 0 ? 1 : -1;
-                    }
+                    far = far || s[k] > 1 || s[k] < -1;
+                    s[k] = max(-1, min(1, s[k]));
                 }
+                const int errb = (ig > T(0) ? 0 : ERRB_NAN) | (far ? ERRB_SUPERLUMINAL : 0);
+                if (errb) atomicOr(&A.ctr->err, errb);
                 const T cw[3] = {A.cq[0] * w, A.cq[1] * w, A.cq[2] * w};
                 crossed = (s[0] | s[1] | s[2]) != 0;
                 if (!crossed) {
