@@ -106,8 +106,8 @@ __device__ __forceinline__ int slot_offset(int q) {
 // tile index of the cell's origin edge; a stride coprime to the 32 banks keeps the
 // push and the drain free of bank conflicts.
 constexpr int QCAP = QCAP_;   // records per warp: one record kind of a particle step adds at most
-                              // 32 (the queue is drained in between and after every step that
-                              // added some); a flush stages 32
+                              // 32 (the queue is drained before a kind that would not fit and
+                              // before every flush); a flush stages 32
 constexpr int QS = 14;        // words per record: 12 values, the key, one pad (pairs stay aligned)
 // words of one warp's queue: QCAP records, or the 32 staged sums of a flush with the
 // second half shifted by 16 words, whichever is larger
@@ -125,9 +125,9 @@ template <typename T> struct WarpQueue {
 };
 
 // Append, for every lane, the record (ka, va) if want_a and (kb, vb) if want_b: 12
-// values of the cell with origin index k (warp-collective).  Called with an empty
-// queue; when both kinds together exceed its capacity, the first kind is drained
-// before the second is queued.
+// values of the cell with origin index k (warp-collective).  The queue is drained
+// first whenever a kind's records would not fit; otherwise records accumulate until
+// the row's flush, so one drain pass adds the records of several particle steps.
 template <typename T>
 __device__ __forceinline__ void q_drain(WarpQueue<T> Q, int& qn, int lane, uint32_t sJa, int qoff);
 template <typename T>
@@ -137,6 +137,7 @@ __device__ __forceinline__ void q_push(WarpQueue<T> Q, int& qn, bool want_a, int
     const unsigned ma = __ballot_sync(0xffffffffu, want_a), mb = __ballot_sync(0xffffffffu, want_b);
     if (!(ma | mb)) return;
     const unsigned lt = (1u << lane) - 1u;
+    if (qn + __popc(ma) > QCAP) q_drain(Q, qn, lane, sJa, qoff);
     if (want_a) Q.put(qn + __popc(ma & lt), ka, va);
     qn += __popc(ma);
     if (qn + __popc(mb) > QCAP) q_drain(Q, qn, lane, sJa, qoff);
@@ -394,17 +395,18 @@ k_tile_push(const __grid_constant__ CUtensorMap tE0, const __grid_constant__ CUt
     Q.rec = reinterpret_cast<T*>(sQ) + (size_t)warp * QWORDS;
     const int qoff = slot_offset(lane < 12 ? lane : (lane < 24 ? lane - 12 : 0));
     int qn = 0;                   // queued records (warp-uniform)
-    const long long seg = A.pa.seg_start[tile];
+    const int seg = A.pa.seg_start[tile];   // slots of a block are below 2^31
     const int ngroups = (cnt + R - 1) / R;
     double kacc = 0.0;
     int left = 0;                 // particles this lane moved out of the tile or removed
+    int esc = 0;                  // of those, removed at an open x face
     // the next particle's state, loaded one particle step ahead (L1-cached loads: the
     // R slots of a lane share a 32-byte sector)
     int n_lc = HOLE;
     T n_d[3], n_u[3], n_w;
     auto prefetch = [&](int i) {
         const bool in = i < cnt;
-        const long long q = seg + (in ? i : 0);   // slots past count read slot 0, unused
+        const int q = seg + (in ? i : 0);   // slots past count read slot 0, unused
         const int c = __ldg(A.pa.cell + q);
         n_lc = in ? c : HOLE;
 #pragma unroll
@@ -452,7 +454,7 @@ k_tile_push(const __grid_constant__ CUtensorMap tE0, const __grid_constant__ CUt
 #pragma unroll 1
         for (int r = 0; r < R; ++r) {
             const int i = s0 + r;
-            const long long p = seg + i;
+            const int p = seg + i;
             const int lc = n_lc;
             const bool active = lc >= 0;
             T u[3] = {n_u[0], n_u[1], n_u[2]}, d2[3] = {T(0), T(0), T(0)}, w = n_w;
@@ -507,7 +509,7 @@ k_tile_push(const __grid_constant__ CUtensorMap tE0, const __grid_constant__ CUt
                 if (stay) nlc = nx | (ny << 3) | (nz << 6);
                 // the particle's slot in its start cell's output range: the state after
                 // the step, or a hole
-                const long long o = seg + (obase >= 0 ? obase + r * ostride : atomicAdd(&s_off[lc], 1));
+                const int o = seg + (obase >= 0 ? obase + r * ostride : atomicAdd(&s_off[lc], 1));
                 __stcs(A.pb.cell + o, stay ? nlc : HOLE);
                 if (stay) {
 #pragma unroll
@@ -532,17 +534,15 @@ k_tile_push(const __grid_constant__ CUtensorMap tE0, const __grid_constant__ CUt
             }
             q_push(Q, qn, active && !summed, tile_index(0, x, y, z), v, crossed,
                    tile_index(0, x + s[0], y + s[1], z + s[2]), v2, lane, sJa, qoff);
-            if (qn) q_drain(Q, qn, lane, sJa, qoff);
             // movers: to the global list with their wrapped global cell; a particle that
             // left an open x face is removed instead
             int gxm = 0;
             if (move) {
                 gxm = x_after(A.g, ox + x + s[0]);
-                if (gxm < 0) move = false;
-            }
-            {
-                const unsigned gone = __ballot_sync(0xffffffffu, active && !stay && !move);
-                if (gone && lane == __ffs(gone) - 1) atomicAdd(&A.ctr->escaped, __popc(gone));
+                if (gxm < 0) {
+                    move = false;
+                    ++esc;
+                }
             }
             const int slot = warp_reserve(&A.ctr->mover_count[A.parity], move);
             if (move) {
@@ -565,10 +565,13 @@ k_tile_push(const __grid_constant__ CUtensorMap tE0, const __grid_constant__ CUt
                 }
             }
         }
+        if (qn) q_drain(Q, qn, lane, sJa, qoff);   // the flush stages its sums in the queue
         flush_warp<T>(acc, key >= 0 ? tile_index(0, key & 7, (key >> 3) & 7, key >> 6) : -1, lane, Q, sJa, qoff);
     }
-    for (int o = 16; o > 0; o >>= 1) left += __shfl_xor_sync(0xffffffffu, left, o);
+    left = __reduce_add_sync(0xffffffffu, left);
+    esc = __reduce_add_sync(0xffffffffu, esc);
     if (lane == 0 && left) atomicAdd(&s_left, left);
+    if (lane == 0 && esc) atomicAdd(&A.ctr->escaped, esc);
     __syncthreads();
     // the output segment: the input cells' ranges (with the holes of the departed) and,
     // appended later, this step's arrivals
