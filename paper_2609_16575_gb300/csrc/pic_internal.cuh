@@ -30,7 +30,9 @@ constexpr int MBAR_MAX_POLLS = 1 << 24;
 
 template <typename T> struct Prec;
 template <> struct Prec<float> {
-    static constexpr int THREADS = 256;   // tile kernel CTA
+    // tile kernel CTA: 10 warps and 2 CTAs per SM hold 20 warps at 96 registers; the
+    // kernel is latency-bound, so resident warps count for more than registers
+    static constexpr int THREADS = 320;
     static constexpr int MINB = 2;
     static constexpr int R = 4;        // consecutive particle slots per lane (one 16-byte load per array)
     static constexpr int BX = 12;      // TMA box inner extent: 12 floats = 48 B (multiple of 16 B)
