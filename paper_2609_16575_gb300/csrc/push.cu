@@ -461,6 +461,7 @@ k_tile_push(const __grid_constant__ CUtensorMap tE0, const __grid_constant__ CUt
             const T d1[3] = {n_d[0], n_d[1], n_d[2]};
             prefetch(r + 1 < R ? i + 1 : ((row + NW) * 32 + lane) * R);
             P2 v[6], v2[6];
+            T cw[3] = {T(0), T(0), T(0)};
             int s[3] = {0, 0, 0};
             int x = 0, y = 0, z = 0, nlc = -1;
             bool stay = false, move = false, crossed = false;
@@ -483,26 +484,25 @@ k_tile_push(const __grid_constant__ CUtensorMap tE0, const __grid_constant__ CUt
                 }
                 const int errb = (ig > T(0) ? 0 : ERRB_NAN) | (far ? ERRB_SUPERLUMINAL : 0);
                 if (errb) atomicOr(&A.ctr->err, errb);
-                const T cw[3] = {A.cq[0] * w, A.cq[1] * w, A.cq[2] * w};
+#pragma unroll
+                for (int k = 0; k < 3; ++k) cw[k] = A.cq[k] * w;
                 crossed = (s[0] | s[1] | s[2]) != 0;
-                if (!crossed) {
-                    // both zigzag segments lie in the start cell: their two midpoint
-                    // products and D_p D_r / 48 terms add up to one straight segment
-                    // x1 -> x2 with midpoint weights and the D_p D_r / 12 term
-                    T D[3], Wm[3];
+                // the segment in the start cell, without a branch: for a particle that
+                // stays in its cell both zigzag segments lie there, and their two
+                // midpoint products and D_p D_r / 48 terms add up to the straight
+                // segment x1 -> x2 (midpoint weights, D_p D_r / 12 term); for a crosser
+                // it is the relay split's first segment.  The second segment's flux and
+                // midpoint follow below, once for the warp's crossers.
+                const T h = crossed ? T(0.5) : T(1);
+                T Fa[3], Wa[3];
 #pragma unroll
-                    for (int k = 0; k < 3; ++k) {
-                        D[k] = d2[k] - d1[k];
-                        Wm[k] = d1[k] + T(0.5) * D[k];
-                    }
-                    segment_values_pairs(cw, D, Wm, v);
-                } else {
-                    T F1[3], F2[3], W1[3], W2[3];
-#pragma unroll
-                    for (int k = 0; k < 3; ++k) relay(d1[k], d2[k], s[k], F1[k], F2[k], W1[k], W2[k]);
-                    segment_values_pairs(cw, F1, W1, v);
-                    segment_values_pairs(cw, F2, W2, v2);
+                for (int k = 0; k < 3; ++k) {
+                    const T D = d2[k] - d1[k];
+                    const T up = s[k] > 0 ? T(1) : T(0);
+                    Fa[k] = s[k] == 0 ? h * D : up - d1[k];
+                    Wa[k] = s[k] == 0 ? d1[k] + T(0.5) * h * D : T(0.5) * (d1[k] + up);
                 }
+                segment_values_pairs(cw, Fa, Wa, v);
                 const int nx = x + s[0], ny = y + s[1], nz = z + s[2];
                 stay = nx >= 0 && nx < ext[0] && ny >= 0 && ny < ext[1] && nz >= 0 && nz < ext[2];
                 move = !stay;
@@ -526,6 +526,17 @@ k_tile_push(const __grid_constant__ CUtensorMap tE0, const __grid_constant__ CUt
             {   // cell histogram of the output, one shared atomic per warp and cell
                 const unsigned grp = __match_any_sync(0xffffffffu, nlc >= 0 ? nlc : -1 - lane);
                 if (nlc >= 0 && lane == __ffs(grp) - 1) atomicAdd(&s_hn[nlc], __popc(grp));
+            }
+            // a crosser's second segment, in the cell it moved to (relay split)
+            if (__any_sync(0xffffffffu, crossed)) {
+                T F2[3], W2[3];
+#pragma unroll
+                for (int k = 0; k < 3; ++k) {
+                    const T dn = s[k] < 0 ? T(1) : T(0);
+                    F2[k] = s[k] == 0 ? T(0.5) * (d2[k] - d1[k]) : d2[k] - dn;
+                    W2[k] = s[k] == 0 ? d1[k] + T(0.75) * (d2[k] - d1[k]) : T(0.5) * (d2[k] + dn);
+                }
+                segment_values_pairs(cw, F2, W2, v2);
             }
             const bool summed = active && lc == key;
             if (summed) {
