@@ -421,10 +421,12 @@ def timed_steps(ctx, torch, steps, dist):
     return ms, launches, kt
 
 
-# FP64 tile kernel: FP64 operations per particle-step (2 DFMA + DADD + DMUL thread
-# instructions, counted by ncu on the thermal workload: 1.584e9 DFMA, 1.338e9 DADD,
-# 0.803e9 DMUL for 16,777,216 particles), and the FP64 peak of a GB300 from its unit
-# counts and clock: 2 FP64 FMA per clock per SM x 152 SMs x 2.07 GHz x 2 operations.
+# FP64 tile kernel: FP64 operations the method needs per particle-step (2 DFMA + DADD +
+# DMUL thread instructions, counted by ncu on the thermal workload with the kernel that
+# evaluated only the deposit branch each particle needs: 1.584e9 DFMA, 1.338e9 DADD,
+# 0.803e9 DMUL for 16,777,216 particles; the branch-free kernel executes 369.8 per
+# particle, the extra ones discarded), and the FP64 peak of a GB300 from its unit counts
+# and clock: 2 FP64 FMA per clock per SM x 152 SMs x 2.07 GHz x 2 operations.
 FP64_OPS_PER_PARTICLE = 316.5
 FP64_PEAK_TFLOPS = 2 * 152 * 2.07e9 * 2 / 1e12
 
