@@ -44,7 +44,8 @@ constexpr int PSX = 10, PSY = 10, PSZ = 9;   // z-paired staged fields: x, y -1.
 constexpr int PS = PSX * PSY * PSZ;          // pairs per component
 // Shared memory of the tile kernel, in order: the warps' record queues; the z-paired
 // fields; the J tile, which first receives the six raw E, B boxes from TMA (it is
-// cleared once they have been converted to pairs); the mbarrier.  Offsets are
+// cleared once they have been converted to pairs); the warps' staged movers; the
+// mbarrier.  Offsets are
 // multiples of 128 bytes.
 __host__ __device__ constexpr size_t align128(size_t b) { return (b + 127) / 128 * 128; }
 constexpr int QWORDS_ = (QCAP_ * 14 > 32 * 14 + 16 ? QCAP_ * 14 : 32 * 14 + 16);   // QWORDS below
@@ -56,9 +57,13 @@ template <typename T> __host__ __device__ constexpr size_t jtile_bytes() {
     return align128((size_t)JT_ELEMS * 8 > (size_t)6 * box_stride<T>() * sizeof(T) ? (size_t)JT_ELEMS * 8
                                                                                   : (size_t)6 * box_stride<T>() * sizeof(T));
 }
+constexpr int MQ = 32;   // staged movers per warp (a particle step adds at most 32)
+template <typename T> __host__ __device__ constexpr size_t movers_bytes() {
+    return align128((size_t)(Prec<T>::THREADS / 32) * MQ * sizeof(Rec<T>));
+}
 template <typename T> constexpr size_t tile_smem_bytes() {
     // + 128: the kernel rounds the dynamic shared base up to a 128-byte boundary
-    return region_a_bytes<T>() + pairs_bytes<T>() + jtile_bytes<T>() + 16 + 128;
+    return region_a_bytes<T>() + pairs_bytes<T>() + jtile_bytes<T>() + movers_bytes<T>() + 16 + 128;
 }
 
 __device__ __forceinline__ void block_add_double(double v, double* dst) {
@@ -72,18 +77,6 @@ __device__ __forceinline__ void block_add_double(double v, double* dst) {
         for (int w = 0; w < (int)(blockDim.x >> 5); ++w) s += red[w];
         atomicAdd(dst, s);
     }
-}
-
-// Reserve one slot per set lane in a device list, one atomic per warp.
-__device__ __forceinline__ int warp_reserve(int* counter, bool want) {
-    unsigned m = __ballot_sync(0xffffffffu, want);
-    if (m == 0) return -1;
-    int lane = threadIdx.x & 31;
-    int leader = __ffs(m) - 1;
-    int base = 0;
-    if (lane == leader) base = atomicAdd(counter, __popc(m));
-    base = __shfl_sync(0xffffffffu, base, leader);
-    return want ? base + __popc(m & ((1u << lane) - 1)) : -1;
 }
 
 // Index of the shared J tile element of (component, local x, y, z), -1..9 each.
@@ -264,6 +257,25 @@ template <> struct RowCells<2> {
     static __device__ __forceinline__ int key(const int c[2]) { return c[0] >= 0 ? c[0] : c[1]; }
 };
 
+// Write a warp's mq staged movers to the global mover list: one counter atomic per
+// batch (the only global atomic whose result a warp waits for), then the records by
+// the lanes (warp-collective).
+template <typename T>
+__device__ __forceinline__ void movers_flush(const PushArgs<T>& A, const Rec<T>* sM, int& mq, int lane) {
+    __syncwarp();
+    int base = 0;
+    if (lane == 0) base = atomicAdd(&A.ctr->mover_count[A.parity], mq);
+    base = __shfl_sync(0xffffffffu, base, 0);
+    bool over = false;
+    for (int j = lane; j < mq; j += 32) {
+        if (base + j < A.mover_cap) A.movers[base + j] = sM[j];
+        else over = true;
+    }
+    if (over) atomicOr(&A.ctr->err, ERRB_OVERFLOW);
+    __syncwarp();
+    mq = 0;
+}
+
 // One CTA per tile.  The tile's particles are read from one SoA block and written to
 // the other, grouped by the cell each particle starts the step in: the block read is
 // grouped by the cells of the step before, so only the particles that crossed a cell
@@ -294,7 +306,8 @@ k_tile_push(const __grid_constant__ CUtensorMap tE0, const __grid_constant__ CUt
     unsigned char* sJ = smem + region_a_bytes<T>() + pairs_bytes<T>();
     T* sF = reinterpret_cast<T*>(sJ);                       // raw boxes, then the J tile
     const uint32_t sJa = smem_u32(sJ);
-    uint64_t* bar = reinterpret_cast<uint64_t*>(sJ + jtile_bytes<T>());
+    Rec<T>* sM = reinterpret_cast<Rec<T>*>(sJ + jtile_bytes<T>()) + (threadIdx.x >> 5) * MQ;   // this warp's movers
+    uint64_t* bar = reinterpret_cast<uint64_t*>(sJ + jtile_bytes<T>() + movers_bytes<T>());
     __shared__ int s_off[TILE_CELLS];   // next free output slot of each input cell's range
     __shared__ int s_hn[TILE_CELLS];    // cell histogram of the output
     __shared__ int s_wsum[8];
@@ -400,6 +413,7 @@ k_tile_push(const __grid_constant__ CUtensorMap tE0, const __grid_constant__ CUt
     double kacc = 0.0;
     int left = 0;                 // particles this lane moved out of the tile or removed
     int esc = 0;                  // of those, removed at an open x face
+    int mq = 0;                   // staged movers of this warp (warp-uniform)
     // the next particle's state, loaded one particle step ahead (L1-cached loads: the
     // R slots of a lane share a 32-byte sector)
     int n_lc = HOLE;
@@ -545,8 +559,9 @@ k_tile_push(const __grid_constant__ CUtensorMap tE0, const __grid_constant__ CUt
             }
             q_push(Q, qn, active && !summed, tile_index(0, x, y, z), v, crossed,
                    tile_index(0, x + s[0], y + s[1], z + s[2]), v2, lane, sJa, qoff);
-            // movers: to the global list with their wrapped global cell; a particle that
-            // left an open x face is removed instead
+            // movers: staged in shared memory with their wrapped global cell and written to
+            // the global list in batches; a particle that left an open x face is removed
+            // instead
             int gxm = 0;
             if (move) {
                 gxm = x_after(A.g, ox + x + s[0]);
@@ -555,10 +570,10 @@ k_tile_push(const __grid_constant__ CUtensorMap tE0, const __grid_constant__ CUt
                     ++esc;
                 }
             }
-            const int slot = warp_reserve(&A.ctr->mover_count[A.parity], move);
-            if (move) {
-                if (slot < A.mover_cap) {
-                    Rec<T> rc;
+            if (const unsigned mm = __ballot_sync(0xffffffffu, move)) {
+                if (mq + __popc(mm) > MQ) movers_flush(A, sM, mq, lane);
+                if (move) {
+                    Rec<T>& rc = sM[mq + __popc(mm & ((1u << lane) - 1u))];
                     const int gy = wrap_idx(oy + y + s[1], A.g.n[1]);
                     const int gz = wrap_idx(oz + z + s[2], A.g.n[2]);
                     rc.cell = (gz * A.g.n[1] + gy) * A.g.n[0] + gxm;
@@ -570,15 +585,14 @@ k_tile_push(const __grid_constant__ CUtensorMap tE0, const __grid_constant__ CUt
                     rc.u[1] = u[1];
                     rc.u[2] = u[2];
                     rc.w = w;
-                    A.movers[slot] = rc;
-                } else {
-                    atomicOr(&A.ctr->err, ERRB_OVERFLOW);
                 }
+                mq += __popc(mm);
             }
         }
         if (qn) q_drain(Q, qn, lane, sJa, qoff);   // the flush stages its sums in the queue
         flush_warp<T>(acc, key >= 0 ? tile_index(0, key & 7, (key >> 3) & 7, key >> 6) : -1, lane, Q, sJa, qoff);
     }
+    if (mq) movers_flush(A, sM, mq, lane);
     left = __reduce_add_sync(0xffffffffu, left);
     esc = __reduce_add_sync(0xffffffffu, esc);
     if (lane == 0 && left) atomicAdd(&s_left, left);
