@@ -75,6 +75,7 @@ def lib():
                                   ctypes.POINTER(_dp), ctypes.POINTER(_dp), _dp]
             L.or_run.argtypes = [_ip, _dp, ctypes.c_double, _dp, ctypes.c_int, _dp, _lp,
                                  ctypes.POINTER(_dp), ctypes.POINTER(_dp), ctypes.c_long, _dp, ctypes.c_long, _dp]
+            L.or_window_shift.argtypes = [_ip, _dp, _dp, ctypes.c_int, _lp, ctypes.POINTER(_dp), ctypes.POINTER(_dp)]
             L.or_gauss_x.argtypes = [_ip, _dp, _dp, _dp]
             L.or_gauss_x.restype = ctypes.c_double
             _lib = L
@@ -240,6 +241,92 @@ def run(n, d, dt, F, species, nsteps=1, step0=0, laser=None):
     las = None if laser is None else np.ascontiguousarray(laser, dtype=np.float64)
     lib().or_run(pn, pd, dt, _p(F), ns, _p(qm), npc.ctypes.data_as(_lp), ptrs, cptrs, nsteps, _p(diag), int(step0),
                  None if las is None else _p(las))
+    return diag
+
+
+# --------------------------------------------------------------------------
+# Moving window (section 2.2, the operations at the end of a cycle; section 4, the
+# laser-wakefield run).  ``window`` is a dict:
+#   start, every  the window moves one cell along +x after every cycle s with
+#                 s >= start and (s - start) % every == every - 1;
+#   species       index of the species that receives the new plasma;
+#   ppc           (px, py, pz): the new plasma of a cell is a px x py x pz lattice at
+#                 offsets (2a + 1) / (2 p) along each dimension, at rest;
+#   density, x0, ramp   its density at absolute x (cell units): density * clip((x -
+#                 x0) / ramp, 0, 1) (a step at x0 when ramp = 0); a particle carries
+#                 weight density(x) dV / (px py pz), and none is made where it is 0.
+# ``origin`` is the absolute x (cells) of the window's cell 0: the number of moves.
+
+def window_moves_before(window, step):
+    """Moves made by the cycles before ``step``."""
+    s0, e = int(window["start"]), int(window["every"])
+    return max(0, (int(step) - s0) // e) if step > s0 else 0
+
+
+def window_moves_after(window, step):
+    """Whether cycle ``step`` ends with a move."""
+    s0, e = int(window["start"]), int(window["every"])
+    return step >= s0 and (step - s0) % e == e - 1
+
+
+def window_shift(n, d, F, species):
+    """One move of the window (open x only): E and B shift one cell toward -x with a
+    vacuum last column, particle cells drop by one and cell 0 leaves (weight 0)."""
+    n_, d_, pn, pd = _grid(n, d)
+    ns = len(species)
+    npc = np.array([s.n for s in species], dtype=np.int64)
+    ptrs = (_dp * ns)(*[_p(s.Q) for s in species])
+    cptrs = (_dp * ns)(*[_p(s.C) for s in species])
+    lib().or_window_shift(pn, pd, _p(F), ns, npc.ctypes.data_as(_lp), ptrs, cptrs)
+
+
+def window_plasma(n, d, window, origin):
+    """The new plasma of the window's last column when its cell 0 is at absolute x =
+    ``origin``: a (7, m) array (positions in window cell units, momenta 0, weights),
+    ordered by z cell, y cell, z offset, y offset, x offset (x fastest)."""
+    nx, ny, nz = int(n[0]), int(n[1]), int(n[2])
+    px, py, pz = (int(v) for v in window["ppc"])
+    offx = (2 * np.arange(px) + 1) / (2.0 * px)
+    offy = (2 * np.arange(py) + 1) / (2.0 * py)
+    offz = (2 * np.arange(pz) + 1) / (2.0 * pz)
+    X = float(origin + nx - 1) + offx                    # absolute x of the x offsets
+    ramp = float(window["ramp"])
+    if ramp > 0:
+        prof = float(window["density"]) * np.clip((X - float(window["x0"])) / ramp, 0.0, 1.0)
+    else:
+        prof = float(window["density"]) * (X >= float(window["x0"]))
+    w = prof * d[0] * d[1] * d[2] / (px * py * pz)
+    a_on = np.nonzero(w > 0)[0]
+    rows = []
+    for k in range(nz):
+        for j in range(ny):
+            for c in range(pz):
+                for b in range(py):
+                    for a in a_on:
+                        rows.append((nx - 1 + offx[a], j + offy[b], k + offz[c], 0.0, 0.0, 0.0, w[a]))
+    if not rows:
+        return np.zeros((7, 0))
+    return np.array(rows, dtype=np.float64).T
+
+
+def run_window(n, d, dt, F, species, nsteps, window, step0=0, laser=None):
+    """``run`` with the moving window: after each cycle that ends with a move, the
+    window shifts and species ``window["species"]`` receives the new column's plasma
+    (appended in the order of ``window_plasma``).  Returns the (nsteps, 3) energy
+    history."""
+    origin = window_moves_before(window, step0)
+    diag = np.zeros((nsteps, 3))
+    for s in range(step0, step0 + nsteps):
+        diag[s - step0] = run(n, d, dt, F, species, 1, step0=s, laser=laser)[0]
+        if window_moves_after(window, s):
+            window_shift(n, d, F, species)
+            origin += 1
+            new = window_plasma(n, d, window, origin)
+            if new.shape[1]:
+                sp = species[int(window["species"])]
+                add = Species(sp.q, sp.m, new)
+                sp.C = np.ascontiguousarray(np.concatenate([sp.C, add.C], axis=1))
+                sp.Q = np.ascontiguousarray(np.concatenate([sp.Q, add.Q], axis=1))
     return diag
 
 

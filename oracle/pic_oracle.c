@@ -550,6 +550,46 @@ void or_run(const int* n, const double* d, double dt, double* F, int ns, const d
     for (long s = 0; s < nsteps; s++) or_step(n, d, dt, F, ns, qm, np, P, C, diag + 3 * s, step0 + s, laser);
 }
 
+/* ------------------------------------------------------------------------ */
+/* Moving window (section 2.2: one of the operations at the end of a cycle, before the
+ * next one begins; section 4: the laser-wakefield run moves its window).  On an open x
+ * dimension (n[3] = 1) the window moves one cell along +x:
+ *   - every E and B value takes the value one cell further along x, and the new last
+ *     value of each line is vacuum (zero): the x-node components Ey, Ez, Bx end at the
+ *     face plane x = nx, the x-half components Ex, By, Bz at x = nx - 1/2;
+ *   - every particle's x cell drops by one; a particle that was in cell 0 leaves the
+ *     window (its weight is set to 0, as for a particle leaving through a face).
+ * J is left as it is (the next cycle recomputes it).  The new plasma of the last
+ * column is added by the caller.                                                  */
+void or_window_shift(const int* n, const double* d, double* F, int ns, const long* np, double** P, double** C)
+{
+    or_grid g = mkgrid(n, d, 0.0);
+    long N = ncells(&g);
+    int nx = n[0];
+    if (!g.open_x) return;
+    for (int comp = 0; comp < 6; comp++) {
+        int x_node = (comp == 1 || comp == 2 || comp == 3);   /* Ey, Ez, Bx */
+        long last = x_node ? nx : nx - 1;
+        double* A = F + comp * N;
+        for (long k = 0; k < n[2]; k++)
+            for (long j = 0; j < n[1]; j++) {
+                for (long i = 0; i < last; i++) A[cell_index(&g, i, j, k)] = A[cell_index(&g, i + 1, j, k)];
+                A[cell_index(&g, last, j, k)] = 0.0;
+            }
+    }
+    for (int s = 0; s < ns; s++) {
+        long cnt = np[s];
+        for (long p = 0; p < cnt; p++) {
+            if (P[s][6 * cnt + p] == 0.0) continue;   /* already removed */
+            if (C[s][p] < 1.0) {
+                P[s][6 * cnt + p] = 0.0;               /* cell 0 leaves the window */
+            } else {
+                C[s][p] -= 1.0;
+            }
+        }
+    }
+}
+
 /* Gauss's law for an initial state whose charge varies along x only
  * (section 2.3, Eq. (2) in discrete form): Ex(i+1/2) = Ex(i-1/2) + dx rho(i)
  * along every x line, with zero line mean.  rho_total includes the ion
