@@ -101,6 +101,38 @@ typedef struct pic_laser_desc {
     double yc, zc;
 } pic_laser_desc;
 
+/* Moving window on an open x (section 2.2: an operation at the end of the cycle, before
+ * the next begins; section 4: the laser-wakefield run moves its window along the
+ * pulse).  After every cycle s with s >= start and (s - start) % every == every - 1 the
+ * window moves one cell along +x:
+ *   - every E and B value takes the value one cell further along x; the new last
+ *     value of each x line is zero (the x-node components Ey, Ez, Bx end at the face
+ *     x = n[0], the x-half components Ex, By, Bz at x = n[0] - 1/2); J, which the next
+ *     cycle recomputes, is not moved (pic_get_fields returns the last cycle's J in the
+ *     frame it was deposited in);
+ *   - every particle's x cell drops by one (so a particle's position is always relative
+ *     to the window); a particle that would be in cell -1 leaves the window and is
+ *     counted in n_escaped like one that leaves through a face;
+ *   - species `species` receives the plasma of the new last column, at rest
+ *     (u^{n+1/2} = 0): a ppc[0] x ppc[1] x ppc[2] lattice per cell at offsets
+ *     (2a + 1) / (2 ppc[d]) along each dimension, with weight
+ *     density(X) d[0] d[1] d[2] / (ppc[0] ppc[1] ppc[2]), where X is the particle's
+ *     absolute x in cells (window cell + moves so far) and
+ *     density(X) = density * clamp((X - x0) / ramp, 0, 1) (a step at x0 when ramp = 0);
+ *     no particle is made where density(X) = 0.  With track_ids the new particles get
+ *     the ids after those loaded, in the order z cell, y cell, z offset, y offset,
+ *     x offset (x fastest), move after move.
+ * Cell values move exactly (no interpolation); the window moves one whole cell at a
+ * time.  every = ceil(d[0] / dt) keeps it at or behind the speed of light. */
+typedef struct pic_window_desc {
+    int32_t start;        /* first cycle that may end with a move (>= 0) */
+    int32_t every;        /* cycles per move (>= 1) */
+    int32_t species;      /* index of the species that receives the new plasma */
+    int32_t ppc[3];       /* lattice of the new plasma per cell (each >= 1, product <= 4096) */
+    double density;       /* plateau density (> 0) */
+    double x0, ramp;      /* density profile along absolute x (cells); ramp >= 0 */
+} pic_window_desc;
+
 /* A particle species (section 2.1, Eqs. (8)-(11)): q, m per physical particle;
  * a super-particle of weight w carries q w and m w. */
 typedef struct pic_species_desc {
@@ -122,14 +154,16 @@ typedef struct pic_diag {
     double U_B;              /* 1/2 dV sum B^n^2, B^n = B^{n-1/2} - dt/2 curl E^n (Eq. (21)) */
     double K_half;           /* sum w m (gamma^{n-1/2} - 1) over all species */
     double gauss_max;        /* max_nodes |div E^n - rho^n - rho_ion| (Eq. (2)) */
-    double gauss_change_max; /* max_nodes |G^n - G^ref|; G^ref = G at the first pic_diagnostics */
+    double gauss_change_max; /* max_nodes |G^n - G^ref|; G^ref = G at the first pic_diagnostics (taken
+                                again at the first call after a moving-window move) */
     double rho_max;          /* max_nodes |rho^n| (electrons + ions) */
     double cont_max;         /* max_nodes |(rho^n - rho^{n-1})/dt + div J^{n-1/2}| (Eq. (12)) when the
-                                previous pic_diagnostics call was exactly one step earlier, else NaN */
+                                previous pic_diagnostics call was exactly one step earlier and the
+                                window did not move in between, else NaN */
     double J_max;            /* max |J^{n-1/2}| over components and cells */
     int64_t n_alive;         /* particles held, all species */
     int64_t n_spilled;       /* particles currently outside their tile segment (spill list) */
-    int64_t n_escaped;       /* particles removed through the open x faces so far */
+    int64_t n_escaped;       /* particles removed through the open x faces or by the window so far */
 } pic_diag;
 
 /* Create a context: validates n, d and the CFL bound of Eq. (15) (section 2.3),
@@ -153,6 +187,16 @@ pic_status pic_load_species(pic_ctx* ctx, const pic_species_desc* desc, int32_t*
  * bc_x = 1; PIC_ERR_ARG for a plane outside 1..n[0]-1. */
 pic_status pic_set_laser(pic_ctx* ctx, const pic_laser_desc* laser);
 
+/* Set the moving window of an open x.  Call it before the species that receives the
+ * new plasma is loaded: that species' tile segments are then sized for the plateau
+ * density everywhere (a tile fills up as the plasma comes in).  PIC_ERR_STATE without
+ * bc_x = 1, after stepping, or when the species is already loaded; PIC_ERR_ARG for
+ * out-of-range values.  NULL switches the window off (before stepping only). */
+pic_status pic_set_moving_window(pic_ctx* ctx, const pic_window_desc* window);
+
+/* Moves of the window so far (0 without a window). */
+int64_t pic_window_moves(const pic_ctx* ctx);
+
 /* Advance nsteps cycles (section 2.2, Fig. 2), asynchronously on the context's
  * stream.  J of the last cycle is kept for pic_get_fields and pic_diagnostics. */
 pic_status pic_step(pic_ctx* ctx, int32_t nsteps);
@@ -165,9 +209,10 @@ pic_status pic_sync(pic_ctx* ctx);
 pic_status pic_get_fields(pic_ctx* ctx, double* E, double* B, double* J, int32_t device_pointers);
 
 /* Copy one species out as 7 rows of *n FP64 values: X, Y, Z (cell units), ux, uy,
- * uz, w.  With track_ids the rows are in load order (*n = the number loaded; a
- * particle removed through an open x face reads as NaN in every row), else in tile
- * order (*n = the number alive).  out may be NULL to query *n.  Synchronises. */
+ * uz, w.  With track_ids the rows are in load order (*n = the number loaded, plus the
+ * number a moving window has injected; a particle removed through an open x face or
+ * by the window reads as NaN in every row), else in tile order (*n = the number
+ * alive).  out may be NULL to query *n.  Synchronises. */
 pic_status pic_get_particles(pic_ctx* ctx, int32_t species, double* out, int64_t* n, int32_t device_pointers);
 
 /* FP64 device reductions of the current state (section 3.3 diagnostics).

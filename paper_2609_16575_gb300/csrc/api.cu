@@ -135,12 +135,20 @@ void update_jscale(pic_ctx* c) {
 // One cycle of section 2.2, Fig. 2: Faraday half step, per species the tile push, the
 // spill-list push, the mover append (and the periodic tile sort), Faraday half step,
 // Ampere.  J is cleared by Ampere unless keep_j.  Expects J = 0 on entry.
+bool window_moves_after(const pic_ctx* c, int64_t step) {
+    if (!c->window_on) return false;
+    const pic_window_desc& W = c->window;
+    return step >= W.start && (step - W.start) % W.every == W.every - 1;
+}
+
 pic_status step_once(pic_ctx* c, double* rec, bool keep_j) {
     c->jscale_J = c->jscale;
+    const bool move = window_moves_after(c, c->step);
     pic_status st = launch_faraday_half(c, rec);
     if (st != PIC_OK) return st;
-    for (auto& sp : c->species) {
-        st = launch_push_species(c, sp, (int)(c->step & 1), rec ? rec + 2 : nullptr);
+    for (size_t k = 0; k < c->species.size(); ++k) {
+        st = launch_push_species(c, c->species[k], (int)(c->step & 1), rec ? rec + 2 : nullptr, move ? 1 : 0,
+                                 move && (int)k == c->window.species);
         if (st != PIC_OK) return st;
     }
     st = launch_faraday_half(c, nullptr);
@@ -154,6 +162,11 @@ pic_status step_once(pic_ctx* c, double* rec, bool keep_j) {
     if (c->g.open_x) {
         st = launch_open_x_after_ampere(c);    // Mur condition on the two x faces
         if (st != PIC_OK) return st;
+    }
+    if (move) {   // the end of the cycle: the window moves one cell along +x
+        st = launch_window_shift(c);
+        if (st != PIC_OK) return st;
+        c->window_moves++;
     }
     c->step++;
     return PIC_OK;
@@ -329,6 +342,10 @@ pic_status pic_load_species(pic_ctx* c, const pic_species_desc* d, int32_t* spec
 pic_status pic_step(pic_ctx* c, int32_t nsteps) {
     if (!c || nsteps < 0) return PIC_ERR_ARG;
     if (nsteps == 0) return PIC_OK;
+    if (c->window_on && c->window.species >= (int)c->species.size()) {
+        c->err = "pic_step: the moving window's species is not loaded";
+        return PIC_ERR_STATE;
+    }
     cudaSetDevice(c->desc.device);
     update_jscale(c);
     if (c->j_dirty) {
@@ -370,6 +387,45 @@ pic_status pic_set_laser(pic_ctx* c, const pic_laser_desc* laser) {
     return PIC_OK;
 }
 
+pic_status pic_set_moving_window(pic_ctx* c, const pic_window_desc* w) {
+    if (!c) return PIC_ERR_ARG;
+    if (!c->g.open_x) {
+        c->err = "pic_set_moving_window needs an open x (bc_x = 1)";
+        return PIC_ERR_STATE;
+    }
+    if (c->step != 0) {
+        c->err = "pic_set_moving_window must precede stepping";
+        return PIC_ERR_STATE;
+    }
+    if (!w) {
+        c->window_on = false;
+        return PIC_OK;
+    }
+    if (w->start < 0 || w->every < 1 || w->species < 0 || !(w->density > 0) || !std::isfinite(w->density) ||
+        !std::isfinite(w->x0) || !(w->ramp >= 0) || !std::isfinite(w->ramp)) {
+        c->err = "pic_set_moving_window: start >= 0, every >= 1, species >= 0, density > 0, ramp >= 0";
+        return PIC_ERR_ARG;
+    }
+    long long ppc = 1;
+    for (int k = 0; k < 3; ++k) {
+        if (w->ppc[k] < 1) return PIC_ERR_ARG;
+        ppc *= w->ppc[k];
+    }
+    if (w->ppc[0] > MAX_WINDOW_PPCX || ppc > 4096) {
+        c->err = "pic_set_moving_window: ppc[0] <= 64 and ppc[0] ppc[1] ppc[2] <= 4096";
+        return PIC_ERR_ARG;
+    }
+    if (w->species < (int)c->species.size()) {
+        c->err = "pic_set_moving_window must precede loading the species it fills";
+        return PIC_ERR_STATE;
+    }
+    c->window = *w;
+    c->window_on = true;
+    return PIC_OK;
+}
+
+int64_t pic_window_moves(const pic_ctx* c) { return c ? c->window_moves : 0; }
+
 pic_status pic_sync(pic_ctx* c) {
     if (!c) return PIC_ERR_ARG;
     cudaSetDevice(c->desc.device);
@@ -409,7 +465,7 @@ pic_status pic_get_particles(pic_ctx* c, int32_t species, double* out, int64_t* 
     pic_status st = pic_sync(c);
     if (st != PIC_OK && st != PIC_ERR_TILE_OVERFLOW) return st;
     SpeciesDev& s = c->species[species];
-    int64_t alive = c->desc.track_ids ? s.n_loaded : count_alive(c, s, nullptr);
+    int64_t alive = c->desc.track_ids ? s.n_loaded + s.n_injected : count_alive(c, s, nullptr);
     if (alive < 0) return cuda_fail(c, cudaGetLastError(), "count_alive");
     *n = alive;
     if (!out || alive == 0) return PIC_OK;

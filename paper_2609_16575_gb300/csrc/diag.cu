@@ -171,7 +171,11 @@ static pic_status diag_t(pic_ctx* c, pic_diag* out) {
                                                      s.m, s.q / dv, c->rho, c->dacc);
         GBPIC_CHECK(c, cudaGetLastError());
     }
-    const int cont_valid = (c->rho_prev_step >= 0 && c->step == c->rho_prev_step + 1 && c->j_dirty) ? 1 : 0;
+    // a window move changes the frame: no continuity check across it, and the Gauss
+    // reference is taken again
+    const int cont_valid = (c->rho_prev_step >= 0 && c->step == c->rho_prev_step + 1 && c->j_dirty &&
+                            c->window_moves_at_rho == c->window_moves) ? 1 : 0;
+    if (c->gref_valid && c->window_moves_at_gref != c->window_moves) c->gref_valid = false;
     {
         LaunchScope ls(c, KC_OTHER);
         k_nodes<T><<<1024, 256, 0, c->stream>>>(g, f, dd, c->desc.rho_ion, dt, c->jscale_J, c->rho, c->rho_prev, c->gref,
@@ -199,8 +203,10 @@ static pic_status diag_t(pic_ctx* c, pic_diag* out) {
         GBPIC_CHECK(c, cudaMemcpy(&h, s.ctr, sizeof(Counters), cudaMemcpyDeviceToHost));
         out->n_escaped += h.escaped;
     }
+    if (!c->gref_valid) c->window_moves_at_gref = c->window_moves;
     c->gref_valid = true;
     c->rho_prev_step = c->step;
+    c->window_moves_at_rho = c->window_moves;
     return PIC_OK;
 }
 

@@ -19,6 +19,7 @@ constexpr int TILE_CELLS = 512;
 constexpr int SB = 10;           // staged E/B extent per dim: local cells -1..8
 constexpr int SJ = 11;           // shared J extent per dim: local nodes/edges -1..9
 constexpr int SJ3 = SJ * SJ * SJ;
+constexpr int MAX_WINDOW_PPCX = 64;  // moving window: largest lattice of the new plasma along x
 constexpr int PUSH_WARPS_MAX = 16;   // the tile kernel's CTA has at most 512 threads
 constexpr int HOLE = -1;             // cell value of a slot whose particle left the tile last step
 
@@ -533,6 +534,7 @@ struct SpeciesDev {
     int spill_cap = 0;
     Counters* ctr = nullptr;
     double jscale = 0;               // physical J per fixed-point unit from this species
+    int64_t n_injected = 0;          // particles a moving window has added (ids from n_loaded on)
     std::vector<int> h_seg_start, h_cap;
 };
 
@@ -592,6 +594,12 @@ struct pic_ctx {
     bool laser_on = false;
     pic_laser_desc laser{};
     void* mur_old = nullptr;
+    // moving window (open x)
+    bool window_on = false;
+    pic_window_desc window{};
+    int64_t window_moves = 0;
+    int64_t window_moves_at_rho = -1;   // window_moves when rho_prev was taken
+    int64_t window_moves_at_gref = 0;   // window_moves when the Gauss reference was taken
 };
 
 namespace gbpic {
@@ -599,7 +607,9 @@ namespace gbpic {
 // launchers (defined in the .cu files)
 pic_status launch_faraday_half(pic_ctx* c, double* rec);
 pic_status launch_ampere(pic_ctx* c, bool zero_j);
-pic_status launch_push_species(pic_ctx* c, SpeciesDev& s, int parity, double* krec);
+pic_status launch_push_species(pic_ctx* c, SpeciesDev& s, int parity, double* krec, int xshift, bool inject);
+pic_status launch_window_shift(pic_ctx* c);
+bool window_moves_after(const pic_ctx* c, int64_t step);
 pic_status launch_backpush(pic_ctx* c, SpeciesDev& s);
 template <typename T> pic_status curl_to_b(pic_ctx* c, T* const E[3], T* const B[3], double coef);
 template <typename T> pic_status curl_to_e(pic_ctx* c, T* const E[3], T* const B[3], double coef);

@@ -31,6 +31,7 @@ template <typename T> struct PushArgs {
     int parity;
     double* krec;   // optional: accumulate sum w m ((g_old + g_new)/2 - 1) here
     double mass;
+    int xshift;     // 1: the window moves after this cycle (stored x cells drop by one)
 };
 
 template <typename T> __host__ __device__ constexpr int box_elems() { return SB * SB * Prec<T>::BX; }
@@ -518,8 +519,11 @@ k_tile_push(const __grid_constant__ CUtensorMap tE0, const __grid_constant__ CUt
                     Wa[k] = s[k] == 0 ? d1[k] + T(0.5) * h * D : T(0.5) * (d1[k] + up);
                 }
                 segment_values_pairs(cw, Fa, Wa, v);
-                const int nx = x + s[0], ny = y + s[1], nz = z + s[2];
-                stay = nx >= 0 && nx < ext[0] && ny >= 0 && ny < ext[1] && nz >= 0 && nz < ext[2];
+                // when the window moves after this cycle the stored x cell drops by one; a
+                // particle that crossed the window's front face leaves all the same
+                const int nx = x + s[0] - A.xshift, ny = y + s[1], nz = z + s[2];
+                stay = nx >= 0 && nx < ext[0] && ny >= 0 && ny < ext[1] && nz >= 0 && nz < ext[2] &&
+                       (A.xshift == 0 || ox + x + s[0] < A.g.n[0]);
                 move = !stay;
                 if (stay) nlc = nx | (ny << 3) | (nz << 6);
                 // the particle's slot in its start cell's output range: the state after
@@ -566,6 +570,7 @@ k_tile_push(const __grid_constant__ CUtensorMap tE0, const __grid_constant__ CUt
             int gxm = 0;
             if (move) {
                 gxm = x_after(A.g, ox + x + s[0]);
+                if (gxm >= 0) gxm -= A.xshift;   // the window's first column leaves
                 if (gxm < 0) {
                     move = false;
                     ++esc;
@@ -658,8 +663,9 @@ __global__ void __launch_bounds__(256) k_list_push(PushArgs<T> A) {
         }
         const T cw[3] = {A.cq[0] * r.w, A.cq[1] * r.w, A.cq[2] * r.w};
         zigzag_deposit<T>(add, gx, gy, gz, r.d, s, d2, cw);
-        const int nxg = x_after(A.g, gx + s[0]);
-        if (nxg < 0) {   // left an open x face: removed
+        int nxg = x_after(A.g, gx + s[0]);
+        if (nxg >= 0) nxg -= A.xshift;   // a window move: the first column leaves
+        if (nxg < 0) {   // left an open x face (or the window): removed
             atomicAdd(&A.ctr->escaped, 1);
             continue;
         }
@@ -747,6 +753,54 @@ __global__ void __launch_bounds__(256) k_backpush(PushArgs<T> A, const T* B0x, c
 }
 
 // ---------------------------------------------------------------------------
+// Moving window: the plasma of the window's new last column (section 4 set-up), at rest,
+// into the mover list, from where the append places it in its tiles.  Particle t of the
+// column (t = 0 .. m - 1) is, x fastest: x offset a (of the na offsets whose density is
+// not zero), y offset b, z offset c, y cell j, z cell k; its id is id_base + t.
+struct InjectArgs {
+    int nx, ny, py, pz, na;
+    long long m;
+    long long id_base;
+    double offx[MAX_WINDOW_PPCX];   // in-cell x offset of each active x offset
+    double wx[MAX_WINDOW_PPCX];     // weight of a particle at it
+};
+
+template <typename T>
+__global__ void __launch_bounds__(256) k_inject(PushArgs<T> A, InjectArgs I) {
+    const int lane = threadIdx.x & 31;
+    const long long stride = (long long)gridDim.x * blockDim.x;
+    // whole warps iterate together (the counter reservation is a warp vote)
+    for (long long t0 = blockIdx.x * (long long)blockDim.x + (threadIdx.x & ~31); t0 < I.m; t0 += stride) {
+        const long long t = t0 + lane;
+        const bool valid = t < I.m;
+        const unsigned mm = __ballot_sync(0xffffffffu, valid);
+        int base = 0;
+        if (lane == 0) base = atomicAdd(&A.ctr->mover_count[A.parity], __popc(mm));
+        base = __shfl_sync(0xffffffffu, base, 0);
+        if (!valid) continue;
+        long long r = t;
+        const int a = (int)(r % I.na);
+        r /= I.na;
+        const int b = (int)(r % I.py);
+        r /= I.py;
+        const int c = (int)(r % I.pz);
+        r /= I.pz;
+        const int j = (int)(r % I.ny), k = (int)(r / I.ny);
+        Rec<T> rc;
+        rc.cell = (k * I.ny + j) * I.nx + (I.nx - 1);
+        rc.id = (int)(I.id_base + t);
+        rc.d[0] = (T)I.offx[a];
+        rc.d[1] = (T)((2.0 * b + 1.0) / (2.0 * I.py));
+        rc.d[2] = (T)((2.0 * c + 1.0) / (2.0 * I.pz));
+        rc.u[0] = rc.u[1] = rc.u[2] = T(0);
+        rc.w = (T)I.wx[a];
+        const int slot = base + lane;   // the valid lanes are the low ones
+        if (slot < A.mover_cap) A.movers[slot] = rc;
+        else atomicOr(&A.ctr->err, ERRB_OVERFLOW);
+    }
+}
+
+// ---------------------------------------------------------------------------
 // Host launchers.
 
 
@@ -804,9 +858,60 @@ static pic_status launch_tile(pic_ctx* c, PushArgs<T>& A) {
     return PIC_OK;
 }
 
+// The moving window's new column for species s (host part of k_inject): the active x
+// offsets and their weights from the density profile at the particles' absolute x.
 template <typename T>
-static pic_status push_species_t(pic_ctx* c, SpeciesDev& s, int parity, double* krec) {
+static pic_status inject_t(pic_ctx* c, SpeciesDev& s, PushArgs<T>& A) {
+    const pic_window_desc& W = c->window;
+    const Geom& g = c->g;
+    const double* d = c->desc.d;
+    InjectArgs I{};
+    I.nx = g.n[0];
+    I.ny = g.n[1];
+    I.py = W.ppc[1];
+    I.pz = W.ppc[2];
+    const long long origin = c->window_moves + 1;   // cell 0 of the window after this move
+    const int ppc = W.ppc[0] * W.ppc[1] * W.ppc[2];
+    int na = 0;
+    for (int a = 0; a < W.ppc[0]; ++a) {
+        const double off = (2.0 * a + 1.0) / (2.0 * W.ppc[0]);
+        const double X = (double)(origin + g.n[0] - 1) + off;
+        double prof;
+        if (W.ramp > 0) {
+            const double r = (X - W.x0) / W.ramp;
+            prof = W.density * (r < 0.0 ? 0.0 : (r > 1.0 ? 1.0 : r));
+        } else {
+            prof = X >= W.x0 ? W.density : 0.0;
+        }
+        const double w = prof * d[0] * d[1] * d[2] / ppc;
+        if (w > 0) {
+            I.offx[na] = off;
+            I.wx[na] = w;
+            ++na;
+        }
+    }
+    I.na = na;
+    I.m = (long long)na * W.ppc[1] * W.ppc[2] * g.n[1] * g.n[2];
+    if (I.m == 0) return PIC_OK;
+    I.id_base = s.n_loaded + s.n_injected;
+    if (c->desc.track_ids && I.id_base + I.m > 0x7fffffffLL) {
+        c->err = "moving window: more than 2^31 particle ids";
+        return PIC_ERR_TILE_OVERFLOW;
+    }
+    {
+        LaunchScope ls(c, KC_OTHER);
+        const long long blocks = std::min<long long>((I.m + 255) / 256, 8LL * sm_count(c));
+        k_inject<T><<<(unsigned)blocks, 256, 0, c->stream>>>(A, I);
+        GBPIC_CHECK(c, cudaGetLastError());
+    }
+    s.n_injected += I.m;
+    return PIC_OK;
+}
+
+template <typename T>
+static pic_status push_species_t(pic_ctx* c, SpeciesDev& s, int parity, double* krec, int xshift, bool inject) {
     PushArgs<T> A = make_args<T>(c, s, parity, krec, 1.0);
+    A.xshift = xshift;
     const bool ids = c->desc.track_ids != 0, rec = krec != nullptr;
     pic_status st;
     if (ids) st = rec ? launch_tile<T, true, true>(c, A) : launch_tile<T, true, false>(c, A);
@@ -819,6 +924,10 @@ static pic_status push_species_t(pic_ctx* c, SpeciesDev& s, int parity, double* 
         else k_list_push<T, false><<<grid, 256, 0, c->stream>>>(A);
         GBPIC_CHECK(c, cudaGetLastError());
     }
+    if (inject) {
+        st = inject_t<T>(c, s, A);
+        if (st != PIC_OK) return st;
+    }
     {
         LaunchScope ls(c, KC_APPEND);
         if (ids) k_append<T, true><<<grid, 256, 0, c->stream>>>(A);
@@ -829,9 +938,9 @@ static pic_status push_species_t(pic_ctx* c, SpeciesDev& s, int parity, double* 
     return PIC_OK;
 }
 
-pic_status launch_push_species(pic_ctx* c, SpeciesDev& s, int parity, double* krec) {
-    return c->prec == PIC_FP64 ? push_species_t<double>(c, s, parity, krec)
-                               : push_species_t<float>(c, s, parity, krec);
+pic_status launch_push_species(pic_ctx* c, SpeciesDev& s, int parity, double* krec, int xshift, bool inject) {
+    return c->prec == PIC_FP64 ? push_species_t<double>(c, s, parity, krec, xshift, inject)
+                               : push_species_t<float>(c, s, parity, krec, xshift, inject);
 }
 
 template <typename T>

@@ -121,8 +121,13 @@ static pic_status load_t(pic_ctx* c, const pic_species_desc* d, SpeciesDev& s) {
     }
     double wmax = 0;
     memcpy(&wmax, &h_wbits, 8);
-    // tile capacities and segment starts (host), key positions within segments
+    // tile capacities and segment starts (host), key positions within segments; the
+    // species that a moving window fills gets room for the plateau density in every
+    // tile (the plasma comes in at the window's front)
     const double slack = d->capacity_slack > 0 ? d->capacity_slack : 0.25;
+    const bool window_species = c->window_on && c->window.species == (int)c->species.size() - 1;
+    const long long window_ppc =
+        window_species ? (long long)c->window.ppc[0] * c->window.ppc[1] * c->window.ppc[2] : 0;
     s.h_seg_start.assign(ntile, 0);
     s.h_cap.assign(ntile, 0);
     std::vector<int> h_count(ntile, 0);
@@ -130,7 +135,14 @@ static pic_status load_t(pic_ctx* c, const pic_species_desc* d, SpeciesDev& s) {
     for (int t = 0; t < ntile; ++t) {
         long long cnt = 0;
         for (int l = 0; l < TILE_CELLS; ++l) cnt += h_hist[(size_t)t * TILE_CELLS + l];
-        long long cap = cnt + std::max<long long>((long long)std::ceil(slack * cnt), 32);
+        long long want = cnt;
+        if (window_species) {
+            const int tx = t % g.nt[0], ty = (t / g.nt[0]) % g.nt[1], tz = t / (g.nt[0] * g.nt[1]);
+            const long long cells = (long long)std::min(TILE, g.n[0] - tx * TILE) *
+                                    std::min(TILE, g.n[1] - ty * TILE) * std::min(TILE, g.n[2] - tz * TILE);
+            want = std::max(want, cells * window_ppc);
+        }
+        long long cap = want + std::max<long long>((long long)std::ceil(slack * want), 32);
         cap = (cap + 31) / 32 * 32;
         s.h_seg_start[t] = (int)total;
         s.h_cap[t] = (int)cap;
@@ -197,8 +209,9 @@ static pic_status load_t(pic_ctx* c, const pic_species_desc* d, SpeciesDev& s) {
         k_scatter<T><<<grid, 256, 0, c->stream>>>(g, X, U, W, n, hist, pa, c->desc.track_ids);
         GBPIC_CHECK(c, cudaGetLastError());
     }
-    // mover and spill lists
-    s.mover_cap = (int)std::min<long long>(std::max<long long>(n / 4, 65536), 0x7fffff00LL);
+    // mover and spill lists (a window move sends the first cell column of every tile to
+    // the tile before it: an eighth of the particles, plus the new column's plasma)
+    s.mover_cap = (int)std::min<long long>(std::max<long long>(window_species ? total / 4 : n / 4, 65536), 0x7fffff00LL);
     s.spill_cap = (int)std::min<long long>(std::max<long long>(n / 16, 65536), 0x7fffff00LL);
     s.movers = dev_alloc(c, sizeof(Rec<T>) * (size_t)s.mover_cap);
     s.spill = dev_alloc(c, sizeof(Rec<T>) * (size_t)s.spill_cap);
@@ -214,6 +227,10 @@ static pic_status load_t(pic_ctx* c, const pic_species_desc* d, SpeciesDev& s) {
     // for the straight-segment correction) maps to 2^JBITS units
     const double* dd = c->desc.d;
     const double dmin2 = std::min(dd[0] * dd[1], std::min(dd[1] * dd[2], dd[2] * dd[0]));
+    if (window_species) {   // the heaviest particle the window will bring in
+        const pic_window_desc& W = c->window;
+        wmax = std::max(wmax, W.density * dd[0] * dd[1] * dd[2] / (double)window_ppc);
+    }
     const double bound = std::fabs(d->q) * wmax / (c->desc.dt * dmin2) * 1.25;
     s.jscale = bound > 0 ? bound / std::ldexp(1.0, Prec<T>::JBITS) : 0.0;
     return PIC_OK;

@@ -297,6 +297,59 @@ static pic_status open_after_t(pic_ctx* c) {
     return PIC_OK;
 }
 
+// ---------------------------------------------------------------------------
+// Moving window (section 2.2: an operation at the end of the cycle; section 4): every
+// E and B value of an x line takes the value one cell further along +x, and the last
+// value of the line (x = n for the x-node components Ey, Ez, Bx, x = n - 1/2 for the
+// x-half components Ex, By, Bz) becomes zero.  One warp per padded (y, z) line, so the
+// y and z ghost lines move with the lines they copy; the line is moved in place 32
+// values at a time (each chunk is read before any of it is written, and the next chunk
+// starts past what this one wrote).
+template <typename T> struct ShiftArgs {
+    T* F[6];
+    int last[6];   // the last moved x index of each component
+};
+
+template <typename T>
+__global__ void __launch_bounds__(128) k_window_shift(Geom g, ShiftArgs<T> S) {
+    const int lane = threadIdx.x & 31;
+    const long long line = blockIdx.x * 4LL + (threadIdx.x >> 5);
+    if (line >= (long long)g.Gy * g.Gz) return;   // whole warps
+    T* L = S.F[blockIdx.y] + line * g.Px;          // L[i + 1] holds x = i, i = -1 .. Px - 2
+    const int last = S.last[blockIdx.y];
+    for (int x0 = 0; x0 <= last; x0 += 32) {
+        const int i = x0 + lane;
+        const T v = i < last ? L[i + 2] : T(0);
+        __syncwarp();
+        if (i <= last) L[i + 1] = v;
+        __syncwarp();
+    }
+}
+
+template <typename T>
+static pic_status window_shift_t(pic_ctx* c) {
+    const Geom& g = c->g;
+    ShiftArgs<T> S;
+    for (int k = 0; k < 3; ++k) {
+        S.F[k] = static_cast<T*>(c->E[k]);
+        S.F[3 + k] = static_cast<T*>(c->B[k]);
+    }
+    // x nodes: Ey, Ez (E) and Bx (B); x halves: Ex, By, Bz
+    const int n = g.n[0];
+    const int last[6] = {n - 1, n, n, n, n - 1, n - 1};
+    for (int k = 0; k < 6; ++k) S.last[k] = last[k];
+    const long long lines = (long long)g.Gy * g.Gz;
+    dim3 grid((unsigned)((lines + 3) / 4), 6);
+    LaunchScope ls(c, KC_OTHER);
+    k_window_shift<T><<<grid, 128, 0, c->stream>>>(g, S);
+    GBPIC_CHECK(c, cudaGetLastError());
+    return PIC_OK;
+}
+
+pic_status launch_window_shift(pic_ctx* c) {
+    return c->prec == PIC_FP64 ? window_shift_t<double>(c) : window_shift_t<float>(c);
+}
+
 pic_status launch_open_x_before_ampere(pic_ctx* c) {
     return c->prec == PIC_FP64 ? open_before_t<double>(c) : open_before_t<float>(c);
 }

@@ -49,6 +49,12 @@ class pic_laser_desc(ctypes.Structure):
                 ("yc", ctypes.c_double), ("zc", ctypes.c_double)]
 
 
+class pic_window_desc(ctypes.Structure):
+    _fields_ = [("start", ctypes.c_int32), ("every", ctypes.c_int32), ("species", ctypes.c_int32),
+                ("ppc", ctypes.c_int32 * 3), ("density", ctypes.c_double), ("x0", ctypes.c_double),
+                ("ramp", ctypes.c_double)]
+
+
 class pic_species_desc(ctypes.Structure):
     _fields_ = [("q", ctypes.c_double), ("m", ctypes.c_double), ("n", ctypes.c_int64),
                 ("X", ctypes.c_void_p), ("u", ctypes.c_void_p), ("w", ctypes.c_void_p),
@@ -103,6 +109,9 @@ def lib():
             L.pic_adjoint_backward.argtypes = [P, P, P, ctypes.POINTER(ctypes.c_double), ctypes.POINTER(ctypes.c_void_p),
                                                ctypes.c_int32]
             L.pic_set_laser.argtypes = [P, ctypes.POINTER(pic_laser_desc)]
+            L.pic_set_moving_window.argtypes = [P, ctypes.POINTER(pic_window_desc)]
+            L.pic_window_moves.argtypes = [P]
+            L.pic_window_moves.restype = ctypes.c_int64
             L.pic_gauss_check_static.argtypes = [P, ctypes.POINTER(ctypes.c_double), ctypes.POINTER(ctypes.c_double)]
             L.pic_launch_count.argtypes = [P]
             L.pic_launch_count.restype = ctypes.c_int64
@@ -115,7 +124,7 @@ def lib():
             for name in ("pic_init_grid", "pic_set_fields", "pic_load_species", "pic_step", "pic_sync",
                          "pic_get_fields", "pic_get_particles", "pic_diagnostics", "pic_get_history",
                          "pic_set_timing", "pic_kernel_times", "pic_adjoint_forward", "pic_adjoint_backward",
-                         "pic_gauss_check_static", "pic_set_laser"):
+                         "pic_gauss_check_static", "pic_set_laser", "pic_set_moving_window"):
                 getattr(L, name).restype = ctypes.c_int
             _lib = L
     return _lib
@@ -324,6 +333,16 @@ class Context:
         """Laser sheet of an open x (see pic_laser_desc)."""
         L = pic_laser_desc(a0, omega, w0, tau, t_peak, int(plane), 0, yc, zc)
         _check(self.ptr, lib().pic_set_laser(self.ptr, ctypes.byref(L)), "pic_set_laser")
+
+    def set_moving_window(self, start, every, species, ppc, density, x0, ramp):
+        """Moving window of an open x (see pic_window_desc); before loading `species`."""
+        W = pic_window_desc(int(start), int(every), int(species), (ctypes.c_int32 * 3)(*[int(v) for v in ppc]),
+                            float(density), float(x0), float(ramp))
+        _check(self.ptr, lib().pic_set_moving_window(self.ptr, ctypes.byref(W)), "pic_set_moving_window")
+
+    def window_moves(self):
+        """Moves of the window so far."""
+        return int(lib().pic_window_moves(self.ptr))
 
     def gauss_check_static(self):
         """(gauss_max, rho_max) from the allocation-free entry point."""
