@@ -228,6 +228,27 @@ def other_workloads(torch, peak):
                                    "yee": yee_line(kt, ncell, peak),
                                    "note": "steps 4-23 of the run: the pulse has not reached the plasma yet"}
     ctx.close()
+    # the same run with the moving window: a one-cell move every ceil(dx / dt) = 3 cycles
+    # from the first cycle on, the new column's plasma injected at each move
+    wl = W.lwfa(window_start=0)
+    ctx = gbpic.Context(wl.n, wl.d, wl.dt, precision=gbpic.PIC_FP32, rho_ion=wl.rho_ion, bc_x=1)
+    ctx.set_laser(*wl.laser.as_tuple())
+    ctx.set_moving_window(*wl.window.as_tuple())
+    s = wl.species[0]
+    ctx.load_species_array(s.q, s.m, s.P, s.momenta_at_half_step)
+    time_steps(ctx, torch, 3)
+    n_before, m_before = ctx.diagnostics()["n_alive"], ctx.window_moves()
+    steps = 30
+    ms, kt = time_steps(ctx, torch, steps)
+    n_after, m_after = ctx.diagnostics()["n_alive"], ctx.window_moves()
+    npart = 0.5 * (n_before + n_after)
+    out["lwfa_512x128x128_window_f32"] = {
+        "value": npart * steps / (ms / 1e3), "unit": UNIT, "steps": steps, "ms_per_step": ms / steps,
+        "particles": [n_before, n_after], "moves": m_after - m_before, "every": wl.window.every,
+        "kernels": {k: {"launches": v[0], "ms": round(v[1], 3)} for k, v in kt.items() if v[0]},
+        "note": "steps 4-33 with a moving window; 'other' holds the field shift, the injection, the "
+                "laser sheet and the Mur faces"}
+    ctx.close()
     return out
 
 

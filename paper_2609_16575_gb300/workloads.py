@@ -42,6 +42,7 @@ class Workload:
     steps: int = 1
     bc_x: int = 0                      # 1: open x (absorbing faces, particles leaving in x removed)
     laser: object = None               # LaserInput for an open x
+    window: object = None              # WindowInput (moving window) for an open x
 
     @property
     def ncells(self) -> int:
@@ -151,8 +152,29 @@ class LaserInput:
         return (self.a0, self.omega, self.w0, self.tau, self.t_peak, self.plane, self.yc, self.zc)
 
 
+@dataclass
+class WindowInput:
+    """Moving window of an open x (see pic_window_desc): moves one cell along +x after
+    every `every`-th cycle from `start`; the new column gets a ppc lattice of the density
+    profile density * clip((X - x0) / ramp, 0, 1) at rest."""
+    start: int
+    every: int
+    species: int
+    ppc: tuple
+    density: float
+    x0: float
+    ramp: float
+
+    def as_tuple(self):
+        return (self.start, self.every, self.species, self.ppc, self.density, self.x0, self.ramp)
+
+    def as_dict(self):
+        return dict(start=self.start, every=self.every, species=self.species, ppc=self.ppc, density=self.density,
+                    x0=self.x0, ramp=self.ramp)
+
+
 def lwfa(n=(512, 128, 128), ppc_per_dim=2, density=0.01, x0=20, ramp=50, a0=2.0, w0_lambda=8.0, fwhm_periods=10.0,
-         courant=0.5, steps=2000, plane=2) -> Workload:
+         courant=0.5, steps=2000, plane=2, window_start=None) -> Workload:
     """Laser wakefield in an underdense plasma (units of the laser: omega0 = 1, c = 1,
     lambda = 2 pi, density in units of the critical density): dx = lambda/20,
     dy = dz = lambda/8; open x (absorbing faces), periodic y and z; electrons on a
@@ -161,7 +183,9 @@ def lwfa(n=(512, 128, 128), ppc_per_dim=2, density=0.01, x0=20, ramp=50, a0=2.0,
     linearly polarised (y) Gaussian pulse (a0, waist w0_lambda wavelengths, intensity
     FWHM fwhm_periods periods) enters through a current sheet on the node plane
     `plane`, peaking two FWHM after t = 0.  Returns the workload (bc_x = 1) with
-    `.laser` set."""
+    `.laser` set, and with `.window` set when window_start is given: a window moving one
+    cell every ceil(dx / (c dt)) cycles from that cycle on (at or behind the speed of
+    light) that brings in the same lattice and density profile."""
     lam = 2 * np.pi
     dd = (lam / 20, lam / 8, lam / 8)
     nn = tuple(int(v) for v in n)
@@ -178,6 +202,9 @@ def lwfa(n=(512, 128, 128), ppc_per_dim=2, density=0.01, x0=20, ramp=50, a0=2.0,
     tau = fwhm_periods * lam
     wl.laser = LaserInput(a0, 1.0, w0_lambda * lam, tau, 2.0 * tau, plane, nn[1] / 2.0, nn[2] / 2.0)
     wl.bc_x = 1
+    if window_start is not None:
+        every = int(np.ceil(dd[0] / wl.dt))
+        wl.window = WindowInput(int(window_start), every, 0, (ppc_per_dim,) * 3, float(density), float(x0), float(ramp))
     return wl
 
 
