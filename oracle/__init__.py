@@ -72,9 +72,10 @@ def lib():
             L.or_backpush.argtypes = [_ip, _dp, ctypes.c_double, _dp, _dp, ctypes.c_double, ctypes.c_double,
                                       ctypes.c_long, _dp, _dp]
             L.or_step.argtypes = [_ip, _dp, ctypes.c_double, _dp, ctypes.c_int, _dp, _lp,
-                                  ctypes.POINTER(_dp), ctypes.POINTER(_dp), _dp]
+                                  ctypes.POINTER(_dp), ctypes.POINTER(_dp), _dp, ctypes.c_long, _dp, _dp]
             L.or_run.argtypes = [_ip, _dp, ctypes.c_double, _dp, ctypes.c_int, _dp, _lp,
-                                 ctypes.POINTER(_dp), ctypes.POINTER(_dp), ctypes.c_long, _dp, ctypes.c_long, _dp]
+                                 ctypes.POINTER(_dp), ctypes.POINTER(_dp), ctypes.c_long, _dp, ctypes.c_long, _dp, _dp]
+            L.or_current_filter.argtypes = [_ip, _dp, _dp, ctypes.c_int, ctypes.c_int]
             L.or_window_shift.argtypes = [_ip, _dp, _dp, ctypes.c_int, _lp, ctypes.POINTER(_dp), ctypes.POINTER(_dp)]
             L.or_gauss_x.argtypes = [_ip, _dp, _dp, _dp]
             L.or_gauss_x.restype = ctypes.c_double
@@ -224,12 +225,14 @@ def backpush(n, d, dt, E, Bhalf, species):
                       species.q, species.m, species.n, _p(species.Q), _p(species.C))
 
 
-def run(n, d, dt, F, species, nsteps=1, step0=0, laser=None):
+def run(n, d, dt, F, species, nsteps=1, step0=0, laser=None, current_filter=None):
     """Advance the state ``F`` (9, nz, ny, nx[+1]) and the species in place by ``nsteps``
     cycles of Fig. 2.  Returns the (nsteps, 3) energy history (U_E, U_B, K) of the
     time levels n = 0 .. nsteps-1; on return F[6:9] holds the last J^{n+1/2}.
     ``step0`` is the index of the first cycle (it sets the laser time); ``laser`` =
-    (a0, omega, w0, tau_fwhm, t_peak, i_s, yc, zc) adds the soft laser sheet."""
+    (a0, omega, w0, tau_fwhm, t_peak, i_s, yc, zc) adds the soft laser sheet;
+    ``current_filter`` = (passes, compensate) filters the particle current each cycle
+    (see ``current_filter``)."""
     n, d, pn, pd = _grid(n, d)
     assert F.dtype == np.float64 and F.flags.c_contiguous and F.shape[0] == 9
     ns = len(species)
@@ -239,9 +242,21 @@ def run(n, d, dt, F, species, nsteps=1, step0=0, laser=None):
     cptrs = (_dp * ns)(*[_p(s.C) for s in species])
     diag = np.zeros((nsteps, 3))
     las = None if laser is None else np.ascontiguousarray(laser, dtype=np.float64)
+    filt = None if current_filter is None else np.ascontiguousarray(current_filter, dtype=np.float64)
     lib().or_run(pn, pd, dt, _p(F), ns, _p(qm), npc.ctypes.data_as(_lp), ptrs, cptrs, nsteps, _p(diag), int(step0),
-                 None if las is None else _p(las))
+                 None if las is None else _p(las), None if filt is None else _p(filt))
     return diag
+
+
+def current_filter(n, d, J, passes, compensate=True):
+    """Filter J (3, nz, ny, nx[+1]) in place: along each dimension one convolution with
+    `passes` binomial stencils (1/4, 1/2, 1/4) and, when compensating, the stencil
+    (-p/4, 1 + p/2, -p/4); periodic dimensions wrap, an open x filters x = 0 .. nx-1
+    with zero outside (the compensated binomial smoothing of section 2.2; reading, the
+    paper gives no scheme)."""
+    n_, d_, pn, pd = _grid(n, d)
+    assert J.dtype == np.float64 and J.flags.c_contiguous
+    lib().or_current_filter(pn, pd, _p(J), int(passes), int(bool(compensate)))
 
 
 # --------------------------------------------------------------------------
@@ -309,7 +324,7 @@ def window_plasma(n, d, window, origin):
     return np.array(rows, dtype=np.float64).T
 
 
-def run_window(n, d, dt, F, species, nsteps, window, step0=0, laser=None):
+def run_window(n, d, dt, F, species, nsteps, window, step0=0, laser=None, current_filter=None):
     """``run`` with the moving window: after each cycle that ends with a move, the
     window shifts and species ``window["species"]`` receives the new column's plasma
     (appended in the order of ``window_plasma``).  Returns the (nsteps, 3) energy
@@ -317,7 +332,7 @@ def run_window(n, d, dt, F, species, nsteps, window, step0=0, laser=None):
     origin = window_moves_before(window, step0)
     diag = np.zeros((nsteps, 3))
     for s in range(step0, step0 + nsteps):
-        diag[s - step0] = run(n, d, dt, F, species, 1, step0=s, laser=laser)[0]
+        diag[s - step0] = run(n, d, dt, F, species, 1, step0=s, laser=laser, current_filter=current_filter)[0]
         if window_moves_after(window, s):
             window_shift(n, d, F, species)
             origin += 1

@@ -463,8 +463,69 @@ static void laser_source(const or_grid* g, const double* laser, double t, double
         }
 }
 
+/* ------------------------------------------------------------------------ */
+/* Compensated binomial current filter: section 2.2 counts "compensated smoothing"
+ * among the operations of a cycle and section 2.6 lists a current-filtering module,
+ * without giving a scheme (the runs of section 4 use none).  Reading: along each
+ * dimension, one convolution of every J component with the kernel made of `passes`
+ * binomial stencils (1/4, 1/2, 1/4) and, when compensate is set, the compensating
+ * stencil (-p/4, 1 + p/2, -p/4), p = passes.  Per dimension a mode of wave number k
+ * is multiplied by (1 - s)^p, times (1 + p s) when compensated, s = sin^2(k d / 2):
+ * the compensated product is flat to fourth order in k.  Periodic dimensions wrap;
+ * along an open x the values x = 0 .. nx - 1 are filtered with zero outside them (the
+ * face plane x = nx of Jy, Jz is left as it is).  It acts on the particles' current
+ * after the deposit, before the laser sheet and Ampere's law.                      */
+static int filter_kernel(int passes, int compensate, double* K)
+{
+    double cur[64] = {1.0}, nxt[64];
+    int len = 1;
+    double b[3] = {0.25, 0.5, 0.25};
+    double c[3] = {-passes / 4.0, 1.0 + passes / 2.0, -passes / 4.0};
+    int steps = passes + (compensate ? 1 : 0);
+    for (int q = 0; q < steps; q++) {
+        const double* st = q < passes ? b : c;
+        for (int i = 0; i < len + 2; i++) nxt[i] = 0.0;
+        for (int i = 0; i < len; i++)
+            for (int m = 0; m < 3; m++) nxt[i + m] += cur[i] * st[m];
+        len += 2;
+        for (int i = 0; i < len; i++) cur[i] = nxt[i];
+    }
+    for (int i = 0; i < len; i++) K[i] = cur[i];
+    return (len - 1) / 2;   /* half width */
+}
+
+void or_current_filter(const int* n, const double* d, double* J, int passes, int compensate)
+{
+    or_grid g = mkgrid(n, d, 0.0);
+    long N = ncells(&g);
+    double K[64];
+    int h = filter_kernel(passes, compensate, K);
+    long nxf = n[0];   /* x values filtered per line (the face plane of an open x is not) */
+    double* tmp = (double*)malloc(sizeof(double) * N);
+    for (int comp = 0; comp < 3; comp++) {
+        double* A = J + comp * N;
+        for (int dim = 0; dim < 3; dim++) {
+            for (long k = 0; k < n[2]; k++)
+                for (long j = 0; j < n[1]; j++)
+                    for (long i = 0; i < nxf; i++) {
+                        double sum = 0.0;
+                        for (int m = -h; m <= h; m++) {
+                            long ii = i + (dim == 0 ? m : 0), jj = j + (dim == 1 ? m : 0), kk = k + (dim == 2 ? m : 0);
+                            if (g.open_x && (ii < 0 || ii >= nxf)) continue;   /* zero outside */
+                            sum += K[m + h] * A[cell_index(&g, ii, jj, kk)];
+                        }
+                        tmp[cell_index(&g, i, j, k)] = sum;
+                    }
+            for (long k = 0; k < n[2]; k++)
+                for (long j = 0; j < n[1]; j++)
+                    for (long i = 0; i < nxf; i++) A[cell_index(&g, i, j, k)] = tmp[cell_index(&g, i, j, k)];
+        }
+    }
+    free(tmp);
+}
+
 void or_step(const int* n, const double* d, double dt, double* F, int ns, const double* qm, const long* np,
-             double** P, double** C, double* diag, long step, const double* laser)
+             double** P, double** C, double* diag, long step, const double* laser, const double* filt)
 {
     or_grid g = mkgrid(n, d, dt);
     long N = ncells(&g);
@@ -518,6 +579,7 @@ void or_step(const int* n, const double* d, double dt, double* F, int ns, const 
             Ps[5 * cnt + p] = u[2];
         }
     }
+    if (filt && filt[0] > 0) or_current_filter(n, d, J, (int)filt[0], (int)filt[1]);
     if (laser) laser_source(&g, laser, (step + 0.5) * dt, J);
     double* old = NULL;
     if (g.open_x) {
@@ -545,9 +607,9 @@ void or_step(const int* n, const double* d, double dt, double* F, int ns, const 
 
 /* Several cycles; diag receives 3 values per step.                          */
 void or_run(const int* n, const double* d, double dt, double* F, int ns, const double* qm, const long* np,
-            double** P, double** C, long nsteps, double* diag, long step0, const double* laser)
+            double** P, double** C, long nsteps, double* diag, long step0, const double* laser, const double* filt)
 {
-    for (long s = 0; s < nsteps; s++) or_step(n, d, dt, F, ns, qm, np, P, C, diag + 3 * s, step0 + s, laser);
+    for (long s = 0; s < nsteps; s++) or_step(n, d, dt, F, ns, qm, np, P, C, diag + 3 * s, step0 + s, laser, filt);
 }
 
 /* ------------------------------------------------------------------------ */
