@@ -197,6 +197,22 @@ pic_status pic_set_moving_window(pic_ctx* ctx, const pic_window_desc* window);
 /* Moves of the window so far (0 without a window). */
 int64_t pic_window_moves(const pic_ctx* ctx);
 
+/* Compensated binomial current filter.  Section 2.2 counts "compensated smoothing"
+ * among the operations of a cycle and section 2.6 lists a current-filtering module;
+ * the paper gives no scheme and its runs use none, so it is off by default.  With
+ * passes > 0, each cycle filters the particles' current J^{n+1/2} after the deposit and
+ * before the laser sheet and Ampere's law: along x, y and z in turn, one convolution of
+ * every component with `passes` binomial stencils (1/4, 1/2, 1/4) and, when
+ * compensate = 1, the compensator (-p/4, 1 + p/2, -p/4), p = passes.  A Fourier mode of
+ * wave number k_d is multiplied by prod_d (1 - s_d)^p (1 + p s_d), s_d = sin^2(k_d d_d / 2)
+ * (without the compensator: prod_d (1 - s_d)^p).  Periodic dimensions wrap; along an open
+ * x the values x = 0 .. n[0] - 1 are filtered with zero outside them.  The filtered J no
+ * longer satisfies the discrete continuity equation (cont_max reports how far).
+ * Allocates a second J set (3 N values) on the first filtered cycle.  PIC_ERR_ARG unless
+ * 0 <= passes <= 8 and compensate is 0 or 1; passes = 0 switches it off.  The adjoint
+ * refuses a filtered context (PIC_ERR_STATE). */
+pic_status pic_set_current_filter(pic_ctx* ctx, int32_t passes, int32_t compensate);
+
 /* Advance nsteps cycles (section 2.2, Fig. 2), asynchronously on the context's
  * stream.  J of the last cycle is kept for pic_get_fields and pic_diagnostics. */
 pic_status pic_step(pic_ctx* ctx, int32_t nsteps);

@@ -153,6 +153,10 @@ pic_status step_once(pic_ctx* c, double* rec, bool keep_j) {
     }
     st = launch_faraday_half(c, nullptr);
     if (st != PIC_OK) return st;
+    if (c->filter_passes > 0) {
+        st = launch_current_filter(c);         // the particles' J, before the laser sheet
+        if (st != PIC_OK) return st;
+    }
     if (c->g.open_x) {
         st = launch_open_x_before_ampere(c);   // laser sheet into J, face planes saved for Mur
         if (st != PIC_OK) return st;
@@ -425,6 +429,33 @@ pic_status pic_set_moving_window(pic_ctx* c, const pic_window_desc* w) {
 }
 
 int64_t pic_window_moves(const pic_ctx* c) { return c ? c->window_moves : 0; }
+
+pic_status pic_set_current_filter(pic_ctx* c, int32_t passes, int32_t compensate) {
+    if (!c) return PIC_ERR_ARG;
+    if (passes < 0 || passes > MAX_FILTER_PASSES || (compensate != 0 && compensate != 1)) {
+        c->err = "pic_set_current_filter: 0 <= passes <= 8, compensate 0 or 1";
+        return PIC_ERR_ARG;
+    }
+    c->filter_passes = passes;
+    c->filter_compensate = passes > 0 ? compensate : 0;
+    // the per-dimension kernel: `passes` binomial stencils, then the compensator
+    double cur[2 * MAX_FILTER_PASSES + 3] = {1.0}, nxt[2 * MAX_FILTER_PASSES + 3];
+    int len = 1;
+    const double b[3] = {0.25, 0.5, 0.25};
+    const double q[3] = {-passes / 4.0, 1.0 + passes / 2.0, -passes / 4.0};
+    const int stages = passes + c->filter_compensate;
+    for (int st = 0; st < stages; ++st) {
+        const double* sten = st < passes ? b : q;
+        for (int i = 0; i < len + 2; ++i) nxt[i] = 0.0;
+        for (int i = 0; i < len; ++i)
+            for (int m = 0; m < 3; ++m) nxt[i + m] += cur[i] * sten[m];
+        len += 2;
+        for (int i = 0; i < len; ++i) cur[i] = nxt[i];
+    }
+    for (int i = 0; i < len; ++i) c->filter_K[i] = cur[i];
+    c->filter_h = (len - 1) / 2;
+    return PIC_OK;
+}
 
 pic_status pic_sync(pic_ctx* c) {
     if (!c) return PIC_ERR_ARG;

@@ -20,6 +20,7 @@ constexpr int SB = 10;           // staged E/B extent per dim: local cells -1..8
 constexpr int SJ = 11;           // shared J extent per dim: local nodes/edges -1..9
 constexpr int SJ3 = SJ * SJ * SJ;
 constexpr int MAX_WINDOW_PPCX = 64;  // moving window: largest lattice of the new plasma along x
+constexpr int MAX_FILTER_PASSES = 8; // current filter: binomial passes per dimension
 constexpr int PUSH_WARPS_MAX = 16;   // the tile kernel's CTA has at most 512 threads
 constexpr int HOLE = -1;             // cell value of a slot whose particle left the tile last step
 
@@ -600,6 +601,12 @@ struct pic_ctx {
     int64_t window_moves = 0;
     int64_t window_moves_at_rho = -1;   // window_moves when rho_prev was taken
     int64_t window_moves_at_gref = 0;   // window_moves when the Gauss reference was taken
+    // compensated binomial current filter (0 passes: off)
+    int filter_passes = 0;
+    int filter_compensate = 0;
+    int filter_h = 0;                   // half width of the per-dimension kernel
+    double filter_K[2 * gbpic::MAX_FILTER_PASSES + 3] = {};
+    void* Jtmp[3] = {};                 // second J set (the filter ping-pongs)
 };
 
 namespace gbpic {
@@ -609,6 +616,7 @@ pic_status launch_faraday_half(pic_ctx* c, double* rec);
 pic_status launch_ampere(pic_ctx* c, bool zero_j);
 pic_status launch_push_species(pic_ctx* c, SpeciesDev& s, int parity, double* krec, int xshift, bool inject);
 pic_status launch_window_shift(pic_ctx* c);
+pic_status launch_current_filter(pic_ctx* c);
 bool window_moves_after(const pic_ctx* c, int64_t step);
 pic_status launch_backpush(pic_ctx* c, SpeciesDev& s);
 template <typename T> pic_status curl_to_b(pic_ctx* c, T* const E[3], T* const B[3], double coef);

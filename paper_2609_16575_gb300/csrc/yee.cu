@@ -7,6 +7,7 @@
 // halo pass.
 #include <cmath>
 
+#include <algorithm>
 #include "pic_internal.cuh"
 
 namespace gbpic {
@@ -348,6 +349,151 @@ static pic_status window_shift_t(pic_ctx* c) {
 
 pic_status launch_window_shift(pic_ctx* c) {
     return c->prec == PIC_FP64 ? window_shift_t<double>(c) : window_shift_t<float>(c);
+}
+
+// ---------------------------------------------------------------------------
+// Compensated binomial current filter (section 2.2 "compensated smoothing", section 2.6
+// current filtering; the paper gives no scheme): along each dimension one convolution
+// of every J component with the kernel K (p binomial stencils (1/4, 1/2, 1/4), then the
+// compensator (-p/4, 1 + p/2, -p/4)); periodic dimensions wrap, an open x counts the
+// values outside x = 0 .. n - 1 as zero.  One thread per value; the neighbours along x
+// are coalesced, those along y and z are whole x lines apart.
+template <typename A> struct FilterArgs {
+    const A* src[3];
+    A* dst[3];
+    double K[2 * MAX_FILTER_PASSES + 3];         // the kernel (FP64 path)
+    long long Kn[2 * MAX_FILTER_PASSES + 3];     // its numerators over 2^shift (fixed-point path)
+    int shift;
+    int h;
+};
+
+// One filtered value: FP64 sum on the FP64 path; on the FP32 path's 64-bit fixed-point J
+// the exact integer sum of the numerators (128-bit), rounded once to the J unit (ties up)
+// — the kernel's weights are dyadic, so nothing else is rounded.
+// On the fixed-point path each tap splits the 64-bit value into its signed high and
+// unsigned low 32-bit halves and adds kn times each into a 64-bit sum (|kn| < 2^21, so
+// neither sum can overflow in 2H + 1 <= 19 taps); the halves are joined once, exactly,
+// in 128 bits.
+struct FixedSum {
+    long long hi = 0, lo = 0;
+};
+struct FilterSum {
+    __device__ static __forceinline__ double tap(double acc, double k, long long, double v) { return acc + k * v; }
+    __device__ static __forceinline__ FixedSum tap(FixedSum acc, double, long long kn, long long v) {
+        const int k32 = (int)kn;
+        acc.hi += (long long)(int)(v >> 32) * k32;
+        acc.lo += (long long)(unsigned)(v & 0xffffffffLL) * k32;
+        return acc;
+    }
+    __device__ static __forceinline__ double finish(double acc, int) { return acc; }
+    __device__ static __forceinline__ long long finish(FixedSum acc, int shift) {
+        const __int128 total = ((__int128)acc.hi << 32) + acc.lo;
+        return (long long)((total + ((__int128)1 << (shift - 1))) >> shift);
+    }
+};
+template <typename A> struct FilterAcc;
+template <> struct FilterAcc<double> { using t = double; };
+template <> struct FilterAcc<long long> { using t = FixedSum; };
+
+
+// Thread (i, j, k) of component c: blockIdx.x covers x in chunks of 128, blockIdx.y is
+// y, blockIdx.z is z + n_z c.  Neighbours along `dim` at stride `stride` (values); H is
+// the kernel's half width, so the 2H + 1 taps are unrolled and their loads overlap.
+template <typename A, int H>
+__global__ void __launch_bounds__(128) k_filter_dim(Geom g, FilterArgs<A> F, int dim) {
+    const int i = blockIdx.x * 128 + threadIdx.x;
+    if (i >= g.n[0]) return;
+    const int j = blockIdx.y, comp = blockIdx.z / g.n[2], k = blockIdx.z - comp * g.n[2];
+    const int at = dim == 0 ? i : (dim == 1 ? j : k);
+    const int nd = dim == 0 ? g.n[0] : (dim == 1 ? g.n[1] : g.n[2]);
+    const long long stride = dim == 0 ? 1LL : (dim == 1 ? (long long)g.n[0] : (long long)g.n[0] * g.n[1]);
+    const long long e = g.cidx(i, j, k);
+    // (selects, not an indexed parameter array, which would be copied to local memory)
+    const A* src = comp == 0 ? F.src[0] : (comp == 1 ? F.src[1] : F.src[2]);
+    A* dst = comp == 0 ? F.dst[0] : (comp == 1 ? F.dst[1] : F.dst[2]);
+    const A* line = src + (e - (long long)at * stride);   // the value at position 0 along dim
+    const bool bounded = dim == 0 && g.open_x;
+    A v[2 * H + 1];
+#pragma unroll
+    for (int t = 0; t <= 2 * H; ++t) {
+        int q = at + t - H;
+        bool in = true;
+        if (bounded) {
+            in = q >= 0 && q < nd;                  // zero outside an open x
+        } else if (nd > H) {
+            q += q < 0 ? nd : (q >= nd ? -nd : 0);  // one wrap suffices
+        } else {
+            q %= nd;
+            if (q < 0) q += nd;
+        }
+        v[t] = in ? line[(long long)q * stride] : A(0);
+    }
+    typename FilterAcc<A>::t sum{};
+#pragma unroll
+    for (int t = 0; t <= 2 * H; ++t) sum = FilterSum::tap(sum, F.K[t], F.Kn[t], v[t]);
+    dst[e] = FilterSum::finish(sum, F.shift);
+}
+
+template <typename A, int H>
+static void launch_filter_h(pic_ctx* c, dim3 grid, const FilterArgs<A>& F, int dim) {
+    k_filter_dim<A, H><<<grid, 128, 0, c->stream>>>(c->g, F, dim);
+}
+
+template <typename A>
+static void launch_filter(pic_ctx* c, dim3 grid, const FilterArgs<A>& F, int dim) {
+    static_assert(MAX_FILTER_PASSES == 8, "half widths 1 .. 9 below");
+    switch (F.h) {
+        case 1: launch_filter_h<A, 1>(c, grid, F, dim); break;
+        case 2: launch_filter_h<A, 2>(c, grid, F, dim); break;
+        case 3: launch_filter_h<A, 3>(c, grid, F, dim); break;
+        case 4: launch_filter_h<A, 4>(c, grid, F, dim); break;
+        case 5: launch_filter_h<A, 5>(c, grid, F, dim); break;
+        case 6: launch_filter_h<A, 6>(c, grid, F, dim); break;
+        case 7: launch_filter_h<A, 7>(c, grid, F, dim); break;
+        case 8: launch_filter_h<A, 8>(c, grid, F, dim); break;
+        default: launch_filter_h<A, 9>(c, grid, F, dim); break;
+    }
+}
+
+template <typename T>
+static pic_status current_filter_t(pic_ctx* c) {
+    using A = typename JTraits<T>::acc_t;
+    const Geom& g = c->g;
+    for (int k = 0; k < 3; ++k) {
+        if (!c->Jtmp[k]) {
+            c->Jtmp[k] = dev_alloc(c, sizeof(long long) * (size_t)g.N);
+            if (!c->Jtmp[k]) return PIC_ERR_OOM;
+        }
+    }
+    FilterArgs<A> F;
+    F.shift = 2 * (c->filter_passes + c->filter_compensate);   // the kernel's weights are k / 4^stages
+    for (int m = 0; m < 2 * c->filter_h + 1; ++m) {
+        F.K[m] = c->filter_K[m];
+        F.Kn[m] = (long long)std::llround(std::ldexp(c->filter_K[m], F.shift));   // exact
+    }
+    F.h = c->filter_h;
+    if (g.n[1] > 65535 || 3LL * g.n[2] > 65535) {
+        c->err = "current filter: n[1] <= 65535 and n[2] <= 21845";
+        return PIC_ERR_ARG;
+    }
+    const dim3 grid((unsigned)((g.n[0] + 127) / 128), (unsigned)g.n[1], (unsigned)(3 * g.n[2]));
+    for (int dim = 0; dim < 3; ++dim) {   // x, y, z; each pass writes the other J set
+        for (int k = 0; k < 3; ++k) {
+            F.src[k] = static_cast<const A*>(c->J[k]);
+            F.dst[k] = static_cast<A*>(c->Jtmp[k]);
+        }
+        {
+            LaunchScope ls(c, KC_OTHER);
+            launch_filter<A>(c, grid, F, dim);
+            GBPIC_CHECK(c, cudaGetLastError());
+        }
+        for (int k = 0; k < 3; ++k) std::swap(c->J[k], c->Jtmp[k]);
+    }
+    return PIC_OK;
+}
+
+pic_status launch_current_filter(pic_ctx* c) {
+    return c->prec == PIC_FP64 ? current_filter_t<double>(c) : current_filter_t<float>(c);
 }
 
 pic_status launch_open_x_before_ampere(pic_ctx* c) {

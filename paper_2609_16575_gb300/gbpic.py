@@ -110,6 +110,7 @@ def lib():
                                                ctypes.c_int32]
             L.pic_set_laser.argtypes = [P, ctypes.POINTER(pic_laser_desc)]
             L.pic_set_moving_window.argtypes = [P, ctypes.POINTER(pic_window_desc)]
+            L.pic_set_current_filter.argtypes = [P, ctypes.c_int32, ctypes.c_int32]
             L.pic_window_moves.argtypes = [P]
             L.pic_window_moves.restype = ctypes.c_int64
             L.pic_gauss_check_static.argtypes = [P, ctypes.POINTER(ctypes.c_double), ctypes.POINTER(ctypes.c_double)]
@@ -124,7 +125,8 @@ def lib():
             for name in ("pic_init_grid", "pic_set_fields", "pic_load_species", "pic_step", "pic_sync",
                          "pic_get_fields", "pic_get_particles", "pic_diagnostics", "pic_get_history",
                          "pic_set_timing", "pic_kernel_times", "pic_adjoint_forward", "pic_adjoint_backward",
-                         "pic_gauss_check_static", "pic_set_laser", "pic_set_moving_window"):
+                         "pic_gauss_check_static", "pic_set_laser", "pic_set_moving_window",
+                         "pic_set_current_filter"):
                 getattr(L, name).restype = ctypes.c_int
             _lib = L
     return _lib
@@ -339,6 +341,11 @@ class Context:
         W = pic_window_desc(int(start), int(every), int(species), (ctypes.c_int32 * 3)(*[int(v) for v in ppc]),
                             float(density), float(x0), float(ramp))
         _check(self.ptr, lib().pic_set_moving_window(self.ptr, ctypes.byref(W)), "pic_set_moving_window")
+
+    def set_current_filter(self, passes, compensate=True):
+        """Compensated binomial current filter (see pic_set_current_filter); 0 passes: off."""
+        _check(self.ptr, lib().pic_set_current_filter(self.ptr, int(passes), int(compensate)),
+               "pic_set_current_filter")
 
     def window_moves(self):
         """Moves of the window so far."""
