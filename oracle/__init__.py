@@ -72,9 +72,10 @@ def lib():
             L.or_backpush.argtypes = [_ip, _dp, ctypes.c_double, _dp, _dp, ctypes.c_double, ctypes.c_double,
                                       ctypes.c_long, _dp, _dp]
             L.or_step.argtypes = [_ip, _dp, ctypes.c_double, _dp, ctypes.c_int, _dp, _lp,
-                                  ctypes.POINTER(_dp), ctypes.POINTER(_dp), _dp, ctypes.c_long, _dp, _dp]
+                                  ctypes.POINTER(_dp), ctypes.POINTER(_dp), _dp, ctypes.c_long, _dp, _dp, _dp]
             L.or_run.argtypes = [_ip, _dp, ctypes.c_double, _dp, ctypes.c_int, _dp, _lp,
-                                 ctypes.POINTER(_dp), ctypes.POINTER(_dp), ctypes.c_long, _dp, ctypes.c_long, _dp, _dp]
+                                 ctypes.POINTER(_dp), ctypes.POINTER(_dp), ctypes.c_long, _dp, ctypes.c_long, _dp, _dp,
+                                 _dp]
             L.or_current_filter.argtypes = [_ip, _dp, _dp, ctypes.c_int, ctypes.c_int]
             L.or_window_shift.argtypes = [_ip, _dp, _dp, ctypes.c_int, _lp, ctypes.POINTER(_dp), ctypes.POINTER(_dp)]
             L.or_gauss_x.argtypes = [_ip, _dp, _dp, _dp]
@@ -225,14 +226,16 @@ def backpush(n, d, dt, E, Bhalf, species):
                       species.q, species.m, species.n, _p(species.Q), _p(species.C))
 
 
-def run(n, d, dt, F, species, nsteps=1, step0=0, laser=None, current_filter=None):
+def run(n, d, dt, F, species, nsteps=1, step0=0, laser=None, current_filter=None, guide=None):
     """Advance the state ``F`` (9, nz, ny, nx[+1]) and the species in place by ``nsteps``
     cycles of Fig. 2.  Returns the (nsteps, 3) energy history (U_E, U_B, K) of the
     time levels n = 0 .. nsteps-1; on return F[6:9] holds the last J^{n+1/2}.
     ``step0`` is the index of the first cycle (it sets the laser time); ``laser`` =
     (a0, omega, w0, tau_fwhm, t_peak, i_s, yc, zc) adds the soft laser sheet;
     ``current_filter`` = (passes, compensate) filters the particle current each cycle
-    (see ``current_filter``)."""
+    (see ``current_filter``); ``guide`` = dict(pec_y, pec_z, port, e0, omega, tau,
+    mode_y) adds perfectly conducting walls on the planes y = 0 / z = 0 and a hard TE
+    port on the face x = 0 of an open x (see ``pic_oracle.c``)."""
     n, d, pn, pd = _grid(n, d)
     assert F.dtype == np.float64 and F.flags.c_contiguous and F.shape[0] == 9
     ns = len(species)
@@ -243,8 +246,13 @@ def run(n, d, dt, F, species, nsteps=1, step0=0, laser=None, current_filter=None
     diag = np.zeros((nsteps, 3))
     las = None if laser is None else np.ascontiguousarray(laser, dtype=np.float64)
     filt = None if current_filter is None else np.ascontiguousarray(current_filter, dtype=np.float64)
+    gd = None
+    if guide is not None:
+        gd = np.array([guide.get("pec_y", 0), guide.get("pec_z", 0), guide.get("port", 0), guide.get("e0", 0.0),
+                       guide.get("omega", 0.0), guide.get("tau", 1.0), guide.get("mode_y", 1)], dtype=np.float64)
     lib().or_run(pn, pd, dt, _p(F), ns, _p(qm), npc.ctypes.data_as(_lp), ptrs, cptrs, nsteps, _p(diag), int(step0),
-                 None if las is None else _p(las), None if filt is None else _p(filt))
+                 None if las is None else _p(las), None if filt is None else _p(filt),
+                 None if gd is None else _p(gd))
     return diag
 
 

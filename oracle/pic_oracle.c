@@ -25,6 +25,9 @@
  * Time levels (section 2.2, Fig. 2): a state holds E^n, B^{n-1/2}, x^n, u^{n-1/2}.
  */
 #include <math.h>
+#ifndef M_PI
+#define M_PI 3.14159265358979323846
+#endif
 #include <stdlib.h>
 #include <string.h>
 #include <stdint.h>
@@ -524,8 +527,47 @@ void or_current_filter(const int* n, const double* d, double* J, int passes, int
     free(tmp);
 }
 
+/* ------------------------------------------------------------------------ */
+/* Perfectly conducting walls and a waveguide port (section 3.2: the Yee solver is
+ * verified on the TE10 mode of a perfectly conducting rectangular guide driven at its
+ * input plane; the paper gives no discretisation of either).
+ * guide = {pec_y, pec_z, port, e0, omega, tau, mode_y}.
+ * pec_y: the node plane y = 0 is a perfect conductor, its tangential Ex and Ez are
+ *   held at zero; with y periodic that plane is both walls of a guide 0 <= y <= ny.
+ * pec_z: likewise the plane z = 0 (Ex, Ey).
+ * port (open x only): a hard source on the face x = 0 that replaces the absorbing
+ *   condition there: Ez(0, j, k) = e0 g(t) sin(mode_y pi j / ny) sin(omega t), Ey(0, j, k)
+ *   = 0, g(t) = 1 - exp(-t / tau), t the time of the new E (the envelope of section
+ *   3.2 that suppresses the start-up transient).
+ * Applied after Ampere's law (and the Mur faces): port first, then the walls.       */
+static void port_source(const or_grid* g, const double* guide, double t, double* E)
+{
+    long N = ncells(g);
+    double e0 = guide[3], om = guide[4], tau = guide[5];
+    double m = guide[6];
+    double amp = e0 * (1.0 - exp(-t / tau)) * sin(om * t);
+    for (long k = 0; k < g->n[2]; k++)
+        for (long j = 0; j < g->n[1]; j++) {
+            E[N + cell_index(g, 0, j, k)] = 0.0;
+            E[2 * N + cell_index(g, 0, j, k)] = amp * sin(m * M_PI * (double)j / g->n[1]);
+        }
+}
+
+static void pec_walls(const or_grid* g, const double* guide, double* E)
+{
+    long N = ncells(g);
+    for (long k = 0; k < g->n[2]; k++)
+        for (long j = 0; j < g->n[1]; j++)
+            for (long i = 0; i < g->nxs; i++) {
+                long c = cell_index(g, i, j, k);
+                if (guide[0] != 0 && j == 0) { E[c] = 0.0; E[2 * N + c] = 0.0; }
+                if (guide[1] != 0 && k == 0) { E[c] = 0.0; E[N + c] = 0.0; }
+            }
+}
+
 void or_step(const int* n, const double* d, double dt, double* F, int ns, const double* qm, const long* np,
-             double** P, double** C, double* diag, long step, const double* laser, const double* filt)
+             double** P, double** C, double* diag, long step, const double* laser, const double* filt,
+             const double* guide)
 {
     or_grid g = mkgrid(n, d, dt);
     long N = ncells(&g);
@@ -598,6 +640,10 @@ void or_step(const int* n, const double* d, double dt, double* F, int ns, const 
         mur_x(&g, old, E);
         free(old);
     }
+    if (guide) {
+        if (guide[2] != 0 && g.open_x) port_source(&g, guide, (step + 1) * dt, E);
+        if (guide[0] != 0 || guide[1] != 0) pec_walls(&g, guide, E);
+    }
     diag[0] = 0.5 * dV * UE;
     diag[1] = 0.5 * dV * UB;
     diag[2] = K;
@@ -607,9 +653,11 @@ void or_step(const int* n, const double* d, double dt, double* F, int ns, const 
 
 /* Several cycles; diag receives 3 values per step.                          */
 void or_run(const int* n, const double* d, double dt, double* F, int ns, const double* qm, const long* np,
-            double** P, double** C, long nsteps, double* diag, long step0, const double* laser, const double* filt)
+            double** P, double** C, long nsteps, double* diag, long step0, const double* laser, const double* filt,
+            const double* guide)
 {
-    for (long s = 0; s < nsteps; s++) or_step(n, d, dt, F, ns, qm, np, P, C, diag + 3 * s, step0 + s, laser, filt);
+    for (long s = 0; s < nsteps; s++)
+        or_step(n, d, dt, F, ns, qm, np, P, C, diag + 3 * s, step0 + s, laser, filt, guide);
 }
 
 /* ------------------------------------------------------------------------ */
