@@ -54,6 +54,9 @@ def parse():
                    help="only time the FP64 checkpointed adjoint of the differentiable run over this many steps")
     p.add_argument("--stress", type=int, default=0,
                    help="also run the 256^3 x 32 ppc precision-stress workload for this many steps (FP32 and FP64)")
+    p.add_argument("--waveguide", type=int, default=0,
+                   help="run the first N grids of the TE10 waveguide convergence study (FP64) and exit")
+    p.add_argument("--waveguide-fp32", action="store_true", help="the waveguide study on the FP32 path")
     p.add_argument("--small", action="store_true", help="32^3 cells instead of 128^3 (smoke)")
     p.add_argument("--cells", type=int, default=0, help="cells per dimension (profiling cases); 0 = 128")
     p.add_argument("--sort-every", type=int, default=0, help="tile re-sort cadence passed to the library")
@@ -266,6 +269,87 @@ def other_workloads(torch, peak):
         "note": "steps 4-33 with a moving window; 'other' holds the field shift, the injection, the "
                 "laser sheet and the Mur faces"}
     ctx.close()
+    return out
+
+
+# The TE10 waveguide of the Yee verification (section 3.2): a = 3 cm, b = a / 2, length
+# 1 m, excitation 9 GHz with the envelope 1 - exp(-t / 2 periods), Courant number 0.5.
+# Grids: the node counts (across a, across b, along the guide) and step counts of the
+# paper's convergence table, with its errors of the steady-state E amplitude for context.
+WAVEGUIDE_GRIDS = [(12, 6, 376, 1251, 4.54e-2), (23, 12, 751, 2501, 4.37e-3), (46, 23, 1501, 5001, 2.95e-3),
+                   (91, 46, 3001, 10001, 3.74e-4), (181, 91, 6001, 20001, 8.41e-5)]
+
+
+def _fit_wave(x, f, beta0):
+    """Amplitude and wave number of f(x) = A sin(beta x - phi) (least squares over beta)."""
+    import numpy as np
+
+    def resid(beta):
+        A = np.stack([np.sin(beta * x), np.cos(beta * x)], 1)
+        c, *_ = np.linalg.lstsq(A, f, rcond=None)
+        r = f - A @ c
+        return float(r @ r), float(np.hypot(*c))
+
+    betas = np.linspace(0.97 * beta0, 1.03 * beta0, 601)
+    best = min(betas, key=lambda b: resid(b)[0])
+    lo, hi = best - (betas[1] - betas[0]), best + (betas[1] - betas[0])
+    for _ in range(80):   # golden-section refinement
+        m1, m2 = lo + 0.382 * (hi - lo), lo + 0.618 * (hi - lo)
+        if resid(m1)[0] < resid(m2)[0]:
+            hi = m2
+        else:
+            lo = m1
+    beta = 0.5 * (lo + hi)
+    return resid(beta)[1], beta
+
+
+def waveguide_convergence(torch, count, fp64=True):
+    """The TE10 convergence study on the GPU (FP64 by default: an accuracy study that
+    FP32 rounding must not limit), in units of the excitation: time in
+    periods, length in free-space wavelengths (c = 1, omega = 2 pi).  The guide's length
+    runs along the open x, its width a along y and its height b along z, closed by the
+    wall planes y = 0 and z = 0; the port drives Ez = sin(pi y / a) on x = 0.  At the end
+    of each run the steady part of Ez along the guide's axis (from L/16 to where the
+    envelope has risen, 1 - exp(-10)) is fitted with A sin(beta x - phi): A against the
+    port amplitude at the probe's y, beta against the continuous guide's
+    sqrt(omega^2 - (pi / a)^2); rates are least-squares slopes against the cell diagonal."""
+    import numpy as np
+    from paper_2609_16575_gb300 import gbpic
+
+    lam0 = 299792458.0 / 9e9
+    a, b, L = 0.03 / lam0, 0.015 / lam0, 1.0 / lam0
+    om = 2 * np.pi
+    beta_c = np.sqrt(om ** 2 - (np.pi / a) ** 2)
+    vg = beta_c / om
+    rows = []
+    for na, nb, nl, nt, paper_eps in WAVEGUIDE_GRIDS[:count]:
+        n = (nl - 1, na - 1, nb - 1)
+        d = (L / n[0], a / n[1], b / n[2])
+        dt = 0.5 / np.sqrt(sum(1.0 / v ** 2 for v in d))
+        ctx = gbpic.Context(n, d, dt, precision=gbpic.PIC_FP64 if fp64 else gbpic.PIC_FP32, bc_x=1)
+        ctx.set_pec(1, 1)
+        ctx.set_port(1.0, om, 2.0, 1)
+        ms, _ = time_steps(ctx, torch, nt)
+        E, _, _ = ctx.get_fields()
+        ctx.close()
+        t_end = nt * dt
+        j = n[1] // 2
+        x = np.arange(n[0] + 1) * d[0]
+        x_hi = vg * (t_end - 20.0)          # the envelope has risen to 1 - exp(-10) behind here
+        sel = (x >= L / 16) & (x <= x_hi)
+        f = E[2, n[2] // 2, j, sel]
+        A, beta = _fit_wave(x[sel], f, beta_c)
+        A_ref = np.sin(np.pi * j * d[1] / a)
+        rows.append({"nodes": [na, nb, nl], "cells": list(n), "steps": nt, "dh": float(np.sqrt(sum(v * v for v in d)) * lam0),
+                     "eps_amplitude": abs(A - A_ref) / A_ref, "eps_beta": abs(beta - beta_c) / beta_c,
+                     "paper_eps_E0": paper_eps, "cell_updates_per_s": n[0] * n[1] * n[2] * nt / (ms / 1e3),
+                     "fit_wavelengths": float((x_hi - L / 16))})
+    out = {"workload": "TE10 waveguide a = 3 cm, b = 1.5 cm, L = 1 m, 9 GHz, Courant 0.5, "
+                       + ("FP64" if fp64 else "FP32"), "grids": rows}
+    if len(rows) >= 3:
+        lh = np.log([r["dh"] for r in rows])
+        for key in ("eps_amplitude", "eps_beta"):
+            out[key + "_rate"] = float(np.polyfit(lh, np.log([r[key] for r in rows]), 1)[0])
     return out
 
 
@@ -620,6 +704,15 @@ def run_gbpic(args):
 
 def main():
     args = parse()
+    if args.waveguide > 0:
+        import torch
+
+        torch.cuda.set_device(0)
+        import __graft_entry__
+
+        __graft_entry__.build()
+        print(json.dumps(waveguide_convergence(torch, args.waveguide, not args.waveguide_fp32)), flush=True)
+        return 0
     if args.adjoint_only > 0:
         import torch
 

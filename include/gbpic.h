@@ -133,6 +133,19 @@ typedef struct pic_window_desc {
     double x0, ramp;      /* density profile along absolute x (cells); ramp >= 0 */
 } pic_window_desc;
 
+/* Waveguide port on the face x = 0 of an open x (section 3.2: the Yee solver is verified
+ * on the TE10 mode of a conducting rectangular guide driven at its input plane).  A hard
+ * source: after every Ampere step it sets Ez(0, j, k) = e0 g(t) sin(mode_y pi j / n[1])
+ * sin(omega t) and Ey(0, j, k) = 0, with g(t) = 1 - exp(-t / tau) (the start-up envelope
+ * of section 3.2) and t the time of the new E; it replaces the Mur condition on that
+ * face.  With the wall plane y = 0 (pic_set_pec) the profile is the discrete TE_m0 mode
+ * of the guide 0 <= y <= n[1] d[1]. */
+typedef struct pic_port_desc {
+    double e0, omega, tau;   /* amplitude, angular frequency, envelope rise time (> 0) */
+    int32_t mode_y;          /* half waves across y (>= 1) */
+    int32_t reserved;
+} pic_port_desc;
+
 /* A particle species (section 2.1, Eqs. (8)-(11)): q, m per physical particle;
  * a super-particle of weight w carries q w and m w. */
 typedef struct pic_species_desc {
@@ -196,6 +209,18 @@ pic_status pic_set_moving_window(pic_ctx* ctx, const pic_window_desc* window);
 
 /* Moves of the window so far (0 without a window). */
 int64_t pic_window_moves(const pic_ctx* ctx);
+
+/* Perfectly conducting wall planes (section 3.2 waveguide).  pec_y = 1: the node plane
+ * y = 0 conducts, its tangential Ex and Ez are held at zero after every Ampere step; in
+ * the periodic y that plane is both walls of a guide 0 <= y <= n[1] d[1] (nothing
+ * couples across it).  pec_z = 1: likewise the plane z = 0 (Ex, Ey).  The walls act on
+ * the fields only: PIC_ERR_STATE once a species is loaded (and loading a species fails
+ * while a wall is set). */
+pic_status pic_set_pec(pic_ctx* ctx, int32_t pec_y, int32_t pec_z);
+
+/* Set (or, with NULL, remove) the port of the face x = 0.  PIC_ERR_STATE without
+ * bc_x = 1; PIC_ERR_ARG for tau <= 0, mode_y < 1 or non-finite values. */
+pic_status pic_set_port(pic_ctx* ctx, const pic_port_desc* port);
 
 /* Compensated binomial current filter.  Section 2.2 counts "compensated smoothing"
  * among the operations of a cycle and section 2.6 lists a current-filtering module;

@@ -167,6 +167,10 @@ pic_status step_once(pic_ctx* c, double* rec, bool keep_j) {
         st = launch_open_x_after_ampere(c);    // Mur condition on the two x faces
         if (st != PIC_OK) return st;
     }
+    if (c->port_on || c->pec_y || c->pec_z) {
+        st = launch_guide(c);                  // the port on x = 0, then the wall planes
+        if (st != PIC_OK) return st;
+    }
     if (move) {   // the end of the cycle: the window moves one cell along +x
         st = launch_window_shift(c);
         if (st != PIC_OK) return st;
@@ -325,6 +329,10 @@ pic_status pic_set_fields(pic_ctx* c, const double* E, const double* B, int32_t 
 pic_status pic_load_species(pic_ctx* c, const pic_species_desc* d, int32_t* species_id) {
     if (!c || !d) return PIC_ERR_ARG;
     if (d->n < 0 || (d->n > 0 && (!d->X || !d->u || !d->w)) || !(d->m > 0) || !std::isfinite(d->q)) return PIC_ERR_ARG;
+    if (c->pec_y || c->pec_z) {
+        c->err = "pic_load_species: the conducting walls act on the fields only";
+        return PIC_ERR_STATE;
+    }
     cudaSetDevice(c->desc.device);
     c->species.emplace_back();
     SpeciesDev& s = c->species.back();
@@ -429,6 +437,37 @@ pic_status pic_set_moving_window(pic_ctx* c, const pic_window_desc* w) {
 }
 
 int64_t pic_window_moves(const pic_ctx* c) { return c ? c->window_moves : 0; }
+
+pic_status pic_set_pec(pic_ctx* c, int32_t pec_y, int32_t pec_z) {
+    if (!c) return PIC_ERR_ARG;
+    if ((pec_y != 0 && pec_y != 1) || (pec_z != 0 && pec_z != 1)) return PIC_ERR_ARG;
+    if ((pec_y || pec_z) && !c->species.empty()) {
+        c->err = "pic_set_pec: the conducting walls act on the fields only (species are loaded)";
+        return PIC_ERR_STATE;
+    }
+    c->pec_y = pec_y;
+    c->pec_z = pec_z;
+    return PIC_OK;
+}
+
+pic_status pic_set_port(pic_ctx* c, const pic_port_desc* p) {
+    if (!c) return PIC_ERR_ARG;
+    if (!c->g.open_x) {
+        c->err = "pic_set_port needs an open x (bc_x = 1)";
+        return PIC_ERR_STATE;
+    }
+    if (!p) {
+        c->port_on = false;
+        return PIC_OK;
+    }
+    if (!(p->tau > 0) || p->mode_y < 1 || !std::isfinite(p->e0) || !std::isfinite(p->omega) || !std::isfinite(p->tau)) {
+        c->err = "pic_set_port: tau > 0, mode_y >= 1, finite e0 and omega";
+        return PIC_ERR_ARG;
+    }
+    c->port = *p;
+    c->port_on = true;
+    return PIC_OK;
+}
 
 pic_status pic_set_current_filter(pic_ctx* c, int32_t passes, int32_t compensate) {
     if (!c) return PIC_ERR_ARG;

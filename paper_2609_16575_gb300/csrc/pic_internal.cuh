@@ -607,6 +607,10 @@ struct pic_ctx {
     int filter_h = 0;                   // half width of the per-dimension kernel
     double filter_K[2 * gbpic::MAX_FILTER_PASSES + 3] = {};
     void* Jtmp[3] = {};                 // second J set (the filter ping-pongs)
+    // perfectly conducting wall planes (y = 0, z = 0) and the port on the face x = 0
+    int pec_y = 0, pec_z = 0;
+    bool port_on = false;
+    pic_port_desc port{};
 };
 
 namespace gbpic {
@@ -617,6 +621,7 @@ pic_status launch_ampere(pic_ctx* c, bool zero_j);
 pic_status launch_push_species(pic_ctx* c, SpeciesDev& s, int parity, double* krec, int xshift, bool inject);
 pic_status launch_window_shift(pic_ctx* c);
 pic_status launch_current_filter(pic_ctx* c);
+pic_status launch_guide(pic_ctx* c);
 bool window_moves_after(const pic_ctx* c, int64_t step);
 pic_status launch_backpush(pic_ctx* c, SpeciesDev& s);
 template <typename T> pic_status curl_to_b(pic_ctx* c, T* const E[3], T* const B[3], double coef);

@@ -496,6 +496,64 @@ pic_status launch_current_filter(pic_ctx* c) {
     return c->prec == PIC_FP64 ? current_filter_t<double>(c) : current_filter_t<float>(c);
 }
 
+// ---------------------------------------------------------------------------
+// Perfectly conducting wall planes and the waveguide port (section 3.2 verification:
+// the TE10 mode of a conducting rectangular guide driven at its input plane).  After
+// Ampere's law (and the Mur faces): the port sets Ez(0, j, k) = amp sin(m pi j / n_y)
+// and Ey(0, j, k) = 0 on the face x = 0 (amp = e0 g(t) sin(omega t), from the host);
+// then the wall planes hold their tangential E at zero: Ex, Ez on y = 0, Ex, Ey on
+// z = 0.  In the periodic y (z) the plane y = 0 is both walls of a guide of width n_y.
+// Every value is stored with its y and z ghost images; the wall kernel also covers the
+// x ghost columns (they hold copies of the same, zero, values).
+template <typename T>
+__global__ void k_port(Geom g, T* Ey, T* Ez, double amp, int mode_y) {
+    const int j = blockIdx.x * blockDim.x + threadIdx.x, k = blockIdx.y;
+    if (j >= g.n[1]) return;
+    const double prof = sin(mode_y * 3.14159265358979323846 * (double)j / g.n[1]);
+    store1_yz(g, Ey, 0, j, k, T(0));
+    store1_yz(g, Ez, 0, j, k, (T)(amp * prof));
+}
+
+template <typename T>
+__global__ void k_pec(Geom g, T* Ex, T* Ey, T* Ez, int pec_y, int pec_z) {
+    const int i = blockIdx.x * blockDim.x + threadIdx.x - 1;   // padded x: -1 .. Px - 2
+    if (i > g.Px - 2) return;
+    const int t = blockIdx.y;
+    if (pec_y && t < g.n[2]) {
+        store1_yz(g, Ex, i, 0, t, T(0));
+        store1_yz(g, Ez, i, 0, t, T(0));
+    }
+    if (pec_z && t < g.n[1]) {
+        store1_yz(g, Ex, i, t, 0, T(0));
+        store1_yz(g, Ey, i, t, 0, T(0));
+    }
+}
+
+template <typename T>
+static pic_status guide_t(pic_ctx* c) {
+    const Geom& g = c->g;
+    if (c->port_on) {
+        const pic_port_desc& P = c->port;
+        const double t = (c->step + 1) * c->desc.dt;   // the time of the new E
+        const double amp = P.e0 * (1.0 - std::exp(-t / P.tau)) * std::sin(P.omega * t);
+        LaunchScope ls(c, KC_OTHER);
+        k_port<T><<<dim3((g.n[1] + 127) / 128, g.n[2]), 128, 0, c->stream>>>(g, (T*)c->E[1], (T*)c->E[2], amp,
+                                                                              P.mode_y);
+        GBPIC_CHECK(c, cudaGetLastError());
+    }
+    if (c->pec_y || c->pec_z) {
+        LaunchScope ls(c, KC_OTHER);
+        k_pec<T><<<dim3((g.Px + 127) / 128, std::max(g.n[1], g.n[2])), 128, 0, c->stream>>>(
+            g, (T*)c->E[0], (T*)c->E[1], (T*)c->E[2], c->pec_y, c->pec_z);
+        GBPIC_CHECK(c, cudaGetLastError());
+    }
+    return PIC_OK;
+}
+
+pic_status launch_guide(pic_ctx* c) {
+    return c->prec == PIC_FP64 ? guide_t<double>(c) : guide_t<float>(c);
+}
+
 pic_status launch_open_x_before_ampere(pic_ctx* c) {
     return c->prec == PIC_FP64 ? open_before_t<double>(c) : open_before_t<float>(c);
 }

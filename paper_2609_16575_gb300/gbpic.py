@@ -55,6 +55,11 @@ class pic_window_desc(ctypes.Structure):
                 ("ramp", ctypes.c_double)]
 
 
+class pic_port_desc(ctypes.Structure):
+    _fields_ = [("e0", ctypes.c_double), ("omega", ctypes.c_double), ("tau", ctypes.c_double),
+                ("mode_y", ctypes.c_int32), ("reserved", ctypes.c_int32)]
+
+
 class pic_species_desc(ctypes.Structure):
     _fields_ = [("q", ctypes.c_double), ("m", ctypes.c_double), ("n", ctypes.c_int64),
                 ("X", ctypes.c_void_p), ("u", ctypes.c_void_p), ("w", ctypes.c_void_p),
@@ -111,6 +116,8 @@ def lib():
             L.pic_set_laser.argtypes = [P, ctypes.POINTER(pic_laser_desc)]
             L.pic_set_moving_window.argtypes = [P, ctypes.POINTER(pic_window_desc)]
             L.pic_set_current_filter.argtypes = [P, ctypes.c_int32, ctypes.c_int32]
+            L.pic_set_pec.argtypes = [P, ctypes.c_int32, ctypes.c_int32]
+            L.pic_set_port.argtypes = [P, ctypes.POINTER(pic_port_desc)]
             L.pic_window_moves.argtypes = [P]
             L.pic_window_moves.restype = ctypes.c_int64
             L.pic_gauss_check_static.argtypes = [P, ctypes.POINTER(ctypes.c_double), ctypes.POINTER(ctypes.c_double)]
@@ -126,7 +133,7 @@ def lib():
                          "pic_get_fields", "pic_get_particles", "pic_diagnostics", "pic_get_history",
                          "pic_set_timing", "pic_kernel_times", "pic_adjoint_forward", "pic_adjoint_backward",
                          "pic_gauss_check_static", "pic_set_laser", "pic_set_moving_window",
-                         "pic_set_current_filter"):
+                         "pic_set_current_filter", "pic_set_pec", "pic_set_port"):
                 getattr(L, name).restype = ctypes.c_int
             _lib = L
     return _lib
@@ -346,6 +353,15 @@ class Context:
         """Compensated binomial current filter (see pic_set_current_filter); 0 passes: off."""
         _check(self.ptr, lib().pic_set_current_filter(self.ptr, int(passes), int(compensate)),
                "pic_set_current_filter")
+
+    def set_pec(self, pec_y, pec_z):
+        """Conducting wall planes y = 0 / z = 0 (see pic_set_pec); fields only."""
+        _check(self.ptr, lib().pic_set_pec(self.ptr, int(pec_y), int(pec_z)), "pic_set_pec")
+
+    def set_port(self, e0, omega, tau, mode_y=1):
+        """Hard TE port on the face x = 0 of an open x (see pic_port_desc)."""
+        P = pic_port_desc(float(e0), float(omega), float(tau), int(mode_y), 0)
+        _check(self.ptr, lib().pic_set_port(self.ptr, ctypes.byref(P)), "pic_set_port")
 
     def window_moves(self):
         """Moves of the window so far."""
