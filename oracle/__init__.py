@@ -77,6 +77,7 @@ def lib():
                                  ctypes.POINTER(_dp), ctypes.POINTER(_dp), ctypes.c_long, _dp, ctypes.c_long, _dp, _dp,
                                  _dp]
             L.or_current_filter.argtypes = [_ip, _dp, _dp, ctypes.c_int, ctypes.c_int]
+            L.or_esirkepov.argtypes = [_ip, _dp, ctypes.c_double, ctypes.c_double, _dp, _dp, _dp]
             L.or_window_shift.argtypes = [_ip, _dp, _dp, ctypes.c_int, _lp, ctypes.POINTER(_dp), ctypes.POINTER(_dp)]
             L.or_gauss_x.argtypes = [_ip, _dp, _dp, _dp]
             L.or_gauss_x.restype = ctypes.c_double
@@ -191,6 +192,14 @@ def zigzag(n, d, dt, qw, X1, X2, J):
     lib().or_zigzag(pn, pd, dt, qw, _p(f(X1)), _p(f(X2)), _p(J))
 
 
+def esirkepov(n, d, dt, qw, X1, X2, J):
+    """Accumulate Esirkepov's current of one straight move X1 -> X2 (cell units, X2
+    unwrapped, under one cell per dimension) into J, with the CIC shape."""
+    n, d, pn, pd = _grid(n, d)
+    f = lambda v: np.ascontiguousarray(v, dtype=np.float64)
+    lib().or_esirkepov(pn, pd, dt, qw, _p(f(X1)), _p(f(X2)), _p(J))
+
+
 def rho(n, d, species, rho_ion=0.0):
     """Node charge density: CIC of every species plus the uniform background rho_ion."""
     shape = field_shape(n)
@@ -234,8 +243,9 @@ def run(n, d, dt, F, species, nsteps=1, step0=0, laser=None, current_filter=None
     (a0, omega, w0, tau_fwhm, t_peak, i_s, yc, zc) adds the soft laser sheet;
     ``current_filter`` = (passes, compensate) filters the particle current each cycle
     (see ``current_filter``); ``guide`` = dict(pec_y, pec_z, port, e0, omega, tau,
-    mode_y) adds perfectly conducting walls on the planes y = 0 / z = 0 and a hard TE
-    port on the face x = 0 of an open x (see ``pic_oracle.c``)."""
+    mode_y, esirkepov) adds perfectly conducting walls on the planes y = 0 / z = 0, a
+    hard TE port on the face x = 0 of an open x, and with esirkepov = 1 deposits J with
+    Esirkepov's scheme instead of ZigZag (see ``pic_oracle.c``)."""
     n, d, pn, pd = _grid(n, d)
     assert F.dtype == np.float64 and F.flags.c_contiguous and F.shape[0] == 9
     ns = len(species)
@@ -249,7 +259,8 @@ def run(n, d, dt, F, species, nsteps=1, step0=0, laser=None, current_filter=None
     gd = None
     if guide is not None:
         gd = np.array([guide.get("pec_y", 0), guide.get("pec_z", 0), guide.get("port", 0), guide.get("e0", 0.0),
-                       guide.get("omega", 0.0), guide.get("tau", 1.0), guide.get("mode_y", 1)], dtype=np.float64)
+                       guide.get("omega", 0.0), guide.get("tau", 1.0), guide.get("mode_y", 1),
+                       guide.get("esirkepov", 0)], dtype=np.float64)
     lib().or_run(pn, pd, dt, _p(F), ns, _p(qm), npc.ctypes.data_as(_lp), ptrs, cptrs, nsteps, _p(diag), int(step0),
                  None if las is None else _p(las), None if filt is None else _p(filt),
                  None if gd is None else _p(gd))

@@ -329,6 +329,68 @@ static void zigzag(const or_grid* g, double qw, const long c0[3], const double X
     segment_current(g, qw, cell2, D2, W2, J);
 }
 
+/* Esirkepov's charge-conserving deposit (Esirkepov 2001; section 2.5 names it among
+ * the charge-conserving schemes, the paper's runs use ZigZag) with the same first-order
+ * (CIC) particle shape.  For a straight move X1 -> X2 (cell units relative to cell c0,
+ * less than one cell per dimension) let S0, S1 be the node weights 1 - |X - node| before
+ * and after, DS = S1 - S0 (on the three nodes b .. b + 2 per dimension, b the lower of
+ * the two cells), and
+ *   Wx = DSx (S0y S0z + DSy S0z / 2 + S0y DSz / 2 + DSy DSz / 3)   (y, z cyclically);
+ * then Jx(i + 1/2) = -(q w / (dt dy dz)) sum_{i' <= i} Wx(i'), the sum along x from the
+ * support's first node, and likewise Jy, Jz.  The W sum to the change of the node
+ * charge, so the discrete continuity equation holds exactly.                        */
+static double cic(double r) { r = fabs(r); return r < 1.0 ? 1.0 - r : 0.0; }
+
+static void esirkepov(const or_grid* g, double qw, const long c0[3], const double X1[3], const double X2[3], double* J)
+{
+    long N = ncells(g);
+    double C[3] = {qw / (g->dt * g->d[1] * g->d[2]),
+                   qw / (g->dt * g->d[2] * g->d[0]),
+                   qw / (g->dt * g->d[0] * g->d[1])};
+    long b[3];
+    double S0[3][3], DS[3][3];
+    for (int d = 0; d < 3; d++) {
+        long f1 = (long)floor(X1[d]), f2 = (long)floor(X2[d]);
+        b[d] = f1 < f2 ? f1 : f2;
+        for (int m = 0; m < 3; m++) {
+            double node = (double)(b[d] + m);
+            S0[d][m] = cic(X1[d] - node);
+            DS[d][m] = cic(X2[d] - node) - S0[d][m];
+        }
+    }
+    for (int comp = 0; comp < 3; comp++) {
+        int p = (comp + 1) % 3, r = (comp + 2) % 3;
+        for (int jp = 0; jp < 3; jp++)
+            for (int jr = 0; jr < 3; jr++) {
+                double acc = 0.0;
+                for (int i = 0; i < 2; i++) {   /* edges b + 1/2 and b + 3/2 along comp */
+                    double W = DS[comp][i] * (S0[p][jp] * S0[r][jr] + 0.5 * DS[p][jp] * S0[r][jr]
+                                              + 0.5 * S0[p][jp] * DS[r][jr] + DS[p][jp] * DS[r][jr] / 3.0);
+                    acc += W;
+                    long idx[3];
+                    idx[comp] = c0[comp] + b[comp] + i;
+                    idx[p] = c0[p] + b[p] + jp;
+                    idx[r] = c0[r] + b[r] + jr;
+                    long e = cell_index(g, idx[0], idx[1], idx[2]);
+                    if (e >= 0 && acc != 0.0) J[comp * N + e] += -C[comp] * acc;
+                }
+            }
+    }
+}
+
+void or_esirkepov(const int* n, const double* d, double dt, double qw, const double* X1, const double* X2, double* J)
+{
+    or_grid g = mkgrid(n, d, dt);
+    long c0[3];
+    double a[3], bb[3];
+    for (int k = 0; k < 3; k++) {
+        c0[k] = (long)floor(X1[k]);
+        a[k] = X1[k] - (double)c0[k];
+        bb[k] = X2[k] - (double)c0[k];
+    }
+    esirkepov(&g, qw, c0, a, bb, J);
+}
+
 void or_zigzag(const int* n, const double* d, double dt, double qw, const double* X1, const double* X2, double* J)
 {
     or_grid g = mkgrid(n, d, dt);
@@ -531,7 +593,8 @@ void or_current_filter(const int* n, const double* d, double* J, int passes, int
 /* Perfectly conducting walls and a waveguide port (section 3.2: the Yee solver is
  * verified on the TE10 mode of a perfectly conducting rectangular guide driven at its
  * input plane; the paper gives no discretisation of either).
- * guide = {pec_y, pec_z, port, e0, omega, tau, mode_y}.
+ * guide = {pec_y, pec_z, port, e0, omega, tau, mode_y, deposit}; deposit = 1 selects
+ * Esirkepov's deposit instead of ZigZag (see esirkepov).
  * pec_y: the node plane y = 0 is a perfect conductor, its tangential Ex and Ez are
  *   held at zero; with y periodic that plane is both walls of a guide 0 <= y <= ny.
  * pec_z: likewise the plane z = 0 (Ex, Ey).
@@ -603,7 +666,8 @@ void or_step(const int* n, const double* d, double dt, double* F, int ns, const 
             K += w * m * (0.5 * (g_old + g_new) - 1.0);
             double X2[3];
             for (int dd = 0; dd < 3; dd++) X2[dd] = X1[dd] + dt * u[dd] / (g_new * d[dd]);
-            zigzag(&g, q * w, cell, X1, X2, J);
+            if (guide && guide[7] != 0) esirkepov(&g, q * w, cell, X1, X2, J);
+            else zigzag(&g, q * w, cell, X1, X2, J);
             int gone = 0;
             for (int dd = 0; dd < 3; dd++) {
                 /* new cell and offset; an offset that rounds to 1 starts the next cell */
