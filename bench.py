@@ -248,6 +248,22 @@ def other_workloads(torch, peak):
         "kernels": {k: {"launches": v[0], "ms": round(v[1], 3)} for k, v in kt.items() if v[0]},
         "note": "'other' holds the filter: 3 passes over J (3 x 8 bytes read and written per cell each)"}
     ctx.close()
+    # the thermal workload with Esirkepov's deposit (the crossers' currents from their
+    # 3x3x3 supports, computed by the whole warp)
+    wl = W.thermal((128, 128, 128), WORKLOAD["d"], WORKLOAD["ppc"], WORKLOAD["u_th"], seed=WORKLOAD["seed"])
+    ctx = gbpic.Context(wl.n, wl.d, wl.dt, precision=gbpic.PIC_FP32, rho_ion=wl.rho_ion)
+    ctx.set_deposit(gbpic.PIC_DEPOSIT_ESIRKEPOV)
+    s = wl.species[0]
+    ctx.load_species_array(s.q, s.m, s.P, True)
+    del wl
+    time_steps(ctx, torch, 3)
+    steps = 10
+    ms, kt = time_steps(ctx, torch, steps)
+    out["thermal_128_esirkepov_f32"] = {
+        "value": s.n * steps / (ms / 1e3), "unit": UNIT, "steps": steps, "ms_per_step": ms / steps,
+        "particles": s.n, "deposit": "Esirkepov (CIC)",
+        "kernels": {k: {"launches": v[0], "ms": round(v[1], 3)} for k, v in kt.items() if v[0]}}
+    ctx.close()
     # the same run with the moving window: a one-cell move every ceil(dx / dt) = 3 cycles
     # from the first cycle on, the new column's plasma injected at each move
     wl = W.lwfa(window_start=0)

@@ -222,6 +222,18 @@ pic_status pic_set_pec(pic_ctx* ctx, int32_t pec_y, int32_t pec_z);
  * bc_x = 1; PIC_ERR_ARG for tau <= 0, mode_y < 1 or non-finite values. */
 pic_status pic_set_port(pic_ctx* ctx, const pic_port_desc* port);
 
+/* The current deposit (section 2.5): PIC_DEPOSIT_ZIGZAG (default, the paper's: Umeda et
+ * al. 2003) or PIC_DEPOSIT_ESIRKEPOV (Esirkepov 2001, which section 2.5 names among the
+ * charge-conserving schemes), both with the first-order (CIC) particle shape and exact
+ * discrete continuity.  For a move inside one cell they give the same current (the
+ * exact flux of the straight segment through the trilinear cloud); a move across cell
+ * faces is one straight segment for Esirkepov (weights Wx = DSx (S0y S0z + DSy S0z / 2 +
+ * S0y DSz / 2 + DSy DSz / 3) on the 3x3x3 support, Jx the running sum of -q w Wx /
+ * (dt dy dz) along x) and two relayed segments for ZigZag.  The adjoint supports ZigZag
+ * only (PIC_ERR_STATE).  Call before stepping or between steps. */
+typedef enum pic_deposit { PIC_DEPOSIT_ZIGZAG = 0, PIC_DEPOSIT_ESIRKEPOV = 1 } pic_deposit;
+pic_status pic_set_deposit(pic_ctx* ctx, int32_t deposit);
+
 /* Compensated binomial current filter.  Section 2.2 counts "compensated smoothing"
  * among the operations of a cycle and section 2.6 lists a current-filtering module;
  * the paper gives no scheme and its runs use none, so it is off by default.  With

@@ -646,8 +646,10 @@ extern "C" {
 
 pic_status pic_adjoint_forward(pic_ctx* c, int32_t nsteps, int32_t ckpt_every, double* loss) {
     if (!c || nsteps < 1 || ckpt_every < 1 || !loss) return PIC_ERR_ARG;
-    if (!c->desc.track_ids || c->species.empty() || c->g.open_x || c->filter_passes > 0) {
-        c->err = "pic_adjoint_forward needs track_ids, at least one species, a periodic box and no current filter";
+    if (!c->desc.track_ids || c->species.empty() || c->g.open_x || c->filter_passes > 0 ||
+        c->deposit != PIC_DEPOSIT_ZIGZAG) {
+        c->err = "pic_adjoint_forward needs track_ids, at least one species, a periodic box, no current filter "
+                 "and the ZigZag deposit";
         return PIC_ERR_STATE;
     }
     cudaSetDevice(c->desc.device);

@@ -469,6 +469,16 @@ pic_status pic_set_port(pic_ctx* c, const pic_port_desc* p) {
     return PIC_OK;
 }
 
+pic_status pic_set_deposit(pic_ctx* c, int32_t deposit) {
+    if (!c) return PIC_ERR_ARG;
+    if (deposit != PIC_DEPOSIT_ZIGZAG && deposit != PIC_DEPOSIT_ESIRKEPOV) {
+        c->err = "pic_set_deposit: PIC_DEPOSIT_ZIGZAG or PIC_DEPOSIT_ESIRKEPOV";
+        return PIC_ERR_ARG;
+    }
+    c->deposit = deposit;
+    return PIC_OK;
+}
+
 pic_status pic_set_current_filter(pic_ctx* c, int32_t passes, int32_t compensate) {
     if (!c) return PIC_ERR_ARG;
     if (passes < 0 || passes > MAX_FILTER_PASSES || (compensate != 0 && compensate != 1)) {

@@ -453,6 +453,67 @@ __device__ __forceinline__ void zigzag_deposit(AddFn Add, int x, int y, int z, c
     }
 }
 
+// Esirkepov's charge-conserving deposit (Esirkepov 2001; section 2.5 names it next to
+// ZigZag) with the CIC shape, for a move from offsets d1 in cell (x, y, z) to offsets d2
+// in cell (x, y, z) + s.  Per dimension the support is the nodes b .. b + 2, b = min(0, s)
+// (relative to the start cell), with S0, S1 the node weights before and after and
+// DS = S1 - S0;  Wx = DSx (S0y S0z + DSy S0z / 2 + S0y DSz / 2 + DSy DSz / 3) (y, z
+// cyclically) and Jx at the edge b + i + 1/2 is -cw_x times the sum of Wx over the
+// nodes b .. b + i.  esk_value returns one of the 54 values (component comp, edge i of
+// 2, nodes jp, jr of 3 along the two other dimensions in cyclic order); X1, X2 are the
+// positions relative to the support's first node.
+template <typename T> __device__ __forceinline__ T cic_w(T r) {
+    r = r < T(0) ? -r : r;
+    return r < T(1) ? T(1) - r : T(0);
+}
+// element k of a 3-vector by selects (a runtime index into a local array would put the
+// array in local memory)
+template <typename T> __device__ __forceinline__ T sel3(const T a[3], int k) {
+    return k == 0 ? a[0] : (k == 1 ? a[1] : a[2]);
+}
+template <typename T>
+__device__ __forceinline__ T esk_value(const T X1[3], const T X2[3], const T cw[3], int comp, int i, int jp, int jr) {
+    const int p = comp == 2 ? 0 : comp + 1, r = comp == 0 ? 2 : comp - 1;
+    const T x1p = sel3(X1, p), x2p = sel3(X2, p), x1r = sel3(X1, r), x2r = sel3(X2, r);
+    const T x1c = sel3(X1, comp), x2c = sel3(X2, comp);
+    const T s0p = cic_w(x1p - T(jp)), dsp = cic_w(x2p - T(jp)) - s0p;
+    const T s0r = cic_w(x1r - T(jr)), dsr = cic_w(x2r - T(jr)) - s0r;
+    const T t = s0p * s0r + T(0.5) * dsp * s0r + T(0.5) * s0p * dsr + dsp * dsr / T(3);
+    T acc = (cic_w(x2c) - cic_w(x1c)) * t;
+    if (i == 1) acc += (cic_w(x2c - T(1)) - cic_w(x1c - T(1))) * t;
+    return -sel3(cw, comp) * acc;
+}
+
+// The whole Esirkepov deposit of one move through Add(comp, x, y, z, fixed) (global
+// or tile coordinates of the J component's location).
+template <typename T, typename AddFn>
+__device__ __forceinline__ void esirkepov_deposit(AddFn Add, int x, int y, int z, const T d1[3], const int s[3],
+                                                  const T d2[3], const T cw[3]) {
+    int b[3];
+    T X1[3], X2[3];
+#pragma unroll
+    for (int k = 0; k < 3; ++k) {
+        b[k] = s[k] < 0 ? -1 : 0;
+        X1[k] = d1[k] - T(b[k]);
+        X2[k] = d2[k] + T(s[k] - b[k]);
+    }
+    const int o[3] = {x + b[0], y + b[1], z + b[2]};
+    for (int comp = 0; comp < 3; ++comp) {
+        const int p = comp == 2 ? 0 : comp + 1, r = comp == 0 ? 2 : comp - 1;
+        for (int i = 0; i < 2; ++i)
+            for (int jp = 0; jp < 3; ++jp)
+                for (int jr = 0; jr < 3; ++jr) {
+                    const T v = esk_value(X1, X2, cw, comp, i, jp, jr);
+                    if (v == T(0)) continue;
+                    int c3[3];
+                    c3[comp] = o[comp] + i;
+                    c3[p] = o[p] + jp;
+                    c3[r] = o[r] + jr;
+                    Add(comp, c3[0], c3[1], c3[2], to_acc(v));
+                }
+    }
+}
+
 __device__ __forceinline__ int wrap_idx(int i, int n) {
     i %= n;
     return i < 0 ? i + n : i;
@@ -611,6 +672,7 @@ struct pic_ctx {
     int pec_y = 0, pec_z = 0;
     bool port_on = false;
     pic_port_desc port{};
+    int deposit = 0;                    // pic_deposit: ZigZag or Esirkepov
 };
 
 namespace gbpic {

@@ -258,6 +258,52 @@ template <> struct RowCells<2> {
     static __device__ __forceinline__ int key(const int c[2]) { return c[0] >= 0 ? c[0] : c[1]; }
 };
 
+// Esirkepov's deposit of the cell crossers of one particle step (warp-collective): the
+// record queue is drained, each crosser writes its record there (positions relative to
+// the first node of its 3x3x3 support, cw, the support's first node packed), and the 32
+// lanes share the 54 stencil values of every record (see esk_value).
+constexpr int ESK_WORDS = 10;   // X1[3], X2[3], cw[3], packed first node
+static_assert(32 * ESK_WORDS <= QWORDS, "the crossers' records fit in the record queue");
+template <typename T>
+__device__ __forceinline__ void esk_crossers(WarpQueue<T> Q, int& qn, int lane, uint32_t sJa, int qoff, bool mine, int x,
+                                             int y, int z, const T d1[3], const T d2[3], const int s[3], const T cw[3]) {
+    if (qn) q_drain(Q, qn, lane, sJa, qoff);
+    const unsigned mc = __ballot_sync(0xffffffffu, mine);
+    if (mine) {
+        T* rec = Q.rec + __popc(mc & ((1u << lane) - 1u)) * ESK_WORDS;
+        int b[3];
+#pragma unroll
+        for (int k = 0; k < 3; ++k) {
+            b[k] = s[k] < 0 ? -1 : 0;
+            rec[k] = d1[k] - T(b[k]);
+            rec[3 + k] = d2[k] + T(s[k] - b[k]);
+            rec[6 + k] = cw[k];
+        }
+        // first node of the support, local -1 .. 7 per dimension, packed in 4 bits each
+        *reinterpret_cast<int*>(rec + 9) = (x + b[0] + 1) | ((y + b[1] + 1) << 4) | ((z + b[2] + 1) << 8);
+    }
+    __syncwarp();
+    const int m = __popc(mc);
+    for (int it = lane; it < m * 54; it += 32) {
+        const int r = it / 54, q = it - 54 * r;
+        const int comp = q / 18, rem = q - 18 * comp;
+        const int i = rem / 9, jp = (rem - 9 * i) / 3, jr = rem - 9 * i - 3 * jp;
+        const T* rec = Q.rec + r * ESK_WORDS;
+        const T X1[3] = {rec[0], rec[1], rec[2]}, X2[3] = {rec[3], rec[4], rec[5]}, c3w[3] = {rec[6], rec[7], rec[8]};
+        const T v = esk_value(X1, X2, c3w, comp, i, jp, jr);
+        if (v == T(0)) continue;
+        const int pk = *reinterpret_cast<const int*>(rec + 9);
+        // the value's location: edge i along comp, node jp along the next dimension and
+        // jr along the one after (cyclic), from the support's first node
+        const int ax = comp == 0 ? i : (comp == 2 ? jp : jr);
+        const int ay = comp == 1 ? i : (comp == 0 ? jp : jr);
+        const int az = comp == 2 ? i : (comp == 1 ? jp : jr);
+        tile_add(sJa, tile_index(comp, (pk & 15) - 1 + ax, ((pk >> 4) & 15) - 1 + ay, ((pk >> 8) & 15) - 1 + az),
+                 JT_ELEMS, v);
+    }
+    __syncwarp();
+}
+
 // Write a warp's mq staged movers to the global mover list: one counter atomic per
 // batch (the only global atomic whose result a warp waits for), then the records by
 // the lanes (warp-collective).
@@ -288,7 +334,7 @@ __device__ __forceinline__ void movers_flush(const PushArgs<T>& A, const Rec<T>*
 // R particles nearly always start in one cell: their straight-segment currents are
 // summed in registers and each row ends with one warp flush of those sums; everything
 // else goes through the warp's record queue.
-template <typename T, bool IDS, bool RECK>
+template <typename T, bool IDS, bool RECK, bool ESK>
 __global__ void __launch_bounds__(Prec<T>::THREADS, Prec<T>::MINB)
 k_tile_push(const __grid_constant__ CUtensorMap tE0, const __grid_constant__ CUtensorMap tE1,
             const __grid_constant__ CUtensorMap tE2, const __grid_constant__ CUtensorMap tB0,
@@ -547,7 +593,7 @@ k_tile_push(const __grid_constant__ CUtensorMap tE0, const __grid_constant__ CUt
                 if (nlc >= 0 && lane == __ffs(grp) - 1) atomicAdd(&s_hn[nlc], __popc(grp));
             }
             // a crosser's second segment, in the cell it moved to (relay split)
-            if (__any_sync(0xffffffffu, crossed)) {
+            if (!ESK && __any_sync(0xffffffffu, crossed)) {
                 T F2[3], W2[3];
 #pragma unroll
                 for (int k = 0; k < 3; ++k) {
@@ -557,13 +603,16 @@ k_tile_push(const __grid_constant__ CUtensorMap tE0, const __grid_constant__ CUt
                 }
                 segment_values_pairs(cw, F2, W2, v2);
             }
-            const bool summed = active && lc == key;
+            // with Esirkepov's deposit a crosser's whole current is its own stencil (below)
+            const bool esk_cross = ESK && crossed;
+            const bool summed = active && lc == key && !esk_cross;
             if (summed) {
 #pragma unroll
                 for (int q = 0; q < 6; ++q) acc[q] = Pair<T>::add(acc[q], v[q]);
             }
-            q_push(Q, qn, active && !summed, tile_index(0, x, y, z), v, crossed,
+            q_push(Q, qn, active && !summed && !esk_cross, tile_index(0, x, y, z), v, !ESK && crossed,
                    tile_index(0, x + s[0], y + s[1], z + s[2]), v2, lane, sJa, qoff);
+            if (ESK && __any_sync(0xffffffffu, esk_cross)) esk_crossers<T>(Q, qn, lane, sJa, qoff, esk_cross, x, y, z, d1, d2, s, cw);
             // movers: staged in shared memory with their wrapped global cell and written to
             // the global list in batches; a particle that left an open x face is removed
             // instead
@@ -629,7 +678,7 @@ k_tile_push(const __grid_constant__ CUtensorMap tE0, const __grid_constant__ CUt
 }
 
 // Spill-list particles: same arithmetic with global-memory gather and deposit.
-template <typename T, bool RECK>
+template <typename T, bool RECK, bool ESK>
 __global__ void __launch_bounds__(256) k_list_push(PushArgs<T> A) {
     const int n = min(A.ctr->spill_count[A.parity], A.spill_cap);
     double kacc = 0.0;
@@ -662,7 +711,8 @@ __global__ void __launch_bounds__(256) k_list_push(PushArgs<T> A) {
             }
         }
         const T cw[3] = {A.cq[0] * r.w, A.cq[1] * r.w, A.cq[2] * r.w};
-        zigzag_deposit<T>(add, gx, gy, gz, r.d, s, d2, cw);
+        if (ESK) esirkepov_deposit<T>(add, gx, gy, gz, r.d, s, d2, cw);
+        else zigzag_deposit<T>(add, gx, gy, gz, r.d, s, d2, cw);
         int nxg = x_after(A.g, gx + s[0]);
         if (nxg >= 0) nxg -= A.xshift;   // a window move: the first column leaves
         if (nxg < 0) {   // left an open x face (or the window): removed
@@ -841,9 +891,9 @@ static int sm_count(pic_ctx* c) {
     return v > 0 ? v : 152;
 }
 
-template <typename T, bool IDS, bool RECK>
+template <typename T, bool IDS, bool RECK, bool ESK>
 static pic_status launch_tile(pic_ctx* c, PushArgs<T>& A) {
-    auto kern = k_tile_push<T, IDS, RECK>;
+    auto kern = k_tile_push<T, IDS, RECK, ESK>;
     const size_t smem = tile_smem_bytes<T>();
     static bool attr_set = false;
     if (!attr_set) {
@@ -914,14 +964,25 @@ static pic_status push_species_t(pic_ctx* c, SpeciesDev& s, int parity, double* 
     A.xshift = xshift;
     const bool ids = c->desc.track_ids != 0, rec = krec != nullptr;
     pic_status st;
-    if (ids) st = rec ? launch_tile<T, true, true>(c, A) : launch_tile<T, true, false>(c, A);
-    else st = rec ? launch_tile<T, false, true>(c, A) : launch_tile<T, false, false>(c, A);
+    const bool esk = c->deposit == PIC_DEPOSIT_ESIRKEPOV;
+    if (esk) {
+        if (ids) st = rec ? launch_tile<T, true, true, true>(c, A) : launch_tile<T, true, false, true>(c, A);
+        else st = rec ? launch_tile<T, false, true, true>(c, A) : launch_tile<T, false, false, true>(c, A);
+    } else {
+        if (ids) st = rec ? launch_tile<T, true, true, false>(c, A) : launch_tile<T, true, false, false>(c, A);
+        else st = rec ? launch_tile<T, false, true, false>(c, A) : launch_tile<T, false, false, false>(c, A);
+    }
     if (st != PIC_OK) return st;
     const int grid = 2 * sm_count(c);
     {
         LaunchScope ls(c, KC_LIST_PUSH);
-        if (rec) k_list_push<T, true><<<grid, 256, 0, c->stream>>>(A);
-        else k_list_push<T, false><<<grid, 256, 0, c->stream>>>(A);
+        if (esk) {
+            if (rec) k_list_push<T, true, true><<<grid, 256, 0, c->stream>>>(A);
+            else k_list_push<T, false, true><<<grid, 256, 0, c->stream>>>(A);
+        } else {
+            if (rec) k_list_push<T, true, false><<<grid, 256, 0, c->stream>>>(A);
+            else k_list_push<T, false, false><<<grid, 256, 0, c->stream>>>(A);
+        }
         GBPIC_CHECK(c, cudaGetLastError());
     }
     if (inject) {

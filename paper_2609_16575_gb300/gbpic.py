@@ -29,6 +29,8 @@ PIC_FP64 = 1
 STATUS_NAMES = {0: "PIC_OK", 1: "PIC_ERR_ARG", 2: "PIC_ERR_CFL", 3: "PIC_ERR_OOM", 4: "PIC_ERR_CUDA",
                 5: "PIC_ERR_TILE_OVERFLOW", 6: "PIC_ERR_SUPERLUMINAL", 7: "PIC_ERR_NAN", 8: "PIC_ERR_STATE",
                 9: "PIC_ERR_TIMEOUT", 10: "PIC_ERR_NO_DEVICE"}
+PIC_DEPOSIT_ZIGZAG = 0
+PIC_DEPOSIT_ESIRKEPOV = 1
 
 ALLOC_FN = ctypes.CFUNCTYPE(ctypes.c_void_p, ctypes.c_size_t, ctypes.c_void_p)
 FREE_FN = ctypes.CFUNCTYPE(None, ctypes.c_void_p, ctypes.c_void_p)
@@ -117,6 +119,7 @@ def lib():
             L.pic_set_moving_window.argtypes = [P, ctypes.POINTER(pic_window_desc)]
             L.pic_set_current_filter.argtypes = [P, ctypes.c_int32, ctypes.c_int32]
             L.pic_set_pec.argtypes = [P, ctypes.c_int32, ctypes.c_int32]
+            L.pic_set_deposit.argtypes = [P, ctypes.c_int32]
             L.pic_set_port.argtypes = [P, ctypes.POINTER(pic_port_desc)]
             L.pic_window_moves.argtypes = [P]
             L.pic_window_moves.restype = ctypes.c_int64
@@ -133,7 +136,7 @@ def lib():
                          "pic_get_fields", "pic_get_particles", "pic_diagnostics", "pic_get_history",
                          "pic_set_timing", "pic_kernel_times", "pic_adjoint_forward", "pic_adjoint_backward",
                          "pic_gauss_check_static", "pic_set_laser", "pic_set_moving_window",
-                         "pic_set_current_filter", "pic_set_pec", "pic_set_port"):
+                         "pic_set_current_filter", "pic_set_pec", "pic_set_port", "pic_set_deposit"):
                 getattr(L, name).restype = ctypes.c_int
             _lib = L
     return _lib
@@ -353,6 +356,10 @@ class Context:
         """Compensated binomial current filter (see pic_set_current_filter); 0 passes: off."""
         _check(self.ptr, lib().pic_set_current_filter(self.ptr, int(passes), int(compensate)),
                "pic_set_current_filter")
+
+    def set_deposit(self, scheme):
+        """PIC_DEPOSIT_ZIGZAG (0, default) or PIC_DEPOSIT_ESIRKEPOV (1)."""
+        _check(self.ptr, lib().pic_set_deposit(self.ptr, int(scheme)), "pic_set_deposit")
 
     def set_pec(self, pec_y, pec_z):
         """Conducting wall planes y = 0 / z = 0 (see pic_set_pec); fields only."""
