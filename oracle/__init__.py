@@ -78,6 +78,9 @@ def lib():
                                  _dp]
             L.or_current_filter.argtypes = [_ip, _dp, _dp, ctypes.c_int, ctypes.c_int]
             L.or_esirkepov.argtypes = [_ip, _dp, ctypes.c_double, ctypes.c_double, _dp, _dp, _dp]
+            L.or_push.argtypes = [_ip, _dp, ctypes.c_double, _dp, _dp, ctypes.c_double, ctypes.c_double, ctypes.c_long,
+                                  _dp, _dp, _dp, ctypes.c_int]
+            L.or_push.restype = ctypes.c_double
             L.or_window_shift.argtypes = [_ip, _dp, _dp, ctypes.c_int, _lp, ctypes.POINTER(_dp), ctypes.POINTER(_dp)]
             L.or_gauss_x.argtypes = [_ip, _dp, _dp, _dp]
             L.or_gauss_x.restype = ctypes.c_double
@@ -198,6 +201,15 @@ def esirkepov(n, d, dt, qw, X1, X2, J):
     n, d, pn, pd = _grid(n, d)
     f = lambda v: np.ascontiguousarray(v, dtype=np.float64)
     lib().or_esirkepov(pn, pd, dt, qw, _p(f(X1)), _p(f(X2)), _p(J))
+
+
+def push(n, d, dt, E, Bn, species, J, esirkepov=False):
+    """The particle part of one cycle for one species (gather of E^n and B^n = ``Bn``,
+    Boris, move, deposit into J), in place; returns the species' kinetic energy at the
+    cycle's time level.  The same code as inside ``run``."""
+    n_, d_, pn, pd = _grid(n, d)
+    return lib().or_push(pn, pd, dt, _p(np.ascontiguousarray(E)), _p(np.ascontiguousarray(Bn)), species.q, species.m,
+                         species.n, _p(species.Q), _p(species.C), _p(J), int(bool(esirkepov)))
 
 
 def rho(n, d, species, rho_ion=0.0):

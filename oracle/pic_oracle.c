@@ -628,6 +628,62 @@ static void pec_walls(const or_grid* g, const double* guide, double* E)
             }
 }
 
+/* The particle part of the cycle (section 2.2, Fig. 2, steps 3-4) for one species of
+ * charge q and mass m: gather E^n, B^n at x^n (Bn holds B^n), Boris push, move, and the
+ * current of the move into J (ZigZag, or Esirkepov when esk is set); a particle that
+ * leaves an open x is removed (weight 0).  Returns the species' kinetic energy at time
+ * level n, sum w m ((gamma^{n-1/2} + gamma^{n+1/2}) / 2 - 1).                       */
+static double push_species(const or_grid* gp, double q, double m, long cnt, double* Ps, double* Cs,
+                           const double* E, const double* Bn, double* J, int esk)
+{
+    const or_grid g = *gp;
+    const int* n = g.n;
+    const double* d = g.d;
+    double dt = g.dt;
+    double K = 0.0;
+    for (long p = 0; p < cnt; p++) {
+        if (Ps[6 * cnt + p] == 0.0) continue;   /* removed through an open face */
+        long cell[3] = {(long)Cs[p], (long)Cs[cnt + p], (long)Cs[2 * cnt + p]};
+        double X1[3] = {Ps[p], Ps[cnt + p], Ps[2 * cnt + p]};          /* offsets: X relative to cell */
+        double u[3] = {Ps[3 * cnt + p], Ps[4 * cnt + p], Ps[5 * cnt + p]};
+        double w = Ps[6 * cnt + p];
+        double Ep[3], Bp[3];
+        gather(&g, E, Bn, cell, X1, Ep, Bp);
+        double g_old = gamma_of(u);
+        or_boris(q * dt / (2.0 * m), Ep, Bp, u);
+        double g_new = gamma_of(u);
+        K += w * m * (0.5 * (g_old + g_new) - 1.0);
+        double X2[3];
+        for (int dd = 0; dd < 3; dd++) X2[dd] = X1[dd] + dt * u[dd] / (g_new * d[dd]);
+        if (esk) esirkepov(&g, q * w, cell, X1, X2, J);
+        else zigzag(&g, q * w, cell, X1, X2, J);
+        int gone = 0;
+        for (int dd = 0; dd < 3; dd++) {
+            /* new cell and offset; an offset that rounds to 1 starts the next cell */
+            double f = floor(X2[dd]);
+            double o = X2[dd] - f;
+            long cn = cell[dd] + (long)f;
+            if (o >= 1.0) { o = 0.0; cn += 1; }
+            if (dd == 0 && g.open_x && (cn < 0 || cn >= n[0])) gone = 1;
+            Cs[dd * cnt + p] = (double)wrapi(cn, n[dd]);
+            Ps[dd * cnt + p] = o;
+        }
+        if (gone) Ps[6 * cnt + p] = 0.0;
+        Ps[3 * cnt + p] = u[0];
+        Ps[4 * cnt + p] = u[1];
+        Ps[5 * cnt + p] = u[2];
+    }
+    return K;
+}
+
+/* push_species as an entry point: E and Bn (B^n) are read, J is added to.             */
+double or_push(const int* n, const double* d, double dt, const double* E, const double* Bn, double q, double m, long np,
+               double* P, double* C, double* J, int esk)
+{
+    or_grid g = mkgrid(n, d, dt);
+    return push_species(&g, q, m, np, P, C, E, Bn, J, esk);
+}
+
 void or_step(const int* n, const double* d, double dt, double* F, int ns, const double* qm, const long* np,
              double** P, double** C, double* diag, long step, const double* laser, const double* filt,
              const double* guide)
@@ -652,38 +708,7 @@ void or_step(const int* n, const double* d, double dt, double* F, int ns, const 
         double* Ps = P[s];
         double* Cs = C[s];
         long cnt = np[s];
-        for (long p = 0; p < cnt; p++) {
-            if (Ps[6 * cnt + p] == 0.0) continue;   /* removed through an open face */
-            long cell[3] = {(long)Cs[p], (long)Cs[cnt + p], (long)Cs[2 * cnt + p]};
-            double X1[3] = {Ps[p], Ps[cnt + p], Ps[2 * cnt + p]};          /* offsets: X relative to cell */
-            double u[3] = {Ps[3 * cnt + p], Ps[4 * cnt + p], Ps[5 * cnt + p]};
-            double w = Ps[6 * cnt + p];
-            double Ep[3], Bp[3];
-            gather(&g, E, Bn, cell, X1, Ep, Bp);
-            double g_old = gamma_of(u);
-            or_boris(q * dt / (2.0 * m), Ep, Bp, u);
-            double g_new = gamma_of(u);
-            K += w * m * (0.5 * (g_old + g_new) - 1.0);
-            double X2[3];
-            for (int dd = 0; dd < 3; dd++) X2[dd] = X1[dd] + dt * u[dd] / (g_new * d[dd]);
-            if (guide && guide[7] != 0) esirkepov(&g, q * w, cell, X1, X2, J);
-            else zigzag(&g, q * w, cell, X1, X2, J);
-            int gone = 0;
-            for (int dd = 0; dd < 3; dd++) {
-                /* new cell and offset; an offset that rounds to 1 starts the next cell */
-                double f = floor(X2[dd]);
-                double o = X2[dd] - f;
-                long cn = cell[dd] + (long)f;
-                if (o >= 1.0) { o = 0.0; cn += 1; }
-                if (dd == 0 && g.open_x && (cn < 0 || cn >= n[0])) gone = 1;
-                Cs[dd * cnt + p] = (double)wrapi(cn, n[dd]);
-                Ps[dd * cnt + p] = o;
-            }
-            if (gone) Ps[6 * cnt + p] = 0.0;
-            Ps[3 * cnt + p] = u[0];
-            Ps[4 * cnt + p] = u[1];
-            Ps[5 * cnt + p] = u[2];
-        }
+        K += push_species(&g, q, m, cnt, Ps, Cs, E, Bn, J, guide && guide[7] != 0);
     }
     if (filt && filt[0] > 0) or_current_filter(n, d, J, (int)filt[0], (int)filt[1]);
     if (laser) laser_source(&g, laser, (step + 0.5) * dt, J);
