@@ -268,6 +268,23 @@ pic_status pic_get_fields(pic_ctx* ctx, double* E, double* B, double* J, int32_t
  * alive).  out may be NULL to query *n.  Synchronises. */
 pic_status pic_get_particles(pic_ctx* ctx, int32_t species, double* out, int64_t* n, int32_t device_pointers);
 
+/* Checkpoint / resume.  pic_save_state writes the dynamical state to a host byte blob
+ * that the library allocates (*blob; *bytes its size; release it with pic_free_state):
+ * E^n and B^{n-1/2}, every species' particles held (positions, u^{n-1/2}, weights, and
+ * with track_ids their ids), their charge, mass, fixed-point J unit and counters
+ * (loaded, injected, escaped), the step count and the window's moves.  Synchronises.
+ * pic_load_state restores it into a fresh context (no species loaded, no step taken)
+ * created with the same grid, time step, precision, bc_x and track_ids; settings that are
+ * not state (laser, window, filter, walls, port, deposit, energy recording) are set on the
+ * new context by the caller first, the window before pic_load_state.  The particles are
+ * sorted into tiles again, so the run continues as if it had not stopped up to the
+ * rounding of the current's partial sums, which follow the particles' order in the tiles.
+ * PIC_ERR_ARG for a blob of another configuration or a damaged one, PIC_ERR_STATE for a
+ * context that is not fresh. */
+pic_status pic_save_state(pic_ctx* ctx, void** blob, size_t* bytes);
+void pic_free_state(void* blob);
+pic_status pic_load_state(pic_ctx* ctx, const void* blob, size_t bytes);
+
 /* FP64 device reductions of the current state (section 3.3 diagnostics).
  * Synchronises. */
 pic_status pic_diagnostics(pic_ctx* ctx, pic_diag* out);

@@ -4,6 +4,8 @@
 
 #include <algorithm>
 #include <cmath>
+#include <cstddef>
+#include <cstdlib>
 #include <cstdio>
 #include <cstring>
 #include <new>
@@ -183,6 +185,33 @@ pic_status step_once(pic_ctx* c, double* rec, bool keep_j) {
 }  // namespace gbpic
 
 using namespace gbpic;
+
+// Checkpoint / resume helpers (the blob layout of pic_save_state).
+namespace gbpic {
+pic_status load_species_ids(pic_ctx* c, const pic_species_desc* d, SpeciesDev& s, const double* ids);
+}
+
+namespace {
+constexpr char kStateMagic[8] = {'G', 'B', 'P', 'I', 'C', 'S', 'T', '1'};
+struct StateHeader {
+    char magic[8];
+    int32_t version, precision, n[3], bc_x, track_ids, nspecies;
+    double d[3], dt;
+    int64_t step, window_moves;
+};
+struct SpeciesHeader {
+    double q, m, jscale;
+    int64_t n_loaded, n_injected, escaped, rows;
+};
+template <typename V> void put(std::vector<unsigned char>& b, const V& v) {
+    const unsigned char* p = reinterpret_cast<const unsigned char*>(&v);
+    b.insert(b.end(), p, p + sizeof(V));
+}
+void put_doubles(std::vector<unsigned char>& b, const double* p, size_t n) {
+    const unsigned char* q = reinterpret_cast<const unsigned char*>(p);
+    b.insert(b.end(), q, q + n * sizeof(double));
+}
+}  // namespace
 
 extern "C" {
 
@@ -466,6 +495,165 @@ pic_status pic_set_port(pic_ctx* c, const pic_port_desc* p) {
     }
     c->port = *p;
     c->port_on = true;
+    return PIC_OK;
+}
+
+// ---------------------------------------------------------------------------
+// Checkpoint / resume: the dynamical state as a host byte blob.
+
+
+pic_status pic_save_state(pic_ctx* c, void** blob, size_t* bytes) {
+    if (!c || !blob || !bytes) return PIC_ERR_ARG;
+    *blob = nullptr;
+    *bytes = 0;
+    pic_status st = pic_sync(c);
+    if (st != PIC_OK) return st;
+    std::vector<unsigned char> b;
+    StateHeader h{};
+    memcpy(h.magic, kStateMagic, 8);
+    h.version = 1;
+    h.precision = c->prec;
+    for (int k = 0; k < 3; ++k) {
+        h.n[k] = c->g.n[k];
+        h.d[k] = c->desc.d[k];
+    }
+    h.bc_x = c->g.open_x;
+    h.track_ids = c->desc.track_ids ? 1 : 0;
+    h.nspecies = (int32_t)c->species.size();
+    h.dt = c->desc.dt;
+    h.step = c->step;
+    h.window_moves = c->window_moves;
+    put(b, h);
+    for (int k = 0; k < h.nspecies; ++k) {
+        SpeciesDev& s = c->species[k];
+        int64_t rows = 0;
+        st = pic_get_particles(c, k, nullptr, &rows, 0);
+        if (st != PIC_OK) return st;
+        std::vector<double> P((size_t)7 * rows);
+        if (rows > 0) {
+            st = pic_get_particles(c, k, P.data(), &rows, 0);
+            if (st != PIC_OK) return st;
+        }
+        Counters ctr;
+        GBPIC_CHECK(c, cudaMemcpy(&ctr, s.ctr, sizeof(Counters), cudaMemcpyDeviceToHost));
+        // the particles held (removed ids read as NaN and are left out; with ids each
+        // keeps its own)
+        std::vector<int64_t> keep;
+        for (int64_t p = 0; p < rows; ++p)
+            if (std::isfinite(P[(size_t)6 * rows + p])) keep.push_back(p);
+        SpeciesHeader sh{s.q, s.m, s.jscale, s.n_loaded, s.n_injected, (int64_t)ctr.escaped, (int64_t)keep.size()};
+        put(b, sh);
+        std::vector<double> col(keep.size());
+        for (int r = 0; r < 7; ++r) {
+            for (size_t i = 0; i < keep.size(); ++i) col[i] = P[(size_t)r * rows + keep[i]];
+            put_doubles(b, col.data(), col.size());
+        }
+        if (h.track_ids) {
+            for (size_t i = 0; i < keep.size(); ++i) col[i] = (double)keep[i];
+            put_doubles(b, col.data(), col.size());
+        }
+    }
+    const size_t NH = (size_t)c->g.host_N();
+    std::vector<double> E(3 * NH), B(3 * NH);
+    st = pic_get_fields(c, E.data(), B.data(), nullptr, 0);
+    if (st != PIC_OK) return st;
+    put_doubles(b, E.data(), E.size());
+    put_doubles(b, B.data(), B.size());
+    void* out = std::malloc(b.size());
+    if (!out) return PIC_ERR_OOM;
+    memcpy(out, b.data(), b.size());
+    *blob = out;
+    *bytes = b.size();
+    return PIC_OK;
+}
+
+void pic_free_state(void* blob) { std::free(blob); }
+
+pic_status pic_load_state(pic_ctx* c, const void* blob, size_t bytes) {
+    if (!c || !blob || bytes < sizeof(StateHeader)) return PIC_ERR_ARG;
+    StateHeader h;
+    memcpy(&h, blob, sizeof(h));
+    bool same = memcmp(h.magic, kStateMagic, 8) == 0 && h.version == 1 && h.precision == c->prec &&
+                h.bc_x == c->g.open_x && h.track_ids == (c->desc.track_ids ? 1 : 0) && h.dt == c->desc.dt;
+    for (int k = 0; k < 3; ++k) same = same && h.n[k] == c->g.n[k] && h.d[k] == c->desc.d[k];
+    if (!same) {
+        c->err = "pic_load_state: the state was saved from a context of another grid, precision or ids setting";
+        return PIC_ERR_ARG;
+    }
+    if (!c->species.empty() || c->step != 0) {
+        c->err = "pic_load_state needs a fresh context (no species loaded, no steps taken)";
+        return PIC_ERR_STATE;
+    }
+    const unsigned char* p = static_cast<const unsigned char*>(blob) + sizeof(h);
+    const unsigned char* end = static_cast<const unsigned char*>(blob) + bytes;
+    auto take = [&](size_t n) -> const unsigned char* {
+        if ((size_t)(end - p) < n) return nullptr;
+        const unsigned char* q = p;
+        p += n;
+        return q;
+    };
+    struct Sp {
+        SpeciesHeader sh;
+        std::vector<double> cols;   // 7 rows (+ ids)
+    };
+    std::vector<Sp> sps(h.nspecies < 0 ? 0 : h.nspecies);
+    for (auto& sp : sps) {
+        const unsigned char* q = take(sizeof(SpeciesHeader));
+        if (!q) return PIC_ERR_ARG;
+        memcpy(&sp.sh, q, sizeof(SpeciesHeader));
+        if (sp.sh.rows < 0) return PIC_ERR_ARG;
+        const size_t nv = (size_t)sp.sh.rows * (h.track_ids ? 8 : 7);
+        q = take(nv * sizeof(double));
+        if (!q) return PIC_ERR_ARG;
+        sp.cols.resize(nv);
+        memcpy(sp.cols.data(), q, nv * sizeof(double));
+    }
+    const size_t NH = (size_t)c->g.host_N();
+    const unsigned char* qe = take(3 * NH * sizeof(double));
+    const unsigned char* qb = take(3 * NH * sizeof(double));
+    if (!qe || !qb || p != end) {
+        c->err = "pic_load_state: truncated or malformed state";
+        return PIC_ERR_ARG;
+    }
+    std::vector<double> E(3 * NH), B(3 * NH);
+    memcpy(E.data(), qe, E.size() * sizeof(double));
+    memcpy(B.data(), qb, B.size() * sizeof(double));
+    pic_status st = pic_set_fields(c, E.data(), B.data(), 0);
+    if (st != PIC_OK) return st;
+    cudaSetDevice(c->desc.device);
+    for (auto& sp : sps) {
+        const int64_t n = sp.sh.rows;
+        std::vector<double> X(3 * (size_t)n), U(3 * (size_t)n), W((size_t)n);
+        memcpy(X.data(), sp.cols.data(), 3 * n * sizeof(double));
+        memcpy(U.data(), sp.cols.data() + 3 * n, 3 * n * sizeof(double));
+        memcpy(W.data(), sp.cols.data() + 6 * n, n * sizeof(double));
+        pic_species_desc d{};
+        d.q = sp.sh.q;
+        d.m = sp.sh.m;
+        d.n = n;
+        d.X = X.data();
+        d.u = U.data();
+        d.w = W.data();
+        d.momenta_at_half_step = 1;
+        c->species.emplace_back();
+        SpeciesDev& s = c->species.back();
+        st = load_species_ids(c, &d, s, h.track_ids ? sp.cols.data() + 7 * n : nullptr);
+        if (st != PIC_OK) {
+            c->species.pop_back();
+            return st;
+        }
+        s.n_loaded = sp.sh.n_loaded;
+        s.n_injected = sp.sh.n_injected;
+        s.jscale = sp.sh.jscale;   // the fixed-point unit of J, as before
+        const int escaped = (int)sp.sh.escaped;
+        GBPIC_CHECK(c, cudaMemcpy(reinterpret_cast<char*>(s.ctr) + offsetof(Counters, escaped), &escaped, sizeof(int),
+                                  cudaMemcpyHostToDevice));
+    }
+    c->step = h.step;
+    c->window_moves = h.window_moves;
+    c->gref_valid = false;
+    c->rho_prev_step = -1;
+    update_jscale(c);
     return PIC_OK;
 }
 

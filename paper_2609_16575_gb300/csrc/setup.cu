@@ -55,8 +55,8 @@ __global__ void k_keys(Geom g, const double* X, const double* w, long long n, in
 }
 
 template <typename T>
-__global__ void k_scatter(Geom g, const double* X, const double* U, const double* w, long long n, int* keypos,
-                          ParticleArrays<T> pa, int track_ids) {
+__global__ void k_scatter(Geom g, const double* X, const double* U, const double* w, const double* ids, long long n,
+                          int* keypos, ParticleArrays<T> pa, int track_ids) {
     for (long long p = blockIdx.x * (long long)blockDim.x + threadIdx.x; p < n; p += (long long)gridDim.x * blockDim.x) {
         const double Xp[3] = {X[p], X[n + p], X[2 * n + p]};
         int c[3];
@@ -70,30 +70,35 @@ __global__ void k_scatter(Geom g, const double* X, const double* U, const double
             pa.u[k][q] = (T)U[k * n + p];
         }
         pa.w[q] = (T)w[p];
-        if (track_ids) pa.id[q] = (int)p;
+        if (track_ids) pa.id[q] = ids ? (int)ids[p] : (int)p;
     }
 }
 
 static size_t align256(size_t b) { return (b + 255) & ~(size_t)255; }
 
+// ids: optional FP64 load-order ids of the particles (host or device like X), for a
+// restored state; without them particle p gets id p.
 template <typename T>
-static pic_status load_t(pic_ctx* c, const pic_species_desc* d, SpeciesDev& s) {
+static pic_status load_t(pic_ctx* c, const pic_species_desc* d, SpeciesDev& s, const double* ids_in) {
     const long long n = d->n;
     const Geom& g = c->g;
     const int ntile = g.nt[0] * g.nt[1] * g.nt[2];
     const long long nkeys = (long long)ntile * TILE_CELLS;
     // staging: device copies of the FP64 inputs
-    const double *X = d->X, *U = d->u, *W = d->w;
+    const double *X = d->X, *U = d->u, *W = d->w, *IDS = ids_in;
     double* stage = nullptr;
     if (!d->device_pointers && n > 0) {
-        stage = static_cast<double*>(dev_alloc(c, sizeof(double) * 7 * n));
+        stage = static_cast<double*>(dev_alloc(c, sizeof(double) * (ids_in ? 8 : 7) * n));
         if (!stage) return PIC_ERR_OOM;
         GBPIC_CHECK(c, cudaMemcpyAsync(stage, d->X, sizeof(double) * 3 * n, cudaMemcpyHostToDevice, c->stream));
         GBPIC_CHECK(c, cudaMemcpyAsync(stage + 3 * n, d->u, sizeof(double) * 3 * n, cudaMemcpyHostToDevice, c->stream));
         GBPIC_CHECK(c, cudaMemcpyAsync(stage + 6 * n, d->w, sizeof(double) * n, cudaMemcpyHostToDevice, c->stream));
+        if (ids_in)
+            GBPIC_CHECK(c, cudaMemcpyAsync(stage + 7 * n, ids_in, sizeof(double) * n, cudaMemcpyHostToDevice, c->stream));
         X = stage;
         U = stage + 3 * n;
         W = stage + 6 * n;
+        IDS = ids_in ? stage + 7 * n : nullptr;
     }
     int* hist = static_cast<int*>(dev_alloc(c, sizeof(int) * (nkeys + 2) + 8));
     if (!hist) return PIC_ERR_OOM;
@@ -206,7 +211,7 @@ static pic_status load_t(pic_ctx* c, const pic_species_desc* d, SpeciesDev& s) {
     GBPIC_CHECK(c, cudaMemcpyAsync(s.hist[0], h_hist.data(), sizeof(int) * nkeys, cudaMemcpyHostToDevice, c->stream));
     if (n > 0) {
         LaunchScope ls(c, KC_OTHER);
-        k_scatter<T><<<grid, 256, 0, c->stream>>>(g, X, U, W, n, hist, pa, c->desc.track_ids);
+        k_scatter<T><<<grid, 256, 0, c->stream>>>(g, X, U, W, IDS, n, hist, pa, c->desc.track_ids);
         GBPIC_CHECK(c, cudaGetLastError());
     }
     // mover and spill lists (a window move sends the first cell column of every tile to
@@ -237,7 +242,11 @@ static pic_status load_t(pic_ctx* c, const pic_species_desc* d, SpeciesDev& s) {
 }
 
 pic_status load_species_impl(pic_ctx* c, const pic_species_desc* d, SpeciesDev& s) {
-    return c->prec == PIC_FP64 ? load_t<double>(c, d, s) : load_t<float>(c, d, s);
+    return c->prec == PIC_FP64 ? load_t<double>(c, d, s, nullptr) : load_t<float>(c, d, s, nullptr);
+}
+
+pic_status load_species_ids(pic_ctx* c, const pic_species_desc* d, SpeciesDev& s, const double* ids) {
+    return c->prec == PIC_FP64 ? load_t<double>(c, d, s, ids) : load_t<float>(c, d, s, ids);
 }
 
 // ---------------------------------------------------------------------------

@@ -120,6 +120,10 @@ def lib():
             L.pic_set_current_filter.argtypes = [P, ctypes.c_int32, ctypes.c_int32]
             L.pic_set_pec.argtypes = [P, ctypes.c_int32, ctypes.c_int32]
             L.pic_set_deposit.argtypes = [P, ctypes.c_int32]
+            L.pic_save_state.argtypes = [P, ctypes.POINTER(ctypes.c_void_p), ctypes.POINTER(ctypes.c_size_t)]
+            L.pic_load_state.argtypes = [P, ctypes.c_void_p, ctypes.c_size_t]
+            L.pic_free_state.argtypes = [ctypes.c_void_p]
+            L.pic_free_state.restype = None
             L.pic_set_port.argtypes = [P, ctypes.POINTER(pic_port_desc)]
             L.pic_window_moves.argtypes = [P]
             L.pic_window_moves.restype = ctypes.c_int64
@@ -136,7 +140,8 @@ def lib():
                          "pic_get_fields", "pic_get_particles", "pic_diagnostics", "pic_get_history",
                          "pic_set_timing", "pic_kernel_times", "pic_adjoint_forward", "pic_adjoint_backward",
                          "pic_gauss_check_static", "pic_set_laser", "pic_set_moving_window",
-                         "pic_set_current_filter", "pic_set_pec", "pic_set_port", "pic_set_deposit"):
+                         "pic_set_current_filter", "pic_set_pec", "pic_set_port", "pic_set_deposit",
+                         "pic_save_state", "pic_load_state"):
                 getattr(L, name).restype = ctypes.c_int
             _lib = L
     return _lib
@@ -356,6 +361,20 @@ class Context:
         """Compensated binomial current filter (see pic_set_current_filter); 0 passes: off."""
         _check(self.ptr, lib().pic_set_current_filter(self.ptr, int(passes), int(compensate)),
                "pic_set_current_filter")
+
+    def save_state(self):
+        """The dynamical state as bytes (see pic_save_state)."""
+        blob, size = ctypes.c_void_p(), ctypes.c_size_t()
+        _check(self.ptr, lib().pic_save_state(self.ptr, ctypes.byref(blob), ctypes.byref(size)), "pic_save_state")
+        try:
+            return ctypes.string_at(blob, size.value)
+        finally:
+            lib().pic_free_state(blob)
+
+    def load_state(self, data):
+        """Restore a state from save_state into this fresh context (see pic_load_state)."""
+        buf = ctypes.create_string_buffer(bytes(data), len(data))
+        _check(self.ptr, lib().pic_load_state(self.ptr, buf, len(data)), "pic_load_state")
 
     def set_deposit(self, scheme):
         """PIC_DEPOSIT_ZIGZAG (0, default) or PIC_DEPOSIT_ESIRKEPOV (1)."""
