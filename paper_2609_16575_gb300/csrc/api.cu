@@ -10,6 +10,7 @@
 #include <cstring>
 #include <new>
 
+#include <nvtx3/nvToolsExt.h>
 #include "pic_internal.cuh"
 
 namespace gbpic {
@@ -52,14 +53,20 @@ static cudaEvent_t take_event(pic_ctx* c) {
     return e;
 }
 
+// Kernel classes as named by pic_kernel_times and by the NVTX ranges around each launch
+// (a profiler's timeline shows them; without one attached the ranges cost nothing).
+static const char* const kKernelClassNames[KC_COUNT] = {"faraday_half", "tile_push", "list_push", "append",
+                                                        "ampere",       "sort",      "other"};
+
 void timing_begin(pic_ctx* c, int cls, cudaEvent_t* a) {
-    (void)cls;
+    nvtxRangePushA(kKernelClassNames[cls]);
     if (!c->timing) return;
     *a = take_event(c);
     cudaEventRecord(*a, c->stream);
 }
 
 void timing_end(pic_ctx* c, int cls, cudaEvent_t a) {
+    nvtxRangePop();
     if (!c->timing || !a) return;
     cudaEvent_t b = take_event(c);
     cudaEventRecord(b, c->stream);
@@ -786,8 +793,7 @@ pic_status pic_set_timing(pic_ctx* c, int32_t enable) {
 }
 
 pic_status pic_kernel_times(pic_ctx* c, int32_t max, const char** names, int64_t* launches, double* ms, int32_t* count) {
-    static const char* kNames[KC_COUNT] = {"faraday_half", "tile_push", "list_push", "append", "ampere", "sort",
-                                           "other"};
+    const char* const* kNames = kKernelClassNames;
     if (!c || !count) return PIC_ERR_ARG;
     GBPIC_CHECK(c, cudaStreamSynchronize(c->stream));
     for (auto& p : c->pending) {

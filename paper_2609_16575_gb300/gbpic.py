@@ -13,6 +13,7 @@ no CPU fallback.
 from __future__ import annotations
 
 import ctypes
+import math
 import os
 import threading
 
@@ -321,6 +322,18 @@ class Context:
         d = pic_diag()
         _check(self.ptr, lib().pic_diagnostics(self.ptr, ctypes.byref(d)), "pic_diagnostics")
         return d.as_dict()
+
+    def log_diagnostics(self, path, **extra):
+        """Append the current diagnostics (and any extra keys) to a JSON-lines file; returns
+        the record."""
+        import json
+        import time
+
+        rec = dict(self.diagnostics(), wall_time=time.time(), **extra)
+        with open(path, "a") as f:
+            f.write(json.dumps({k: (v if not isinstance(v, float) or math.isfinite(v) else None)
+                                for k, v in rec.items()}) + "\n")
+        return rec
 
     def history(self, max_records=1 << 16):
         cnt = ctypes.c_int32()

@@ -116,3 +116,21 @@ def test_state_argument_checks():
     assert fresh.diagnostics()["n_alive"] == a.diagnostics()["n_alive"]
     a.close()
     fresh.close()
+
+
+def test_diagnostics_log(tmp_path):
+    """The JSON-lines log: one record per call, non-finite values written as null."""
+    import json
+
+    wl = W.thermal((16, 8, 8), 0.2, 2, 0.1, seed=133)
+    a = _new(wl, FP32)
+    _load(a, wl, FP32)
+    path = tmp_path / "diag.jsonl"
+    a.log_diagnostics(path, run="t")
+    a.step(1)
+    a.log_diagnostics(path, run="t")
+    recs = [json.loads(line) for line in open(path)]
+    assert [r["step"] for r in recs] == [0, 1]
+    assert recs[0]["cont_max"] is None and recs[1]["cont_max"] is not None
+    assert recs[1]["n_alive"] == wl.species[0].P.shape[1] and recs[1]["run"] == "t"
+    a.close()
