@@ -260,8 +260,9 @@ template <> struct RowCells<2> {
 
 // Esirkepov's deposit of the cell crossers of one particle step (warp-collective): the
 // record queue is drained, each crosser writes its record there (positions relative to
-// the first node of its 3x3x3 support, cw, the support's first node packed), and the 32
-// lanes share the 54 stencil values of every record (see esk_value).
+// the first node of its support, cw, the first node and the crossed dimensions packed),
+// and the 32 lanes share the non-zero stencil values of each record in turn (20 of the
+// 3x3x3 support's 54 for a move across one face; see esk_value).
 constexpr int ESK_WORDS = 10;   // X1[3], X2[3], cw[3], packed first node
 static_assert(32 * ESK_WORDS <= QWORDS, "the crossers' records fit in the record queue");
 template <typename T>
@@ -279,27 +280,51 @@ __device__ __forceinline__ void esk_crossers(WarpQueue<T> Q, int& qn, int lane, 
             rec[3 + k] = d2[k] + T(s[k] - b[k]);
             rec[6 + k] = cw[k];
         }
-        // first node of the support, local -1 .. 7 per dimension, packed in 4 bits each
-        *reinterpret_cast<int*>(rec + 9) = (x + b[0] + 1) | ((y + b[1] + 1) << 4) | ((z + b[2] + 1) << 8);
+        // first node of the support (local -1 .. 7 per dimension, 4 bits each) and which
+        // dimensions the move crossed (one bit each)
+        *reinterpret_cast<int*>(rec + 9) = (x + b[0] + 1) | ((y + b[1] + 1) << 4) | ((z + b[2] + 1) << 8) |
+                                           ((s[0] != 0) << 12) | ((s[1] != 0) << 13) | ((s[2] != 0) << 14);
     }
     __syncwarp();
+    // only the support's non-zero part: along a dimension the move did not cross, the
+    // third node carries no weight and the second edge no current
     const int m = __popc(mc);
-    for (int it = lane; it < m * 54; it += 32) {
-        const int r = it / 54, q = it - 54 * r;
-        const int comp = q / 18, rem = q - 18 * comp;
-        const int i = rem / 9, jp = (rem - 9 * i) / 3, jr = rem - 9 * i - 3 * jp;
+    for (int r = 0; r < m; ++r) {
         const T* rec = Q.rec + r * ESK_WORDS;
-        const T X1[3] = {rec[0], rec[1], rec[2]}, X2[3] = {rec[3], rec[4], rec[5]}, c3w[3] = {rec[6], rec[7], rec[8]};
-        const T v = esk_value(X1, X2, c3w, comp, i, jp, jr);
-        if (v == T(0)) continue;
         const int pk = *reinterpret_cast<const int*>(rec + 9);
+        const int cx = (pk >> 12) & 1, cy = (pk >> 13) & 1, cz = (pk >> 14) & 1;
+        // values of component c: (1 + crossed_c) edges x (2 + crossed_p) x (2 + crossed_r) nodes
+        const int n0 = (1 + cx) * (2 + cy) * (2 + cz), n1 = (1 + cy) * (2 + cz) * (2 + cx);
+        const int n2 = (1 + cz) * (2 + cx) * (2 + cy);
+        for (int t = lane; t < n0 + n1 + n2; t += 32) {
+            int comp, q;
+            if (t < n0) {
+                comp = 0;
+                q = t;
+            } else if (t < n0 + n1) {
+                comp = 1;
+                q = t - n0;
+            } else {
+                comp = 2;
+                q = t - n0 - n1;
+            }
+            const int cc = comp == 0 ? cx : (comp == 1 ? cy : cz);
+            const int cp = comp == 0 ? cy : (comp == 1 ? cz : cx);   // the next dimension, cyclic
+            const int np_ = 2 + cp, nr = 2 + (comp == 0 ? cz : (comp == 1 ? cx : cy));
+            (void)cc;
+            const int i = q / (np_ * nr), rem = q - i * np_ * nr;
+            const int jp = rem / nr, jr = rem - jp * nr;
+            const T X1[3] = {rec[0], rec[1], rec[2]}, X2[3] = {rec[3], rec[4], rec[5]}, c3w[3] = {rec[6], rec[7], rec[8]};
+            const T v = esk_value(X1, X2, c3w, comp, i, jp, jr);
+            if (v == T(0)) continue;
         // the value's location: edge i along comp, node jp along the next dimension and
         // jr along the one after (cyclic), from the support's first node
-        const int ax = comp == 0 ? i : (comp == 2 ? jp : jr);
-        const int ay = comp == 1 ? i : (comp == 0 ? jp : jr);
-        const int az = comp == 2 ? i : (comp == 1 ? jp : jr);
-        tile_add(sJa, tile_index(comp, (pk & 15) - 1 + ax, ((pk >> 4) & 15) - 1 + ay, ((pk >> 8) & 15) - 1 + az),
-                 JT_ELEMS, v);
+            const int ax = comp == 0 ? i : (comp == 2 ? jp : jr);
+            const int ay = comp == 1 ? i : (comp == 0 ? jp : jr);
+            const int az = comp == 2 ? i : (comp == 1 ? jp : jr);
+            tile_add(sJa, tile_index(comp, (pk & 15) - 1 + ax, ((pk >> 4) & 15) - 1 + ay, ((pk >> 8) & 15) - 1 + az),
+                     JT_ELEMS, v);
+        }
     }
     __syncwarp();
 }
