@@ -6,6 +6,7 @@
 //                 (leaving holes) and flushes J to HBM with integer atomics.
 //   k_list_push   the same step for particles held in the spill list (global-memory
 //                 gather and deposit).
+//   k_inject      the moving window's new plasma, into the mover list.
 //   k_append      puts movers into the segment of their new tile (or the spill list).
 #include <cuda/std/cstdint>
 
@@ -308,17 +309,15 @@ __device__ __forceinline__ void esk_crossers(WarpQueue<T> Q, int& qn, int lane, 
                 comp = 2;
                 q = t - n0 - n1;
             }
-            const int cc = comp == 0 ? cx : (comp == 1 ? cy : cz);
             const int cp = comp == 0 ? cy : (comp == 1 ? cz : cx);   // the next dimension, cyclic
             const int np_ = 2 + cp, nr = 2 + (comp == 0 ? cz : (comp == 1 ? cx : cy));
-            (void)cc;
             const int i = q / (np_ * nr), rem = q - i * np_ * nr;
             const int jp = rem / nr, jr = rem - jp * nr;
             const T X1[3] = {rec[0], rec[1], rec[2]}, X2[3] = {rec[3], rec[4], rec[5]}, c3w[3] = {rec[6], rec[7], rec[8]};
             const T v = esk_value(X1, X2, c3w, comp, i, jp, jr);
             if (v == T(0)) continue;
-        // the value's location: edge i along comp, node jp along the next dimension and
-        // jr along the one after (cyclic), from the support's first node
+            // the value's location: edge i along comp, node jp along the next dimension
+            // and jr along the one after (cyclic), from the support's first node
             const int ax = comp == 0 ? i : (comp == 2 ? jp : jr);
             const int ay = comp == 1 ? i : (comp == 0 ? jp : jr);
             const int az = comp == 2 ? i : (comp == 1 ? jp : jr);
