@@ -116,3 +116,45 @@ def test_diagnostics_match_oracle_sums():
     rho = oracle.rho(wl.n, wl.d, osp, wl.rho_ion)
     G = oracle.divergence(wl.n, wl.d, F[0:3]) - rho
     assert abs(d["gauss_max"] / np.abs(G).max() - 1) < 1e-10
+
+
+@pytest.mark.parametrize("prec", [FP32, FP64])
+def test_div_b_stays_zero(prec):
+    """Faraday's law keeps div B at its initial value (zero here) on the GPU: a hot plasma
+    under a divergence-free plane-wave B, 40 cycles."""
+    from pic_runs import plane_wave_fields
+
+    wl = W.thermal((16, 16, 8), 0.2, 4, 0.3, seed=141)
+    wl.E, wl.B = plane_wave_fields(wl.n, wl.d, wl.dt)
+    ctx = run_gpu(wl, prec, 40)
+    E, B, _ = ctx.get_fields()
+    div = oracle.divergence_b(wl.n, wl.d, B)
+    scale = np.abs(B).max() / min(wl.d)
+    assert np.abs(div).max() <= (1e-5 if prec == FP32 else 1e-13) * scale, np.abs(div).max() / scale
+    assert np.abs(B).max() > 1e-3
+    ctx.close()
+
+
+def test_wakefield_plausible():
+    """Plausibility of the laser wakefield (section 4: the peak accelerating field is
+    about the cold wave-breaking field E_wb = omega_p m c / e): a short a0 = 2 pulse into
+    n = 0.01 n_c with a moving window; the largest longitudinal field behind the pulse
+    on the axis is of order E_wb = 0.1 (laser units)."""
+    wl = W.lwfa(n=(256, 64, 64), ppc_per_dim=1, density=0.01, x0=20, ramp=20, a0=2.0, w0_lambda=2.0,
+                fwhm_periods=4.0, plane=2, window_start=700)
+    from paper_2609_16575_gb300 import gbpic
+
+    ctx = gbpic.Context(wl.n, wl.d, wl.dt, precision=FP32, rho_ion=0.0, bc_x=1)
+    ctx.set_laser(*wl.laser.as_tuple())
+    ctx.set_moving_window(*wl.window.as_tuple())
+    s = wl.species[0]
+    ctx.load_species_array(s.q, s.m, s.P, s.momenta_at_half_step)
+    ctx.step(1400)
+    E, _, _ = ctx.get_fields()
+    ey = np.abs(E[1, 32, 32, :])
+    front = int(np.argmax(ey))                          # the pulse
+    ex = E[0, 32, 32, :max(front - 40, 1)]              # behind it
+    e_wb = np.sqrt(0.01)
+    assert ctx.window_moves() > 100
+    assert 0.2 * e_wb < np.abs(ex).max() < 3.0 * e_wb, np.abs(ex).max() / e_wb
+    ctx.close()
