@@ -509,7 +509,26 @@ pic_status pic_set_port(pic_ctx* c, const pic_port_desc* p) {
 // Checkpoint / resume: the dynamical state as a host byte blob.
 
 
+static pic_status save_state_impl(pic_ctx* c, void** blob, size_t* bytes);
+static pic_status load_state_impl(pic_ctx* c, const void* blob, size_t bytes);
+
 pic_status pic_save_state(pic_ctx* c, void** blob, size_t* bytes) {
+    try {
+        return save_state_impl(c, blob, bytes);
+    } catch (const std::bad_alloc&) {
+        return PIC_ERR_OOM;   // host memory for the blob
+    }
+}
+
+pic_status pic_load_state(pic_ctx* c, const void* blob, size_t bytes) {
+    try {
+        return load_state_impl(c, blob, bytes);
+    } catch (const std::bad_alloc&) {
+        return PIC_ERR_OOM;
+    }
+}
+
+static pic_status save_state_impl(pic_ctx* c, void** blob, size_t* bytes) {
     if (!c || !blob || !bytes) return PIC_ERR_ARG;
     *blob = nullptr;
     *bytes = 0;
@@ -576,7 +595,7 @@ pic_status pic_save_state(pic_ctx* c, void** blob, size_t* bytes) {
 
 void pic_free_state(void* blob) { std::free(blob); }
 
-pic_status pic_load_state(pic_ctx* c, const void* blob, size_t bytes) {
+static pic_status load_state_impl(pic_ctx* c, const void* blob, size_t bytes) {
     if (!c || !blob || bytes < sizeof(StateHeader)) return PIC_ERR_ARG;
     StateHeader h;
     memcpy(&h, blob, sizeof(h));
@@ -603,12 +622,20 @@ pic_status pic_load_state(pic_ctx* c, const void* blob, size_t bytes) {
         SpeciesHeader sh;
         std::vector<double> cols;   // 7 rows (+ ids)
     };
-    std::vector<Sp> sps(h.nspecies < 0 ? 0 : h.nspecies);
+    // counts bounded by what the blob can hold before any allocation or size arithmetic
+    if (h.nspecies < 0 || (size_t)h.nspecies > bytes / sizeof(SpeciesHeader)) {
+        c->err = "pic_load_state: malformed state";
+        return PIC_ERR_ARG;
+    }
+    std::vector<Sp> sps(h.nspecies);
     for (auto& sp : sps) {
         const unsigned char* q = take(sizeof(SpeciesHeader));
         if (!q) return PIC_ERR_ARG;
         memcpy(&sp.sh, q, sizeof(SpeciesHeader));
-        if (sp.sh.rows < 0) return PIC_ERR_ARG;
+        if (sp.sh.rows < 0 || (uint64_t)sp.sh.rows > bytes / (7 * sizeof(double))) {
+            c->err = "pic_load_state: malformed state";
+            return PIC_ERR_ARG;
+        }
         const size_t nv = (size_t)sp.sh.rows * (h.track_ids ? 8 : 7);
         q = take(nv * sizeof(double));
         if (!q) return PIC_ERR_ARG;

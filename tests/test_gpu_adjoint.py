@@ -93,7 +93,7 @@ def test_autograd_function():
     L = autodiff.field_energy(u, A, setup)
     gu, gA = torch.autograd.grad(L, [u, A])
     L2, dA, du, _ = _gpu_loss(wl, P, 0.05, E_dir, B_dir, 12, 5)
-    assert abs(float(L) - L2) <= 1e-13 * abs(L2)
+    assert abs(float(L.detach()) - L2) <= 1e-13 * abs(L2)
     assert np.abs(gu.numpy() - du).max() <= 1e-13 * np.abs(du).max()
     assert abs(float(gA) - dA) <= 1e-13 * abs(dA)
 
