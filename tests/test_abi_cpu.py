@@ -76,3 +76,22 @@ def test_no_device_is_reported_not_faked(L):
     ok = _desc(gbpic)
     assert L.pic_init_grid(ctypes.byref(ok), ctypes.byref(out)) == 10
     assert not out.value
+
+
+def test_new_entry_points_reject_a_null_context(L):
+    """Every setter and the checkpoint calls return PIC_ERR_ARG for a null context (no
+    device needed); pic_window_moves reads 0 and pic_free_state accepts NULL."""
+    from paper_2609_16575_gb300 import gbpic
+
+    assert L.pic_set_moving_window(None, None) == 1
+    assert L.pic_window_moves(None) == 0
+    assert L.pic_set_current_filter(None, 1, 1) == 1
+    assert L.pic_set_pec(None, 1, 0) == 1
+    assert L.pic_set_port(None, None) == 1
+    assert L.pic_set_deposit(None, 1) == 1
+    blob, size = ctypes.c_void_p(), ctypes.c_size_t()
+    assert L.pic_save_state(None, ctypes.byref(blob), ctypes.byref(size)) == 1
+    assert L.pic_load_state(None, None, 0) == 1
+    L.pic_free_state(None)
+    # the binding mirrors the enumerations of the header
+    assert (gbpic.PIC_DEPOSIT_ZIGZAG, gbpic.PIC_DEPOSIT_ESIRKEPOV) == (0, 1)
