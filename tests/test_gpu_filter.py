@@ -1,5 +1,5 @@
 """GPU parity of the compensated binomial current filter (section 2.2 "compensated
-smoothing", section 2.6 current filtering; the scheme is this build's reading) against
+smoothing", section 2.6 current filtering; the scheme is a reading of those passages) against
 the FP64 oracle, on a periodic thermal plasma and on the open-x laser wakefield with a
 moving window."""
 import math
