@@ -138,3 +138,26 @@ def test_window_plasma_order_and_weights():
                                rtol=1e-15)
     assert np.allclose(P[2, :4], [0.25, 0.25, 0.75, 0.75])   # z offset before y cell changes
     assert np.allclose(P[1, 4:8], [1.5, 1.5, 1.5, 1.5])
+
+
+def test_lwfa_window_continues_the_loaded_plasma():
+    """The laser-wakefield workload's window brings in exactly the plasma that its loader
+    puts in the same absolute cells of a longer box (lattice, ramp and weights), and moves
+    no faster than light."""
+    from paper_2609_16575_gb300 import workloads as W
+
+    n = (24, 4, 4)                                     # new columns at x = 24 .. 62 cross the ramp 20 .. 50
+    kw = dict(ppc_per_dim=2, density=0.01, x0=20, ramp=30)
+    wl = W.lwfa(n=n, window_start=0, **kw)
+    win = wl.window.as_dict()
+    assert win["every"] * wl.dt >= wl.d[0]
+    long_box = W.lwfa(n=(n[0] + 40, n[1], n[2]), **kw).species[0].P
+    for origin in (1, 13, 27, 39):
+        new = oracle.window_plasma(n, wl.d, win, origin)
+        col = origin + n[0] - 1                        # the new column's absolute x
+        ref = long_box[:, (long_box[0] >= col) & (long_box[0] < col + 1)].copy()
+        ref[0] -= origin                               # into window coordinates
+        a = new[:, np.lexsort(new[::-1])]
+        b = ref[:, np.lexsort(ref[::-1])]
+        assert a.shape == b.shape, (origin, a.shape, b.shape)
+        np.testing.assert_array_equal(a, b)
