@@ -207,6 +207,12 @@ pic_status pic_set_laser(pic_ctx* ctx, const pic_laser_desc* laser);
  * out-of-range values.  NULL switches the window off (before stepping only). */
 pic_status pic_set_moving_window(pic_ctx* ctx, const pic_window_desc* window);
 
+/* Set the uniform immobile background charge density rho_ion (the value of the grid
+ * description; diagnostics only: it enters the Gauss residual and rho_max).  The Gauss
+ * reference of gauss_change_max is taken again at the next pic_diagnostics.
+ * PIC_ERR_ARG for a non-finite value. */
+pic_status pic_set_background(pic_ctx* ctx, double rho_ion);
+
 /* Moves of the window so far (0 without a window). */
 int64_t pic_window_moves(const pic_ctx* ctx);
 
@@ -323,6 +329,12 @@ pic_status pic_kernel_times(pic_ctx* ctx, int32_t max, const char** names, int64
 pic_status pic_adjoint_forward(pic_ctx* ctx, int32_t nsteps, int32_t ckpt_every, double* loss);
 pic_status pic_adjoint_backward(pic_ctx* ctx, const double* E_dir, const double* B_dir, double* dL_dA,
                                 double* const* dL_du, int32_t device_pointers);
+
+/* pic_adjoint_forward followed by pic_adjoint_backward in one call: the loss and its
+ * gradients for the next nsteps cycles from the current state (same arguments and
+ * errors as the two calls). */
+pic_status pic_adjoint_run(pic_ctx* ctx, int32_t nsteps, int32_t ckpt_every, const double* E_dir, const double* B_dir,
+                           double* loss, double* dL_dA, double* const* dL_du, int32_t device_pointers);
 
 /* Allocation-free Gauss check.  The paper has no counterpart: this entry point exists
  * for callers that cannot allocate device memory, e.g. an application whose memory

@@ -703,6 +703,13 @@ pic_status pic_adjoint_backward(pic_ctx* c, const double* E_dir, const double* B
     return pic_sync(c);
 }
 
+pic_status pic_adjoint_run(pic_ctx* c, int32_t nsteps, int32_t ckpt_every, const double* E_dir, const double* B_dir,
+                           double* loss, double* dL_dA, double* const* dL_du, int32_t device_pointers) {
+    pic_status st = pic_adjoint_forward(c, nsteps, ckpt_every, loss);
+    if (st != PIC_OK) return st;
+    return pic_adjoint_backward(c, E_dir, B_dir, dL_dA, dL_du, device_pointers);
+}
+
 }  // extern "C"
 
 namespace gbpic {

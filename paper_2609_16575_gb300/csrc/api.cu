@@ -474,6 +474,13 @@ pic_status pic_set_moving_window(pic_ctx* c, const pic_window_desc* w) {
 
 int64_t pic_window_moves(const pic_ctx* c) { return c ? c->window_moves : 0; }
 
+pic_status pic_set_background(pic_ctx* c, double rho_ion) {
+    if (!c || !std::isfinite(rho_ion)) return PIC_ERR_ARG;
+    c->desc.rho_ion = rho_ion;
+    c->gref_valid = false;   // the Gauss reference includes the background
+    return PIC_OK;
+}
+
 pic_status pic_set_pec(pic_ctx* c, int32_t pec_y, int32_t pec_z) {
     if (!c) return PIC_ERR_ARG;
     if ((pec_y != 0 && pec_y != 1) || (pec_z != 0 && pec_z != 1)) return PIC_ERR_ARG;

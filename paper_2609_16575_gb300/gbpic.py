@@ -120,6 +120,10 @@ def lib():
             L.pic_set_moving_window.argtypes = [P, ctypes.POINTER(pic_window_desc)]
             L.pic_set_current_filter.argtypes = [P, ctypes.c_int32, ctypes.c_int32]
             L.pic_set_pec.argtypes = [P, ctypes.c_int32, ctypes.c_int32]
+            L.pic_set_background.argtypes = [P, ctypes.c_double]
+            L.pic_adjoint_run.argtypes = [P, ctypes.c_int32, ctypes.c_int32, P, P, ctypes.POINTER(ctypes.c_double),
+                                          ctypes.POINTER(ctypes.c_double), ctypes.POINTER(ctypes.c_void_p),
+                                          ctypes.c_int32]
             L.pic_set_deposit.argtypes = [P, ctypes.c_int32]
             L.pic_save_state.argtypes = [P, ctypes.POINTER(ctypes.c_void_p), ctypes.POINTER(ctypes.c_size_t)]
             L.pic_load_state.argtypes = [P, ctypes.c_void_p, ctypes.c_size_t]
@@ -142,7 +146,7 @@ def lib():
                          "pic_set_timing", "pic_kernel_times", "pic_adjoint_forward", "pic_adjoint_backward",
                          "pic_gauss_check_static", "pic_set_laser", "pic_set_moving_window",
                          "pic_set_current_filter", "pic_set_pec", "pic_set_port", "pic_set_deposit",
-                         "pic_save_state", "pic_load_state"):
+                         "pic_save_state", "pic_load_state", "pic_set_background", "pic_adjoint_run"):
                 getattr(L, name).restype = ctypes.c_int
             _lib = L
     return _lib
@@ -393,6 +397,10 @@ class Context:
         """PIC_DEPOSIT_ZIGZAG (0, default) or PIC_DEPOSIT_ESIRKEPOV (1)."""
         _check(self.ptr, lib().pic_set_deposit(self.ptr, int(scheme)), "pic_set_deposit")
 
+    def set_background(self, rho_ion):
+        """Uniform immobile background charge density (diagnostics only)."""
+        _check(self.ptr, lib().pic_set_background(self.ptr, float(rho_ion)), "pic_set_background")
+
     def set_pec(self, pec_y, pec_z):
         """Conducting wall planes y = 0 / z = 0 (see pic_set_pec); fields only."""
         _check(self.ptr, lib().pic_set_pec(self.ptr, int(pec_y), int(pec_z)), "pic_set_pec")
@@ -430,3 +438,14 @@ class Context:
         _check(self.ptr, lib().pic_adjoint_backward(self.ptr, pe, pb, ctypes.byref(dA), ptrs, 0),
                "pic_adjoint_backward")
         return dA.value, outs
+
+    def adjoint_run(self, nsteps, ckpt_every, E_dir=None, B_dir=None):
+        """Forward and backward in one call: (loss, dL/dA, [dL/du^{-1/2} per species])."""
+        outs = [np.zeros((3, n)) for n in self.species_n]
+        ptrs = (ctypes.c_void_p * max(len(outs), 1))(*[o.ctypes.data for o in outs])
+        loss, dA = ctypes.c_double(), ctypes.c_double()
+        pe, _ = _ptr(E_dir)
+        pb, _ = _ptr(B_dir)
+        _check(self.ptr, lib().pic_adjoint_run(self.ptr, int(nsteps), int(ckpt_every), pe, pb, ctypes.byref(loss),
+                                               ctypes.byref(dA), ptrs, 0), "pic_adjoint_run")
+        return loss.value, dA.value, outs

@@ -116,3 +116,38 @@ def test_fp32_adjoint_against_fp64():
     assert abs(L32 - L64) <= 1e-5 * abs(L64)
     assert abs(dA32 - dA64) <= 1e-3 * abs(dA64), (dA32, dA64)
     assert np.abs(du32 - du64).max() <= 1e-3 * np.abs(du64).max(), np.abs(du32 - du64).max() / np.abs(du64).max()
+
+
+def test_adjoint_run_is_forward_then_backward():
+    """pic_adjoint_run gives the loss and gradients of forward + backward."""
+    from paper_2609_16575_gb300 import gbpic
+
+    wl = W.thermal((4, 4, 4), 0.2, 2, 0.2, seed=35)
+    E_dir, B_dir = plane_wave_fields(wl.n, wl.d, wl.dt, amplitude=1.0)
+    A = 0.05
+    P = wl.species[0].P
+    L, dA, du, _ = _gpu_loss(wl, P, A, E_dir, B_dir, 12, 5)
+    ctx = gbpic.Context(wl.n, wl.d, wl.dt, precision=gbpic.PIC_FP64, track_ids=True)
+    ctx.set_fields(A * E_dir, A * B_dir)
+    ctx.load_species_array(-1.0, 1.0, P)
+    L2, dA2, du2 = ctx.adjoint_run(12, 5, E_dir, B_dir)
+    ctx.close()
+    assert L2 == pytest.approx(L, rel=1e-14)
+    assert dA2 == pytest.approx(dA, rel=1e-12)
+    assert np.abs(du2[0] - du).max() <= 1e-12 * np.abs(du).max()
+
+
+def test_background_enters_the_gauss_residual():
+    """pic_set_background changes rho_max by the background, as a uniform charge does."""
+    from paper_2609_16575_gb300 import gbpic
+
+    wl = W.thermal((8, 8, 8), 0.2, 2, 0.1, seed=36)
+    ctx = gbpic.Context(wl.n, wl.d, wl.dt, precision=gbpic.PIC_FP64, rho_ion=0.0)
+    ctx.load_species_array(-1.0, 1.0, wl.species[0].P)
+    r0 = ctx.diagnostics()["rho_max"]
+    ctx.set_background(1.0)
+    d1 = ctx.diagnostics()
+    assert d1["rho_max"] < r0            # the ions neutralise the electrons' charge
+    with pytest.raises(gbpic.PicError):
+        ctx.set_background(float("nan"))
+    ctx.close()
