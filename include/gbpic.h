@@ -158,6 +158,12 @@ typedef struct pic_species_desc {
                                       backward Boris half step with E^0, B^0 (section 2.4) */
     int32_t device_pointers;       /* 1: X, u, w are device pointers */
     double capacity_slack;         /* tile segment headroom fraction; 0 -> 0.25 */
+    int64_t mover_capacity;        /* records of the list of particles changing tile in one step;
+                                      0 -> max(n / 4, 65536) (a quarter of the slots with a
+                                      moving window).  A step with more movers loses particles
+                                      and reports PIC_ERR_TILE_OVERFLOW */
+    int64_t spill_capacity;        /* records of the list of movers whose tile segment is full;
+                                      0 -> max(n / 16, 65536); overflow as above */
 } pic_species_desc;
 
 typedef struct pic_diag {
@@ -174,6 +180,8 @@ typedef struct pic_diag {
                                 previous pic_diagnostics call was exactly one step earlier and the
                                 window did not move in between, else NaN */
     double J_max;            /* max |J^{n-1/2}| over components and cells */
+                             /* (the maxima report +inf when a value they range over is not
+                                finite, so a run that blew up cannot show a small residual) */
     int64_t n_alive;         /* particles held, all species */
     int64_t n_spilled;       /* particles currently outside their tile segment (spill list) */
     int64_t n_escaped;       /* particles removed through the open x faces or by the window so far */
@@ -307,6 +315,16 @@ pic_status pic_set_timing(pic_ctx* ctx, int32_t enable);
 pic_status pic_kernel_times(pic_ctx* ctx, int32_t max, const char** names, int64_t* launches, double* ms,
                             int32_t* count);
 
+/* Bound on the tile kernel's wait for its TMA-staged field boxes, in polls of the
+ * mbarrier (each poll may suspend the thread for a short, hardware-defined time).  The
+ * default (a negative value restores it) is 2^24 polls; 0 gives up without waiting.  A
+ * tile whose wait gives up still waits (bounded) for its copies in flight, then drops its
+ * particles; the next synchronising call returns PIC_ERR_TIMEOUT and the context's state
+ * is no longer valid (destroy it).  The bound exists so that a stalled copy becomes an
+ * error status instead of a hung device, and so that this path can be exercised; it
+ * applies to every tile kernel launched after the call.  PIC_ERR_ARG for a null ctx. */
+pic_status pic_set_wait_limit(pic_ctx* ctx, int32_t polls);
+
 /* Differentiation: a hand-written discrete adjoint of the cycle of section 2.2.
  * The loss is the field energy of the final state, L = U_E + U_B at time level N
  * (E^N and B^N of Eq. (21)), as in pic_diagnostics.
@@ -346,10 +364,11 @@ pic_status pic_adjoint_run(pic_ctx* ctx, int32_t nsteps, int32_t ckpt_every, con
  * static device array of the library instead of memory it allocates:
  *   - at most 1,048,576 cells (2^20, e.g. 128 x 128 x 64); a larger grid returns
  *     PIC_ERR_ARG with the reason in pic_last_error;
- *   - the array (8 MB) is held by every GPU that loads the library until the process
- *     exits; the first call on a device looks up the array's device address
- *     (cudaGetSymbolAddress, with that device current): make that first call before
- *     any stream capture;
+ *   - the array (8 MB) is held until the process exits by every GPU on which a
+ *     context was created: pic_init_grid looks up its device address
+ *     (cudaGetSymbolAddress, with that device current), which loads the library's
+ *     module there and commits the array, so this entry point itself triggers no
+ *     module load; called for a device without a context it returns PIC_ERR_STATE;
  *   - all calls share the array and it keeps the last call's contents; each call
  *     clears what it uses, but calls whose work overlaps on the GPU race on it.
  * It calls no cudaMalloc or cudaFree and allocates nothing through the context's

@@ -652,7 +652,7 @@ pic_status pic_adjoint_forward(pic_ctx* c, int32_t nsteps, int32_t ckpt_every, d
                  "and the ZigZag deposit";
         return PIC_ERR_STATE;
     }
-    cudaSetDevice(c->desc.device);
+    DeviceScope dscope_(c->desc.device);
     adjoint_release(c);
     AdjointState* S = new AdjointState();
     c->adj = S;
@@ -696,7 +696,7 @@ pic_status pic_adjoint_backward(pic_ctx* c, const double* E_dir, const double* B
         c->err = "pic_adjoint_backward needs a preceding pic_adjoint_forward";
         return PIC_ERR_STATE;
     }
-    cudaSetDevice(c->desc.device);
+    DeviceScope dscope_(c->desc.device);
     pic_status st = c->prec == PIC_FP64 ? backward_t<double>(c, *S, E_dir, B_dir, dL_dA, dL_du, device_pointers)
                                         : backward_t<float>(c, *S, E_dir, B_dir, dL_dA, dL_du, device_pointers);
     if (st != PIC_OK) return st;

@@ -268,7 +268,8 @@ pic_status pic_init_grid(const pic_grid_desc* desc, pic_ctx** out) {
     cudaDeviceProp prop;
     if (cudaGetDeviceProperties(&prop, desc->device) != cudaSuccess || prop.major * 10 + prop.minor != 103)
         return PIC_ERR_NO_DEVICE;
-    if (cudaSetDevice(desc->device) != cudaSuccess) return PIC_ERR_NO_DEVICE;
+    DeviceScope dscope_(desc->device);
+    if (!dscope_.ok) return PIC_ERR_NO_DEVICE;
 
     pic_ctx* c = new (std::nothrow) pic_ctx();
     if (!c) return PIC_ERR_OOM;
@@ -324,6 +325,7 @@ pic_status pic_init_grid(const pic_grid_desc* desc, pic_ctx** out) {
         cudaMemsetAsync(c->hist, 0, sizeof(double) * 3 * (size_t)c->hist_cap, c->stream);
     }
     pic_status st = make_tensor_maps(c);
+    if (st == PIC_OK) st = static_scratch_prepare(c);
     if (st != PIC_OK) {
         std::fprintf(stderr, "gbpic: %s\n", c->err.c_str());
         pic_destroy(c);
@@ -341,7 +343,7 @@ pic_status pic_init_grid(const pic_grid_desc* desc, pic_ctx** out) {
 
 pic_status pic_set_fields(pic_ctx* c, const double* E, const double* B, int32_t device_pointers) {
     if (!c) return PIC_ERR_ARG;
-    cudaSetDevice(c->desc.device);
+    DeviceScope dscope_(c->desc.device);
     const size_t nb = sizeof(double) * 3 * (size_t)c->g.host_N();
     const double *dE = E, *dB = B;
     double* stage = nullptr;
@@ -365,11 +367,12 @@ pic_status pic_set_fields(pic_ctx* c, const double* E, const double* B, int32_t 
 pic_status pic_load_species(pic_ctx* c, const pic_species_desc* d, int32_t* species_id) {
     if (!c || !d) return PIC_ERR_ARG;
     if (d->n < 0 || (d->n > 0 && (!d->X || !d->u || !d->w)) || !(d->m > 0) || !std::isfinite(d->q)) return PIC_ERR_ARG;
+    if (d->mover_capacity < 0 || d->spill_capacity < 0) return PIC_ERR_ARG;
     if (c->pec_y || c->pec_z) {
         c->err = "pic_load_species: the conducting walls act on the fields only";
         return PIC_ERR_STATE;
     }
-    cudaSetDevice(c->desc.device);
+    DeviceScope dscope_(c->desc.device);
     c->species.emplace_back();
     SpeciesDev& s = c->species.back();
     pic_status st = load_species_impl(c, d, s);
@@ -394,7 +397,7 @@ pic_status pic_step(pic_ctx* c, int32_t nsteps) {
         c->err = "pic_step: the moving window's species is not loaded";
         return PIC_ERR_STATE;
     }
-    cudaSetDevice(c->desc.device);
+    DeviceScope dscope_(c->desc.device);
     update_jscale(c);
     if (c->j_dirty) {
         for (int k = 0; k < 3; ++k)
@@ -520,6 +523,8 @@ static pic_status save_state_impl(pic_ctx* c, void** blob, size_t* bytes);
 static pic_status load_state_impl(pic_ctx* c, const void* blob, size_t bytes);
 
 pic_status pic_save_state(pic_ctx* c, void** blob, size_t* bytes) {
+    if (!c) return PIC_ERR_ARG;
+    DeviceScope dscope_(c->desc.device);
     try {
         return save_state_impl(c, blob, bytes);
     } catch (const std::bad_alloc&) {
@@ -528,6 +533,8 @@ pic_status pic_save_state(pic_ctx* c, void** blob, size_t* bytes) {
 }
 
 pic_status pic_load_state(pic_ctx* c, const void* blob, size_t bytes) {
+    if (!c) return PIC_ERR_ARG;
+    DeviceScope dscope_(c->desc.device);
     try {
         return load_state_impl(c, blob, bytes);
     } catch (const std::bad_alloc&) {
@@ -661,7 +668,7 @@ static pic_status load_state_impl(pic_ctx* c, const void* blob, size_t bytes) {
     memcpy(B.data(), qb, B.size() * sizeof(double));
     pic_status st = pic_set_fields(c, E.data(), B.data(), 0);
     if (st != PIC_OK) return st;
-    cudaSetDevice(c->desc.device);
+    DeviceScope dscope_(c->desc.device);
     for (auto& sp : sps) {
         const int64_t n = sp.sh.rows;
         std::vector<double> X(3 * (size_t)n), U(3 * (size_t)n), W((size_t)n);
@@ -735,15 +742,22 @@ pic_status pic_set_current_filter(pic_ctx* c, int32_t passes, int32_t compensate
     return PIC_OK;
 }
 
+pic_status pic_set_wait_limit(pic_ctx* c, int32_t polls) {
+    if (!c) return PIC_ERR_ARG;
+    c->wait_polls = polls < 0 ? -1 : polls;
+    return PIC_OK;
+}
+
 pic_status pic_sync(pic_ctx* c) {
     if (!c) return PIC_ERR_ARG;
-    cudaSetDevice(c->desc.device);
+    DeviceScope dscope_(c->desc.device);
     GBPIC_CHECK(c, cudaStreamSynchronize(c->stream));
     return device_errors(c);
 }
 
 pic_status pic_get_fields(pic_ctx* c, double* E, double* B, double* J, int32_t device_pointers) {
     if (!c) return PIC_ERR_ARG;
+    DeviceScope dscope_(c->desc.device);
     pic_status st = pic_sync(c);
     if (st != PIC_OK && st != PIC_ERR_TILE_OVERFLOW) return st;
     const size_t nb = sizeof(double) * 3 * (size_t)c->g.host_N();
@@ -771,6 +785,7 @@ pic_status pic_get_fields(pic_ctx* c, double* E, double* B, double* J, int32_t d
 
 pic_status pic_get_particles(pic_ctx* c, int32_t species, double* out, int64_t* n, int32_t device_pointers) {
     if (!c || !n || species < 0 || species >= (int32_t)c->species.size()) return PIC_ERR_ARG;
+    DeviceScope dscope_(c->desc.device);
     pic_status st = pic_sync(c);
     if (st != PIC_OK && st != PIC_ERR_TILE_OVERFLOW) return st;
     SpeciesDev& s = c->species[species];
@@ -796,6 +811,7 @@ pic_status pic_get_particles(pic_ctx* c, int32_t species, double* out, int64_t* 
 
 pic_status pic_diagnostics(pic_ctx* c, pic_diag* out) {
     if (!c || !out) return PIC_ERR_ARG;
+    DeviceScope dscope_(c->desc.device);
     pic_status st = pic_sync(c);
     if (st != PIC_OK) return st;
     return diagnostics_impl(c, out);
@@ -803,6 +819,7 @@ pic_status pic_diagnostics(pic_ctx* c, pic_diag* out) {
 
 pic_status pic_get_history(pic_ctx* c, double* out, int32_t max_records, int32_t* count) {
     if (!c || !count) return PIC_ERR_ARG;
+    DeviceScope dscope_(c->desc.device);
     *count = 0;
     if (!c->hist) return PIC_OK;
     GBPIC_CHECK(c, cudaStreamSynchronize(c->stream));
@@ -821,6 +838,7 @@ pic_status pic_get_history(pic_ctx* c, double* out, int32_t max_records, int32_t
 
 pic_status pic_set_timing(pic_ctx* c, int32_t enable) {
     if (!c) return PIC_ERR_ARG;
+    DeviceScope dscope_(c->desc.device);
     GBPIC_CHECK(c, cudaStreamSynchronize(c->stream));
     c->timing = enable != 0;
     return PIC_OK;
@@ -829,6 +847,7 @@ pic_status pic_set_timing(pic_ctx* c, int32_t enable) {
 pic_status pic_kernel_times(pic_ctx* c, int32_t max, const char** names, int64_t* launches, double* ms, int32_t* count) {
     const char* const* kNames = kKernelClassNames;
     if (!c || !count) return PIC_ERR_ARG;
+    DeviceScope dscope_(c->desc.device);
     GBPIC_CHECK(c, cudaStreamSynchronize(c->stream));
     for (auto& p : c->pending) {
         float t = 0;
@@ -855,7 +874,7 @@ pic_status pic_kernel_times(pic_ctx* c, int32_t max, const char** names, int64_t
 
 void pic_destroy(pic_ctx* c) {
     if (!c) return;
-    cudaSetDevice(c->desc.device);
+    DeviceScope dscope_(c->desc.device);
     if (c->stream) cudaStreamSynchronize(c->stream);
     adjoint_free(c);
     for (auto& p : c->pending) {

@@ -102,21 +102,21 @@ __global__ void k_nodes(Geom g, Fields<T> f, const double* d, double rho_ion, do
                             ((double)f.E[2][c] - (double)f.E[2][c - sz]) / d[2];
         const double rt = rho[e] + rho_ion;
         const double G = divE - rt;
-        mg = fmax(mg, fabs(G));
-        mr = fmax(mr, fabs(rt));
-        if (gref_valid) mgc = fmax(mgc, fabs(G - gref[e]));
+        mg = max_nf(mg, fabs(G));
+        mr = max_nf(mr, fabs(rt));
+        if (gref_valid) mgc = max_nf(mgc, fabs(G - gref[e]));
         else gref[e] = G;
         // an open x has no edge left of node 0: its Jx there is zero
         const long long ex = (g.open_x && i == 0) ? -1 : g.cidx(wrap_idx(i - 1, g.n[0]), j, k);
         const long long ey = g.cidx(i, wrap_idx(j - 1, g.n[1]), k);
         const long long ez = g.cidx(i, j, wrap_idx(k - 1, g.n[2]));
         const double jx = (double)f.J[0][e] * jscale, jy = (double)f.J[1][e] * jscale, jz = (double)f.J[2][e] * jscale;
-        mj = fmax(mj, fmax(fabs(jx), fmax(fabs(jy), fabs(jz))));
+        mj = max_nf(mj, fmax(fabs(jx), fmax(fabs(jy), fabs(jz))));
         if (cont_valid) {
             const double jxm = ex < 0 ? 0.0 : (double)f.J[0][ex] * jscale;
             const double divJ = (jx - jxm) / d[0] + (jy - (double)f.J[1][ey] * jscale) / d[1] +
                                 (jz - (double)f.J[2][ez] * jscale) / d[2];
-            mc = fmax(mc, fabs((rho[e] - rho_prev[e]) / dt + divJ));
+            mc = max_nf(mc, fabs((rho[e] - rho_prev[e]) / dt + divJ));
         }
         rho_prev[e] = rho[e];
     }

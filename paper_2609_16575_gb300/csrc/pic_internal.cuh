@@ -514,10 +514,18 @@ __device__ __forceinline__ void esirkepov_deposit(AddFn Add, int x, int y, int z
     }
 }
 
+// Running maximum of non-negative values that lets a non-finite value through as +inf
+// (fmax alone returns the other operand of a NaN, which would hide a run that blew up).
+__device__ __forceinline__ double max_nf(double m, double v) { return isfinite(v) ? fmax(m, v) : HUGE_VAL; }
+
 __device__ __forceinline__ int wrap_idx(int i, int n) {
     i %= n;
     return i < 0 ? i + n : i;
 }
+
+// Periodic wrap of an index at most one period outside [0, n) (-n <= i < 2n): a cell
+// index after a move of at most one cell, without a division.
+__device__ __forceinline__ int wrap1(int i, int n) { return i < 0 ? i + n : (i >= n ? i - n : i); }
 
 // Ghost images of interior index i along a periodic dimension of n cells.
 __device__ __forceinline__ int images(int i, int n, int out[3]) {
@@ -569,6 +577,11 @@ __device__ __forceinline__ void store1_yz(const Geom& g, T* a, int i, int j, int
 __device__ __forceinline__ int x_after(const Geom& g, int gx) {
     if (g.open_x) return (gx < 0 || gx >= g.n[0]) ? -1 : gx;
     return wrap_idx(gx, g.n[0]);
+}
+// The same for a global x at most one cell outside the box (-1 <= gx <= n).
+__device__ __forceinline__ int x_after1(const Geom& g, int gx) {
+    if (g.open_x) return (gx < 0 || gx >= g.n[0]) ? -1 : gx;
+    return wrap1(gx, g.n[0]);
 }
 
 // ---------------------------------------------------------------------------
@@ -673,6 +686,7 @@ struct pic_ctx {
     bool port_on = false;
     pic_port_desc port{};
     int deposit = 0;                    // pic_deposit: ZigZag or Esirkepov
+    int wait_polls = -1;                // tile kernel staging wait limit (negative: MBAR_MAX_POLLS)
 };
 
 namespace gbpic {
@@ -700,6 +714,7 @@ pic_status pack_fields(pic_ctx* c, double* E, double* B, double* J);   // device
 pic_status unpack_fields(pic_ctx* c, const double* E, const double* B); // device inputs
 pic_status diagnostics_impl(pic_ctx* c, pic_diag* out);
 pic_status make_tensor_maps(pic_ctx* c);
+pic_status static_scratch_prepare(pic_ctx* c);   // static_check.cu
 
 // helpers (api.cu)
 void* dev_alloc(pic_ctx* c, size_t bytes);
@@ -714,6 +729,29 @@ int64_t count_alive(pic_ctx* c, SpeciesDev& s, int64_t* spilled);
         cudaError_t e_ = (call);                                          \
         if (e_ != cudaSuccess) return ::gbpic::cuda_fail((c), e_, #call); \
     } while (0)
+
+// Makes a device current for one entry point and gives the caller's current device
+// back when the entry point returns, so that a host program driving several devices
+// keeps the device it had selected.
+struct DeviceScope {
+    int prev = -1;
+    bool ok = true;
+    explicit DeviceScope(int dev) {
+        if (cudaGetDevice(&prev) != cudaSuccess) {
+            cudaGetLastError();
+            prev = -1;
+        }
+        if (prev != dev) ok = cudaSetDevice(dev) == cudaSuccess;
+    }
+    ~DeviceScope() {
+        if (prev >= 0) {
+            int cur = -1;
+            if (cudaGetDevice(&cur) == cudaSuccess && cur != prev) cudaSetDevice(prev);
+        }
+    }
+    DeviceScope(const DeviceScope&) = delete;
+    DeviceScope& operator=(const DeviceScope&) = delete;
+};
 
 // Bracket one launch with optional timing events and count it.
 struct LaunchScope {

@@ -33,6 +33,7 @@ template <typename T> struct PushArgs {
     double* krec;   // optional: accumulate sum w m ((g_old + g_new)/2 - 1) here
     double mass;
     int xshift;     // 1: the window moves after this cycle (stored x cells drop by one)
+    int wait_polls; // polls of the TMA staging wait before it gives up (ERRB_TIMEOUT); 0: at once
 };
 
 template <typename T> __host__ __device__ constexpr int box_elems() { return SB * SB * Prec<T>::BX; }
@@ -347,60 +348,29 @@ __device__ __forceinline__ void movers_flush(const PushArgs<T>& A, const Rec<T>*
     mq = 0;
 }
 
-// One CTA per tile.  The tile's particles are read from one SoA block and written to
-// the other, grouped by the cell each particle starts the step in: the block read is
-// grouped by the cells of the step before, so only the particles that crossed a cell
-// face last step (and the movers appended at the segment's end) are out of place.  The
-// output ranges come from the cell histogram of the input (kept from the previous
-// step); a particle that leaves the tile leaves a hole in its range, and the histogram
-// of the output's cells is built for the next step.  Lane l of warp w handles the R
-// consecutive input slots of slot group 32 row + l for rows w, w + warps, ...; a lane's
-// R particles nearly always start in one cell: their straight-segment currents are
-// summed in registers and each row ends with one warp flush of those sums; everything
-// else goes through the warp's record queue.
-template <typename T, bool IDS, bool RECK, bool ESK>
-__global__ void __launch_bounds__(Prec<T>::THREADS, Prec<T>::MINB)
-k_tile_push(const __grid_constant__ CUtensorMap tE0, const __grid_constant__ CUtensorMap tE1,
-            const __grid_constant__ CUtensorMap tE2, const __grid_constant__ CUtensorMap tB0,
-            const __grid_constant__ CUtensorMap tB1, const __grid_constant__ CUtensorMap tB2, PushArgs<T> A) {
-    extern __shared__ __align__(128) unsigned char smem_raw[];
-    unsigned char* smem = reinterpret_cast<unsigned char*>((reinterpret_cast<uintptr_t>(smem_raw) + 127) & ~uintptr_t(127));
-    using Acc = typename JTraits<T>::acc_t;
-    constexpr int NT = Prec<T>::THREADS, NW = NT / 32, R = Prec<T>::R;
+// Start of a tile: one thread issues the six TMA box loads of E and B
+// (local cells -1..8, origin at the tile's ghost corner) completing on one mbarrier while
+// the first 256 threads scan the input cell histogram into the output cell ranges; then
+// the boxes are rewritten as z pairs and the J tile that shared their space is cleared.
+// The wait for the boxes is bounded by A.wait_polls polls: a tile that gives up raises
+// ERRB_TIMEOUT, waits (bounded again, MBAR_MAX_POLLS) for the copies in flight, drops its
+// particles (count, holes and the output histogram set to zero, so later steps read
+// nothing stale) and returns false.
+template <typename T, int NT>
+__device__ __forceinline__ bool tile_prologue(const PushArgs<T>& A, int tile, int cnt, int ox, int oy, int oz,
+                                              const int* hin, int* hout, const CUtensorMap& tE0,
+                                              const CUtensorMap& tE1, const CUtensorMap& tE2,
+                                              const CUtensorMap& tB0, const CUtensorMap& tB1,
+                                              const CUtensorMap& tB2, T* sF, typename Pair<T>::t* sP,
+                                              unsigned char* sJ, uint64_t* bar, int* s_off, int* s_hn, int* s_wsum,
+                                              int* s_timeout, int* s_total, int* s_left) {
     constexpr int BX = Prec<T>::BX;
     constexpr int BS = box_stride<T>();
-    static_assert(NW <= PUSH_WARPS_MAX, "tile kernel CTA too large");
     static_assert(NT >= 256 && NT % 32 == 0, "the histogram scan uses the first 256 threads");
-    using P2 = typename Pair<T>::t;
-    unsigned char* sQ = smem;
-    P2* sP = reinterpret_cast<P2*>(smem + region_a_bytes<T>());
-    unsigned char* sJ = smem + region_a_bytes<T>() + pairs_bytes<T>();
-    T* sF = reinterpret_cast<T*>(sJ);                       // raw boxes, then the J tile
-    const uint32_t sJa = smem_u32(sJ);
-    Rec<T>* sM = reinterpret_cast<Rec<T>*>(sJ + jtile_bytes<T>()) + (threadIdx.x >> 5) * MQ;   // this warp's movers
-    uint64_t* bar = reinterpret_cast<uint64_t*>(sJ + jtile_bytes<T>() + movers_bytes<T>());
-    __shared__ int s_off[TILE_CELLS];   // next free output slot of each input cell's range
-    __shared__ int s_hn[TILE_CELLS];    // cell histogram of the output
-    __shared__ int s_wsum[8];
-    __shared__ int s_timeout, s_total, s_left;
-
-    const int tile = blockIdx.x;
-    const int cnt = min(A.pa.count[tile], A.pa.cap[tile]);
-    const int* hin = A.hin + (size_t)tile * TILE_CELLS;
-    int* hout = A.hout + (size_t)tile * TILE_CELLS;
     const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
-    if (cnt == 0) {
-        for (int i = threadIdx.x; i < TILE_CELLS; i += NT) hout[i] = 0;
-        if (threadIdx.x == 0) A.pa.holes[tile] = 0;
-        return;
-    }
-    const int ntx = A.g.nt[0], nty = A.g.nt[1];
-    const int tx = tile % ntx, ty = (tile / ntx) % nty, tz = tile / (ntx * nty);
-    const int ox = tx * TILE, oy = ty * TILE, oz = tz * TILE;
-
     if (threadIdx.x == 0) {
-        s_timeout = 0;
-        s_left = 0;
+        *s_timeout = 0;
+        *s_left = 0;
         mbar_init(bar, 1);
         fence_mbar_init();
     }
@@ -436,36 +406,40 @@ k_tile_push(const __grid_constant__ CUtensorMap tE0, const __grid_constant__ CUt
             s_off[2 * threadIdx.x + 1] = excl + a0;
             s_hn[2 * threadIdx.x] = 0;
             s_hn[2 * threadIdx.x + 1] = 0;
-            if (threadIdx.x == 255) s_total = woff + incl;
+            if (threadIdx.x == 255) *s_total = woff + incl;
         }
     }
-    {
-        int polls = 0;
-        while (!mbar_try_wait(bar, 0)) {
-            if (++polls > MBAR_MAX_POLLS) {
-                s_timeout = 1;
-                break;
-            }
+    for (int polls = 0;; ++polls) {
+        if (polls >= A.wait_polls) {   // (a bound of 0 gives up without waiting)
+            *s_timeout = 1;
+            break;
         }
+        if (mbar_try_wait(bar, 0)) break;
     }
     __syncthreads();
-    if (s_timeout) {
+    if (*s_timeout) {
         if (threadIdx.x == 0) {
             atomicOr(&A.ctr->err, ERRB_TIMEOUT);
             // wait (bounded) for the copies still in flight before the CTA exits
             int polls = 0;
             while (!mbar_try_wait(bar, 0) && ++polls < MBAR_MAX_POLLS) {
             }
+            A.pa.count[tile] = 0;
+            A.pa.holes[tile] = 0;
         }
+        for (int i = threadIdx.x; i < TILE_CELLS; i += NT) hout[i] = 0;
         __syncthreads();
-        return;
+        return false;
     }
-    // z pairs (F(x, y, z), F(x, y, z + 1)) of every component, local x, y -1..8, z -1..7
-    for (int e = threadIdx.x; e < 6 * PS; e += NT) {
-        const int c = e / PS, r = e - c * PS;
-        const int xi = r % PSX, yi = (r / PSX) % PSY, zi = r / (PSX * PSY);
-        const T* F = sF + c * BS + (zi * SB + yi) * BX + xi;
-        sP[e] = Pair<T>::make(F[0], F[SB * BX]);
+    // z pairs (F(x, y, z), F(x, y, z + 1)) of every component, local x, y -1..8, z -1..7:
+    // one x row of PSX pairs per thread and pass
+    for (int row = threadIdx.x; row < 6 * PSZ * PSY; row += NT) {
+        const int c = row / (PSZ * PSY), r = row - c * (PSZ * PSY);
+        const int zi = r / PSY, yi = r - zi * PSY;
+        const T* F = sF + c * BS + (zi * SB + yi) * BX;
+        typename Pair<T>::t* dst = sP + c * PS + (zi * PSY + yi) * PSX;
+#pragma unroll
+        for (int xi = 0; xi < PSX; ++xi) dst[xi] = Pair<T>::make(F[xi], F[xi + SB * BX]);
     }
     __syncthreads();   // the raw boxes are consumed: clear the J tile in their place
     {
@@ -473,6 +447,89 @@ k_tile_push(const __grid_constant__ CUtensorMap tE0, const __grid_constant__ CUt
         for (int i = threadIdx.x; i < JT_ELEMS; i += NT) z[i] = 0ull;
     }
     __syncthreads();
+    return true;
+}
+
+// The J tile into HBM: element (comp, lx, ly, lz), local -1..9, is
+// added to the global edge of its wrapped cell (the periodic guard layers fold onto the
+// other side of the box; what lies outside an open x is dropped) with the 64-bit
+// fixed-point (FP32) or FP64 atomic add.  gidx[SJ d + l + 1] is the global index along
+// dimension d of local l (x: -1 outside an open x), filled by the caller.
+template <typename T, int NT>
+__device__ __forceinline__ void tile_flush_j(const PushArgs<T>& A, const unsigned char* sJ, const int* gidx) {
+    using Acc = typename JTraits<T>::acc_t;
+    for (int e = threadIdx.x; e < JT_ELEMS; e += NT) {
+        const Acc v = tile_get(sJ, e, JT_ELEMS, T(0));
+        if (v == Acc(0)) continue;
+        const int comp = e / SJ3, r = e - comp * SJ3;
+        const int lz = r / (SJ * SJ), r2 = r - lz * (SJ * SJ);
+        const int ly = r2 / SJ, lx = r2 - ly * SJ;
+        const int gx = gidx[lx];
+        if (gx < 0) continue;   // current leaving an open x face
+        acc_atomic(A.f.J[comp] + A.g.cidx(gx, gidx[SJ + ly], gidx[2 * SJ + lz]), v);
+    }
+}
+// Fill the table of tile_flush_j (threads 0 .. 3 SJ - 1).
+template <typename T>
+__device__ __forceinline__ void tile_flush_index(const PushArgs<T>& A, int ox, int oy, int oz, int* gidx) {
+    const int t = threadIdx.x;
+    if (t < 3 * SJ) {
+        const int d = t / SJ, l = t - d * SJ - 1;
+        gidx[t] = d == 0 ? x_after(A.g, ox + l) : (d == 1 ? wrap_idx(oy + l, A.g.n[1]) : wrap_idx(oz + l, A.g.n[2]));
+    }
+}
+
+// One CTA per tile.  The tile's particles are read from one SoA block and written to
+// the other, grouped by the cell each particle starts the step in: the block read is
+// grouped by the cells of the step before, so only the particles that crossed a cell
+// face last step (and the movers appended at the segment's end) are out of place.  The
+// output ranges come from the cell histogram of the input (kept from the previous
+// step); a particle that leaves the tile leaves a hole in its range, and the histogram
+// of the output's cells is built for the next step.  Lane l of warp w handles the R
+// consecutive input slots of slot group 32 row + l for rows w, w + warps, ...; a lane's
+// R particles nearly always start in one cell: their straight-segment currents are
+// summed in registers and each row ends with one warp flush of those sums; everything
+// else goes through the warp's record queue.
+template <typename T, bool IDS, bool RECK, bool ESK>
+__global__ void __launch_bounds__(Prec<T>::THREADS, Prec<T>::MINB)
+k_tile_push(const __grid_constant__ CUtensorMap tE0, const __grid_constant__ CUtensorMap tE1,
+            const __grid_constant__ CUtensorMap tE2, const __grid_constant__ CUtensorMap tB0,
+            const __grid_constant__ CUtensorMap tB1, const __grid_constant__ CUtensorMap tB2, PushArgs<T> A) {
+    extern __shared__ __align__(128) unsigned char smem_raw[];
+    unsigned char* smem = reinterpret_cast<unsigned char*>((reinterpret_cast<uintptr_t>(smem_raw) + 127) & ~uintptr_t(127));
+    using Acc = typename JTraits<T>::acc_t;
+    constexpr int NT = Prec<T>::THREADS, NW = NT / 32, R = Prec<T>::R;
+    static_assert(NW <= PUSH_WARPS_MAX, "tile kernel CTA too large");
+    using P2 = typename Pair<T>::t;
+    unsigned char* sQ = smem;
+    P2* sP = reinterpret_cast<P2*>(smem + region_a_bytes<T>());
+    unsigned char* sJ = smem + region_a_bytes<T>() + pairs_bytes<T>();
+    T* sF = reinterpret_cast<T*>(sJ);                       // raw boxes, then the J tile
+    const uint32_t sJa = smem_u32(sJ);
+    Rec<T>* sM = reinterpret_cast<Rec<T>*>(sJ + jtile_bytes<T>()) + (threadIdx.x >> 5) * MQ;   // this warp's movers
+    uint64_t* bar = reinterpret_cast<uint64_t*>(sJ + jtile_bytes<T>() + movers_bytes<T>());
+    __shared__ int s_off[TILE_CELLS];   // next free output slot of each input cell's range
+    __shared__ int s_hn[TILE_CELLS];    // cell histogram of the output
+    __shared__ int s_wsum[8];
+    __shared__ int s_timeout, s_total, s_left;
+
+    const int tile = blockIdx.x;
+    const int cnt = min(A.pa.count[tile], A.pa.cap[tile]);
+    const int* hin = A.hin + (size_t)tile * TILE_CELLS;
+    int* hout = A.hout + (size_t)tile * TILE_CELLS;
+    const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
+    if (cnt == 0) {
+        for (int i = threadIdx.x; i < TILE_CELLS; i += NT) hout[i] = 0;
+        if (threadIdx.x == 0) A.pa.holes[tile] = 0;
+        return;
+    }
+    const int ntx = A.g.nt[0], nty = A.g.nt[1];
+    const int tx = tile % ntx, ty = (tile / ntx) % nty, tz = tile / (ntx * nty);
+    const int ox = tx * TILE, oy = ty * TILE, oz = tz * TILE;
+
+    if (!tile_prologue<T, NT>(A, tile, cnt, ox, oy, oz, hin, hout, tE0, tE1, tE2, tB0, tB1, tB2, sF, sP, sJ, bar, s_off,
+                              s_hn, s_wsum, &s_timeout, &s_total, &s_left))
+        return;
 
     const int ext[3] = {min(TILE, A.g.n[0] - ox), min(TILE, A.g.n[1] - oy), min(TILE, A.g.n[2] - oz)};
     WarpQueue<T> Q;
@@ -642,7 +699,7 @@ k_tile_push(const __grid_constant__ CUtensorMap tE0, const __grid_constant__ CUt
             // instead
             int gxm = 0;
             if (move) {
-                gxm = x_after(A.g, ox + x + s[0]);
+                gxm = x_after1(A.g, ox + x + s[0]);
                 if (gxm >= 0) gxm -= A.xshift;   // the window's first column leaves
                 if (gxm < 0) {
                     move = false;
@@ -653,8 +710,8 @@ k_tile_push(const __grid_constant__ CUtensorMap tE0, const __grid_constant__ CUt
                 if (mq + __popc(mm) > MQ) movers_flush(A, sM, mq, lane);
                 if (move) {
                     Rec<T>& rc = sM[mq + __popc(mm & ((1u << lane) - 1u))];
-                    const int gy = wrap_idx(oy + y + s[1], A.g.n[1]);
-                    const int gz = wrap_idx(oz + z + s[2], A.g.n[2]);
+                    const int gy = wrap1(oy + y + s[1], A.g.n[1]);
+                    const int gz = wrap1(oz + z + s[2], A.g.n[2]);
                     rc.cell = (gz * A.g.n[1] + gy) * A.g.n[0] + gxm;
                     rc.id = IDS ? A.pa.id[p] : 0;
                     rc.d[0] = d2[0];
@@ -676,6 +733,8 @@ k_tile_push(const __grid_constant__ CUtensorMap tE0, const __grid_constant__ CUt
     esc = __reduce_add_sync(0xffffffffu, esc);
     if (lane == 0 && left) atomicAdd(&s_left, left);
     if (lane == 0 && esc) atomicAdd(&A.ctr->escaped, esc);
+    __shared__ int s_gidx[3 * SJ];
+    tile_flush_index(A, ox, oy, oz, s_gidx);
     __syncthreads();
     // the output segment: the input cells' ranges (with the holes of the departed) and,
     // appended later, this step's arrivals
@@ -684,20 +743,8 @@ k_tile_push(const __grid_constant__ CUtensorMap tE0, const __grid_constant__ CUt
         A.pa.count[tile] = s_total;
         A.pa.holes[tile] = s_left;
     }
-
     // flush the shared J tile to HBM (periodic wrap of the guard layers)
-    for (int e = threadIdx.x; e < JT_ELEMS; e += NT) {
-        const Acc v = tile_get(sJ, e, JT_ELEMS, T(0));
-        if (v == Acc(0)) continue;
-        const int comp = e / SJ3;
-        const int r = e - comp * SJ3;
-        const int lx = r % SJ - 1, ly = (r / SJ) % SJ - 1, lz = r / (SJ * SJ) - 1;
-        const int gx = x_after(A.g, ox + lx);
-        if (gx < 0) continue;   // current leaving an open x face
-        const int gy = wrap_idx(oy + ly, A.g.n[1]);
-        const int gz = wrap_idx(oz + lz, A.g.n[2]);
-        acc_atomic(A.f.J[comp] + A.g.cidx(gx, gy, gz), v);
-    }
+    tile_flush_j<T, NT>(A, sJ, s_gidx);
     if (RECK) block_add_double(kacc, A.krec);
 }
 
@@ -906,6 +953,7 @@ static PushArgs<T> make_args(pic_ctx* c, SpeciesDev& s, int parity, double* krec
     A.parity = parity;
     A.krec = krec;
     A.mass = s.m;
+    A.wait_polls = c->wait_polls >= 0 ? c->wait_polls : MBAR_MAX_POLLS;
     return A;
 }
 

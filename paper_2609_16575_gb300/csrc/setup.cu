@@ -216,8 +216,11 @@ static pic_status load_t(pic_ctx* c, const pic_species_desc* d, SpeciesDev& s, c
     }
     // mover and spill lists (a window move sends the first cell column of every tile to
     // the tile before it: an eighth of the particles, plus the new column's plasma)
-    s.mover_cap = (int)std::min<long long>(std::max<long long>(window_species ? total / 4 : n / 4, 65536), 0x7fffff00LL);
-    s.spill_cap = (int)std::min<long long>(std::max<long long>(n / 16, 65536), 0x7fffff00LL);
+    s.mover_cap = (int)std::min<long long>(
+        d->mover_capacity > 0 ? d->mover_capacity : std::max<long long>(window_species ? total / 4 : n / 4, 65536),
+        0x7fffff00LL);
+    s.spill_cap = (int)std::min<long long>(d->spill_capacity > 0 ? d->spill_capacity : std::max<long long>(n / 16, 65536),
+                                           0x7fffff00LL);
     s.movers = dev_alloc(c, sizeof(Rec<T>) * (size_t)s.mover_cap);
     s.spill = dev_alloc(c, sizeof(Rec<T>) * (size_t)s.spill_cap);
     if (!s.movers || !s.spill) return PIC_ERR_OOM;

@@ -10,6 +10,7 @@
 // each call clears what it uses first; calls whose work overlaps on the GPU (two
 // contexts on different streams of one device, for instance) race on it.
 #include <algorithm>
+#include <atomic>
 #include <cstring>
 #include <string>
 
@@ -24,8 +25,20 @@ static __device__ __align__(256) double g_static_scratch[STATIC_MAX_CELLS + 32];
 
 // Device address of g_static_scratch per device ordinal.  In host code the symbol
 // name is only a host-side stand-in, so the address is looked up once per device
-// (with that device current) and passed to the kernels.
-static double* s_scratch[STATIC_MAX_DEVICES];
+// (with that device current) and passed to the kernels.  The lookup loads this file's
+// module on the device and commits the array, so it is done by pic_init_grid (which
+// may allocate), not by the allocation-free entry point.
+static std::atomic<double*> s_scratch[STATIC_MAX_DEVICES];
+
+// Called by pic_init_grid with the context's device current.
+pic_status static_scratch_prepare(pic_ctx* c) {
+    const int dev = c->desc.device;
+    if (dev < 0 || dev >= STATIC_MAX_DEVICES || s_scratch[dev].load()) return PIC_OK;
+    double* p = nullptr;
+    GBPIC_CHECK(c, cudaGetSymbolAddress(reinterpret_cast<void**>(&p), g_static_scratch));
+    s_scratch[dev].store(p);
+    return PIC_OK;
+}
 
 template <typename T>
 __global__ void k_static_charge(Geom g, ParticleArrays<T> pa, const Rec<T>* spill, int nsp, double qdv, double* rho) {
@@ -68,8 +81,8 @@ __global__ void k_static_gauss(Geom g, const T* E0, const T* E1, const T* E2, do
         const double divE = ((double)E0[c] - (double)E0[c - 1]) / d0 + ((double)E1[c] - (double)E1[c - sy]) / d1 +
                             ((double)E2[c] - (double)E2[c - sz]) / d2;
         const double rt = rho[e] + rho_ion;
-        mg = fmax(mg, fabs(divE - rt));
-        mr = fmax(mr, fabs(rt));
+        mg = max_nf(mg, fabs(divE - rt));
+        mr = max_nf(mr, fabs(rt));
     }
     for (int o = 16; o > 0; o >>= 1) {
         mg = fmax(mg, __shfl_xor_sync(0xffffffffu, mg, o));
@@ -127,15 +140,14 @@ extern "C" pic_status pic_gauss_check_static(pic_ctx* c, double* gauss_max, doub
     }
     const int dev = c->desc.device;
     if (dev < 0 || dev >= STATIC_MAX_DEVICES) return PIC_ERR_ARG;
-    GBPIC_CHECK(c, cudaSetDevice(dev));
+    DeviceScope dscope_(dev);
     pic_status st = pic_sync(c);
     if (st != PIC_OK) return st;
-    if (!s_scratch[dev]) {
-        // first call on this device: look up the device address of the static array
-        double* p = nullptr;
-        GBPIC_CHECK(c, cudaGetSymbolAddress(reinterpret_cast<void**>(&p), g_static_scratch));
-        s_scratch[dev] = p;
+    double* scratch = s_scratch[dev].load();
+    if (!scratch) {
+        c->err = "pic_gauss_check_static: the static scratch of this device was not set up by pic_init_grid";
+        return PIC_ERR_STATE;
     }
-    return c->prec == PIC_FP64 ? gauss_static_t<double>(c, s_scratch[dev], gauss_max, rho_max)
-                               : gauss_static_t<float>(c, s_scratch[dev], gauss_max, rho_max);
+    return c->prec == PIC_FP64 ? gauss_static_t<double>(c, scratch, gauss_max, rho_max)
+                               : gauss_static_t<float>(c, scratch, gauss_max, rho_max);
 }

@@ -67,7 +67,8 @@ class pic_species_desc(ctypes.Structure):
     _fields_ = [("q", ctypes.c_double), ("m", ctypes.c_double), ("n", ctypes.c_int64),
                 ("X", ctypes.c_void_p), ("u", ctypes.c_void_p), ("w", ctypes.c_void_p),
                 ("momenta_at_half_step", ctypes.c_int32), ("device_pointers", ctypes.c_int32),
-                ("capacity_slack", ctypes.c_double)]
+                ("capacity_slack", ctypes.c_double), ("mover_capacity", ctypes.c_int64),
+                ("spill_capacity", ctypes.c_int64)]
 
 
 class pic_diag(ctypes.Structure):
@@ -125,6 +126,7 @@ def lib():
                                           ctypes.POINTER(ctypes.c_double), ctypes.POINTER(ctypes.c_void_p),
                                           ctypes.c_int32]
             L.pic_set_deposit.argtypes = [P, ctypes.c_int32]
+            L.pic_set_wait_limit.argtypes = [P, ctypes.c_int32]
             L.pic_save_state.argtypes = [P, ctypes.POINTER(ctypes.c_void_p), ctypes.POINTER(ctypes.c_size_t)]
             L.pic_load_state.argtypes = [P, ctypes.c_void_p, ctypes.c_size_t]
             L.pic_free_state.argtypes = [ctypes.c_void_p]
@@ -146,7 +148,8 @@ def lib():
                          "pic_set_timing", "pic_kernel_times", "pic_adjoint_forward", "pic_adjoint_backward",
                          "pic_gauss_check_static", "pic_set_laser", "pic_set_moving_window",
                          "pic_set_current_filter", "pic_set_pec", "pic_set_port", "pic_set_deposit",
-                         "pic_save_state", "pic_load_state", "pic_set_background", "pic_adjoint_run"):
+                         "pic_save_state", "pic_load_state", "pic_set_background", "pic_adjoint_run",
+                         "pic_set_wait_limit"):
                 getattr(L, name).restype = ctypes.c_int
             _lib = L
     return _lib
@@ -228,9 +231,10 @@ class Context:
     and enqueues on torch's current stream of ``device``."""
 
     def __init__(self, n, d, dt, precision=PIC_FP32, rho_ion=0.0, device=0, track_ids=False, record_every=0,
-                 history_capacity=0, use_torch=True, sort_every=0, bc_x=0):
+                 history_capacity=0, use_torch=True, sort_every=0, bc_x=0, allocator=None):
+        """``allocator``: an object with ``alloc``/``free`` callbacks (ALLOC_FN, FREE_FN) in
+        place of torch's caching allocator (the stream stays torch's)."""
         stream = None
-        allocator = None
         if use_torch:
             import torch
 
@@ -239,7 +243,8 @@ class Context:
             # torch's default stream has handle 0; pass cudaStreamLegacy (0x1) so that the
             # library enqueues on that same stream instead of creating its own
             stream = s.cuda_stream or 1
-            allocator = _TorchAllocator(device, s.cuda_stream)
+            if allocator is None:
+                allocator = _TorchAllocator(device, s.cuda_stream)
         self.n = tuple(int(v) for v in n[:3])
         self.bc_x = int(bc_x)
         self.ncell = self.n[0] * self.n[1] * self.n[2]
@@ -270,7 +275,8 @@ class Context:
             raise ValueError("E and B must both be host or both be device arrays")
         _check(self.ptr, lib().pic_set_fields(self.ptr, pe, pb, de or db), "pic_set_fields")
 
-    def load_species(self, q, m, X, u, w, momenta_at_half_step=True, capacity_slack=0.0):
+    def load_species(self, q, m, X, u, w, momenta_at_half_step=True, capacity_slack=0.0, mover_capacity=0,
+                     spill_capacity=0):
         """X, u: (3, n) float64; w: (n,) float64 (numpy or CUDA torch)."""
         n = int(w.shape[0])
         desc = pic_species_desc()
@@ -284,19 +290,23 @@ class Context:
         desc.momenta_at_half_step = int(bool(momenta_at_half_step))
         desc.device_pointers = dx
         desc.capacity_slack = float(capacity_slack)
+        desc.mover_capacity = int(mover_capacity)
+        desc.spill_capacity = int(spill_capacity)
         sid = ctypes.c_int32()
         _check(self.ptr, lib().pic_load_species(self.ptr, ctypes.byref(desc), ctypes.byref(sid)), "pic_load_species")
         self.species_n.append(n)
         return sid.value
 
-    def load_species_array(self, q, m, P, momenta_at_half_step=True, capacity_slack=0.0):
+    def load_species_array(self, q, m, P, momenta_at_half_step=True, capacity_slack=0.0, mover_capacity=0,
+                           spill_capacity=0):
         """P: (7, n) float64 rows X, Y, Z, ux, uy, uz, w."""
         if isinstance(P, np.ndarray):
             P = np.ascontiguousarray(P, dtype=np.float64)
             return self.load_species(q, m, np.ascontiguousarray(P[0:3]), np.ascontiguousarray(P[3:6]),
-                                     np.ascontiguousarray(P[6]), momenta_at_half_step, capacity_slack)
+                                     np.ascontiguousarray(P[6]), momenta_at_half_step, capacity_slack, mover_capacity,
+                                     spill_capacity)
         return self.load_species(q, m, P[0:3].contiguous(), P[3:6].contiguous(), P[6].contiguous(),
-                                 momenta_at_half_step, capacity_slack)
+                                 momenta_at_half_step, capacity_slack, mover_capacity, spill_capacity)
 
     def step(self, nsteps=1):
         _check(self.ptr, lib().pic_step(self.ptr, int(nsteps)), "pic_step")
@@ -345,6 +355,9 @@ class Context:
         _check(self.ptr, lib().pic_get_history(self.ptr, out.ctypes.data, max_records, ctypes.byref(cnt)),
                "pic_get_history")
         return out[:cnt.value]
+
+    def set_wait_limit(self, polls):
+        _check(self.ptr, lib().pic_set_wait_limit(self.ptr, int(polls)), "pic_set_wait_limit")
 
     def set_timing(self, enable=True):
         _check(self.ptr, lib().pic_set_timing(self.ptr, int(bool(enable))), "pic_set_timing")

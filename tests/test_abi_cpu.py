@@ -78,6 +78,22 @@ def test_no_device_is_reported_not_faked(L):
     assert not out.value
 
 
+def test_species_descriptor_layout_matches_the_header():
+    """The binding's pic_species_desc has the header's fields in the header's order
+    (the capacities were appended, so older callers that zero the struct keep working)."""
+    from paper_2609_16575_gb300 import gbpic
+
+    src = open(os.path.join(ROOT, "include", "gbpic.h")).read()
+    body = src[src.index("typedef struct pic_species_desc {"):src.index("} pic_species_desc;")]
+    body = re.sub(r"/\*.*?\*/", "", body, flags=re.S)
+    fields = []
+    for decl in body.split(";")[:-1]:
+        decl = decl.replace("typedef struct pic_species_desc {", "").strip()
+        declarators = decl.split(None, 1)[1]          # after the type: "x, y" or "*X"
+        fields += re.findall(r"\**\s*(\w+)\s*(?:,|$)", declarators)
+    assert [f for f, _ in gbpic.pic_species_desc._fields_] == fields
+
+
 def test_new_entry_points_reject_a_null_context(L):
     """Every setter and the checkpoint calls return PIC_ERR_ARG for a null context (no
     device needed); pic_window_moves reads 0 and pic_free_state accepts NULL."""
@@ -89,6 +105,7 @@ def test_new_entry_points_reject_a_null_context(L):
     assert L.pic_set_pec(None, 1, 0) == 1
     assert L.pic_set_port(None, None) == 1
     assert L.pic_set_deposit(None, 1) == 1
+    assert L.pic_set_wait_limit(None, 1) == 1
     blob, size = ctypes.c_void_p(), ctypes.c_size_t()
     assert L.pic_save_state(None, ctypes.byref(blob), ctypes.byref(size)) == 1
     assert L.pic_load_state(None, None, 0) == 1

@@ -3,6 +3,8 @@ reference of the same cycle and against central finite differences of the FP64 G
 forward map.  Loss: final field energy; parameters: initial momenta u^{-1/2} and the
 amplitude A of the initial plane-wave field."""
 import numpy as np
+
+import oracle
 import pytest
 import torch
 
@@ -54,7 +56,8 @@ def test_adjoint_matches_central_differences():
     """Differentiable-run workload, reduced (16^3, 4 per cell, u_th = 0.02, plane wave,
     40 steps, checkpoints every 10): directional derivative along a random momentum
     direction and the amplitude derivative agree with central differences (perturbations
-    small enough that no particle's cell-crossing pattern changes; checked)."""
+    small enough that no particle ends in another cell; the full-size test below checks
+    the cells at every step)."""
     wl = W.differentiable(n=16, ppc=4, steps=40)
     E_dir, B_dir = plane_wave_fields(wl.n, wl.d, wl.dt, amplitude=1.0)
     A = 0.05
@@ -77,6 +80,91 @@ def test_adjoint_matches_central_differences():
     LAm, _ = _gpu_loss(wl, P, A - hA, E_dir, B_dir, 40, 10, want_grad=False)
     fdA = (LAp - LAm) / (2 * hA)
     assert abs(fdA - dA) <= 1e-4 * abs(dA), (fdA, dA)
+
+
+def _cell_checksum(ctx, n, npart):
+    """Two integer sums that change when any particle's cell changes: sum of the linear
+    cell index and sum of (id + 1) times it, from a device-side read-out (rows in id
+    order)."""
+    import ctypes
+
+    from paper_2609_16575_gb300 import gbpic
+
+    out = torch.empty((7, npart), dtype=torch.float64, device="cuda")
+    cnt = ctypes.c_int64(npart)
+    assert gbpic.lib().pic_get_particles(ctx.ptr, 0, ctypes.c_void_p(out.data_ptr()), ctypes.byref(cnt), 1) == 0
+    c = torch.floor(out[0:3]).to(torch.int64)
+    lin = (c[2] * n[1] + c[1]) * n[0] + c[0]
+    ids = torch.arange(1, npart + 1, device="cuda", dtype=torch.int64)
+    return int(lin.sum()), int((lin * ids).sum())
+
+
+def _checked_forward(wl, P, A, E_dir, B_dir, nsteps):
+    """The FP64 forward map: L = U_E + U_B after nsteps, and the per-step cell checksums."""
+    from paper_2609_16575_gb300 import gbpic
+
+    ctx = gbpic.Context(wl.n, wl.d, wl.dt, precision=gbpic.PIC_FP64, track_ids=True)
+    ctx.set_fields(A * E_dir, A * B_dir)
+    ctx.load_species_array(-1.0, 1.0, P)
+    sums = []
+    for _ in range(nsteps):
+        ctx.step(1)
+        sums.append(_cell_checksum(ctx, wl.n, P.shape[1]))
+    d = ctx.diagnostics()
+    ctx.close()
+    return d["U_E"] + d["U_B"], sums
+
+
+def test_adjoint_matches_central_differences_on_the_differentiable_run():
+    """The differentiable-run workload at its full size: 32^3 cells, 16 per cell (524,288
+    electrons), u_th = 0.02, plane wave of amplitude 0.05, 200 steps, checkpoints every 20.
+    The adjoint's amplitude derivative and its momentum gradient along random directions
+    (on 2048 particles each) agree with central differences of the FP64 forward map to
+    1e-4.  A perturbation
+    counts only if no particle's cell changes differently at any step (per-step cell
+    checksums of the perturbed runs equal the unperturbed run's); another direction is
+    drawn otherwise."""
+    wl = W.differentiable()
+    E_dir, B_dir = plane_wave_fields(wl.n, wl.d, wl.dt, amplitude=1.0)
+    A = 0.05
+    P = wl.species[0].P
+    L, dA, du, _ = _gpu_loss(wl, P, A, E_dir, B_dir, 200, 20)
+    L0, sums0 = _checked_forward(wl, P, A, E_dir, B_dir, 200)
+    assert abs(L0 - L) <= 1e-12 * abs(L)
+    # amplitude: the largest step of the list whose perturbed runs keep every cell
+    for rel in (1e-8, 2e-9, 5e-10, 1e-10):
+        hA = rel * A
+        LAp, sp = _checked_forward(wl, P, A + hA, E_dir, B_dir, 200)
+        LAm, sm = _checked_forward(wl, P, A - hA, E_dir, B_dir, 200)
+        if sp == sums0 and sm == sums0:
+            break
+    else:
+        pytest.fail("every amplitude step changed a cell crossing")
+    fdA = (LAp - LAm) / (2 * hA)
+    assert abs(fdA - dA) <= 1e-4 * abs(dA), (rel, fdA, dA)
+    # momenta, along random directions on 2048 random particles (a direction over every
+    # particle shifts some crossing by a step almost surely at any usable h)
+    rng = np.random.default_rng(6)
+    checked = 0
+    for attempt in range(6):
+        v = np.zeros((3, P.shape[1]))
+        pick = rng.choice(P.shape[1], 2048, replace=False)
+        v[:, pick] = rng.standard_normal((3, pick.size))
+        h = 1e-8 if attempt < 3 else 1e-9
+        Pp, Pm = P.copy(), P.copy()
+        Pp[3:6] += h * v
+        Pm[3:6] -= h * v
+        Lp, sp = _checked_forward(wl, Pp, A, E_dir, B_dir, 200)
+        Lm, sm = _checked_forward(wl, Pm, A, E_dir, B_dir, 200)
+        if sp != sums0 or sm != sums0:
+            continue   # a crossing moved by a step: not a differentiable neighbourhood
+        fd = (Lp - Lm) / (2 * h)
+        ad = float((du * v).sum())
+        assert abs(fd - ad) <= 1e-4 * abs(ad), (fd, ad)
+        checked += 1
+        if checked == 2:
+            break
+    assert checked >= 1
 
 
 def test_autograd_function():
@@ -138,16 +226,27 @@ def test_adjoint_run_is_forward_then_backward():
 
 
 def test_background_enters_the_gauss_residual():
-    """pic_set_background changes rho_max by the background, as a uniform charge does."""
+    """pic_set_background: rho_max and gauss_max become max |rho + rho_ion| of the
+    oracle's CIC charge of the same particles (E = 0, so G = -(rho + rho_ion)), and the
+    Gauss reference is taken again at the next pic_diagnostics."""
     from paper_2609_16575_gb300 import gbpic
 
     wl = W.thermal((8, 8, 8), 0.2, 2, 0.1, seed=36)
+    P = wl.species[0].P
     ctx = gbpic.Context(wl.n, wl.d, wl.dt, precision=gbpic.PIC_FP64, rho_ion=0.0)
-    ctx.load_species_array(-1.0, 1.0, wl.species[0].P)
-    r0 = ctx.diagnostics()["rho_max"]
-    ctx.set_background(1.0)
-    d1 = ctx.diagnostics()
-    assert d1["rho_max"] < r0            # the ions neutralise the electrons' charge
+    ctx.load_species_array(-1.0, 1.0, P)
+    sp = [oracle.Species(-1.0, 1.0, P.copy())]
+    for rho_ion in (0.0, 1.0, 0.25):
+        if rho_ion:
+            ctx.set_background(rho_ion)
+        ref = np.abs(oracle.rho(wl.n, wl.d, sp, rho_ion)).max()
+        d1 = ctx.diagnostics()
+        d2 = ctx.diagnostics()
+        for dd in (d1, d2):
+            assert dd["rho_max"] == pytest.approx(ref, rel=1e-12, abs=1e-12)
+            assert dd["gauss_max"] == pytest.approx(ref, rel=1e-12, abs=1e-12)
+        assert d1["gauss_change_max"] == 0.0          # the reference is taken again here
+        assert d2["gauss_change_max"] <= 1e-12 * ref  # nothing stepped (charge sums in any order)
     with pytest.raises(gbpic.PicError):
         ctx.set_background(float("nan"))
     ctx.close()

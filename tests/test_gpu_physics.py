@@ -57,16 +57,38 @@ def test_cold_plasma_fp64_against_oracle():
     assert np.abs(hist_g.sum(1) / hist_o.sum(1) - 1).max() < 1e-9
 
 
-def test_thermal_fp32_energy_history_within_one_percent():
-    """FP32 bulk against the FP64 oracle over 100 steps of a 32^3 thermal plasma:
-    trajectories separate, the energy history agrees within 1%."""
-    wl = W.thermal((32, 32, 32), 0.2, 16, 0.05, seed=10, steps=100)
+@pytest.mark.parametrize("ppc,u_th", [(16, 0.05), (32, 0.1)])
+def test_thermal_fp32_energy_history_within_one_percent(ppc, u_th):
+    """FP32 bulk against the FP64 oracle over 100 steps of a 32^3 thermal plasma, in the
+    shape of the 128^3 thermal workload (u_th = 0.05) and of the 256^3 precision-stress
+    workload (32 per cell, u_th = 0.1): trajectories separate, the energy history agrees
+    within 1%."""
+    wl = W.thermal((32, 32, 32), 0.2, ppc, u_th, seed=10, steps=100)
     ctx = run_gpu(wl, FP32, wl.steps, track_ids=False, record_every=1)
     _, _, hist_o = run_oracle(wl, FP32, wl.steps)
     hist_g = ctx.history()
     tot_g, tot_o = hist_g.sum(1), hist_o.sum(1)
     assert np.abs(tot_g / tot_o - 1).max() < 1e-2
     assert np.abs(hist_g[:, 2] / hist_o[:, 2] - 1).max() < 1e-2
+
+
+def test_cold_plasma_fp32_frequency():
+    """The cold-plasma workload on the FP32 path (FP32-representable inputs on both
+    sides): the frequency fitted to the Ex mode over 200 steps is within 0.5% of the
+    oracle's (and of the closed-form discrete frequency)."""
+    wl = _cold_plasma()
+    wl.E = wl.E.astype(np.float32).astype(np.float64)
+    amps_g = []
+    run_gpu(wl, FP32, wl.steps,
+            per_step=lambda c, k: amps_g.append(np.fft.rfft(c.get_fields()[0][0].mean(axis=(0, 1)))[1]))
+    amps_o = []
+    run_oracle(wl, FP32, wl.steps, per_step=lambda F, sp, k: amps_o.append(np.fft.rfft(F[0].mean(axis=(0, 1)))[1]))
+    t = np.arange(wl.steps) * wl.dt
+    a_g, a_o = np.array(amps_g), np.array(amps_o)
+    pick = (lambda a: a.imag) if np.abs(a_o.imag).max() > np.abs(a_o.real).max() else (lambda a: a.real)
+    w_g, w_o = _fit(t, pick(a_g)), _fit(t, pick(a_o))
+    assert abs(w_g / w_o - 1) < 5e-3, (w_g, w_o)
+    assert abs(w_g / oracle.cold_plasma_omega(2 * np.pi / 16, wl.dt) - 1) < 5e-3
 
 
 @pytest.mark.parametrize("prec", [FP32, FP64])

@@ -17,15 +17,20 @@ pytestmark = pytest.mark.gpu
 TOL = 1e-12   # both are FP64 reductions of the same quantities; only atomic order differs
 
 
-@pytest.mark.parametrize("prec", [FP32, FP64])
-def test_static_gauss_check_matches_diagnostics(prec):
+@pytest.mark.parametrize("prec,bc_x", [(FP32, 0), (FP64, 0), (FP32, 1), (FP64, 1)])
+def test_static_gauss_check_matches_diagnostics(prec, bc_x):
+    """Periodic box, and an open x (bc_x = 1: the face node x = n has no charge slot and
+    particles leave through both faces) where the charge scatter drops that node."""
     import torch
     from paper_2609_16575_gb300 import gbpic
 
     wl = W.thermal((24, 16, 16), 0.2, 8, 0.2, seed=41)
     E, B = plane_wave_fields(wl.n, wl.d, wl.dt)
+    if bc_x:   # an open x line holds n + 1 nodes of Ey, Ez, Bx: no field on the face
+        E = np.concatenate([E, np.zeros(E.shape[:-1] + (1,))], axis=-1)
+        B = np.concatenate([B, np.zeros(B.shape[:-1] + (1,))], axis=-1)
     P = W.quantize_fp32(wl.species[0].P) if prec == FP32 else wl.species[0].P
-    ctx = gbpic.Context(wl.n, wl.d, wl.dt, precision=prec, rho_ion=wl.rho_ion)
+    ctx = gbpic.Context(wl.n, wl.d, wl.dt, precision=prec, rho_ion=wl.rho_ion, bc_x=bc_x)
     ctx.set_fields(E, B)
     ctx.load_species_array(-1.0, 1.0, P)
     ctx.step(3)
