@@ -2,22 +2,25 @@
 """Benchmark of the GB300 explicit EM-PIC hot path (KEMPIC-3D cycle: Faraday half
 step, fused gather + Boris + zigzag deposit, Faraday half step, Ampere).
 
-Workload: thermal plasma, 128^3 periodic cells, dx = 0.2 c/w_p, 64 electrons per
-cell (134,217,728 particles) at uniform random positions with Maxwellian momenta
-u_th = 0.05 c, immobile ions, dt = 0.5 x Courant, FP32 bulk.  One step = one full
-PIC cycle over every particle and cell.  Prints one JSON line (rank 0).
+Headline workload: thermal plasma, 256^3 periodic cells, dx = 0.2 c/w_p, 32 electrons
+per cell (536,870,912 particles) at uniform random positions with Maxwellian momenta
+u_th = 0.1 c (drawn on the device: torch's Philox generator, seed 1238), immobile ions,
+dt = 0.5 x Courant, FP32 bulk; the FP64 GPU path runs the same inputs.  One step = one
+full PIC cycle over every particle and cell.  Prints one JSON line (rank 0).
 
   python bench.py [--gpus N] [--steps K] [--warmup W] [--impl gbpic|reference]
 
-Under torchrun every rank runs its own replica (the method has no exchange step on
-one GPU; replicas only) and the value is the sum over ranks of particle-steps
-divided by the slowest rank's time.
+Under torchrun every rank runs its own replica (the method has no exchange step on one
+GPU; replicas only) and the value is the sum over ranks of particle-steps divided by
+the slowest rank's time.
 """
 from __future__ import annotations
 
 import argparse
+import ctypes
 import hashlib
 import json
+import multiprocessing
 import os
 import statistics
 import subprocess
@@ -32,7 +35,12 @@ sys.path.insert(0, ROOT)
 
 METRIC = "particle pushes/s incl. deposit (FP32 vs FP64 GPU), % HBM roofline"
 UNIT = "particle-steps/s"
-WORKLOAD = dict(n=(128, 128, 128), d=0.2, ppc=64, u_th=0.05, seed=1235)
+# the headline: the largest single-GPU workload (256^3 x 32 per cell, u_th = 0.1); the
+# 128^3 x 64 thermal plasma (u_th = 0.05) is timed as an extra and selectable here
+WORKLOADS = {
+    "stress256": dict(name="stress256", n=(256, 256, 256), d=0.2, ppc=32, u_th=0.1, seed=1238),
+    "thermal128": dict(name="thermal128", n=(128, 128, 128), d=0.2, ppc=64, u_th=0.05, seed=1235),
+}
 # algorithmic bytes (what the method must move; sorting, ghosts and the fixed-point
 # width of J are overheads counted against the achieved fraction)
 PART_BYTES = {"f32": 60, "f64": 112}       # read cell + 3 offsets + 3 momenta + w, write all but w
@@ -43,23 +51,22 @@ STEP_GRID_BYTES = {"f32": 108, "f64": 216}  # + Yee: read E, B, J, write E, B, z
 def parse():
     p = argparse.ArgumentParser()
     p.add_argument("--gpus", type=int, default=1)
-    p.add_argument("--steps", type=int, default=50)
+    p.add_argument("--steps", type=int, default=20)
     p.add_argument("--warmup", type=int, default=5)
     p.add_argument("--impl", default="gbpic", choices=["gbpic", "reference"])
+    p.add_argument("--workload", default="stress256", choices=sorted(WORKLOADS))
     p.add_argument("--no-e2e", action="store_true")
     p.add_argument("--no-fp64", action="store_true")
     p.add_argument("--no-cpu-baseline", action="store_true")
     p.add_argument("--no-extra", action="store_true", help="skip the other workloads and the adjoint cost")
     p.add_argument("--adjoint-only", type=int, default=0,
                    help="only time the FP64 checkpointed adjoint of the differentiable run over this many steps")
-    p.add_argument("--stress", type=int, default=0,
-                   help="also run the 256^3 x 32 ppc precision-stress workload for this many steps (FP32 and FP64)")
     p.add_argument("--waveguide", type=int, default=0,
                    help="run the first N grids of the TE10 waveguide convergence study (FP64) and exit")
     p.add_argument("--waveguide-fp32", action="store_true", help="the waveguide study on the FP32 path")
-    p.add_argument("--small", action="store_true", help="32^3 cells instead of 128^3 (smoke)")
-    p.add_argument("--cells", type=int, default=0, help="cells per dimension (profiling cases); 0 = 128")
-    p.add_argument("--sort-every", type=int, default=0, help="tile re-sort cadence passed to the library")
+    p.add_argument("--small", action="store_true", help="32^3 cells instead of the headline grid (smoke)")
+    p.add_argument("--cells", type=int, default=0, help="cells per dimension of the headline workload (profiling)")
+    p.add_argument("--ppc", type=int, default=0, help="electrons per cell of the headline workload (profiling)")
     return p.parse_args()
 
 
@@ -150,30 +157,85 @@ class Clocks:
         return {"sm_mhz": statistics.median(sm), "sm_max_mhz": smax, "reasons": sorted(reasons), "samples": len(sm)}
 
 
-def make_workload(small, rank, cells=0):
-    from paper_2609_16575_gb300 import workloads as W
+def workload_spec(args):
+    """The headline workload, with the profiling overrides of the grid and ppc."""
+    spec = dict(WORKLOADS[args.workload])
+    if args.small:
+        spec["n"] = (32, 32, 32)
+    elif args.cells:
+        spec["n"] = (args.cells,) * 3
+    if args.ppc:
+        spec["ppc"] = args.ppc
+    return spec
 
-    n = (32, 32, 32) if small else (cells,) * 3 if cells else WORKLOAD["n"]
-    return W.thermal(n, WORKLOAD["d"], WORKLOAD["ppc"], WORKLOAD["u_th"], seed=WORKLOAD["seed"] + rank)
+
+def describe(spec):
+    n = spec["n"]
+    npart = n[0] * n[1] * n[2] * spec["ppc"]
+    return (f"thermal plasma {n[0]}x{n[1]}x{n[2]} periodic cells, dx={spec['d']}, {spec['ppc']} electrons per cell "
+            f"({npart:,}), u_th={spec['u_th']}, immobile ions, dt=0.5 Courant; inputs drawn on the device "
+            f"(Philox, seed {spec['seed']} + rank)")
 
 
-def cpu_baseline(steps=10, n=32):
-    """The FP64 oracle, as it stands, on a bounded sample of the same workload shape:
-    a 32^3-cell box at 64 per cell (2.1M particles), `steps` cycles, one host core."""
+def _oracle_sample(q, barrier, n, d, ppc, u_th, seed, warmup, steps):
+    """One host process: the FP64 oracle, as it stands, on an n^3 thermal sample."""
     import oracle
     from paper_2609_16575_gb300 import workloads as W
 
-    wl = W.thermal((n, n, n), WORKLOAD["d"], WORKLOAD["ppc"], WORKLOAD["u_th"], seed=WORKLOAD["seed"])
+    wl = W.thermal((n, n, n), d, ppc, u_th, seed=seed)
     sp = [oracle.Species(s.q, s.m, s.P) for s in wl.species]
     F = oracle.empty_fields(wl.n)
-    oracle.run(wl.n, wl.d, wl.dt, F, sp, 1)    # warm (page-in, library load)
-    t0 = time.perf_counter()
+    oracle.run(wl.n, wl.d, wl.dt, F, sp, max(int(warmup), 1))    # page-in, library load
+    barrier.wait()
+    t0 = time.monotonic()
     oracle.run(wl.n, wl.d, wl.dt, F, sp, steps)
-    dt = time.perf_counter() - t0
-    npart = wl.nparticles
-    return {"value": npart * steps / dt, "unit": UNIT, "cores": 1, "kind": "oracle",
-            "sample": f"thermal {n}^3 cells x 64 ppc ({npart} particles), {steps} cycles, FP64, single thread",
-            "seconds": round(dt, 2)}
+    t1 = time.monotonic()
+    q.put((wl.nparticles, steps, t0, t1))
+
+
+def oracle_rate(workers, spec, n=32, warmup=1, steps=10):
+    """Particle-steps/s of `workers` concurrent single-thread oracle processes (spawned,
+    each on its own seeded n^3 sample of the workload's ppc and u_th, all started
+    together behind a barrier): total particle-steps over the wall time from the first
+    start to the last end."""
+    import oracle
+
+    oracle.build()
+    mp = multiprocessing.get_context("spawn")
+    q, bar = mp.Queue(), mp.Barrier(workers)
+    procs = [mp.Process(target=_oracle_sample,
+                        args=(q, bar, n, spec["d"], spec["ppc"], spec["u_th"], spec["seed"] + i, warmup, steps))
+             for i in range(workers)]
+    for p in procs:
+        p.start()
+    res = [q.get(timeout=1800) for _ in procs]
+    for p in procs:
+        p.join()
+    wall = max(r[3] for r in res) - min(r[2] for r in res)
+    total = sum(r[0] * r[1] for r in res)
+    return total / wall, wall, res[0][0]
+
+
+def host_cores():
+    try:
+        return len(os.sched_getaffinity(0))
+    except AttributeError:
+        return os.cpu_count() or 1
+
+
+def cpu_baseline(spec, steps=10, n=32):
+    """The FP64 oracle, as it stands, on a bounded sample of the workload (a 32^3 box at
+    the workload's ppc and u_th, `steps` cycles): on one host core and on every core of
+    the host (one process per core, each on its own sample)."""
+    v1, w1, npart = oracle_rate(1, spec, n, 1, steps)
+    cores = host_cores()
+    vn, wn, _ = oracle_rate(cores, spec, n, 1, steps) if cores > 1 else (v1, w1, npart)
+    sample = (f"thermal {n}^3 cells x {spec['ppc']} ppc, u_th={spec['u_th']} ({npart:,} particles per process), "
+              f"{steps} cycles, FP64 oracle")
+    return {"value": vn, "unit": UNIT, "cores": cores, "kind": "oracle",
+            "sample": sample + f", {cores} processes (one per host core, nproc = {cores})",
+            "seconds": round(wn, 2),
+            "single_core": {"value": v1, "unit": UNIT, "cores": 1, "seconds": round(w1, 2)}}
 
 
 def time_steps(ctx, torch, steps):
@@ -192,14 +254,45 @@ def time_steps(ctx, torch, steps):
     return a.elapsed_time(b), kt
 
 
-def other_workloads(torch, peak):
-    """Throughput on the other workload shapes: the cold-plasma oscillation (16^3, 8 per
-    cell, FP64 and FP32) and the laser wakefield (512 x 128 x 128, open x, 8 per cell,
-    FP32)."""
+def kernel_table(kt):
+    return {k: {"launches": v[0], "ms": round(v[1], 3)} for k, v in kt.items() if v[0]}
+
+
+def thermal_context(torch, gbpic, W, spec, prec):
+    """A context holding the thermal workload `spec`, inputs drawn on the device."""
+    X, U, w, dt = W.thermal_device(torch, spec["n"], spec["d"], spec["ppc"], spec["u_th"], spec["seed"])
+    ctx = gbpic.Context(spec["n"], (spec["d"],) * 3, dt, precision=prec, rho_ion=1.0,
+                        device=torch.cuda.current_device())
+    ctx.load_species(-1.0, 1.0, X, U, w, True)
+    npart = int(w.shape[0])
+    del X, U, w
+    return ctx, npart
+
+
+def other_workloads(torch, peak, peak_kind):
+    """Throughput on the other workload shapes: the 128^3 x 64 thermal plasma (FP32, its
+    own roofline), the cold-plasma oscillation (16^3, 8 per cell, FP64 and FP32), the
+    laser wakefield (512 x 128 x 128, open x, 8 per cell, FP32) timed while the pulse
+    crosses the density ramp, and the thermal plasma with the current filter, with
+    Esirkepov's deposit and the wakefield with a moving window."""
     from paper_2609_16575_gb300 import gbpic
     from paper_2609_16575_gb300 import workloads as W
 
     out = {}
+    spec = WORKLOADS["thermal128"]
+    ncell = spec["n"][0] ** 3
+    ctx, npart = thermal_context(torch, gbpic, W, spec, gbpic.PIC_FP32)
+    time_steps(ctx, torch, 5)
+    steps = 20
+    ms, kt = time_steps(ctx, torch, steps)
+    ctx.close()
+    out["thermal128_f32"] = {
+        "value": npart * steps / (ms / 1e3), "unit": UNIT, "steps": steps, "ms_per_step": ms / steps,
+        "workload": describe(spec), "particles": npart,
+        "roofline": roofline(kt, "f32", npart, ncell, peak, peak_kind,
+                             committed_traffic("tile_push", "thermal128", npart)),
+        "yee": yee_line(kt, ncell, peak), "kernels": kernel_table(kt)}
+
     wl = W.cold_plasma(n=16)
     for prec, name in ((gbpic.PIC_FP64, "f64"), (gbpic.PIC_FP32, "f32")):
         ctx = gbpic.Context(wl.n, wl.d, wl.dt, precision=prec, rho_ion=wl.rho_ion)
@@ -211,61 +304,57 @@ def other_workloads(torch, peak):
                                           "ms_per_step": ms / 200, "particles": s.n,
                                           "note": "launch-bound: 32,768 particles fill 8 tiles"}
         ctx.close()
+
+    # the laser wakefield: 1000 cycles first (the pulse peak, injected at t = 2 FWHM, has
+    # then entered the density ramp), then 20 timed cycles
     wl = W.lwfa()
     ctx = gbpic.Context(wl.n, wl.d, wl.dt, precision=gbpic.PIC_FP32, rho_ion=wl.rho_ion, bc_x=1)
     ctx.set_laser(*wl.laser.as_tuple())
     s = wl.species[0]
     ctx.load_species_array(s.q, s.m, s.P, s.momenta_at_half_step)
-    time_steps(ctx, torch, 3)
+    del wl.species[0].P
+    ctx.step(1000)
+    ctx.sync()
+    n0 = ctx.diagnostics()["n_alive"]
     steps = 20
     ms, kt = time_steps(ctx, torch, steps)
-    npart = s.n
+    d1 = ctx.diagnostics()
     ncell = wl.n[0] * wl.n[1] * wl.n[2]
-    tl, tms = kt["tile_push"]
-    algo = PART_BYTES["f32"] * npart + TILE_GRID_BYTES["f32"] * ncell
-    achieved = algo / (tms / tl / 1e3) / 1e9
-    out["lwfa_512x128x128_f32"] = {"value": npart * steps / (ms / 1e3), "unit": UNIT, "steps": steps,
-                                   "ms_per_step": ms / steps, "particles": npart,
-                                   "tile_push": {"avg_launch_ms": tms / tl, "achieved_gbs": achieved,
-                                                 "frac": achieved / peak},
-                                   "yee": yee_line(kt, ncell, peak),
-                                   "note": "steps 4-23 of the run: the pulse has not reached the plasma yet"}
+    npart = 0.5 * (n0 + d1["n_alive"])
+    out["lwfa_512x128x128_f32"] = {
+        "value": npart * steps / (ms / 1e3), "unit": UNIT, "steps": steps, "ms_per_step": ms / steps,
+        "particles": [n0, d1["n_alive"]], "U_E": d1["U_E"], "K_half": d1["K_half"],
+        "roofline": roofline(kt, "f32", npart, ncell, peak, peak_kind, None),
+        "yee": yee_line(kt, ncell, peak), "kernels": kernel_table(kt),
+        "note": "cycles 1001-1020: the pulse (peak at t = 2 FWHM on the source plane) is crossing the density ramp"}
     ctx.close()
-    # the thermal workload with the compensated binomial current filter (1 pass per
-    # dimension and the compensator): the cost of the three filter passes per cycle
-    wl = W.thermal((128, 128, 128), WORKLOAD["d"], WORKLOAD["ppc"], WORKLOAD["u_th"], seed=WORKLOAD["seed"])
-    ctx = gbpic.Context(wl.n, wl.d, wl.dt, precision=gbpic.PIC_FP32, rho_ion=wl.rho_ion)
-    ctx.set_current_filter(1, True)
-    s = wl.species[0]
-    ctx.load_species_array(s.q, s.m, s.P, True)
-    del wl
-    time_steps(ctx, torch, 3)
-    steps = 10
-    ms, kt = time_steps(ctx, torch, steps)
-    out["thermal_128_filtered_f32"] = {
-        "value": s.n * steps / (ms / 1e3), "unit": UNIT, "steps": steps, "ms_per_step": ms / steps,
-        "particles": s.n, "filter": "1 binomial pass + compensator per dimension",
-        "kernels": {k: {"launches": v[0], "ms": round(v[1], 3)} for k, v in kt.items() if v[0]},
-        "note": "'other' holds the filter: 3 passes over J (3 x 8 bytes read and written per cell each)"}
-    ctx.close()
-    # the thermal workload with Esirkepov's deposit (the crossers' currents from their
-    # 3x3x3 supports, computed by the whole warp)
-    wl = W.thermal((128, 128, 128), WORKLOAD["d"], WORKLOAD["ppc"], WORKLOAD["u_th"], seed=WORKLOAD["seed"])
-    ctx = gbpic.Context(wl.n, wl.d, wl.dt, precision=gbpic.PIC_FP32, rho_ion=wl.rho_ion)
-    ctx.set_deposit(gbpic.PIC_DEPOSIT_ESIRKEPOV)
-    s = wl.species[0]
-    ctx.load_species_array(s.q, s.m, s.P, True)
-    del wl
-    time_steps(ctx, torch, 3)
-    steps = 10
-    ms, kt = time_steps(ctx, torch, steps)
-    out["thermal_128_esirkepov_f32"] = {
-        "value": s.n * steps / (ms / 1e3), "unit": UNIT, "steps": steps, "ms_per_step": ms / steps,
-        "particles": s.n, "deposit": "Esirkepov (CIC)",
-        "kernels": {k: {"launches": v[0], "ms": round(v[1], 3)} for k, v in kt.items() if v[0]}}
-    ctx.close()
-    # the same run with the moving window: a one-cell move every ceil(dx / dt) = 3 cycles
-    # from the first cycle on, the new column's plasma injected at each move
+
+    # the thermal plasma with the compensated binomial current filter (1 pass per
+    # dimension and the compensator) and with Esirkepov's deposit
+    for key, setup in (("thermal128_filtered_f32", lambda c: c.set_current_filter(1, True)),
+                       ("thermal128_esirkepov_f32", lambda c: c.set_deposit(gbpic.PIC_DEPOSIT_ESIRKEPOV))):
+        X, U, w, dt = W.thermal_device(torch, spec["n"], spec["d"], spec["ppc"], spec["u_th"], spec["seed"])
+        ctx = gbpic.Context(spec["n"], (spec["d"],) * 3, dt, precision=gbpic.PIC_FP32, rho_ion=1.0)
+        setup(ctx)
+        ctx.load_species(-1.0, 1.0, X, U, w, True)
+        npart = int(w.shape[0])
+        del X, U, w
+        time_steps(ctx, torch, 3)
+        steps = 10
+        ms, kt = time_steps(ctx, torch, steps)
+        ctx.close()
+        out[key] = {"value": npart * steps / (ms / 1e3), "unit": UNIT, "steps": steps, "ms_per_step": ms / steps,
+                    "particles": npart, "kernels": kernel_table(kt)}
+    out["thermal128_filtered_f32"]["note"] = ("'other' holds the filter: 1 binomial pass per dimension and the "
+                                              "compensator, each over J")
+    base = out["thermal128_f32"]["kernels"]["tile_push"]
+    esk = out["thermal128_esirkepov_f32"]["kernels"].get("tile_push")
+    if esk:
+        out["thermal128_esirkepov_f32"]["tile_push_over_zigzag"] = (esk["ms"] / esk["launches"]) / (
+            base["ms"] / base["launches"])
+
+    # the wakefield with the moving window: a one-cell move every ceil(dx / dt) = 3
+    # cycles from the first cycle on, the new column's plasma injected at each move
     wl = W.lwfa(window_start=0)
     ctx = gbpic.Context(wl.n, wl.d, wl.dt, precision=gbpic.PIC_FP32, rho_ion=wl.rho_ion, bc_x=1)
     ctx.set_laser(*wl.laser.as_tuple())
@@ -281,8 +370,8 @@ def other_workloads(torch, peak):
     out["lwfa_512x128x128_window_f32"] = {
         "value": npart * steps / (ms / 1e3), "unit": UNIT, "steps": steps, "ms_per_step": ms / steps,
         "particles": [n_before, n_after], "moves": m_after - m_before, "every": wl.window.every,
-        "kernels": {k: {"launches": v[0], "ms": round(v[1], 3)} for k, v in kt.items() if v[0]},
-        "note": "steps 4-33 with a moving window; 'other' holds the field shift, the injection, the "
+        "kernels": kernel_table(kt),
+        "note": "cycles 4-33 with a moving window; 'other' holds the field shift, the injection, the "
                 "laser sheet and the Mur faces"}
     ctx.close()
     return out
@@ -419,67 +508,27 @@ def adjoint_cost(torch, steps=200, precisions=("f64", "f32")):
     return out
 
 
-def stress_run(torch, steps):
-    """The precision-stress workload: 256^3 periodic cells, 32 electrons per cell
-    (536,870,912), u_th = 0.1, dx = 0.2, immobile ions.  Inputs are drawn on the device
-    (torch's Philox generator, seed 1238: uniform positions, Gaussian momenta) and loaded
-    through device pointers.  FP32 and FP64 paths from the same inputs: throughput,
-    relative change of the total energy U_E + U_B + K over `steps` cycles, and the
-    largest change of the Gauss residual."""
-    from paper_2609_16575_gb300 import gbpic
-    from paper_2609_16575_gb300 import workloads as W
-
-    n, ppc, d, u_th = 256, 32, 0.2, 0.1
-    npart = n ** 3 * ppc
-    gen = torch.Generator(device="cuda")
-    gen.manual_seed(1238)
-    X = torch.rand((3, npart), generator=gen, device="cuda", dtype=torch.float64) * n
-    X.clamp_(max=n * (1 - 2 ** -40))
-    U = torch.randn((3, npart), generator=gen, device="cuda", dtype=torch.float64) * u_th
-    w = torch.full((npart,), d ** 3 / ppc, device="cuda", dtype=torch.float64)
-    dt = W.courant_dt((d, d, d), 0.5)
-    out = {"workload": f"256^3 periodic, 32 ppc ({npart:,} electrons), u_th=0.1, dx=0.2, dt=0.5 Courant, "
-                       f"{steps} steps, inputs drawn on the device (Philox, seed 1238)"}
-    for prec, name in ((gbpic.PIC_FP32, "f32"), (gbpic.PIC_FP64, "f64")):
-        ctx = gbpic.Context((n, n, n), (d, d, d), dt, precision=prec, rho_ion=1.0)
-        ctx.load_species(-1.0, 1.0, X, U, w, True)
-        d0 = ctx.diagnostics()
-        torch.cuda.synchronize()
-        st = torch.cuda.current_stream()
-        a, b = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
-        a.record(st)
-        ctx.step(steps)
-        b.record(st)
-        torch.cuda.synchronize()
-        ms = a.elapsed_time(b)
-        d1 = ctx.diagnostics()
-        e0 = d0["U_E"] + d0["U_B"] + d0["K_half"]
-        e1 = d1["U_E"] + d1["U_B"] + d1["K_half"]
-        out[name] = {"value": npart * steps / (ms / 1e3), "unit": UNIT, "ms_per_step": ms / steps,
-                     "energy_rel_change": (e1 - e0) / e0, "gauss_change_max": d1["gauss_change_max"],
-                     "rho_max": d1["rho_max"], "n_alive": d1["n_alive"]}
-        ctx.close()
-        del ctx
-    del X, U, w
-    return out
-
-
-def arm_config(n, npart, ncell, world, sort_every):
+def arm_config(spec, world):
     """The workload description both arms print."""
-    return {"workload": (f"thermal plasma {n}^3 periodic, dx=0.2, 64 ppc ({npart:,} electrons), "
-                         "u_th=0.05, immobile ions, dt=0.5 Courant"),
-            "particles_per_gpu": npart, "cells": ncell, "precision": "fp32 bulk, fp64 reductions",
+    n = spec["n"]
+    npart = n[0] * n[1] * n[2] * spec["ppc"]
+    return {"workload": describe(spec), "cells": n[0] * n[1] * n[2], "particles_per_gpu": npart,
+            "precision": "fp32 bulk (the fp64 path on the same inputs under 'fp64'), fp64 reductions",
             "parallelism": f"replicas x{world}",
-            "l2": "inputs larger than L2 (particle SoA 4.3 GB per GPU)"}
+            "l2": f"inputs larger than L2 (particle SoA {npart * 32 * 2 / 1e9:.1f} GB per GPU, double-buffered)"}
 
 
-# Yee kernels per cell and step (FP32): two Faraday half steps (read E, B; write B: 36 B
-# each) and Ampere (read E, B and the 64-bit J; write E; clear J: 84 B)
-YEE_BYTES_PER_CELL = 2 * 36 + 84
+# Yee bytes per cell and step the method must move (FP32): read E, B and J, write E and
+# B, clear J = 72 B.  The implementation moves 156 B: two Faraday half steps (read E, B;
+# write B: 36 B each) and Ampere (read E, B and the 64-bit fixed-point J; write E; clear
+# J: 84 B).
+YEE_BYTES_PER_CELL = 72
+YEE_IMPL_BYTES_PER_CELL = 2 * 36 + 84
 
 
 def yee_line(kt, ncell, peak):
-    """Yee cell updates per second from the CUDA-event times of the field kernels."""
+    """Yee cell updates per second from the CUDA-event times of the field kernels, with
+    the HBM fraction of the method's 72 B per cell."""
     fl, fms = kt.get("faraday_half", (0, 0.0))
     al, ams = kt.get("ampere", (0, 0.0))
     if not al or not fl:
@@ -488,34 +537,27 @@ def yee_line(kt, ncell, peak):
     gbs = YEE_BYTES_PER_CELL * ncell / per_step_s / 1e9
     return {"cell_updates_per_s": ncell / per_step_s, "ms_per_step": per_step_s * 1e3,
             "bytes_per_cell": YEE_BYTES_PER_CELL, "achieved_gbs": gbs, "frac_of_hbm": gbs / peak,
-            "note": "fields (about 105 MB at 128^3) largely stay in the 129 MB L2 between kernels"}
+            "implementation_bytes_per_cell": YEE_IMPL_BYTES_PER_CELL,
+            "note": "three kernels per step (two Faraday half steps and Ampere with the J clear)"}
 
 
 def run_reference(args):
+    """The reference arm: the FP64 oracle, as it stands, on the host's cores (one
+    process per core); each step is one oracle cycle of every process over its own 32^3
+    sample of the headline workload."""
     rank = int(os.environ.get("RANK", "0"))
     if rank != 0:
         return 0
-    import oracle
-
-    oracle.build()
-    from paper_2609_16575_gb300 import workloads as W
-
-    # each step: one oracle cycle over a 16^3-cell box at 64 per cell (262,144 particles)
-    wl = W.thermal((16, 16, 16), WORKLOAD["d"], WORKLOAD["ppc"], WORKLOAD["u_th"], seed=WORKLOAD["seed"])
-    sp = [oracle.Species(s.q, s.m, s.P) for s in wl.species]
-    F = oracle.empty_fields(wl.n)
-    oracle.run(wl.n, wl.d, wl.dt, F, sp, args.warmup)
-    t0 = time.perf_counter()
-    oracle.run(wl.n, wl.d, wl.dt, F, sp, args.steps)
-    dt = time.perf_counter() - t0
-    value = wl.nparticles * args.steps / dt
-    sample = f"thermal 16^3 cells x 64 ppc ({wl.nparticles} particles) per step, FP64 oracle, single thread"
+    spec = workload_spec(args)
+    cores = host_cores()
+    value, wall, npart = oracle_rate(cores, spec, 32, args.warmup, args.steps)
+    sample = (f"per step: one FP64 oracle cycle in each of {cores} processes (one per host core, nproc = {cores}), "
+              f"each on its own thermal 32^3 x {spec['ppc']} ppc sample ({npart:,} particles), u_th={spec['u_th']}")
     line = {"impl": "reference", "metric": METRIC, "value": value, "unit": UNIT, "n_gpus": args.gpus,
-            "steps": args.steps, "warmup": args.warmup, "ms_per_step": dt / args.steps * 1e3,
+            "steps": args.steps, "warmup": args.warmup, "ms_per_step": wall / args.steps * 1e3,
             "higher_is_better": True, "scaling": "weak", "vs_baseline": None, "dtype": "f64", "data": "synthetic",
-            "config": arm_config(WORKLOAD["n"][0], WORKLOAD["ppc"] * WORKLOAD["n"][0] ** 3, WORKLOAD["n"][0] ** 3,
-                                 args.gpus, args.sort_every),
-            "cpu_baseline": {"value": value, "unit": UNIT, "cores": 1, "kind": "oracle", "sample": sample},
+            "config": arm_config(spec, args.gpus),
+            "cpu_baseline": {"value": value, "unit": UNIT, "cores": cores, "kind": "oracle", "sample": sample},
             "e2e": {"value": value, "unit": UNIT, "h2d_bytes_per_step": 0, "d2h_bytes_per_step": 0}}
     print(json.dumps(line), flush=True)
     return 0
@@ -569,14 +611,26 @@ FP64_OPS_PER_PARTICLE = 316.5
 FP64_PEAK_TFLOPS = 2 * 152 * 2.07e9 * 2 / 1e12
 
 
-def fp64_alu_roofline(kt, n_particles):
+def fp64_alu_roofline(kt, n_particles, peak=None, peak_kind=None):
+    """FP64 operations per launch of the FP64 tile kernel over its average launch time,
+    against `peak` TFLOP/s (default: the unit-count figure above)."""
+    if peak is None:
+        peak, peak_kind = FP64_PEAK_TFLOPS, "derived: 2 DFMA/clock/SM x 152 SMs x 2.07 GHz"
     launches, ms = kt["tile_push"]
     avg_s = ms / max(launches, 1) / 1e3
     achieved = FP64_OPS_PER_PARTICLE * n_particles / avg_s / 1e12
-    return {"bound": "alu", "achieved": achieved, "peak": FP64_PEAK_TFLOPS, "unit": "TFLOP/s",
-            "frac": achieved / FP64_PEAK_TFLOPS, "kernel": "k_tile_push<double>",
-            "peak_kind": "derived: 2 DFMA/clock/SM x 152 SMs x 2.07 GHz (a DFMA probe reached 1.02 TFLOP/s)",
+    return {"bound": "alu", "achieved": achieved, "peak": peak, "unit": "TFLOP/s",
+            "frac": achieved / peak, "kernel": "k_tile_push<double>", "peak_kind": peak_kind,
             "ops_per_particle": FP64_OPS_PER_PARTICLE}
+
+
+def measured_fp64_peak(gbpic, dev):
+    """TFLOP/s of the library's FP64 FMA probe (8 independent DFMA chains per thread,
+    every SM busy), or None."""
+    try:
+        return gbpic.probe_fp64_rate(dev) / 1e12
+    except Exception:
+        return None
 
 
 def roofline(kt, dtype, n_particles, ncell, peak, peak_kind, traffic):
@@ -587,6 +641,10 @@ def roofline(kt, dtype, n_particles, ncell, peak, peak_kind, traffic):
     return {"bound": "hbm", "achieved": achieved, "peak": peak, "unit": "GB/s", "frac": achieved / peak,
             "traffic": traffic, "kernel": "k_tile_push", "peak_kind": f"{peak_kind} hbm_gbs (copy)",
             "algorithmic_bytes_per_launch": algo, "avg_launch_ms": avg_s * 1e3}
+
+
+def energy(d):
+    return d["U_E"] + d["U_B"] + d["K_half"]
 
 
 def run_gbpic(args):
@@ -607,71 +665,85 @@ def run_gbpic(args):
 
     __graft_entry__.build()
     from paper_2609_16575_gb300 import gbpic
+    from paper_2609_16575_gb300 import workloads as W
 
-    wl = make_workload(args.small, rank, args.cells)
-    P = wl.species[0].P
-    npart = P.shape[1]
-    ncell = wl.ncells
+    spec = workload_spec(args)
+    n, d, ppc = spec["n"], (spec["d"],) * 3, spec["ppc"]
+    ncell = n[0] * n[1] * n[2]
     peak, peak_kind = peaks()
     dev = torch.cuda.current_device()
+    # this rank's inputs, drawn on the device; both precisions and the end-to-end run
+    # start from them
+    X, U, w, dt = W.thermal_device(torch, n, spec["d"], ppc, spec["u_th"], spec["seed"] + rank)
+    npart = int(w.shape[0])
 
     # --- FP32, inputs resident in HBM
-    ctx = gbpic.Context(wl.n, wl.d, wl.dt, precision=gbpic.PIC_FP32, rho_ion=wl.rho_ion, device=dev,
-                        sort_every=args.sort_every)
-    ctx.set_fields(None, None)
-    ctx.load_species_array(-1.0, 1.0, P)
+    ctx = gbpic.Context(n, d, dt, precision=gbpic.PIC_FP32, rho_ion=1.0, device=dev)
+    ctx.load_species(-1.0, 1.0, X, U, w, True)
+    d0 = ctx.diagnostics()
     ctx.step(args.warmup)
     ctx.sync()
     with Clocks(dev) as clk:
         ms, launches, kt = timed_steps(ctx, torch, args.steps, dist)
     clocks = clk.summary()
-    diag = ctx.diagnostics()
-    ctx.sync()
-    if diag["n_alive"] != npart:
-        raise RuntimeError(f"particles lost: {diag['n_alive']} of {npart}")
+    d1 = ctx.diagnostics()
     ctx.close()
     del ctx
+    if d1["n_alive"] != npart:
+        raise RuntimeError(f"particles lost: {d1['n_alive']} of {npart}")
     ms_all, value = replica_rate(ms, npart, args.steps, dist)
-    wk = f"thermal{wl.n[0]}"
-    traffic = committed_traffic("tile_push", wk, npart)
+    traffic = committed_traffic("tile_push", spec["name"], npart)
     rl = roofline(kt, "f32", npart, ncell, peak, peak_kind, traffic)
-    step_bytes = PART_BYTES["f32"] + STEP_GRID_BYTES["f32"] / WORKLOAD["ppc"]
-    kernels = {k: {"launches": v[0], "ms": round(v[1], 3)} for k, v in kt.items() if v[0]}
+    step_bytes = PART_BYTES["f32"] + STEP_GRID_BYTES["f32"] / ppc
+    f32_checks = {"cycles": args.warmup + args.steps, "energy_rel_change": (energy(d1) - energy(d0)) / energy(d0),
+                  "gauss_change_max": d1["gauss_change_max"], "rho_max": d1["rho_max"]}
 
-    # --- FP64 GPU path on the same workload
+    # --- FP64 GPU path on the same inputs
     fp64 = None
     if not args.no_fp64:
-        k64 = max(3, args.steps // 10)
-        ctx = gbpic.Context(wl.n, wl.d, wl.dt, precision=gbpic.PIC_FP64, rho_ion=wl.rho_ion, device=dev)
-        ctx.set_fields(None, None)
-        ctx.load_species_array(-1.0, 1.0, P)
+        k64 = max(3, args.steps // 4)
+        ctx = gbpic.Context(n, d, dt, precision=gbpic.PIC_FP64, rho_ion=1.0, device=dev)
+        ctx.load_species(-1.0, 1.0, X, U, w, True)
+        e0 = ctx.diagnostics()
         ctx.step(2)
         ctx.sync()
         ms64, _, kt64 = timed_steps(ctx, torch, k64, dist)
+        e1 = ctx.diagnostics()
         ctx.close()
         del ctx
-        v64 = npart * k64 / (ms64 / 1e3)
-        fp64 = {"value": v64 * world, "unit": UNIT, "steps": k64, "ms_per_step": ms64 / k64,
+        if e1["n_alive"] != npart:
+            raise RuntimeError(f"FP64 path lost particles: {e1['n_alive']} of {npart}")
+        ms64, v64 = replica_rate(ms64, npart, k64, dist)
+        fpk = measured_fp64_peak(gbpic, dev)
+        fp64 = {"value": v64, "unit": UNIT, "steps": k64, "ms_per_step": ms64 / k64,
                 "roofline": roofline(kt64, "f64", npart, ncell, peak, peak_kind, None),
-                "alu_roofline": fp64_alu_roofline(kt64, npart),
-                "step_hbm_frac": v64 * (PART_BYTES["f64"] + STEP_GRID_BYTES["f64"] / WORKLOAD["ppc"]) / 1e9 / peak}
+                "alu_roofline": fp64_alu_roofline(
+                    kt64, npart, *((fpk, "measured: the library's DFMA probe (pic_probe_fp64_rate) on this GPU")
+                                   if fpk else (None, None))),
+                "step_hbm_frac": v64 / world * (PART_BYTES["f64"] + STEP_GRID_BYTES["f64"] / ppc) / 1e9 / peak,
+                "kernels": kernel_table(kt64),
+                "checks": {"cycles": 2 + k64, "energy_rel_change": (energy(e1) - energy(e0)) / energy(e0),
+                           "gauss_change_max": e1["gauss_change_max"]}}
 
-    # --- end to end through the public API: host (pinned) inputs in, diagnostics out
+    # --- end to end through the public API: the FP64 particle arrays from pinned host
+    # memory into a new context, the steps, the FP64 diagnostics back to the host
     e2e = None
     if not args.no_e2e:
-        pinned = torch.empty(P.shape, dtype=torch.float64, pin_memory=True)
-        pinned.numpy()[:] = P
-        Ph = pinned.numpy()
+        host = [torch.empty(t.shape, dtype=torch.float64, pin_memory=True) for t in (X, U, w)]
+        for h, t in zip(host, (X, U, w)):
+            h.copy_(t)
+        del X, U, w
         torch.cuda.synchronize()
+        torch.cuda.empty_cache()
+        Xh, Uh, wh = (h.numpy() for h in host)
         if dist is not None:
             dist.barrier()
+        torch.cuda.synchronize()
         t0 = time.perf_counter()
-        ctx = gbpic.Context(wl.n, wl.d, wl.dt, precision=gbpic.PIC_FP32, rho_ion=wl.rho_ion, device=dev)
-        ctx.set_fields(None, None)
-        ctx.load_species_array(-1.0, 1.0, Ph)
+        ctx = gbpic.Context(n, d, dt, precision=gbpic.PIC_FP32, rho_ion=1.0, device=dev)
+        ctx.load_species(-1.0, 1.0, Xh, Uh, wh, True)
         ctx.step(args.steps)
         d_e2e = ctx.diagnostics()
-        torch.cuda.synchronize()
         t_e2e = time.perf_counter() - t0
         ctx.close()
         del ctx
@@ -679,39 +751,41 @@ def run_gbpic(args):
             t = torch.tensor([t_e2e], device="cuda", dtype=torch.float64)
             dist.all_reduce(t, op=dist.ReduceOp.MAX)
             t_e2e = float(t.item())
-        ntile = (wl.n[0] // 8) * (wl.n[1] // 8) * (wl.n[2] // 8)
+        ntile = (n[0] // 8) * (n[1] // 8) * (n[2] // 8)
+        # particle arrays + the loader's per-tile tables up; its histogram, counters and
+        # the diagnostics down
         h2d = 7 * 8 * npart + 4 * ntile * 512 + 12 * ntile
-        d2h = 4 * ntile * 512 + 8 * 8 + 4 * ntile
+        d2h = 4 * ntile * 512 + 8 * 8 + 4 * ntile + ctypes.sizeof(gbpic.pic_diag)
         e2e = {"value": npart * world * args.steps / t_e2e, "unit": UNIT,
                "h2d_bytes_per_step": h2d // args.steps, "d2h_bytes_per_step": d2h // args.steps,
-               "includes": "context creation, H2D of the FP64 particle arrays from pinned memory, tile sort, "
-                           f"{args.steps} steps, FP64 diagnostics and their D2H",
+               "seconds": t_e2e,
+               "includes": "context creation, H2D of the FP64 particle arrays from pinned host memory, tile sort, "
+                           f"{args.steps} steps, FP64 diagnostics and their D2H (bytes per step = per run / steps)",
                "check_n_alive": d_e2e["n_alive"] == npart}
-        del pinned
+        del host, Xh, Uh, wh
+    else:
+        del X, U, w
+    torch.cuda.empty_cache()
 
     cpu = None
     if rank == 0 and world == 1 and not args.no_cpu_baseline:
-        cpu = cpu_baseline()
-    extra, adj, stress = None, None, None
+        cpu = cpu_baseline(spec)
+    extra, adj = None, None
     if rank == 0 and world == 1 and not args.no_extra:
-        extra = other_workloads(torch, peak)
+        extra = other_workloads(torch, peak, peak_kind)
         adj = adjoint_cost(torch)
-    if rank == 0 and world == 1 and args.stress > 0:
-        stress = stress_run(torch, args.stress)
 
     if rank == 0:
         line = {"metric": METRIC, "value": value, "unit": UNIT, "n_gpus": world, "steps": args.steps,
                 "warmup": args.warmup, "ms_per_step": ms_all / args.steps, "higher_is_better": True,
                 "scaling": "weak", "vs_baseline": None, "dtype": "f32", "data": "synthetic",
-                "config": arm_config(wl.n[0], npart, ncell, world, args.sort_every),
+                "config": arm_config(spec, world),
                 "roofline": rl,
                 "step_hbm_frac": value / world * step_bytes / 1e9 / peak,
                 "cell_steps_per_s": ncell * world * args.steps / (ms_all / 1e3),
-                "yee": yee_line(kt, ncell * world, peak),
-                "kernels": kernels, "gpu_launches": launches, "clocks": clocks, "e2e": e2e,
-                "cpu_baseline": cpu, "fp64": fp64, "other_workloads": extra, "adjoint": adj}
-        if stress is not None:
-            line["precision_stress"] = stress
+                "yee": yee_line(kt, ncell, peak),
+                "kernels": kernel_table(kt), "gpu_launches": launches, "clocks": clocks, "checks": f32_checks,
+                "e2e": e2e, "cpu_baseline": cpu, "fp64": fp64, "other_workloads": extra, "adjoint": adj}
         print(json.dumps(line), flush=True)
     if dist is not None:
         dist.destroy_process_group()

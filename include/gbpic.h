@@ -375,6 +375,12 @@ pic_status pic_adjoint_run(pic_ctx* ctx, int32_t nsteps, int32_t ckpt_every, con
  * allocator.  Synchronises. */
 pic_status pic_gauss_check_static(pic_ctx* ctx, double* gauss_max, double* rho_max);
 
+/* Measurement utility (the paper has no counterpart): the FP64 fused multiply-add rate
+ * of the given device in FLOP/s (2 per FMA), from a kernel of independent FMA chains
+ * timed with CUDA events (about 0.1 s; synchronises the device's default stream).
+ * PIC_ERR_ARG for a null output, PIC_ERR_NO_DEVICE without that device. */
+pic_status pic_probe_fp64_rate(int32_t device, double* flops_per_s);
+
 /* Total kernel launches the library has issued on this context. */
 int64_t pic_launch_count(const pic_ctx* ctx);
 

@@ -127,6 +127,7 @@ def lib():
                                           ctypes.c_int32]
             L.pic_set_deposit.argtypes = [P, ctypes.c_int32]
             L.pic_set_wait_limit.argtypes = [P, ctypes.c_int32]
+            L.pic_probe_fp64_rate.argtypes = [ctypes.c_int32, ctypes.POINTER(ctypes.c_double)]
             L.pic_save_state.argtypes = [P, ctypes.POINTER(ctypes.c_void_p), ctypes.POINTER(ctypes.c_size_t)]
             L.pic_load_state.argtypes = [P, ctypes.c_void_p, ctypes.c_size_t]
             L.pic_free_state.argtypes = [ctypes.c_void_p]
@@ -149,7 +150,7 @@ def lib():
                          "pic_gauss_check_static", "pic_set_laser", "pic_set_moving_window",
                          "pic_set_current_filter", "pic_set_pec", "pic_set_port", "pic_set_deposit",
                          "pic_save_state", "pic_load_state", "pic_set_background", "pic_adjoint_run",
-                         "pic_set_wait_limit"):
+                         "pic_set_wait_limit", "pic_probe_fp64_rate"):
                 getattr(L, name).restype = ctypes.c_int
             _lib = L
     return _lib
@@ -224,6 +225,13 @@ def pic_init_grid(n, d, dt, precision=PIC_FP32, rho_ion=0.0, device=0, stream=No
     out = ctypes.c_void_p()
     _check(None, lib().pic_init_grid(ctypes.byref(desc), ctypes.byref(out)), "pic_init_grid")
     return out, (desc, allocator)
+
+
+def probe_fp64_rate(device=0):
+    """FP64 FMA rate of the device in FLOP/s (pic_probe_fp64_rate)."""
+    v = ctypes.c_double()
+    _check(None, lib().pic_probe_fp64_rate(int(device), ctypes.byref(v)), "pic_probe_fp64_rate")
+    return v.value
 
 
 class Context:

@@ -231,3 +231,23 @@ def wrap_positions(P: np.ndarray, n) -> np.ndarray:
         Q[dim] = np.mod(Q[dim], n[dim])
         Q[dim][Q[dim] >= n[dim]] = 0.0
     return Q
+
+
+def thermal_device(torch, n, d=0.2, ppc=32, u_th=0.1, seed=1238, courant=0.5, device="cuda"):
+    """The thermal plasma drawn on the device with torch's Philox generator (for
+    workloads too large to draw and upload from the host in reasonable time): positions
+    uniform in [0, n_d) per dimension, then momenta N(0, u_th^2) per component (at the
+    half step), weights d^3 / ppc.  Returns (X (3, N), U (3, N), w (N,), dt) as float64
+    tensors on `device`; the same seed gives the same numbers on the same device type."""
+    nn = tuple(int(v) for v in (n if hasattr(n, "__len__") else (n, n, n)))
+    npart = nn[0] * nn[1] * nn[2] * int(ppc)
+    gen = torch.Generator(device=device)
+    gen.manual_seed(int(seed))
+    X = torch.rand((3, npart), generator=gen, device=device, dtype=torch.float64)
+    for dim in range(3):
+        X[dim].mul_(nn[dim])
+        # rounding of the product can give exactly n_d: fold it back into the box
+        X[dim].masked_fill_(X[dim] >= nn[dim], 0.0)
+    U = torch.randn((3, npart), generator=gen, device=device, dtype=torch.float64).mul_(u_th)
+    w = torch.full((npart,), d ** 3 / ppc, device=device, dtype=torch.float64)
+    return X, U, w, courant_dt((d, d, d), courant)

@@ -106,6 +106,7 @@ def test_new_entry_points_reject_a_null_context(L):
     assert L.pic_set_port(None, None) == 1
     assert L.pic_set_deposit(None, 1) == 1
     assert L.pic_set_wait_limit(None, 1) == 1
+    assert L.pic_probe_fp64_rate(0, None) == 1
     blob, size = ctypes.c_void_p(), ctypes.c_size_t()
     assert L.pic_save_state(None, ctypes.byref(blob), ctypes.byref(size)) == 1
     assert L.pic_load_state(None, None, 0) == 1
