@@ -40,6 +40,9 @@ __device__ __forceinline__ int key_of(const Geom& g, const int c[3]) {
 template <typename T>
 __global__ void k_keys(Geom g, const double* X, const double* w, long long n, int* hist, int* bad,
                        unsigned long long* wmax_bits) {
+    // the largest weight: a thread's own maximum, then the warp's, then one atomic per
+    // warp (positive doubles order like their bit patterns)
+    unsigned long long wbits = 0;
     for (long long p = blockIdx.x * (long long)blockDim.x + threadIdx.x; p < n; p += (long long)gridDim.x * blockDim.x) {
         const double Xp[3] = {X[p], X[n + p], X[2 * n + p]};
         int c[3];
@@ -50,8 +53,14 @@ __global__ void k_keys(Geom g, const double* X, const double* w, long long n, in
             continue;
         }
         atomicAdd(hist + key_of(g, c), 1);
-        atomicMax(wmax_bits, (unsigned long long)__double_as_longlong(wp));
+        const unsigned long long b = (unsigned long long)__double_as_longlong(wp);
+        wbits = b > wbits ? b : wbits;
     }
+    for (int o = 16; o > 0; o >>= 1) {
+        const unsigned long long v = __shfl_xor_sync(0xffffffffu, wbits, o);
+        wbits = v > wbits ? v : wbits;
+    }
+    if ((threadIdx.x & 31) == 0 && wbits) atomicMax(wmax_bits, wbits);
 }
 
 template <typename T>
