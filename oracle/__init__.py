@@ -67,10 +67,11 @@ def lib():
                                          ctypes.c_long, ctypes.c_int, _dp, _dp]
             L.or_zigzag.argtypes = [_ip, _dp, ctypes.c_double, ctypes.c_double, _dp, _dp, _dp]
             L.or_rho.argtypes = [_ip, _dp, ctypes.c_double, ctypes.c_long, _dp, _dp, _dp]
+            L.or_rho_tsc.argtypes = [_ip, _dp, ctypes.c_double, ctypes.c_long, _dp, _dp, _dp]
             L.or_divergence.argtypes = [_ip, _dp, _dp, _dp]
             L.or_divergence_b.argtypes = [_ip, _dp, _dp, _dp]
             L.or_backpush.argtypes = [_ip, _dp, ctypes.c_double, _dp, _dp, ctypes.c_double, ctypes.c_double,
-                                      ctypes.c_long, _dp, _dp]
+                                      ctypes.c_long, _dp, _dp, ctypes.c_int]
             L.or_step.argtypes = [_ip, _dp, ctypes.c_double, _dp, ctypes.c_int, _dp, _lp,
                                   ctypes.POINTER(_dp), ctypes.POINTER(_dp), _dp, ctypes.c_long, _dp, _dp, _dp]
             L.or_run.argtypes = [_ip, _dp, ctypes.c_double, _dp, ctypes.c_int, _dp, _lp,
@@ -78,8 +79,10 @@ def lib():
                                  _dp]
             L.or_current_filter.argtypes = [_ip, _dp, _dp, ctypes.c_int, ctypes.c_int]
             L.or_esirkepov.argtypes = [_ip, _dp, ctypes.c_double, ctypes.c_double, _dp, _dp, _dp]
+            L.or_esirkepov_tsc.argtypes = [_ip, _dp, ctypes.c_double, ctypes.c_double, _dp, _dp, _dp]
+            L.or_gather_tsc.argtypes = [_ip, _dp, _dp, _dp, _dp, _dp, _dp]
             L.or_push.argtypes = [_ip, _dp, ctypes.c_double, _dp, _dp, ctypes.c_double, ctypes.c_double, ctypes.c_long,
-                                  _dp, _dp, _dp, ctypes.c_int]
+                                  _dp, _dp, _dp, ctypes.c_int, ctypes.c_int]
             L.or_push.restype = ctypes.c_double
             L.or_window_shift.argtypes = [_ip, _dp, _dp, ctypes.c_int, _lp, ctypes.POINTER(_dp), ctypes.POINTER(_dp)]
             L.or_gauss_x.argtypes = [_ip, _dp, _dp, _dp]
@@ -160,13 +163,15 @@ def ampere(n, d, dt, E, B, J):
     lib().or_ampere(pn, pd, dt, _p(E), _p(B), _p(J))
 
 
-def gather(n, d, E, B, X):
-    """Staggered CIC interpolation of E and B at one position X (cell units), section 2.5."""
+def gather(n, d, E, B, X, shape=1):
+    """Staggered interpolation of E and B at one position X (cell units), section 2.5:
+    CIC (shape 1) or the quadratic TSC weights (shape 2)."""
     n, d, pn, pd = _grid(n, d)
     X = np.ascontiguousarray(X, dtype=np.float64)
     Ep = np.zeros(3)
     Bp = np.zeros(3)
-    lib().or_gather(pn, pd, _p(E), _p(B), _p(X), _p(Ep), _p(Bp))
+    fn = lib().or_gather_tsc if shape == 2 else lib().or_gather
+    fn(pn, pd, _p(np.ascontiguousarray(E)), _p(np.ascontiguousarray(B)), _p(X), _p(Ep), _p(Bp))
     return Ep, Bp
 
 
@@ -203,22 +208,31 @@ def esirkepov(n, d, dt, qw, X1, X2, J):
     lib().or_esirkepov(pn, pd, dt, qw, _p(f(X1)), _p(f(X2)), _p(J))
 
 
-def push(n, d, dt, E, Bn, species, J, esirkepov=False):
+def esirkepov_tsc(n, d, dt, qw, X1, X2, J):
+    """Accumulate Esirkepov's current of one straight move X1 -> X2 (cell units, X2
+    unwrapped, under one cell per dimension) into J, with the quadratic (TSC) shape."""
+    n, d, pn, pd = _grid(n, d)
+    f = lambda v: np.ascontiguousarray(v, dtype=np.float64)
+    lib().or_esirkepov_tsc(pn, pd, dt, qw, _p(f(X1)), _p(f(X2)), _p(J))
+
+
+def push(n, d, dt, E, Bn, species, J, esirkepov=False, shape=1):
     """The particle part of one cycle for one species (gather of E^n and B^n = ``Bn``,
     Boris, move, deposit into J), in place; returns the species' kinetic energy at the
     cycle's time level.  The same code as inside ``run``."""
     n_, d_, pn, pd = _grid(n, d)
     return lib().or_push(pn, pd, dt, _p(np.ascontiguousarray(E)), _p(np.ascontiguousarray(Bn)), species.q, species.m,
-                         species.n, _p(species.Q), _p(species.C), _p(J), int(bool(esirkepov)))
+                         species.n, _p(species.Q), _p(species.C), _p(J), int(bool(esirkepov)), int(shape))
 
 
-def rho(n, d, species, rho_ion=0.0):
-    """Node charge density: CIC of every species plus the uniform background rho_ion."""
-    shape = field_shape(n)
+def rho(n, d, species, rho_ion=0.0, shape=1):
+    """Node charge density: CIC (shape 1) or TSC (shape 2) of every species plus the
+    uniform background rho_ion."""
     n, d, pn, pd = _grid(n, d)
-    out = np.full(shape, float(rho_ion))
+    out = np.full(field_shape(n), float(rho_ion))
+    fn = lib().or_rho_tsc if shape == 2 else lib().or_rho
     for s in species:
-        lib().or_rho(pn, pd, s.q, s.n, _p(s.Q), _p(s.C), _p(out))
+        fn(pn, pd, s.q, s.n, _p(s.Q), _p(s.C), _p(out))
     return out
 
 
@@ -240,11 +254,12 @@ def divergence_b(n, d, B):
     return out
 
 
-def backpush(n, d, dt, E, Bhalf, species):
-    """u^0 -> u^{-1/2} by a backward Boris half step with E^0, B^0 (in place)."""
+def backpush(n, d, dt, E, Bhalf, species, shape=1):
+    """u^0 -> u^{-1/2} by a backward Boris half step with E^0, B^0 (in place), the
+    fields gathered with the CIC (shape 1) or TSC (shape 2) weights."""
     n, d, pn, pd = _grid(n, d)
     lib().or_backpush(pn, pd, dt, _p(np.ascontiguousarray(E)), _p(np.ascontiguousarray(Bhalf)),
-                      species.q, species.m, species.n, _p(species.Q), _p(species.C))
+                      species.q, species.m, species.n, _p(species.Q), _p(species.C), int(shape))
 
 
 def run(n, d, dt, F, species, nsteps=1, step0=0, laser=None, current_filter=None, guide=None):
@@ -255,9 +270,10 @@ def run(n, d, dt, F, species, nsteps=1, step0=0, laser=None, current_filter=None
     (a0, omega, w0, tau_fwhm, t_peak, i_s, yc, zc) adds the soft laser sheet;
     ``current_filter`` = (passes, compensate) filters the particle current each cycle
     (see ``current_filter``); ``guide`` = dict(pec_y, pec_z, port, e0, omega, tau,
-    mode_y, esirkepov) adds perfectly conducting walls on the planes y = 0 / z = 0, a
-    hard TE port on the face x = 0 of an open x, and with esirkepov = 1 deposits J with
-    Esirkepov's scheme instead of ZigZag (see ``pic_oracle.c``)."""
+    mode_y, esirkepov, shape) adds perfectly conducting walls on the planes y = 0 / z = 0,
+    a hard TE port on the face x = 0 of an open x, with esirkepov = 1 deposits J with
+    Esirkepov's scheme instead of ZigZag, and with shape = 2 uses the quadratic (TSC)
+    particle shape for the gather and Esirkepov's deposit (see ``pic_oracle.c``)."""
     n, d, pn, pd = _grid(n, d)
     assert F.dtype == np.float64 and F.flags.c_contiguous and F.shape[0] == 9
     ns = len(species)
@@ -272,7 +288,7 @@ def run(n, d, dt, F, species, nsteps=1, step0=0, laser=None, current_filter=None
     if guide is not None:
         gd = np.array([guide.get("pec_y", 0), guide.get("pec_z", 0), guide.get("port", 0), guide.get("e0", 0.0),
                        guide.get("omega", 0.0), guide.get("tau", 1.0), guide.get("mode_y", 1),
-                       guide.get("esirkepov", 0)], dtype=np.float64)
+                       guide.get("esirkepov", 0), guide.get("shape", 1)], dtype=np.float64)
     lib().or_run(pn, pd, dt, _p(F), ns, _p(qm), npc.ctypes.data_as(_lp), ptrs, cptrs, nsteps, _p(diag), int(step0),
                  None if las is None else _p(las), None if filt is None else _p(filt),
                  None if gd is None else _p(gd))

@@ -220,6 +220,63 @@ void or_gather(const int* n, const double* d, const double* E, const double* B, 
 }
 
 /* ------------------------------------------------------------------------ */
+/* Higher-order particle shape (section 2.5, Eq. (16) with l = 1; section 5 lists
+ * higher-order shapes as an extension).  The cloud b1 is a triangle two cells wide;
+ * its overlap with the unit cell around a sample point gives the quadratic B-spline
+ * weight (the triangular-shaped cloud, TSC) of a sample at distance r, in cell units:
+ *   W2(r) = 3/4 - r^2              for |r| <= 1/2,
+ *           (3/2 - |r|)^2 / 2      for 1/2 <= |r| <= 3/2,
+ *           0                      beyond.
+ * As with b0 (CIC), every field component is interpolated from its own Yee location
+ * (Eqs. (17)-(18)): the three samples nearest the particle along each dimension.     */
+static double tsc_w(double r)
+{
+    r = fabs(r);
+    if (r <= 0.5) return 0.75 - r * r;
+    if (r < 1.5) return 0.5 * (1.5 - r) * (1.5 - r);
+    return 0.0;
+}
+
+static double interp_component_tsc(const or_grid* g, const double* F, const int half[3], const long cell[3],
+                                   const double off[3])
+{
+    long base[3];
+    double w[3][3];
+    for (int d = 0; d < 3; d++) {
+        double p = half[d] ? off[d] - 0.5 : off[d];   /* offset relative to the sample lattice */
+        double m = floor(p + 0.5);                     /* the nearest sample */
+        base[d] = cell[d] + (long)m - 1;
+        for (int a = 0; a < 3; a++) w[d][a] = tsc_w(p - (m - 1.0 + a));
+    }
+    double v = 0.0;
+    for (int c = 0; c < 3; c++)
+        for (int b = 0; b < 3; b++)
+            for (int a = 0; a < 3; a++)
+                v += w[0][a] * w[1][b] * w[2][c] * at(g, F, base[0] + a, base[1] + b, base[2] + c);
+    return v;
+}
+
+static void gather_tsc(const or_grid* g, const double* E, const double* B, const long cell[3], const double off[3],
+                       double Ep[3], double Bp[3])
+{
+    long N = ncells(g);
+    for (int c = 0; c < 3; c++) {
+        Ep[c] = interp_component_tsc(g, E + c * N, HALF_E[c], cell, off);
+        Bp[c] = interp_component_tsc(g, B + c * N, HALF_B[c], cell, off);
+    }
+}
+
+void or_gather_tsc(const int* n, const double* d, const double* E, const double* B, const double* X, double* Ep,
+                   double* Bp)
+{
+    or_grid g = mkgrid(n, d, 0.0);
+    long cell[3];
+    double off[3];
+    split(X, cell, off);
+    gather_tsc(&g, E, B, cell, off, Ep, Bp);
+}
+
+/* ------------------------------------------------------------------------ */
 /* Relativistic Boris push, section 2.4 (leapfrog Eqs. (19)-(20), Boris 1970):
  * half electric kick, magnetic rotation, half electric kick.
  * eps = q dt / (2 m).  u enters as u^{n-1/2} and leaves as u^{n+1/2}.       */
@@ -391,6 +448,68 @@ void or_esirkepov(const int* n, const double* d, double dt, double qw, const dou
     esirkepov(&g, qw, c0, a, bb, J);
 }
 
+/* Esirkepov's deposit with the quadratic (TSC) shape above (Esirkepov 2001 holds for any
+ * shape factorised over the dimensions).  For a straight move X1 -> X2 (cell units
+ * relative to cell c0, less than one cell per dimension) the node weights before and
+ * after, S0 = W2(X1 - node) and S1 = W2(X2 - node), are taken on the four nodes
+ * b .. b + 3 per dimension, b = min(m1, m2) - 1 with m the node nearest to X; DS =
+ * S1 - S0 and
+ *   Wx = DSx (S0y S0z + DSy S0z / 2 + S0y DSz / 2 + DSy DSz / 3)   (y, z cyclically),
+ *   Jx(i + 1/2) = -(q w / (dt dy dz)) sum_{i' <= i} Wx(i'),
+ * the running sum along x from the support's first node (the sum over all four nodes
+ * is zero, so the edges b + 1/2 .. b + 5/2 carry the current).                      */
+static void esirkepov_tsc(const or_grid* g, double qw, const long c0[3], const double X1[3], const double X2[3],
+                          double* J)
+{
+    long N = ncells(g);
+    double C[3] = {qw / (g->dt * g->d[1] * g->d[2]),
+                   qw / (g->dt * g->d[2] * g->d[0]),
+                   qw / (g->dt * g->d[0] * g->d[1])};
+    long b[3];
+    double S0[3][4], DS[3][4];
+    for (int d = 0; d < 3; d++) {
+        long m1 = (long)floor(X1[d] + 0.5), m2 = (long)floor(X2[d] + 0.5);
+        b[d] = (m1 < m2 ? m1 : m2) - 1;
+        for (int m = 0; m < 4; m++) {
+            double node = (double)(b[d] + m);
+            S0[d][m] = tsc_w(X1[d] - node);
+            DS[d][m] = tsc_w(X2[d] - node) - S0[d][m];
+        }
+    }
+    for (int comp = 0; comp < 3; comp++) {
+        int p = (comp + 1) % 3, r = (comp + 2) % 3;
+        for (int jp = 0; jp < 4; jp++)
+            for (int jr = 0; jr < 4; jr++) {
+                double acc = 0.0;
+                for (int i = 0; i < 3; i++) {   /* edges b + 1/2 .. b + 5/2 along comp */
+                    double W = DS[comp][i] * (S0[p][jp] * S0[r][jr] + 0.5 * DS[p][jp] * S0[r][jr]
+                                              + 0.5 * S0[p][jp] * DS[r][jr] + DS[p][jp] * DS[r][jr] / 3.0);
+                    acc += W;
+                    long idx[3];
+                    idx[comp] = c0[comp] + b[comp] + i;
+                    idx[p] = c0[p] + b[p] + jp;
+                    idx[r] = c0[r] + b[r] + jr;
+                    long e = cell_index(g, idx[0], idx[1], idx[2]);
+                    if (e >= 0 && acc != 0.0) J[comp * N + e] += -C[comp] * acc;
+                }
+            }
+    }
+}
+
+void or_esirkepov_tsc(const int* n, const double* d, double dt, double qw, const double* X1, const double* X2,
+                      double* J)
+{
+    or_grid g = mkgrid(n, d, dt);
+    long c0[3];
+    double a[3], bb[3];
+    for (int k = 0; k < 3; k++) {
+        c0[k] = (long)floor(X1[k]);
+        a[k] = X1[k] - (double)c0[k];
+        bb[k] = X2[k] - (double)c0[k];
+    }
+    esirkepov_tsc(&g, qw, c0, a, bb, J);
+}
+
 void or_zigzag(const int* n, const double* d, double dt, double qw, const double* X1, const double* X2, double* J)
 {
     or_grid g = mkgrid(n, d, dt);
@@ -426,6 +545,31 @@ void or_rho(const int* n, const double* d, double q, long np, const double* P, c
                     double wgt = (a ? s[0] : 1.0 - s[0]) * (b ? s[1] : 1.0 - s[1]) * (c ? s[2] : 1.0 - s[2]);
                     long e = cell_index(&g, base[0] + a, base[1] + b, base[2] + c);
                     if (e >= 0) rho[e] += qw * wgt;
+                }
+    }
+}
+
+/* Charge density on the nodes with the quadratic (TSC) shape: rho(node) += q w / dV *
+ * W2(X - node_x) W2(Y - node_y) W2(Z - node_z) over the 3 x 3 x 3 nearest nodes.     */
+void or_rho_tsc(const int* n, const double* d, double q, long np, const double* P, const double* C, double* rho)
+{
+    or_grid g = mkgrid(n, d, 0.0);
+    double dV = d[0] * d[1] * d[2];
+    for (long p = 0; p < np; p++) {
+        long base[3];
+        double w[3][3];
+        for (int dd = 0; dd < 3; dd++) {
+            double off = P[dd * np + p];
+            double m = floor(off + 0.5);
+            base[dd] = (long)C[dd * np + p] + (long)m - 1;
+            for (int a = 0; a < 3; a++) w[dd][a] = tsc_w(off - (m - 1.0 + a));
+        }
+        double qw = q * P[6 * np + p] / dV;
+        for (int c = 0; c < 3; c++)
+            for (int b = 0; b < 3; b++)
+                for (int a = 0; a < 3; a++) {
+                    long e = cell_index(&g, base[0] + a, base[1] + b, base[2] + c);
+                    if (e >= 0) rho[e] += qw * w[0][a] * w[1][b] * w[2][c];
                 }
     }
 }
@@ -467,7 +611,7 @@ void or_divergence_b(const int* n, const double* d, const double* B, double* out
  * momentum only, u^0 -> u^{-1/2} (section 2.4, momenta at half-integer times),
  * with E^0 and B^0 = B^{-1/2} - (dt/2) curl E^0.                             */
 void or_backpush(const int* n, const double* d, double dt, const double* E, const double* Bhalf,
-                 double q, double m, long np, double* P, const double* C)
+                 double q, double m, long np, double* P, const double* C, int shape)
 {
     or_grid g = mkgrid(n, d, dt);
     long N = ncells(&g);
@@ -479,7 +623,8 @@ void or_backpush(const int* n, const double* d, double dt, const double* E, cons
         double off[3] = {P[p], P[np + p], P[2 * np + p]};
         double u[3] = {P[3 * np + p], P[4 * np + p], P[5 * np + p]};
         double Ep[3], Bp[3];
-        gather(&g, E, B0, cell, off, Ep, Bp);
+        if (shape == 2) gather_tsc(&g, E, B0, cell, off, Ep, Bp);
+        else gather(&g, E, B0, cell, off, Ep, Bp);
         or_boris(q * (-0.5 * dt) / (2.0 * m), Ep, Bp, u);
         P[3 * np + p] = u[0];
         P[4 * np + p] = u[1];
@@ -593,8 +738,9 @@ void or_current_filter(const int* n, const double* d, double* J, int passes, int
 /* Perfectly conducting walls and a waveguide port (section 3.2: the Yee solver is
  * verified on the TE10 mode of a perfectly conducting rectangular guide driven at its
  * input plane; the paper gives no discretisation of either).
- * guide = {pec_y, pec_z, port, e0, omega, tau, mode_y, deposit}; deposit = 1 selects
- * Esirkepov's deposit instead of ZigZag (see esirkepov).
+ * guide = {pec_y, pec_z, port, e0, omega, tau, mode_y, deposit, shape}; deposit = 1
+ * selects Esirkepov's deposit instead of ZigZag (see esirkepov); shape = 2 selects the
+ * quadratic (TSC) particle shape for the gather and Esirkepov's deposit (see tsc_w).
  * pec_y: the node plane y = 0 is a perfect conductor, its tangential Ex and Ez are
  *   held at zero; with y periodic that plane is both walls of a guide 0 <= y <= ny.
  * pec_z: likewise the plane z = 0 (Ex, Ey).
@@ -634,7 +780,7 @@ static void pec_walls(const or_grid* g, const double* guide, double* E)
  * leaves an open x is removed (weight 0).  Returns the species' kinetic energy at time
  * level n, sum w m ((gamma^{n-1/2} + gamma^{n+1/2}) / 2 - 1).                       */
 static double push_species(const or_grid* gp, double q, double m, long cnt, double* Ps, double* Cs,
-                           const double* E, const double* Bn, double* J, int esk)
+                           const double* E, const double* Bn, double* J, int esk, int shape)
 {
     const or_grid g = *gp;
     const int* n = g.n;
@@ -648,14 +794,16 @@ static double push_species(const or_grid* gp, double q, double m, long cnt, doub
         double u[3] = {Ps[3 * cnt + p], Ps[4 * cnt + p], Ps[5 * cnt + p]};
         double w = Ps[6 * cnt + p];
         double Ep[3], Bp[3];
-        gather(&g, E, Bn, cell, X1, Ep, Bp);
+        if (shape == 2) gather_tsc(&g, E, Bn, cell, X1, Ep, Bp);
+        else gather(&g, E, Bn, cell, X1, Ep, Bp);
         double g_old = gamma_of(u);
         or_boris(q * dt / (2.0 * m), Ep, Bp, u);
         double g_new = gamma_of(u);
         K += w * m * (0.5 * (g_old + g_new) - 1.0);
         double X2[3];
         for (int dd = 0; dd < 3; dd++) X2[dd] = X1[dd] + dt * u[dd] / (g_new * d[dd]);
-        if (esk) esirkepov(&g, q * w, cell, X1, X2, J);
+        if (shape == 2) esirkepov_tsc(&g, q * w, cell, X1, X2, J);
+        else if (esk) esirkepov(&g, q * w, cell, X1, X2, J);
         else zigzag(&g, q * w, cell, X1, X2, J);
         int gone = 0;
         for (int dd = 0; dd < 3; dd++) {
@@ -678,10 +826,10 @@ static double push_species(const or_grid* gp, double q, double m, long cnt, doub
 
 /* push_species as an entry point: E and Bn (B^n) are read, J is added to.             */
 double or_push(const int* n, const double* d, double dt, const double* E, const double* Bn, double q, double m, long np,
-               double* P, double* C, double* J, int esk)
+               double* P, double* C, double* J, int esk, int shape)
 {
     or_grid g = mkgrid(n, d, dt);
-    return push_species(&g, q, m, np, P, C, E, Bn, J, esk);
+    return push_species(&g, q, m, np, P, C, E, Bn, J, esk, shape);
 }
 
 void or_step(const int* n, const double* d, double dt, double* F, int ns, const double* qm, const long* np,
@@ -708,7 +856,7 @@ void or_step(const int* n, const double* d, double dt, double* F, int ns, const 
         double* Ps = P[s];
         double* Cs = C[s];
         long cnt = np[s];
-        K += push_species(&g, q, m, cnt, Ps, Cs, E, Bn, J, guide && guide[7] != 0);
+        K += push_species(&g, q, m, cnt, Ps, Cs, E, Bn, J, guide && guide[7] != 0, guide ? (int)guide[8] : 1);
     }
     if (filt && filt[0] > 0) or_current_filter(n, d, J, (int)filt[0], (int)filt[1]);
     if (laser) laser_source(&g, laser, (step + 0.5) * dt, J);
