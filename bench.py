@@ -332,7 +332,8 @@ def other_workloads(torch, peak, peak_kind):
     # the thermal plasma with the compensated binomial current filter (1 pass per
     # dimension and the compensator) and with Esirkepov's deposit
     for key, setup in (("thermal128_filtered_f32", lambda c: c.set_current_filter(1, True)),
-                       ("thermal128_esirkepov_f32", lambda c: c.set_deposit(gbpic.PIC_DEPOSIT_ESIRKEPOV))):
+                       ("thermal128_esirkepov_f32", lambda c: c.set_deposit(gbpic.PIC_DEPOSIT_ESIRKEPOV)),
+                       ("thermal128_tsc_f32", lambda c: c.set_shape(gbpic.PIC_SHAPE_TSC))):
         X, U, w, dt = W.thermal_device(torch, spec["n"], spec["d"], spec["ppc"], spec["u_th"], spec["seed"])
         ctx = gbpic.Context(spec["n"], (spec["d"],) * 3, dt, precision=gbpic.PIC_FP32, rho_ion=1.0)
         setup(ctx)
@@ -345,6 +346,8 @@ def other_workloads(torch, peak, peak_kind):
         ctx.close()
         out[key] = {"value": npart * steps / (ms / 1e3), "unit": UNIT, "steps": steps, "ms_per_step": ms / steps,
                     "particles": npart, "kernels": kernel_table(kt)}
+    out["thermal128_tsc_f32"]["note"] = ("quadratic (TSC) shape: 27-point gather per component and Esirkepov's "
+                                         "deposit on the 4 x 4 x 4 support, every particle")
     out["thermal128_filtered_f32"]["note"] = ("'other' holds the filter: 1 binomial pass per dimension and the "
                                               "compensator, each over J")
     base = out["thermal128_f32"]["kernels"]["tile_push"]

@@ -248,6 +248,22 @@ pic_status pic_set_port(pic_ctx* ctx, const pic_port_desc* port);
 typedef enum pic_deposit { PIC_DEPOSIT_ZIGZAG = 0, PIC_DEPOSIT_ESIRKEPOV = 1 } pic_deposit;
 pic_status pic_set_deposit(pic_ctx* ctx, int32_t deposit);
 
+/* The particle shape (section 2.5, Eq. (16); section 5 lists higher-order shapes as an
+ * extension): PIC_SHAPE_CIC (default, the paper's zeroth-order cloud b0: first-order
+ * CIC interpolation and the deposit pic_set_deposit selects) or PIC_SHAPE_TSC (the
+ * first-order cloud b1: quadratic B-spline weights W2(r) = 3/4 - r^2 for |r| <= 1/2,
+ * (3/2 - |r|)^2 / 2 for 1/2 <= |r| <= 3/2).  With TSC every field component is
+ * interpolated from its own Yee location with its 27 nearest samples, the current is
+ * Esirkepov's with the same shape on the 4 x 4 x 4 nodes a move touches (whatever
+ * pic_set_deposit says), the back-push gathers with TSC, and pic_diagnostics takes the
+ * node charge with TSC, so continuity and Gauss's law hold exactly as with CIC.  TSC
+ * needs a periodic box without conducting walls (PIC_ERR_STATE for bc_x = 1 or walls
+ * set, and pic_set_pec fails while TSC is set); the adjoint and
+ * pic_gauss_check_static support CIC only (PIC_ERR_STATE).  Call before stepping or
+ * between steps; PIC_ERR_ARG for another value. */
+typedef enum pic_shape { PIC_SHAPE_CIC = 1, PIC_SHAPE_TSC = 2 } pic_shape;
+pic_status pic_set_shape(pic_ctx* ctx, int32_t shape);
+
 /* Compensated binomial current filter.  Section 2.2 counts "compensated smoothing"
  * among the operations of a cycle and section 2.6 lists a current-filtering module;
  * the paper gives no scheme and its runs use none, so it is off by default.  With

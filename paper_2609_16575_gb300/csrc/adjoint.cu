@@ -647,9 +647,9 @@ extern "C" {
 pic_status pic_adjoint_forward(pic_ctx* c, int32_t nsteps, int32_t ckpt_every, double* loss) {
     if (!c || nsteps < 1 || ckpt_every < 1 || !loss) return PIC_ERR_ARG;
     if (!c->desc.track_ids || c->species.empty() || c->g.open_x || c->filter_passes > 0 ||
-        c->deposit != PIC_DEPOSIT_ZIGZAG) {
+        c->deposit != PIC_DEPOSIT_ZIGZAG || c->shape != PIC_SHAPE_CIC) {
         c->err = "pic_adjoint_forward needs track_ids, at least one species, a periodic box, no current filter "
-                 "and the ZigZag deposit";
+                 "and the ZigZag deposit with the CIC shape";
         return PIC_ERR_STATE;
     }
     DeviceScope dscope_(c->desc.device);

@@ -491,6 +491,10 @@ pic_status pic_set_pec(pic_ctx* c, int32_t pec_y, int32_t pec_z) {
         c->err = "pic_set_pec: the conducting walls act on the fields only (species are loaded)";
         return PIC_ERR_STATE;
     }
+    if ((pec_y || pec_z) && c->shape != PIC_SHAPE_CIC) {
+        c->err = "pic_set_pec: the TSC shape supports a periodic box only";
+        return PIC_ERR_STATE;
+    }
     c->pec_y = pec_y;
     c->pec_z = pec_z;
     return PIC_OK;
@@ -712,6 +716,22 @@ pic_status pic_set_deposit(pic_ctx* c, int32_t deposit) {
         return PIC_ERR_ARG;
     }
     c->deposit = deposit;
+    return PIC_OK;
+}
+
+pic_status pic_set_shape(pic_ctx* c, int32_t shape) {
+    if (!c) return PIC_ERR_ARG;
+    if (shape != PIC_SHAPE_CIC && shape != PIC_SHAPE_TSC) {
+        c->err = "pic_set_shape: PIC_SHAPE_CIC or PIC_SHAPE_TSC";
+        return PIC_ERR_ARG;
+    }
+    if (shape == PIC_SHAPE_TSC && (c->g.open_x || c->pec_y || c->pec_z)) {
+        c->err = "pic_set_shape: the TSC shape needs a periodic box without conducting walls";
+        return PIC_ERR_STATE;
+    }
+    c->shape = shape;
+    c->gref_valid = false;        // the Gauss reference and the continuity check use the
+    c->rho_prev_step = -1;        // charge of the shape
     return PIC_OK;
 }
 

@@ -50,15 +50,39 @@ __global__ void k_energy(Geom g, Fields<T> f, double hx, double hy, double hz, d
     acc_sum(acc, S_UB, sb * half_dv);
 }
 
-// Kinetic energy at u^{n-1/2} and the FP64 CIC charge of the nodes.
+// Node weights of the quadratic (TSC) shape for in-cell offset d: the nodes m - 1 ..
+// m + 1 around the nearest node m (0 or 1), first node returned.
+__device__ __forceinline__ int tsc_node_weights(double d, double w[3]) {
+    const int m = d >= 0.5 ? 1 : 0;
+    const double e = d - m, a = 0.5 - e, b = 0.5 + e;
+    w[0] = 0.5 * a * a;
+    w[1] = 0.75 - e * e;
+    w[2] = 0.5 * b * b;
+    return m - 1;
+}
+
+// Kinetic energy at u^{n-1/2} and the FP64 charge of the nodes with the particle
+// shape: CIC (shape 1) or TSC (shape 2, periodic box).
 template <typename T>
 __global__ void k_particles(Geom g, ParticleArrays<T> pa, const Rec<T>* spill, int nsp, double q, double m,
-                            double qdv, double* rho, double* acc) {
+                            double qdv, double* rho, double* acc, int shape) {
     const int ntile = g.nt[0] * g.nt[1] * g.nt[2];
     double ks = 0;
     auto one = [&](int gx, int gy, int gz, double dx, double dy, double dz, double ux, double uy, double uz, double w) {
         const double u2 = ux * ux + uy * uy + uz * uz;
         ks += w * m * (u2 / (sqrt(1.0 + u2) + 1.0));
+        if (shape == 2) {
+            double tx[3], ty[3], tz[3];
+            const int bx = gx + tsc_node_weights(dx, tx), by = gy + tsc_node_weights(dy, ty),
+                      bz = gz + tsc_node_weights(dz, tz);
+            for (int c = 0; c < 3; ++c)
+                for (int b = 0; b < 3; ++b)
+                    for (int a = 0; a < 3; ++a) {
+                        const long long e = g.cidx(wrap_idx(bx + a, g.n[0]), wrap_idx(by + b, g.n[1]), wrap_idx(bz + c, g.n[2]));
+                        atomicAdd(rho + e, qdv * w * tx[a] * ty[b] * tz[c]);
+                    }
+            return;
+        }
         const double wx[2] = {1.0 - dx, dx}, wy[2] = {1.0 - dy, dy}, wz[2] = {1.0 - dz, dz};
         for (int c = 0; c < 2; ++c)
             for (int b = 0; b < 2; ++b)
@@ -168,7 +192,7 @@ static pic_status diag_t(pic_ctx* c, pic_diag* out) {
         spilled += sp;
         LaunchScope ls(c, KC_OTHER);
         k_particles<T><<<1024, 256, 0, c->stream>>>(g, arrays<T>(s), static_cast<const Rec<T>*>(s.spill), (int)sp, s.q,
-                                                     s.m, s.q / dv, c->rho, c->dacc);
+                                                     s.m, s.q / dv, c->rho, c->dacc, c->shape);
         GBPIC_CHECK(c, cudaGetLastError());
     }
     // a window move changes the frame: no continuity check across it, and the Gauss

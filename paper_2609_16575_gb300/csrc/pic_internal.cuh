@@ -686,6 +686,7 @@ struct pic_ctx {
     bool port_on = false;
     pic_port_desc port{};
     int deposit = 0;                    // pic_deposit: ZigZag or Esirkepov
+    int shape = 1;                      // pic_shape: CIC (1) or quadratic TSC (2)
     int wait_polls = -1;                // tile kernel staging wait limit (negative: MBAR_MAX_POLLS)
 };
 

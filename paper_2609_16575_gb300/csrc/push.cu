@@ -10,31 +10,9 @@
 //   k_append      puts movers into the segment of their new tile (or the spill list).
 #include <cuda/std/cstdint>
 
-#include "pic_internal.cuh"
+#include "push_common.cuh"
 
 namespace gbpic {
-
-template <typename T> struct PushArgs {
-    Geom g;
-    ParticleArrays<T> pa;   // the block the step reads
-    ParticleArrays<T> pb;   // the block the step writes (tile kernel, append)
-    const int* hin;         // per tile: cell histogram of pa (TILE_CELLS ints)
-    int* hout;              // per tile: cell histogram of pb, built by the step
-    Fields<T> f;
-    T eps;          // q dt / (2 m)
-    T dtd[3];       // dt / d_d
-    T cq[3];        // q / (dt d_p d_r) / jscale : fixed-point units per unit weight
-    Rec<T>* movers;
-    int mover_cap;
-    Rec<T>* spill;
-    int spill_cap;
-    Counters* ctr;
-    int parity;
-    double* krec;   // optional: accumulate sum w m ((g_old + g_new)/2 - 1) here
-    double mass;
-    int xshift;     // 1: the window moves after this cycle (stored x cells drop by one)
-    int wait_polls; // polls of the TMA staging wait before it gives up (ERRB_TIMEOUT); 0: at once
-};
 
 template <typename T> __host__ __device__ constexpr int box_elems() { return SB * SB * Prec<T>::BX; }
 template <typename T> __host__ __device__ constexpr int box_stride() {
@@ -50,7 +28,6 @@ constexpr int PS = PSX * PSY * PSZ;          // pairs per component
 // cleared once they have been converted to pairs); the warps' staged movers; the
 // mbarrier.  Offsets are
 // multiples of 128 bytes.
-__host__ __device__ constexpr size_t align128(size_t b) { return (b + 127) / 128 * 128; }
 constexpr int QWORDS_ = (QCAP_ * 14 > 32 * 14 + 16 ? QCAP_ * 14 : 32 * 14 + 16);   // QWORDS below
 template <typename T> __host__ __device__ constexpr size_t region_a_bytes() {
     return align128((size_t)(Prec<T>::THREADS / 32) * QWORDS_ * sizeof(T));
@@ -60,26 +37,12 @@ template <typename T> __host__ __device__ constexpr size_t jtile_bytes() {
     return align128((size_t)JT_ELEMS * 8 > (size_t)6 * box_stride<T>() * sizeof(T) ? (size_t)JT_ELEMS * 8
                                                                                   : (size_t)6 * box_stride<T>() * sizeof(T));
 }
-constexpr int MQ = 32;   // staged movers per warp (a particle step adds at most 32)
 template <typename T> __host__ __device__ constexpr size_t movers_bytes() {
     return align128((size_t)(Prec<T>::THREADS / 32) * MQ * sizeof(Rec<T>));
 }
 template <typename T> constexpr size_t tile_smem_bytes() {
     // + 128: the kernel rounds the dynamic shared base up to a 128-byte boundary
     return region_a_bytes<T>() + pairs_bytes<T>() + jtile_bytes<T>() + movers_bytes<T>() + 16 + 128;
-}
-
-__device__ __forceinline__ void block_add_double(double v, double* dst) {
-    for (int o = 16; o > 0; o >>= 1) v += __shfl_xor_sync(0xffffffffu, v, o);
-    __shared__ double red[PUSH_WARPS_MAX];
-    int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
-    if (lane == 0) red[warp] = v;
-    __syncthreads();
-    if (threadIdx.x == 0) {
-        double s = 0;
-        for (int w = 0; w < (int)(blockDim.x >> 5); ++w) s += red[w];
-        atomicAdd(dst, s);
-    }
 }
 
 // Index of the shared J tile element of (component, local x, y, z), -1..9 each.
@@ -332,22 +295,6 @@ __device__ __forceinline__ void esk_crossers(WarpQueue<T> Q, int& qn, int lane, 
 // Write a warp's mq staged movers to the global mover list: one counter atomic per
 // batch (the only global atomic whose result a warp waits for), then the records by
 // the lanes (warp-collective).
-template <typename T>
-__device__ __forceinline__ void movers_flush(const PushArgs<T>& A, const Rec<T>* sM, int& mq, int lane) {
-    __syncwarp();
-    int base = 0;
-    if (lane == 0) base = atomicAdd(&A.ctr->mover_count[A.parity], mq);
-    base = __shfl_sync(0xffffffffu, base, 0);
-    bool over = false;
-    for (int j = lane; j < mq; j += 32) {
-        if (base + j < A.mover_cap) A.movers[base + j] = sM[j];
-        else over = true;
-    }
-    if (over) atomicOr(&A.ctr->err, ERRB_OVERFLOW);
-    __syncwarp();
-    mq = 0;
-}
-
 // Start of a tile: one thread issues the six TMA box loads of E and B
 // (local cells -1..8, origin at the tile's ghost corner) completing on one mbarrier while
 // the first 256 threads scan the input cell histogram into the output cell ranges; then
@@ -385,30 +332,8 @@ __device__ __forceinline__ bool tile_prologue(const PushArgs<T>& A, int tile, in
         tma_load_3d(sF + 4 * BS, &tB1, ox, oy, oz, bar);
         tma_load_3d(sF + 5 * BS, &tB2, ox, oy, oz, bar);
     }
-    // output ranges: exclusive scan of the input histogram (two cells per thread of the
-    // first 256 threads)
-    {
-        const bool sc = threadIdx.x < 256;
-        const int a0 = sc ? hin[2 * threadIdx.x] : 0, a1 = sc ? hin[2 * threadIdx.x + 1] : 0;
-        int incl = a0 + a1;
-#pragma unroll
-        for (int o = 1; o < 32; o <<= 1) {
-            const int y = __shfl_up_sync(0xffffffffu, incl, o);
-            if (lane >= o) incl += y;
-        }
-        if (lane == 31 && sc) s_wsum[warp] = incl;
-        __syncthreads();
-        if (sc) {
-            int woff = 0;
-            for (int w2 = 0; w2 < warp; ++w2) woff += s_wsum[w2];
-            const int excl = woff + incl - (a0 + a1);
-            s_off[2 * threadIdx.x] = excl;
-            s_off[2 * threadIdx.x + 1] = excl + a0;
-            s_hn[2 * threadIdx.x] = 0;
-            s_hn[2 * threadIdx.x + 1] = 0;
-            if (threadIdx.x == 255) *s_total = woff + incl;
-        }
-    }
+    // output ranges: exclusive scan of the input histogram
+    hist_scan(hin, s_off, s_hn, s_wsum, s_total);
     for (int polls = 0;; ++polls) {
         if (polls >= A.wait_polls) {   // (a bound of 0 gives up without waiting)
             *s_timeout = 1;
@@ -1037,7 +962,10 @@ static pic_status push_species_t(pic_ctx* c, SpeciesDev& s, int parity, double* 
     const bool ids = c->desc.track_ids != 0, rec = krec != nullptr;
     pic_status st;
     const bool esk = c->deposit == PIC_DEPOSIT_ESIRKEPOV;
-    if (esk) {
+    const bool tsc = c->shape == PIC_SHAPE_TSC;
+    if (tsc) {
+        st = launch_tsc_push<T>(c, A, ids, rec);   // its tile step and spill-list step
+    } else if (esk) {
         if (ids) st = rec ? launch_tile<T, true, true, true>(c, A) : launch_tile<T, true, false, true>(c, A);
         else st = rec ? launch_tile<T, false, true, true>(c, A) : launch_tile<T, false, false, true>(c, A);
     } else {
@@ -1046,7 +974,7 @@ static pic_status push_species_t(pic_ctx* c, SpeciesDev& s, int parity, double* 
     }
     if (st != PIC_OK) return st;
     const int grid = 2 * sm_count(c);
-    {
+    if (!tsc) {
         LaunchScope ls(c, KC_LIST_PUSH);
         if (esk) {
             if (rec) k_list_push<T, true, true><<<grid, 256, 0, c->stream>>>(A);
@@ -1092,7 +1020,11 @@ static pic_status backpush_t(pic_ctx* c, SpeciesDev& s) {
     for (int k = 0; k < 3; ++k) c->B[k] = saved[k];
     if (st != PIC_OK) return st;
     PushArgs<T> A = make_args<T>(c, s, 0, nullptr, -0.5);
-    {
+    if (c->shape == PIC_SHAPE_TSC) {
+        st = launch_tsc_backpush<T>(c, A, static_cast<const T*>(B0[0]), static_cast<const T*>(B0[1]),
+                                    static_cast<const T*>(B0[2]));
+        if (st != PIC_OK) return st;
+    } else {
         LaunchScope ls(c, KC_OTHER);
         k_backpush<T><<<4 * sm_count(c), 256, 0, c->stream>>>(A, B0[0], B0[1], B0[2]);
         GBPIC_CHECK(c, cudaGetLastError());

@@ -140,6 +140,10 @@ extern "C" pic_status pic_gauss_check_static(pic_ctx* c, double* gauss_max, doub
     }
     const int dev = c->desc.device;
     if (dev < 0 || dev >= STATIC_MAX_DEVICES) return PIC_ERR_ARG;
+    if (c->shape != PIC_SHAPE_CIC) {
+        c->err = "pic_gauss_check_static: the CIC shape only";
+        return PIC_ERR_STATE;
+    }
     DeviceScope dscope_(dev);
     pic_status st = pic_sync(c);
     if (st != PIC_OK) return st;

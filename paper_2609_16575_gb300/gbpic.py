@@ -32,6 +32,8 @@ STATUS_NAMES = {0: "PIC_OK", 1: "PIC_ERR_ARG", 2: "PIC_ERR_CFL", 3: "PIC_ERR_OOM
                 9: "PIC_ERR_TIMEOUT", 10: "PIC_ERR_NO_DEVICE"}
 PIC_DEPOSIT_ZIGZAG = 0
 PIC_DEPOSIT_ESIRKEPOV = 1
+PIC_SHAPE_CIC = 1
+PIC_SHAPE_TSC = 2
 
 ALLOC_FN = ctypes.CFUNCTYPE(ctypes.c_void_p, ctypes.c_size_t, ctypes.c_void_p)
 FREE_FN = ctypes.CFUNCTYPE(None, ctypes.c_void_p, ctypes.c_void_p)
@@ -127,6 +129,8 @@ def lib():
                                           ctypes.c_int32]
             L.pic_set_deposit.argtypes = [P, ctypes.c_int32]
             L.pic_set_wait_limit.argtypes = [P, ctypes.c_int32]
+            L.pic_set_shape.argtypes = [P, ctypes.c_int32]
+            L.pic_set_shape.restype = ctypes.c_int
             L.pic_probe_fp64_rate.argtypes = [ctypes.c_int32, ctypes.POINTER(ctypes.c_double)]
             L.pic_save_state.argtypes = [P, ctypes.POINTER(ctypes.c_void_p), ctypes.POINTER(ctypes.c_size_t)]
             L.pic_load_state.argtypes = [P, ctypes.c_void_p, ctypes.c_size_t]
@@ -417,6 +421,10 @@ class Context:
     def set_deposit(self, scheme):
         """PIC_DEPOSIT_ZIGZAG (0, default) or PIC_DEPOSIT_ESIRKEPOV (1)."""
         _check(self.ptr, lib().pic_set_deposit(self.ptr, int(scheme)), "pic_set_deposit")
+
+    def set_shape(self, shape):
+        """PIC_SHAPE_CIC (1, default) or PIC_SHAPE_TSC (2: quadratic shape, Esirkepov's deposit)."""
+        _check(self.ptr, lib().pic_set_shape(self.ptr, int(shape)), "pic_set_shape")
 
     def set_background(self, rho_ion):
         """Uniform immobile background charge density (diagnostics only)."""

@@ -105,6 +105,7 @@ def test_new_entry_points_reject_a_null_context(L):
     assert L.pic_set_pec(None, 1, 0) == 1
     assert L.pic_set_port(None, None) == 1
     assert L.pic_set_deposit(None, 1) == 1
+    assert L.pic_set_shape(None, 2) == 1
     assert L.pic_set_wait_limit(None, 1) == 1
     assert L.pic_probe_fp64_rate(0, None) == 1
     blob, size = ctypes.c_void_p(), ctypes.c_size_t()
