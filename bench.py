@@ -61,12 +61,17 @@ def parse():
     p.add_argument("--no-extra", action="store_true", help="skip the other workloads and the adjoint cost")
     p.add_argument("--adjoint-only", type=int, default=0,
                    help="only time the FP64 checkpointed adjoint of the differentiable run over this many steps")
+    p.add_argument("--adjoint-prec", default="f64", choices=["f32", "f64", "both"],
+                   help="precision of the --adjoint-only timing")
     p.add_argument("--waveguide", type=int, default=0,
                    help="run the first N grids of the TE10 waveguide convergence study (FP64) and exit")
     p.add_argument("--waveguide-fp32", action="store_true", help="the waveguide study on the FP32 path")
     p.add_argument("--small", action="store_true", help="32^3 cells instead of the headline grid (smoke)")
     p.add_argument("--cells", type=int, default=0, help="cells per dimension of the headline workload (profiling)")
     p.add_argument("--ppc", type=int, default=0, help="electrons per cell of the headline workload (profiling)")
+    p.add_argument("--deposit", default="zigzag", choices=["zigzag", "esirkepov"],
+                   help="current deposit of the headline run (profiling the variants)")
+    p.add_argument("--shape", default="cic", choices=["cic", "tsc"], help="particle shape of the headline run")
     return p.parse_args()
 
 
@@ -81,7 +86,7 @@ def peaks():
 
 def kernel_source_hash():
     h = hashlib.sha256()
-    for name in ("push.cu", "pic_internal.cuh"):
+    for name in ("push.cu", "push_common.cuh", "pic_internal.cuh"):
         with open(os.path.join(ROOT, "paper_2609_16575_gb300", "csrc", name), "rb") as f:
             h.update(f.read())
     return h.hexdigest()[:16]
@@ -680,8 +685,15 @@ def run_gbpic(args):
     X, U, w, dt = W.thermal_device(torch, n, spec["d"], ppc, spec["u_th"], spec["seed"] + rank)
     npart = int(w.shape[0])
 
+    def variant(c):
+        if args.deposit == "esirkepov":
+            c.set_deposit(gbpic.PIC_DEPOSIT_ESIRKEPOV)
+        if args.shape == "tsc":
+            c.set_shape(gbpic.PIC_SHAPE_TSC)
+
     # --- FP32, inputs resident in HBM
     ctx = gbpic.Context(n, d, dt, precision=gbpic.PIC_FP32, rho_ion=1.0, device=dev)
+    variant(ctx)
     ctx.load_species(-1.0, 1.0, X, U, w, True)
     d0 = ctx.diagnostics()
     ctx.step(args.warmup)
@@ -706,6 +718,7 @@ def run_gbpic(args):
     if not args.no_fp64:
         k64 = max(3, args.steps // 4)
         ctx = gbpic.Context(n, d, dt, precision=gbpic.PIC_FP64, rho_ion=1.0, device=dev)
+        variant(ctx)
         ctx.load_species(-1.0, 1.0, X, U, w, True)
         e0 = ctx.diagnostics()
         ctx.step(2)
@@ -744,6 +757,7 @@ def run_gbpic(args):
         torch.cuda.synchronize()
         t0 = time.perf_counter()
         ctx = gbpic.Context(n, d, dt, precision=gbpic.PIC_FP32, rho_ion=1.0, device=dev)
+        variant(ctx)
         ctx.load_species(-1.0, 1.0, Xh, Uh, wh, True)
         ctx.step(args.steps)
         d_e2e = ctx.diagnostics()
@@ -782,7 +796,8 @@ def run_gbpic(args):
         line = {"metric": METRIC, "value": value, "unit": UNIT, "n_gpus": world, "steps": args.steps,
                 "warmup": args.warmup, "ms_per_step": ms_all / args.steps, "higher_is_better": True,
                 "scaling": "weak", "vs_baseline": None, "dtype": "f32", "data": "synthetic",
-                "config": arm_config(spec, world),
+                "config": dict(arm_config(spec, world), **({"variant": f"deposit={args.deposit}, shape={args.shape}"}
+                                                            if args.deposit != "zigzag" or args.shape != "cic" else {})),
                 "roofline": rl,
                 "step_hbm_frac": value / world * step_bytes / 1e9 / peak,
                 "cell_steps_per_s": ncell * world * args.steps / (ms_all / 1e3),
@@ -813,7 +828,8 @@ def main():
         import __graft_entry__
 
         __graft_entry__.build()
-        print(json.dumps(adjoint_cost(torch, args.adjoint_only, ("f64",))), flush=True)
+        precs = ("f32", "f64") if args.adjoint_prec == "both" else (args.adjoint_prec,)
+        print(json.dumps(adjoint_cost(torch, args.adjoint_only, precs)), flush=True)
         return 0
     if args.impl == "reference":
         return run_reference(args)

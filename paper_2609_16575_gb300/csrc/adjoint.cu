@@ -132,7 +132,7 @@ template <typename T> struct AdjArgs {
     int nsp;
     const T* E[3];      // E^n
     const T* Bn[3];     // B_n = B^{n-1/2} - dt/2 curl E^n
-    const double* lEn[3];   // lambda of E^{n+1} (padded): lambda_J = -dt lEn
+    const T* lJ[3];     // lambda_J = -dt lambda of E^{n+1} (padded), in the working precision
     double* accE[3];    // gather^T accumulators (compact)
     double* accB[3];
     double* lX;         // 3 x nload lambda of positions (cell units), load order
@@ -166,15 +166,16 @@ __device__ __forceinline__ C interp_grad(const Geom& g, const T* F, const int b[
     return v;
 }
 
-// FP64 accumulation of lam times the trilinear weights of component comp through
-// Add(comp, x, y, z, value) at the eight nodes from base b.
+// lam times the trilinear weights of component comp, through Add(comp, x, y, z, value)
+// at the eight nodes from base b (the value in arithmetic C; the accumulator decides
+// its own precision).
 template <typename C, typename AddFn>
 __device__ __forceinline__ void scatter_trilinear(AddFn Add, int comp, const int b[3], const C s[3], C lam) {
     if (lam == C(0)) return;
     const C w0[2] = {C(1) - s[0], s[0]}, w1[2] = {C(1) - s[1], s[1]}, w2[2] = {C(1) - s[2], s[2]};
     for (int cc = 0; cc < 2; ++cc)
         for (int bb = 0; bb < 2; ++bb)
-            for (int aa = 0; aa < 2; ++aa) Add(comp, b[0] + aa, b[1] + bb, b[2] + cc, (double)(lam * w0[aa] * w1[bb] * w2[cc]));
+            for (int aa = 0; aa < 2; ++aa) Add(comp, b[0] + aa, b[1] + bb, b[2] + cc, lam * w0[aa] * w1[bb] * w2[cc]);
 }
 
 // Derivatives of S = sum_q L_q v_q(F, W) for one straight segment (the 12 edge
@@ -270,9 +271,9 @@ __device__ void adjoint_particle(const AdjArgs<T>& A, AddFn Add, int gx, int gy,
     for (int q = 0; q < 12; ++q) {
         int comp, ex, ey, ez;
         slot_edge(q, gx, gy, gz, comp, ex, ey, ez);
-        L1[q] = (C)(-A.dt * A.lEn[comp][g.pidx(wrap_idx(ex, g.n[0]), wrap_idx(ey, g.n[1]), wrap_idx(ez, g.n[2]))]);
+        L1[q] = (C)A.lJ[comp][g.pidx(wrap2(ex, g.n[0]), wrap2(ey, g.n[1]), wrap2(ez, g.n[2]))];
         slot_edge(q, gx + st[0], gy + st[1], gz + st[2], comp, ex, ey, ez);
-        L2[q] = (C)(-A.dt * A.lEn[comp][g.pidx(wrap_idx(ex, g.n[0]), wrap_idx(ey, g.n[1]), wrap_idx(ez, g.n[2]))]);
+        L2[q] = (C)A.lJ[comp][g.pidx(wrap2(ex, g.n[0]), wrap2(ey, g.n[1]), wrap2(ez, g.n[2]))];
     }
     const C Cw[3] = {(C)A.C[0] * w, (C)A.C[1] * w, (C)A.C[2] * w};
     C gF1[3], gW1[3], gF2[3], gW2[3];
@@ -331,20 +332,23 @@ __device__ void adjoint_particle(const AdjArgs<T>& A, AddFn Add, int gx, int gy,
 
 // Each CTA takes a chunk of ADJ_CHUNK slots of one tile (blocks beyond the tiles'
 // chunks take the spill list).  The gather^T contributions of the chunk are summed in a
-// shared FP64 box of the tile's nodes -1..8 per dimension and added to the global
-// accumulators once per node.  Lane l of warp w handles slots 32 l + w + 8 m: the lanes
+// shared box of the tile's nodes -1..8 per dimension and added to the global FP64
+// accumulators once per node.  The box holds the working precision: FP64 sums on the
+// FP64 path, FP32 sums of at most ADJ_CHUNK terms on the FP32 path (whose per-particle
+// Jacobians are FP32 already), where FP64 additions would run on the GPU's narrow FP64
+// pipe.  Lane l of warp w handles slots 32 l + w + 8 m: the lanes
 // of a warp sit 32 slots apart in the cell-sorted segment, so they rarely add to the
 // same node at once (shared FP64 additions to one address serialise).
 constexpr int AB = 10;           // nodes per dimension of the shared adjoint box
 constexpr int ADJ_CHUNK = 1024;  // slots per CTA (8 warps x 32 lanes x 4)
 template <typename T>
 __global__ void __launch_bounds__(256) k_adj_particles(AdjArgs<T> A, int chunks_per_tile) {
-    __shared__ double sacc[6 * AB * AB * AB];
+    __shared__ T sacc[6 * AB * AB * AB];
     const Geom& g = A.g;
     const int nt = g.nt[0] * g.nt[1] * g.nt[2];
-    auto gadd = [&](int comp, int x, int y, int z, double v) {
+    auto gadd = [&](int comp, int x, int y, int z, T v) {
         double* acc = comp < 3 ? A.accE[comp] : A.accB[comp - 3];
-        atomicAdd(acc + g.cidx(wrap_idx(x, g.n[0]), wrap_idx(y, g.n[1]), wrap_idx(z, g.n[2])), v);
+        atomicAdd(acc + g.cidx(wrap_idx(x, g.n[0]), wrap_idx(y, g.n[1]), wrap_idx(z, g.n[2])), (double)v);
     };
     const long long nblk_tiles = (long long)nt * chunks_per_tile;
     if (blockIdx.x >= nblk_tiles) {   // the spill list
@@ -362,9 +366,9 @@ __global__ void __launch_bounds__(256) k_adj_particles(AdjArgs<T> A, int chunks_
     if (i0 >= cnt) return;
     const int tx = t % g.nt[0], ty = (t / g.nt[0]) % g.nt[1], tz = t / (g.nt[0] * g.nt[1]);
     const int ox = tx * TILE, oy = ty * TILE, oz = tz * TILE;
-    for (int i = threadIdx.x; i < 6 * AB * AB * AB; i += blockDim.x) sacc[i] = 0.0;
+    for (int i = threadIdx.x; i < 6 * AB * AB * AB; i += blockDim.x) sacc[i] = T(0);
     __syncthreads();
-    auto sadd = [&](int comp, int x, int y, int z, double v) {
+    auto sadd = [&](int comp, int x, int y, int z, T v) {
         atomicAdd(sacc + ((comp * AB + (z - oz + 1)) * AB + (y - oy + 1)) * AB + (x - ox + 1), v);
     };
     const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
@@ -381,11 +385,18 @@ __global__ void __launch_bounds__(256) k_adj_particles(AdjArgs<T> A, int chunks_
     }
     __syncthreads();
     for (int e = threadIdx.x; e < 6 * AB * AB * AB; e += blockDim.x) {
-        const double v = sacc[e];
-        if (v == 0.0) continue;
+        const T v = sacc[e];
+        if (v == T(0)) continue;
         const int lx = e % AB, ly = (e / AB) % AB, lz = (e / (AB * AB)) % AB, comp = e / (AB * AB * AB);
         gadd(comp, ox + lx - 1, oy + ly - 1, oz + lz - 1, v);
     }
+}
+
+// dst (working precision, padded) = scale * src (FP64, padded), ghosts included.
+template <typename T>
+__global__ void k_to_working(long long n, const double* src, T* dst, double scale) {
+    for (long long e = blockIdx.x * (long long)blockDim.x + threadIdx.x; e < n; e += (long long)gridDim.x * blockDim.x)
+        dst[e] = (T)(scale * src[e]);
 }
 
 // dst (FP64, padded) = scale * src (working precision, padded), ghosts included.
@@ -426,6 +437,7 @@ struct AdjBuffers {
     double* lE[3] = {};
     double* lB[3] = {};
     double* lEn[3] = {};
+    void* lJ[3] = {};       // -dt lEn in the working precision
     double* accE[3] = {};
     double* accB[3] = {};
     void* Bn[3] = {};
@@ -437,6 +449,12 @@ static pic_status adjoint_step_t(pic_ctx* c, AdjBuffers& b) {
     const double dt = c->desc.dt, h = 0.5 * dt;
     const size_t pb = sizeof(double) * (size_t)c->g.padded_size();
     for (int k = 0; k < 3; ++k) GBPIC_CHECK(c, cudaMemcpyAsync(b.lEn[k], b.lE[k], pb, cudaMemcpyDeviceToDevice, c->stream));
+    {   // lambda_J = -dt lambda_E^{n+1}, once per node in the working precision
+        LaunchScope ls(c, KC_OTHER);
+        for (int k = 0; k < 3; ++k)
+            k_to_working<T><<<1024, 256, 0, c->stream>>>(c->g.padded_size(), b.lEn[k], static_cast<T*>(b.lJ[k]), -dt);
+        GBPIC_CHECK(c, cudaGetLastError());
+    }
     // lB += dt C_E lE  (the Faraday stencil computes B - coef curl E)
     pic_status st = curl_to_b<double>(c, b.lE, b.lB, -dt);
     if (st != PIC_OK) return st;
@@ -471,7 +489,7 @@ static pic_status adjoint_step_t(pic_ctx* c, AdjBuffers& b) {
         for (int k = 0; k < 3; ++k) {
             A.E[k] = E[k];
             A.Bn[k] = Bn[k];
-            A.lEn[k] = b.lEn[k];
+            A.lJ[k] = static_cast<const T*>(b.lJ[k]);
             A.accE[k] = b.accE[k];
             A.accB[k] = b.accB[k];
         }
@@ -546,7 +564,8 @@ static pic_status backward_t(pic_ctx* c, AdjointState& S, const double* Ed, cons
         b.accE[k] = static_cast<double*>(alloc(cb));
         b.accB[k] = static_cast<double*>(alloc(cb));
         b.Bn[k] = alloc(fb);
-        if (!b.lE[k] || !b.lB[k] || !b.lEn[k] || !b.accE[k] || !b.accB[k] || !b.Bn[k]) return PIC_ERR_OOM;
+        b.lJ[k] = alloc(fb);
+        if (!b.lE[k] || !b.lB[k] || !b.lEn[k] || !b.accE[k] || !b.accB[k] || !b.Bn[k] || !b.lJ[k]) return PIC_ERR_OOM;
     }
     for (auto& s : c->species) {
         double* x = static_cast<double*>(alloc(sizeof(double) * 3 * std::max<int64_t>(s.n_loaded, 1)));

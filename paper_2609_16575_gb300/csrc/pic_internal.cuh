@@ -526,6 +526,12 @@ __device__ __forceinline__ int wrap_idx(int i, int n) {
 // Periodic wrap of an index at most one period outside [0, n) (-n <= i < 2n): a cell
 // index after a move of at most one cell, without a division.
 __device__ __forceinline__ int wrap1(int i, int n) { return i < 0 ? i + n : (i >= n ? i - n : i); }
+// The same for -n <= i < 3n (an edge next to a moved cell on a grid of one cell or more).
+__device__ __forceinline__ int wrap2(int i, int n) {
+    i = i < 0 ? i + n : i;
+    i = i >= n ? i - n : i;
+    return i >= n ? i - n : i;
+}
 
 // Ghost images of interior index i along a periodic dimension of n cells.
 __device__ __forceinline__ int images(int i, int n, int out[3]) {

@@ -86,20 +86,38 @@ template <typename T> struct WarpQueue {
 // Append, for every lane, the record (ka, va) if want_a and (kb, vb) if want_b: 12
 // values of the cell with origin index k (warp-collective).  The queue is drained
 // first whenever a kind's records would not fit; otherwise records accumulate until
-// the row's flush, so one drain pass adds the records of several particle steps.
+// the row's flush, so one drain pass adds the records of several particle steps.  With
+// Esirkepov's deposit the top of the queue's words holds the me stacked crosser
+// records (esk_stack), which lowers the capacity; they are processed first when even
+// an empty queue would not hold a kind's records.
 template <typename T>
 __device__ __forceinline__ void q_drain(WarpQueue<T> Q, int& qn, int lane, uint32_t sJa, int qoff);
 template <typename T>
-__device__ __forceinline__ void q_push(WarpQueue<T> Q, int& qn, bool want_a, int ka, const typename Pair<T>::t va[6],
-                                       bool want_b, int kb, const typename Pair<T>::t vb[6], int lane, uint32_t sJa,
-                                       int qoff) {
+__device__ __forceinline__ void esk_process(WarpQueue<T> Q, int& me, int lane, uint32_t sJa);
+constexpr int ESK_WORDS = 10;   // X1[3], X2[3], cw[3], packed first node
+constexpr int ESK_BATCH = 16;   // stacked crosser records per warp before they are processed
+static_assert(32 * ESK_WORDS <= QWORDS, "one particle step's crosser records fit in the record queue");
+__device__ __forceinline__ int q_cap(int me) {
+    const int c = (QWORDS - me * ESK_WORDS) / QS;
+    return c < QCAP ? c : QCAP;
+}
+template <typename T, bool ESK>
+__device__ __forceinline__ void q_push(WarpQueue<T> Q, int& qn, int& me, bool want_a, int ka,
+                                       const typename Pair<T>::t va[6], bool want_b, int kb,
+                                       const typename Pair<T>::t vb[6], int lane, uint32_t sJa, int qoff) {
     const unsigned ma = __ballot_sync(0xffffffffu, want_a), mb = __ballot_sync(0xffffffffu, want_b);
     if (!(ma | mb)) return;
     const unsigned lt = (1u << lane) - 1u;
-    if (qn + __popc(ma) > QCAP) q_drain(Q, qn, lane, sJa, qoff);
+    if (qn + __popc(ma) > (ESK ? q_cap(me) : QCAP)) {
+        q_drain(Q, qn, lane, sJa, qoff);
+        if (ESK && __popc(ma) > q_cap(me)) esk_process(Q, me, lane, sJa);
+    }
     if (want_a) Q.put(qn + __popc(ma & lt), ka, va);
     qn += __popc(ma);
-    if (qn + __popc(mb) > QCAP) q_drain(Q, qn, lane, sJa, qoff);
+    if (qn + __popc(mb) > (ESK ? q_cap(me) : QCAP)) {
+        q_drain(Q, qn, lane, sJa, qoff);
+        if (ESK && __popc(mb) > q_cap(me)) esk_process(Q, me, lane, sJa);
+    }
     if (want_b) Q.put(qn + __popc(mb & lt), kb, vb);
     qn += __popc(mb);
 }
@@ -223,20 +241,101 @@ template <> struct RowCells<2> {
     static __device__ __forceinline__ int key(const int c[2]) { return c[0] >= 0 ? c[0] : c[1]; }
 };
 
-// Esirkepov's deposit of the cell crossers of one particle step (warp-collective): the
-// record queue is drained, each crosser writes its record there (positions relative to
-// the first node of its support, cw, the first node and the crossed dimensions packed),
-// and the 32 lanes share the non-zero stencil values of each record in turn (20 of the
-// 3x3x3 support's 54 for a move across one face; see esk_value).
-constexpr int ESK_WORDS = 10;   // X1[3], X2[3], cw[3], packed first node
-static_assert(32 * ESK_WORDS <= QWORDS, "the crossers' records fit in the record queue");
+// Esirkepov's deposit of the cell crossers (warp-collective).  A crosser's record
+// (positions relative to the first node of its support, cw, the first node and the
+// crossed dimensions packed) is stacked at the top of the warp's record-queue words,
+// record e at QWORDS - (e + 1) ESK_WORDS, beside the ZigZag-style records below; a
+// batch of up to ESK_BATCH records is processed at once: the non-zero stencil values of
+// all its records (20 of the 3x3x3 support's 54 for a move across one face; see
+// esk_value) are numbered consecutively and the 32 lanes take them in turn, so neither
+// a crosser forces the record queue to drain nor does a lone crosser leave most lanes
+// idle.
+template <typename T> __device__ __forceinline__ T* esk_rec(WarpQueue<T> Q, int e) {
+    return Q.rec + QWORDS - (e + 1) * ESK_WORDS;
+}
+__device__ __forceinline__ void esk_counts(int pk, int& n0, int& n1, int& n2) {
+    const int cx = (pk >> 12) & 1, cy = (pk >> 13) & 1, cz = (pk >> 14) & 1;
+    // values of component c: (1 + crossed_c) edges x (2 + crossed_p) x (2 + crossed_r) nodes
+    n0 = (1 + cx) * (2 + cy) * (2 + cz);
+    n1 = (1 + cy) * (2 + cz) * (2 + cx);
+    n2 = (1 + cz) * (2 + cx) * (2 + cy);
+}
 template <typename T>
-__device__ __forceinline__ void esk_crossers(WarpQueue<T> Q, int& qn, int lane, uint32_t sJa, int qoff, bool mine, int x,
-                                             int y, int z, const T d1[3], const T d2[3], const int s[3], const T cw[3]) {
-    if (qn) q_drain(Q, qn, lane, sJa, qoff);
+__device__ __forceinline__ void esk_process(WarpQueue<T> Q, int& me, int lane, uint32_t sJa) {
+    __syncwarp();
+    int cnt = 0;
+    if (lane < me) {
+        int n0, n1, n2;
+        esk_counts(*reinterpret_cast<const int*>(esk_rec(Q, lane) + 9), n0, n1, n2);
+        cnt = n0 + n1 + n2;
+    }
+    int incl = cnt;
+#pragma unroll
+    for (int o = 1; o < 32; o <<= 1) {
+        const int y = __shfl_up_sync(0xffffffffu, incl, o);
+        if (lane >= o) incl += y;
+    }
+    const int excl = incl - cnt;
+    const int total = __shfl_sync(0xffffffffu, incl, 31);
+    for (int base = 0; base < total; base += 32) {
+        const int v = base + lane;
+        // the record holding value v: the last r < me with excl_r <= v
+        int r = 0;
+#pragma unroll
+        for (int st = 16; st > 0; st >>= 1) {
+            const int cand = r + st;
+            const int ec = __shfl_sync(0xffffffffu, excl, cand & 31);
+            if (cand < me && ec <= v) r = cand;
+        }
+        const int er = __shfl_sync(0xffffffffu, excl, r);
+        if (v >= total) continue;
+        const T* rec = esk_rec(Q, r);
+        const int pk = *reinterpret_cast<const int*>(rec + 9);
+        int n0, n1, n2;
+        esk_counts(pk, n0, n1, n2);
+        const int cx = (pk >> 12) & 1, cy = (pk >> 13) & 1, cz = (pk >> 14) & 1;
+        const int t = v - er;
+        int comp, q;
+        if (t < n0) {
+            comp = 0;
+            q = t;
+        } else if (t < n0 + n1) {
+            comp = 1;
+            q = t - n0;
+        } else {
+            comp = 2;
+            q = t - n0 - n1;
+        }
+        const int cp = comp == 0 ? cy : (comp == 1 ? cz : cx);   // the next dimension, cyclic
+        const int np_ = 2 + cp, nr = 2 + (comp == 0 ? cz : (comp == 1 ? cx : cy));
+        const int i = q / (np_ * nr), rem = q - i * np_ * nr;
+        const int jp = rem / nr, jr = rem - jp * nr;
+        const T X1[3] = {rec[0], rec[1], rec[2]}, X2[3] = {rec[3], rec[4], rec[5]}, c3w[3] = {rec[6], rec[7], rec[8]};
+        const T val = esk_value(X1, X2, c3w, comp, i, jp, jr);
+        if (val == T(0)) continue;
+        // the value's location: edge i along comp, node jp along the next dimension and
+        // jr along the one after (cyclic), from the support's first node
+        const int ax = comp == 0 ? i : (comp == 2 ? jp : jr);
+        const int ay = comp == 1 ? i : (comp == 0 ? jp : jr);
+        const int az = comp == 2 ? i : (comp == 1 ? jp : jr);
+        tile_add(sJa, tile_index(comp, (pk & 15) - 1 + ax, ((pk >> 4) & 15) - 1 + ay, ((pk >> 8) & 15) - 1 + az),
+                 JT_ELEMS, val);
+    }
+    __syncwarp();
+    me = 0;
+}
+// Stack the records of this particle step's crossers (mine), processing the stacked
+// batch first when it would grow past ESK_BATCH or meet the queued records.
+template <typename T>
+__device__ __forceinline__ void esk_stack(WarpQueue<T> Q, int& qn, int& me, int lane, uint32_t sJa, int qoff,
+                                          bool mine, int x, int y, int z, const T d1[3], const T d2[3], const int s[3],
+                                          const T cw[3]) {
     const unsigned mc = __ballot_sync(0xffffffffu, mine);
+    const int nn = __popc(mc);
+    if (me + nn > ESK_BATCH || qn * QS + (me + nn) * ESK_WORDS > QWORDS) esk_process(Q, me, lane, sJa);
+    if (qn * QS + (me + nn) * ESK_WORDS > QWORDS) q_drain(Q, qn, lane, sJa, qoff);
     if (mine) {
-        T* rec = Q.rec + __popc(mc & ((1u << lane) - 1u)) * ESK_WORDS;
+        T* rec = esk_rec(Q, me + __popc(mc & ((1u << lane) - 1u)));
         int b[3];
 #pragma unroll
         for (int k = 0; k < 3; ++k) {
@@ -250,46 +349,7 @@ __device__ __forceinline__ void esk_crossers(WarpQueue<T> Q, int& qn, int lane, 
         *reinterpret_cast<int*>(rec + 9) = (x + b[0] + 1) | ((y + b[1] + 1) << 4) | ((z + b[2] + 1) << 8) |
                                            ((s[0] != 0) << 12) | ((s[1] != 0) << 13) | ((s[2] != 0) << 14);
     }
-    __syncwarp();
-    // only the support's non-zero part: along a dimension the move did not cross, the
-    // third node carries no weight and the second edge no current
-    const int m = __popc(mc);
-    for (int r = 0; r < m; ++r) {
-        const T* rec = Q.rec + r * ESK_WORDS;
-        const int pk = *reinterpret_cast<const int*>(rec + 9);
-        const int cx = (pk >> 12) & 1, cy = (pk >> 13) & 1, cz = (pk >> 14) & 1;
-        // values of component c: (1 + crossed_c) edges x (2 + crossed_p) x (2 + crossed_r) nodes
-        const int n0 = (1 + cx) * (2 + cy) * (2 + cz), n1 = (1 + cy) * (2 + cz) * (2 + cx);
-        const int n2 = (1 + cz) * (2 + cx) * (2 + cy);
-        for (int t = lane; t < n0 + n1 + n2; t += 32) {
-            int comp, q;
-            if (t < n0) {
-                comp = 0;
-                q = t;
-            } else if (t < n0 + n1) {
-                comp = 1;
-                q = t - n0;
-            } else {
-                comp = 2;
-                q = t - n0 - n1;
-            }
-            const int cp = comp == 0 ? cy : (comp == 1 ? cz : cx);   // the next dimension, cyclic
-            const int np_ = 2 + cp, nr = 2 + (comp == 0 ? cz : (comp == 1 ? cx : cy));
-            const int i = q / (np_ * nr), rem = q - i * np_ * nr;
-            const int jp = rem / nr, jr = rem - jp * nr;
-            const T X1[3] = {rec[0], rec[1], rec[2]}, X2[3] = {rec[3], rec[4], rec[5]}, c3w[3] = {rec[6], rec[7], rec[8]};
-            const T v = esk_value(X1, X2, c3w, comp, i, jp, jr);
-            if (v == T(0)) continue;
-            // the value's location: edge i along comp, node jp along the next dimension
-            // and jr along the one after (cyclic), from the support's first node
-            const int ax = comp == 0 ? i : (comp == 2 ? jp : jr);
-            const int ay = comp == 1 ? i : (comp == 0 ? jp : jr);
-            const int az = comp == 2 ? i : (comp == 1 ? jp : jr);
-            tile_add(sJa, tile_index(comp, (pk & 15) - 1 + ax, ((pk >> 4) & 15) - 1 + ay, ((pk >> 8) & 15) - 1 + az),
-                     JT_ELEMS, v);
-        }
-    }
-    __syncwarp();
+    me += nn;
 }
 
 // Write a warp's mq staged movers to the global mover list: one counter atomic per
@@ -461,6 +521,7 @@ k_tile_push(const __grid_constant__ CUtensorMap tE0, const __grid_constant__ CUt
     Q.rec = reinterpret_cast<T*>(sQ) + (size_t)warp * QWORDS;
     const int qoff = slot_offset(lane < 12 ? lane : (lane < 24 ? lane - 12 : 0));
     int qn = 0;                   // queued records (warp-uniform)
+    int me = 0;                   // stacked Esirkepov crosser records (warp-uniform)
     const int seg = A.pa.seg_start[tile];   // slots of a block are below 2^31
     const int ngroups = (cnt + R - 1) / R;
     double kacc = 0.0;
@@ -616,9 +677,10 @@ k_tile_push(const __grid_constant__ CUtensorMap tE0, const __grid_constant__ CUt
 #pragma unroll
                 for (int q = 0; q < 6; ++q) acc[q] = Pair<T>::add(acc[q], v[q]);
             }
-            q_push(Q, qn, active && !summed && !esk_cross, tile_index(0, x, y, z), v, !ESK && crossed,
-                   tile_index(0, x + s[0], y + s[1], z + s[2]), v2, lane, sJa, qoff);
-            if (ESK && __any_sync(0xffffffffu, esk_cross)) esk_crossers<T>(Q, qn, lane, sJa, qoff, esk_cross, x, y, z, d1, d2, s, cw);
+            q_push<T, ESK>(Q, qn, me, active && !summed && !esk_cross, tile_index(0, x, y, z), v, !ESK && crossed,
+                           tile_index(0, x + s[0], y + s[1], z + s[2]), v2, lane, sJa, qoff);
+            if (ESK && __any_sync(0xffffffffu, esk_cross))
+                esk_stack<T>(Q, qn, me, lane, sJa, qoff, esk_cross, x, y, z, d1, d2, s, cw);
             // movers: staged in shared memory with their wrapped global cell and written to
             // the global list in batches; a particle that left an open x face is removed
             // instead
@@ -651,6 +713,7 @@ k_tile_push(const __grid_constant__ CUtensorMap tE0, const __grid_constant__ CUt
             }
         }
         if (qn) q_drain(Q, qn, lane, sJa, qoff);   // the flush stages its sums in the queue
+        if (ESK && me) esk_process(Q, me, lane, sJa);
         flush_warp<T>(acc, key >= 0 ? tile_index(0, key & 7, (key >> 3) & 7, key >> 6) : -1, lane, Q, sJa, qoff);
     }
     if (mq) movers_flush(A, sM, mq, lane);
