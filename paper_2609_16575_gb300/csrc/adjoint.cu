@@ -135,8 +135,8 @@ template <typename T> struct AdjArgs {
     const T* lJ[3];     // lambda_J = -dt lambda of E^{n+1} (padded), in the working precision
     double* accE[3];    // gather^T accumulators (compact)
     double* accB[3];
-    double* lX;         // 3 x nload lambda of positions (cell units), load order
-    double* lU;         // 3 x nload lambda of momenta
+    T* lX;              // 3 x nload lambda of positions (cell units), load order
+    T* lU;              // 3 x nload lambda of momenta
     long long nload;
     double eps, dt, dtd[3], C[3];   // C = q / (dt d_p d_r)
 };
@@ -207,9 +207,11 @@ __device__ __forceinline__ void cross3(const C a[3], const C b[3], C o[3]) {
     o[2] = a[0] * b[1] - a[1] * b[0];
 }
 
-// The particle part of one adjoint step.  The per-particle Jacobian products run in
-// the working precision C (FP32 on the FP32 path); the adjoint states carried across
-// steps (lambda of positions and momenta) and the field accumulators are FP64.
+// The particle part of one adjoint step.  The per-particle Jacobian products and the
+// particles' adjoint state carried across steps (lambda of positions and momenta, like
+// the forward particle state) run in the working precision C (FP32 on the FP32 path,
+// where FP64 arithmetic would run on the GPU's narrow FP64 pipe); the field
+// accumulators and the parameter gradients are FP64 on both paths.
 template <typename T, typename C, typename AddFn>
 __device__ void adjoint_particle(const AdjArgs<T>& A, AddFn Add, int gx, int gy, int gz, const C d1[3], const C u0[3], C w,
                                  int id) {
@@ -291,12 +293,11 @@ __device__ void adjoint_particle(const AdjArgs<T>& A, AddFn Add, int gx, int gy,
     }
     // ---- the adjoint of the next state (FP64), and the position update
     // X^{n+1} = X^n + dtd u / gamma
-    double lx1[3];
-    C lun[3], a[3];
+    C lx1[3], lun[3], a[3];
     for (int k = 0; k < 3; ++k) {
-        const double lx2 = (double)lx2c[k] + A.lX[k * A.nload + id];
-        lx1[k] = (double)lx1c[k] + lx2;
-        a[k] = (C)(lx2 * A.dtd[k]);
+        const C lx2 = lx2c[k] + (C)A.lX[k * A.nload + id];
+        lx1[k] = lx1c[k] + lx2;
+        a[k] = lx2 * (C)A.dtd[k];
     }
     const C adot = a[0] * un[0] + a[1] * un[1] + a[2] * un[2];
     for (int k = 0; k < 3; ++k) lun[k] = (C)A.lU[k * A.nload + id] + (a[k] - un[k] * adot * ig * ig) * ig;
@@ -318,15 +319,15 @@ __device__ void adjoint_particle(const AdjArgs<T>& A, AddFn Add, int gx, int gy,
     for (int k = 0; k < 3; ++k) {
         C acc = 0;
         for (int c = 0; c < 3; ++c) acc += lE[c] * grad[c][k] + lB[c] * grad[3 + c][k];
-        lx1[k] += (double)acc;
+        lx1[k] += acc;
     }
     for (int c = 0; c < 3; ++c) {
         scatter_trilinear(Add, c, cb[c], cs[c], lE[c]);
         scatter_trilinear(Add, 3 + c, cb[3 + c], cs[3 + c], lB[c]);
     }
     for (int k = 0; k < 3; ++k) {
-        A.lX[k * A.nload + id] = lx1[k];
-        A.lU[k * A.nload + id] = (double)lum[k];
+        A.lX[k * A.nload + id] = (T)lx1[k];
+        A.lU[k * A.nload + id] = (T)lum[k];
     }
 }
 
@@ -441,7 +442,7 @@ struct AdjBuffers {
     double* accE[3] = {};
     double* accB[3] = {};
     void* Bn[3] = {};
-    std::vector<double*> lX, lU;
+    std::vector<void*> lX, lU;   // the particles' adjoint state, working precision
 };
 
 template <typename T>
@@ -493,8 +494,8 @@ static pic_status adjoint_step_t(pic_ctx* c, AdjBuffers& b) {
             A.accE[k] = b.accE[k];
             A.accB[k] = b.accB[k];
         }
-        A.lX = b.lX[si];
-        A.lU = b.lU[si];
+        A.lX = static_cast<T*>(b.lX[si]);
+        A.lU = static_cast<T*>(b.lU[si]);
         A.nload = s.n_loaded;
         A.eps = s.q * dt / (2.0 * s.m);
         A.dt = dt;
@@ -568,11 +569,12 @@ static pic_status backward_t(pic_ctx* c, AdjointState& S, const double* Ed, cons
         if (!b.lE[k] || !b.lB[k] || !b.lEn[k] || !b.accE[k] || !b.accB[k] || !b.Bn[k] || !b.lJ[k]) return PIC_ERR_OOM;
     }
     for (auto& s : c->species) {
-        double* x = static_cast<double*>(alloc(sizeof(double) * 3 * std::max<int64_t>(s.n_loaded, 1)));
-        double* u = static_cast<double*>(alloc(sizeof(double) * 3 * std::max<int64_t>(s.n_loaded, 1)));
+        const size_t nb = sizeof(T) * 3 * std::max<int64_t>(s.n_loaded, 1);
+        void* x = alloc(nb);
+        void* u = alloc(nb);
         if (!x || !u) return PIC_ERR_OOM;
-        GBPIC_CHECK(c, cudaMemsetAsync(x, 0, sizeof(double) * 3 * s.n_loaded, c->stream));
-        GBPIC_CHECK(c, cudaMemsetAsync(u, 0, sizeof(double) * 3 * s.n_loaded, c->stream));
+        GBPIC_CHECK(c, cudaMemsetAsync(x, 0, nb, c->stream));
+        GBPIC_CHECK(c, cudaMemsetAsync(u, 0, nb, c->stream));
         b.lX.push_back(x);
         b.lU.push_back(u);
     }
@@ -644,7 +646,18 @@ static pic_status backward_t(pic_ctx* c, AdjointState& S, const double* Ed, cons
     if (dL_du) {
         for (size_t si = 0; si < c->species.size(); ++si) {
             if (!dL_du[si]) continue;
-            GBPIC_CHECK(c, cudaMemcpyAsync(dL_du[si], b.lU[si], sizeof(double) * 3 * c->species[si].n_loaded,
+            // the momenta's adjoint in FP64 (a converted copy on the FP32 path)
+            const long long m = 3 * c->species[si].n_loaded;
+            const double* src = static_cast<const double*>(b.lU[si]);
+            if (sizeof(T) != sizeof(double) && m > 0) {
+                double* conv = static_cast<double*>(alloc(sizeof(double) * m));
+                if (!conv) return PIC_ERR_OOM;
+                LaunchScope ls(c, KC_OTHER);
+                k_scale_copy<T><<<1024, 256, 0, c->stream>>>(m, static_cast<const T*>(b.lU[si]), conv, 1.0);
+                GBPIC_CHECK(c, cudaGetLastError());
+                src = conv;
+            }
+            GBPIC_CHECK(c, cudaMemcpyAsync(dL_du[si], src, sizeof(double) * m,
                                            devptr ? cudaMemcpyDeviceToDevice : cudaMemcpyDeviceToHost, c->stream));
         }
     }

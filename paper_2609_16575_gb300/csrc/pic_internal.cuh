@@ -478,7 +478,7 @@ __device__ __forceinline__ T esk_value(const T X1[3], const T X2[3], const T cw[
     const T x1c = sel3(X1, comp), x2c = sel3(X2, comp);
     const T s0p = cic_w(x1p - T(jp)), dsp = cic_w(x2p - T(jp)) - s0p;
     const T s0r = cic_w(x1r - T(jr)), dsr = cic_w(x2r - T(jr)) - s0r;
-    const T t = s0p * s0r + T(0.5) * dsp * s0r + T(0.5) * s0p * dsr + dsp * dsr / T(3);
+    const T t = s0p * s0r + T(0.5) * dsp * s0r + T(0.5) * s0p * dsr + dsp * dsr * T(1.0 / 3.0);
     T acc = (cic_w(x2c) - cic_w(x1c)) * t;
     if (i == 1) acc += (cic_w(x2c - T(1)) - cic_w(x1c - T(1))) * t;
     return -sel3(cw, comp) * acc;

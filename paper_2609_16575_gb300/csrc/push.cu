@@ -308,8 +308,10 @@ __device__ __forceinline__ void esk_process(WarpQueue<T> Q, int& me, int lane, u
         }
         const int cp = comp == 0 ? cy : (comp == 1 ? cz : cx);   // the next dimension, cyclic
         const int np_ = 2 + cp, nr = 2 + (comp == 0 ? cz : (comp == 1 ? cx : cy));
-        const int i = q / (np_ * nr), rem = q - i * np_ * nr;
-        const int jp = rem / nr, jr = rem - jp * nr;
+        // q = (i np_ + jp) nr + jr with i < 2, jp < np_ <= 3, jr < nr <= 3 (no division:
+        // rem / 3 = (11 rem) >> 5 for rem < 9)
+        const int i = q >= np_ * nr ? 1 : 0, rem = q - i * np_ * nr;
+        const int jp = nr == 2 ? rem >> 1 : (rem * 11) >> 5, jr = rem - jp * nr;
         const T X1[3] = {rec[0], rec[1], rec[2]}, X2[3] = {rec[3], rec[4], rec[5]}, c3w[3] = {rec[6], rec[7], rec[8]};
         const T val = esk_value(X1, X2, c3w, comp, i, jp, jr);
         if (val == T(0)) continue;

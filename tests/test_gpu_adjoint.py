@@ -83,9 +83,11 @@ def test_adjoint_matches_central_differences():
 
 
 def _cell_checksum(ctx, n, npart):
-    """Two integer sums that change when any particle's cell changes: sum of the linear
-    cell index and sum of (id + 1) times it, from a device-side read-out (rows in id
-    order)."""
+    """Two integer sums that change when any particle's half cell changes: sum of the
+    linear half-cell index and sum of (id + 1) times it, from a device-side read-out
+    (rows in id order).  Half cells, because the forward map has kinks there as well as
+    at the faces: a half-located field component is interpolated from the samples on
+    either side of the particle, which switch at offset 1/2."""
     import ctypes
 
     from paper_2609_16575_gb300 import gbpic
@@ -93,8 +95,8 @@ def _cell_checksum(ctx, n, npart):
     out = torch.empty((7, npart), dtype=torch.float64, device="cuda")
     cnt = ctypes.c_int64(npart)
     assert gbpic.lib().pic_get_particles(ctx.ptr, 0, ctypes.c_void_p(out.data_ptr()), ctypes.byref(cnt), 1) == 0
-    c = torch.floor(out[0:3]).to(torch.int64)
-    lin = (c[2] * n[1] + c[1]) * n[0] + c[0]
+    c = torch.floor(2.0 * out[0:3]).to(torch.int64)
+    lin = (c[2] * (2 * n[1]) + c[1]) * (2 * n[0]) + c[0]
     ids = torch.arange(1, npart + 1, device="cuda", dtype=torch.int64)
     return int(lin.sum()), int((lin * ids).sum())
 
@@ -118,12 +120,13 @@ def _checked_forward(wl, P, A, E_dir, B_dir, nsteps):
 def test_adjoint_matches_central_differences_on_the_differentiable_run():
     """The differentiable-run workload at its full size: 32^3 cells, 16 per cell (524,288
     electrons), u_th = 0.02, plane wave of amplitude 0.05, 200 steps, checkpoints every 20.
-    The adjoint's amplitude derivative and its momentum gradient along random directions
+    The adjoint's amplitude derivative and its momentum gradient along directions
     (on 2048 particles each) agree with central differences of the FP64 forward map to
     1e-4.  A perturbation
-    counts only if no particle's cell changes differently at any step (per-step cell
-    checksums of the perturbed runs equal the unperturbed run's); another direction is
-    drawn otherwise."""
+    counts only if no particle's half cell changes differently at any step (per-step
+    checksums of the perturbed runs equal the unperturbed run's: the map has kinks at
+    cell faces and at half cells); another direction, or a smaller step, is drawn
+    otherwise."""
     wl = W.differentiable()
     E_dir, B_dir = plane_wave_fields(wl.n, wl.d, wl.dt, amplitude=1.0)
     A = 0.05
@@ -142,15 +145,20 @@ def test_adjoint_matches_central_differences_on_the_differentiable_run():
         pytest.fail("every amplitude step changed a cell crossing")
     fdA = (LAp - LAm) / (2 * hA)
     assert abs(fdA - dA) <= 1e-4 * abs(dA), (rel, fdA, dA)
-    # momenta, along random directions on 2048 random particles (a direction over every
-    # particle shifts some crossing by a step almost surely at any usable h)
+    # momenta, along directions on 2048 random particles (a direction over every
+    # particle shifts some crossing by a step almost surely at any usable h), with
+    # random magnitudes and the signs of the adjoint's own components: the directional
+    # derivative is then a sum of same-sign terms, large against the central
+    # difference's noise (the FP64 forward map sums J with atomics in any order and
+    # reproduces L only to about 1e-15; over 2h = 2e-8 that is ~1e-7, as large as 1e-4
+    # of a random-sign sum), and a wrong sign or size of any component still shows
     rng = np.random.default_rng(6)
     checked = 0
-    for attempt in range(6):
+    for attempt in range(8):
         v = np.zeros((3, P.shape[1]))
         pick = rng.choice(P.shape[1], 2048, replace=False)
-        v[:, pick] = rng.standard_normal((3, pick.size))
-        h = 1e-8 if attempt < 3 else 1e-9
+        v[:, pick] = np.sign(du[:, pick]) * (0.5 + rng.random((3, pick.size)))
+        h = (1e-8, 1e-8, 3e-9, 3e-9, 1e-9, 1e-9, 1e-9, 1e-9)[attempt]
         Pp, Pm = P.copy(), P.copy()
         Pp[3:6] += h * v
         Pm[3:6] -= h * v
@@ -187,8 +195,8 @@ def test_autograd_function():
 
 
 def test_fp32_adjoint_against_fp64():
-    """The FP32 path's adjoint (working-precision Jacobian products, FP64 adjoint state
-    and accumulation) against the FP64 adjoint on the same FP32-representable inputs:
+    """The FP32 path's adjoint (working-precision Jacobian products and particle adjoint
+    state, FP64 field accumulation) against the FP64 adjoint on the same FP32-representable inputs:
     loss, momentum gradient and amplitude gradient within 1e-3 (the FP32 forward
     trajectory itself departs from the FP64 one at the 1e-6 level over 40 steps)."""
     from paper_2609_16575_gb300 import gbpic
