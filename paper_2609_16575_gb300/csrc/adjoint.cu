@@ -54,6 +54,68 @@ static size_t field_bytes(pic_ctx* c) { return (size_t)c->g.padded_size() * c->e
 static int ntiles(pic_ctx* c) { return c->g.nt[0] * c->g.nt[1] * c->g.nt[2]; }
 static size_t rec_bytes(pic_ctx* c) { return c->prec == PIC_FP64 ? sizeof(Rec<double>) : sizeof(Rec<float>); }
 
+// Several device-to-device copies in one launch (a snapshot is a dozen buffers; at the
+// sizes of the differentiable run one launch per buffer cost more than the bytes).
+// Blocks stride over each item in the widest units that both its addresses allow:
+// 16-byte vectors when both are 16-byte aligned, then 4-byte words when both are
+// 4-byte aligned, then bytes (a snapshot's tile counts sit at 4-byte offsets).
+constexpr int MCOPY_MAX = 16;
+struct CopyList {
+    const void* src[MCOPY_MAX];
+    void* dst[MCOPY_MAX];
+    long long bytes[MCOPY_MAX];
+    int n;
+};
+__global__ void k_multi_copy(CopyList L) {
+    const long long t0 = blockIdx.x * (long long)blockDim.x + threadIdx.x, st = (long long)gridDim.x * blockDim.x;
+    for (int it = 0; it < L.n; ++it) {
+        const uintptr_t al = reinterpret_cast<uintptr_t>(L.src[it]) | reinterpret_cast<uintptr_t>(L.dst[it]);
+        const long long nb = L.bytes[it];
+        long long done = 0;
+        if ((al & 15) == 0) {
+            const uint4* s = static_cast<const uint4*>(L.src[it]);
+            uint4* d = static_cast<uint4*>(L.dst[it]);
+            const long long n16 = nb >> 4;
+            for (long long e = t0; e < n16; e += st) d[e] = s[e];
+            done = n16 << 4;
+        }
+        if ((al & 3) == 0) {
+            const unsigned* s = static_cast<const unsigned*>(L.src[it]);
+            unsigned* d = static_cast<unsigned*>(L.dst[it]);
+            const long long nw = nb >> 2;
+            for (long long e = (done >> 2) + t0; e < nw; e += st) d[e] = s[e];
+            done = nw << 2;
+        }
+        const unsigned char* s = static_cast<const unsigned char*>(L.src[it]);
+        unsigned char* d = static_cast<unsigned char*>(L.dst[it]);
+        for (long long e = done + t0; e < nb; e += st) d[e] = s[e];
+    }
+}
+struct MultiCopy {
+    pic_ctx* c;
+    CopyList L{};
+    pic_status st = PIC_OK;
+    explicit MultiCopy(pic_ctx* cc) : c(cc) {}
+    void add(void* dst, const void* src, size_t bytes) {
+        if (st != PIC_OK || bytes == 0) return;
+        if (L.n == MCOPY_MAX) flush();
+        L.src[L.n] = src;
+        L.dst[L.n] = dst;
+        L.bytes[L.n] = (long long)bytes;
+        ++L.n;
+    }
+    pic_status flush() {
+        if (st == PIC_OK && L.n > 0) {
+            LaunchScope ls(c, KC_OTHER);
+            k_multi_copy<<<1024, 256, 0, c->stream>>>(L);
+            const cudaError_t e = cudaGetLastError();
+            if (e != cudaSuccess) st = cuda_fail(c, e, "k_multi_copy");
+        }
+        L.n = 0;
+        return st;
+    }
+};
+
 static pic_status snap_alloc(pic_ctx* c, Snapshot& S) {
     if (S.alloc) return PIC_OK;
     for (int k = 0; k < 6; ++k)
@@ -75,47 +137,49 @@ static pic_status snap_save(pic_ctx* c, Snapshot& S) {
     pic_status st = snap_alloc(c, S);
     if (st != PIC_OK) return st;
     const size_t fb = field_bytes(c);
+    MultiCopy M(c);
     for (int k = 0; k < 3; ++k) {
-        GBPIC_CHECK(c, cudaMemcpyAsync(S.fields[k], c->E[k], fb, cudaMemcpyDeviceToDevice, c->stream));
-        GBPIC_CHECK(c, cudaMemcpyAsync(S.fields[3 + k], c->B[k], fb, cudaMemcpyDeviceToDevice, c->stream));
+        M.add(S.fields[k], c->E[k], fb);
+        M.add(S.fields[3 + k], c->B[k], fb);
     }
     for (size_t i = 0; i < c->species.size(); ++i) {
         SpeciesDev& s = c->species[i];
         SpeciesSnap& z = S.sp[i];
         z.cur = s.cur;
-        GBPIC_CHECK(c, cudaMemcpyAsync(z.part, s.base[s.cur], s.pbytes, cudaMemcpyDeviceToDevice, c->stream));
-        GBPIC_CHECK(c, cudaMemcpyAsync(z.counts, s.count, sizeof(int) * ntiles(c), cudaMemcpyDeviceToDevice, c->stream));
-        GBPIC_CHECK(c, cudaMemcpyAsync(static_cast<int*>(z.counts) + ntiles(c), s.holes, sizeof(int) * ntiles(c),
-                                       cudaMemcpyDeviceToDevice, c->stream));
-        GBPIC_CHECK(c, cudaMemcpyAsync(static_cast<int*>(z.counts) + 2 * ntiles(c), s.hist[s.cur],
-                                       sizeof(int) * TILE_CELLS * ntiles(c), cudaMemcpyDeviceToDevice, c->stream));
-        GBPIC_CHECK(c, cudaMemcpyAsync(z.ctr, s.ctr, sizeof(Counters), cudaMemcpyDeviceToDevice, c->stream));
-        GBPIC_CHECK(c, cudaMemcpyAsync(z.spill, s.spill, rec_bytes(c) * s.spill_cap, cudaMemcpyDeviceToDevice, c->stream));
+        M.add(z.part, s.base[s.cur], s.pbytes);
+        M.add(z.counts, s.count, sizeof(int) * ntiles(c));
+        M.add(static_cast<int*>(z.counts) + ntiles(c), s.holes, sizeof(int) * ntiles(c));
+        M.add(static_cast<int*>(z.counts) + 2 * ntiles(c), s.hist[s.cur], sizeof(int) * TILE_CELLS * ntiles(c));
+        M.add(z.ctr, s.ctr, sizeof(Counters));
+        M.add(z.spill, s.spill, rec_bytes(c) * s.spill_cap);
     }
+    st = M.flush();
+    if (st != PIC_OK) return st;
     S.step = c->step;
     return PIC_OK;
 }
 
 static pic_status snap_restore(pic_ctx* c, const Snapshot& S) {
     const size_t fb = field_bytes(c);
+    MultiCopy M(c);
     for (int k = 0; k < 3; ++k) {
-        GBPIC_CHECK(c, cudaMemcpyAsync(c->E[k], S.fields[k], fb, cudaMemcpyDeviceToDevice, c->stream));
-        GBPIC_CHECK(c, cudaMemcpyAsync(c->B[k], S.fields[3 + k], fb, cudaMemcpyDeviceToDevice, c->stream));
-        GBPIC_CHECK(c, cudaMemsetAsync(c->J[k], 0, sizeof(long long) * (size_t)c->g.N, c->stream));
+        M.add(c->E[k], S.fields[k], fb);
+        M.add(c->B[k], S.fields[3 + k], fb);
     }
     for (size_t i = 0; i < c->species.size(); ++i) {
         SpeciesDev& s = c->species[i];
         const SpeciesSnap& z = S.sp[i];
         s.cur = z.cur;
-        GBPIC_CHECK(c, cudaMemcpyAsync(s.base[s.cur], z.part, s.pbytes, cudaMemcpyDeviceToDevice, c->stream));
-        GBPIC_CHECK(c, cudaMemcpyAsync(s.count, z.counts, sizeof(int) * ntiles(c), cudaMemcpyDeviceToDevice, c->stream));
-        GBPIC_CHECK(c, cudaMemcpyAsync(s.holes, static_cast<const int*>(z.counts) + ntiles(c), sizeof(int) * ntiles(c),
-                                       cudaMemcpyDeviceToDevice, c->stream));
-        GBPIC_CHECK(c, cudaMemcpyAsync(s.hist[s.cur], static_cast<const int*>(z.counts) + 2 * ntiles(c),
-                                       sizeof(int) * TILE_CELLS * ntiles(c), cudaMemcpyDeviceToDevice, c->stream));
-        GBPIC_CHECK(c, cudaMemcpyAsync(s.ctr, z.ctr, sizeof(Counters), cudaMemcpyDeviceToDevice, c->stream));
-        GBPIC_CHECK(c, cudaMemcpyAsync(s.spill, z.spill, rec_bytes(c) * s.spill_cap, cudaMemcpyDeviceToDevice, c->stream));
+        M.add(s.base[s.cur], z.part, s.pbytes);
+        M.add(s.count, z.counts, sizeof(int) * ntiles(c));
+        M.add(s.holes, static_cast<const int*>(z.counts) + ntiles(c), sizeof(int) * ntiles(c));
+        M.add(s.hist[s.cur], static_cast<const int*>(z.counts) + 2 * ntiles(c), sizeof(int) * TILE_CELLS * ntiles(c));
+        M.add(s.ctr, z.ctr, sizeof(Counters));
+        M.add(s.spill, z.spill, rec_bytes(c) * s.spill_cap);
     }
+    pic_status st = M.flush();
+    if (st != PIC_OK) return st;
+    for (int k = 0; k < 3; ++k) GBPIC_CHECK(c, cudaMemsetAsync(c->J[k], 0, sizeof(long long) * (size_t)c->g.N, c->stream));
     c->step = S.step;
     c->j_dirty = false;
     return PIC_OK;
@@ -129,7 +193,9 @@ template <typename T> struct AdjArgs {
     Geom g;
     ParticleArrays<T> pa;
     const Rec<T>* spill;
-    int nsp;
+    const Counters* ctr;   // the spill count of the state: ctr->spill_count[parity]
+    int parity;
+    int spill_cap;
     const T* E[3];      // E^n
     const T* Bn[3];     // B_n = B^{n-1/2} - dt/2 curl E^n
     const T* lJ[3];     // lambda_J = -dt lambda of E^{n+1} (padded), in the working precision
@@ -353,7 +419,8 @@ __global__ void __launch_bounds__(256) k_adj_particles(AdjArgs<T> A, int chunks_
     };
     const long long nblk_tiles = (long long)nt * chunks_per_tile;
     if (blockIdx.x >= nblk_tiles) {   // the spill list
-        for (long long i = (blockIdx.x - nblk_tiles) * blockDim.x + threadIdx.x; i < A.nsp;
+        const int nsp = min(A.ctr->spill_count[A.parity], A.spill_cap);
+        for (long long i = (blockIdx.x - nblk_tiles) * blockDim.x + threadIdx.x; i < nsp;
              i += (gridDim.x - nblk_tiles) * blockDim.x) {
             const Rec<T> r = A.spill[i];
             adjoint_particle<T, T>(A, gadd, r.cell % g.n[0], (r.cell / g.n[0]) % g.n[1], r.cell / (g.n[0] * g.n[1]),
@@ -393,11 +460,15 @@ __global__ void __launch_bounds__(256) k_adj_particles(AdjArgs<T> A, int chunks_
     }
 }
 
-// dst (working precision, padded) = scale * src (FP64, padded), ghosts included.
+// dst_k (working precision, padded) = scale * src_k (FP64, padded), ghosts included.
 template <typename T>
-__global__ void k_to_working(long long n, const double* src, T* dst, double scale) {
-    for (long long e = blockIdx.x * (long long)blockDim.x + threadIdx.x; e < n; e += (long long)gridDim.x * blockDim.x)
-        dst[e] = (T)(scale * src[e]);
+__global__ void k_to_working3(long long n, const double* s0, const double* s1, const double* s2, T* d0, T* d1, T* d2,
+                              double scale) {
+    for (long long e = blockIdx.x * (long long)blockDim.x + threadIdx.x; e < n; e += (long long)gridDim.x * blockDim.x) {
+        d0[e] = (T)(scale * s0[e]);
+        d1[e] = (T)(scale * s1[e]);
+        d2[e] = (T)(scale * s2[e]);
+    }
 }
 
 // dst (FP64, padded) = scale * src (working precision, padded), ghosts included.
@@ -407,12 +478,16 @@ __global__ void k_scale_copy(long long n, const T* src, double* dst, double scal
         dst[e] = scale * (double)src[e];
 }
 
-// l (padded, FP64) += acc (compact), for the three components, with ghost images.
-__global__ void k_merge(Geom g, double* l0, double* l1, double* l2, const double* a0, const double* a1, const double* a2) {
+
+// lE += accE and lB += accB (acc: the six compact accumulators in one block), ghost
+// images included.
+__global__ void k_merge6(Geom g, double* e0, double* e1, double* e2, double* b0, double* b1, double* b2,
+                         const double* acc) {
     for (long long e = blockIdx.x * (long long)blockDim.x + threadIdx.x; e < g.N; e += (long long)gridDim.x * blockDim.x) {
         const int i = (int)(e % g.n[0]), j = (int)((e / g.n[0]) % g.n[1]), k = (int)(e / ((long long)g.n[0] * g.n[1]));
         const long long p = g.pidx(i, j, k);
-        store3(g, l0, l1, l2, i, j, k, l0[p] + a0[e], l1[p] + a1[e], l2[p] + a2[e]);
+        store3(g, e0, e1, e2, i, j, k, e0[p] + acc[e], e1[p] + acc[g.N + e], e2[p] + acc[2 * g.N + e]);
+        store3(g, b0, b1, b2, i, j, k, b0[p] + acc[3 * g.N + e], b1[p] + acc[4 * g.N + e], b2[p] + acc[5 * g.N + e]);
     }
 }
 
@@ -437,23 +512,46 @@ __global__ void k_dot(Geom g, const double* lE0, const double* lE1, const double
 struct AdjBuffers {
     double* lE[3] = {};
     double* lB[3] = {};
-    double* lEn[3] = {};
-    void* lJ[3] = {};       // -dt lEn in the working precision
-    double* accE[3] = {};
+    void* lJ[3] = {};       // -dt lambda_E^{n+1} in the working precision
+    double* accE[3] = {};   // accE[0..2] and accB[0..2] are one contiguous block
     double* accB[3] = {};
     void* Bn[3] = {};
     std::vector<void*> lX, lU;   // the particles' adjoint state, working precision
 };
 
+// The particle arrays of a snapshot: the live block layout the snapshot copied, rebased
+// onto the snapshot's copy, with its tile counts and holes.
 template <typename T>
-static pic_status adjoint_step_t(pic_ctx* c, AdjBuffers& b) {
+static ParticleArrays<T> snap_view(pic_ctx* c, SpeciesDev& s, const SpeciesSnap& z) {
+    ParticleArrays<T> v = z.cur == s.cur ? arrays<T>(s) : arrays_alt<T>(s);
+    const unsigned char* b0 = static_cast<const unsigned char*>(s.base[z.cur]);
+    unsigned char* nb = static_cast<unsigned char*>(z.part);
+    auto rebase = [&](auto* p) {
+        return reinterpret_cast<decltype(p)>(nb + (reinterpret_cast<const unsigned char*>(p) - b0));
+    };
+    v.cell = rebase(v.cell);
+    for (int k = 0; k < 3; ++k) {
+        v.d[k] = rebase(v.d[k]);
+        v.u[k] = rebase(v.u[k]);
+    }
+    v.w = rebase(v.w);
+    v.id = rebase(v.id);
+    v.count = static_cast<int*>(z.counts);
+    v.holes = static_cast<int*>(z.counts) + ntiles(c);
+    return v;
+}
+
+// One adjoint step at the state held by snapshot Z (read in place: the live state is
+// not touched).
+template <typename T>
+static pic_status adjoint_step_t(pic_ctx* c, AdjBuffers& b, const Snapshot& Z) {
     const double dt = c->desc.dt, h = 0.5 * dt;
-    const size_t pb = sizeof(double) * (size_t)c->g.padded_size();
-    for (int k = 0; k < 3; ++k) GBPIC_CHECK(c, cudaMemcpyAsync(b.lEn[k], b.lE[k], pb, cudaMemcpyDeviceToDevice, c->stream));
-    {   // lambda_J = -dt lambda_E^{n+1}, once per node in the working precision
+    {   // lambda_J = -dt lambda_E^{n+1} (lE before this step's field updates), once per
+        // node in the working precision
         LaunchScope ls(c, KC_OTHER);
-        for (int k = 0; k < 3; ++k)
-            k_to_working<T><<<1024, 256, 0, c->stream>>>(c->g.padded_size(), b.lEn[k], static_cast<T*>(b.lJ[k]), -dt);
+        k_to_working3<T><<<1024, 256, 0, c->stream>>>(c->g.padded_size(), b.lE[0], b.lE[1], b.lE[2],
+                                                      static_cast<T*>(b.lJ[0]), static_cast<T*>(b.lJ[1]),
+                                                      static_cast<T*>(b.lJ[2]), -dt);
         GBPIC_CHECK(c, cudaGetLastError());
     }
     // lB += dt C_E lE  (the Faraday stencil computes B - coef curl E)
@@ -466,27 +564,30 @@ static pic_status adjoint_step_t(pic_ctx* c, AdjBuffers& b) {
     const size_t fb = (size_t)c->g.padded_size() * sizeof(T);
     T* Bn[3];
     T* E[3];
-    for (int k = 0; k < 3; ++k) {
-        Bn[k] = static_cast<T*>(b.Bn[k]);
-        E[k] = static_cast<T*>(c->E[k]);
-        GBPIC_CHECK(c, cudaMemcpyAsync(Bn[k], c->B[k], fb, cudaMemcpyDeviceToDevice, c->stream));
+    {
+        MultiCopy M(c);
+        for (int k = 0; k < 3; ++k) {
+            Bn[k] = static_cast<T*>(b.Bn[k]);
+            E[k] = static_cast<T*>(Z.fields[k]);
+            M.add(Bn[k], Z.fields[3 + k], fb);
+        }
+        st = M.flush();
+        if (st != PIC_OK) return st;
     }
     st = curl_to_b<T>(c, E, Bn, h);
     if (st != PIC_OK) return st;
-    for (int k = 0; k < 3; ++k) {
-        GBPIC_CHECK(c, cudaMemsetAsync(b.accE[k], 0, sizeof(double) * (size_t)c->g.N, c->stream));
-        GBPIC_CHECK(c, cudaMemsetAsync(b.accB[k], 0, sizeof(double) * (size_t)c->g.N, c->stream));
-    }
+    // the six gather^T accumulators are one block
+    GBPIC_CHECK(c, cudaMemsetAsync(b.accE[0], 0, 6 * sizeof(double) * (size_t)c->g.N, c->stream));
     for (size_t si = 0; si < c->species.size(); ++si) {
         SpeciesDev& s = c->species[si];
-        Counters h_ctr;
-        GBPIC_CHECK(c, cudaMemcpyAsync(&h_ctr, s.ctr, sizeof(Counters), cudaMemcpyDeviceToHost, c->stream));
-        GBPIC_CHECK(c, cudaStreamSynchronize(c->stream));
+        const SpeciesSnap& z = Z.sp[si];
         AdjArgs<T> A{};
         A.g = c->g;
-        A.pa = arrays<T>(s);
-        A.spill = static_cast<const Rec<T>*>(s.spill);
-        A.nsp = std::min(h_ctr.spill_count[c->step & 1], s.spill_cap);
+        A.pa = snap_view<T>(c, s, z);
+        A.spill = static_cast<const Rec<T>*>(z.spill);
+        A.ctr = static_cast<const Counters*>(z.ctr);
+        A.parity = (int)(Z.step & 1);
+        A.spill_cap = s.spill_cap;
         for (int k = 0; k < 3; ++k) {
             A.E[k] = E[k];
             A.Bn[k] = Bn[k];
@@ -507,15 +608,18 @@ static pic_status adjoint_step_t(pic_ctx* c, AdjBuffers& b) {
         int maxcap = 0;
         for (int cap : s.h_cap) maxcap = std::max(maxcap, cap);
         const int chunks = std::max(1, (maxcap + ADJ_CHUNK - 1) / ADJ_CHUNK);
-        const long long blocks = (long long)ntiles(c) * chunks + std::max(1, (A.nsp + 255) / 256);
+        // the spill list's blocks (its count stays on the device: no host round trip)
+        int sms = 0;
+        cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, c->desc.device);
+        const int spill_blocks = std::max(1, std::min((s.spill_cap + 255) / 256, 2 * std::max(sms, 1)));
+        const long long blocks = (long long)ntiles(c) * chunks + spill_blocks;
         LaunchScope ls(c, KC_OTHER);
         k_adj_particles<T><<<(unsigned)blocks, 256, 0, c->stream>>>(A, chunks);
         GBPIC_CHECK(c, cudaGetLastError());
     }
     {
         LaunchScope ls(c, KC_OTHER);
-        k_merge<<<1024, 256, 0, c->stream>>>(c->g, b.lE[0], b.lE[1], b.lE[2], b.accE[0], b.accE[1], b.accE[2]);
-        k_merge<<<1024, 256, 0, c->stream>>>(c->g, b.lB[0], b.lB[1], b.lB[2], b.accB[0], b.accB[1], b.accB[2]);
+        k_merge6<<<1024, 256, 0, c->stream>>>(c->g, b.lE[0], b.lE[1], b.lE[2], b.lB[0], b.lB[1], b.lB[2], b.accE[0]);
         GBPIC_CHECK(c, cudaGetLastError());
     }
     // lE -= h C_B lB  (B_n = B^{n-1/2} - h C_E E^n)
@@ -558,15 +662,16 @@ static pic_status backward_t(pic_ctx* c, AdjointState& S, const double* Ed, cons
         if (p) temp.push_back(p);
         return p;
     };
+    double* acc6 = static_cast<double*>(alloc(6 * cb));   // accE[0..2], accB[0..2], contiguous
+    if (!acc6) return PIC_ERR_OOM;
     for (int k = 0; k < 3; ++k) {
         b.lE[k] = static_cast<double*>(alloc(pb));
         b.lB[k] = static_cast<double*>(alloc(pb));
-        b.lEn[k] = static_cast<double*>(alloc(pb));
-        b.accE[k] = static_cast<double*>(alloc(cb));
-        b.accB[k] = static_cast<double*>(alloc(cb));
+        b.accE[k] = acc6 + k * (size_t)c->g.N;
+        b.accB[k] = acc6 + (3 + k) * (size_t)c->g.N;
         b.Bn[k] = alloc(fb);
         b.lJ[k] = alloc(fb);
-        if (!b.lE[k] || !b.lB[k] || !b.lEn[k] || !b.accE[k] || !b.accB[k] || !b.Bn[k] || !b.lJ[k]) return PIC_ERR_OOM;
+        if (!b.lE[k] || !b.lB[k] || !b.Bn[k] || !b.lJ[k]) return PIC_ERR_OOM;
     }
     for (auto& s : c->species) {
         const size_t nb = sizeof(T) * 3 * std::max<int64_t>(s.n_loaded, 1);
@@ -616,9 +721,7 @@ static pic_status backward_t(pic_ctx* c, AdjointState& S, const double* Ed, cons
             }
         }
         for (int n = e - 1; n >= a; --n) {
-            st = snap_restore(c, S.seg[n - a]);
-            if (st != PIC_OK) return st;
-            st = adjoint_step_t<T>(c, b);
+            st = adjoint_step_t<T>(c, b, S.seg[n - a]);
             if (st != PIC_OK) return st;
         }
     }
