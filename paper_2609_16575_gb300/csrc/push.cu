@@ -395,7 +395,7 @@ __device__ __forceinline__ bool tile_prologue(const PushArgs<T>& A, int tile, in
         tma_load_3d(sF + 5 * BS, &tB2, ox, oy, oz, bar);
     }
     // output ranges: exclusive scan of the input histogram
-    hist_scan(hin, s_off, s_hn, s_wsum, s_total);
+    hist_scan<true>(hin, s_off, s_hn, s_wsum, s_total);
     for (int polls = 0;; ++polls) {
         if (polls >= A.wait_polls) {   // (a bound of 0 gives up without waiting)
             *s_timeout = 1;
@@ -657,9 +657,20 @@ k_tile_push(const __grid_constant__ CUtensorMap tE0, const __grid_constant__ CUt
                     ++left;
                 }
             }
-            {   // cell histogram of the output, one shared atomic per warp and cell
-                const unsigned grp = __match_any_sync(0xffffffffu, nlc >= 0 ? nlc : -1 - lane);
-                if (nlc >= 0 && lane == __ffs(grp) - 1) atomicAdd(&s_hn[nlc], __popc(grp));
+            // cell histogram of the output: it starts as the input histogram (every
+            // particle counted in its start cell); a particle that changes cell or leaves
+            // the tile moves its count.  In a cycle that ends with a window move every
+            // stored cell changes: the counts then move once per warp and cell.
+            if (A.xshift == 0) {
+                if (active && nlc != lc) {
+                    atomicSub(&s_hn[lc], 1);
+                    if (nlc >= 0) atomicAdd(&s_hn[nlc], 1);
+                }
+            } else {
+                const unsigned g1 = __match_any_sync(0xffffffffu, active ? lc : -1 - lane);
+                if (active && lane == __ffs(g1) - 1) atomicSub(&s_hn[lc], __popc(g1));
+                const unsigned g2 = __match_any_sync(0xffffffffu, nlc >= 0 ? nlc : -1 - lane);
+                if (nlc >= 0 && lane == __ffs(g2) - 1) atomicAdd(&s_hn[nlc], __popc(g2));
             }
             // a crosser's second segment, in the cell it moved to (relay split)
             if (!ESK && __any_sync(0xffffffffu, crossed)) {

@@ -64,8 +64,10 @@ __device__ __forceinline__ void movers_flush(const PushArgs<T>& A, const Rec<T>*
 
 // Output ranges of a tile step: exclusive scan of the input cell histogram hin (two
 // cells per thread of the first 256 threads) into s_off, the output histogram s_hn
-// cleared, the total into *s_total.  The caller synchronises the block before using
-// them.
+// cleared (or, with hn_from_input, set to the input histogram, for a step that then
+// applies only the particles that change cell), the total into *s_total.  The caller
+// synchronises the block before using them.
+template <bool hn_from_input = false>
 __device__ __forceinline__ void hist_scan(const int* hin, int* s_off, int* s_hn, int* s_wsum, int* s_total) {
     const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
     const bool sc = threadIdx.x < 256;
@@ -84,8 +86,8 @@ __device__ __forceinline__ void hist_scan(const int* hin, int* s_off, int* s_hn,
         const int excl = woff + incl - (a0 + a1);
         s_off[2 * threadIdx.x] = excl;
         s_off[2 * threadIdx.x + 1] = excl + a0;
-        s_hn[2 * threadIdx.x] = 0;
-        s_hn[2 * threadIdx.x + 1] = 0;
+        s_hn[2 * threadIdx.x] = hn_from_input ? a0 : 0;
+        s_hn[2 * threadIdx.x + 1] = hn_from_input ? a1 : 0;
         if (threadIdx.x == 255) *s_total = woff + incl;
     }
 }
