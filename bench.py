@@ -758,10 +758,13 @@ def run_gbpic(args):
         t0 = time.perf_counter()
         ctx = gbpic.Context(n, d, dt, precision=gbpic.PIC_FP32, rho_ion=1.0, device=dev)
         variant(ctx)
-        ctx.load_species(-1.0, 1.0, Xh, Uh, wh, True)
+        t1 = time.perf_counter()
+        ctx.load_species(-1.0, 1.0, Xh, Uh, wh, True)   # returns once the sort is done
+        t2 = time.perf_counter()
         ctx.step(args.steps)
         d_e2e = ctx.diagnostics()
         t_e2e = time.perf_counter() - t0
+        phases = {"context_s": t1 - t0, "load_s": t2 - t1, "steps_and_diagnostics_s": t_e2e - (t2 - t0)}
         ctx.close()
         del ctx
         if dist is not None:
@@ -778,7 +781,7 @@ def run_gbpic(args):
                "seconds": t_e2e,
                "includes": "context creation, H2D of the FP64 particle arrays from pinned host memory, tile sort, "
                            f"{args.steps} steps, FP64 diagnostics and their D2H (bytes per step = per run / steps)",
-               "check_n_alive": d_e2e["n_alive"] == npart}
+               "check_n_alive": d_e2e["n_alive"] == npart, "phases": phases}
         del host, Xh, Uh, wh
     else:
         del X, U, w

@@ -609,6 +609,7 @@ struct SpeciesDev {
     int* cap = nullptr;
     int* holes = nullptr;
     int* hist[2] = {nullptr, nullptr};    // per tile and block: particles per cell (TILE_CELLS ints)
+    int* split_buf = nullptr;             // split tiles: output ranges (TILE_CELLS per tile), input counts
     void* movers = nullptr;
     int mover_cap = 0;
     void* spill = nullptr;

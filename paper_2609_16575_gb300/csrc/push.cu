@@ -365,7 +365,7 @@ __device__ __forceinline__ void esk_stack(WarpQueue<T> Q, int& qn, int& me, int 
 // ERRB_TIMEOUT, waits (bounded again, MBAR_MAX_POLLS) for the copies in flight, drops its
 // particles (count, holes and the output histogram set to zero, so later steps read
 // nothing stale) and returns false.
-template <typename T, int NT>
+template <typename T, int NT, bool SCAN = true>
 __device__ __forceinline__ bool tile_prologue(const PushArgs<T>& A, int tile, int cnt, int ox, int oy, int oz,
                                               const int* hin, int* hout, const CUtensorMap& tE0,
                                               const CUtensorMap& tE1, const CUtensorMap& tE2,
@@ -376,7 +376,6 @@ __device__ __forceinline__ bool tile_prologue(const PushArgs<T>& A, int tile, in
     constexpr int BX = Prec<T>::BX;
     constexpr int BS = box_stride<T>();
     static_assert(NT >= 256 && NT % 32 == 0, "the histogram scan uses the first 256 threads");
-    const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
     if (threadIdx.x == 0) {
         *s_timeout = 0;
         *s_left = 0;
@@ -394,8 +393,9 @@ __device__ __forceinline__ bool tile_prologue(const PushArgs<T>& A, int tile, in
         tma_load_3d(sF + 4 * BS, &tB1, ox, oy, oz, bar);
         tma_load_3d(sF + 5 * BS, &tB2, ox, oy, oz, bar);
     }
-    // output ranges: exclusive scan of the input histogram
-    hist_scan<true>(hin, s_off, s_hn, s_wsum, s_total);
+    // output ranges: exclusive scan of the input histogram (a split tile's ranges come
+    // from k_split_prep)
+    if (SCAN) hist_scan<true>(hin, s_off, s_hn, s_wsum, s_total);
     for (int polls = 0;; ++polls) {
         if (polls >= A.wait_polls) {   // (a bound of 0 gives up without waiting)
             *s_timeout = 1;
@@ -477,7 +477,7 @@ __device__ __forceinline__ void tile_flush_index(const PushArgs<T>& A, int ox, i
 // R particles nearly always start in one cell: their straight-segment currents are
 // summed in registers and each row ends with one warp flush of those sums; everything
 // else goes through the warp's record queue.
-template <typename T, bool IDS, bool RECK, bool ESK>
+template <typename T, bool IDS, bool RECK, bool ESK, bool SPLIT>
 __global__ void __launch_bounds__(Prec<T>::THREADS, Prec<T>::MINB)
 k_tile_push(const __grid_constant__ CUtensorMap tE0, const __grid_constant__ CUtensorMap tE1,
             const __grid_constant__ CUtensorMap tE2, const __grid_constant__ CUtensorMap tB0,
@@ -500,22 +500,30 @@ k_tile_push(const __grid_constant__ CUtensorMap tE0, const __grid_constant__ CUt
     __shared__ int s_wsum[8];
     __shared__ int s_timeout, s_total, s_left;
 
-    const int tile = blockIdx.x;
-    const int cnt = min(A.pa.count[tile], A.pa.cap[tile]);
+    // a split tile is handled by A.parts CTAs, part p taking every A.parts-th row of
+    // each warp's rows; its output ranges and histogram then live in global memory
+    const int tile = SPLIT ? blockIdx.x / A.parts : blockIdx.x;
+    const int part = SPLIT ? blockIdx.x - tile * A.parts : 0;
+    const int nparts = SPLIT ? A.parts : 1;
+    const int cnt = min(SPLIT ? A.cnt_in[tile] : A.pa.count[tile], A.pa.cap[tile]);
     const int* hin = A.hin + (size_t)tile * TILE_CELLS;
     int* hout = A.hout + (size_t)tile * TILE_CELLS;
+    int* const offp = SPLIT ? A.goff + (size_t)tile * TILE_CELLS : s_off;   // next free output slot per cell
+    int* const hnp = SPLIT ? hout : s_hn;                                 // output histogram
     const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
     if (cnt == 0) {
-        for (int i = threadIdx.x; i < TILE_CELLS; i += NT) hout[i] = 0;
-        if (threadIdx.x == 0) A.pa.holes[tile] = 0;
+        if (!SPLIT) {
+            for (int i = threadIdx.x; i < TILE_CELLS; i += NT) hout[i] = 0;
+            if (threadIdx.x == 0) A.pa.holes[tile] = 0;
+        }
         return;
     }
     const int ntx = A.g.nt[0], nty = A.g.nt[1];
     const int tx = tile % ntx, ty = (tile / ntx) % nty, tz = tile / (ntx * nty);
     const int ox = tx * TILE, oy = ty * TILE, oz = tz * TILE;
 
-    if (!tile_prologue<T, NT>(A, tile, cnt, ox, oy, oz, hin, hout, tE0, tE1, tE2, tB0, tB1, tB2, sF, sP, sJ, bar, s_off,
-                              s_hn, s_wsum, &s_timeout, &s_total, &s_left))
+    if (!tile_prologue<T, NT, !SPLIT>(A, tile, cnt, ox, oy, oz, hin, hout, tE0, tE1, tE2, tB0, tB1, tB2, sF, sP, sJ,
+                                       bar, s_off, s_hn, s_wsum, &s_timeout, &s_total, &s_left))
         return;
 
     const int ext[3] = {min(TILE, A.g.n[0] - ox), min(TILE, A.g.n[1] - oy), min(TILE, A.g.n[2] - oz)};
@@ -547,7 +555,8 @@ k_tile_push(const __grid_constant__ CUtensorMap tE0, const __grid_constant__ CUt
         }
         n_w = __ldcg(A.pa.w + q);
     };
-    prefetch((warp * 32 + lane) * R);
+    const int row0 = warp + NW * part, rstep = NW * nparts;   // this warp's rows
+    prefetch((row0 * 32 + lane) * R);
     int n_cells[R];               // the cells of the next row's R slots
     auto prefetch_cells = [&](int i0) {
         if (i0 < cnt) RowCells<R>::ld(A.pa.cell + seg + i0, n_cells);
@@ -555,9 +564,9 @@ k_tile_push(const __grid_constant__ CUtensorMap tE0, const __grid_constant__ CUt
         for (int r = 0; r < R; ++r)
             if (i0 + r >= cnt) n_cells[r] = HOLE;
     };
-    prefetch_cells((warp * 32 + lane) * R);
+    prefetch_cells((row0 * 32 + lane) * R);
 
-    for (int row = warp; row * 32 < ngroups; row += NW) {
+    for (int row = row0; row * 32 < ngroups; row += rstep) {
         P2 acc[6];                // summed straight-segment currents of start cell `key`
         int key = RowCells<R>::key(n_cells);
         // output slots: the lanes whose R particles start in one cell claim R slots each
@@ -571,7 +580,7 @@ k_tile_push(const __grid_constant__ CUtensorMap tE0, const __grid_constant__ CUt
             const unsigned grp = __match_any_sync(0xffffffffu, uni ? n_cells[0] : -1 - lane);
             const int leader = __ffs(grp) - 1;
             int b = 0;
-            if (uni && lane == leader) b = atomicAdd(&s_off[n_cells[0]], R * __popc(grp));
+            if (uni && lane == leader) b = atomicAdd(&offp[n_cells[0]], R * __popc(grp));
             b = __shfl_sync(0xffffffffu, b, leader);
             // particle r of the group's k-th lane takes slot b + r G + k (G lanes): at each
             // particle step the group writes G consecutive slots
@@ -581,7 +590,7 @@ k_tile_push(const __grid_constant__ CUtensorMap tE0, const __grid_constant__ CUt
 #pragma unroll
         for (int q = 0; q < 6; ++q) acc[q] = Pair<T>::splat(T(0));
         const int s0 = (row * 32 + lane) * R;   // first slot of this lane
-        prefetch_cells(((row + NW) * 32 + lane) * R);
+        prefetch_cells(((row + rstep) * 32 + lane) * R);
 #pragma unroll 1
         for (int r = 0; r < R; ++r) {
             const int i = s0 + r;
@@ -590,7 +599,7 @@ k_tile_push(const __grid_constant__ CUtensorMap tE0, const __grid_constant__ CUt
             const bool active = lc >= 0;
             T u[3] = {n_u[0], n_u[1], n_u[2]}, d2[3] = {T(0), T(0), T(0)}, w = n_w;
             const T d1[3] = {n_d[0], n_d[1], n_d[2]};
-            prefetch(r + 1 < R ? i + 1 : ((row + NW) * 32 + lane) * R);
+            prefetch(r + 1 < R ? i + 1 : ((row + rstep) * 32 + lane) * R);
             P2 v[6], v2[6];
             T cw[3] = {T(0), T(0), T(0)};
             int s[3] = {0, 0, 0};
@@ -643,7 +652,7 @@ k_tile_push(const __grid_constant__ CUtensorMap tE0, const __grid_constant__ CUt
                 if (stay) nlc = nx | (ny << 3) | (nz << 6);
                 // the particle's slot in its start cell's output range: the state after
                 // the step, or a hole
-                const int o = seg + (obase >= 0 ? obase + r * ostride : atomicAdd(&s_off[lc], 1));
+                const int o = seg + (obase >= 0 ? obase + r * ostride : atomicAdd(&offp[lc], 1));
                 __stcs(A.pb.cell + o, stay ? nlc : HOLE);
                 if (stay) {
 #pragma unroll
@@ -663,14 +672,14 @@ k_tile_push(const __grid_constant__ CUtensorMap tE0, const __grid_constant__ CUt
             // stored cell changes: the counts then move once per warp and cell.
             if (A.xshift == 0) {
                 if (active && nlc != lc) {
-                    atomicSub(&s_hn[lc], 1);
-                    if (nlc >= 0) atomicAdd(&s_hn[nlc], 1);
+                    atomicSub(&hnp[lc], 1);
+                    if (nlc >= 0) atomicAdd(&hnp[nlc], 1);
                 }
             } else {
                 const unsigned g1 = __match_any_sync(0xffffffffu, active ? lc : -1 - lane);
-                if (active && lane == __ffs(g1) - 1) atomicSub(&s_hn[lc], __popc(g1));
+                if (active && lane == __ffs(g1) - 1) atomicSub(&hnp[lc], __popc(g1));
                 const unsigned g2 = __match_any_sync(0xffffffffu, nlc >= 0 ? nlc : -1 - lane);
-                if (nlc >= 0 && lane == __ffs(g2) - 1) atomicAdd(&s_hn[nlc], __popc(g2));
+                if (nlc >= 0 && lane == __ffs(g2) - 1) atomicAdd(&hnp[nlc], __popc(g2));
             }
             // a crosser's second segment, in the cell it moved to (relay split)
             if (!ESK && __any_sync(0xffffffffu, crossed)) {
@@ -732,21 +741,46 @@ k_tile_push(const __grid_constant__ CUtensorMap tE0, const __grid_constant__ CUt
     if (mq) movers_flush(A, sM, mq, lane);
     left = __reduce_add_sync(0xffffffffu, left);
     esc = __reduce_add_sync(0xffffffffu, esc);
-    if (lane == 0 && left) atomicAdd(&s_left, left);
+    if (lane == 0 && left) atomicAdd(SPLIT ? &A.pa.holes[tile] : &s_left, left);
     if (lane == 0 && esc) atomicAdd(&A.ctr->escaped, esc);
     __shared__ int s_gidx[3 * SJ];
     tile_flush_index(A, ox, oy, oz, s_gidx);
     __syncthreads();
     // the output segment: the input cells' ranges (with the holes of the departed) and,
-    // appended later, this step's arrivals
-    for (int i = threadIdx.x; i < TILE_CELLS; i += NT) hout[i] = s_hn[i];
-    if (threadIdx.x == 0) {
-        A.pa.count[tile] = s_total;
-        A.pa.holes[tile] = s_left;
+    // appended later, this step's arrivals (a split tile's count, holes and histogram are
+    // set by k_split_prep and updated in global memory)
+    if (!SPLIT) {
+        for (int i = threadIdx.x; i < TILE_CELLS; i += NT) hout[i] = s_hn[i];
+        if (threadIdx.x == 0) {
+            A.pa.count[tile] = s_total;
+            A.pa.holes[tile] = s_left;
+        }
     }
     // flush the shared J tile to HBM (periodic wrap of the guard layers)
     tile_flush_j<T, NT>(A, sJ, s_gidx);
     if (RECK) block_add_double(kacc, A.krec);
+}
+
+// Before a step whose tiles are split over several CTAs: per tile, the output cell
+// ranges (exclusive scan of the input histogram) into goff, the output histogram set to
+// the input one (the CTAs then move the counts of the particles that change cell), the
+// input count kept in cnt_in, the new count (the ranges' total) and zero holes.
+template <typename T>
+__global__ void __launch_bounds__(256) k_split_prep(PushArgs<T> A) {
+    __shared__ int s_off[TILE_CELLS], s_hn[TILE_CELLS], s_wsum[8], s_total;
+    const int tile = blockIdx.x;
+    const int* hin = A.hin + (size_t)tile * TILE_CELLS;
+    hist_scan<true>(hin, s_off, s_hn, s_wsum, &s_total);
+    __syncthreads();
+    for (int i = threadIdx.x; i < TILE_CELLS; i += blockDim.x) {
+        A.goff[(size_t)tile * TILE_CELLS + i] = s_off[i];
+        A.hout[(size_t)tile * TILE_CELLS + i] = s_hn[i];
+    }
+    if (threadIdx.x == 0) {
+        const_cast<int*>(A.cnt_in)[tile] = A.pa.count[tile];
+        A.pa.count[tile] = s_total;
+        A.pa.holes[tile] = 0;
+    }
 }
 
 // Spill-list particles: same arithmetic with global-memory gather and deposit.
@@ -964,9 +998,9 @@ static int sm_count(pic_ctx* c) {
     return v > 0 ? v : 152;
 }
 
-template <typename T, bool IDS, bool RECK, bool ESK>
+template <typename T, bool IDS, bool RECK, bool ESK, bool SPLIT = false>
 static pic_status launch_tile(pic_ctx* c, PushArgs<T>& A) {
-    auto kern = k_tile_push<T, IDS, RECK, ESK>;
+    auto kern = k_tile_push<T, IDS, RECK, ESK, SPLIT>;
     const size_t smem = tile_smem_bytes<T>();
     static bool attr_set = false;
     if (!attr_set) {
@@ -975,8 +1009,12 @@ static pic_status launch_tile(pic_ctx* c, PushArgs<T>& A) {
     }
     const int ntile = c->g.nt[0] * c->g.nt[1] * c->g.nt[2];
     LaunchScope ls(c, KC_TILE_PUSH);
-    kern<<<ntile, Prec<T>::THREADS, smem, c->stream>>>(c->tmap[0], c->tmap[1], c->tmap[2], c->tmap[3], c->tmap[4],
-                                                     c->tmap[5], A);
+    if (SPLIT) {
+        k_split_prep<T><<<ntile, 256, 0, c->stream>>>(A);
+        GBPIC_CHECK(c, cudaGetLastError());
+    }
+    kern<<<ntile * (SPLIT ? A.parts : 1), Prec<T>::THREADS, smem, c->stream>>>(c->tmap[0], c->tmap[1], c->tmap[2],
+                                                                            c->tmap[3], c->tmap[4], c->tmap[5], A);
     GBPIC_CHECK(c, cudaGetLastError());
     return PIC_OK;
 }
@@ -1039,11 +1077,34 @@ static pic_status push_species_t(pic_ctx* c, SpeciesDev& s, int parity, double* 
     pic_status st;
     const bool esk = c->deposit == PIC_DEPOSIT_ESIRKEPOV;
     const bool tsc = c->shape == PIC_SHAPE_TSC;
+    {   // a grid of fewer tiles than SMs splits each tile's rows over several CTAs (the
+        // ZigZag kernel), up to two CTAs per SM and at least one row of slots per CTA
+        const int ntile = c->g.nt[0] * c->g.nt[1] * c->g.nt[2];
+        const int sms = sm_count(c);
+        A.parts = 1;
+        if (!esk && !tsc && ntile < sms) {
+            int maxcap = 0;
+            for (int cap : s.h_cap) maxcap = std::max(maxcap, cap);
+            const int rows = (maxcap + 32 * Prec<T>::R - 1) / (32 * Prec<T>::R);
+            A.parts = std::max(1, std::min((2 * sms + ntile - 1) / ntile, rows));
+        }
+        if (A.parts > 1) {
+            if (!s.split_buf) {
+                s.split_buf = static_cast<int*>(dev_alloc(c, sizeof(int) * (size_t)ntile * (TILE_CELLS + 1)));
+                if (!s.split_buf) return PIC_ERR_OOM;
+            }
+            A.goff = s.split_buf;
+            A.cnt_in = s.split_buf + (size_t)ntile * TILE_CELLS;
+        }
+    }
     if (tsc) {
         st = launch_tsc_push<T>(c, A, ids, rec);   // its tile step and spill-list step
     } else if (esk) {
         if (ids) st = rec ? launch_tile<T, true, true, true>(c, A) : launch_tile<T, true, false, true>(c, A);
         else st = rec ? launch_tile<T, false, true, true>(c, A) : launch_tile<T, false, false, true>(c, A);
+    } else if (A.parts > 1) {   // fewer tiles than SMs: several CTAs per tile
+        if (ids) st = rec ? launch_tile<T, true, true, false, true>(c, A) : launch_tile<T, true, false, false, true>(c, A);
+        else st = rec ? launch_tile<T, false, true, false, true>(c, A) : launch_tile<T, false, false, false, true>(c, A);
     } else {
         if (ids) st = rec ? launch_tile<T, true, true, false>(c, A) : launch_tile<T, true, false, false>(c, A);
         else st = rec ? launch_tile<T, false, true, false>(c, A) : launch_tile<T, false, false, false>(c, A);

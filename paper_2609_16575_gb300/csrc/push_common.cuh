@@ -29,6 +29,12 @@ template <typename T> struct PushArgs {
     double mass;
     int xshift;     // 1: the window moves after this cycle (stored x cells drop by one)
     int wait_polls; // polls of the TMA staging wait before it gives up (ERRB_TIMEOUT); 0: at once
+    // a tile split over several CTAs (grids with fewer tiles than SMs): `parts` CTAs per
+    // tile, the tiles' output cell ranges (next free slot, TILE_CELLS per tile) and input
+    // counts prepared by k_split_prep
+    int parts;
+    int* goff;
+    const int* cnt_in;
 };
 
 // Sum of one double per thread of the block, added to *dst by thread 0.
