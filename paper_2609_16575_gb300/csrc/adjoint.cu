@@ -212,13 +212,21 @@ template <typename T> struct AdjArgs {
 template <typename T, typename C>
 __device__ __forceinline__ C interp_grad(const Geom& g, const T* F, const int b[3], const C s[3], C grad[3]) {
     C f[2][2][2];
+    // the eight samples from the base's padded index (local -1 .. n: no wrap needed)
+    const long long base = g.pidx(b[0], b[1], b[2]), sy = g.Px, sz = (long long)g.Px * g.Gy;
+    #pragma unroll
     for (int cc = 0; cc < 2; ++cc)
+        #pragma unroll
         for (int bb = 0; bb < 2; ++bb)
-            for (int aa = 0; aa < 2; ++aa) f[cc][bb][aa] = (C)F[g.pidx(b[0] + aa, b[1] + bb, b[2] + cc)];
+            #pragma unroll
+            for (int aa = 0; aa < 2; ++aa) f[cc][bb][aa] = (C)F[base + aa + bb * sy + cc * sz];
     const C w0[2] = {C(1) - s[0], s[0]}, w1[2] = {C(1) - s[1], s[1]}, w2[2] = {C(1) - s[2], s[2]};
     C v = 0, g0 = 0, g1 = 0, g2 = 0;
+    #pragma unroll
     for (int cc = 0; cc < 2; ++cc)
+        #pragma unroll
         for (int bb = 0; bb < 2; ++bb)
+            #pragma unroll
             for (int aa = 0; aa < 2; ++aa) {
                 const C x = f[cc][bb][aa];
                 v += w0[aa] * w1[bb] * w2[cc] * x;
@@ -239,8 +247,11 @@ template <typename C, typename AddFn>
 __device__ __forceinline__ void scatter_trilinear(AddFn Add, int comp, const int b[3], const C s[3], C lam) {
     if (lam == C(0)) return;
     const C w0[2] = {C(1) - s[0], s[0]}, w1[2] = {C(1) - s[1], s[1]}, w2[2] = {C(1) - s[2], s[2]};
+    #pragma unroll
     for (int cc = 0; cc < 2; ++cc)
+        #pragma unroll
         for (int bb = 0; bb < 2; ++bb)
+            #pragma unroll
             for (int aa = 0; aa < 2; ++aa) Add(comp, b[0] + aa, b[1] + bb, b[2] + cc, lam * w0[aa] * w1[bb] * w2[cc]);
 }
 
@@ -286,6 +297,7 @@ __device__ void adjoint_particle(const AdjArgs<T>& A, AddFn Add, int gx, int gy,
     // ---- forward recompute: staggered gather with weights and their gradients
     int hb[3], nb[3];
     C hs[3], ns[3];
+    #pragma unroll
     for (int k = 0; k < 3; ++k) {
         if (d1[k] >= C(0.5)) {
             hb[k] = gc[k];
@@ -301,7 +313,9 @@ __device__ void adjoint_particle(const AdjArgs<T>& A, AddFn Add, int gx, int gy,
     C val[6], grad[6][3];
     int cb[6][3];
     C cs[6][3];
+    #pragma unroll
     for (int comp = 0; comp < 6; ++comp) {
+        #pragma unroll
         for (int k = 0; k < 3; ++k) {
             cb[comp][k] = HF[comp][k] ? hb[k] : nb[k];
             cs[comp][k] = HF[comp][k] ? hs[k] : ns[k];
@@ -313,41 +327,57 @@ __device__ void adjoint_particle(const AdjArgs<T>& A, AddFn Add, int gx, int gy,
     // Boris with its intermediates (section 2.4)
     const C eps = (C)A.eps;
     C um[3], t[3], s[3], up[3], upl[3], un[3], tmp[3];
+    #pragma unroll
     for (int k = 0; k < 3; ++k) um[k] = u0[k] + eps * Ep[k];
     const C gm = sqrt(C(1) + um[0] * um[0] + um[1] * um[1] + um[2] * um[2]);
+    #pragma unroll
     for (int k = 0; k < 3; ++k) t[k] = eps * Bp[k] / gm;
     const C t2 = t[0] * t[0] + t[1] * t[1] + t[2] * t[2];
     const C f = C(2) / (C(1) + t2);
+    #pragma unroll
     for (int k = 0; k < 3; ++k) s[k] = f * t[k];
     cross3(um, t, tmp);
+    #pragma unroll
     for (int k = 0; k < 3; ++k) up[k] = um[k] + tmp[k];
     cross3(up, s, tmp);
+    #pragma unroll
     for (int k = 0; k < 3; ++k) upl[k] = um[k] + tmp[k];
+    #pragma unroll
     for (int k = 0; k < 3; ++k) un[k] = upl[k] + eps * Ep[k];
     const C gn = sqrt(C(1) + un[0] * un[0] + un[1] * un[1] + un[2] * un[2]);
     const C ig = C(1) / gn;
     // move and zigzag relay (cell-relative, as the forward kernels)
     C d2[3], F1[3], F2[3], W1[3], W2[3];
     int st[3];
+    #pragma unroll
     for (int k = 0; k < 3; ++k) {
         st[k] = advance(d1[k], (C)A.dtd[k] * un[k] * ig, d2[k]);
         st[k] = st[k] > 1 ? 1 : (st[k] < -1 ? -1 : st[k]);
         relay(d1[k], d2[k], st[k], F1[k], F2[k], W1[k], W2[k]);
     }
     // ---- deposit^T: lambda_J = -dt lambda_E^{n+1} at the edges of both segment cells
+    // the edges of the start cell and of the (wrapped) end cell: padded indices from each
+    // cell's origin (edges up to local n, inside the padded range with its valid ghosts)
     C L1[12], L2[12];
-    for (int q = 0; q < 12; ++q) {
-        int comp, ex, ey, ez;
-        slot_edge(q, gx, gy, gz, comp, ex, ey, ez);
-        L1[q] = (C)A.lJ[comp][g.pidx(wrap2(ex, g.n[0]), wrap2(ey, g.n[1]), wrap2(ez, g.n[2]))];
-        slot_edge(q, gx + st[0], gy + st[1], gz + st[2], comp, ex, ey, ez);
-        L2[q] = (C)A.lJ[comp][g.pidx(wrap2(ex, g.n[0]), wrap2(ey, g.n[1]), wrap2(ez, g.n[2]))];
+    {
+        const long long sy = g.Px, sz = (long long)g.Px * g.Gy;
+        const long long o1 = g.pidx(gx, gy, gz);
+        const long long o2 = g.pidx(wrap1(gx + st[0], g.n[0]), wrap1(gy + st[1], g.n[1]), wrap1(gz + st[2], g.n[2]));
+#pragma unroll
+        for (int q = 0; q < 12; ++q) {
+            int comp, ex, ey, ez;
+            slot_edge(q, 0, 0, 0, comp, ex, ey, ez);
+            const long long off = ex + ey * sy + ez * sz;
+            L1[q] = (C)A.lJ[comp][o1 + off];
+            L2[q] = (C)A.lJ[comp][o2 + off];
+        }
     }
     const C Cw[3] = {(C)A.C[0] * w, (C)A.C[1] * w, (C)A.C[2] * w};
     C gF1[3], gW1[3], gF2[3], gW2[3];
     segment_vjp(Cw, F1, W1, L1, gF1, gW1);
     segment_vjp(Cw, F2, W2, L2, gF2, gW2);
     C lx1c[3], lx2c[3];
+    #pragma unroll
     for (int k = 0; k < 3; ++k) {
         if (st[k] == 0) {   // F1 = F2 = (x2 - x1)/2, W1 = (3 x1 + x2)/4, W2 = (x1 + 3 x2)/4
             lx1c[k] = C(-0.5) * (gF1[k] + gF2[k]) + C(0.75) * gW1[k] + C(0.25) * gW2[k];
@@ -360,37 +390,49 @@ __device__ void adjoint_particle(const AdjArgs<T>& A, AddFn Add, int gx, int gy,
     // ---- the adjoint of the next state (FP64), and the position update
     // X^{n+1} = X^n + dtd u / gamma
     C lx1[3], lun[3], a[3];
+    #pragma unroll
     for (int k = 0; k < 3; ++k) {
         const C lx2 = lx2c[k] + (C)A.lX[k * A.nload + id];
         lx1[k] = lx1c[k] + lx2;
         a[k] = lx2 * (C)A.dtd[k];
     }
     const C adot = a[0] * un[0] + a[1] * un[1] + a[2] * un[2];
+    #pragma unroll
     for (int k = 0; k < 3; ++k) lun[k] = (C)A.lU[k * A.nload + id] + (a[k] - un[k] * adot * ig * ig) * ig;
     // ---- Boris^T
     C lum[3], lup[3], ls[3], lt[3], lE[3], lB[3];
+    #pragma unroll
     for (int k = 0; k < 3; ++k) lum[k] = lun[k];           // upl = um + up x s, lambda_upl = lun
     cross3(s, lun, lup);                                     // lambda_up = s x lambda_upl
     cross3(lun, up, ls);                                     // lambda_s = lambda_upl x up
     cross3(t, lup, tmp);                                     // up = um + um x t
+    #pragma unroll
     for (int k = 0; k < 3; ++k) lum[k] += lup[k] + tmp[k];
     cross3(lup, um, lt);
     const C lst = ls[0] * t[0] + ls[1] * t[1] + ls[2] * t[2];   // s = f t, f = 2 / (1 + t.t)
+    #pragma unroll
     for (int k = 0; k < 3; ++k) lt[k] += f * ls[k] - f * f * lst * t[k];
+    #pragma unroll
     for (int k = 0; k < 3; ++k) lB[k] = eps / gm * lt[k];    // t = eps B / gm
     const C lgm = -(lt[0] * t[0] + lt[1] * t[1] + lt[2] * t[2]) / gm;
+    #pragma unroll
     for (int k = 0; k < 3; ++k) lum[k] += lgm * um[k] / gm;   // gm = sqrt(1 + um.um)
+    #pragma unroll
     for (int k = 0; k < 3; ++k) lE[k] = eps * (lun[k] + lum[k]);   // um = u + eps E and the final kick
     // ---- gather^T
+    #pragma unroll
     for (int k = 0; k < 3; ++k) {
         C acc = 0;
+        #pragma unroll
         for (int c = 0; c < 3; ++c) acc += lE[c] * grad[c][k] + lB[c] * grad[3 + c][k];
         lx1[k] += acc;
     }
+    #pragma unroll
     for (int c = 0; c < 3; ++c) {
         scatter_trilinear(Add, c, cb[c], cs[c], lE[c]);
         scatter_trilinear(Add, 3 + c, cb[3 + c], cs[3 + c], lB[c]);
     }
+    #pragma unroll
     for (int k = 0; k < 3; ++k) {
         A.lX[k * A.nload + id] = (T)lx1[k];
         A.lU[k * A.nload + id] = (T)lum[k];
