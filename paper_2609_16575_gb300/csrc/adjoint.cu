@@ -15,7 +15,7 @@
 //     weights), position update^T, Boris^T, gather^T (scatter into lE, lB and the
 //     derivative of the interpolation weights)
 //   lE  <- lE - h C_B lB              (from B_n = B^{n-1/2} - h C_E E^n)
-// The driver keeps a full-state snapshot every K steps, recomputes each segment
+// The host loop keeps a full-state snapshot every K steps, recomputes each segment
 // forward, and runs the adjoint steps in reverse; all adjoint arithmetic and the
 // parameter-gradient reductions are FP64.
 #include <algorithm>
@@ -549,7 +549,7 @@ __global__ void k_dot(Geom g, const double* lE0, const double* lE1, const double
 }
 
 // ---------------------------------------------------------------------------
-// Driver.
+// The backward host loop.
 
 struct AdjBuffers {
     double* lE[3] = {};

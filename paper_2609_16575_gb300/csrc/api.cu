@@ -91,7 +91,7 @@ pic_status make_tensor_maps(pic_ctx* c) {
     cudaDriverEntryPointQueryResult q;
     GBPIC_CHECK(c, cudaGetDriverEntryPointByVersion("cuTensorMapEncodeTiled", &fn, 12000, cudaEnableDefault, &q));
     if (q != cudaDriverEntryPointSuccess || !fn) {
-        c->err = "cuTensorMapEncodeTiled not available from the driver";
+        c->err = "cuTensorMapEncodeTiled not available from the CUDA driver library";
         return PIC_ERR_CUDA;
     }
     auto encode = reinterpret_cast<PFN_cuTensorMapEncodeTiled_v12000>(fn);
