@@ -16,6 +16,8 @@
 //                     -2..10, flushed to HBM with integer (FP32) or FP64 atomics.
 //   k_tsc_list_push   the spill list's particles with global-memory gather and deposit.
 // The shape supports periodic boundaries (the host rejects an open x).
+#include <type_traits>
+
 #include "push_common.cuh"
 
 namespace gbpic {
@@ -191,18 +193,17 @@ __device__ __forceinline__ int tsc_j_index(int comp, int x, int y, int z) {
 // element here can receive more terms than the 4096 that keep the lo word below 2^32,
 // so the lo add returns the old word and a wrap carries 2^32 (2^12 units of 2^20) into
 // the hi word: the sum stays exact for any number of terms.
-__device__ __forceinline__ void tsc_tile_add(uint32_t base, int e, float v) {
+__device__ __forceinline__ void tsc_tile_add(unsigned* words, int e, float v) {
     const float hf = floorf(v * 9.5367431640625e-07f);   // v / 2^20
     const int hi = __float2int_rz(hf);
     const unsigned lo = (unsigned)__float2int_rn(__fmaf_rn(hf, -1048576.0f, v));
-    unsigned old;
-    asm volatile("atom.shared.add.u32 %0, [%1], %2;" : "=r"(old) : "r"(base + 4u * e), "r"(lo) : "memory");
+    // (the atomics are left to the compiler, without a memory clobber, so that the
+    // independent adds of one particle overlap instead of waiting one by one)
+    const unsigned old = atomicAdd(words + e, lo);
     const unsigned carry = (old + lo < old) ? 4096u : 0u;
-    asm volatile("red.shared.add.u32 [%0], %1;" ::"r"(base + 4u * (TSJ_ELEMS + e)), "r"((unsigned)hi + carry) : "memory");
+    atomicAdd(words + TSJ_ELEMS + e, (unsigned)hi + carry);
 }
-__device__ __forceinline__ void tsc_tile_add(uint32_t base, int e, double v) {
-    asm volatile("red.shared.add.f64 [%0], %1;" ::"r"(base + 8u * e), "d"(v) : "memory");
-}
+__device__ __forceinline__ void tsc_tile_add(double* vals, int e, double v) { atomicAdd(vals + e, v); }
 
 template <typename T, bool IDS, bool RECK>
 __global__ void __launch_bounds__(TSC_THREADS) k_tsc_tile_push(PushArgs<T> A) {
@@ -212,7 +213,9 @@ __global__ void __launch_bounds__(TSC_THREADS) k_tsc_tile_push(PushArgs<T> A) {
     constexpr int NT = TSC_THREADS;
     T* sF = reinterpret_cast<T*>(smem);
     unsigned char* sJ = smem + align128((size_t)6 * TSF3 * sizeof(T));
-    const uint32_t sJa = smem_u32(sJ);
+    // the J tile's words: two 32-bit halves per element (FP32) or one double (FP64)
+    using JW = typename std::conditional<JTraits<T>::fixed, unsigned, double>::type;
+    JW* sJw = reinterpret_cast<JW*>(sJ);
     Rec<T>* sM = reinterpret_cast<Rec<T>*>(sJ + align128((size_t)TSJ_ELEMS * 8)) + (threadIdx.x >> 5) * MQ;
     __shared__ int s_off[TILE_CELLS];
     __shared__ int s_hn[TILE_CELLS];
@@ -300,7 +303,7 @@ __global__ void __launch_bounds__(TSC_THREADS) k_tsc_tile_push(PushArgs<T> A) {
             if (errb) atomicOr(&A.ctr->err, errb);
             const T cw[3] = {A.cq[0] * w, A.cq[1] * w, A.cq[2] * w};
             esirkepov_tsc<T>(
-                [&](int comp, int ax, int ay, int az, T v) { tsc_tile_add(sJa, tsc_j_index(comp, x + ax, y + ay, z + az), v); },
+                [&](int comp, int ax, int ay, int az, T v) { tsc_tile_add(sJw, tsc_j_index(comp, x + ax, y + ay, z + az), v); },
                 d1, s, d2, cw);
             const int nx = x + s[0], ny = y + s[1], nz = z + s[2];
             const bool stay = nx >= 0 && nx < ext[0] && ny >= 0 && ny < ext[1] && nz >= 0 && nz < ext[2];
