@@ -653,7 +653,8 @@ static pic_status adjoint_step_t(pic_ctx* c, AdjBuffers& b, const Snapshot& Z) {
         // the spill list's blocks (its count stays on the device: no host round trip)
         int sms = 0;
         cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, c->desc.device);
-        const int spill_blocks = std::max(1, std::min((s.spill_cap + 255) / 256, 2 * std::max(sms, 1)));
+        // (the list is usually empty or short: a few blocks stride over it)
+        const int spill_blocks = std::max(1, std::min((s.spill_cap + 255) / 256, std::max(sms / 4, 1)));
         const long long blocks = (long long)ntiles(c) * chunks + spill_blocks;
         LaunchScope ls(c, KC_OTHER);
         k_adj_particles<T><<<(unsigned)blocks, 256, 0, c->stream>>>(A, chunks);

@@ -777,7 +777,7 @@ __global__ void __launch_bounds__(256) k_split_prep(PushArgs<T> A) {
         A.hout[(size_t)tile * TILE_CELLS + i] = s_hn[i];
     }
     if (threadIdx.x == 0) {
-        const_cast<int*>(A.cnt_in)[tile] = A.pa.count[tile];
+        A.cnt_in[tile] = A.pa.count[tile];
         A.pa.count[tile] = s_total;
         A.pa.holes[tile] = 0;
     }

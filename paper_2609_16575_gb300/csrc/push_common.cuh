@@ -34,7 +34,7 @@ template <typename T> struct PushArgs {
     // counts prepared by k_split_prep
     int parts;
     int* goff;
-    const int* cnt_in;
+    int* cnt_in;
 };
 
 // Sum of one double per thread of the block, added to *dst by thread 0.

@@ -59,3 +59,9 @@ def test_wave_fit_recovers_amplitude_and_wave_number(bench):
         A, b = bench._fit_wave(x, amp * np.sin(beta * x - phi), 5.22)
         assert A == pytest.approx(amp, rel=1e-9)
         assert b == pytest.approx(beta, rel=1e-9)
+
+
+def test_host_memory_and_cores_are_positive(bench):
+    """The end-to-end leg's host-memory check and the oracle baseline's core count."""
+    assert bench.host_memory_available() > 0
+    assert bench.host_cores() >= 1
