@@ -83,6 +83,66 @@ __global__ void k_scatter(Geom g, const double* X, const double* U, const double
     }
 }
 
+// Loader staging record: one particle's working-precision state in one aligned
+// 32-byte (FP32) or 64-byte (FP64) block, so that the scatter into random slots writes
+// whole DRAM sectors (eight separate 4-byte stores per particle leave eight partly
+// written sectors); k_unpack then writes the SoA arrays tile by tile, coalesced.
+template <typename T> struct LoadRec;
+template <> struct alignas(32) LoadRec<float> {
+    int cell;
+    float d[3], u[3], w;
+};
+template <> struct alignas(64) LoadRec<double> {
+    int cell, id;
+    double d[3], u[3], w;
+};
+static_assert(sizeof(LoadRec<float>) == 32 && sizeof(LoadRec<double>) == 64, "loader records fill whole sectors");
+
+template <typename T>
+__global__ void k_scatter_rec(Geom g, const double* X, const double* U, const double* w, const double* ids, long long n,
+                              int* keypos, LoadRec<T>* recs, int* id_out, int track_ids) {
+    for (long long p = blockIdx.x * (long long)blockDim.x + threadIdx.x; p < n; p += (long long)gridDim.x * blockDim.x) {
+        const double Xp[3] = {X[p], X[n + p], X[2 * n + p]};
+        int c[3];
+        T dl[3];
+        if (!locate<T>(g, Xp, c, dl)) continue;
+        const int key = key_of(g, c);
+        const int q = atomicAdd(keypos + key, 1);
+        LoadRec<T> r;
+        r.cell = key & (TILE_CELLS - 1);
+        for (int k = 0; k < 3; ++k) {
+            r.d[k] = dl[k];
+            r.u[k] = (T)U[k * n + p];
+        }
+        r.w = (T)w[p];
+        const int id = ids ? (int)ids[p] : (int)p;
+        if constexpr (sizeof(T) == 8) r.id = id;
+        else if (track_ids) id_out[q] = id;
+        recs[q] = r;
+    }
+}
+
+template <typename T>
+__global__ void __launch_bounds__(256) k_unpack_rec(const LoadRec<T>* recs, ParticleArrays<T> pa, int ntile, int track_ids) {
+    for (int t = blockIdx.x; t < ntile; t += gridDim.x) {
+        const int cnt = pa.count[t];
+        const long long s0 = pa.seg_start[t];
+        for (int i = threadIdx.x; i < cnt; i += blockDim.x) {
+            const long long q = s0 + i;
+            const LoadRec<T> r = recs[q];
+            pa.cell[q] = r.cell;
+            for (int k = 0; k < 3; ++k) {
+                pa.d[k][q] = r.d[k];
+                pa.u[k][q] = r.u[k];
+            }
+            pa.w[q] = r.w;
+            if constexpr (sizeof(T) == 8) {
+                if (track_ids) pa.id[q] = r.id;
+            }
+        }
+    }
+}
+
 static size_t align256(size_t b) { return (b + 255) & ~(size_t)255; }
 
 // ids: optional FP64 load-order ids of the particles (host or device like X), for a
@@ -219,9 +279,21 @@ static pic_status load_t(pic_ctx* c, const pic_species_desc* d, SpeciesDev& s, c
     // the cell histogram of the loaded block (the tile kernel's output ranges)
     GBPIC_CHECK(c, cudaMemcpyAsync(s.hist[0], h_hist.data(), sizeof(int) * nkeys, cudaMemcpyHostToDevice, c->stream));
     if (n > 0) {
+        // through whole-sector staging records when their buffer can be had, else
+        // straight into the SoA arrays
+        LoadRec<T>* recs = static_cast<LoadRec<T>*>(dev_alloc(c, sizeof(LoadRec<T>) * (size_t)total));
         LaunchScope ls(c, KC_OTHER);
-        k_scatter<T><<<grid, 256, 0, c->stream>>>(g, X, U, W, IDS, n, hist, pa, c->desc.track_ids);
-        GBPIC_CHECK(c, cudaGetLastError());
+        if (recs) {
+            k_scatter_rec<T><<<grid, 256, 0, c->stream>>>(g, X, U, W, IDS, n, hist, recs, pa.id, c->desc.track_ids);
+            GBPIC_CHECK(c, cudaGetLastError());
+            k_unpack_rec<T><<<std::min(ntile, 65535), 256, 0, c->stream>>>(recs, pa, ntile, c->desc.track_ids);
+            GBPIC_CHECK(c, cudaGetLastError());
+            GBPIC_CHECK(c, cudaStreamSynchronize(c->stream));
+            dev_free(c, recs);
+        } else {
+            k_scatter<T><<<grid, 256, 0, c->stream>>>(g, X, U, W, IDS, n, hist, pa, c->desc.track_ids);
+            GBPIC_CHECK(c, cudaGetLastError());
+        }
     }
     // mover and spill lists (a window move sends the first cell column of every tile to
     // the tile before it: an eighth of the particles, plus the new column's plasma)
