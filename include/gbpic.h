@@ -347,7 +347,11 @@ pic_status pic_set_wait_limit(pic_ctx* ctx, int32_t polls);
  *
  * pic_adjoint_forward advances nsteps cycles from the current state s^0, keeping a
  * device-memory snapshot of the full state every ckpt_every steps, and returns L.
- * Needs track_ids = 1 (gradients are reported per loaded particle).
+ * Needs track_ids = 1 (gradients are reported per loaded particle).  It reserves, in
+ * one device allocation, the checkpoints, min(nsteps, ckpt_every) recomputed states and
+ * the backward pass's buffers (PIC_ERR_OOM if that fails), so that the backward pass
+ * allocates nothing; the reservation lives until the next pic_adjoint_forward or
+ * pic_destroy.
  *
  * pic_adjoint_backward returns, for that L,
  *   dL_du[s]: for each species s (an array of species pointers, entries may be
@@ -356,10 +360,12 @@ pic_status pic_set_wait_limit(pic_ctx* ctx, int32_t polls);
  *             initial fields are E^0 = A E_dir and B^{-1/2} = A B_dir (E_dir, B_dir:
  *             3*N FP64 values in the host field layout, either may be NULL).
  * It restores each checkpoint, recomputes the segment's states and runs the adjoint
- * kernels (Yee^T, deposit^T, position^T, Boris^T, gather^T) in reverse; adjoint
- * arithmetic and parameter-gradient sums are FP64.  Afterwards the context holds the
- * final state s^N again.  device_pointers = 1: E_dir, B_dir and dL_du are device
- * pointers.  Synchronises. */
+ * kernels (Yee^T, deposit^T, position^T, Boris^T, gather^T) in reverse; the field
+ * adjoints and parameter-gradient sums are FP64, the per-particle Jacobian products
+ * run in the context's precision.  Afterwards the context holds the final state s^N
+ * again.  device_pointers = 1: E_dir, B_dir and dL_du are device pointers.
+ * PIC_ERR_STATE without a preceding pic_adjoint_forward, or when a species was loaded
+ * since.  Synchronises. */
 pic_status pic_adjoint_forward(pic_ctx* ctx, int32_t nsteps, int32_t ckpt_every, double* loss);
 pic_status pic_adjoint_backward(pic_ctx* ctx, const double* E_dir, const double* B_dir, double* dL_dA,
                                 double* const* dL_du, int32_t device_pointers);

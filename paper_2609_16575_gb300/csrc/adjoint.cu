@@ -16,8 +16,9 @@
 //     derivative of the interpolation weights)
 //   lE  <- lE - h C_B lB              (from B_n = B^{n-1/2} - h C_E E^n)
 // The host loop keeps a full-state snapshot every K steps, recomputes each segment
-// forward, and runs the adjoint steps in reverse; all adjoint arithmetic and the
-// parameter-gradient reductions are FP64.
+// forward, and runs the adjoint steps in reverse.  The field adjoints, the gather^T
+// accumulators and the parameter-gradient reductions are FP64; the per-particle
+// Jacobian products and the particles' adjoint state use the working precision.
 #include <algorithm>
 #include <cmath>
 #include <vector>
@@ -38,7 +39,19 @@ struct Snapshot {
     void* fields[6] = {};
     std::vector<SpeciesSnap> sp;
     int64_t step = 0;
-    bool alloc = false;
+};
+
+// The backward host loop's device buffers.
+struct AdjBuffers {
+    double* lE[3] = {};
+    double* lB[3] = {};
+    void* lJ[3] = {};       // -dt lambda_E^{n+1} in the working precision
+    double* accE[3] = {};   // accE[0..2] and accB[0..2] are one contiguous block
+    double* accB[3] = {};
+    void* Bn[3] = {};
+    std::vector<void*> lX, lU;   // the particles' adjoint state, working precision
+    std::vector<double*> conv;   // FP64 copies of lU for dL_du (FP32 path only)
+    double* stage = nullptr;     // the directions E_dir, B_dir and the dL_dA sum
 };
 
 struct AdjointState {
@@ -47,6 +60,9 @@ struct AdjointState {
     std::vector<Snapshot> ckpt;
     std::vector<Snapshot> seg;
     Snapshot final_;
+    AdjBuffers buf;
+    void* block = nullptr;                 // the one device allocation all of the above use
+    std::vector<int64_t> species_loaded;   // n_loaded per species at the forward pass
     bool ready = false;
 };
 
@@ -116,26 +132,82 @@ struct MultiCopy {
     }
 };
 
-static pic_status snap_alloc(pic_ctx* c, Snapshot& S) {
-    if (S.alloc) return PIC_OK;
-    for (int k = 0; k < 6; ++k)
-        if (!(S.fields[k] = dev_alloc(c, field_bytes(c)))) return PIC_ERR_OOM;
+// The adjoint's device memory is one block, reserved by pic_adjoint_forward and carved
+// into the checkpoints, the segment's recomputed states, the final state and the
+// backward pass's buffers: cudaMalloc and cudaFree synchronise the device and take tens
+// of microseconds each, and a backward pass had made some two hundred of them.  Carve
+// runs twice: once with a null base to size the block, once to hand out its pieces
+// (each 256-byte aligned).
+struct Carve {
+    unsigned char* base = nullptr;
+    size_t off = 0;
+    void* take(size_t n) {
+        void* r = base ? base + off : nullptr;
+        off += (n + 255) & ~size_t(255);
+        return r;
+    }
+};
+
+static void snap_carve(pic_ctx* c, Carve& cv, Snapshot& S) {
+    for (int k = 0; k < 6; ++k) S.fields[k] = cv.take(field_bytes(c));
     S.sp.resize(c->species.size());
     for (size_t i = 0; i < c->species.size(); ++i) {
         SpeciesDev& s = c->species[i];
         SpeciesSnap& z = S.sp[i];
-        if (!(z.part = dev_alloc(c, s.pbytes)) ||
-            !(z.counts = dev_alloc(c, (2 + TILE_CELLS) * sizeof(int) * ntiles(c))) ||
-            !(z.ctr = dev_alloc(c, sizeof(Counters))) || !(z.spill = dev_alloc(c, rec_bytes(c) * s.spill_cap)))
-            return PIC_ERR_OOM;
+        z.part = cv.take(s.pbytes);
+        z.counts = cv.take((2 + TILE_CELLS) * sizeof(int) * ntiles(c));
+        z.ctr = cv.take(sizeof(Counters));
+        z.spill = cv.take(rec_bytes(c) * s.spill_cap);
     }
-    S.alloc = true;
+}
+
+static void buffers_carve(pic_ctx* c, Carve& cv, AdjBuffers& b) {
+    const size_t pb = sizeof(double) * (size_t)c->g.padded_size();
+    const size_t cb = sizeof(double) * (size_t)c->g.N;
+    const size_t fb = field_bytes(c);
+    double* acc6 = static_cast<double*>(cv.take(6 * cb));   // accE[0..2], accB[0..2], contiguous
+    for (int k = 0; k < 3; ++k) {
+        b.lE[k] = static_cast<double*>(cv.take(pb));
+        b.lB[k] = static_cast<double*>(cv.take(pb));
+        b.accE[k] = acc6 ? acc6 + k * (size_t)c->g.N : nullptr;
+        b.accB[k] = acc6 ? acc6 + (3 + k) * (size_t)c->g.N : nullptr;
+        b.Bn[k] = cv.take(fb);
+        b.lJ[k] = cv.take(fb);
+    }
+    b.lX.clear();
+    b.lU.clear();
+    b.conv.clear();
+    for (auto& s : c->species) {
+        const size_t m = 3 * (size_t)std::max<int64_t>(s.n_loaded, 1);
+        b.lX.push_back(cv.take(c->esize * m));
+        b.lU.push_back(cv.take(c->esize * m));
+        b.conv.push_back(c->esize == sizeof(double) ? nullptr : static_cast<double*>(cv.take(sizeof(double) * m)));
+    }
+    b.stage = static_cast<double*>(cv.take(sizeof(double) * (6 * (size_t)c->g.N + 1)));
+}
+
+// Sizes and reserves the block for the state's checkpoints and segment states.
+static pic_status adjoint_reserve(pic_ctx* c, AdjointState& S) {
+    size_t total = 0;
+    for (int pass = 0; pass < 2; ++pass) {
+        if (pass == 1) {
+            S.block = dev_alloc(c, total);
+            if (!S.block) return PIC_ERR_OOM;
+        }
+        Carve cv;
+        cv.base = static_cast<unsigned char*>(S.block);
+        for (auto& z : S.ckpt) snap_carve(c, cv, z);
+        for (auto& z : S.seg) snap_carve(c, cv, z);
+        snap_carve(c, cv, S.final_);
+        buffers_carve(c, cv, S.buf);
+        total = cv.off;
+    }
+    S.species_loaded.clear();
+    for (auto& s : c->species) S.species_loaded.push_back(s.n_loaded);
     return PIC_OK;
 }
 
 static pic_status snap_save(pic_ctx* c, Snapshot& S) {
-    pic_status st = snap_alloc(c, S);
-    if (st != PIC_OK) return st;
     const size_t fb = field_bytes(c);
     MultiCopy M(c);
     for (int k = 0; k < 3; ++k) {
@@ -153,7 +225,7 @@ static pic_status snap_save(pic_ctx* c, Snapshot& S) {
         M.add(z.ctr, s.ctr, sizeof(Counters));
         M.add(z.spill, s.spill, rec_bytes(c) * s.spill_cap);
     }
-    st = M.flush();
+    const pic_status st = M.flush();
     if (st != PIC_OK) return st;
     S.step = c->step;
     return PIC_OK;
@@ -289,39 +361,44 @@ __device__ __forceinline__ void cross3(const C a[3], const C b[3], C o[3]) {
 // the forward particle state) run in the working precision C (FP32 on the FP32 path,
 // where FP64 arithmetic would run on the GPU's narrow FP64 pipe); the field
 // accumulators and the parameter gradients are FP64 on both paths.
-template <typename T, typename C, typename AddFn>
-__device__ void adjoint_particle(const AdjArgs<T>& A, AddFn Add, int gx, int gy, int gz, const C d1[3], const C u0[3], C w,
-                                 int id) {
+// The trilinear stencil of field component comp (E_c half a cell along c, B_c half a
+// cell along the other two) at a particle in cell gc with in-cell offsets d1: the base
+// node b and the fractions s (section 2.5's staggered CIC weights).
+template <typename C>
+__device__ __forceinline__ void adj_stencil(const int gc[3], const C d1[3], int comp, int b[3], C s[3]) {
+    #pragma unroll
+    for (int k = 0; k < 3; ++k) {
+        const bool half = comp < 3 ? k == comp : k != comp - 3;
+        if (!half) {
+            b[k] = gc[k];
+            s[k] = d1[k];
+        } else if (d1[k] >= C(0.5)) {
+            b[k] = gc[k];
+            s[k] = d1[k] - C(0.5);
+        } else {
+            b[k] = gc[k] - 1;
+            s[k] = d1[k] + C(0.5);
+        }
+    }
+}
+
+// Returns in lam the adjoint of the six gathered components (lambda_E, lambda_B at the
+// particle), which the caller scatters through the stencils of adj_stencil (gather^T),
+// and updates the particle's own adjoint state in lX, lU.
+template <typename T, typename C>
+__device__ void adjoint_particle(const AdjArgs<T>& A, int gx, int gy, int gz, const C d1[3], const C u0[3], C w, int id,
+                                 C lam[6]) {
     const Geom& g = A.g;
     const int gc[3] = {gx, gy, gz};
     // ---- forward recompute: staggered gather with weights and their gradients
-    int hb[3], nb[3];
-    C hs[3], ns[3];
-    #pragma unroll
-    for (int k = 0; k < 3; ++k) {
-        if (d1[k] >= C(0.5)) {
-            hb[k] = gc[k];
-            hs[k] = d1[k] - C(0.5);
-        } else {
-            hb[k] = gc[k] - 1;
-            hs[k] = d1[k] + C(0.5);
-        }
-        nb[k] = gc[k];
-        ns[k] = d1[k];
-    }
-    const int HF[6][3] = {{1, 0, 0}, {0, 1, 0}, {0, 0, 1}, {0, 1, 1}, {1, 0, 1}, {1, 1, 0}};
     C val[6], grad[6][3];
-    int cb[6][3];
-    C cs[6][3];
     #pragma unroll
     for (int comp = 0; comp < 6; ++comp) {
-        #pragma unroll
-        for (int k = 0; k < 3; ++k) {
-            cb[comp][k] = HF[comp][k] ? hb[k] : nb[k];
-            cs[comp][k] = HF[comp][k] ? hs[k] : ns[k];
-        }
+        int cb[3];
+        C cs[3];
+        adj_stencil(gc, d1, comp, cb, cs);
         const T* F = comp < 3 ? A.E[comp] : A.Bn[comp - 3];
-        val[comp] = interp_grad<T, C>(g, F, cb[comp], cs[comp], grad[comp]);
+        val[comp] = interp_grad<T, C>(g, F, cb, cs, grad[comp]);
     }
     const C Ep[3] = {val[0], val[1], val[2]}, Bp[3] = {val[3], val[4], val[5]};
     // Boris with its intermediates (section 2.4)
@@ -429,8 +506,8 @@ __device__ void adjoint_particle(const AdjArgs<T>& A, AddFn Add, int gx, int gy,
     }
     #pragma unroll
     for (int c = 0; c < 3; ++c) {
-        scatter_trilinear(Add, c, cb[c], cs[c], lE[c]);
-        scatter_trilinear(Add, 3 + c, cb[3 + c], cs[3 + c], lB[c]);
+        lam[c] = lE[c];
+        lam[3 + c] = lB[c];
     }
     #pragma unroll
     for (int k = 0; k < 3; ++k) {
@@ -439,20 +516,39 @@ __device__ void adjoint_particle(const AdjArgs<T>& A, AddFn Add, int gx, int gy,
     }
 }
 
-// Each CTA takes a chunk of ADJ_CHUNK slots of one tile (blocks beyond the tiles'
+// gather^T of one particle through Add(comp, x, y, z, value).
+template <typename C, typename AddFn>
+__device__ __forceinline__ void scatter_particle(AddFn Add, const int gc[3], const C d1[3], const C lam[6]) {
+    #pragma unroll
+    for (int comp = 0; comp < 6; ++comp) {
+        int b[3];
+        C sf[3];
+        adj_stencil(gc, d1, comp, b, sf);
+        scatter_trilinear(Add, comp, b, sf, lam[comp]);
+    }
+}
+
+// Each CTA takes a chunk of adj_chunk<T>() slots of one tile (blocks beyond the tiles'
 // chunks take the spill list).  The gather^T contributions of the chunk are summed in a
 // shared box of the tile's nodes -1..8 per dimension and added to the global FP64
 // accumulators once per node.  The box holds the working precision: FP64 sums on the
-// FP64 path, FP32 sums of at most ADJ_CHUNK terms on the FP32 path (whose per-particle
+// FP64 path, FP32 sums of at most one chunk's terms on the FP32 path (whose per-particle
 // Jacobians are FP32 already), where FP64 additions would run on the GPU's narrow FP64
-// pipe.  Lane l of warp w handles slots 32 l + w + 8 m: the lanes
-// of a warp sit 32 slots apart in the cell-sorted segment, so they rarely add to the
-// same node at once (shared FP64 additions to one address serialise).
-constexpr int AB = 10;           // nodes per dimension of the shared adjoint box
-constexpr int ADJ_CHUNK = 1024;  // slots per CTA (8 warps x 32 lanes x 4)
+// pipe.  Lane l of warp w handles slots (chunk / 32) l + w + 8 m: the lanes of a warp sit
+// one or two cells apart in the cell-sorted segment, so they rarely add to the same node
+// at once (shared floating-point additions to one address serialise).  The FP64 kernel
+// holds one CTA per SM (its registers), so its chunks are half as long: twice the CTAs
+// leave a shorter tail.  (64-bit fixed-point sums in two 32-bit words with native
+// shared reductions, as the tile kernel's current tile, ran no faster on the FP32 path:
+// the fixed-point unit needs the chunk's largest lambda before the first addition, so
+// every particle's lambdas had to be staged in shared memory first.)
+constexpr int AB = 10;   // nodes per dimension of the shared adjoint box
+constexpr int ADJ_NB = 6 * AB * AB * AB;
+template <typename T> __host__ __device__ constexpr int adj_chunk() { return sizeof(T) == sizeof(double) ? 512 : 1024; }
 template <typename T>
 __global__ void __launch_bounds__(256) k_adj_particles(AdjArgs<T> A, int chunks_per_tile) {
-    __shared__ T sacc[6 * AB * AB * AB];
+    constexpr int CH = adj_chunk<T>();
+    __shared__ T sacc[ADJ_NB];
     const Geom& g = A.g;
     const int nt = g.nt[0] * g.nt[1] * g.nt[2];
     auto gadd = [&](int comp, int x, int y, int z, T v) {
@@ -465,36 +561,40 @@ __global__ void __launch_bounds__(256) k_adj_particles(AdjArgs<T> A, int chunks_
         for (long long i = (blockIdx.x - nblk_tiles) * blockDim.x + threadIdx.x; i < nsp;
              i += (gridDim.x - nblk_tiles) * blockDim.x) {
             const Rec<T> r = A.spill[i];
-            adjoint_particle<T, T>(A, gadd, r.cell % g.n[0], (r.cell / g.n[0]) % g.n[1], r.cell / (g.n[0] * g.n[1]),
-                                   r.d, r.u, r.w, r.id);
+            const int gc[3] = {r.cell % g.n[0], (r.cell / g.n[0]) % g.n[1], r.cell / (g.n[0] * g.n[1])};
+            T lam[6];
+            adjoint_particle<T, T>(A, gc[0], gc[1], gc[2], r.d, r.u, r.w, r.id, lam);
+            scatter_particle(gadd, gc, r.d, lam);
         }
         return;
     }
     const int t = blockIdx.x / chunks_per_tile, chunk = blockIdx.x % chunks_per_tile;
     const int cnt = min(A.pa.count[t], A.pa.cap[t]);
-    const int i0 = chunk * ADJ_CHUNK;
+    const int i0 = chunk * CH;
     if (i0 >= cnt) return;
     const int tx = t % g.nt[0], ty = (t / g.nt[0]) % g.nt[1], tz = t / (g.nt[0] * g.nt[1]);
     const int ox = tx * TILE, oy = ty * TILE, oz = tz * TILE;
-    for (int i = threadIdx.x; i < 6 * AB * AB * AB; i += blockDim.x) sacc[i] = T(0);
+    for (int i = threadIdx.x; i < ADJ_NB; i += blockDim.x) sacc[i] = T(0);
     __syncthreads();
     auto sadd = [&](int comp, int x, int y, int z, T v) {
         atomicAdd(sacc + ((comp * AB + (z - oz + 1)) * AB + (y - oy + 1)) * AB + (x - ox + 1), v);
     };
     const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
-    for (int m = 0; m < ADJ_CHUNK / 256; ++m) {
-        const int i = i0 + 32 * lane + warp + 8 * m;
+    for (int m = 0; m < CH / 256; ++m) {
+        const int i = i0 + (CH / 32) * lane + warp + 8 * m;
         if (i >= cnt) continue;
         const long long p = (long long)A.pa.seg_start[t] + i;
         const int lc = A.pa.cell[p];
         if (lc < 0) continue;
+        const int gc[3] = {ox + (lc & 7), oy + ((lc >> 3) & 7), oz + (lc >> 6)};
         const T d1[3] = {A.pa.d[0][p], A.pa.d[1][p], A.pa.d[2][p]};
         const T u0[3] = {A.pa.u[0][p], A.pa.u[1][p], A.pa.u[2][p]};
-        adjoint_particle<T, T>(A, sadd, ox + (lc & 7), oy + ((lc >> 3) & 7), oz + (lc >> 6), d1, u0, A.pa.w[p],
-                               A.pa.id[p]);
+        T lam[6];
+        adjoint_particle<T, T>(A, gc[0], gc[1], gc[2], d1, u0, A.pa.w[p], A.pa.id[p], lam);
+        scatter_particle(sadd, gc, d1, lam);
     }
     __syncthreads();
-    for (int e = threadIdx.x; e < 6 * AB * AB * AB; e += blockDim.x) {
+    for (int e = threadIdx.x; e < ADJ_NB; e += blockDim.x) {
         const T v = sacc[e];
         if (v == T(0)) continue;
         const int lx = e % AB, ly = (e / AB) % AB, lz = (e / (AB * AB)) % AB, comp = e / (AB * AB * AB);
@@ -550,16 +650,6 @@ __global__ void k_dot(Geom g, const double* lE0, const double* lE1, const double
 
 // ---------------------------------------------------------------------------
 // The backward host loop.
-
-struct AdjBuffers {
-    double* lE[3] = {};
-    double* lB[3] = {};
-    void* lJ[3] = {};       // -dt lambda_E^{n+1} in the working precision
-    double* accE[3] = {};   // accE[0..2] and accB[0..2] are one contiguous block
-    double* accB[3] = {};
-    void* Bn[3] = {};
-    std::vector<void*> lX, lU;   // the particles' adjoint state, working precision
-};
 
 // The particle arrays of a snapshot: the live block layout the snapshot copied, rebased
 // onto the snapshot's copy, with its tile counts and holes.
@@ -649,7 +739,7 @@ static pic_status adjoint_step_t(pic_ctx* c, AdjBuffers& b, const Snapshot& Z) {
         A.C[2] = s.q / (dt * d[0] * d[1]);
         int maxcap = 0;
         for (int cap : s.h_cap) maxcap = std::max(maxcap, cap);
-        const int chunks = std::max(1, (maxcap + ADJ_CHUNK - 1) / ADJ_CHUNK);
+        const int chunks = std::max(1, (maxcap + adj_chunk<T>() - 1) / adj_chunk<T>());
         // the spill list's blocks (its count stays on the device: no host round trip)
         int sms = 0;
         cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, c->desc.device);
@@ -669,25 +759,11 @@ static pic_status adjoint_step_t(pic_ctx* c, AdjBuffers& b, const Snapshot& Z) {
     return curl_to_e<double>(c, b.lE, b.lB, -h);
 }
 
-static void snap_free(pic_ctx* c, Snapshot& S) {
-    if (!S.alloc) return;
-    for (int k = 0; k < 6; ++k) dev_free(c, S.fields[k]);
-    for (auto& z : S.sp) {
-        dev_free(c, z.part);
-        dev_free(c, z.counts);
-        dev_free(c, z.ctr);
-        dev_free(c, z.spill);
-    }
-    S.alloc = false;
-}
-
 static void adjoint_release(pic_ctx* c) {
     AdjointState* S = static_cast<AdjointState*>(c->adj);
     if (!S) return;
     if (c->stream) cudaStreamSynchronize(c->stream);
-    for (auto& z : S->ckpt) snap_free(c, z);
-    for (auto& z : S->seg) snap_free(c, z);
-    snap_free(c, S->final_);
+    dev_free(c, S->block);
     delete S;
     c->adj = nullptr;
 }
@@ -695,36 +771,13 @@ static void adjoint_release(pic_ctx* c) {
 template <typename T>
 static pic_status backward_t(pic_ctx* c, AdjointState& S, const double* Ed, const double* Bd, double* dL_dA,
                              double* const* dL_du, int devptr) {
-    AdjBuffers b;
-    const size_t pb = sizeof(double) * (size_t)c->g.padded_size();
+    AdjBuffers& b = S.buf;
     const size_t cb = sizeof(double) * (size_t)c->g.N;
     const size_t fb = (size_t)c->g.padded_size() * sizeof(T);
-    std::vector<void*> temp;
-    auto alloc = [&](size_t n) {
-        void* p = dev_alloc(c, n);
-        if (p) temp.push_back(p);
-        return p;
-    };
-    double* acc6 = static_cast<double*>(alloc(6 * cb));   // accE[0..2], accB[0..2], contiguous
-    if (!acc6) return PIC_ERR_OOM;
-    for (int k = 0; k < 3; ++k) {
-        b.lE[k] = static_cast<double*>(alloc(pb));
-        b.lB[k] = static_cast<double*>(alloc(pb));
-        b.accE[k] = acc6 + k * (size_t)c->g.N;
-        b.accB[k] = acc6 + (3 + k) * (size_t)c->g.N;
-        b.Bn[k] = alloc(fb);
-        b.lJ[k] = alloc(fb);
-        if (!b.lE[k] || !b.lB[k] || !b.Bn[k] || !b.lJ[k]) return PIC_ERR_OOM;
-    }
-    for (auto& s : c->species) {
-        const size_t nb = sizeof(T) * 3 * std::max<int64_t>(s.n_loaded, 1);
-        void* x = alloc(nb);
-        void* u = alloc(nb);
-        if (!x || !u) return PIC_ERR_OOM;
-        GBPIC_CHECK(c, cudaMemsetAsync(x, 0, nb, c->stream));
-        GBPIC_CHECK(c, cudaMemsetAsync(u, 0, nb, c->stream));
-        b.lX.push_back(x);
-        b.lU.push_back(u);
+    for (size_t si = 0; si < c->species.size(); ++si) {
+        const size_t nb = sizeof(T) * 3 * std::max<int64_t>(c->species[si].n_loaded, 1);
+        GBPIC_CHECK(c, cudaMemsetAsync(b.lX[si], 0, nb, c->stream));
+        GBPIC_CHECK(c, cudaMemsetAsync(b.lU[si], 0, nb, c->stream));
     }
     // the final state and the adjoint of L = 1/2 dV sum (E^N^2 + B_N^2)
     pic_status st = snap_restore(c, S.final_);
@@ -770,8 +823,7 @@ static pic_status backward_t(pic_ctx* c, AdjointState& S, const double* Ed, cons
     }
     // parameter gradients (FP64)
     if (dL_dA) {
-        double* stage = static_cast<double*>(alloc(sizeof(double) * (6 * (size_t)c->g.N + 1)));
-        if (!stage) return PIC_ERR_OOM;
+        double* stage = b.stage;
         const double* dEd = Ed;
         const double* dBd = Bd;
         if (!devptr) {
@@ -796,8 +848,7 @@ static pic_status backward_t(pic_ctx* c, AdjointState& S, const double* Ed, cons
             const long long m = 3 * c->species[si].n_loaded;
             const double* src = static_cast<const double*>(b.lU[si]);
             if (sizeof(T) != sizeof(double) && m > 0) {
-                double* conv = static_cast<double*>(alloc(sizeof(double) * m));
-                if (!conv) return PIC_ERR_OOM;
+                double* conv = b.conv[si];
                 LaunchScope ls(c, KC_OTHER);
                 k_scale_copy<T><<<1024, 256, 0, c->stream>>>(m, static_cast<const T*>(b.lU[si]), conv, 1.0);
                 GBPIC_CHECK(c, cudaGetLastError());
@@ -807,8 +858,6 @@ static pic_status backward_t(pic_ctx* c, AdjointState& S, const double* Ed, cons
                                            devptr ? cudaMemcpyDeviceToDevice : cudaMemcpyDeviceToHost, c->stream));
         }
     }
-    GBPIC_CHECK(c, cudaStreamSynchronize(c->stream));
-    for (void* p : temp) dev_free(c, p);
     // leave the context at the final state
     st = snap_restore(c, S.final_);
     if (st != PIC_OK) return st;
@@ -838,6 +887,8 @@ pic_status pic_adjoint_forward(pic_ctx* c, int32_t nsteps, int32_t ckpt_every, d
     S->K = ckpt_every;
     S->ckpt.resize((nsteps + ckpt_every - 1) / ckpt_every);
     S->seg.resize(std::min(nsteps, ckpt_every));
+    pic_status st0 = adjoint_reserve(c, *S);
+    if (st0 != PIC_OK) return st0;
     update_jscale(c);
     if (c->j_dirty) {
         for (int k = 0; k < 3; ++k)
@@ -872,6 +923,12 @@ pic_status pic_adjoint_backward(pic_ctx* c, const double* E_dir, const double* B
     AdjointState* S = static_cast<AdjointState*>(c->adj);
     if (!S || !S->ready) {
         c->err = "pic_adjoint_backward needs a preceding pic_adjoint_forward";
+        return PIC_ERR_STATE;
+    }
+    bool same = S->species_loaded.size() == c->species.size();
+    for (size_t i = 0; same && i < c->species.size(); ++i) same = S->species_loaded[i] == c->species[i].n_loaded;
+    if (!same) {
+        c->err = "pic_adjoint_backward: the species changed since pic_adjoint_forward";
         return PIC_ERR_STATE;
     }
     DeviceScope dscope_(c->desc.device);

@@ -8,7 +8,10 @@
 #include <cstdlib>
 #include <cstdio>
 #include <cstring>
+#include <mutex>
 #include <new>
+#include <set>
+#include <tuple>
 
 #include <nvtx3/nvToolsExt.h>
 #include "pic_internal.cuh"
@@ -27,6 +30,16 @@ void* dev_alloc(pic_ctx* c, size_t bytes) {
     if (p) c->allocations.push_back(p);
     else c->err = "device allocation of " + std::to_string(bytes) + " bytes failed";
     return p;
+}
+
+cudaError_t raise_smem_limit(const void* kern, size_t bytes, int dev) {
+    static std::mutex mu;
+    static std::set<std::tuple<const void*, int, size_t>> done;
+    std::lock_guard<std::mutex> lock(mu);
+    if (done.count({kern, dev, bytes})) return cudaSuccess;
+    const cudaError_t e = cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)bytes);
+    if (e == cudaSuccess) done.insert({kern, dev, bytes});
+    return e;
 }
 
 void dev_free(pic_ctx* c, void* p) {

@@ -726,6 +726,10 @@ pic_status static_scratch_prepare(pic_ctx* c);   // static_check.cu
 
 // helpers (api.cu)
 void* dev_alloc(pic_ctx* c, size_t bytes);
+// Raises kernel kern's dynamic shared-memory limit to bytes on device dev, once per
+// (kernel, device, size): cudaFuncSetAttribute acts on the calling thread's current
+// device only.
+cudaError_t raise_smem_limit(const void* kern, size_t bytes, int dev);
 void dev_free(pic_ctx* c, void* p);
 pic_status cuda_fail(pic_ctx* c, cudaError_t e, const char* what);
 void timing_begin(pic_ctx* c, int cls, cudaEvent_t* a);

@@ -105,7 +105,7 @@ template <typename T, bool ESK>
 __device__ __forceinline__ void q_push(WarpQueue<T> Q, int& qn, int& me, bool want_a, int ka,
                                        const typename Pair<T>::t va[6], bool want_b, int kb,
                                        const typename Pair<T>::t vb[6], int lane, uint32_t sJa, int qoff) {
-    const unsigned ma = __ballot_sync(0xffffffffu, want_a), mb = __ballot_sync(0xffffffffu, want_b);
+    const unsigned ma = __ballot_sync(0xffffffffu, want_a), mb = ESK ? 0u : __ballot_sync(0xffffffffu, want_b);
     if (!(ma | mb)) return;
     const unsigned lt = (1u << lane) - 1u;
     if (qn + __popc(ma) > (ESK ? q_cap(me) : QCAP)) {
@@ -1002,11 +1002,7 @@ template <typename T, bool IDS, bool RECK, bool ESK, bool SPLIT = false>
 static pic_status launch_tile(pic_ctx* c, PushArgs<T>& A) {
     auto kern = k_tile_push<T, IDS, RECK, ESK, SPLIT>;
     const size_t smem = tile_smem_bytes<T>();
-    static bool attr_set = false;
-    if (!attr_set) {
-        GBPIC_CHECK(c, cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem));
-        attr_set = true;
-    }
+    GBPIC_CHECK(c, raise_smem_limit(reinterpret_cast<const void*>(kern), smem, c->desc.device));
     const int ntile = c->g.nt[0] * c->g.nt[1] * c->g.nt[2];
     LaunchScope ls(c, KC_TILE_PUSH);
     if (SPLIT) {

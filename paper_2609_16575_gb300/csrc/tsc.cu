@@ -480,7 +480,7 @@ template <typename T, bool IDS, bool RECK>
 static pic_status launch_tsc_tile(pic_ctx* c, PushArgs<T>& A) {
     auto kern = k_tsc_tile_push<T, IDS, RECK>;
     const size_t smem = tsc_smem_bytes<T>();
-    GBPIC_CHECK(c, cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem));
+    GBPIC_CHECK(c, raise_smem_limit(reinterpret_cast<const void*>(kern), smem, c->desc.device));
     const int ntile = c->g.nt[0] * c->g.nt[1] * c->g.nt[2];
     LaunchScope ls(c, KC_TILE_PUSH);
     kern<<<ntile, TSC_THREADS, smem, c->stream>>>(A);

@@ -70,6 +70,30 @@ def test_adjoint_needs_ids_and_a_periodic_box():
     ctx.close()
 
 
+def test_adjoint_backward_refuses_a_changed_species_set():
+    """The backward pass needs the species of its forward pass: without a forward pass,
+    and after a species was loaded since, it returns PIC_ERR_STATE; a new forward pass
+    (which reserves its memory again) makes it work."""
+    from paper_2609_16575_gb300 import gbpic
+
+    wl = W.thermal((8, 8, 8), 0.2, 2, 0.05, seed=75)
+    ctx = gbpic.Context(wl.n, wl.d, wl.dt, precision=1, rho_ion=0.0, track_ids=True)
+    ctx.load_species_array(-1.0, 1.0, wl.species[0].P)
+    with pytest.raises(gbpic.PicError) as e:
+        ctx.adjoint_backward()
+    assert e.value.status == gbpic.PIC_ERR_STATE
+    ctx.adjoint_forward(4, 2)
+    ctx.load_species_array(1.0, 1836.0, wl.species[0].P)
+    with pytest.raises(gbpic.PicError) as e:
+        ctx.adjoint_backward()
+    assert e.value.status == gbpic.PIC_ERR_STATE
+    assert b"species changed" in gbpic.lib().pic_last_error(ctx.ptr)
+    ctx.adjoint_forward(4, 2)
+    _, du = ctx.adjoint_backward()
+    assert len(du) == 2 and all(np.isfinite(g).all() for g in du)
+    ctx.close()
+
+
 # --- failures made on the host, reported by the library without faulting the device ---
 
 @pytest.mark.parametrize("prec", [0, 1])
