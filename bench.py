@@ -376,10 +376,15 @@ def other_workloads(torch, peak, peak_kind):
     out["thermal128_filtered_f32"]["note"] = ("'other' holds the filter: 1 binomial pass per dimension and the "
                                               "compensator, each over J")
     base = out["thermal128_f32"]["kernels"]["tile_push"]
-    esk = out["thermal128_esirkepov_f32"]["kernels"].get("tile_push")
+    ek = out["thermal128_esirkepov_f32"]["kernels"]
+    esk = ek.get("tile_push")
     if esk:
-        out["thermal128_esirkepov_f32"]["tile_push_over_zigzag"] = (esk["ms"] / esk["launches"]) / (
+        # the crossers' deposit runs in its own kernel after the tile kernel
+        cross = ek.get("esk_crossers", {"ms": 0.0})
+        out["thermal128_esirkepov_f32"]["particle_kernels_over_zigzag"] = ((esk["ms"] + cross["ms"]) / esk["launches"]) / (
             base["ms"] / base["launches"])
+        out["thermal128_esirkepov_f32"]["step_over_zigzag"] = (out["thermal128_esirkepov_f32"]["ms_per_step"] /
+                                                               out["thermal128_f32"]["ms_per_step"])
 
     # the wakefield with the moving window: a one-cell move every ceil(dx / dt) = 3
     # cycles from the first cycle on, the new column's plasma injected at each move

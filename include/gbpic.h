@@ -244,7 +244,9 @@ pic_status pic_set_port(pic_ctx* ctx, const pic_port_desc* port);
  * faces is one straight segment for Esirkepov (weights Wx = DSx (S0y S0z + DSy S0z / 2 +
  * S0y DSz / 2 + DSy DSz / 3) on the 3x3x3 support, Jx the running sum of -q w Wx /
  * (dt dy dz) along x) and two relayed segments for ZigZag.  The adjoint supports ZigZag
- * only (PIC_ERR_STATE).  Call before stepping or between steps. */
+ * only (PIC_ERR_STATE).  Call before stepping or between steps.  The first Esirkepov
+ * step of a species reserves device memory for its crossers' records, 40 bytes (FP32)
+ * or 80 bytes (FP64) per particle slot; that step returns PIC_ERR_OOM when it cannot. */
 typedef enum pic_deposit { PIC_DEPOSIT_ZIGZAG = 0, PIC_DEPOSIT_ESIRKEPOV = 1 } pic_deposit;
 pic_status pic_set_deposit(pic_ctx* ctx, int32_t deposit);
 

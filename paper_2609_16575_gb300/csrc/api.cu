@@ -68,8 +68,8 @@ static cudaEvent_t take_event(pic_ctx* c) {
 
 // Kernel classes as named by pic_kernel_times and by the NVTX ranges around each launch
 // (a profiler's timeline shows them; without one attached the ranges cost nothing).
-static const char* const kKernelClassNames[KC_COUNT] = {"faraday_half", "tile_push", "list_push", "append",
-                                                        "ampere",       "sort",      "other"};
+static const char* const kKernelClassNames[KC_COUNT] = {"faraday_half", "tile_push", "list_push",   "append",
+                                                        "ampere",       "sort",      "other",       "esk_crossers"};
 
 void timing_begin(pic_ctx* c, int cls, cudaEvent_t* a) {
     nvtxRangePushA(kKernelClassNames[cls]);
@@ -164,6 +164,12 @@ bool window_moves_after(const pic_ctx* c, int64_t step) {
 }
 
 pic_status step_once(pic_ctx* c, double* rec, bool keep_j) {
+    if (c->deposit == PIC_DEPOSIT_ESIRKEPOV && c->shape == PIC_SHAPE_CIC) {
+        for (auto& s : c->species) {   // before the step changes anything
+            const pic_status st = reserve_esk_records(c, s);
+            if (st != PIC_OK) return st;
+        }
+    }
     c->jscale_J = c->jscale;
     const bool move = window_moves_after(c, c->step);
     pic_status st = launch_faraday_half(c, rec);

@@ -593,7 +593,7 @@ __device__ __forceinline__ int x_after1(const Geom& g, int gx) {
 // ---------------------------------------------------------------------------
 // Host side.
 
-enum KernelClass { KC_FARADAY = 0, KC_TILE_PUSH, KC_LIST_PUSH, KC_APPEND, KC_AMPERE, KC_SORT, KC_OTHER, KC_COUNT };
+enum KernelClass { KC_FARADAY = 0, KC_TILE_PUSH, KC_LIST_PUSH, KC_APPEND, KC_AMPERE, KC_SORT, KC_OTHER, KC_ESK, KC_COUNT };
 
 struct SpeciesDev {
     double q = 0, m = 0;
@@ -610,6 +610,9 @@ struct SpeciesDev {
     int* holes = nullptr;
     int* hist[2] = {nullptr, nullptr};    // per tile and block: particles per cell (TILE_CELLS ints)
     int* split_buf = nullptr;             // split tiles: output ranges (TILE_CELLS per tile), input counts
+    void* esk_buf = nullptr;              // Esirkepov's deposit: exported crosser records (push.cu)
+    int* esk_cnt = nullptr;               // their counts per tile and warp
+    int esk_wcap = 0;                     // records per tile and warp
     void* movers = nullptr;
     int mover_cap = 0;
     void* spill = nullptr;
@@ -735,6 +738,7 @@ pic_status cuda_fail(pic_ctx* c, cudaError_t e, const char* what);
 void timing_begin(pic_ctx* c, int cls, cudaEvent_t* a);
 void timing_end(pic_ctx* c, int cls, cudaEvent_t a);
 int64_t count_alive(pic_ctx* c, SpeciesDev& s, int64_t* spilled);
+pic_status reserve_esk_records(pic_ctx* c, SpeciesDev& s);
 
 #define GBPIC_CHECK(c, call)                                              \
     do {                                                                  \

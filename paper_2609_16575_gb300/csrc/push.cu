@@ -88,12 +88,21 @@ template <typename T> struct WarpQueue {
 // first whenever a kind's records would not fit; otherwise records accumulate until
 // the row's flush, so one drain pass adds the records of several particle steps.  With
 // Esirkepov's deposit the top of the queue's words holds the me stacked crosser
-// records (esk_stack), which lowers the capacity; they are processed first when even
+// records (esk_stack), which lowers the capacity; they are exported first when even
 // an empty queue would not hold a kind's records.
 template <typename T>
 __device__ __forceinline__ void q_drain(WarpQueue<T> Q, int& qn, int lane, uint32_t sJa, int qoff);
+// A warp's segment of the exported crosser records (Esirkepov's deposit): segment seg
+// of buf, cap records each (every particle the warp can step), n of them written
+// (warp-uniform).
+template <typename T> struct EskOut {
+    T* buf;
+    int cap;
+    int seg;
+    int n;
+};
 template <typename T>
-__device__ __forceinline__ void esk_process(WarpQueue<T> Q, int& me, int lane, uint32_t sJa);
+__device__ __forceinline__ void esk_flush(WarpQueue<T> Q, int& me, int lane, EskOut<T>& eo, Counters* ctr);
 constexpr int ESK_WORDS = 10;   // X1[3], X2[3], cw[3], packed first node
 constexpr int ESK_BATCH = 16;   // stacked crosser records per warp before they are processed
 static_assert(32 * ESK_WORDS <= QWORDS, "one particle step's crosser records fit in the record queue");
@@ -102,21 +111,21 @@ __device__ __forceinline__ int q_cap(int me) {
     return c < QCAP ? c : QCAP;
 }
 template <typename T, bool ESK>
-__device__ __forceinline__ void q_push(WarpQueue<T> Q, int& qn, int& me, bool want_a, int ka,
-                                       const typename Pair<T>::t va[6], bool want_b, int kb,
+__device__ __forceinline__ void q_push(WarpQueue<T> Q, int& qn, int& me, EskOut<T>& eo, Counters* ctr, bool want_a,
+                                       int ka, const typename Pair<T>::t va[6], bool want_b, int kb,
                                        const typename Pair<T>::t vb[6], int lane, uint32_t sJa, int qoff) {
     const unsigned ma = __ballot_sync(0xffffffffu, want_a), mb = ESK ? 0u : __ballot_sync(0xffffffffu, want_b);
     if (!(ma | mb)) return;
     const unsigned lt = (1u << lane) - 1u;
     if (qn + __popc(ma) > (ESK ? q_cap(me) : QCAP)) {
         q_drain(Q, qn, lane, sJa, qoff);
-        if (ESK && __popc(ma) > q_cap(me)) esk_process(Q, me, lane, sJa);
+        if (ESK && __popc(ma) > q_cap(me)) esk_flush(Q, me, lane, eo, ctr);
     }
     if (want_a) Q.put(qn + __popc(ma & lt), ka, va);
     qn += __popc(ma);
     if (qn + __popc(mb) > (ESK ? q_cap(me) : QCAP)) {
         q_drain(Q, qn, lane, sJa, qoff);
-        if (ESK && __popc(mb) > q_cap(me)) esk_process(Q, me, lane, sJa);
+        if (ESK && __popc(mb) > q_cap(me)) esk_flush(Q, me, lane, eo, ctr);
     }
     if (want_b) Q.put(qn + __popc(mb & lt), kb, vb);
     qn += __popc(mb);
@@ -241,100 +250,94 @@ template <> struct RowCells<2> {
     static __device__ __forceinline__ int key(const int c[2]) { return c[0] >= 0 ? c[0] : c[1]; }
 };
 
-// Esirkepov's deposit of the cell crossers (warp-collective).  A crosser's record
-// (positions relative to the first node of its support, cw, the first node and the
-// crossed dimensions packed) is stacked at the top of the warp's record-queue words,
-// record e at QWORDS - (e + 1) ESK_WORDS, beside the ZigZag-style records below; a
-// batch of up to ESK_BATCH records is processed at once: the non-zero stencil values of
-// all its records (20 of the 3x3x3 support's 54 for a move across one face; see
-// esk_value) are numbered consecutively and the 32 lanes take them in turn, so neither
-// a crosser forces the record queue to drain nor does a lone crosser leave most lanes
-// idle.
+// Esirkepov's deposit of the cell crossers.  A crosser's record (positions relative to
+// the first node of its support, cw, the first node and the crossed dimensions packed)
+// is stacked at the top of the warp's record-queue words, record e at
+// QWORDS - (e + 1) ESK_WORDS, beside the ZigZag-style records below, so that a crosser
+// does not force the record queue to drain; a batch of up to ESK_BATCH records is
+// copied at once to the warp's segment of the global record list, and k_esk_crossers
+// deposits the list after the tile kernel.  (Deposited inside the tile kernel, with the
+// batch's values spread over the lanes, the crossers had cost the kernel a third of its
+// time: the deposit ran at the kernel's low issue rate and its code crowded the
+// instruction cache.)
 template <typename T> __device__ __forceinline__ T* esk_rec(WarpQueue<T> Q, int e) {
     return Q.rec + QWORDS - (e + 1) * ESK_WORDS;
 }
-__device__ __forceinline__ void esk_counts(int pk, int& n0, int& n1, int& n2) {
-    const int cx = (pk >> 12) & 1, cy = (pk >> 13) & 1, cz = (pk >> 14) & 1;
-    // values of component c: (1 + crossed_c) edges x (2 + crossed_p) x (2 + crossed_r) nodes
-    n0 = (1 + cx) * (2 + cy) * (2 + cz);
-    n1 = (1 + cy) * (2 + cz) * (2 + cx);
-    n2 = (1 + cz) * (2 + cx) * (2 + cy);
-}
+// The stacked batch out of the queue words into the warp's export segment (the records
+// e = me - 1 .. 0 are contiguous words).  The segment holds every particle the warp can
+// step, so it cannot fill; a batch that would not fit (a broken launch) is dropped with
+// the overflow error bit.
 template <typename T>
-__device__ __forceinline__ void esk_process(WarpQueue<T> Q, int& me, int lane, uint32_t sJa) {
+__device__ __forceinline__ void esk_flush(WarpQueue<T> Q, int& me, int lane, EskOut<T>& eo, Counters* ctr) {
     __syncwarp();
-    int cnt = 0;
-    if (lane < me) {
-        int n0, n1, n2;
-        esk_counts(*reinterpret_cast<const int*>(esk_rec(Q, lane) + 9), n0, n1, n2);
-        cnt = n0 + n1 + n2;
-    }
-    int incl = cnt;
-#pragma unroll
-    for (int o = 1; o < 32; o <<= 1) {
-        const int y = __shfl_up_sync(0xffffffffu, incl, o);
-        if (lane >= o) incl += y;
-    }
-    const int excl = incl - cnt;
-    const int total = __shfl_sync(0xffffffffu, incl, 31);
-    for (int base = 0; base < total; base += 32) {
-        const int v = base + lane;
-        // the record holding value v: the last r < me with excl_r <= v
-        int r = 0;
-#pragma unroll
-        for (int st = 16; st > 0; st >>= 1) {
-            const int cand = r + st;
-            const int ec = __shfl_sync(0xffffffffu, excl, cand & 31);
-            if (cand < me && ec <= v) r = cand;
-        }
-        const int er = __shfl_sync(0xffffffffu, excl, r);
-        if (v >= total) continue;
-        const T* rec = esk_rec(Q, r);
-        const int pk = *reinterpret_cast<const int*>(rec + 9);
-        int n0, n1, n2;
-        esk_counts(pk, n0, n1, n2);
-        const int cx = (pk >> 12) & 1, cy = (pk >> 13) & 1, cz = (pk >> 14) & 1;
-        const int t = v - er;
-        int comp, q;
-        if (t < n0) {
-            comp = 0;
-            q = t;
-        } else if (t < n0 + n1) {
-            comp = 1;
-            q = t - n0;
-        } else {
-            comp = 2;
-            q = t - n0 - n1;
-        }
-        const int cp = comp == 0 ? cy : (comp == 1 ? cz : cx);   // the next dimension, cyclic
-        const int np_ = 2 + cp, nr = 2 + (comp == 0 ? cz : (comp == 1 ? cx : cy));
-        // q = (i np_ + jp) nr + jr with i < 2, jp < np_ <= 3, jr < nr <= 3 (no division:
-        // rem / 3 = (11 rem) >> 5 for rem < 9)
-        const int i = q >= np_ * nr ? 1 : 0, rem = q - i * np_ * nr;
-        const int jp = nr == 2 ? rem >> 1 : (rem * 11) >> 5, jr = rem - jp * nr;
-        const T X1[3] = {rec[0], rec[1], rec[2]}, X2[3] = {rec[3], rec[4], rec[5]}, c3w[3] = {rec[6], rec[7], rec[8]};
-        const T val = esk_value(X1, X2, c3w, comp, i, jp, jr);
-        if (val == T(0)) continue;
-        // the value's location: edge i along comp, node jp along the next dimension and
-        // jr along the one after (cyclic), from the support's first node
-        const int ax = comp == 0 ? i : (comp == 2 ? jp : jr);
-        const int ay = comp == 1 ? i : (comp == 0 ? jp : jr);
-        const int az = comp == 2 ? i : (comp == 1 ? jp : jr);
-        tile_add(sJa, tile_index(comp, (pk & 15) - 1 + ax, ((pk >> 4) & 15) - 1 + ay, ((pk >> 8) & 15) - 1 + az),
-                 JT_ELEMS, val);
+    if (eo.n + me <= eo.cap) {
+        const T* src = esk_rec(Q, me - 1);
+        T* dst = eo.buf + ((size_t)eo.seg * eo.cap + eo.n) * ESK_WORDS;
+        for (int j = lane; j < me * ESK_WORDS; j += 32) dst[j] = src[j];
+        eo.n += me;
+    } else if (lane == 0) {
+        atomicOr(&ctr->err, ERRB_OVERFLOW);
     }
     __syncwarp();
     me = 0;
 }
-// Stack the records of this particle step's crossers (mine), processing the stacked
+
+// Esirkepov's deposit of one exported crosser record into a shared J tile (one thread):
+// its non-zero values (along a dimension the move did not cross, the third node and the
+// second edge carry nothing: 20 of the 3x3x3 support's 54 for a move across one face),
+// in esk_value's arithmetic, with the node weights S0 and DS = S1 - S0 of each dimension
+// computed once for the record.
+template <typename T>
+__device__ __forceinline__ void esk_record(const T* rec, uint32_t sJa) {
+    const T X1[3] = {rec[0], rec[1], rec[2]}, X2[3] = {rec[3], rec[4], rec[5]};
+    const int pk = *reinterpret_cast<const int*>(rec + 9);
+    const int base = tile_index(0, (pk & 15) - 1, ((pk >> 4) & 15) - 1, ((pk >> 8) & 15) - 1);
+    const int crossed[3] = {(pk >> 12) & 1, (pk >> 13) & 1, (pk >> 14) & 1};
+    T s0[3][3], ds[3][3];
+#pragma unroll
+    for (int k = 0; k < 3; ++k)
+#pragma unroll
+        for (int j = 0; j < 3; ++j) {
+            s0[k][j] = cic_w(X1[k] - T(j));
+            ds[k][j] = cic_w(X2[k] - T(j)) - s0[k][j];
+        }
+    constexpr int stride[3] = {1, SJ, SJ * SJ};
+#pragma unroll
+    for (int comp = 0; comp < 3; ++comp) {
+        const int p = comp == 2 ? 0 : comp + 1, r = comp == 0 ? 2 : comp - 1;
+        const T cw = rec[6 + comp];
+        const int e0 = base + comp * SJ3;
+#pragma unroll
+        for (int jp = 0; jp < 3; ++jp) {
+            if (jp == 2 && !crossed[p]) continue;
+#pragma unroll
+            for (int jr = 0; jr < 3; ++jr) {
+                if (jr == 2 && !crossed[r]) continue;
+                const T t = s0[p][jp] * s0[r][jr] + T(0.5) * ds[p][jp] * s0[r][jr] + T(0.5) * s0[p][jp] * ds[r][jr] +
+                            ds[p][jp] * ds[r][jr] * T(1.0 / 3.0);
+                const int e = e0 + jp * stride[p] + jr * stride[r];
+                T acc = ds[comp][0] * t;
+                const T v0 = -cw * acc;
+                if (v0 != T(0)) tile_add(sJa, e, JT_ELEMS, v0);
+                if (crossed[comp]) {
+                    acc += ds[comp][1] * t;
+                    const T v1 = -cw * acc;
+                    if (v1 != T(0)) tile_add(sJa, e + stride[comp], JT_ELEMS, v1);
+                }
+            }
+        }
+    }
+}
+
+// Stack the records of this particle step's crossers (mine), exporting the stacked
 // batch first when it would grow past ESK_BATCH or meet the queued records.
 template <typename T>
-__device__ __forceinline__ void esk_stack(WarpQueue<T> Q, int& qn, int& me, int lane, uint32_t sJa, int qoff,
-                                          bool mine, int x, int y, int z, const T d1[3], const T d2[3], const int s[3],
-                                          const T cw[3]) {
+__device__ __forceinline__ void esk_stack(WarpQueue<T> Q, int& qn, int& me, EskOut<T>& eo, Counters* ctr, int lane,
+                                          uint32_t sJa, int qoff, bool mine, int x, int y, int z, const T d1[3], const T d2[3],
+                                          const int s[3], const T cw[3]) {
     const unsigned mc = __ballot_sync(0xffffffffu, mine);
     const int nn = __popc(mc);
-    if (me + nn > ESK_BATCH || qn * QS + (me + nn) * ESK_WORDS > QWORDS) esk_process(Q, me, lane, sJa);
+    if (me + nn > ESK_BATCH || qn * QS + (me + nn) * ESK_WORDS > QWORDS) esk_flush(Q, me, lane, eo, ctr);
     if (qn * QS + (me + nn) * ESK_WORDS > QWORDS) q_drain(Q, qn, lane, sJa, qoff);
     if (mine) {
         T* rec = esk_rec(Q, me + __popc(mc & ((1u << lane) - 1u)));
@@ -532,6 +535,7 @@ k_tile_push(const __grid_constant__ CUtensorMap tE0, const __grid_constant__ CUt
     const int qoff = slot_offset(lane < 12 ? lane : (lane < 24 ? lane - 12 : 0));
     int qn = 0;                   // queued records (warp-uniform)
     int me = 0;                   // stacked Esirkepov crosser records (warp-uniform)
+    EskOut<T> eo{A.esk_buf, A.esk_wcap, tile * NW + warp, 0};   // this warp's export segment
     const int seg = A.pa.seg_start[tile];   // slots of a block are below 2^31
     const int ngroups = (cnt + R - 1) / R;
     double kacc = 0.0;
@@ -699,10 +703,10 @@ k_tile_push(const __grid_constant__ CUtensorMap tE0, const __grid_constant__ CUt
 #pragma unroll
                 for (int q = 0; q < 6; ++q) acc[q] = Pair<T>::add(acc[q], v[q]);
             }
-            q_push<T, ESK>(Q, qn, me, active && !summed && !esk_cross, tile_index(0, x, y, z), v, !ESK && crossed,
+            q_push<T, ESK>(Q, qn, me, eo, A.ctr, active && !summed && !esk_cross, tile_index(0, x, y, z), v, !ESK && crossed,
                            tile_index(0, x + s[0], y + s[1], z + s[2]), v2, lane, sJa, qoff);
             if (ESK && __any_sync(0xffffffffu, esk_cross))
-                esk_stack<T>(Q, qn, me, lane, sJa, qoff, esk_cross, x, y, z, d1, d2, s, cw);
+                esk_stack<T>(Q, qn, me, eo, A.ctr, lane, sJa, qoff, esk_cross, x, y, z, d1, d2, s, cw);
             // movers: staged in shared memory with their wrapped global cell and written to
             // the global list in batches; a particle that left an open x face is removed
             // instead
@@ -735,10 +739,11 @@ k_tile_push(const __grid_constant__ CUtensorMap tE0, const __grid_constant__ CUt
             }
         }
         if (qn) q_drain(Q, qn, lane, sJa, qoff);   // the flush stages its sums in the queue
-        if (ESK && me) esk_process(Q, me, lane, sJa);
+        if (ESK && me) esk_flush(Q, me, lane, eo, A.ctr);
         flush_warp<T>(acc, key >= 0 ? tile_index(0, key & 7, (key >> 3) & 7, key >> 6) : -1, lane, Q, sJa, qoff);
     }
     if (mq) movers_flush(A, sM, mq, lane);
+    if (ESK && lane == 0) A.esk_cnt[(size_t)tile * NW + warp] = eo.n;
     left = __reduce_add_sync(0xffffffffu, left);
     esc = __reduce_add_sync(0xffffffffu, esc);
     if (lane == 0 && left) atomicAdd(SPLIT ? &A.pa.holes[tile] : &s_left, left);
@@ -759,6 +764,45 @@ k_tile_push(const __grid_constant__ CUtensorMap tE0, const __grid_constant__ CUt
     // flush the shared J tile to HBM (periodic wrap of the guard layers)
     tile_flush_j<T, NT>(A, sJ, s_gidx);
     if (RECK) block_add_double(kacc, A.krec);
+}
+
+// Esirkepov's deposit of the crossers a tile kernel exported: one CTA per tile, one
+// record per thread into a shared J tile of the tile kernel's layout, then the tile's
+// flush into HBM.  The counts it consumed are zeroed for the next step (a warp that
+// exports nothing writes no count).
+template <typename T>
+__global__ void __launch_bounds__(256) k_esk_crossers(PushArgs<T> A) {
+    constexpr int NW = Prec<T>::THREADS / 32;
+    extern __shared__ __align__(16) unsigned char sJc[];
+    __shared__ int s_pre[NW + 1];
+    __shared__ int s_gidx[3 * SJ];
+    const int tile = blockIdx.x;
+    int* cnt = A.esk_cnt + (size_t)tile * NW;
+    if (threadIdx.x == 0) {
+        int sum = 0;
+        for (int w = 0; w < NW; ++w) {
+            s_pre[w] = sum;
+            sum += min(cnt[w], A.esk_wcap);
+        }
+        s_pre[NW] = sum;
+    }
+    __syncthreads();
+    const int total = s_pre[NW];
+    if (total == 0) return;
+    for (int i = threadIdx.x; i < 2 * JT_ELEMS; i += blockDim.x) reinterpret_cast<unsigned*>(sJc)[i] = 0u;
+    const int ntx = A.g.nt[0], nty = A.g.nt[1];
+    const int tx = tile % ntx, ty = (tile / ntx) % nty, tz = tile / (ntx * nty);
+    tile_flush_index(A, tx * TILE, ty * TILE, tz * TILE, s_gidx);
+    if (threadIdx.x < NW) cnt[threadIdx.x] = 0;
+    __syncthreads();
+    const uint32_t sJa = smem_u32(sJc);
+    for (int k = threadIdx.x; k < total; k += blockDim.x) {
+        int w = 0;
+        while (w + 1 < NW && s_pre[w + 1] <= k) ++w;
+        esk_record(A.esk_buf + (((size_t)tile * NW + w) * A.esk_wcap + (k - s_pre[w])) * ESK_WORDS, sJa);
+    }
+    __syncthreads();
+    tile_flush_j<T, 256>(A, sJc, s_gidx);
 }
 
 // Before a step whose tiles are split over several CTAs: per tile, the output cell
@@ -1065,6 +1109,37 @@ static pic_status inject_t(pic_ctx* c, SpeciesDev& s, PushArgs<T>& A) {
     return PIC_OK;
 }
 
+// Esirkepov's crossers' export segments of species s, per tile and warp: every
+// particle the warp can step (its rows of 32 R slots of the largest tile capacity), so
+// that none can fill.  Reserved once, before the species' first Esirkepov step.
+template <typename T>
+static pic_status reserve_esk_t(pic_ctx* c, SpeciesDev& s) {
+    if (s.esk_buf) return PIC_OK;
+    constexpr int NWT = Prec<T>::THREADS / 32, ROW = 32 * Prec<T>::R;
+    int maxcap = 0;
+    for (int cap : s.h_cap) maxcap = std::max(maxcap, cap);
+    const int rows = (maxcap + ROW - 1) / ROW;
+    const int wcap = std::max(1, (rows + NWT - 1) / NWT) * ROW;
+    const size_t nseg = (size_t)c->g.nt[0] * c->g.nt[1] * c->g.nt[2] * NWT;
+    const size_t bytes = nseg * (size_t)wcap * ESK_WORDS * sizeof(T);
+    void* buf = dev_alloc(c, bytes);
+    int* cnt = buf ? static_cast<int*>(dev_alloc(c, nseg * sizeof(int))) : nullptr;
+    if (!cnt) {
+        if (buf) dev_free(c, buf);
+        c->err = "Esirkepov's deposit: no device memory for the crossers' records (" + std::to_string(bytes) + " bytes)";
+        return PIC_ERR_OOM;
+    }
+    GBPIC_CHECK(c, cudaMemsetAsync(cnt, 0, nseg * sizeof(int), c->stream));
+    s.esk_buf = buf;
+    s.esk_cnt = cnt;
+    s.esk_wcap = wcap;
+    return PIC_OK;
+}
+
+pic_status reserve_esk_records(pic_ctx* c, SpeciesDev& s) {
+    return c->prec == PIC_FP64 ? reserve_esk_t<double>(c, s) : reserve_esk_t<float>(c, s);
+}
+
 template <typename T>
 static pic_status push_species_t(pic_ctx* c, SpeciesDev& s, int parity, double* krec, int xshift, bool inject) {
     PushArgs<T> A = make_args<T>(c, s, parity, krec, 1.0);
@@ -1093,11 +1168,26 @@ static pic_status push_species_t(pic_ctx* c, SpeciesDev& s, int parity, double* 
             A.cnt_in = s.split_buf + (size_t)ntile * TILE_CELLS;
         }
     }
+    const int ntile_all = c->g.nt[0] * c->g.nt[1] * c->g.nt[2];
+    if (esk && !tsc && !s.esk_buf) {
+        c->err = "Esirkepov's deposit: the crossers' record list is not reserved";
+        return PIC_ERR_STATE;
+    }
+    if (esk) {
+        A.esk_buf = static_cast<T*>(s.esk_buf);
+        A.esk_cnt = s.esk_cnt;
+        A.esk_wcap = s.esk_wcap;
+    }
     if (tsc) {
         st = launch_tsc_push<T>(c, A, ids, rec);   // its tile step and spill-list step
     } else if (esk) {
         if (ids) st = rec ? launch_tile<T, true, true, true>(c, A) : launch_tile<T, true, false, true>(c, A);
         else st = rec ? launch_tile<T, false, true, true>(c, A) : launch_tile<T, false, false, true>(c, A);
+        if (st == PIC_OK) {
+            LaunchScope ls(c, KC_ESK);
+            k_esk_crossers<T><<<ntile_all, 256, 8 * JT_ELEMS, c->stream>>>(A);
+            GBPIC_CHECK(c, cudaGetLastError());
+        }
     } else if (A.parts > 1) {   // fewer tiles than SMs: several CTAs per tile
         if (ids) st = rec ? launch_tile<T, true, true, false, true>(c, A) : launch_tile<T, true, false, false, true>(c, A);
         else st = rec ? launch_tile<T, false, true, false, true>(c, A) : launch_tile<T, false, false, false, true>(c, A);

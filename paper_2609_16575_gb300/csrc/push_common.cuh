@@ -35,6 +35,12 @@ template <typename T> struct PushArgs {
     int parts;
     int* goff;
     int* cnt_in;
+    // Esirkepov's deposit: the crossers' records, exported by the tile kernel's warps
+    // (esk_wcap records per warp and tile, counts in esk_cnt) and deposited by
+    // k_esk_crossers
+    T* esk_buf;
+    int* esk_cnt;
+    int esk_wcap;
 };
 
 // Sum of one double per thread of the block, added to *dst by thread 0.

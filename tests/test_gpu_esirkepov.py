@@ -63,6 +63,31 @@ def test_esirkepov_hot_plasma(prec):
 
 
 @pytest.mark.parametrize("prec", [FP32, FP64])
+def test_esirkepov_relativistic_crossers(prec):
+    """A relativistic plasma (u_th = 1, 16 per cell: about 30 % of the particles cross a
+    face every step) for 4 cycles: the tile kernel's warps export every crosser's record
+    in batches and k_esk_crossers deposits them once per step, against the oracle."""
+    from paper_2609_16575_gb300 import gbpic
+
+    wl = W.thermal((16, 16, 8), 0.2, 16, 1.0, seed=103)
+    ctx, F, osp = _ctx(wl, prec, gbpic.PIC_DEPOSIT_ESIRKEPOV)
+    ctx.set_timing(True)
+    ctx.step(4)
+    kt = ctx.kernel_times()
+    assert kt["esk_crossers"][0] == 4
+    oracle.run(wl.n, wl.d, wl.dt, F, osp, 4, guide=ESK)
+    tol = 2e-5 if prec == FP32 else 1e-11
+    E, B, J = ctx.get_fields()
+    assert rel_err(E, F[0:3]) <= tol, rel_err(E, F[0:3])
+    assert rel_err(B, F[3:6]) <= tol, rel_err(B, F[3:6])
+    assert rel_err(J, F[6:9]) <= tol, rel_err(J, F[6:9])
+    P = ctx.get_particles(0)
+    assert np.abs(wrapped_diff(P[0:3], osp[0].P[0:3], wl.n)).max() <= (1e-4 if prec == FP32 else 1e-11)
+    assert rel_err(P[3:6], osp[0].P[3:6]) <= tol
+    ctx.close()
+
+
+@pytest.mark.parametrize("prec", [FP32, FP64])
 def test_esirkepov_spill_and_open_x(prec):
     """A fast beam into tiles that held nothing at load (the overflow is pushed from the
     spill list) leaving through the open face x = n: Esirkepov everywhere."""
