@@ -137,9 +137,14 @@ __device__ __forceinline__ void gather_tsc(FetchC Fc, int x, int y, int z, T dx,
 // over the nodes b .. b + i.  Add(comp, ox, oy, oz, v) receives each non-zero value v
 // (working precision, fixed-point units on the FP32 path) with the offsets of the
 // component's location from the start cell.
+// Along a dimension whose nearest node did not change (m1 = m2) the fourth node b + 3
+// carries neither weight (it lies 3/2 or more from both positions, where W2 and its
+// change vanish exactly), and the third edge carries the sum of the three weight
+// changes, zero but for rounding: both are skipped unless the nearest node changed.
 template <typename T, typename AddFn>
 __device__ __forceinline__ void esirkepov_tsc(AddFn Add, const T d1[3], const int s[3], const T d2[3], const T cw[3]) {
     int b[3];
+    bool wide[3];
     T S0[3][4], DS[3][4];
 #pragma unroll
     for (int k = 0; k < 3; ++k) {
@@ -150,6 +155,7 @@ __device__ __forceinline__ void esirkepov_tsc(AddFn Add, const T d1[3], const in
         const int m1 = X1 >= T(0.5) ? 1 : 0;
         const int m2 = (int)floor(X2 + T(0.5));
         b[k] = min(m1, m2) - 1;
+        wide[k] = m1 != m2;
 #pragma unroll
         for (int j = 0; j < 4; ++j) {
             const T r = X1 - T(b[k] + j);
@@ -161,15 +167,18 @@ __device__ __forceinline__ void esirkepov_tsc(AddFn Add, const T d1[3], const in
     for (int comp = 0; comp < 3; ++comp) {
         const int p = comp == 2 ? 0 : comp + 1, r = comp == 0 ? 2 : comp - 1;
 #pragma unroll
-        for (int jp = 0; jp < 4; ++jp)
+        for (int jp = 0; jp < 4; ++jp) {
+            if (jp == 3 && !wide[p]) continue;
 #pragma unroll
             for (int jr = 0; jr < 4; ++jr) {
+                if (jr == 3 && !wide[r]) continue;
                 const T t = S0[p][jp] * S0[r][jr] + T(0.5) * DS[p][jp] * S0[r][jr] + T(0.5) * S0[p][jp] * DS[r][jr] +
                             DS[p][jp] * DS[r][jr] * T(1.0 / 3.0);
                 if (t == T(0)) continue;
                 T acc = T(0);
 #pragma unroll
                 for (int i = 0; i < 3; ++i) {
+                    if (i == 2 && !wide[comp]) continue;
                     acc += DS[comp][i] * t;
                     const T v = -cw[comp] * acc;
                     if (v == T(0)) continue;
@@ -180,6 +189,7 @@ __device__ __forceinline__ void esirkepov_tsc(AddFn Add, const T d1[3], const in
                     Add(comp, o[0], o[1], o[2], v);
                 }
             }
+        }
     }
 }
 
@@ -189,24 +199,39 @@ __device__ __forceinline__ int tsc_j_index(int comp, int x, int y, int z) {
 }
 
 // Add v (fixed-point units) to a split 32-bit element of the J tile (the layout of
-// tile_add: lo word at e, hi word at NE + e, element = hi * 2^20 + lo).  A deposit
-// element here can receive more terms than the 4096 that keep the lo word below 2^32,
-// so the lo add returns the old word and a wrap carries 2^32 (2^12 units of 2^20) into
-// the hi word: the sum stays exact for any number of terms.
+// tile_add: lo word at e, hi word at NE + e, element = hi * 2^20 + lo, lo in [0, 2^20]
+// per term).  A deposit element here can receive more terms in one tile step than the
+// 4096 that keep a lo word below 2^32, so the tile kernel folds the lo words into the
+// hi words (tsc_fold) after every TSC_FOLD particles: at most TSC_FOLD terms reach a
+// word between two folds, and the adds stay reductions that return nothing.
+constexpr int TSC_FOLD_ITERS = 15;                        // loop iterations between folds
+constexpr int TSC_FOLD = TSC_FOLD_ITERS * TSC_THREADS;    // 3840 particles: lo < 2^20 (3841)
+static_assert(TSC_FOLD < 4095, "a lo word holds the terms between two folds");
 __device__ __forceinline__ void tsc_tile_add(unsigned* words, int e, float v) {
     const float hf = floorf(v * 9.5367431640625e-07f);   // v / 2^20
     const int hi = __float2int_rz(hf);
     const unsigned lo = (unsigned)__float2int_rn(__fmaf_rn(hf, -1048576.0f, v));
     // (the atomics are left to the compiler, without a memory clobber, so that the
     // independent adds of one particle overlap instead of waiting one by one)
-    const unsigned old = atomicAdd(words + e, lo);
-    const unsigned carry = (old + lo < old) ? 4096u : 0u;
-    atomicAdd(words + TSJ_ELEMS + e, (unsigned)hi + carry);
+    atomicAdd(words + e, lo);
+    atomicAdd(words + TSJ_ELEMS + e, (unsigned)hi);
 }
 __device__ __forceinline__ void tsc_tile_add(double* vals, int e, double v) { atomicAdd(vals + e, v); }
+// hi += lo >> 20, lo &= 2^20 - 1 for every element (block-wide, between barriers): the
+// element hi * 2^20 + lo keeps its value.
+__device__ __forceinline__ void tsc_fold(unsigned* words) {
+    for (int e = threadIdx.x; e < TSJ_ELEMS; e += TSC_THREADS) {
+        const unsigned lo = words[e];
+        if (lo >> 20) {
+            words[e] = lo & 0xFFFFFu;
+            words[TSJ_ELEMS + e] += lo >> 20;
+        }
+    }
+}
+__device__ __forceinline__ void tsc_fold(double*) {}
 
 template <typename T, bool IDS, bool RECK>
-__global__ void __launch_bounds__(TSC_THREADS) k_tsc_tile_push(PushArgs<T> A) {
+__global__ void __launch_bounds__(TSC_THREADS, sizeof(T) == sizeof(float) ? 2 : 1) k_tsc_tile_push(PushArgs<T> A) {
     extern __shared__ __align__(128) unsigned char smem_raw[];
     unsigned char* smem = reinterpret_cast<unsigned char*>((reinterpret_cast<uintptr_t>(smem_raw) + 127) & ~uintptr_t(127));
     using Acc = typename JTraits<T>::acc_t;
@@ -266,9 +291,19 @@ __global__ void __launch_bounds__(TSC_THREADS) k_tsc_tile_push(PushArgs<T> A) {
         const T* F = sF + comp * TSF3;
         return [F](int i, int j, int k) -> T { return F[((k + 1) * TSF + (j + 1)) * TSF + (i + 1)]; };
     };
-    // whole warps step together (the mover staging is a warp vote)
-    for (int i0 = (threadIdx.x & ~31); i0 < cnt; i0 += NT) {
-        const int i = i0 + lane;
+    // whole warps step together (the mover staging is a warp vote), and the whole block
+    // runs the same iterations (the FP32 tile's folds are block-wide)
+    int iter = 0;
+    for (int base = 0; base < cnt; base += NT) {
+        if constexpr (JTraits<T>::fixed) {
+            if (++iter > TSC_FOLD_ITERS) {
+                iter = 1;
+                __syncthreads();
+                tsc_fold(sJw);
+                __syncthreads();
+            }
+        }
+        const int i = base + threadIdx.x;
         const int p = seg + i;
         const int lc = i < cnt ? __ldcg(A.pa.cell + p) : HOLE;
         const bool active = lc >= 0;
