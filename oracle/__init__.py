@@ -371,15 +371,16 @@ def window_plasma(n, d, window, origin):
     return np.array(rows, dtype=np.float64).T
 
 
-def run_window(n, d, dt, F, species, nsteps, window, step0=0, laser=None, current_filter=None):
+def run_window(n, d, dt, F, species, nsteps, window, step0=0, laser=None, current_filter=None, guide=None):
     """``run`` with the moving window: after each cycle that ends with a move, the
     window shifts and species ``window["species"]`` receives the new column's plasma
-    (appended in the order of ``window_plasma``).  Returns the (nsteps, 3) energy
-    history."""
+    (appended in the order of ``window_plasma``).  ``guide`` is passed to ``run`` (the
+    deposit and shape options).  Returns the (nsteps, 3) energy history."""
     origin = window_moves_before(window, step0)
     diag = np.zeros((nsteps, 3))
     for s in range(step0, step0 + nsteps):
-        diag[s - step0] = run(n, d, dt, F, species, 1, step0=s, laser=laser, current_filter=current_filter)[0]
+        diag[s - step0] = run(n, d, dt, F, species, 1, step0=s, laser=laser, current_filter=current_filter,
+                              guide=guide)[0]
         if window_moves_after(window, s):
             window_shift(n, d, F, species)
             origin += 1

@@ -89,6 +89,38 @@ def test_window_follows_the_oracle(prec):
     ctx.close()
 
 
+@pytest.mark.parametrize("prec", [FP32, FP64])
+def test_window_with_esirkepov(prec):
+    """Esirkepov's deposit under the moving window: the crossers' records are exported in
+    the cycles that end with a move (every stored x cell drops by one) like in the
+    others; 30 cycles from the first move on, fields, J and every electron against the
+    oracle."""
+    from paper_2609_16575_gb300 import gbpic
+
+    wl = _mini_lwfa()
+    win = _window(wl, 0)
+    ctx = _gpu(wl, prec, win)
+    ctx.set_deposit(gbpic.PIC_DEPOSIT_ESIRKEPOV)
+    F, osp = _oracle(wl, prec)
+    ctx.step(30)
+    oracle.run_window(oracle_n(wl), wl.d, wl.dt, F, osp, 30, win, laser=wl.laser.as_tuple(), guide={"esirkepov": 1})
+    assert ctx.window_moves() == oracle.window_moves_before(win, 30) == 10
+    tol_f = 2e-4 if prec == FP32 else 1e-10
+    E, B, J = ctx.get_fields()
+    assert rel_err(E, F[0:3]) <= tol_f, ("E", rel_err(E, F[0:3]))
+    assert rel_err(B, F[3:6]) <= tol_f, ("B", rel_err(B, F[3:6]))
+    assert rel_err(J[..., :-1], F[6:9, ..., :-1]) <= tol_f, "J"
+    P = ctx.get_particles(0)
+    Q = osp[0].P
+    assert P.shape == Q.shape, (P.shape, Q.shape)
+    gone = Q[6] == 0.0
+    assert np.array_equal(np.isnan(P[6]), gone)
+    keep = ~gone
+    assert np.abs(P[0:3, keep] - Q[0:3, keep]).max() <= (1e-4 if prec == FP32 else 1e-11)
+    assert rel_err(P[3:6, keep], Q[3:6, keep]) <= tol_f
+    ctx.close()
+
+
 def test_window_plasma_fills_empty_tiles():
     """A window that starts over vacuum and moves every cycle into a plateau: after 40
     moves the whole front of the window holds the plateau lattice at rest, with the
