@@ -263,19 +263,24 @@ def cpu_baseline(spec, steps=10, n=32):
             "single_core": {"value": v1, "unit": UNIT, "cores": 1, "seconds": round(w1, 2)}}
 
 
-def time_steps(ctx, torch, steps):
-    """CUDA-event time (ms) of `steps` cycles on the context's stream."""
+def time_steps(ctx, torch, steps, kernels=True):
+    """CUDA-event time (ms) of `steps` cycles on the context's stream, with the library's
+    per-kernel times (kernels=True; per-launch events, and the cycles run launch by
+    launch) or without them (the library may then replay the cycles as a CUDA graph)."""
     torch.cuda.synchronize()
     st = torch.cuda.current_stream()
     a, b = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
-    ctx.set_timing(True)
-    ctx.kernel_times()
+    if kernels:
+        ctx.set_timing(True)
+        ctx.kernel_times()
     a.record(st)
     ctx.step(steps)
     b.record(st)
     torch.cuda.synchronize()
-    kt = ctx.kernel_times()
-    ctx.set_timing(False)
+    kt = {}
+    if kernels:
+        kt = ctx.kernel_times()
+        ctx.set_timing(False)
     return a.elapsed_time(b), kt
 
 
@@ -323,11 +328,12 @@ def other_workloads(torch, peak, peak_kind):
         ctx = gbpic.Context(wl.n, wl.d, wl.dt, precision=prec, rho_ion=wl.rho_ion)
         s = wl.species[0]
         ctx.load_species_array(s.q, s.m, s.P, True)
-        time_steps(ctx, torch, 5)
-        ms, _ = time_steps(ctx, torch, 200)
+        time_steps(ctx, torch, 10, kernels=False)
+        ms, _ = time_steps(ctx, torch, 200, kernels=False)
         out[f"cold_plasma_16_{name}"] = {"value": s.n * 200 / (ms / 1e3), "unit": UNIT, "steps": 200,
                                           "ms_per_step": ms / 200, "particles": s.n,
-                                          "note": "launch-bound: 32,768 particles fill 8 tiles"}
+                                          "note": "launch-bound: 32,768 particles fill 8 tiles; the cycles run as "
+                                                  "a replayed two-cycle CUDA graph"}
         ctx.close()
 
     # the laser wakefield: 1000 cycles first (the pulse peak, injected at t = 2 FWHM, has

@@ -283,7 +283,11 @@ pic_status pic_set_shape(pic_ctx* ctx, int32_t shape);
 pic_status pic_set_current_filter(pic_ctx* ctx, int32_t passes, int32_t compensate);
 
 /* Advance nsteps cycles (section 2.2, Fig. 2), asynchronously on the context's
- * stream.  J of the last cycle is kept for pic_get_fields and pic_diagnostics. */
+ * stream.  J of the last cycle is kept for pic_get_fields and pic_diagnostics.  In a
+ * periodic box without walls, laser, port or moving window, and with neither the energy
+ * history nor pic_set_timing on, a call of 6 or more cycles runs its middle cycles as a
+ * CUDA graph of two cycles captured once per call and launched repeatedly (the same
+ * kernels and results, fewer launch gaps); otherwise every kernel is launched directly. */
 pic_status pic_step(pic_ctx* ctx, int32_t nsteps);
 
 /* Wait for the context's stream; returns the first device-side error raised. */

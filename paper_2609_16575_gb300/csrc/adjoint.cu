@@ -802,22 +802,41 @@ static pic_status backward_t(pic_ctx* c, AdjointState& S, const double* Ed, cons
     }
     st = curl_to_e<double>(c, b.lE, b.lB, -h);
     if (st != PIC_OK) return st;
-    // segments in reverse: restore, recompute the states, adjoint steps backwards
+    // segments in reverse: restore, recompute the states, adjoint steps backwards.  A
+    // segment's recomputation and adjoint steps (some 16 launches per step) run as one
+    // captured CUDA graph when the capture succeeds (the host side of the segment runs
+    // while capturing; the graph of one segment is captured while the previous one runs)
     const int nseg = (int)S.ckpt.size();
     for (int sg = nseg - 1; sg >= 0; --sg) {
         const int a = sg * S.K, e = std::min(S.N, a + S.K);
         st = snap_restore(c, S.ckpt[sg]);
         if (st != PIC_OK) return st;
-        for (int n = a; n < e; ++n) {
-            st = snap_save(c, S.seg[n - a]);
-            if (st != PIC_OK) return st;
-            if (n < e - 1) {
-                st = step_once(c, nullptr, false);
-                if (st != PIC_OK) return st;
+        auto segment = [&]() -> pic_status {
+            for (int n = a; n < e; ++n) {
+                pic_status r = snap_save(c, S.seg[n - a]);
+                if (r != PIC_OK) return r;
+                if (n < e - 1) {
+                    r = step_once(c, nullptr, false);
+                    if (r != PIC_OK) return r;
+                }
             }
-        }
-        for (int n = e - 1; n >= a; --n) {
-            st = adjoint_step_t<T>(c, b, S.seg[n - a]);
+            for (int n = e - 1; n >= a; --n) {
+                const pic_status r = adjoint_step_t<T>(c, b, S.seg[n - a]);
+                if (r != PIC_OK) return r;
+            }
+            return PIC_OK;
+        };
+        const int64_t step0 = c->step, launches0 = c->launches;
+        std::vector<int> cur0;
+        for (auto& sp : c->species) cur0.push_back(sp.cur);
+        bool done = false;
+        st = run_as_graph(c, segment, &done);
+        if (st != PIC_OK) return st;
+        if (!done) {   // the capture failed: the host state back, the segment launched directly
+            c->step = step0;
+            c->launches = launches0;
+            for (size_t i = 0; i < c->species.size(); ++i) c->species[i].cur = cur0[i];
+            st = segment();
             if (st != PIC_OK) return st;
         }
     }

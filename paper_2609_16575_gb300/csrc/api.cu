@@ -239,6 +239,42 @@ void put_doubles(std::vector<unsigned char>& b, const double* p, size_t n) {
 }
 }  // namespace
 
+namespace gbpic {
+
+pic_status run_as_graph(pic_ctx* c, const std::function<pic_status()>& body, bool* done) {
+    *done = false;
+    if (!c->capture_stream && cudaStreamCreateWithFlags(&c->capture_stream, cudaStreamNonBlocking) != cudaSuccess) {
+        cudaGetLastError();
+        c->capture_stream = nullptr;
+        return PIC_OK;
+    }
+    cudaStream_t run_stream = c->stream;
+    c->stream = c->capture_stream;
+    cudaGraph_t graph = nullptr;
+    bool ok = cudaStreamBeginCapture(c->stream, cudaStreamCaptureModeThreadLocal) == cudaSuccess;
+    if (ok) {
+        ok = body() == PIC_OK;
+        ok = cudaStreamEndCapture(c->stream, &graph) == cudaSuccess && ok;
+    }
+    c->stream = run_stream;
+    cudaGraphExec_t exec = nullptr;
+    ok = ok && graph && cudaGraphInstantiate(&exec, graph, 0) == cudaSuccess;
+    if (graph) cudaGraphDestroy(graph);
+    if (!ok) {
+        cudaGetLastError();
+        if (exec) cudaGraphExecDestroy(exec);
+        c->err.clear();
+        return PIC_OK;
+    }
+    const cudaError_t e = cudaGraphLaunch(exec, c->stream);
+    cudaGraphExecDestroy(exec);   // freed once its launch completes
+    if (e != cudaSuccess) return cuda_fail(c, e, "cudaGraphLaunch");
+    *done = true;
+    return PIC_OK;
+}
+
+}  // namespace gbpic
+
 extern "C" {
 
 const char* pic_status_string(pic_status s) {
@@ -409,6 +445,71 @@ pic_status pic_load_species(pic_ctx* c, const pic_species_desc* d, int32_t* spec
     return PIC_OK;
 }
 
+// Whether the cycles of pic_step can run as a replayed two-cycle CUDA graph: nothing
+// in a cycle's launches may depend on the step number beyond its parity (the particle
+// blocks and the parity return to their state after two cycles), and no host work may
+// come between cycles.  The laser, the port, the walls and the moving window change
+// with time; the energy history and the per-kernel timing record host-side per cycle.
+constexpr int GRAPH_MIN_PAIRS = 2;   // fewer pairs do not repay the capture
+static bool graph_cycles(const pic_ctx* c) {
+    return !c->timing && !c->hist && !c->g.open_x && !c->laser_on && !c->port_on && !c->pec_y && !c->pec_z &&
+           !c->window_on && !c->species.empty();
+}
+
+// `pairs` pairs of cycles as one captured graph of two cycles, launched `pairs` times
+// on the context's stream.  The capture runs on a stream of its own (the legacy default
+// stream, torch's, cannot be captured; nothing runs while capturing, so the graph needs
+// no link to it).  Capturing runs the host side of both cycles (step count, block
+// parity), so each further launch advances the host state by two cycles as step_once
+// would.  When the capture or the instantiation fails, the host state is put back and
+// *done is false: the caller steps directly.
+static pic_status step_pairs(pic_ctx* c, int pairs, bool* done) {
+    *done = false;
+    if (c->step_graph) {
+        cudaGraphExecDestroy(c->step_graph);   // freed once its launches in flight complete
+        c->step_graph = nullptr;
+    }
+    if (!c->capture_stream && cudaStreamCreateWithFlags(&c->capture_stream, cudaStreamNonBlocking) != cudaSuccess) {
+        cudaGetLastError();
+        c->capture_stream = nullptr;
+        return PIC_OK;
+    }
+    const int64_t launches0 = c->launches, step0 = c->step;
+    std::vector<int> cur0;
+    for (auto& sp : c->species) cur0.push_back(sp.cur);
+    cudaStream_t run_stream = c->stream;
+    c->stream = c->capture_stream;
+    cudaGraph_t graph = nullptr;
+    bool ok = cudaStreamBeginCapture(c->stream, cudaStreamCaptureModeThreadLocal) == cudaSuccess;
+    if (ok) {
+        ok = step_once(c, nullptr, false) == PIC_OK && step_once(c, nullptr, false) == PIC_OK;
+        ok = cudaStreamEndCapture(c->stream, &graph) == cudaSuccess && ok;
+    }
+    c->stream = run_stream;
+    ok = ok && graph && cudaGraphInstantiate(&c->step_graph, graph, 0) == cudaSuccess;
+    if (graph) cudaGraphDestroy(graph);
+    if (!ok) {
+        cudaGetLastError();
+        if (c->step_graph) cudaGraphExecDestroy(c->step_graph);
+        c->step_graph = nullptr;
+        c->step = step0;
+        c->launches = launches0;
+        for (size_t i = 0; i < c->species.size(); ++i) c->species[i].cur = cur0[i];
+        c->err.clear();
+        return PIC_OK;
+    }
+    const int64_t per_pair = c->launches - launches0;
+    for (int k = 0; k < pairs; ++k) {
+        if (k > 0) {
+            c->step += 2;
+            c->launches += per_pair;
+        }
+        GBPIC_CHECK(c, cudaGraphLaunch(c->step_graph, c->stream));
+    }
+    *done = true;
+    return PIC_OK;
+}
+
 pic_status pic_step(pic_ctx* c, int32_t nsteps) {
     if (!c || nsteps < 0) return PIC_ERR_ARG;
     if (nsteps == 0) return PIC_OK;
@@ -423,7 +524,20 @@ pic_status pic_step(pic_ctx* c, int32_t nsteps) {
             GBPIC_CHECK(c, cudaMemsetAsync(c->J[k], 0, sizeof(long long) * (size_t)c->g.N, c->stream));
         c->j_dirty = false;
     }
+    // launch-bound runs (many short cycles) save the launches' latency as a graph: the
+    // first cycle runs directly (it makes any first-use allocation), the middle ones in
+    // graph pairs, the last directly (it keeps J for pic_get_fields)
+    const int pairs = graph_cycles(c) && nsteps >= 2 + 2 * GRAPH_MIN_PAIRS ? (nsteps - 2) / 2 : 0;
     for (int s = 0; s < nsteps; ++s) {
+        if (s == 1 && pairs > 0) {
+            bool done = false;
+            const pic_status st = step_pairs(c, pairs, &done);
+            if (st != PIC_OK) return st;
+            if (done) {
+                s += 2 * pairs - 1;
+                continue;
+            }
+        }
         double* rec = nullptr;
         if (c->hist && c->step % c->desc.record_every == 0) {
             rec = c->hist + 3 * (c->hist_written % c->hist_cap);
@@ -915,6 +1029,8 @@ void pic_destroy(pic_ctx* c) {
     if (!c) return;
     DeviceScope dscope_(c->desc.device);
     if (c->stream) cudaStreamSynchronize(c->stream);
+    if (c->step_graph) cudaGraphExecDestroy(c->step_graph);
+    if (c->capture_stream) cudaStreamDestroy(c->capture_stream);
     adjoint_free(c);
     for (auto& p : c->pending) {
         cudaEventDestroy(p.a);

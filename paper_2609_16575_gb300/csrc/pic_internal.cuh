@@ -7,6 +7,7 @@
 #include <cuda_runtime.h>
 #include <stdint.h>
 
+#include <functional>
 #include <string>
 #include <vector>
 
@@ -698,6 +699,8 @@ struct pic_ctx {
     int deposit = 0;                    // pic_deposit: ZigZag or Esirkepov
     int shape = 1;                      // pic_shape: CIC (1) or quadratic TSC (2)
     int wait_polls = -1;                // tile kernel staging wait limit (negative: MBAR_MAX_POLLS)
+    cudaGraphExec_t step_graph = nullptr;   // the last two-cycle graph of pic_step (api.cu)
+    cudaStream_t capture_stream = nullptr;  // the stream that graph is captured on
 };
 
 namespace gbpic {
@@ -739,6 +742,11 @@ void timing_begin(pic_ctx* c, int cls, cudaEvent_t* a);
 void timing_end(pic_ctx* c, int cls, cudaEvent_t a);
 int64_t count_alive(pic_ctx* c, SpeciesDev& s, int64_t* spilled);
 pic_status reserve_esk_records(pic_ctx* c, SpeciesDev& s);
+// Captures the work that body enqueues on c->stream as a CUDA graph (on a stream of the
+// context's own: the legacy default stream cannot be captured) and launches it once on
+// c->stream.  *done is false when the capture or instantiation failed and nothing was
+// launched; body's host-side effects then remain for the caller to undo.
+pic_status run_as_graph(pic_ctx* c, const std::function<pic_status()>& body, bool* done);
 
 #define GBPIC_CHECK(c, call)                                              \
     do {                                                                  \

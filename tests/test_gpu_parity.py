@@ -182,3 +182,38 @@ def test_segments_stay_grouped_by_cell(prec):
     # a random order would descend about half the time; u_th = 0.2 moves ~15 % of the
     # particles to another cell per step
     assert descents <= 0.2 * Q.shape[1], (descents, Q.shape[1])
+
+
+@pytest.mark.parametrize("prec", [FP32, FP64])
+@pytest.mark.parametrize("deposit", [0, 1])
+def test_graph_replayed_cycles_match_direct_steps(prec, deposit):
+    """pic_step runs the middle cycles of a long call as a replayed two-cycle CUDA graph
+    (periodic box, no history or timing): 13 cycles in one call against 13 calls of one
+    cycle (no graph), on a grid of fewer tiles than SMs (split tiles) with a fifth of the
+    particles crossing a face per step.  The runs agree to the path's rounding (the order
+    of a cell's particles in its range, hence the grouping of their FP32 partial sums or
+    of the FP64 atomic additions, varies from run to run): 1e-5 / 1e-12 of each array's
+    maximum.  The launch count and the step count advance as for direct steps."""
+    from paper_2609_16575_gb300 import gbpic
+
+    wl = W.thermal((24, 16, 16), 0.2, 8, 0.3, seed=41)
+    wl.E, wl.B = plane_wave_fields(wl.n, wl.d, wl.dt)
+    out = []
+    for calls in ((13,), (1,) * 13):
+        ctx = gbpic.Context(wl.n, wl.d, wl.dt, precision=prec, rho_ion=wl.rho_ion, track_ids=True)
+        ctx.set_deposit(deposit)
+        ctx.set_fields(wl.E, wl.B)
+        ctx.load_species_array(-1.0, 1.0, wl.species[0].P, False)
+        l0 = ctx.launch_count()
+        for k in calls:
+            ctx.step(k)
+        d = ctx.diagnostics()
+        out.append((ctx.get_fields(), ctx.get_particles(0), ctx.launch_count() - l0, d["step"]))
+        ctx.close()
+    (Fa, Pa, La, Sa), (Fb, Pb, Lb, Sb) = out
+    assert Sa == Sb == 13 and La == Lb
+    tol = 1e-5 if prec == FP32 else 1e-12
+    for a, b in zip(Fa, Fb):
+        assert rel_err(a, b) <= tol
+    assert np.abs(wrapped_diff(Pa[0:3], Pb[0:3], wl.n)).max() <= tol * max(wl.n)
+    assert rel_err(Pa[3:6], Pb[3:6]) <= tol
