@@ -793,6 +793,9 @@ def run_gbpic(args):
                 h.copy_(t)
             torch.cuda.synchronize()
             Xh, Uh, wh = (h.numpy() for h in host)
+            # the library allocates through torch's caching allocator: start it from the
+            # state of a fresh process (its cache of the earlier runs' blocks released)
+            torch.cuda.empty_cache()
             if dist is not None and not turns:
                 dist.barrier()
             torch.cuda.synchronize()
