@@ -22,6 +22,7 @@ import hashlib
 import json
 import multiprocessing
 import os
+import re
 import statistics
 import subprocess
 import sys
@@ -84,11 +85,18 @@ def peaks():
         return 6800.0, "fallback"
 
 
-def kernel_source_hash():
+_C_TOKENS = re.compile(r'"(?:\\.|[^"\\])*"|//[^\n]*|/\*.*?\*/', re.S)
+
+
+def kernel_source_hash(root=None):
+    """Hash of the tile kernel's source with comments dropped and whitespace collapsed:
+    a committed ncu capture stays valid across comment and layout edits."""
     h = hashlib.sha256()
     for name in ("push.cu", "push_common.cuh", "pic_internal.cuh"):
-        with open(os.path.join(ROOT, "paper_2609_16575_gb300", "csrc", name), "rb") as f:
-            h.update(f.read())
+        with open(os.path.join(root or ROOT, "paper_2609_16575_gb300", "csrc", name)) as f:
+            text = f.read()
+        code = _C_TOKENS.sub(lambda m: m.group(0) if m.group(0).startswith('"') else " ", text)
+        h.update(" ".join(code.split()).encode())
     return h.hexdigest()[:16]
 
 

@@ -768,8 +768,8 @@ k_tile_push(const __grid_constant__ CUtensorMap tE0, const __grid_constant__ CUt
 
 // Esirkepov's deposit of the crossers a tile kernel exported: one CTA per tile, one
 // record per thread into a shared J tile of the tile kernel's layout, then the tile's
-// flush into HBM.  The counts it consumed are zeroed for the next step (a warp that
-// exports nothing writes no count).
+// flush into HBM.  The counts it consumed are zeroed for the next step (a tile kernel
+// CTA that leaves early, on an empty tile or a staging timeout, writes no counts).
 template <typename T>
 __global__ void __launch_bounds__(256) k_esk_crossers(PushArgs<T> A) {
     constexpr int NW = Prec<T>::THREADS / 32;
