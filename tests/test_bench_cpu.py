@@ -65,3 +65,29 @@ def test_host_memory_and_cores_are_positive(bench):
     """The end-to-end leg's host-memory check and the oracle baseline's core count."""
     assert bench.host_memory_available() > 0
     assert bench.host_cores() >= 1
+
+
+def test_kernel_source_hash_ignores_comments_but_not_code(bench, tmp_path):
+    """The hash that guards the committed traffic figures: a comment or layout edit of the
+    tile kernel's sources keeps it, any code edit (a string literal included) changes it,
+    and the committed traffic files carry the hash of the current source."""
+    csrc = tmp_path / "paper_2609_16575_gb300" / "csrc"
+    csrc.mkdir(parents=True)
+    src = {n: open(os.path.join(ROOT, "paper_2609_16575_gb300", "csrc", n)).read()
+           for n in ("push.cu", "push_common.cuh", "pic_internal.cuh")}
+
+    def hash_of(files):
+        for n, t in files.items():
+            (csrc / n).write_text(t)
+        return bench.kernel_source_hash(str(tmp_path))
+
+    h0 = hash_of(src)
+    assert h0 == bench.kernel_source_hash()
+    edited = dict(src, **{"push.cu": "// a new comment line\n" + src["push.cu"].replace("\n", "\n\n", 3) +
+                          "\n/* a block\n   comment */\n"})
+    assert hash_of(edited) == h0
+    assert hash_of(dict(src, **{"push.cu": src["push.cu"] + "\nint extra_symbol;\n"})) != h0
+    assert hash_of(dict(src, **{"pic_internal.cuh": src["pic_internal.cuh"].replace('"', '" ', 1)})) != h0
+    for name in ("tile_push_stress256.json", "tile_push_thermal128.json"):
+        with open(os.path.join(ROOT, "profiles", name)) as f:
+            assert json.load(f)["source_sha"] == h0
