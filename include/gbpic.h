@@ -332,7 +332,8 @@ pic_status pic_get_history(pic_ctx* ctx, double* out, int32_t max_records, int32
 
 /* Per-kernel timing with CUDA events on the context's stream.  enable = 1 starts
  * accumulating; pic_kernel_times returns, for up to max entries, the kernel class
- * name, number of launches and total milliseconds.  Synchronises. */
+ * name, number of launches and total milliseconds.  Synchronises.  While timing is on,
+ * pic_step launches every kernel directly (no graph replay: one event pair per launch). */
 pic_status pic_set_timing(pic_ctx* ctx, int32_t enable);
 pic_status pic_kernel_times(pic_ctx* ctx, int32_t max, const char** names, int64_t* launches, double* ms,
                             int32_t* count);
